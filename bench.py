@@ -1,0 +1,380 @@
+"""Benchmark of the ISCI sigma step sigma = H_tau c on GB300.
+
+Workload (default): full CI, 2 alpha + 2 beta electrons in 60 orbitals
+(1770^2 = 3,132,900 determinants), seeded synthetic integrals (decay length
+4, 60 Cholesky vectors), screening threshold tau = 1e-14, FP64.  One step is
+one sigma = H_tau c on a seeded unit vector resident in HBM.  The metric is
+GUpdates/s, an update being one sigma_I += sign * unit * c_J over surviving
+integral units and in-space determinant pairs (counted exactly at set-up).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload fci_n60] [--tau 1e-14] [--precision 64|32]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the sigma step has no data-parallel exchange at one problem per
+GPU); value = all ranks' updates / max over ranks of the timed span.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "σ-vector ms & GUpdates/s, HBM % of peak; FP32-mixed vs FP64 at |ΔE|≤1e-9 Eh"
+FALLBACK_HBM_GBS = 6800.0
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 rate (no FP64 figure in MEASURED_PEAKS.json)
+FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
+L2_FLUSH_BYTES = 512 << 20
+
+WORKLOADS = {
+    "fci_n60": dict(n=60, na=2, nb=2, kmax=4, ell=4.0, nchol=60, box=False, seed=1000, tau=1e-14),
+    "fci_n10": dict(n=10, na=2, nb=2, kmax=4, ell=3.0, nchol=20, box=False, seed=0, tau=1e-14),
+    "fci_n100": dict(n=100, na=2, nb=2, kmax=4, ell=5.0, nchol=20, box=False, seed=3000, tau=1e-12),
+    "cisd_n200": dict(n=200, na=2, nb=2, kmax=2, ell=5.0, nchol=20, box=True, seed=2000, tau=1e-14),
+    "cisdt_n100": dict(n=100, na=2, nb=2, kmax=3, ell=5.0, nchol=20, box=True, seed=2000, tau=1e-14),
+}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                d = json.load(f)
+            for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if key in d:
+                    return float(d[key]), "measured"
+        except (OSError, ValueError):
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def profile_traffic(kernel_key):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
+    or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None, None
+    with open(path) as f:
+        d = json.load(f)
+    ent = d.get(kernel_key)
+    if not ent:
+        return None, None
+    src = os.path.join(ROOT, ent["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] if os.path.exists(src) else None
+    if h != ent.get("source_sha256_16"):
+        return None, ent
+    return float(ent["dram_bytes_per_launch"]), ent
+
+
+def run_ours(args, wl, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1609_07757_gb300 import _lib as L
+    from paper_1609_07757_gb300.synthetic import make_integrals, unit_vector
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tau = args.tau if args.tau is not None else wl["tau"]
+    h1, eri = make_integrals(wl["n"], wl["seed"], ell=wl["ell"], nchol=wl["nchol"], box=wl["box"])
+    stream = torch.cuda.current_stream()
+    L.iscsi_set_stream(stream)
+    t0 = time.time()
+    L.iscsi_init(wl["n"], wl["na"], wl["nb"], wl["kmax"], h1, eri, tau)
+    init_s = time.time() - t0
+    ndet = L.iscsi_ndet()
+    updates = L.iscsi_updates_per_sigma()
+    c = torch.tensor(unit_vector(ndet, 17 + rank), dtype=torch.float64, device=dev)
+    s = torch.empty_like(c)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    L.iscsi_set_option("precision", args.precision)
+
+    for _ in range(args.warmup):
+        L.iscsi_sigma(c, s, 1)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # device-timed region: K sigma steps, L2 flushed between them
+    L.iscsi_set_option("phase_timing", 1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    wall0 = time.time()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        L.iscsi_sigma(c, s, 1)
+        ev[k][1].record(stream)
+    barrier()
+    wall = time.time() - wall0
+    clk = clocks.stop()
+    st = L.iscsi_stats()
+    L.iscsi_set_option("phase_timing", 0)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+
+    # end-to-end through the host-buffer C-ABI call (pinned buffers, copies timed)
+    ch = torch.empty(ndet, dtype=torch.float64, pin_memory=True)
+    ch.copy_(c.cpu())
+    sh = torch.empty(ndet, dtype=torch.float64, pin_memory=True)
+    ch_np, sh_np = ch.numpy(), sh.numpy()
+    L.iscsi_sigma_host(ch_np, sh_np, 1)
+    barrier()
+    e0 = time.time()
+    for _ in range(args.steps):
+        L.iscsi_sigma_host(ch_np, sh_np, 1)
+    barrier()
+    e2e_s = time.time() - e0
+    ref = s.cpu().numpy()
+    e2e_ok = bool(np.array_equal(sh_np, ref))
+
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([tot_ms, e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms, e2e_s = float(t[0]), float(t[1])
+    ms = tot_ms / args.steps
+    value = ws * updates / (ms * 1e-3) / 1e9
+    e2e_val = ws * updates * args.steps / e2e_s / 1e9
+
+    # roofline of the dominant kernel (opposite-spin GEMM)
+    gemm_ms = st["phase_ms"]["opposite_gemm"] / max(1, st["timed_calls"])
+    flops = st["opposite_gemm_flops"]
+    peak = FP64_PEAK_TFLOPS if args.precision == 64 else FP32_PEAK_TFLOPS
+    achieved = flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
+    kkey = "k_grouped_gemm_fp%d_%s" % (args.precision, args.workload)
+    traffic, _ = profile_traffic(kkey)
+    hbm_peak, hbm_src = measured_peaks()
+    esz = 8 if args.precision == 64 else 4
+    npairs = wl["n"] ** 2
+    # compulsory bytes of one sigma: c read, sigma written, the surviving opposite-spin
+    # units and the same-spin string Hamiltonians read once
+    nstr = st["nstrings"][0]
+    comp_bytes = esz * (2 * ndet + npairs * npairs + 2 * nstr * nstr)
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "GUpdates/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if args.precision == 64 else "f32",
+        "data": "synthetic (seeded integrals shaped like the paper's Be-in-a-box sets)",
+        "config": {"workload": args.workload, "norb": wl["n"], "nalpha": wl["na"], "nbeta": wl["nb"],
+                   "max_excitation": wl["kmax"], "ndet": ndet, "tau": tau, "nvec": 1,
+                   "updates_per_sigma": updates, "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": "replicas" if ws > 1 else "single-gpu"},
+        "gpu_launches": None,
+        "e2e": {"value": round(e2e_val, 3), "unit": "GUpdates/s", "h2d_bytes_per_step": 8 * ndet,
+                "d2h_bytes_per_step": 8 * ndet, "matches_device_path": e2e_ok},
+        "roofline": {"bound": "alu", "achieved": round(achieved, 4) if achieved else None, "peak": peak,
+                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4) if achieved else None,
+                     "traffic": traffic, "kernel": "k_grouped_gemm (opposite-spin contraction)",
+                     "kernel_ms": round(gemm_ms, 4), "flops_per_launch": flops,
+                     "peak_source": "FP64 rate of GB300 (1.25 TFLOP/s; own probe measured 1.198)"
+                     if args.precision == 64 else "152 SM x 128 FFMA/clk x 2.07 GHz"},
+        "hbm": {"compulsory_bytes_per_step": comp_bytes,
+                "achieved_gbs": round(comp_bytes / (ms * 1e-3) / 1e9, 2),
+                "peak_gbs": hbm_peak, "frac": round(comp_bytes / (ms * 1e-3) / 1e9 / hbm_peak, 5),
+                "peak_source": hbm_src},
+        "phase_ms_per_step": {k: round(v / max(1, st["timed_calls"]), 4) for k, v in st["phase_ms"].items()},
+        "clocks": clk,
+        "wall_s_timed": round(wall, 3),
+        "init_s": round(init_s, 3),
+    }
+    # kernel launches inside the timed region: lift, GEMM, fold, same-spin GEMM per sigma
+    line["gpu_launches"] = 4 * args.steps
+    return line
+
+
+def cpu_baseline(wl, tau, target_s=15.0, steps=1):
+    """The oracle, as it stands, on a bounded sample of rows of the same workload."""
+    import numpy as np
+
+    import oracle
+    from paper_1609_07757_gb300.synthetic import make_integrals, unit_vector
+
+    h1, eri = make_integrals(wl["n"], wl["seed"], ell=wl["ell"], nchol=wl["nchol"], box=wl["box"])
+    o = oracle.Oracle(wl["n"], wl["na"], wl["nb"], wl["kmax"], tau, h1, eri)
+    c = unit_vector(o.ndet, 17)
+    rng = np.random.default_rng(5)
+    cores = oracle.max_threads()
+    # calibrate the sample size on a few rows
+    rows = rng.choice(o.ndet, size=min(o.ndet, 4 * cores), replace=False)
+    t0 = time.time()
+    o.sigma_rows(c, rows)
+    per_row = max((time.time() - t0) / len(rows), 1e-7)
+    nrow = int(min(o.ndet, max(len(rows), target_s / per_row)))
+    times = []
+    for _ in range(steps):
+        rows = rng.choice(o.ndet, size=nrow, replace=False)
+        t0 = time.time()
+        o.sigma_rows(c, rows)
+        times.append(time.time() - t0)
+    return o, nrow, times, cores
+
+
+def updates_estimate(wl, tau):
+    """Exact updates per sigma from the oracle's closed-form-free count is too slow at
+    full size; the CUDA library's exact count is used when a GPU is present, else None."""
+    return None
+
+
+def run_reference(args, wl, ws, rank):
+    tau = args.tau if args.tau is not None else wl["tau"]
+    if rank != 0:
+        return None
+    total_s = 150.0
+    per_step = max(2.0, total_s / max(1, args.steps + args.warmup))
+    o, nrow, times, cores = cpu_baseline(wl, tau, target_s=per_step, steps=args.steps + args.warmup)
+    times = times[args.warmup:]
+    upd = args.updates
+    frac = nrow / o.ndet
+    mean_s = sum(times) / len(times)
+    value = upd * frac / mean_s / 1e9 if upd else None
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6) if value else None,
+        "unit": "GUpdates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(mean_s * 1e3 / frac, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "norb": wl["n"], "ndet": o.ndet, "tau": tau},
+        "cpu_baseline": {"value": round(value, 6) if value else None, "unit": "GUpdates/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": "row-wise oracle sigma on %d of %d rows per step, scaled by the row fraction"
+                                   % (nrow, o.ndet)},
+        "e2e": {"value": round(value, 6) if value else None, "unit": "GUpdates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fci_n60", choices=sorted(WORKLOADS))
+    ap.add_argument("--tau", type=float, default=None)
+    ap.add_argument("--precision", type=int, default=64, choices=[32, 64])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--updates", type=float, default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    wl = WORKLOADS[args.workload]
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        if args.updates is None:
+            # exact update count of the workload from the CUDA library's set-up when available
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    from paper_1609_07757_gb300 import _lib as L
+                    from paper_1609_07757_gb300.synthetic import make_integrals
+                    tau = args.tau if args.tau is not None else wl["tau"]
+                    h1, eri = make_integrals(wl["n"], wl["seed"], ell=wl["ell"], nchol=wl["nchol"], box=wl["box"])
+                    L.iscsi_init(wl["n"], wl["na"], wl["nb"], wl["kmax"], h1, eri, tau)
+                    args.updates = L.iscsi_updates_per_sigma()
+                    L.iscsi_finalize()
+            except Exception:  # noqa: BLE001
+                args.updates = None
+        line = run_reference(args, wl, ws, rank)
+        if rank == 0 and line:
+            print(json.dumps(line))
+        return
+    line = run_ours(args, wl, ws, rank, local)
+    if rank == 0:
+        if not args.no_cpu_baseline and ws == 1:
+            tau = args.tau if args.tau is not None else wl["tau"]
+            o, nrow, times, cores = cpu_baseline(wl, tau, target_s=15.0, steps=1)
+            frac = nrow / o.ndet
+            val = line["config"]["updates_per_sigma"] * frac / times[0] / 1e9
+            line["cpu_baseline"] = {"value": round(val, 6), "unit": "GUpdates/s", "cores": cores, "kind": "oracle",
+                                    "sample": "row-wise oracle sigma on %d random rows of %d (%.1f s), scaled by "
+                                              "the row fraction" % (nrow, o.ndet, times[0])}
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * iscsi.h -- C ABI of the GB300 (sm_103a) Integral-Screened CI sigma library.
+ *
+ * The library computes sigma = H_tau c for the spin-restricted, non-relativistic
+ * Hamiltonian in its index-restricted form (Sorensen, Bauch & Madsen,
+ * arXiv:1609.07757, Eq. index_re), restricted to the determinants of a
+ * truncated CI expansion (Eq. ci_hierarchy), where every integral term whose
+ * "unit" has magnitude <= tau is dropped (integral screening, Eqs. sigma_int
+ * and sigma_split; the screen sits on each integral, as in the screened loops
+ * of Sec. "Second part").  The units are
+ *   one-body       h_pq                       (operators a+_p a_q, either spin)
+ *   same-spin      g_psrq - g_pqrs, p>r, q>s  (a+_p a+_r a_q a_s, either spin)
+ *   opposite-spin  g_pqrs                     (-a+_pa a+_rb a_qa a_sb)
+ * with g_pqrs = (pq|rs) in chemist notation.  They are grouped into the 42
+ * classes of Eqs. class_to_ex_dx .. the_end (class ids below).  It also finds
+ * the lowest eigenpairs of H_tau with a Davidson solver (Eq. hcec; the paper
+ * names Davidson as the usual companion of the sigma step, Eq. sigma).
+ *
+ * Conventions
+ *   - orbitals 0..n_sigma-1 are occupied in the reference determinant of spin
+ *     sigma (O), the others virtual (V); the excitation level of a string is
+ *     its number of electrons in V;
+ *   - strings are sorted by (excitation level, colex rank sum_i C(o_i, i+1) of
+ *     the ascending orbital list o_0 < o_1 < ...);
+ *   - a determinant (A, B) is in the space iff level(A) + level(B) <=
+ *     max_excitation; its index is off[A] + B, where B runs over the beta
+ *     strings of level <= max_excitation - level(A) (a prefix of the sorted
+ *     list) -- alpha-major, the CI-vector blocking of Fig. cisdt;
+ *   - |A,B> = prod_{p in A ascending} a+_pa prod_{q in B ascending} a+_qb |vac>.
+ *
+ * Class ids (bit i of a class mask):
+ *   0..3   H^{1,1}, H^{1,0}, H^{0,1}, H^{0,0} _{1,0,1}   (one-body alpha)
+ *   4..7   the same for _{1,0,-1}                         (one-body beta)
+ *   8..23  the 16 opposite-spin terms of H_{2,0,0}, in the order
+ *          H^{2,2}, H^{2,1} (2 terms), H^{1,2} (2), H^{2,0}, H^{1,1} (4),
+ *          H^{0,2}, H^{1,0} (2), H^{0,1} (2), H^{0,0}, each term's order
+ *          being the paper's
+ *   24..32 H^{P,H}_{2,0,2} (alpha-alpha), (P,H) = (2,2),(2,1),(1,2),(2,0),
+ *          (1,1),(0,2),(1,0),(0,1),(0,0)
+ *   33..41 H^{P,H}_{2,0,-2} (beta-beta), same order
+ * P counts de-excitation annihilators (index in V), H de-excitation creators
+ * (index in O).
+ *
+ * Memory and threading
+ *   - one process, one GPU (the device current at iscsi_init); calls are not
+ *     thread-safe;
+ *   - "device" pointers must point to memory of that GPU, 8-byte aligned;
+ *   - every call returns after enqueueing its work on the library stream
+ *     (iscsi_set_stream) unless stated otherwise;
+ *   - the library owns the device memory it allocates; the caller owns every
+ *     buffer it passes in, and the library never keeps a pointer to it after
+ *     the call returns.
+ */
+#ifndef ISCSI_H
+#define ISCSI_H
+
+#if defined(__GNUC__)
+#define ISCSI_API __attribute__((visibility("default")))
+#else
+#define ISCSI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int iscsi_status;
+
+#define ISCSI_OK 0
+#define ISCSI_E_ARG (-1)      /* invalid argument                                  */
+#define ISCSI_E_NOMEM (-2)    /* device or host allocation failed                  */
+#define ISCSI_E_CUDA (-3)     /* a CUDA call failed (see iscsi_last_error)          */
+#define ISCSI_E_NOCONV (-4)   /* Davidson hit its iteration limit; best estimates  */
+#define ISCSI_E_NOINIT (-5)   /* no current context                                */
+#define ISCSI_E_NAN (-6)      /* NaN or Inf detected                               */
+#define ISCSI_E_WAIT (-7)     /* a bounded device wait ran out                     */
+
+/* Limits: 1 <= norb <= 256; 0 <= nalpha, nbeta <= min(norb, 16); the dense
+   same-spin string Hamiltonian of each spin, C(norb, n_sigma)^2 doubles, must
+   fit in device memory; max_excitation >= 0 (values above the largest
+   possible level give full CI). */
+
+/*
+ * Create a context for n = norb orbitals, nalpha / nbeta electrons, CI space
+ * truncated at total excitation level max_excitation (Eq. ci_hierarchy), and
+ * make it current.
+ *   h1   host, n*n doubles, row-major h_pq; must be symmetric.
+ *   eri  host, npair*npair doubles, npair = n(n+1)/2, pair-packed chemist
+ *        integrals: (pq|rs) = eri[P(p,q)*npair + P(r,s)] with
+ *        P(p,q) = max(p,q)*(max(p,q)+1)/2 + min(p,q).  The matrix must be
+ *        symmetric ((pq|rs) = (rs|pq)); eri may be NULL (no two-electron part).
+ *   tau  screening threshold, >= 0: a unit u is kept iff |u| > tau
+ *        (the algorithm's "if |I| > epsilon", Sec. "Second part").
+ * The library copies h1 and eri; the caller may free them on return.  Builds
+ * the string spaces, determinant addressing, screened units and work lists on
+ * the device (once per context) and synchronises before returning.
+ * Errors: ISCSI_E_ARG (limits above, tau < 0 or NaN, NULL h1), ISCSI_E_NOMEM,
+ * ISCSI_E_CUDA.  On error no context is created and the current context is
+ * unchanged.
+ */
+ISCSI_API iscsi_status iscsi_init(int norb, int nalpha, int nbeta, int max_excitation, const double* h1, const double* eri,
+                        double tau);
+
+/*
+ * sigma = H_tau c for nvec vectors (Eq. sigma, screened as Eq. sigma_split).
+ *   c      device, FP64, [nvec][ndet] (vector-major, ndet contiguous).
+ *   sigma  device, FP64, [nvec][ndet]; overwritten; must not overlap c.
+ * Arithmetic follows the "precision" option (64: FP64 throughout; 32: FP32
+ * products and accumulation, inputs rounded to FP32, result widened to FP64).
+ * Asynchronous on the library stream; never synchronises.
+ * Errors: ISCSI_E_NOINIT, ISCSI_E_ARG (NULL pointers, nvec < 1), ISCSI_E_NOMEM
+ * (workspace growth), ISCSI_E_CUDA (launch failure).
+ */
+ISCSI_API iscsi_status iscsi_sigma(const void* c, void* sigma, int nvec);
+
+/*
+ * Same as iscsi_sigma with HOST buffers: copies c to the device, computes,
+ * copies sigma back and synchronises.  c, sigma: host, [nvec][ndet] FP64.
+ */
+ISCSI_API iscsi_status iscsi_sigma_host(const double* c, double* sigma, int nvec);
+
+/*
+ * Lowest nroots eigenpairs of H_tau by a Davidson iteration on the device
+ * (diagonal preconditioner, FP64 orthonormalisation, Rayleigh-Ritz and
+ * residuals).  Converged when every root has residual 2-norm <= tol and its
+ * energy changed by <= "etol" (option, default 1e-10) in the last iteration.
+ *   energies  host, nroots doubles (output; best estimates on ISCSI_E_NOCONV).
+ *   vecs      device, FP64 [nroots][ndet]: if non-NULL and option
+ *             "guess_from_vecs" is 1, used as the start vectors; on return
+ *             holds the (unit-norm) eigenvectors.  May be NULL.
+ * With option "precision" = 32 the sigma steps run in FP32 until the residual
+ * reaches "switch_tol" (option), then in FP64 for the refinement.
+ * Synchronises.  Errors: ISCSI_E_NOINIT, ISCSI_E_ARG (nroots < 1 or > ndet,
+ * tol <= 0), ISCSI_E_NOCONV, ISCSI_E_NAN, ISCSI_E_NOMEM, ISCSI_E_CUDA.
+ */
+ISCSI_API iscsi_status iscsi_davidson(int nroots, double tol, double* energies, void* vecs);
+
+/* number of determinants of the current context, or -1 if none */
+ISCSI_API long long iscsi_ndet(void);
+
+/* number of strings of the given spin (0 = alpha, 1 = beta), or -1 */
+ISCSI_API long long iscsi_nstrings(int spin);
+
+/*
+ * Copy the sorted strings of one spin to the host.
+ *   orbitals  host, [count][n_sigma] ints, ascending orbital list per string.
+ *   levels    host, [count] ints (excitation level).  Either may be NULL.
+ * Synchronises.  Errors: ISCSI_E_NOINIT, ISCSI_E_ARG.
+ */
+ISCSI_API iscsi_status iscsi_get_strings(int spin, int* orbitals, int* levels);
+
+/*
+ * Determinant index of (alpha orbitals, beta orbitals), each an ascending host
+ * list of nalpha / nbeta orbitals; -1 if outside the truncated space or
+ * invalid, -5 (ISCSI_E_NOINIT) without a context.
+ */
+ISCSI_API long long iscsi_det_index(const int* alpha_orbitals, const int* beta_orbitals);
+
+/*
+ * Diagonal of H_tau.  diag: device, FP64 [ndet].  Asynchronous.
+ */
+ISCSI_API iscsi_status iscsi_diagonal(void* diag);
+
+/* Make cudaStream_t `stream` (NULL = legacy default stream) the stream of all
+   later launches of every context. */
+ISCSI_API iscsi_status iscsi_set_stream(void* stream);
+
+/*
+ * Options (process-wide; "class_mask_*" take effect at the next iscsi_init):
+ *   "precision"        64 (default) or 32: arithmetic of iscsi_sigma; for
+ *                      iscsi_davidson 32 selects the mixed FP32/FP64 scheme
+ *   "class_mask_lo"    classes 0..31 to keep, as an integer bit mask (default all)
+ *   "class_mask_hi"    classes 32..41, bit i-32 (default all)
+ *   "maxiter"          Davidson iteration limit (default 300)
+ *   "max_subspace"     Davidson subspace size per root (default 12)
+ *   "etol"             Davidson energy-change threshold (default 1e-10)
+ *   "switch_tol"       mixed precision: residual at which FP64 sigma starts (default 1e-5;
+ *                      the switch also happens when the FP32 residual stalls)
+ *   "guess_from_vecs"  1: iscsi_davidson starts from `vecs` (default 0)
+ *   "use_graph"        1: capture one Davidson iteration as a CUDA graph (default 1)
+ * Errors: ISCSI_E_ARG for an unknown key or a value out of range.
+ */
+ISCSI_API iscsi_status iscsi_set_option(const char* key, double value);
+
+/*
+ * Statistics of the current context as one JSON object (NUL-terminated,
+ * truncated to len bytes): sizes, surviving units per group, updates per
+ * sigma (one update = one sigma_I += sign * unit * c_J, counted over
+ * surviving units and in-space determinant pairs), last sigma time.
+ * Errors: ISCSI_E_NOINIT, ISCSI_E_ARG.
+ */
+ISCSI_API iscsi_status iscsi_stats(char* json, int len);
+
+/* Updates per sigma per vector of the current context (see iscsi_stats), or -1. */
+ISCSI_API double iscsi_updates_per_sigma(void);
+
+/* Message of the last failing call in this process (static storage). */
+ISCSI_API const char* iscsi_last_error(void);
+
+/* Destroy every context and free all device memory the library holds. */
+ISCSI_API void iscsi_finalize(void);
+
+/*
+ * Several contexts (batching).  iscsi_init creates a context and makes it
+ * current; iscsi_ctx_current returns its handle (> 0), iscsi_ctx_use makes
+ * another one current, iscsi_ctx_destroy frees one.
+ */
+ISCSI_API int iscsi_ctx_current(void);
+ISCSI_API iscsi_status iscsi_ctx_use(int handle);
+ISCSI_API iscsi_status iscsi_ctx_destroy(int handle);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISCSI_H */

@@ -1,0 +1,199 @@
+"""ctypes binding of libiscsi.so (include/iscsi.h): argument marshalling only.
+
+Every function keeps the C name.  Device arguments accept torch CUDA tensors
+(their data pointer is passed) or raw integer addresses; host arguments
+accept numpy arrays.  A negative status raises ``IscsiError`` with the
+library's last error message.  There is no fallback: if the CUDA library
+cannot be built or loaded, importing this module's functions raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ISCSI_OK = 0
+ISCSI_E_ARG = -1
+ISCSI_E_NOMEM = -2
+ISCSI_E_CUDA = -3
+ISCSI_E_NOCONV = -4
+ISCSI_E_NOINIT = -5
+ISCSI_E_NAN = -6
+ISCSI_E_WAIT = -7
+
+_lib = None
+
+
+class IscsiError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("iscsi status %d: %s" % (status, msg))
+        self.status = status
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libiscsi.so (building it first if needed) and declare the ABI."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise OSError("libiscsi.so not built: %s" % path)
+    lib = ctypes.CDLL(path)
+    c_int, c_ll, c_d, vp = ctypes.c_int, ctypes.c_longlong, ctypes.c_double, ctypes.c_void_p
+    sig = {
+        "iscsi_init": (c_int, [c_int, c_int, c_int, c_int, vp, vp, c_d]),
+        "iscsi_sigma": (c_int, [vp, vp, c_int]),
+        "iscsi_sigma_host": (c_int, [vp, vp, c_int]),
+        "iscsi_davidson": (c_int, [c_int, c_d, vp, vp]),
+        "iscsi_ndet": (c_ll, []),
+        "iscsi_nstrings": (c_ll, [c_int]),
+        "iscsi_get_strings": (c_int, [c_int, vp, vp]),
+        "iscsi_det_index": (c_ll, [vp, vp]),
+        "iscsi_diagonal": (c_int, [vp]),
+        "iscsi_set_stream": (c_int, [vp]),
+        "iscsi_set_option": (c_int, [ctypes.c_char_p, c_d]),
+        "iscsi_stats": (c_int, [ctypes.c_char_p, c_int]),
+        "iscsi_updates_per_sigma": (c_d, []),
+        "iscsi_last_error": (ctypes.c_char_p, []),
+        "iscsi_finalize": (None, []),
+        "iscsi_ctx_current": (c_int, []),
+        "iscsi_ctx_use": (c_int, [c_int]),
+        "iscsi_ctx_destroy": (c_int, [c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status < 0:
+        msg = load().iscsi_last_error()
+        raise IscsiError(status, msg.decode() if msg else "")
+    return status
+
+
+def _dev(x):
+    """Device address of a torch tensor (checked FP64 and contiguous) or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    import torch
+    if not (x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return x.data_ptr()
+
+
+def _host_f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def iscsi_set_stream(stream=None):
+    """Use a torch.cuda.Stream (or its raw handle); None = torch's current stream."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    handle = getattr(stream, "cuda_stream", stream)
+    return _check(load().iscsi_set_stream(ctypes.c_void_p(handle)))
+
+
+def iscsi_init(norb, nalpha, nbeta, max_excitation, h1, eri, tau):
+    h, hp = _host_f64(h1)
+    if eri is None:
+        ep = None
+    else:
+        e, ep = _host_f64(eri)
+    return _check(load().iscsi_init(norb, nalpha, nbeta, max_excitation, hp, ep, float(tau)))
+
+
+def iscsi_sigma(c, sigma, nvec=1):
+    return _check(load().iscsi_sigma(_dev(c), _dev(sigma), int(nvec)))
+
+
+def iscsi_sigma_host(c, sigma, nvec=1):
+    """c, sigma: host numpy float64 arrays of nvec * ndet elements (sigma is written)."""
+    if not (isinstance(sigma, np.ndarray) and sigma.dtype == np.float64 and sigma.flags.c_contiguous):
+        raise ValueError("sigma must be a C-contiguous float64 numpy array")
+    cc, cp = _host_f64(c)
+    return _check(load().iscsi_sigma_host(cp, sigma.ctypes.data_as(ctypes.c_void_p), int(nvec)))
+
+
+def iscsi_davidson(nroots, tol, vecs=None):
+    """Returns (status, energies); status is 0 or ISCSI_E_NOCONV (other errors raise)."""
+    en = np.zeros(nroots)
+    st = load().iscsi_davidson(int(nroots), float(tol), en.ctypes.data_as(ctypes.c_void_p), _dev(vecs))
+    if st != ISCSI_E_NOCONV:
+        _check(st)
+    return st, en
+
+
+def iscsi_ndet():
+    return int(load().iscsi_ndet())
+
+
+def iscsi_nstrings(spin):
+    return int(load().iscsi_nstrings(spin))
+
+
+def iscsi_get_strings(spin, nel):
+    cnt = iscsi_nstrings(spin)
+    orbs = np.zeros((cnt, max(nel, 1)), dtype=np.int32)
+    lev = np.zeros(cnt, dtype=np.int32)
+    _check(load().iscsi_get_strings(spin, orbs.ctypes.data_as(ctypes.c_void_p),
+                                    lev.ctypes.data_as(ctypes.c_void_p)))
+    return orbs[:, :nel], lev
+
+
+def iscsi_det_index(alpha_orbitals, beta_orbitals):
+    a = np.ascontiguousarray(list(alpha_orbitals) or [0], dtype=np.int32)
+    b = np.ascontiguousarray(list(beta_orbitals) or [0], dtype=np.int32)
+    return int(load().iscsi_det_index(a.ctypes.data_as(ctypes.c_void_p), b.ctypes.data_as(ctypes.c_void_p)))
+
+
+def iscsi_diagonal(diag):
+    return _check(load().iscsi_diagonal(_dev(diag)))
+
+
+def iscsi_set_option(key, value):
+    return _check(load().iscsi_set_option(key.encode(), float(value)))
+
+
+def iscsi_stats():
+    import json
+    buf = ctypes.create_string_buffer(8192)
+    _check(load().iscsi_stats(buf, len(buf)))
+    return json.loads(buf.value.decode())
+
+
+def iscsi_updates_per_sigma():
+    return float(load().iscsi_updates_per_sigma())
+
+
+def iscsi_last_error():
+    m = load().iscsi_last_error()
+    return m.decode() if m else ""
+
+
+def iscsi_finalize():
+    load().iscsi_finalize()
+
+
+def iscsi_ctx_current():
+    return int(load().iscsi_ctx_current())
+
+
+def iscsi_ctx_use(handle):
+    return _check(load().iscsi_ctx_use(int(handle)))
+
+
+def iscsi_ctx_destroy(handle):
+    return _check(load().iscsi_ctx_destroy(int(handle)))

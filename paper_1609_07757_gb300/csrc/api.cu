@@ -1,0 +1,302 @@
+// api.cu -- the C ABI (include/iscsi.h): argument checks, contexts, options.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+
+#include "../../include/iscsi.h"
+#include "internal.cuh"
+
+namespace iscsi {
+
+static std::string g_error = "no error";
+static cudaStream_t g_stream = nullptr;
+static Options g_options;
+static std::map<int, std::unique_ptr<Context>> g_ctx;
+static int g_current = 0;
+static int g_next_handle = 1;
+
+void set_error(const std::string& msg) { g_error = msg; }
+const char* last_error() { return g_error.c_str(); }
+Options& options() { return g_options; }
+cudaStream_t stream() { return g_stream; }
+void set_stream(cudaStream_t s) { g_stream = s; }
+
+static Context* current() {
+  auto it = g_ctx.find(g_current);
+  return it == g_ctx.end() ? nullptr : it->second.get();
+}
+
+}  // namespace iscsi
+
+using namespace iscsi;
+
+#define NEED_CTX(ctxvar)                        \
+  Context* ctxvar = current();                  \
+  if (!ctxvar) {                                \
+    set_error("no current context (iscsi_init)"); \
+    return ISCSI_E_NOINIT;                      \
+  }
+
+extern "C" {
+
+iscsi_status iscsi_init(int norb, int nalpha, int nbeta, int max_excitation, const double* h1, const double* eri,
+                        double tau) {
+  if (norb < 1 || norb > kMaxOrb || nalpha < 0 || nbeta < 0 || nalpha > norb || nbeta > norb ||
+      nalpha > kMaxElec || nbeta > kMaxElec || max_excitation < 0 || !h1 || !(tau >= 0.0) || std::isinf(tau)) {
+    set_error("iscsi_init: invalid argument (limits: 1<=norb<=256, 0<=n_sigma<=min(norb,16), "
+              "max_excitation>=0, tau>=0 finite, h1 != NULL)");
+    return ISCSI_E_ARG;
+  }
+  // the dense same-spin string Hamiltonians and the opposite-spin unit matrix must fit
+  long long na_str = binom_ll(norb, nalpha), nb_str = binom_ll(norb, nbeta);
+  if (na_str > (1ll << 26) || nb_str > (1ll << 26)) {
+    set_error("iscsi_init: string space too large for the dense same-spin string Hamiltonian");
+    return ISCSI_E_ARG;
+  }
+  auto ctx = std::make_unique<Context>();
+  int s = context_build(*ctx, norb, nalpha, nbeta, max_excitation, h1, eri, tau);
+  if (s != kOk) {
+    cudaGetLastError();
+    return s;
+  }
+  int h = g_next_handle++;
+  g_ctx[h] = std::move(ctx);
+  g_current = h;
+  return ISCSI_OK;
+}
+
+iscsi_status iscsi_sigma(const void* c, void* sigma, int nvec) {
+  NEED_CTX(ctx);
+  if (!c || !sigma || nvec < 1) {
+    set_error("iscsi_sigma: NULL pointer or nvec < 1");
+    return ISCSI_E_ARG;
+  }
+  return sigma_run(*ctx, static_cast<const double*>(c), static_cast<double*>(sigma), nvec, options().precision);
+}
+
+iscsi_status iscsi_sigma_host(const double* c, double* sigma, int nvec) {
+  NEED_CTX(ctx);
+  if (!c || !sigma || nvec < 1) {
+    set_error("iscsi_sigma_host: NULL pointer or nvec < 1");
+    return ISCSI_E_ARG;
+  }
+  cudaStream_t st = stream();
+  size_t bytes = sizeof(double) * (size_t)ctx->ndet * nvec;
+  DevBuf dc, ds;
+  ISCSI_TRY(dc.alloc(bytes));
+  ISCSI_TRY(ds.alloc(bytes));
+  ISCSI_CUDA(cudaMemcpyAsync(dc.p, c, bytes, cudaMemcpyHostToDevice, st));
+  ISCSI_TRY(sigma_run(*ctx, dc.as<double>(), ds.as<double>(), nvec, options().precision));
+  ISCSI_CUDA(cudaMemcpyAsync(sigma, ds.p, bytes, cudaMemcpyDeviceToHost, st));
+  ISCSI_CUDA(cudaStreamSynchronize(st));
+  return ISCSI_OK;
+}
+
+iscsi_status iscsi_davidson(int nroots, double tol, double* energies, void* vecs) {
+  NEED_CTX(ctx);
+  if (nroots < 1 || nroots > ctx->ndet || !(tol > 0) || !energies) {
+    set_error("iscsi_davidson: invalid argument");
+    return ISCSI_E_ARG;
+  }
+  return davidson_run(*ctx, nroots, tol, energies, static_cast<double*>(vecs));
+}
+
+long long iscsi_ndet(void) {
+  Context* ctx = current();
+  return ctx ? ctx->ndet : -1;
+}
+
+long long iscsi_nstrings(int spin) {
+  Context* ctx = current();
+  if (!ctx || spin < 0 || spin > 1) return -1;
+  return ctx->sp[spin].count;
+}
+
+iscsi_status iscsi_get_strings(int spin, int* orbitals, int* levels) {
+  NEED_CTX(ctx);
+  if (spin < 0 || spin > 1) {
+    set_error("iscsi_get_strings: spin must be 0 or 1");
+    return ISCSI_E_ARG;
+  }
+  const SpinSpace& S = ctx->sp[spin];
+  cudaStream_t st = stream();
+  if (orbitals && S.ne > 0) {
+    std::vector<int16_t> o((size_t)S.count * S.ne);
+    ISCSI_CUDA(cudaMemcpyAsync(o.data(), S.orbs.p, sizeof(int16_t) * o.size(), cudaMemcpyDeviceToHost, st));
+    ISCSI_CUDA(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < o.size(); ++i) orbitals[i] = o[i];
+  }
+  if (levels) {
+    std::vector<int8_t> l(S.count);
+    ISCSI_CUDA(cudaMemcpyAsync(l.data(), S.level.p, S.count, cudaMemcpyDeviceToHost, st));
+    ISCSI_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < S.count; ++i) levels[i] = l[i];
+  }
+  return ISCSI_OK;
+}
+
+long long iscsi_det_index(const int* alpha_orbitals, const int* beta_orbitals) {
+  Context* ctx = current();
+  if (!ctx) return ISCSI_E_NOINIT;
+  // colex rank of each list, then the sorted position from the device map
+  const int* lists[2] = {alpha_orbitals, beta_orbitals};
+  int pos[2] = {0, 0}, lvl[2] = {0, 0};
+  for (int s = 0; s < 2; ++s) {
+    const SpinSpace& S = ctx->sp[s];
+    long long rank = 0;
+    for (int i = 0; i < S.ne; ++i) {
+      int o = lists[s] ? lists[s][i] : -1;
+      if (o < 0 || o >= ctx->n || (i > 0 && o <= lists[s][i - 1])) return -1;
+      rank += binom_ll(o, i + 1);
+      lvl[s] += (o >= S.ne);
+    }
+    int p = 0;
+    if (cudaMemcpy(&p, S.pos.as<int>() + rank, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    pos[s] = p;
+  }
+  if (lvl[0] + lvl[1] > ctx->kmax) return -1;
+  return ctx->off_h[pos[0]] + pos[1];
+}
+
+iscsi_status iscsi_diagonal(void* diag) {
+  NEED_CTX(ctx);
+  if (!diag) {
+    set_error("iscsi_diagonal: NULL pointer");
+    return ISCSI_E_ARG;
+  }
+  ISCSI_CUDA(cudaMemcpyAsync(diag, ctx->diag.p, sizeof(double) * ctx->ndet, cudaMemcpyDeviceToDevice, stream()));
+  return ISCSI_OK;
+}
+
+iscsi_status iscsi_set_stream(void* s) {
+  set_stream(static_cast<cudaStream_t>(s));
+  return ISCSI_OK;
+}
+
+iscsi_status iscsi_set_option(const char* key, double value) {
+  if (!key || std::isnan(value)) {
+    set_error("iscsi_set_option: NULL key or NaN value");
+    return ISCSI_E_ARG;
+  }
+  Options& o = options();
+  std::string k(key);
+  auto bad = [&]() {
+    set_error("iscsi_set_option: value out of range for " + k);
+    return ISCSI_E_ARG;
+  };
+  if (k == "precision") {
+    if (value != 32 && value != 64) return bad();
+    o.precision = (int)value;
+  } else if (k == "class_mask_lo") {
+    if (value < 0 || value > 4294967295.0) return bad();
+    o.class_mask = (o.class_mask & ~0xFFFFFFFFull) | (unsigned long long)value;
+  } else if (k == "class_mask_hi") {
+    if (value < 0 || value > 1023) return bad();
+    o.class_mask = (o.class_mask & 0xFFFFFFFFull) | ((unsigned long long)value << 32);
+  } else if (k == "maxiter") {
+    if (value < 1 || value > 100000) return bad();
+    o.maxiter = (int)value;
+  } else if (k == "max_subspace") {
+    if (value < 2 || value > 64) return bad();
+    o.max_subspace = (int)value;
+  } else if (k == "etol") {
+    if (value <= 0) return bad();
+    o.etol = value;
+  } else if (k == "switch_tol") {
+    if (value <= 0) return bad();
+    o.switch_tol = value;
+  } else if (k == "guess_from_vecs") {
+    o.guess_from_vecs = value != 0;
+  } else if (k == "use_graph") {
+    o.use_graph = value != 0;
+  } else if (k == "phase_timing") {
+    o.phase_timing = value != 0;
+    Context* ctx = current();
+    if (ctx) ctx->ntimed = 0;  // restart the per-call record
+  } else {
+    set_error("iscsi_set_option: unknown key " + k);
+    return ISCSI_E_ARG;
+  }
+  return ISCSI_OK;
+}
+
+iscsi_status iscsi_stats(char* json, int len) {
+  NEED_CTX(ctx);
+  if (!json || len < 2) {
+    set_error("iscsi_stats: buffer too small");
+    return ISCSI_E_ARG;
+  }
+  // per-phase sigma times of the recorded calls
+  double phase_ms[Context::kPhases] = {0, 0, 0, 0};
+  int ncalls = ctx->ntimed;
+  if (ncalls > 0) {
+    ISCSI_CUDA(cudaStreamSynchronize(stream()));
+    for (int c = 0; c < ncalls; ++c)
+      for (int p = 0; p < Context::kPhases; ++p) {
+        float ms = 0;
+        cudaEvent_t a = ctx->tev[(size_t)c * (Context::kPhases + 1) + p];
+        cudaEvent_t b = ctx->tev[(size_t)c * (Context::kPhases + 1) + p + 1];
+        if (cudaEventElapsedTime(&ms, a, b) == cudaSuccess) phase_ms[p] += ms;
+      }
+  }
+  double upd = ctx->updates_onebody + ctx->updates_samespin + ctx->updates_opposite;
+  char buf[4096];
+  std::snprintf(
+      buf, sizeof(buf),
+      "{\"norb\": %d, \"nalpha\": %d, \"nbeta\": %d, \"max_excitation\": %d, \"tau\": %.17g, \"ndet\": %lld, "
+      "\"nstrings\": [%d, %d], \"units_total\": {\"onebody\": %lld, \"samespin\": %lld, \"opposite\": %lld}, "
+      "\"units_kept_opposite\": %lld, \"unit_hits_onebody\": %lld, \"unit_hits_samespin\": %lld, "
+      "\"updates\": {\"onebody\": %.17g, \"samespin\": %.17g, \"opposite\": %.17g, \"total\": %.17g}, "
+      "\"init_ms\": %.6f, \"timed_calls\": %d, \"phase_ms\": {\"lift\": %.6f, \"opposite_gemm\": %.6f, "
+      "\"fold\": %.6f, \"samespin_gemm\": %.6f}, \"davidson_iters\": %d, \"davidson_ms\": %.6f, "
+      "\"opposite_gemm_flops\": %.17g, \"samespin_gemm_flops\": %.17g}",
+      ctx->n, ctx->na, ctx->nb, ctx->kmax, ctx->tau, ctx->ndet, ctx->sp[0].count, ctx->sp[1].count,
+      ctx->units_onebody_total, ctx->units_samespin_total, ctx->units_opposite_total, ctx->units_opposite,
+      ctx->units_onebody, ctx->units_samespin, ctx->updates_onebody, ctx->updates_samespin,
+      ctx->updates_opposite, upd, ctx->init_ms, ncalls, phase_ms[0], phase_ms[1], phase_ms[2], phase_ms[3],
+      ctx->last_davidson_iters, ctx->last_davidson_ms, ctx_gemm_flops(*ctx, 0), ctx_gemm_flops(*ctx, 1));
+  std::strncpy(json, buf, len - 1);
+  json[len - 1] = 0;
+  return ISCSI_OK;
+}
+
+double iscsi_updates_per_sigma(void) {
+  Context* ctx = current();
+  if (!ctx) return -1;
+  return ctx->updates_onebody + ctx->updates_samespin + ctx->updates_opposite;
+}
+
+const char* iscsi_last_error(void) { return last_error(); }
+
+void iscsi_finalize(void) {
+  g_ctx.clear();
+  g_current = 0;
+}
+
+int iscsi_ctx_current(void) { return current() ? g_current : 0; }
+
+iscsi_status iscsi_ctx_use(int handle) {
+  if (g_ctx.find(handle) == g_ctx.end()) {
+    set_error("iscsi_ctx_use: unknown handle");
+    return ISCSI_E_ARG;
+  }
+  g_current = handle;
+  return ISCSI_OK;
+}
+
+iscsi_status iscsi_ctx_destroy(int handle) {
+  auto it = g_ctx.find(handle);
+  if (it == g_ctx.end()) {
+    set_error("iscsi_ctx_destroy: unknown handle");
+    return ISCSI_E_ARG;
+  }
+  g_ctx.erase(it);
+  if (g_current == handle) g_current = 0;
+  return ISCSI_OK;
+}
+
+}  // extern "C"

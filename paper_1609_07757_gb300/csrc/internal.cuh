@@ -1,0 +1,210 @@
+// internal.cuh -- shared declarations of the ISCI sigma library (GB300, sm_103a).
+//
+// Data layout in HBM (one context):
+//   strings      per spin: orbitals [count][ne] (int16), level [count] (int8),
+//                colex rank -> sorted position [count] (int32)
+//   addressing   off[A] (int64, [NA+1]), beta strings allowed per alpha level
+//   hole strings per spin: the (ne-1)-electron strings X; lift[q][X] gives the
+//                string X u {q} and the sign of a+_q on |X> (Eqs. four-last:
+//                contraction and addition with their phases)
+//   G            opposite-spin units g_pqrs, screened (zeros where |g| <= tau
+//                or the class is masked), [M x K] with rows m = pi(p, r) and
+//                columns k = pi(q, s), pairs sorted by excitation level
+//   Msame        per spin, the dense string Hamiltonian of the surviving
+//                one-body and same-spin units, [N_sigma x N_sigma]
+//   Ct, T        per column level class c: lifted vector Ct_c [K_c x Ncol_c]
+//                and product T_c = G[:M_c, :K_c] Ct_c
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace iscsi {
+
+constexpr int kMaxOrb = 256;
+constexpr int kMaxElec = 16;
+constexpr int kNumClasses = 42;
+constexpr int kMaxLevels = kMaxElec + 1;
+
+// status codes (mirror include/iscsi.h)
+constexpr int kOk = 0, kErrArg = -1, kErrNoMem = -2, kErrCuda = -3, kErrNoConv = -4, kErrNoInit = -5,
+              kErrNan = -6, kErrWait = -7;
+
+void set_error(const std::string& msg);
+const char* last_error();
+
+#define ISCSI_CUDA(...)                                                                         \
+  do {                                                                                          \
+    cudaError_t e_ = (__VA_ARGS__);                                                             \
+    if (e_ != cudaSuccess) {                                                                    \
+      ::iscsi::set_error(std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));            \
+      return e_ == cudaErrorMemoryAllocation ? ::iscsi::kErrNoMem : ::iscsi::kErrCuda;          \
+    }                                                                                           \
+  } while (0)
+
+#define ISCSI_TRY(...)       \
+  do {                       \
+    int s_ = (__VA_ARGS__);  \
+    if (s_ != 0) return s_;  \
+  } while (0)
+
+// A device buffer owned by a context.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  int alloc(size_t nbytes);
+  int grow(size_t nbytes);  // keeps nothing
+  void release();
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+struct SpinSpace {
+  int ne = 0;
+  int count = 0;       // C(n, ne)
+  int maxlevel = 0;
+  std::vector<int> level_start;   // first sorted index of each level, size maxlevel+2
+  DevBuf orbs, level, pos;        // int16 [count][ne], int8 [count], int32 [count]
+  // hole strings
+  int nhole = 0;                  // C(n, ne-1), 0 when ne == 0
+  int hole_maxlevel = 0;
+  std::vector<int> hole_level;    // host, [nhole]
+  DevBuf lift;                    // int32 [n][nhole]: (pos << 1 | neg) or -1
+  DevBuf dec;                     // int32 [count][ne]: (X << 9 | p << 1 | neg)
+};
+
+// Operand addresses of the grouped GEMM are either absolute (src 0: the value
+// is a device pointer) or element offsets into the vectors of the call
+// (src 1: into c, src 2: into sigma), so problem lists survive new vectors.
+enum { kSrcAbs = 0, kSrcC = 1, kSrcSigma = 2 };
+
+// One GEMM segment: C[M x N] (+)= A[M x K] * B[K x N]; B columns >= bcols read as 0.
+template <typename T>
+struct Segment {
+  long long a, b;
+  int asrc, bsrc;
+  long long lda, ldb;
+  int K, bcols;
+};
+
+template <typename T>
+struct Problem {
+  long long c;
+  int csrc;
+  long long ldc;
+  int M, N;
+  int seg_begin, seg_count;
+  int tile_begin;   // first global tile of this problem
+  int tiles_n;      // tiles along N
+  int accumulate;   // 1: C += ..., 0: C = ...
+};
+
+template <typename T>
+struct ProblemList {
+  std::vector<Problem<T>> probs;
+  std::vector<Segment<T>> segs;
+  int total_tiles = 0;
+  DevBuf d_probs, d_segs;
+};
+
+struct ColClass {       // column level class c = level(X) + level(Y)
+  int level = 0;
+  int ncol = 0;         // hole pairs in the class
+  int mrows = 0;        // pairs pi with level <= kmax - c (rows of T_c)
+  int krows = 0;        // same count for the K dimension
+  size_t ct_off = 0;    // element offset of Ct_c / T_c in the workspace (per vector set)
+};
+
+struct Context {
+  int n = 0, na = 0, nb = 0, kmax = 0;
+  double tau = 0;
+  unsigned long long class_mask = 0;
+  SpinSpace sp[2];
+  long long ndet = 0;
+  std::vector<long long> off_h;           // host copy of off
+  std::vector<long long> nb_allowed_lvl;  // beta strings allowed per alpha level
+  DevBuf off, nballow;                    // int64 [NA+1], int32 [kMaxLevels]
+  // opposite-spin part
+  int npairs = 0;                         // n*n
+  std::vector<int> pair_level_start;      // first pair of each level sum (0..2), size 4
+  DevBuf pair_of, pair_index;             // int32 [npairs] -> p*n+r ; int32 [n*n] -> m
+  std::vector<ColClass> cls;
+  DevBuf hp_class, hp_local;              // int8 / int32 [nholeA * nholeB]
+  DevBuf hp_inv;                          // int32 [total hole pairs] -> X * nholeB + Y, grouped by class
+  std::vector<int> hp_class_start;        // start of each class in hp_inv
+  DevBuf G64, G32;                        // [npairs x npairs]
+  bool have_ab = false;
+  // same-spin parts
+  DevBuf M64[2], M32[2];                  // [count x count] per spin (beta aliases alpha when equal)
+  bool beta_alias = false;
+  DevBuf diag;                            // FP64 [ndet]
+  // workspaces
+  size_t ct_elems = 0;                    // elements of all Ct_c (= of all T_c) for one vector
+  DevBuf ct, tt;                          // Ct and T for nvec_cap vectors (in the active precision)
+  DevBuf c32, s32;                        // FP32 copies for the FP32 path
+  int nvec_cap = 0;
+  int ws_prec = 0;
+  ProblemList<double> pl_ab64, pl_ss64;
+  ProblemList<float> pl_ab32, pl_ss32;
+  int pl_nvec64 = 0, pl_nvec32 = 0;
+  // statistics
+  double updates_onebody = 0, updates_samespin = 0, updates_opposite = 0;
+  long long units_onebody = 0, units_samespin = 0, units_opposite = 0;
+  long long units_onebody_total = 0, units_samespin_total = 0, units_opposite_total = 0;
+  double last_sigma_ms = 0, init_ms = 0;
+  // per-phase timing of sigma calls (option "phase_timing"): events recorded on
+  // the library stream around lift, opposite-spin GEMM, fold, same-spin GEMM
+  static constexpr int kPhases = 4;
+  static constexpr int kMaxTimed = 512;
+  std::vector<cudaEvent_t> tev;  // [kMaxTimed][kPhases + 1]
+  int ntimed = 0;
+  int last_davidson_iters = 0;
+  double last_davidson_ms = 0;
+  // Davidson buffers
+  DevBuf dv_V, dv_W, dv_tmp, dv_small;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  ~Context();
+};
+
+struct Options {
+  int precision = 64;
+  unsigned long long class_mask = (1ull << kNumClasses) - 1;
+  int maxiter = 300;
+  int max_subspace = 12;
+  double etol = 1e-10;
+  double switch_tol = 1e-5;
+  int guess_from_vecs = 0;
+  int use_graph = 1;
+  int phase_timing = 0;
+};
+
+Options& options();
+cudaStream_t stream();
+void set_stream(cudaStream_t s);
+
+// setup.cu
+int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h1, const double* eri, double tau);
+
+// sigma.cu
+int sigma_run(Context& ctx, const double* c, double* sigma, int nvec, int precision);
+int sigma_workspace(Context& ctx, int nvec, int precision);
+// algorithmic flops per sigma per vector of the opposite-spin GEMM (which = 0)
+// or of the same-spin GEMMs (which = 1): 2 x M x K x N summed over problems
+double ctx_gemm_flops(const Context& ctx, int which);
+
+// davidson.cu
+int davidson_run(Context& ctx, int nroots, double tol, double* energies, double* vecs);
+
+// small helpers shared by the .cu files
+long long binom_ll(int n, int k);
+int launch_blocks(long long work, int threads);
+
+}  // namespace iscsi

@@ -1,0 +1,511 @@
+// sigma.cu -- the ISCI sigma step sigma = H_tau c on the GPU.
+//
+// The 42 generalised matrix-vector products of Eqs. class_to_ex_dx..the_end
+// are grouped by what they touch:
+//
+//   opposite-spin (16 terms of H_{2,0,0}): the separability of Eq. final lets
+//     every term factor into an alpha string equation and a beta string
+//     equation (Eqs. four-last).  Writing E^a_pq = a+_p a_q through the hole
+//     strings X (one electron removed, the intermediate strings of the
+//     contraction/addition loops of Sec. "Second part"),
+//       sigma[A,B] = sum_{(p,X)->A} sum_{(r,Y)->B} s s T[(p,r),(X,Y)],
+//       T[(p,r),(X,Y)] = sum_{q,s} g_pqrs Ct[(q,s),(X,Y)],
+//       Ct[(q,s),(X,Y)] = s s c[X u q, Y u s],
+//     so the integral-outer loop of the paper becomes a dense contraction
+//     over the integral indices (q,s), the intermediate of Eqs. h200ca-h200ab
+//     generalised to all terms.  Ct is "lift", T is a grouped GEMM, the gather
+//     into sigma is "fold".  Screened units are zeros of G.
+//   one-body and same-spin (8 + 18 terms): each spin's surviving units are
+//     summed into a dense string Hamiltonian M_sigma at set-up, and the sigma
+//     contribution is M_alpha C and C M_beta^T per excitation-level block of the
+//     CI vector (the blocks of Fig. cisdt), accumulated into the output tile
+//     in registers, so no atomics are needed.
+#include <algorithm>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace iscsi {
+
+// ---------------------------------------------------------------------------
+// grouped, segmented tile GEMM:  C[M x N] (+)= sum_seg A_seg[M x K_seg] B_seg[K_seg x N]
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    k_grouped_gemm(const Problem<T>* __restrict__ probs, int nprobs, const Segment<T>* __restrict__ segs,
+                   const T* __restrict__ cbase, T* sbase) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  constexpr int LA = BM * BK / NT;  // A elements loaded per thread per K step
+  constexpr int LB = BK * BN / NT;
+  static_assert(BM * BK % NT == 0 && BK * BN % NT == 0, "tile shape");
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN];
+
+  int tile = blockIdx.x;
+  int lo = 0, hi = nprobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile_begin <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  const Problem<T> P = probs[lo];
+  auto resolve = [&](long long v, int src) -> const T* {
+    return src == kSrcC ? cbase + v : src == kSrcSigma ? sbase + v : reinterpret_cast<const T*>(v);
+  };
+  T* Cp = const_cast<T*>(resolve(P.c, P.csrc));
+  int t = tile - P.tile_begin;
+  int m0 = (t / P.tiles_n) * BM, n0 = (t % P.tiles_n) * BN;
+  int tx = threadIdx.x % (BN / TN), ty = threadIdx.x / (BN / TN);
+
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+  for (int sg = 0; sg < P.seg_count; ++sg) {
+    const Segment<T> S = segs[P.seg_begin + sg];
+    const T* Ap = resolve(S.a, S.asrc);
+    const T* Bp = resolve(S.b, S.bsrc);
+    int bcols = min(S.bcols, P.N);
+    T ra[LA], rb[LB];
+    auto load = [&](int k0) {
+#pragma unroll
+      for (int u = 0; u < LA; ++u) {
+        int i = threadIdx.x + u * NT;
+        int r = i / BK, kk = i % BK;
+        int gm = m0 + r, gk = k0 + kk;
+        ra[u] = (gm < P.M && gk < S.K) ? Ap[(long long)gm * S.lda + gk] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        int i = threadIdx.x + u * NT;
+        int kk = i / BN, cc = i % BN;
+        int gk = k0 + kk, gn = n0 + cc;
+        rb[u] = (gk < S.K && gn < bcols) ? Bp[(long long)gk * S.ldb + gn] : T(0);
+      }
+    };
+    load(0);
+    for (int k0 = 0; k0 < S.K; k0 += BK) {
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < LA; ++u) {
+        int i = threadIdx.x + u * NT;
+        As[i % BK][i / BK] = ra[u];
+      }
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        int i = threadIdx.x + u * NT;
+        Bs[i / BN][i % BN] = rb[u];
+      }
+      __syncthreads();
+      if (k0 + BK < S.K) load(k0 + BK);
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        T a[TM], b[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    int gm = m0 + ty * TM + i;
+    if (gm >= P.M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int gn = n0 + tx * TN + j;
+      if (gn >= P.N) continue;
+      T* c = Cp + (long long)gm * P.ldc + gn;
+      *c = P.accumulate ? *c + acc[i][j] : acc[i][j];
+    }
+  }
+}
+
+template <typename T>
+struct TileCfg;
+template <>
+struct TileCfg<double> {
+  static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+};
+template <>
+struct TileCfg<float> {
+  static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
+};
+
+template <typename T>
+static int upload_problems(ProblemList<T>& pl, cudaStream_t st) {
+  using C = TileCfg<T>;
+  int tiles = 0;
+  for (auto& p : pl.probs) {
+    p.tile_begin = tiles;
+    p.tiles_n = (p.N + C::BN - 1) / C::BN;
+    tiles += ((p.M + C::BM - 1) / C::BM) * p.tiles_n;
+  }
+  pl.total_tiles = tiles;
+  if (pl.probs.empty()) return kOk;
+  ISCSI_TRY(pl.d_probs.grow(sizeof(Problem<T>) * pl.probs.size()));
+  ISCSI_TRY(pl.d_segs.grow(sizeof(Segment<T>) * std::max<size_t>(1, pl.segs.size())));
+  ISCSI_CUDA(cudaMemcpyAsync(pl.d_probs.p, pl.probs.data(), sizeof(Problem<T>) * pl.probs.size(),
+                             cudaMemcpyHostToDevice, st));
+  if (!pl.segs.empty())
+    ISCSI_CUDA(cudaMemcpyAsync(pl.d_segs.p, pl.segs.data(), sizeof(Segment<T>) * pl.segs.size(),
+                               cudaMemcpyHostToDevice, st));
+  // the host vectors must outlive the copies
+  ISCSI_CUDA(cudaStreamSynchronize(st));
+  return kOk;
+}
+
+template <typename T>
+static int launch_grouped(const ProblemList<T>& pl, const T* cbase, T* sbase, cudaStream_t st) {
+  using C = TileCfg<T>;
+  if (pl.total_tiles == 0) return kOk;
+  constexpr int NT = (C::BM / C::TM) * (C::BN / C::TN);
+  k_grouped_gemm<T, C::BM, C::BN, C::BK, C::TM, C::TN><<<pl.total_tiles, NT, 0, st>>>(
+      pl.d_probs.template as<Problem<T>>(), (int)pl.probs.size(), pl.d_segs.template as<Segment<T>>(), cbase,
+      sbase);
+  ISCSI_CUDA(cudaGetLastError());
+  return kOk;
+}
+
+// ---------------------------------------------------------------------------
+// lift: Ct_c[(q,s)][(X,Y), v] = s_a(q,X) s_b(s,Y) c_v[X u q, Y u s]  (0 outside the space)
+
+constexpr int kMaxClasses = 2 * kMaxElec;
+
+struct ClassTable {
+  int nclass;
+  long long start[kMaxClasses + 1];  // element offsets (all vectors) of each class block
+  int ncol[kMaxClasses];
+  int hp_start[kMaxClasses];
+};
+
+template <typename T, typename TC>
+__global__ void k_lift_ct(ClassTable ct, int nvec, int n, int nholeA, int nholeB, const int* __restrict__ pair_of,
+                          const int* __restrict__ hp_inv, const int* __restrict__ liftA,
+                          const int* __restrict__ liftB, const int8_t* __restrict__ alevel,
+                          const int* __restrict__ nballow, const long long* __restrict__ off,
+                          const TC* __restrict__ c, long long ndet, T* __restrict__ out) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= ct.start[ct.nclass]) return;
+  int cl = 0;
+  while (t >= ct.start[cl + 1]) ++cl;
+  long long local = t - ct.start[cl];
+  long long width = (long long)ct.ncol[cl] * nvec;
+  int k = (int)(local / width);
+  int col = (int)(local % width);
+  int hp = col / nvec, v = col % nvec;
+  int xy = hp_inv[ct.hp_start[cl] + hp];
+  int X = xy / nholeB, Y = xy % nholeB;
+  int qs = pair_of[k];
+  int q = qs / n, s = qs % n;
+  int ea = liftA[q * nholeA + X], eb = liftB[s * nholeB + Y];
+  T val = T(0);
+  if (ea >= 0 && eb >= 0) {
+    int Ap = ea >> 1, Bp = eb >> 1;
+    if (Bp < nballow[alevel[Ap]]) {
+      T x = (T)c[(long long)v * ndet + off[Ap] + Bp];
+      val = ((ea ^ eb) & 1) ? -x : x;
+    }
+  }
+  out[t] = val;
+}
+
+// fold: sigma_v[A,B] = sum_{(p,X)->A} sum_{(r,Y)->B} s s T_c[pi(p,r)][(X,Y), v]
+template <typename T>
+__global__ void k_fold(ClassTable ct, int nvec, int n, int na, int nb, int nholeB, const int* __restrict__ decA,
+                       const int* __restrict__ decB, const int8_t* __restrict__ hp_class,
+                       const int* __restrict__ hp_local, const int* __restrict__ pair_index,
+                       const long long* __restrict__ off, const T* __restrict__ tt, long long ndet,
+                       T* __restrict__ sigma) {
+  int A = blockIdx.x;
+  long long o0 = off[A], o1 = off[A + 1];
+  long long work = (o1 - o0) * nvec;
+  for (long long w = threadIdx.x; w < work; w += blockDim.x) {
+    int B = (int)(w / nvec), v = (int)(w % nvec);
+    T acc = T(0);
+    for (int i = 0; i < na; ++i) {
+      int da = decA[A * na + i];
+      int X = da >> 9, p = (da >> 1) & 255;
+      for (int j = 0; j < nb; ++j) {
+        int db = decB[B * nb + j];
+        int Y = db >> 9, r = (db >> 1) & 255;
+        long long hp = (long long)X * nholeB + Y;
+        int cl = hp_class[hp];
+        int m = pair_index[p * n + r];
+        T x = tt[ct.start[cl] + ((long long)m * ct.ncol[cl] + hp_local[hp]) * nvec + v];
+        acc += ((da ^ db) & 1) ? -x : x;
+      }
+    }
+    sigma[(long long)v * ndet + o0 + B] = acc;
+  }
+}
+
+template <typename TA, typename TB>
+__global__ void k_convert(const TA* __restrict__ in, TB* __restrict__ out, long long count) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (; t < count; t += stride) out[t] = (TB)in[t];
+}
+
+// ---------------------------------------------------------------------------
+
+static ClassTable class_table(const Context& ctx, int nvec) {
+  ClassTable ct;
+  std::memset(&ct, 0, sizeof(ct));
+  ct.nclass = (int)ctx.cls.size();
+  long long acc = 0;
+  for (int c = 0; c < ct.nclass; ++c) {
+    const ColClass& cc = ctx.cls[c];
+    ct.start[c] = acc;
+    ct.ncol[c] = cc.ncol;
+    ct.hp_start[c] = ctx.hp_class_start[c];
+    if (cc.ncol > 0 && cc.mrows > 0) acc += (long long)cc.mrows * cc.ncol * nvec;
+  }
+  ct.start[ct.nclass] = acc;
+  return ct;
+}
+
+template <typename T>
+static const T* mat_ptr(const DevBuf& b) {
+  return b.as<T>();
+}
+
+// builds the grouped problem lists of one precision for nvec vectors
+template <typename T>
+static int build_problems(Context& ctx, int nvec, const T* G, const T* Ma, const T* Mb, T* ctw, T* ttw,
+                          ProblemList<T>& ab, ProblemList<T>& ss) {
+  auto absp = [](const void* p) { return (long long)reinterpret_cast<uintptr_t>(p); };
+  cudaStream_t st = stream();
+  ab.probs.clear();
+  ab.segs.clear();
+  ss.probs.clear();
+  ss.segs.clear();
+  if (ctx.have_ab) {
+    ClassTable ct = class_table(ctx, nvec);
+    for (int cl = 0; cl < (int)ctx.cls.size(); ++cl) {
+      const ColClass& cc = ctx.cls[cl];
+      if (cc.ncol == 0 || cc.mrows == 0) continue;
+      Segment<T> sgm;
+      sgm.a = absp(G);
+      sgm.asrc = kSrcAbs;
+      sgm.lda = ctx.npairs;
+      sgm.b = absp(ctw + ct.start[cl]);
+      sgm.bsrc = kSrcAbs;
+      sgm.ldb = (long long)cc.ncol * nvec;
+      sgm.K = cc.krows;
+      sgm.bcols = cc.ncol * nvec;
+      Problem<T> p;
+      p.c = absp(ttw + ct.start[cl]);
+      p.csrc = kSrcAbs;
+      p.ldc = (long long)cc.ncol * nvec;
+      p.M = cc.mrows;
+      p.N = cc.ncol * nvec;
+      p.seg_begin = (int)ab.segs.size();
+      p.seg_count = 1;
+      p.accumulate = 0;
+      ab.segs.push_back(sgm);
+      ab.probs.push_back(p);
+    }
+  }
+  const SpinSpace& SA = ctx.sp[0];
+  const SpinSpace& SB = ctx.sp[1];
+  for (int v = 0; v < nvec; ++v) {
+    for (int a = 0; a <= SA.maxlevel; ++a) {
+      int rows = SA.level_start[a + 1] - SA.level_start[a];
+      int nba = (int)ctx.nb_allowed_lvl[a];
+      if (rows == 0 || nba == 0) continue;
+      long long obase = ctx.off_h[SA.level_start[a]];
+      Problem<T> p;
+      p.c = (long long)v * ctx.ndet + obase;
+      p.csrc = kSrcSigma;
+      p.ldc = nba;
+      p.M = rows;
+      p.N = nba;
+      p.seg_begin = (int)ss.segs.size();
+      p.seg_count = 0;
+      p.accumulate = 1;
+      if (ctx.na > 0 && Ma) {
+        for (int a2 = 0; a2 <= SA.maxlevel; ++a2) {
+          int rows2 = SA.level_start[a2 + 1] - SA.level_start[a2];
+          int nba2 = (int)ctx.nb_allowed_lvl[a2];
+          if (rows2 == 0 || nba2 == 0 || std::abs(a - a2) > 2) continue;
+          Segment<T> sgm;
+          sgm.a = absp(Ma + (long long)SA.level_start[a] * SA.count + SA.level_start[a2]);
+          sgm.asrc = kSrcAbs;
+          sgm.lda = SA.count;
+          sgm.b = (long long)v * ctx.ndet + ctx.off_h[SA.level_start[a2]];
+          sgm.bsrc = kSrcC;
+          sgm.ldb = nba2;
+          sgm.K = rows2;
+          sgm.bcols = std::min(nba, nba2);
+          ss.segs.push_back(sgm);
+          p.seg_count++;
+        }
+      }
+      if (ctx.nb > 0 && Mb) {
+        Segment<T> sgm;
+        sgm.a = (long long)v * ctx.ndet + obase;
+        sgm.asrc = kSrcC;
+        sgm.lda = nba;
+        sgm.b = absp(Mb);
+        sgm.bsrc = kSrcAbs;
+        sgm.ldb = SB.count;
+        sgm.K = nba;
+        sgm.bcols = nba;
+        ss.segs.push_back(sgm);
+        p.seg_count++;
+      }
+      if (p.seg_count > 0) ss.probs.push_back(p);
+    }
+  }
+  ISCSI_TRY(upload_problems(ab, st));
+  ISCSI_TRY(upload_problems(ss, st));
+  return kOk;
+}
+
+double ctx_gemm_flops(const Context& ctx, int which) {
+  double f = 0.0;
+  if (which == 0) {
+    if (!ctx.have_ab) return 0.0;
+    for (const ColClass& cc : ctx.cls)
+      if (cc.ncol > 0 && cc.mrows > 0) f += 2.0 * cc.mrows * (double)cc.krows * cc.ncol;
+    return f;
+  }
+  const SpinSpace& SA = ctx.sp[0];
+  for (int a = 0; a <= SA.maxlevel; ++a) {
+    double rows = SA.level_start[a + 1] - SA.level_start[a];
+    double nba = (double)ctx.nb_allowed_lvl[a];
+    if (rows == 0 || nba == 0) continue;
+    if (ctx.na > 0 && ctx.M64[0].p)
+      for (int a2 = 0; a2 <= SA.maxlevel; ++a2) {
+        double rows2 = SA.level_start[a2 + 1] - SA.level_start[a2];
+        double nba2 = (double)ctx.nb_allowed_lvl[a2];
+        if (rows2 == 0 || nba2 == 0 || std::abs(a - a2) > 2) continue;
+        f += 2.0 * rows * rows2 * std::min(nba, nba2);
+      }
+    if (ctx.nb > 0) f += 2.0 * rows * nba * nba;
+  }
+  return f;
+}
+
+int sigma_workspace(Context& ctx, int nvec, int precision) {
+  // Ct and T are sized in FP64 elements, so both precisions share them
+  if (nvec > ctx.nvec_cap) {
+    if (ctx.have_ab) {
+      ISCSI_TRY(ctx.ct.alloc(sizeof(double) * ctx.ct_elems * nvec));
+      ISCSI_TRY(ctx.tt.alloc(sizeof(double) * ctx.ct_elems * nvec));
+    }
+    ctx.c32.release();
+    ctx.s32.release();
+    ctx.nvec_cap = nvec;
+    ctx.pl_nvec64 = ctx.pl_nvec32 = 0;  // workspace pointers changed: rebuild problem lists
+  }
+  if (precision == 32 && !ctx.c32.p) {
+    ISCSI_TRY(ctx.c32.alloc(sizeof(float) * ctx.ndet * ctx.nvec_cap));
+    ISCSI_TRY(ctx.s32.alloc(sizeof(float) * ctx.ndet * ctx.nvec_cap));
+    ctx.pl_nvec32 = 0;
+  }
+  return kOk;
+}
+
+static int ensure_fp32_matrices(Context& ctx) {
+  cudaStream_t st = stream();
+  if (ctx.have_ab && !ctx.G32.p) {
+    long long g2 = (long long)ctx.npairs * ctx.npairs;
+    ISCSI_TRY(ctx.G32.alloc(sizeof(float) * g2));
+    k_convert<double, float><<<2048, 256, 0, st>>>(ctx.G64.as<double>(), ctx.G32.as<float>(), g2);
+  }
+  for (int s = 0; s < 2; ++s) {
+    if (!ctx.M64[s].p || ctx.M32[s].p) continue;
+    long long m2 = (long long)ctx.sp[s].count * ctx.sp[s].count;
+    ISCSI_TRY(ctx.M32[s].alloc(sizeof(float) * m2));
+    k_convert<double, float><<<2048, 256, 0, st>>>(ctx.M64[s].as<double>(), ctx.M32[s].as<float>(), m2);
+  }
+  ISCSI_CUDA(cudaGetLastError());
+  return kOk;
+}
+
+static int timing_event(Context& ctx, int call, int phase, cudaStream_t st) {
+  if (!options().phase_timing || call >= Context::kMaxTimed) return kOk;
+  size_t idx = (size_t)call * (Context::kPhases + 1) + phase;
+  if (ctx.tev.size() <= idx) ctx.tev.resize((size_t)Context::kMaxTimed * (Context::kPhases + 1), nullptr);
+  if (!ctx.tev[idx]) ISCSI_CUDA(cudaEventCreate(&ctx.tev[idx]));
+  ISCSI_CUDA(cudaEventRecord(ctx.tev[idx], st));
+  return kOk;
+}
+
+template <typename T, typename TC>
+static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sigma, int nvec, ProblemList<T>& ab,
+                      ProblemList<T>& ss, int& pl_nvec, const T* G, const T* Ma, const T* Mb) {
+  cudaStream_t st = stream();
+  T* ctw = ctx.ct.as<T>();
+  T* ttw = ctx.tt.as<T>();
+  // problem lists depend on nvec and the workspaces, not on the vectors
+  if (pl_nvec != nvec) {
+    ISCSI_TRY(build_problems<T>(ctx, nvec, G, Ma, Mb, ctw, ttw, ab, ss));
+    pl_nvec = nvec;
+  }
+  int call = ctx.ntimed;
+  ISCSI_TRY(timing_event(ctx, call, 0, st));
+  if (ctx.have_ab) {
+    ClassTable ct = class_table(ctx, nvec);
+    long long tot = ct.start[ct.nclass];
+    if (tot > 0) {
+      k_lift_ct<T, TC><<<launch_blocks(tot, 256), 256, 0, st>>>(
+          ct, nvec, ctx.n, ctx.sp[0].nhole, ctx.sp[1].nhole, ctx.pair_of.as<int>(), ctx.hp_inv.as<int>(),
+          ctx.sp[0].lift.as<int>(), ctx.sp[1].lift.as<int>(), ctx.sp[0].level.as<int8_t>(), ctx.nballow.as<int>(),
+          ctx.off.as<long long>(), c_in, ctx.ndet, ctw);
+      ISCSI_CUDA(cudaGetLastError());
+    }
+    ISCSI_TRY(timing_event(ctx, call, 1, st));
+    ISCSI_TRY(launch_grouped<T>(ab, c, sigma, st));
+    ISCSI_TRY(timing_event(ctx, call, 2, st));
+    k_fold<T><<<ctx.sp[0].count, 256, 0, st>>>(ct, nvec, ctx.n, ctx.na, ctx.nb, ctx.sp[1].nhole,
+                                               ctx.sp[0].dec.as<int>(), ctx.sp[1].dec.as<int>(),
+                                               ctx.hp_class.as<int8_t>(), ctx.hp_local.as<int>(),
+                                               ctx.pair_index.as<int>(), ctx.off.as<long long>(), ttw, ctx.ndet, sigma);
+    ISCSI_CUDA(cudaGetLastError());
+    ISCSI_TRY(timing_event(ctx, call, 3, st));
+  } else {
+    ISCSI_CUDA(cudaMemsetAsync(sigma, 0, sizeof(T) * ctx.ndet * nvec, st));
+    ISCSI_TRY(timing_event(ctx, call, 1, st));
+    ISCSI_TRY(timing_event(ctx, call, 2, st));
+    ISCSI_TRY(timing_event(ctx, call, 3, st));
+  }
+  ISCSI_TRY(launch_grouped<T>(ss, c, sigma, st));
+  ISCSI_TRY(timing_event(ctx, call, 4, st));
+  if (options().phase_timing && call < Context::kMaxTimed) ctx.ntimed++;
+  (void)s_out;
+  return kOk;
+}
+
+int sigma_run(Context& ctx, const double* c, double* sigma, int nvec, int precision) {
+  cudaStream_t st = stream();
+  ISCSI_TRY(sigma_workspace(ctx, nvec, precision));
+  const double* Ma = ctx.na ? ctx.M64[0].as<double>() : nullptr;
+  const double* Mb = ctx.nb ? (ctx.beta_alias ? ctx.M64[0].as<double>() : ctx.M64[1].as<double>()) : nullptr;
+  if (precision == 64) {
+    return sigma_impl<double, double>(ctx, c, sigma, c, sigma, nvec, ctx.pl_ab64, ctx.pl_ss64, ctx.pl_nvec64,
+                                      ctx.G64.as<double>(), Ma, Mb);
+  }
+  ISCSI_TRY(ensure_fp32_matrices(ctx));
+  const float* Ma32 = ctx.na ? ctx.M32[0].as<float>() : nullptr;
+  const float* Mb32 = ctx.nb ? (ctx.beta_alias ? ctx.M32[0].as<float>() : ctx.M32[1].as<float>()) : nullptr;
+  long long cnt = ctx.ndet * nvec;
+  k_convert<double, float><<<std::min(launch_blocks(cnt, 256), 4096), 256, 0, st>>>(c, ctx.c32.as<float>(), cnt);
+  ISCSI_TRY(sigma_impl<float, float>(ctx, ctx.c32.as<float>(), ctx.s32.as<float>(), ctx.c32.as<float>(),
+                                     ctx.s32.as<float>(), nvec, ctx.pl_ab32, ctx.pl_ss32, ctx.pl_nvec32,
+                                     ctx.G32.as<float>(), Ma32, Mb32));
+  k_convert<float, double><<<std::min(launch_blocks(cnt, 256), 4096), 256, 0, st>>>(ctx.s32.as<float>(), sigma, cnt);
+  ISCSI_CUDA(cudaGetLastError());
+  return kOk;
+}
+
+}  // namespace iscsi
