@@ -114,6 +114,27 @@ ISCSI_API iscsi_status iscsi_init(int norb, int nalpha, int nbeta, int max_excit
 ISCSI_API iscsi_status iscsi_sigma(const void* c, void* sigma, int nvec);
 
 /*
+ * Allocation-free variant of iscsi_sigma: FP64, one vector, on the current
+ * context.  (The paper has no counterpart; this entry point exists for
+ * callers that cannot allocate device memory when they need sigma -- code
+ * under a memory manager that owns all device memory, or real-time and
+ * callback contexts where cudaMalloc, which may synchronise the device, is not
+ * allowed.)  It allocates nothing: the lifted vector, the contraction product
+ * and the GEMM problem lists live in one static 32 MiB device array that every
+ * GPU loading this library holds until the process exits.
+ *   c      device, FP64 [ndet]; sigma: device, FP64 [ndet], overwritten.
+ * The context must need at most 32 MiB of scratch (full CI with 2+2
+ * electrons: up to 37 orbitals); larger contexts are rejected with
+ * ISCSI_E_ARG and a message naming the bytes needed.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the array: calls
+ * whose work overlaps on the GPU race and must be serialised by the caller.
+ * Asynchronous on the library stream.  Errors: ISCSI_E_NOINIT, ISCSI_E_ARG,
+ * ISCSI_E_CUDA.
+ */
+ISCSI_API iscsi_status iscsi_sigma_noalloc(const void* c, void* sigma);
+
+/*
  * Same as iscsi_sigma with HOST buffers: copies c to the device, computes,
  * copies sigma back and synchronises.  c, sigma: host, [nvec][ndet] FP64.
  */

@@ -49,6 +49,7 @@ def load(build_if_missing=True):
         "iscsi_init": (c_int, [c_int, c_int, c_int, c_int, vp, vp, c_d]),
         "iscsi_sigma": (c_int, [vp, vp, c_int]),
         "iscsi_sigma_host": (c_int, [vp, vp, c_int]),
+        "iscsi_sigma_noalloc": (c_int, [vp, vp]),
         "iscsi_davidson": (c_int, [c_int, c_d, vp, vp]),
         "iscsi_ndet": (c_ll, []),
         "iscsi_nstrings": (c_ll, [c_int]),
@@ -117,6 +118,11 @@ def iscsi_init(norb, nalpha, nbeta, max_excitation, h1, eri, tau):
 
 def iscsi_sigma(c, sigma, nvec=1):
     return _check(load().iscsi_sigma(_dev(c), _dev(sigma), int(nvec)))
+
+
+def iscsi_sigma_noalloc(c, sigma):
+    """FP64 single-vector sigma that allocates no device memory (static scratch)."""
+    return _check(load().iscsi_sigma_noalloc(_dev(c), _dev(sigma)))
 
 
 def iscsi_sigma_host(c, sigma, nvec=1):

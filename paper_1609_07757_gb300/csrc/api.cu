@@ -78,6 +78,15 @@ iscsi_status iscsi_sigma(const void* c, void* sigma, int nvec) {
   return sigma_run(*ctx, static_cast<const double*>(c), static_cast<double*>(sigma), nvec, options().precision);
 }
 
+iscsi_status iscsi_sigma_noalloc(const void* c, void* sigma) {
+  NEED_CTX(ctx);
+  if (!c || !sigma) {
+    set_error("iscsi_sigma_noalloc: NULL pointer");
+    return ISCSI_E_ARG;
+  }
+  return sigma_noalloc_run(*ctx, static_cast<const double*>(c), static_cast<double*>(sigma));
+}
+
 iscsi_status iscsi_sigma_host(const double* c, double* sigma, int nvec) {
   NEED_CTX(ctx);
   if (!c || !sigma || nvec < 1) {

@@ -200,6 +200,11 @@ int sigma_workspace(Context& ctx, int nvec, int precision);
 // or of the same-spin GEMMs (which = 1): 2 x M x K x N summed over problems
 double ctx_gemm_flops(const Context& ctx, int which);
 
+// allocation-free single-vector FP64 sigma on a static device array (sigma.cu)
+int sigma_noalloc_run(Context& ctx, const double* c, double* sigma);
+size_t noalloc_bytes_needed(const Context& ctx);
+size_t noalloc_scratch_bytes();
+
 // davidson.cu
 int davidson_run(Context& ctx, int nroots, double tol, double* energies, double* vecs);
 

@@ -508,4 +508,166 @@ int sigma_run(Context& ctx, const double* c, double* sigma, int nvec, int precis
   return kOk;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free sigma (iscsi_sigma_noalloc).  Some callers cannot call
+// cudaMalloc at the time they need sigma: code running under a memory manager
+// that owns all device memory, real-time or callback contexts where an
+// allocation (which may synchronise the device) is not allowed, or a process
+// whose memory is already committed.  For them this variant keeps every
+// per-call buffer -- the lifted vector Ct, the product T and the GEMM problem
+// lists -- in one file-scope device array of fixed size instead of
+// library-allocated workspace.  It runs the same kernels as iscsi_sigma (FP64,
+// one vector).  The array belongs to the module: every GPU that loads the
+// library holds it until the process exits.  All calls share it, so calls
+// whose work overlaps on the GPU (different streams, or several host threads)
+// race on it and must be serialised by the caller.  Nothing in it has to
+// start at zero: each call overwrites every element it later reads.
+
+constexpr size_t kNoAllocScratchBytes = 32u << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static void* g_noalloc_ptr[64] = {nullptr};
+
+size_t noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
+
+// bytes of scratch one FP64 single-vector sigma of this context needs
+size_t noalloc_bytes_needed(const Context& ctx) {
+  size_t b = ctx.have_ab ? 2 * sizeof(double) * ctx.ct_elems : 0;
+  b = (b + 255) & ~(size_t)255;
+  b += 64 * (sizeof(Problem<double>) + sizeof(Segment<double>)) + 256;
+  return b;
+}
+
+int sigma_noalloc_run(Context& ctx, const double* c, double* sigma) {
+  using C = TileCfg<double>;
+  cudaStream_t st = stream();
+  size_t need = noalloc_bytes_needed(ctx);
+  if (need > kNoAllocScratchBytes) {
+    set_error("iscsi_sigma_noalloc: this context needs " + std::to_string(need) + " bytes of scratch, above the " +
+              std::to_string(kNoAllocScratchBytes) + "-byte static array; use iscsi_sigma");
+    return kErrArg;
+  }
+  // once per device, with that device current: host code only knows the
+  // array through its device address
+  int dev = 0;
+  ISCSI_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("iscsi_sigma_noalloc: device index out of range");
+    return kErrArg;
+  }
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    ISCSI_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = ptr;
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+  double* ctw = reinterpret_cast<double*>(base);
+  double* ttw = ctw + ctx.ct_elems;
+  size_t lists_off = ctx.have_ab ? ((2 * sizeof(double) * ctx.ct_elems + 255) & ~(size_t)255) : 0;
+  Problem<double>* dprobs = reinterpret_cast<Problem<double>*>(base + lists_off);
+  Segment<double>* dsegs = reinterpret_cast<Segment<double>*>(base + lists_off + 64 * sizeof(Problem<double>));
+
+  // problem lists (host vectors, copied into the array below)
+  std::vector<Problem<double>> ab, ss;
+  std::vector<Segment<double>> segs;
+  auto absp = [](const void* p) { return (long long)reinterpret_cast<uintptr_t>(p); };
+  const double* G = ctx.G64.as<double>();
+  const double* Ma = ctx.na ? ctx.M64[0].as<double>() : nullptr;
+  const double* Mb = ctx.nb ? (ctx.beta_alias ? ctx.M64[0].as<double>() : ctx.M64[1].as<double>()) : nullptr;
+  ClassTable ct = class_table(ctx, 1);
+  if (ctx.have_ab) {
+    for (int cl = 0; cl < (int)ctx.cls.size(); ++cl) {
+      const ColClass& cc = ctx.cls[cl];
+      if (cc.ncol == 0 || cc.mrows == 0) continue;
+      Segment<double> g{absp(G), absp(ctw + ct.start[cl]), kSrcAbs, kSrcAbs, ctx.npairs, cc.ncol, cc.krows, cc.ncol};
+      Problem<double> p{};
+      p.c = absp(ttw + ct.start[cl]);
+      p.csrc = kSrcAbs;
+      p.ldc = cc.ncol;
+      p.M = cc.mrows;
+      p.N = cc.ncol;
+      p.seg_begin = (int)segs.size();
+      p.seg_count = 1;
+      p.accumulate = 0;
+      segs.push_back(g);
+      ab.push_back(p);
+    }
+  }
+  const SpinSpace& SA = ctx.sp[0];
+  const SpinSpace& SB = ctx.sp[1];
+  for (int a = 0; a <= SA.maxlevel; ++a) {
+    int rows = SA.level_start[a + 1] - SA.level_start[a];
+    int nba = (int)ctx.nb_allowed_lvl[a];
+    if (rows == 0 || nba == 0) continue;
+    long long obase = ctx.off_h[SA.level_start[a]];
+    Problem<double> p{};
+    p.c = obase;
+    p.csrc = kSrcSigma;
+    p.ldc = nba;
+    p.M = rows;
+    p.N = nba;
+    p.seg_begin = (int)segs.size();
+    p.seg_count = 0;
+    p.accumulate = 1;
+    if (ctx.na > 0 && Ma)
+      for (int a2 = 0; a2 <= SA.maxlevel; ++a2) {
+        int rows2 = SA.level_start[a2 + 1] - SA.level_start[a2];
+        int nba2 = (int)ctx.nb_allowed_lvl[a2];
+        if (rows2 == 0 || nba2 == 0 || std::abs(a - a2) > 2) continue;
+        segs.push_back({absp(Ma + (long long)SA.level_start[a] * SA.count + SA.level_start[a2]),
+                        ctx.off_h[SA.level_start[a2]], kSrcAbs, kSrcC, SA.count, nba2, rows2, std::min(nba, nba2)});
+        p.seg_count++;
+      }
+    if (ctx.nb > 0 && Mb) {
+      segs.push_back({obase, absp(Mb), kSrcC, kSrcAbs, nba, SB.count, nba, nba});
+      p.seg_count++;
+    }
+    if (p.seg_count > 0) ss.push_back(p);
+  }
+  auto tiles_of = [](std::vector<Problem<double>>& v) {
+    int tiles = 0;
+    for (auto& p : v) {
+      p.tile_begin = tiles;
+      p.tiles_n = (p.N + C::BN - 1) / C::BN;
+      tiles += ((p.M + C::BM - 1) / C::BM) * p.tiles_n;
+    }
+    return tiles;
+  };
+  int ab_tiles = tiles_of(ab), ss_tiles = tiles_of(ss);
+  std::vector<Problem<double>> all(ab);
+  all.insert(all.end(), ss.begin(), ss.end());
+  if (all.size() > 64 || segs.size() > 64) {
+    set_error("iscsi_sigma_noalloc: too many GEMM problems for the static lists");
+    return kErrArg;
+  }
+  if (!all.empty())
+    ISCSI_CUDA(cudaMemcpyAsync(dprobs, all.data(), sizeof(Problem<double>) * all.size(), cudaMemcpyHostToDevice, st));
+  if (!segs.empty())
+    ISCSI_CUDA(cudaMemcpyAsync(dsegs, segs.data(), sizeof(Segment<double>) * segs.size(), cudaMemcpyHostToDevice, st));
+  constexpr int NT = (C::BM / C::TM) * (C::BN / C::TN);
+  if (ctx.have_ab) {
+    long long tot = ct.start[ct.nclass];
+    if (tot > 0)
+      k_lift_ct<double, double><<<launch_blocks(tot, 256), 256, 0, st>>>(
+          ct, 1, ctx.n, ctx.sp[0].nhole, ctx.sp[1].nhole, ctx.pair_of.as<int>(), ctx.hp_inv.as<int>(),
+          ctx.sp[0].lift.as<int>(), ctx.sp[1].lift.as<int>(), ctx.sp[0].level.as<int8_t>(), ctx.nballow.as<int>(),
+          ctx.off.as<long long>(), c, ctx.ndet, ctw);
+    if (ab_tiles > 0)
+      k_grouped_gemm<double, C::BM, C::BN, C::BK, C::TM, C::TN>
+          <<<ab_tiles, NT, 0, st>>>(dprobs, (int)ab.size(), dsegs, c, sigma);
+    k_fold<double><<<ctx.sp[0].count, 256, 0, st>>>(ct, 1, ctx.n, ctx.na, ctx.nb, ctx.sp[1].nhole,
+                                                    ctx.sp[0].dec.as<int>(), ctx.sp[1].dec.as<int>(),
+                                                    ctx.hp_class.as<int8_t>(), ctx.hp_local.as<int>(),
+                                                    ctx.pair_index.as<int>(), ctx.off.as<long long>(), ttw, ctx.ndet,
+                                                    sigma);
+  } else {
+    ISCSI_CUDA(cudaMemsetAsync(sigma, 0, sizeof(double) * ctx.ndet, st));
+  }
+  if (ss_tiles > 0)
+    k_grouped_gemm<double, C::BM, C::BN, C::BK, C::TM, C::TN>
+        <<<ss_tiles, NT, 0, st>>>(dprobs + ab.size(), (int)ss.size(), dsegs, c, sigma);
+  ISCSI_CUDA(cudaGetLastError());
+  return kOk;
+}
+
 }  // namespace iscsi
