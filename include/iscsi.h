@@ -107,7 +107,11 @@ ISCSI_API iscsi_status iscsi_init(int norb, int nalpha, int nbeta, int max_excit
  *   sigma  device, FP64, [nvec][ndet]; overwritten; must not overlap c.
  * Arithmetic follows the "precision" option (64: FP64 throughout; 32: FP32
  * products and accumulation, inputs rounded to FP32, result widened to FP64).
- * Asynchronous on the library stream; never synchronises.
+ * Asynchronous on the library stream; does not synchronise except the first
+ * time a new nvec is used (work lists are uploaded once per nvec).  A bounded
+ * device wait that runs out inside the tensor-core kernels is reported as
+ * ISCSI_E_WAIT by the next synchronising call (iscsi_sigma_host,
+ * iscsi_davidson).
  * Errors: ISCSI_E_NOINIT, ISCSI_E_ARG (NULL pointers, nvec < 1), ISCSI_E_NOMEM
  * (workspace growth), ISCSI_E_CUDA (launch failure).
  */
@@ -199,6 +203,13 @@ ISCSI_API iscsi_status iscsi_set_stream(void* stream);
  *                      the switch also happens when the FP32 residual stalls)
  *   "guess_from_vecs"  1: iscsi_davidson starts from `vecs` (default 0)
  *   "use_graph"        1: capture one Davidson iteration as a CUDA graph (default 1)
+ *   "fp64_tc"          1 (default): with precision 64, the opposite-spin
+ *                      contraction runs on the bf16 tensor cores with FP64
+ *                      accuracy (operands cut into exact 7-bit slices, exact
+ *                      integer accumulation of the leading levels; relative
+ *                      error ~1e-14 of sum |g||c|); 0: native FP64 FMA
+ *   "phase_timing"     1: record per-phase CUDA events of every sigma call
+ *                      (reported by iscsi_stats; the record restarts when set)
  * Errors: ISCSI_E_ARG for an unknown key or a value out of range.
  */
 ISCSI_API iscsi_status iscsi_set_option(const char* key, double value);

@@ -102,7 +102,7 @@ iscsi_status iscsi_sigma_host(const double* c, double* sigma, int nvec) {
   ISCSI_TRY(sigma_run(*ctx, dc.as<double>(), ds.as<double>(), nvec, options().precision));
   ISCSI_CUDA(cudaMemcpyAsync(sigma, ds.p, bytes, cudaMemcpyDeviceToHost, st));
   ISCSI_CUDA(cudaStreamSynchronize(st));
-  return ISCSI_OK;
+  return tc_check(*ctx);
 }
 
 iscsi_status iscsi_davidson(int nroots, double tol, double* energies, void* vecs) {
@@ -111,7 +111,9 @@ iscsi_status iscsi_davidson(int nroots, double tol, double* energies, void* vecs
     set_error("iscsi_davidson: invalid argument");
     return ISCSI_E_ARG;
   }
-  return davidson_run(*ctx, nroots, tol, energies, static_cast<double*>(vecs));
+  int s = davidson_run(*ctx, nroots, tol, energies, static_cast<double*>(vecs));
+  int w = tc_check(*ctx);
+  return s != ISCSI_OK ? s : w;
 }
 
 long long iscsi_ndet(void) {
@@ -222,6 +224,8 @@ iscsi_status iscsi_set_option(const char* key, double value) {
     o.guess_from_vecs = value != 0;
   } else if (k == "use_graph") {
     o.use_graph = value != 0;
+  } else if (k == "fp64_tc") {
+    o.fp64_tc = value != 0;
   } else if (k == "phase_timing") {
     o.phase_timing = value != 0;
     Context* ctx = current();

@@ -155,6 +155,11 @@ struct Context {
   ProblemList<double> pl_ab64, pl_ss64;
   ProblemList<float> pl_ab32, pl_ss32;
   int pl_nvec64 = 0, pl_nvec32 = 0;
+  // tensor-core FP64 opposite-spin contraction (sigma_tc.cu)
+  DevBuf oz_gs, oz_gexp, oz_bs, oz_bexp, oz_probs, oz_err;
+  int oz_mpad = 0, oz_kpad = 0;
+  long long oz_bs_elems = 0;
+  int oz_layout_nvec = -1, oz_probs_nvec = -1, oz_nprobs = 0, oz_tiles = 0;
   // statistics
   double updates_onebody = 0, updates_samespin = 0, updates_opposite = 0;
   long long units_onebody = 0, units_samespin = 0, units_opposite = 0;
@@ -184,6 +189,7 @@ struct Options {
   int guess_from_vecs = 0;
   int use_graph = 1;
   int phase_timing = 0;
+  int fp64_tc = 1;  // FP64 opposite-spin contraction on the tensor cores (exact bf16 slices)
 };
 
 Options& options();
@@ -199,6 +205,10 @@ int sigma_workspace(Context& ctx, int nvec, int precision);
 // algorithmic flops per sigma per vector of the opposite-spin GEMM (which = 0)
 // or of the same-spin GEMMs (which = 1): 2 x M x K x N summed over problems
 double ctx_gemm_flops(const Context& ctx, int which);
+
+// sigma_tc.cu: tensor-core FP64 opposite-spin contraction into the T workspace
+int opposite_tc(Context& ctx, const double* c, double* ttw, int nvec);
+int tc_check(Context& ctx);
 
 // allocation-free single-vector FP64 sigma on a static device array (sigma.cu)
 int sigma_noalloc_run(Context& ctx, const double* c, double* sigma);

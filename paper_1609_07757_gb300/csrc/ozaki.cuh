@@ -1,0 +1,285 @@
+// ozaki.cuh -- FP64-accurate contraction T = A * B^T on the bf16 tensor cores.
+//
+// GB300 runs FP64 at ~1.2 TFLOP/s but bf16 MMA at ~2 PFLOP/s, so the FP64
+// opposite-spin contraction is computed from exact bf16 slices (an error-free
+// splitting in the manner of Ozaki's scheme for accurate matrix products):
+//
+//   each row of A (and of B, stored K-major as [N][K]) is scaled by a power of
+//   two 2^-e so that |x| < 1, then cut into S = 7 slices of 7 bits:
+//     x = 2^-7 sum_t a_t 2^-7t,  a_t integers, |a_0| <= 128, |a_t| <= 64;
+//   slice t is stored as the bf16 value a_t 2^-7t (exact: <= 8 significant bits);
+//   the product sum_k x_k y_k = 2^-14 sum_L 2^-7L I_L with
+//     I_L = sum_k sum_{t+u=L} a_t b_u  (integers);
+//   over a K chunk of 256 every |I_L| <= 256 (L+3) 2^12 <= 2^24, so the FP32
+//   tensor-memory accumulator of each level is exact;
+//   levels L = 0..4 are flushed after every chunk into an exact int64 running
+//   sum S = sum_L 2^7(4-L) I_L; levels 5..6 (weight <= 2^-35 of the leading
+//   one) accumulate in one FP32 tail over the whole K; levels >= 7 are dropped.
+//   T = 2^(e_a + e_b - 14) (S 2^-28 + tail).  The tensor core's FP32
+//   accumulation is exact for the integer-valued levels but biased (it does
+//   not round to nearest) for the tail, so the tail carries only levels whose
+//   weight makes that bias negligible over the whole K.  Relative error
+//   ~2^-48 of sum_k |x_k||y_k| (slice truncation, dropped levels, tail).
+//
+// Tile: 128 rows of A x 64 rows of B per CTA, K step 16 (one MMA), 3-stage
+// cp.async pipeline; one thread issues the 28 MMAs of a K step; 6 TMEM
+// accumulators of 64 columns (levels 0..4 and the tail).
+#pragma once
+#include <cuda_bf16.h>
+
+#include "tc_ptx.cuh"
+
+namespace iscsi {
+
+constexpr int OZ_S = 7;            // slices per operand
+constexpr int OZ_BITS = 7;         // bits per slice
+constexpr int OZ_EXACT = 5;        // levels flushed exactly per chunk
+constexpr int OZ_BM = 128;         // rows of A per tile
+constexpr int OZ_BN = 64;          // rows of B per tile
+constexpr int OZ_BK = 16;          // K per stage (one MMA)
+constexpr int OZ_STAGES = 3;
+constexpr int OZ_CHUNK = 256;      // K per exact flush
+constexpr int OZ_THREADS = 128;
+constexpr int OZ_A_SLICE_BYTES = OZ_BM * OZ_BK * 2;   // 4096
+constexpr int OZ_B_SLICE_BYTES = OZ_BN * OZ_BK * 2;   // 2048
+constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_SLICE_BYTES + OZ_B_SLICE_BYTES);
+constexpr int OZ_SUM_BYTES = OZ_BM * OZ_BN * 8;
+constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + OZ_SUM_BYTES + 1024;
+constexpr int OZ_TMEM_COLS = 512;  // 6 x 64 used
+constexpr long long OZ_SPIN = 1ll << 24;
+
+// One product T[M][N] = A[M][K] * B[N][K]^T from slices.  Slices are zero
+// padded: A rows to a multiple of 128, B rows to a multiple of 64, K to a
+// multiple of 16, so tile loads need no bounds checks.
+struct OzProblem {
+  const __nv_bfloat16* as;  // [S][mpad][kpad]
+  const __nv_bfloat16* bs;  // [S][npad][kpad]
+  long long a_slice, b_slice;  // elements between slices
+  const int* a_exp;         // [M] row exponents of A
+  const int* b_exp;         // [N] row exponents of B
+  double* t;                // [M][ldt]
+  long long ldt;
+  int lda, ldb;             // kpad of each operand (row stride in elements)
+  int M, N, K;              // K = padded K (multiple of 16)
+  int tiles_n, tile_begin;
+};
+
+// row exponent e with max_k |X[r][k]| * 2^-e < 1 (0 for an all-zero row)
+__global__ void k_oz_row_exp(const double* __restrict__ X, int rows, int cols, long long ld, int* __restrict__ e) {
+  int r = blockIdx.x;
+  double m = 0.0;
+  for (int k = threadIdx.x; k < cols; k += blockDim.x) m = fmax(m, fabs(X[(long long)r * ld + k]));
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double sm[32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) x = fmax(x, sm[i]);
+    int ex = 0;
+    if (x > 0.0) frexp(x, &ex);  // x = f 2^ex, f in [0.5, 1)
+    e[r] = ex;
+  }
+}
+
+// slices of X (rows x cols, ld) into out[t][row][k] (row stride ldo, zero padded
+// beyond rows/cols up to rows_pad x ldo)
+__global__ void k_oz_slice(const double* __restrict__ X, int rows, int cols, long long ld, const int* __restrict__ e,
+                           __nv_bfloat16* __restrict__ out, long long slice_stride, int ldo, int rows_pad) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long total = (long long)rows_pad * ldo;
+  if (t >= total) return;
+  int r = (int)(t / ldo), k = (int)(t % ldo);
+  double x = (r < rows && k < cols) ? ldexp(X[(long long)r * ld + k], -e[r]) : 0.0;
+#pragma unroll
+  for (int s = 0; s < OZ_S; ++s) {
+    double v = x * 128.0;
+    double a = rint(v);
+    x = v - a;  // exact
+    out[s * slice_stride + t] = __float2bfloat16_rn((float)ldexp(a, -OZ_BITS * s));
+  }
+}
+
+// [rows x 16] bf16 slice tile, K-major, into core-matrix layout:
+// offset(r, kc) = ((r/8)*2 + kc)*128 + (r%8)*16; LBO = 128 B, SBO = 256 B
+__device__ __forceinline__ void oz_load_unit(uint32_t sbase, const __nv_bfloat16* src_row0, int ld, int unit) {
+  int lane = threadIdx.x & 31;
+  int r = unit * 16 + (lane >> 4) * 8 + (lane & 7);
+  int kc = (lane >> 3) & 1;
+  const __nv_bfloat16* src = src_row0 + (long long)r * ld + kc * 8;
+  uint32_t dst = sbase + (uint32_t)(((r >> 3) * 2 + kc) * 128 + (r & 7) * 16);
+  tc::cp_async16(dst, src);
+}
+
+__device__ __forceinline__ void oz_load_stage(uint32_t sstage, const OzProblem& P, int m0, int n0, int k0) {
+  // 84 units of 32 chunks: A 7 slices x 8 units, B 7 slices x 4 units
+  int warp = threadIdx.x >> 5;
+  for (int u = warp; u < OZ_S * 12; u += OZ_THREADS / 32) {
+    if (u < OZ_S * 8) {
+      int s = u / 8, unit = u % 8;
+      oz_load_unit(sstage + s * OZ_A_SLICE_BYTES, P.as + s * P.a_slice + (long long)m0 * P.lda + k0, P.lda, unit);
+    } else {
+      int v = u - OZ_S * 8;
+      int s = v / 4, unit = v % 4;
+      oz_load_unit(sstage + OZ_S * OZ_A_SLICE_BYTES + s * OZ_B_SLICE_BYTES,
+                   P.bs + s * P.b_slice + (long long)n0 * P.ldb + k0, P.ldb, unit);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_oz_gemm(const OzProblem* __restrict__ probs, int nprobs, int* __restrict__ err) {
+  extern __shared__ unsigned char oz_smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
+  uint32_t s_stage0 = tc::smem_u32(smem);
+  long long* sums = reinterpret_cast<long long*>(smem + OZ_STAGES * OZ_STAGE_BYTES);  // [BN][BM]
+  __shared__ uint64_t mbar[OZ_STAGES];
+  __shared__ uint32_t tmem_s;
+  __shared__ int abort_s;
+
+  int tile = blockIdx.x;
+  int lo = 0, hi = nprobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile_begin <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  const OzProblem P = probs[lo];
+  int tl = tile - P.tile_begin;
+  int m0 = (tl / P.tiles_n) * OZ_BM, n0 = (tl % P.tiles_n) * OZ_BN;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) tc::mbar_init(tc::smem_u32(&mbar[s]), 1);
+    abort_s = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tc::smem_u32(&tmem_s), OZ_TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  for (int i = threadIdx.x; i < OZ_BM * OZ_BN; i += OZ_THREADS) sums[i] = 0;
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_s;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(OZ_BM, OZ_BN);
+
+  const int KT = P.K / OZ_BK;
+  const int steps_per_chunk = OZ_CHUNK / OZ_BK;
+  for (int s = 0; s < OZ_STAGES; ++s) {
+    if (s < KT) oz_load_stage(s_stage0 + s * OZ_STAGE_BYTES, P, m0, n0, s * OZ_BK);
+    tc::cp_async_commit();
+  }
+  bool aborted = false;
+  for (int kt = 0; kt < KT; ++kt) {
+    int st = kt % OZ_STAGES;
+    // tile kt is commit group kt (prologue: 0..S-1, then one group per kt >= 1)
+    if (kt == 0) tc::cp_async_wait<OZ_STAGES - 1>();
+    else tc::cp_async_wait<OZ_STAGES - 2>();
+    tc::fence_proxy_async();
+    __syncthreads();
+    int kin = kt % steps_per_chunk;
+    if (threadIdx.x == 0) {
+      tc::fence_after_sync();
+      uint32_t sa = s_stage0 + st * OZ_STAGE_BYTES;
+      uint32_t sb = sa + OZ_S * OZ_A_SLICE_BYTES;
+#pragma unroll
+      for (int L = 0; L < OZ_S; ++L) {
+        uint32_t acc_col = (uint32_t)((L < OZ_EXACT ? L : OZ_EXACT) * OZ_BN);
+#pragma unroll
+        for (int t = 0; t <= L; ++t) {
+          int u = L - t;
+          uint64_t ad = tc::smem_desc(sa + t * OZ_A_SLICE_BYTES, 128, 256);
+          uint64_t bd = tc::smem_desc(sb + u * OZ_B_SLICE_BYTES, 128, 256);
+          uint32_t accum;
+          if (L < OZ_EXACT) accum = (kin == 0 && t == 0) ? 0u : 1u;
+          else accum = (kt == 0 && L == OZ_EXACT && t == 0) ? 0u : 1u;
+          tc::mma_bf16(tmem + acc_col, ad, bd, idesc, accum);
+        }
+      }
+      tc::mma_commit(tc::smem_u32(&mbar[st]));
+    }
+    bool chunk_end = (kin == steps_per_chunk - 1) || (kt == KT - 1);
+    // refill the stage of tile kt-1 once its MMAs completed
+    if (kt >= 1 && kt - 1 + OZ_STAGES < KT) {
+      int ps = (kt - 1) % OZ_STAGES;
+      if (!tc::mbar_wait_bounded(tc::smem_u32(&mbar[ps]), ((kt - 1) / OZ_STAGES) & 1, OZ_SPIN)) abort_s = 1;
+      else oz_load_stage(s_stage0 + ps * OZ_STAGE_BYTES, P, m0, n0, (kt - 1 + OZ_STAGES) * OZ_BK);
+    }
+    if (kt >= 1) tc::cp_async_commit();
+    if (chunk_end) {
+      // all MMAs of this chunk done -> flush the exact levels into the int64 sums
+      if (!tc::mbar_wait_bounded(tc::smem_u32(&mbar[st]), (kt / OZ_STAGES) & 1, OZ_SPIN)) abort_s = 1;
+      __syncthreads();  // abort_s is uniform below (tcgen05.ld is warp-collective)
+      if (!abort_s) {
+        tc::fence_after_sync();
+        int row = warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
+          uint32_t r0[16], r1[16], r2[16], r3[16], r4[16];
+          tc::tmem_ld16(tmem + lane_base + 0 * OZ_BN + c0, r0);
+          tc::tmem_ld16(tmem + lane_base + 1 * OZ_BN + c0, r1);
+          tc::tmem_ld16(tmem + lane_base + 2 * OZ_BN + c0, r2);
+          tc::tmem_ld16(tmem + lane_base + 3 * OZ_BN + c0, r3);
+          tc::tmem_ld16(tmem + lane_base + 4 * OZ_BN + c0, r4);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            // level L holds 2^-7L I_L exactly; recover the integers
+            int i0 = __float2int_rn(__uint_as_float(r0[j]));
+            int i1 = __float2int_rn(__uint_as_float(r1[j]) * 128.0f);
+            int i2 = __float2int_rn(__uint_as_float(r2[j]) * 16384.0f);
+            int i3 = __float2int_rn(__uint_as_float(r3[j]) * 2097152.0f);
+            int i4 = __float2int_rn(__uint_as_float(r4[j]) * 268435456.0f);
+            long long v = ((long long)i0 << 28) + ((long long)i1 << 21) + ((long long)i2 << 14) +
+                          ((long long)i3 << 7) + (long long)i4;
+            sums[(c0 + j) * OZ_BM + row] += v;
+          }
+        }
+        tc::fence_before_sync();
+      }
+    }
+    __syncthreads();
+    if (abort_s) {
+      aborted = true;
+      break;
+    }
+  }
+  tc::cp_async_wait<0>();
+  __syncthreads();
+  if (aborted || abort_s) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+  } else if (KT > 0) {
+    tc::fence_after_sync();
+    int row = warp * 32 + lane;
+    int gm = m0 + row;
+    int ea = gm < P.M ? P.a_exp[gm] : 0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
+      uint32_t rt[16];
+      tc::tmem_ld16(tmem + lane_base + OZ_EXACT * OZ_BN + c0, rt);
+      tc::tmem_wait_ld();
+      if (gm < P.M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          int gn = n0 + c0 + j;
+          if (gn < P.N) {
+            double v = (double)sums[(c0 + j) * OZ_BM + row] * 3.7252902984619141e-09 /* 2^-28 */ +
+                       (double)__uint_as_float(rt[j]);
+            P.t[(long long)gm * P.ldt + gn] = ldexp(v, ea + P.b_exp[gn] - 14);
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, OZ_TMEM_COLS);
+  }
+}
+
+}  // namespace iscsi

@@ -22,6 +22,7 @@
 //     in registers, so no atomics are needed.
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -454,7 +455,20 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
   }
   int call = ctx.ntimed;
   ISCSI_TRY(timing_event(ctx, call, 0, st));
-  if (ctx.have_ab) {
+  bool tc_path = std::is_same<T, double>::value && options().fp64_tc;
+  if (ctx.have_ab && tc_path) {
+    // FP64 opposite-spin contraction on the tensor cores (lift, slice, GEMM)
+    ClassTable ct = class_table(ctx, nvec);
+    ISCSI_TRY(opposite_tc(ctx, reinterpret_cast<const double*>(c_in), reinterpret_cast<double*>(ttw), nvec));
+    ISCSI_TRY(timing_event(ctx, call, 1, st));
+    ISCSI_TRY(timing_event(ctx, call, 2, st));
+    k_fold<T><<<ctx.sp[0].count, 256, 0, st>>>(ct, nvec, ctx.n, ctx.na, ctx.nb, ctx.sp[1].nhole,
+                                               ctx.sp[0].dec.as<int>(), ctx.sp[1].dec.as<int>(),
+                                               ctx.hp_class.as<int8_t>(), ctx.hp_local.as<int>(),
+                                               ctx.pair_index.as<int>(), ctx.off.as<long long>(), ttw, ctx.ndet, sigma);
+    ISCSI_CUDA(cudaGetLastError());
+    ISCSI_TRY(timing_event(ctx, call, 3, st));
+  } else if (ctx.have_ab) {
     ClassTable ct = class_table(ctx, nvec);
     long long tot = ct.start[ct.nclass];
     if (tot > 0) {

@@ -243,3 +243,21 @@ def test_several_contexts():
     assert L.iscsi_ndet() == -1
     L.iscsi_ctx_use(b)
     assert L.iscsi_ndet() > 0
+
+
+@pytest.mark.parametrize("n,na,nb,k,tau", [(10, 2, 2, 4, 1e-14), (11, 2, 2, 2, 1e-6), (7, 3, 2, 3, 0.0),
+                                           (9, 1, 2, 9, 1e-10)])
+def test_fp64_tensor_core_and_native_paths_agree(n, na, nb, k, tau):
+    h1, eri = make_integrals(n, 1100 + n, ell=3.0, nchol=12)
+    L.iscsi_init(n, na, nb, k, h1, eri, tau)
+    o = Oracle(n, na, nb, k, tau, h1, eri)
+    C = np.stack([unit_vector(o.ndet, 60 + v) for v in range(2)])
+    L.iscsi_set_option("fp64_tc", 1)
+    s_tc = gpu_sigma(C, nvec=2).reshape(2, -1)
+    L.iscsi_set_option("fp64_tc", 0)
+    s_nat = gpu_sigma(C, nvec=2).reshape(2, -1)
+    L.iscsi_set_option("fp64_tc", 1)
+    for v in range(2):
+        ref = o.sigma_terms(C[v])[0]
+        assert_close(s_tc[v], ref, REL64)
+        assert_close(s_nat[v], ref, REL64)
