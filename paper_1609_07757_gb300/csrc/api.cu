@@ -226,6 +226,8 @@ iscsi_status iscsi_set_option(const char* key, double value) {
     o.use_graph = value != 0;
   } else if (k == "fp64_tc") {
     o.fp64_tc = value != 0;
+  } else if (k == "samespin_tc") {
+    o.samespin_tc = value != 0;
   } else if (k == "phase_timing") {
     o.phase_timing = value != 0;
     Context* ctx = current();

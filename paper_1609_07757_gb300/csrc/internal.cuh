@@ -21,6 +21,8 @@
 #include <string>
 #include <vector>
 
+#include "ozaki_types.cuh"
+
 namespace iscsi {
 
 constexpr int kMaxOrb = 256;
@@ -115,6 +117,16 @@ struct ProblemList {
   DevBuf d_probs, d_segs;
 };
 
+// a tensor-core work list (problems + segments) kept on the device
+struct OzJob {
+  std::vector<OzProblem> probs;
+  std::vector<OzSeg> segs;
+  DevBuf d_probs, d_segs;
+  int tiles = 0;
+  int nvec = -1;
+  const void* tbase = nullptr;
+};
+
 struct ColClass {       // column level class c = level(X) + level(Y)
   int level = 0;
   int ncol = 0;         // hole pairs in the class
@@ -155,11 +167,17 @@ struct Context {
   ProblemList<double> pl_ab64, pl_ss64;
   ProblemList<float> pl_ab32, pl_ss32;
   int pl_nvec64 = 0, pl_nvec32 = 0;
-  // tensor-core FP64 opposite-spin contraction (sigma_tc.cu)
-  DevBuf oz_gs, oz_gexp, oz_bs, oz_bexp, oz_probs, oz_err;
+  // tensor-core FP64 contractions (sigma_tc.cu)
+  DevBuf oz_gs, oz_gexp, oz_bs, oz_bexp, oz_err;
   int oz_mpad = 0, oz_kpad = 0;
   long long oz_bs_elems = 0;
-  int oz_layout_nvec = -1, oz_probs_nvec = -1, oz_nprobs = 0, oz_tiles = 0;
+  OzJob oz_ab, oz_ss;
+  DevBuf oz_mas, oz_maexp, oz_mbs, oz_mbexp, oz_cs, oz_csexp;
+  std::vector<int> oz_kbase;
+  int oz_ma_rows = 0, oz_ma_ld = 0, oz_mb_rows = 0, oz_mb_ld = 0;
+  long long oz_cs_elems = 0;
+  bool oz_m_ready = false;
+  int pl_ss_tc = -1;  // same-spin routing the FP64 grouped-GEMM list was built for
   // statistics
   double updates_onebody = 0, updates_samespin = 0, updates_opposite = 0;
   long long units_onebody = 0, units_samespin = 0, units_opposite = 0;
@@ -189,7 +207,8 @@ struct Options {
   int guess_from_vecs = 0;
   int use_graph = 1;
   int phase_timing = 0;
-  int fp64_tc = 1;  // FP64 opposite-spin contraction on the tensor cores (exact bf16 slices)
+  int fp64_tc = 1;      // FP64 opposite-spin contraction on the tensor cores (exact bf16 slices)
+  int samespin_tc = 1;  // same for the same-spin blocks large enough for a 128 x 64 tile
 };
 
 Options& options();
@@ -206,8 +225,12 @@ int sigma_workspace(Context& ctx, int nvec, int precision);
 // or of the same-spin GEMMs (which = 1): 2 x M x K x N summed over problems
 double ctx_gemm_flops(const Context& ctx, int which);
 
-// sigma_tc.cu: tensor-core FP64 opposite-spin contraction into the T workspace
-int opposite_tc(Context& ctx, const double* c, double* ttw, int nvec);
+// sigma_tc.cu: tensor-core FP64 contractions
+int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec);  // slices of Ct
+int opposite_tc_gemm(Context& ctx);                                                // T = G Ct
+bool samespin_block_on_tc(const Context& ctx, int a);
+bool samespin_tc_active(const Context& ctx);
+int samespin_tc(Context& ctx, const double* c, double* sigma, int nvec);           // sigma += same-spin
 int tc_check(Context& ctx);
 
 // allocation-free single-vector FP64 sigma on a static device array (sigma.cu)

@@ -27,48 +27,19 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include "ozaki_types.cuh"
 #include "tc_ptx.cuh"
 
 namespace iscsi {
 
-constexpr int OZ_S = 7;            // slices per operand
-constexpr int OZ_BITS = 7;         // bits per slice
-constexpr int OZ_EXACT = 5;        // levels flushed exactly per chunk
-constexpr int OZ_BM = 128;         // rows of A per tile
-constexpr int OZ_BN = 64;          // rows of B per tile
-constexpr int OZ_BK = 16;          // K per stage (one MMA)
-constexpr int OZ_STAGES = 3;
-constexpr int OZ_CHUNK = 256;      // K per exact flush
-constexpr int OZ_THREADS = 128;
-constexpr int OZ_A_SLICE_BYTES = OZ_BM * OZ_BK * 2;   // 4096
-constexpr int OZ_B_SLICE_BYTES = OZ_BN * OZ_BK * 2;   // 2048
-constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_SLICE_BYTES + OZ_B_SLICE_BYTES);
-constexpr int OZ_SUM_BYTES = OZ_BM * OZ_BN * 8;
-constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + OZ_SUM_BYTES + 1024;
-constexpr int OZ_TMEM_COLS = 512;  // 6 x 64 used
-constexpr long long OZ_SPIN = 1ll << 24;
-
-// One product T[M][N] = A[M][K] * B[N][K]^T from slices.  Slices are zero
-// padded: A rows to a multiple of 128, B rows to a multiple of 64, K to a
-// multiple of 16, so tile loads need no bounds checks.
-struct OzProblem {
-  const __nv_bfloat16* as;  // [S][mpad][kpad]
-  const __nv_bfloat16* bs;  // [S][npad][kpad]
-  long long a_slice, b_slice;  // elements between slices
-  const int* a_exp;         // [M] row exponents of A
-  const int* b_exp;         // [N] row exponents of B
-  double* t;                // [M][ldt]
-  long long ldt;
-  int lda, ldb;             // kpad of each operand (row stride in elements)
-  int M, N, K;              // K = padded K (multiple of 16)
-  int tiles_n, tile_begin;
-};
-
-// row exponent e with max_k |X[r][k]| * 2^-e < 1 (0 for an all-zero row)
-__global__ void k_oz_row_exp(const double* __restrict__ X, int rows, int cols, long long ld, int* __restrict__ e) {
+// row exponent e with max_k |X(r,k)| * 2^-e < 1 (0 for an all-zero row);
+// X(r,k) = X[r*ld + k], or X[k*ld + r] when trans
+__global__ void k_oz_row_exp(const double* __restrict__ X, int rows, int cols, long long ld, int trans,
+                             int* __restrict__ e) {
   int r = blockIdx.x;
   double m = 0.0;
-  for (int k = threadIdx.x; k < cols; k += blockDim.x) m = fmax(m, fabs(X[(long long)r * ld + k]));
+  for (int k = threadIdx.x; k < cols; k += blockDim.x)
+    m = fmax(m, fabs(trans ? X[(long long)k * ld + r] : X[(long long)r * ld + k]));
   for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   __shared__ double sm[32];
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
@@ -82,15 +53,19 @@ __global__ void k_oz_row_exp(const double* __restrict__ X, int rows, int cols, l
   }
 }
 
-// slices of X (rows x cols, ld) into out[t][row][k] (row stride ldo, zero padded
-// beyond rows/cols up to rows_pad x ldo)
-__global__ void k_oz_slice(const double* __restrict__ X, int rows, int cols, long long ld, const int* __restrict__ e,
+// slices of X into out[s][row][k] (row stride ldo, rows_pad rows, zero padded).
+// Source column of k: colmap[k] (-1: zero) if colmap, else k (zero beyond cols).
+__global__ void k_oz_slice(const double* __restrict__ X, int rows, int cols, long long ld, int trans,
+                           const int* __restrict__ colmap, const int* __restrict__ e,
                            __nv_bfloat16* __restrict__ out, long long slice_stride, int ldo, int rows_pad) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long total = (long long)rows_pad * ldo;
   if (t >= total) return;
   int r = (int)(t / ldo), k = (int)(t % ldo);
-  double x = (r < rows && k < cols) ? ldexp(X[(long long)r * ld + k], -e[r]) : 0.0;
+  int src = colmap ? colmap[k] : (k < cols ? k : -1);
+  double x = 0.0;
+  if (r < rows && src >= 0)
+    x = ldexp(trans ? X[(long long)src * ld + r] : X[(long long)r * ld + src], -e[r]);
 #pragma unroll
   for (int s = 0; s < OZ_S; ++s) {
     double v = x * 128.0;
@@ -111,24 +86,25 @@ __device__ __forceinline__ void oz_load_unit(uint32_t sbase, const __nv_bfloat16
   tc::cp_async16(dst, src);
 }
 
-__device__ __forceinline__ void oz_load_stage(uint32_t sstage, const OzProblem& P, int m0, int n0, int k0) {
+__device__ __forceinline__ void oz_load_stage(uint32_t sstage, const OzSeg& S, int m0, int n0, int k0) {
   // 84 units of 32 chunks: A 7 slices x 8 units, B 7 slices x 4 units
   int warp = threadIdx.x >> 5;
   for (int u = warp; u < OZ_S * 12; u += OZ_THREADS / 32) {
     if (u < OZ_S * 8) {
       int s = u / 8, unit = u % 8;
-      oz_load_unit(sstage + s * OZ_A_SLICE_BYTES, P.as + s * P.a_slice + (long long)m0 * P.lda + k0, P.lda, unit);
+      oz_load_unit(sstage + s * OZ_A_SLICE_BYTES, S.as + s * S.a_slice + (long long)m0 * S.lda + k0, S.lda, unit);
     } else {
       int v = u - OZ_S * 8;
       int s = v / 4, unit = v % 4;
       oz_load_unit(sstage + OZ_S * OZ_A_SLICE_BYTES + s * OZ_B_SLICE_BYTES,
-                   P.bs + s * P.b_slice + (long long)n0 * P.ldb + k0, P.ldb, unit);
+                   S.bs + s * S.b_slice + (long long)n0 * S.ldb + k0, S.ldb, unit);
     }
   }
 }
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    k_oz_gemm(const OzProblem* __restrict__ probs, int nprobs, int* __restrict__ err) {
+    k_oz_gemm(const OzProblem* __restrict__ probs, int nprobs, const OzSeg* __restrict__ segs, double* tbase,
+              int* __restrict__ err) {
   extern __shared__ unsigned char oz_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
   uint32_t s_stage0 = tc::smem_u32(smem);
@@ -136,6 +112,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   __shared__ uint64_t mbar[OZ_STAGES];
   __shared__ uint32_t tmem_s;
   __shared__ int abort_s;
+  __shared__ OzSeg seg_s[OZ_MAX_SEGS];
+  __shared__ int step0_s[OZ_MAX_SEGS + 1];
+  __shared__ int nseg_s;
 
   int tile = blockIdx.x;
   int lo = 0, hi = nprobs - 1;
@@ -145,6 +124,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     else hi = mid - 1;
   }
   const OzProblem P = probs[lo];
+  double* const Tp = P.t_rel ? tbase + P.t : reinterpret_cast<double*>(P.t);
   int tl = tile - P.tile_begin;
   int m0 = (tl / P.tiles_n) * OZ_BM, n0 = (tl % P.tiles_n) * OZ_BN;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -152,6 +132,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < OZ_STAGES; ++s) tc::mbar_init(tc::smem_u32(&mbar[s]), 1);
     abort_s = 0;
+    // the segments that reach this tile, and their first global K step
+    int ns = 0, steps = 0;
+    for (int g = 0; g < P.seg_count && ns < OZ_MAX_SEGS; ++g) {
+      OzSeg sg = segs[P.seg_begin + g];
+      if (n0 >= sg.nrows_b || sg.K <= 0) continue;
+      seg_s[ns] = sg;
+      step0_s[ns] = steps;
+      steps += sg.K / OZ_BK;
+      ++ns;
+    }
+    step0_s[ns] = steps;
+    nseg_s = ns;
     tc::fence_mbar_init();
   }
   if (warp == 0) {
@@ -165,22 +157,38 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const uint32_t tmem = tmem_s;
   const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
   constexpr uint32_t idesc = tc::idesc_bf16_f32(OZ_BM, OZ_BN);
+  const int nseg = nseg_s;
+  const int total = step0_s[nseg];
+  const int row = warp * 32 + lane;
+  const int gm = m0 + row;
 
-  const int KT = P.K / OZ_BK;
-  const int steps_per_chunk = OZ_CHUNK / OZ_BK;
+  auto seg_of = [&](int g) {
+    int s = 0;
+    while (s + 1 < nseg && g >= step0_s[s + 1]) ++s;
+    return s;
+  };
+  auto load_step = [&](int g, int stage) {
+    int s = seg_of(g);
+    oz_load_stage(s_stage0 + stage * OZ_STAGE_BYTES, seg_s[s], m0, n0, (g - step0_s[s]) * OZ_BK);
+  };
+
   for (int s = 0; s < OZ_STAGES; ++s) {
-    if (s < KT) oz_load_stage(s_stage0 + s * OZ_STAGE_BYTES, P, m0, n0, s * OZ_BK);
+    if (s < total) load_step(s, s);
     tc::cp_async_commit();
   }
   bool aborted = false;
-  for (int kt = 0; kt < KT; ++kt) {
-    int st = kt % OZ_STAGES;
-    // tile kt is commit group kt (prologue: 0..S-1, then one group per kt >= 1)
-    if (kt == 0) tc::cp_async_wait<OZ_STAGES - 1>();
+  int done_segs = 0;
+  for (int g = 0; g < total; ++g) {
+    int st = g % OZ_STAGES;
+    // step g is commit group g (prologue: 0..S-1, then one group per g >= 1)
+    if (g == 0) tc::cp_async_wait<OZ_STAGES - 1>();
     else tc::cp_async_wait<OZ_STAGES - 2>();
     tc::fence_proxy_async();
     __syncthreads();
-    int kin = kt % steps_per_chunk;
+    int sgi = seg_of(g);
+    int local = g - step0_s[sgi];
+    int seg_steps = step0_s[sgi + 1] - step0_s[sgi];
+    int kin = local % (OZ_CHUNK / OZ_BK);
     if (threadIdx.x == 0) {
       tc::fence_after_sync();
       uint32_t sa = s_stage0 + st * OZ_STAGE_BYTES;
@@ -195,27 +203,29 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           uint64_t bd = tc::smem_desc(sb + u * OZ_B_SLICE_BYTES, 128, 256);
           uint32_t accum;
           if (L < OZ_EXACT) accum = (kin == 0 && t == 0) ? 0u : 1u;
-          else accum = (kt == 0 && L == OZ_EXACT && t == 0) ? 0u : 1u;
+          else accum = (local == 0 && L == OZ_EXACT && t == 0) ? 0u : 1u;
           tc::mma_bf16(tmem + acc_col, ad, bd, idesc, accum);
         }
       }
       tc::mma_commit(tc::smem_u32(&mbar[st]));
     }
-    bool chunk_end = (kin == steps_per_chunk - 1) || (kt == KT - 1);
-    // refill the stage of tile kt-1 once its MMAs completed
-    if (kt >= 1 && kt - 1 + OZ_STAGES < KT) {
-      int ps = (kt - 1) % OZ_STAGES;
-      if (!tc::mbar_wait_bounded(tc::smem_u32(&mbar[ps]), ((kt - 1) / OZ_STAGES) & 1, OZ_SPIN)) abort_s = 1;
-      else oz_load_stage(s_stage0 + ps * OZ_STAGE_BYTES, P, m0, n0, (kt - 1 + OZ_STAGES) * OZ_BK);
+    // refill the stage of step g-1 once its MMAs completed
+    if (g >= 1 && g - 1 + OZ_STAGES < total) {
+      int ps = (g - 1) % OZ_STAGES;
+      if (!tc::mbar_wait_bounded(tc::smem_u32(&mbar[ps]), ((g - 1) / OZ_STAGES) & 1, OZ_SPIN)) abort_s = 1;
+      else load_step(g - 1 + OZ_STAGES, ps);
     }
-    if (kt >= 1) tc::cp_async_commit();
+    if (g >= 1) tc::cp_async_commit();
+    bool seg_end = (local == seg_steps - 1);
+    bool chunk_end = (kin == OZ_CHUNK / OZ_BK - 1) || seg_end;
     if (chunk_end) {
-      // all MMAs of this chunk done -> flush the exact levels into the int64 sums
-      if (!tc::mbar_wait_bounded(tc::smem_u32(&mbar[st]), (kt / OZ_STAGES) & 1, OZ_SPIN)) abort_s = 1;
+      // all MMAs so far done -> flush the exact levels into the int64 sums
+      if (!tc::mbar_wait_bounded(tc::smem_u32(&mbar[st]), (g / OZ_STAGES) & 1, OZ_SPIN)) abort_s = 1;
       __syncthreads();  // abort_s is uniform below (tcgen05.ld is warp-collective)
       if (!abort_s) {
         tc::fence_after_sync();
-        int row = warp * 32 + lane;
+        const OzSeg& S = seg_s[sgi];
+        int ea = (seg_end && gm < P.M) ? S.a_exp[gm] : 0;
 #pragma unroll 1
         for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
           uint32_t r0[16], r1[16], r2[16], r3[16], r4[16];
@@ -237,9 +247,28 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                           ((long long)i3 << 7) + (long long)i4;
             sums[(c0 + j) * OZ_BM + row] += v;
           }
+          if (seg_end) {
+            // this segment's result: 2^(ea+eb-14) (S 2^-28 + tail), into T
+            uint32_t rt[16];
+            tc::tmem_ld16(tmem + lane_base + OZ_EXACT * OZ_BN + c0, rt);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              int gn = n0 + c0 + j;
+              long long sv = sums[(c0 + j) * OZ_BM + row];
+              sums[(c0 + j) * OZ_BM + row] = 0;
+              if (gm < P.M && gn < P.N && gn < S.nrows_b) {
+                double v = (double)sv * 3.7252902984619141e-09 /* 2^-28 */ + (double)__uint_as_float(rt[j]);
+                v = ldexp(v, ea + S.b_exp[gn] - 14);
+                double* dst = Tp + (long long)gm * P.ldt + gn;
+                *dst = (P.accumulate || done_segs > 0) ? *dst + v : v;
+              }
+            }
+          }
         }
         tc::fence_before_sync();
       }
+      if (seg_end) ++done_segs;
     }
     __syncthreads();
     if (abort_s) {
@@ -251,28 +280,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   __syncthreads();
   if (aborted || abort_s) {
     if (threadIdx.x == 0) atomicExch(err, 1);
-  } else if (KT > 0) {
-    tc::fence_after_sync();
-    int row = warp * 32 + lane;
-    int gm = m0 + row;
-    int ea = gm < P.M ? P.a_exp[gm] : 0;
-#pragma unroll 1
-    for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
-      uint32_t rt[16];
-      tc::tmem_ld16(tmem + lane_base + OZ_EXACT * OZ_BN + c0, rt);
-      tc::tmem_wait_ld();
-      if (gm < P.M) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          int gn = n0 + c0 + j;
-          if (gn < P.N) {
-            double v = (double)sums[(c0 + j) * OZ_BM + row] * 3.7252902984619141e-09 /* 2^-28 */ +
-                       (double)__uint_as_float(rt[j]);
-            P.t[(long long)gm * P.ldt + gn] = ldexp(v, ea + P.b_exp[gn] - 14);
-          }
-        }
+  } else if (nseg == 0 && !P.accumulate) {
+    // no segment reaches this tile: its block of T is zero
+    if (gm < P.M)
+      for (int j = 0; j < OZ_BN; ++j) {
+        int gn = n0 + j;
+        if (gn < P.N) Tp[(long long)gm * P.ldt + gn] = 0.0;
       }
-    }
   }
   tc::fence_before_sync();
   __syncthreads();

@@ -322,6 +322,7 @@ static int build_problems(Context& ctx, int nvec, const T* G, const T* Ma, const
       int rows = SA.level_start[a + 1] - SA.level_start[a];
       int nba = (int)ctx.nb_allowed_lvl[a];
       if (rows == 0 || nba == 0) continue;
+      if (std::is_same<T, double>::value && ctx.pl_ss_tc == 1 && samespin_block_on_tc(ctx, a)) continue;
       long long obase = ctx.off_h[SA.level_start[a]];
       Problem<T> p;
       p.c = (long long)v * ctx.ndet + obase;
@@ -448,7 +449,12 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
   cudaStream_t st = stream();
   T* ctw = ctx.ct.as<T>();
   T* ttw = ctx.tt.as<T>();
-  // problem lists depend on nvec and the workspaces, not on the vectors
+  // problem lists depend on nvec, the workspaces and the same-spin routing, not on the vectors
+  int ss_tc = (std::is_same<T, double>::value && samespin_tc_active(ctx)) ? 1 : 0;
+  if (std::is_same<T, double>::value && ctx.pl_ss_tc != ss_tc) {
+    ctx.pl_ss_tc = ss_tc;
+    pl_nvec = 0;
+  }
   if (pl_nvec != nvec) {
     ISCSI_TRY(build_problems<T>(ctx, nvec, G, Ma, Mb, ctw, ttw, ab, ss));
     pl_nvec = nvec;
@@ -457,10 +463,11 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
   ISCSI_TRY(timing_event(ctx, call, 0, st));
   bool tc_path = std::is_same<T, double>::value && options().fp64_tc;
   if (ctx.have_ab && tc_path) {
-    // FP64 opposite-spin contraction on the tensor cores (lift, slice, GEMM)
+    // FP64 opposite-spin contraction on the tensor cores (lift + slice, GEMM)
     ClassTable ct = class_table(ctx, nvec);
-    ISCSI_TRY(opposite_tc(ctx, reinterpret_cast<const double*>(c_in), reinterpret_cast<double*>(ttw), nvec));
+    ISCSI_TRY(opposite_tc_operands(ctx, reinterpret_cast<const double*>(c_in), reinterpret_cast<double*>(ttw), nvec));
     ISCSI_TRY(timing_event(ctx, call, 1, st));
+    ISCSI_TRY(opposite_tc_gemm(ctx));
     ISCSI_TRY(timing_event(ctx, call, 2, st));
     k_fold<T><<<ctx.sp[0].count, 256, 0, st>>>(ct, nvec, ctx.n, ctx.na, ctx.nb, ctx.sp[1].nhole,
                                                ctx.sp[0].dec.as<int>(), ctx.sp[1].dec.as<int>(),
@@ -494,6 +501,8 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
     ISCSI_TRY(timing_event(ctx, call, 3, st));
   }
   ISCSI_TRY(launch_grouped<T>(ss, c, sigma, st));
+  if (ss_tc)
+    ISCSI_TRY(samespin_tc(ctx, reinterpret_cast<const double*>(c), reinterpret_cast<double*>(sigma), nvec));
   ISCSI_TRY(timing_event(ctx, call, 4, st));
   if (options().phase_timing && call < Context::kMaxTimed) ctx.ntimed++;
   (void)s_out;

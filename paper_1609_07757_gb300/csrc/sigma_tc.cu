@@ -1,13 +1,19 @@
-// sigma_tc.cu -- the opposite-spin contraction of the FP64 sigma step on the
-// tensor cores (tcgen05), with FP64 accuracy from exact bf16 slices (ozaki.cuh).
+// sigma_tc.cu -- the FP64 sigma step's contractions on the tensor cores
+// (tcgen05), with FP64 accuracy from exact bf16 slices (ozaki.cuh).
 //
-// Per sigma call and column level class c:
-//   1. k_oz_col_exp   : exponent of the largest |Ct| in each column (X,Y,v)
-//   2. k_oz_lift_slice: Ct^T[(X,Y,v)][(q,s)] = s s c[X u q, Y u s] gathered
-//                       through the contraction/addition tables and cut into
-//                       7 bf16 slices (the B operand, K-major)
-//   3. k_oz_gemm      : T_c = G[:M_c, :K_c] Ct_c for all classes in one launch
-// G's slices are built once per context (first use).
+// Opposite spin, per sigma call and column level class c:
+//   k_oz_col_exp    : exponent of the largest |Ct| in each column (X,Y,v)
+//   k_oz_lift_slice : Ct^T[(X,Y,v)][(q,s)] = s s c[X u q, Y u s], gathered
+//                     through the contraction/addition tables and cut into 7
+//                     bf16 slices (the B operand, K-major)
+//   k_oz_gemm       : T_c = G[:M_c, :K_c] Ct_c for all classes, one launch
+// Same spin, per excitation-level block a of the CI vector (rows = alpha
+// strings of level a, columns = the allowed beta prefix):
+//   sigma_a += sum_a' M_alpha[a, a'] C_a'   (A = M_alpha slices, B = C_a'^T)
+//            + C_a M_beta^T                 (A = C_a slices, B = M_beta slices)
+// as one multi-segment product per block; blocks too small for a 128 x 64
+// tile stay on the FP64 grouped GEMM of sigma.cu.
+// G's, M_alpha's and M_beta's slices are built once per context (first use).
 #include <algorithm>
 #include <climits>
 #include <cstring>
@@ -19,6 +25,7 @@
 namespace iscsi {
 
 struct TcClass {
+  int mrows;        // rows of T_c
   int ncols;        // hole pairs x vectors
   int krows;        // K of the class
   int kpad;         // krows rounded up to 16
@@ -35,6 +42,8 @@ struct TcTable {
   TcClass c[2 * kMaxElec];
   long long start[2 * kMaxElec + 1];  // flattened (col, k) element offsets
 };
+
+static inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 __device__ __forceinline__ double tc_gather(const TcClass& C, int nvec, int col, int k, int n, int nholeA,
                                             int nholeB, const int* __restrict__ pair_of,
@@ -117,111 +126,174 @@ __global__ void k_oz_lift_slice(TcTable tt, int n, int nholeA, int nholeB, const
   }
 }
 
-static int tc_prepare_g(Context& ctx) {
-  if (ctx.oz_gs.p) return kOk;
-  cudaStream_t st = stream();
-  int np = ctx.npairs;
-  ctx.oz_mpad = (np + OZ_BM - 1) / OZ_BM * OZ_BM;
-  ctx.oz_kpad = (np + OZ_BK - 1) / OZ_BK * OZ_BK;
-  long long slice = (long long)ctx.oz_mpad * ctx.oz_kpad;
-  ISCSI_TRY(ctx.oz_gs.alloc(sizeof(__nv_bfloat16) * slice * OZ_S));
-  ISCSI_TRY(ctx.oz_gexp.alloc(sizeof(int) * np));
-  ISCSI_TRY(ctx.oz_err.alloc(sizeof(int)));
-  ISCSI_CUDA(cudaMemsetAsync(ctx.oz_err.p, 0, sizeof(int), st));
-  k_oz_row_exp<<<np, 256, 0, st>>>(ctx.G64.as<double>(), np, np, np, ctx.oz_gexp.as<int>());
-  k_oz_slice<<<launch_blocks(slice, 256), 256, 0, st>>>(ctx.G64.as<double>(), np, np, np, ctx.oz_gexp.as<int>(),
-                                                        ctx.oz_gs.as<__nv_bfloat16>(), slice, ctx.oz_kpad,
-                                                        ctx.oz_mpad);
-  ISCSI_CUDA(cudaGetLastError());
-  static bool attr_done = false;
-  if (!attr_done) {
+static int tc_attr() {
+  static bool done = false;
+  if (!done) {
     ISCSI_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES));
-    attr_done = true;
+    done = true;
   }
   return kOk;
 }
 
-// T_c for all column classes (FP64 out, layout of the fold's workspace)
-int opposite_tc(Context& ctx, const double* c, double* ttw, int nvec) {
+static int tc_err_buf(Context& ctx) {
+  if (ctx.oz_err.p) return kOk;
+  ISCSI_TRY(ctx.oz_err.alloc(sizeof(int)));
+  ISCSI_CUDA(cudaMemsetAsync(ctx.oz_err.p, 0, sizeof(int), stream()));
+  return kOk;
+}
+
+// slices of a row-major (or transposed) FP64 matrix with per-row exponents
+static int slice_matrix(const double* X, int rows, int cols, long long ld, int trans, const int* colmap, int ldo,
+                        int rows_pad, int* exps, __nv_bfloat16* out, cudaStream_t st) {
+  if (rows > 0) k_oz_row_exp<<<rows, 256, 0, st>>>(X, rows, cols, ld, trans, exps);
+  long long slice = (long long)rows_pad * ldo;
+  if (slice > 0)
+    k_oz_slice<<<launch_blocks(slice, 256), 256, 0, st>>>(X, rows, cols, ld, trans, colmap, exps, out, slice, ldo,
+                                                          rows_pad);
+  ISCSI_CUDA(cudaGetLastError());
+  return kOk;
+}
+
+static int tc_prepare_g(Context& ctx) {
+  if (ctx.oz_gs.p) return kOk;
   cudaStream_t st = stream();
-  ISCSI_TRY(tc_prepare_g(ctx));
+  ISCSI_TRY(tc_attr());
+  ISCSI_TRY(tc_err_buf(ctx));
+  int np = ctx.npairs;
+  ctx.oz_mpad = round_up(np, OZ_BM);
+  ctx.oz_kpad = round_up(np, OZ_BK);
+  long long slice = (long long)ctx.oz_mpad * ctx.oz_kpad;
+  ISCSI_TRY(ctx.oz_gs.alloc(sizeof(__nv_bfloat16) * slice * OZ_S));
+  ISCSI_TRY(ctx.oz_gexp.alloc(sizeof(int) * np));
+  return slice_matrix(ctx.G64.as<double>(), np, np, np, 0, nullptr, ctx.oz_kpad, ctx.oz_mpad, ctx.oz_gexp.as<int>(),
+                      ctx.oz_gs.as<__nv_bfloat16>(), st);
+}
+
+static int upload_job(OzJob& job, cudaStream_t st) {
+  ISCSI_TRY(job.d_probs.grow(sizeof(OzProblem) * std::max<size_t>(1, job.probs.size())));
+  ISCSI_TRY(job.d_segs.grow(sizeof(OzSeg) * std::max<size_t>(1, job.segs.size())));
+  if (!job.probs.empty())
+    ISCSI_CUDA(cudaMemcpyAsync(job.d_probs.p, job.probs.data(), sizeof(OzProblem) * job.probs.size(),
+                               cudaMemcpyHostToDevice, st));
+  if (!job.segs.empty())
+    ISCSI_CUDA(cudaMemcpyAsync(job.d_segs.p, job.segs.data(), sizeof(OzSeg) * job.segs.size(), cudaMemcpyHostToDevice,
+                               st));
+  ISCSI_CUDA(cudaStreamSynchronize(st));  // the host vectors must outlive the copies
+  return kOk;
+}
+
+static int launch_job(Context& ctx, const OzJob& job, double* tbase, cudaStream_t st) {
+  if (job.tiles == 0) return kOk;
+  k_oz_gemm<<<job.tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(job.d_probs.as<OzProblem>(), (int)job.probs.size(),
+                                                          job.d_segs.as<OzSeg>(), tbase, ctx.oz_err.as<int>());
+  ISCSI_CUDA(cudaGetLastError());
+  return kOk;
+}
+
+static int add_tiles(std::vector<OzProblem>& probs) {
+  int tiles = 0;
+  for (auto& p : probs) {
+    p.tiles_n = round_up(p.N, OZ_BN) / OZ_BN;
+    p.tile_begin = tiles;
+    tiles += (round_up(p.M, OZ_BM) / OZ_BM) * p.tiles_n;
+  }
+  return tiles;
+}
+
+// ---------------------------------------------------------------------------
+// opposite spin
+
+static TcTable ab_table(const Context& ctx, int nvec, long long* bs_elems, long long* exp_elems) {
   TcTable tt;
   std::memset(&tt, 0, sizeof(tt));
   tt.nvec = nvec;
-  std::vector<OzProblem> probs;
-  long long bs_elems = 0, exp_elems = 0, flat = 0, t_off = 0;
-  int tiles = 0;
+  long long bs = 0, ex = 0, flat = 0;
   for (int cl = 0; cl < (int)ctx.cls.size(); ++cl) {
     const ColClass& cc = ctx.cls[cl];
     if (cc.ncol == 0 || cc.mrows == 0) continue;
     TcClass C;
+    C.mrows = cc.mrows;
     C.ncols = cc.ncol * nvec;
     C.krows = cc.krows;
-    C.kpad = (cc.krows + OZ_BK - 1) / OZ_BK * OZ_BK;
-    C.npad = (C.ncols + OZ_BN - 1) / OZ_BN * OZ_BN;
+    C.kpad = round_up(cc.krows, OZ_BK);
+    C.npad = round_up(C.ncols, OZ_BN);
     C.hp_start = ctx.hp_class_start[cl];
-    C.bs_off = bs_elems;
-    C.exp_off = exp_elems;
+    C.bs_off = bs;
+    C.exp_off = ex;
     C.tot = (long long)C.ncols * C.kpad;
     tt.start[tt.nclass] = flat;
     tt.c[tt.nclass++] = C;
     flat += C.tot;
-    OzProblem P;
-    P.as = nullptr;  // set below (base pointer known after allocation)
-    P.a_slice = (long long)ctx.oz_mpad * ctx.oz_kpad;
-    P.b_slice = (long long)C.npad * C.kpad;
-    P.lda = ctx.oz_kpad;
-    P.ldb = C.kpad;
-    P.M = cc.mrows;
-    P.N = C.ncols;
-    P.K = C.kpad;
-    P.ldt = C.ncols;
-    P.tiles_n = C.npad / OZ_BN;
-    P.tile_begin = tiles;
-    tiles += ((cc.mrows + OZ_BM - 1) / OZ_BM) * P.tiles_n;
-    // T_c sits where the fold expects it: classes in order, mrows x ncols each
-    P.t = ttw + t_off;
-    t_off += (long long)cc.mrows * C.ncols;
-    probs.push_back(P);
-    bs_elems += (long long)OZ_S * C.npad * C.kpad;
-    exp_elems += C.ncols;
+    bs += (long long)OZ_S * C.npad * C.kpad;
+    ex += C.ncols;
   }
   tt.start[tt.nclass] = flat;
-  if (probs.empty()) return kOk;
+  *bs_elems = bs;
+  *exp_elems = ex;
+  return tt;
+}
+
+int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec) {
+  cudaStream_t st = stream();
+  ISCSI_TRY(tc_prepare_g(ctx));
+  long long bs_elems = 0, exp_elems = 0;
+  TcTable tt = ab_table(ctx, nvec, &bs_elems, &exp_elems);
+  if (tt.nclass == 0) return kOk;
+  bool rebuild = ctx.oz_ab.nvec != nvec || ctx.oz_ab.tbase != (const void*)ttw;
   if (ctx.oz_bs_elems < bs_elems) {
     ISCSI_TRY(ctx.oz_bs.alloc(sizeof(__nv_bfloat16) * bs_elems));
-    // padding rows of every class stay zero from here on
-    ISCSI_CUDA(cudaMemsetAsync(ctx.oz_bs.p, 0, sizeof(__nv_bfloat16) * bs_elems, st));
     ctx.oz_bs_elems = bs_elems;
-    ctx.oz_layout_nvec = -1;
-    ctx.oz_probs_nvec = -1;  // slice base pointers changed
-  } else if (ctx.oz_layout_nvec != nvec) {
-    ISCSI_CUDA(cudaMemsetAsync(ctx.oz_bs.p, 0, sizeof(__nv_bfloat16) * ctx.oz_bs_elems, st));
+    rebuild = true;
   }
-  ctx.oz_layout_nvec = nvec;
   if ((long long)(ctx.oz_bexp.bytes / sizeof(int)) < exp_elems) {
     ISCSI_TRY(ctx.oz_bexp.alloc(sizeof(int) * exp_elems));
-    ctx.oz_probs_nvec = -1;
+    rebuild = true;
   }
-  if (ctx.oz_probs_nvec != nvec) {
-    // the problem list depends on nvec and the workspaces only: upload once
-    ISCSI_TRY(ctx.oz_probs.grow(sizeof(OzProblem) * probs.size()));
-    for (size_t i = 0; i < probs.size(); ++i) {
-      probs[i].as = ctx.oz_gs.as<__nv_bfloat16>();
-      probs[i].a_exp = ctx.oz_gexp.as<int>();
-      probs[i].bs = ctx.oz_bs.as<__nv_bfloat16>() + tt.c[i].bs_off;
-      probs[i].b_exp = ctx.oz_bexp.as<int>() + tt.c[i].exp_off;
+  if (rebuild) {
+    // padding rows of every class stay zero from here on
+    ISCSI_CUDA(cudaMemsetAsync(ctx.oz_bs.p, 0, sizeof(__nv_bfloat16) * ctx.oz_bs_elems, st));
+    OzJob& job = ctx.oz_ab;
+    job.probs.clear();
+    job.segs.clear();
+    long long t_off = 0;
+    for (int i = 0; i < tt.nclass; ++i) {
+      const TcClass& C = tt.c[i];
+      OzSeg sg;
+      sg.as = ctx.oz_gs.as<__nv_bfloat16>();
+      sg.bs = ctx.oz_bs.as<__nv_bfloat16>() + C.bs_off;
+      sg.a_slice = (long long)ctx.oz_mpad * ctx.oz_kpad;
+      sg.b_slice = (long long)C.npad * C.kpad;
+      sg.a_exp = ctx.oz_gexp.as<int>();
+      sg.b_exp = ctx.oz_bexp.as<int>() + C.exp_off;
+      sg.lda = ctx.oz_kpad;
+      sg.ldb = C.kpad;
+      sg.K = C.kpad;
+      sg.nrows_b = C.ncols;
+      OzProblem P;
+      std::memset(&P, 0, sizeof(P));
+      // T_c sits where the fold expects it: classes in order, mrows x ncols each
+      int mrows = C.mrows;
+      P.t = (long long)reinterpret_cast<uintptr_t>(ttw + t_off);
+      P.t_rel = 0;
+      P.ldt = C.ncols;
+      P.M = mrows;
+      P.N = C.ncols;
+      P.seg_begin = (int)job.segs.size();
+      P.seg_count = 1;
+      P.accumulate = 0;
+      t_off += (long long)mrows * C.ncols;
+      job.segs.push_back(sg);
+      job.probs.push_back(P);
     }
-    ISCSI_CUDA(cudaMemcpyAsync(ctx.oz_probs.p, probs.data(), sizeof(OzProblem) * probs.size(),
-                               cudaMemcpyHostToDevice, st));
-    ISCSI_CUDA(cudaStreamSynchronize(st));  // probs must outlive the copy
-    ctx.oz_probs_nvec = nvec;
-    ctx.oz_nprobs = (int)probs.size();
-    ctx.oz_tiles = tiles;
+    job.tiles = add_tiles(job.probs);
+    ISCSI_TRY(upload_job(job, st));
+    job.nvec = nvec;
+    job.tbase = ttw;
   }
   k_oz_fill_int<<<launch_blocks(exp_elems, 256), 256, 0, st>>>(ctx.oz_bexp.as<int>(), exp_elems, INT_MIN);
   const SpinSpace& SA = ctx.sp[0];
   const SpinSpace& SB = ctx.sp[1];
+  long long flat = tt.start[tt.nclass];
   k_oz_col_exp<<<launch_blocks(flat, 256), 256, 0, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_of.as<int>(),
                                                           ctx.hp_inv.as<int>(), SA.lift.as<int>(), SB.lift.as<int>(),
                                                           SA.level.as<int8_t>(), ctx.nballow.as<int>(),
@@ -232,10 +304,207 @@ int opposite_tc(Context& ctx, const double* c, double* ttw, int nvec) {
       SA.level.as<int8_t>(), ctx.nballow.as<int>(), ctx.off.as<long long>(), c, ctx.ndet, ctx.oz_bexp.as<int>(),
       ctx.oz_bs.as<__nv_bfloat16>());
   ISCSI_CUDA(cudaGetLastError());
-  k_oz_gemm<<<ctx.oz_tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(ctx.oz_probs.as<OzProblem>(), ctx.oz_nprobs,
-                                                             ctx.oz_err.as<int>());
-  ISCSI_CUDA(cudaGetLastError());
   return kOk;
+}
+
+int opposite_tc_gemm(Context& ctx) { return launch_job(ctx, ctx.oz_ab, nullptr, stream()); }
+
+// ---------------------------------------------------------------------------
+// same spin
+
+bool samespin_block_on_tc(const Context& ctx, int a) {
+  const SpinSpace& SA = ctx.sp[0];
+  int rows = SA.level_start[a + 1] - SA.level_start[a];
+  int nba = (int)ctx.nb_allowed_lvl[a];
+  return rows >= OZ_BM && nba >= OZ_BN;
+}
+
+bool samespin_tc_active(const Context& ctx) {
+  if (!options().fp64_tc || !options().samespin_tc) return false;
+  for (int a = 0; a <= ctx.sp[0].maxlevel; ++a)
+    if (samespin_block_on_tc(ctx, a)) return true;
+  return false;
+}
+
+static int tc_prepare_m(Context& ctx) {
+  if (ctx.oz_m_ready) return kOk;
+  cudaStream_t st = stream();
+  ISCSI_TRY(tc_attr());
+  ISCSI_TRY(tc_err_buf(ctx));
+  const SpinSpace& SA = ctx.sp[0];
+  const SpinSpace& SB = ctx.sp[1];
+  int nl = SA.maxlevel + 1;
+  // M_alpha: rows = alpha strings (+ one tile of zero rows), columns grouped
+  // by level with each group padded to 16 so every segment starts aligned
+  ctx.oz_kbase.assign(nl + 1, 0);
+  for (int a = 0; a < nl; ++a) ctx.oz_kbase[a + 1] = ctx.oz_kbase[a] + round_up(SA.level_start[a + 1] - SA.level_start[a], OZ_BK);
+  if (ctx.na > 0 && ctx.M64[0].p) {
+    int kcols = ctx.oz_kbase[nl];
+    std::vector<int> colmap(kcols, -1);
+    for (int a = 0; a < nl; ++a)
+      for (int i = SA.level_start[a]; i < SA.level_start[a + 1]; ++i) colmap[ctx.oz_kbase[a] + i - SA.level_start[a]] = i;
+    DevBuf dmap;
+    ISCSI_TRY(dmap.alloc(sizeof(int) * kcols));
+    ISCSI_CUDA(cudaMemcpyAsync(dmap.p, colmap.data(), sizeof(int) * kcols, cudaMemcpyHostToDevice, st));
+    ctx.oz_ma_rows = SA.count + OZ_BM;
+    ctx.oz_ma_ld = kcols;
+    ISCSI_TRY(ctx.oz_mas.alloc(sizeof(__nv_bfloat16) * OZ_S * (size_t)ctx.oz_ma_rows * kcols));
+    ISCSI_TRY(ctx.oz_maexp.alloc(sizeof(int) * ctx.oz_ma_rows));
+    ISCSI_CUDA(cudaMemsetAsync(ctx.oz_maexp.p, 0, sizeof(int) * ctx.oz_ma_rows, st));
+    ISCSI_TRY(slice_matrix(ctx.M64[0].as<double>(), SA.count, SA.count, SA.count, 0, dmap.as<int>(), kcols,
+                           ctx.oz_ma_rows, ctx.oz_maexp.as<int>(), ctx.oz_mas.as<__nv_bfloat16>(), st));
+    ISCSI_CUDA(cudaStreamSynchronize(st));  // colmap lives until here
+  }
+  if (ctx.nb > 0) {
+    // M_beta[B][B'] as the B operand; the stored beta matrix is M_beta^T
+    // (or the symmetric alpha matrix when shared)
+    const double* Mb = ctx.beta_alias ? ctx.M64[0].as<double>() : ctx.M64[1].as<double>();
+    int trans = ctx.beta_alias ? 0 : 1;
+    ctx.oz_mb_rows = round_up(SB.count, OZ_BN);
+    ctx.oz_mb_ld = round_up(SB.count, OZ_BK);
+    ISCSI_TRY(ctx.oz_mbs.alloc(sizeof(__nv_bfloat16) * OZ_S * (size_t)ctx.oz_mb_rows * ctx.oz_mb_ld));
+    ISCSI_TRY(ctx.oz_mbexp.alloc(sizeof(int) * ctx.oz_mb_rows));
+    ISCSI_TRY(slice_matrix(Mb, SB.count, SB.count, SB.count, trans, nullptr, ctx.oz_mb_ld, ctx.oz_mb_rows,
+                           ctx.oz_mbexp.as<int>(), ctx.oz_mbs.as<__nv_bfloat16>(), st));
+  }
+  ctx.oz_m_ready = true;
+  return kOk;
+}
+
+// workspace layout of the per-call slices of C for (vector v, level block a)
+struct SsBlock {
+  int a, rows, nba, start;
+  long long obase;
+  long long bt_off, ca_off;      // slice-0 element offsets in oz_cs
+  long long bt_exp, ca_exp;      // offsets in oz_csexp
+  int bt_rows, bt_ld, ca_rows, ca_ld;
+};
+
+static std::vector<SsBlock> ss_blocks(const Context& ctx, long long* elems, long long* exps) {
+  std::vector<SsBlock> out;
+  const SpinSpace& SA = ctx.sp[0];
+  long long e = 0, x = 0;
+  for (int a = 0; a <= SA.maxlevel; ++a) {
+    SsBlock b;
+    b.a = a;
+    b.start = SA.level_start[a];
+    b.rows = SA.level_start[a + 1] - SA.level_start[a];
+    b.nba = (int)ctx.nb_allowed_lvl[a];
+    if (b.rows == 0 || b.nba == 0) continue;
+    b.obase = ctx.off_h[b.start];
+    // C_a^T (alpha part operand): rows = beta strings, K = alpha strings of the block
+    b.bt_rows = round_up(b.nba, OZ_BN);
+    b.bt_ld = round_up(b.rows, OZ_BK);
+    b.bt_off = e;
+    e += (long long)OZ_S * b.bt_rows * b.bt_ld;
+    b.bt_exp = x;
+    x += b.bt_rows;
+    // C_a (beta part operand): rows = alpha strings of the block, K = beta strings
+    b.ca_rows = round_up(b.rows, OZ_BM);
+    b.ca_ld = round_up(b.nba, OZ_BK);
+    b.ca_off = e;
+    e += (long long)OZ_S * b.ca_rows * b.ca_ld;
+    b.ca_exp = x;
+    x += b.ca_rows;
+    out.push_back(b);
+  }
+  *elems = e;
+  *exps = x;
+  return out;
+}
+
+int samespin_tc(Context& ctx, const double* c, double* sigma, int nvec) {
+  cudaStream_t st = stream();
+  ISCSI_TRY(tc_prepare_m(ctx));
+  long long elems1 = 0, exps1 = 0;
+  std::vector<SsBlock> blocks = ss_blocks(ctx, &elems1, &exps1);
+  long long elems = elems1 * nvec, nexp = exps1 * nvec;
+  bool rebuild = ctx.oz_ss.nvec != nvec;
+  if (ctx.oz_cs_elems < elems) {
+    ISCSI_TRY(ctx.oz_cs.alloc(sizeof(__nv_bfloat16) * elems));
+    ctx.oz_cs_elems = elems;
+    rebuild = true;
+  }
+  if ((long long)(ctx.oz_csexp.bytes / sizeof(int)) < nexp) {
+    ISCSI_TRY(ctx.oz_csexp.alloc(sizeof(int) * nexp));
+    rebuild = true;
+  }
+  __nv_bfloat16* cs = ctx.oz_cs.as<__nv_bfloat16>();
+  int* cx = ctx.oz_csexp.as<int>();
+  const SpinSpace& SB = ctx.sp[1];
+  if (rebuild) {
+    ISCSI_CUDA(cudaMemsetAsync(ctx.oz_cs.p, 0, sizeof(__nv_bfloat16) * ctx.oz_cs_elems, st));
+    ISCSI_CUDA(cudaMemsetAsync(ctx.oz_csexp.p, 0, sizeof(int) * nexp, st));
+    OzJob& job = ctx.oz_ss;
+    job.probs.clear();
+    job.segs.clear();
+    for (int v = 0; v < nvec; ++v)
+      for (const SsBlock& b : blocks) {
+        if (!samespin_block_on_tc(ctx, b.a)) continue;
+        OzProblem P;
+        std::memset(&P, 0, sizeof(P));
+        P.t = (long long)v * ctx.ndet + b.obase;
+        P.t_rel = 1;
+        P.ldt = b.nba;
+        P.M = b.rows;
+        P.N = b.nba;
+        P.seg_begin = (int)job.segs.size();
+        P.accumulate = 1;
+        if (ctx.na > 0 && ctx.oz_mas.p)
+          for (const SsBlock& b2 : blocks) {
+            if (std::abs(b.a - b2.a) > 2) continue;
+            OzSeg sg;
+            sg.as = ctx.oz_mas.as<__nv_bfloat16>() + (long long)b.start * ctx.oz_ma_ld + ctx.oz_kbase[b2.a];
+            sg.a_slice = (long long)ctx.oz_ma_rows * ctx.oz_ma_ld;
+            sg.a_exp = ctx.oz_maexp.as<int>() + b.start;
+            sg.lda = ctx.oz_ma_ld;
+            sg.bs = cs + v * elems1 + b2.bt_off;
+            sg.b_slice = (long long)b2.bt_rows * b2.bt_ld;
+            sg.b_exp = cx + v * exps1 + b2.bt_exp;
+            sg.ldb = b2.bt_ld;
+            sg.K = b2.bt_ld;
+            sg.nrows_b = std::min(b.nba, b2.nba);
+            job.segs.push_back(sg);
+            P.seg_count++;
+          }
+        if (ctx.nb > 0 && ctx.oz_mbs.p) {
+          OzSeg sg;
+          sg.as = cs + v * elems1 + b.ca_off;
+          sg.a_slice = (long long)b.ca_rows * b.ca_ld;
+          sg.a_exp = cx + v * exps1 + b.ca_exp;
+          sg.lda = b.ca_ld;
+          sg.bs = ctx.oz_mbs.as<__nv_bfloat16>();
+          sg.b_slice = (long long)ctx.oz_mb_rows * ctx.oz_mb_ld;
+          sg.b_exp = ctx.oz_mbexp.as<int>();
+          sg.ldb = ctx.oz_mb_ld;
+          sg.K = b.ca_ld;
+          sg.nrows_b = b.nba;
+          job.segs.push_back(sg);
+          P.seg_count++;
+        }
+        if (P.seg_count > 0) job.probs.push_back(P);
+      }
+    job.tiles = add_tiles(job.probs);
+    ISCSI_TRY(upload_job(job, st));
+    job.nvec = nvec;
+  }
+  // slice this call's C blocks (only the blocks some tensor-core problem reads)
+  for (int v = 0; v < nvec; ++v)
+    for (const SsBlock& b : blocks) {
+      bool used = samespin_block_on_tc(ctx, b.a);
+      for (const SsBlock& b2 : blocks)
+        if (std::abs(b.a - b2.a) <= 2 && samespin_block_on_tc(ctx, b2.a)) used = true;
+      if (!used) continue;
+      const double* X = c + (long long)v * ctx.ndet + b.obase;  // [rows][nba]
+      if (ctx.na > 0)
+        ISCSI_TRY(slice_matrix(X, b.nba, b.rows, b.nba, 1, nullptr, b.bt_ld, b.bt_rows, cx + v * exps1 + b.bt_exp,
+                               cs + v * elems1 + b.bt_off, st));
+      if (ctx.nb > 0 && samespin_block_on_tc(ctx, b.a))
+        ISCSI_TRY(slice_matrix(X, b.rows, b.nba, b.nba, 0, nullptr, b.ca_ld, b.ca_rows, cx + v * exps1 + b.ca_exp,
+                               cs + v * elems1 + b.ca_off, st));
+    }
+  (void)SB;
+  return launch_job(ctx, ctx.oz_ss, sigma, st);
 }
 
 // status of the bounded waits of the tensor-core kernels (synchronises)

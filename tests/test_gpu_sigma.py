@@ -261,3 +261,26 @@ def test_fp64_tensor_core_and_native_paths_agree(n, na, nb, k, tau):
         ref = o.sigma_terms(C[v])[0]
         assert_close(s_tc[v], ref, REL64)
         assert_close(s_nat[v], ref, REL64)
+
+
+@pytest.mark.parametrize("n,k,tau", [(20, 4, 1e-14), (24, 3, 1e-12), (30, 2, 1e-10)])
+def test_samespin_tensor_core_blocks(n, k, tau):
+    # level blocks of >= 128 alpha strings with >= 64 allowed beta strings run the
+    # same-spin products on the tensor cores; compare with the FP64 grouped GEMM
+    h1, eri = make_integrals(n, 1200 + n, ell=4.0, nchol=16)
+    L.iscsi_init(n, 2, 2, k, h1, eri, tau)
+    nd = L.iscsi_ndet()
+    C = np.stack([unit_vector(nd, 70 + v) for v in range(2)])
+    L.iscsi_set_option("samespin_tc", 1)
+    s_tc = gpu_sigma(C, nvec=2).reshape(2, -1)
+    L.iscsi_set_option("samespin_tc", 0)
+    L.iscsi_set_option("fp64_tc", 0)
+    s_nat = gpu_sigma(C, nvec=2).reshape(2, -1)
+    L.iscsi_set_option("samespin_tc", 1)
+    L.iscsi_set_option("fp64_tc", 1)
+    o = Oracle(n, 2, 2, k, tau, h1, eri)
+    rows = np.random.default_rng(1).choice(nd, size=min(nd, 300), replace=False)
+    for v in range(2):
+        assert_close(s_tc[v], s_nat[v], REL64)
+        ref = o.sigma_rows(C[v], rows)
+        assert np.abs(s_tc[v][rows] - ref).max() <= REL64 * np.abs(s_nat[v]).max()
