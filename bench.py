@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 METRIC = "σ-vector ms & GUpdates/s, HBM % of peak; FP32-mixed vs FP64 at |ΔE|≤1e-9 Eh"
 FALLBACK_HBM_GBS = 6800.0
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 rate (no FP64 figure in MEASURED_PEAKS.json)
+BF16_FALLBACK_TFLOPS = 1900.0  # dense bf16, recipe fallback (burst) when MEASURED_PEAKS.json is absent
 FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
 L2_FLUSH_BYTES = 512 << 20
 
@@ -39,6 +40,12 @@ WORKLOADS = {
     "fci_n100": dict(n=100, na=2, nb=2, kmax=4, ell=5.0, nchol=20, box=False, seed=3000, tau=1e-12),
     "cisd_n200": dict(n=200, na=2, nb=2, kmax=2, ell=5.0, nchol=20, box=True, seed=2000, tau=1e-14),
     "cisdt_n100": dict(n=100, na=2, nb=2, kmax=3, ell=5.0, nchol=20, box=True, seed=2000, tau=1e-14),
+    "cisd_n50": dict(n=50, na=2, nb=2, kmax=2, ell=5.0, nchol=20, box=True, seed=2000, tau=1e-14),
+    "cisd_n100": dict(n=100, na=2, nb=2, kmax=2, ell=5.0, nchol=20, box=True, seed=2000, tau=1e-14),
+    "cisd_n150": dict(n=150, na=2, nb=2, kmax=2, ell=5.0, nchol=20, box=True, seed=2000, tau=1e-14),
+    "cisdt_n50": dict(n=50, na=2, nb=2, kmax=3, ell=5.0, nchol=20, box=True, seed=2000, tau=1e-14),
+    "cisdt_n150": dict(n=150, na=2, nb=2, kmax=3, ell=5.0, nchol=20, box=True, seed=2000, tau=1e-14),
+    "cisdt_n200": dict(n=200, na=2, nb=2, kmax=3, ell=5.0, nchol=20, box=True, seed=2000, tau=1e-14),
 }
 
 
@@ -101,18 +108,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def measured_peaks():
+def _peaks_file():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         try:
             with open(path) as f:
-                d = json.load(f)
-            for key in ("hbm_gbs", "hbm_GBs", "hbm"):
-                if key in d:
-                    return float(d[key]), "measured"
+                return json.load(f)
         except (OSError, ValueError):
             pass
+    return None
+
+
+def measured_peaks():
+    d = _peaks_file()
+    if d:
+        for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if key in d:
+                return float(d[key]), "measured"
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def bf16_peak():
+    d = _peaks_file()
+    if d and "bf16_tflops" in d:
+        return float(d["bf16_tflops"]), "measured (burst)"
+    return BF16_FALLBACK_TFLOPS, "fallback (burst)"
 
 
 def profile_traffic(kernel_key):
@@ -210,12 +230,23 @@ def run_ours(args, wl, ws, rank, local):
     value = ws * updates / (ms * 1e-3) / 1e9
     e2e_val = ws * updates * args.steps / e2e_s / 1e9
 
-    # roofline of the dominant kernel (opposite-spin GEMM)
+    # roofline of the dominant kernel (opposite-spin contraction)
     gemm_ms = st["phase_ms"]["opposite_gemm"] / max(1, st["timed_calls"])
-    flops = st["opposite_gemm_flops"]
-    peak = FP64_PEAK_TFLOPS if args.precision == 64 else FP32_PEAK_TFLOPS
+    tc = args.precision == 64 and st.get("fp64_tc", 0) == 1
+    if tc:
+        # tensor-core kernel: bf16 MMA flops it issues (28 exact slice products)
+        flops = st["opposite_tc_bf16_flops"]
+        peak, peak_src = bf16_peak()
+        bound, kname, kkey = "tensor", "k_oz_gemm (tcgen05, FP64-accurate opposite-spin contraction)", \
+            "k_oz_gemm_%s" % args.workload
+    else:
+        flops = st["opposite_gemm_flops"]
+        peak = FP64_PEAK_TFLOPS if args.precision == 64 else FP32_PEAK_TFLOPS
+        peak_src = ("FP64 rate of GB300 (1.25 TFLOP/s; own probe measured 1.198)" if args.precision == 64
+                    else "152 SM x 128 FFMA/clk x 2.07 GHz")
+        bound, kname = "alu", "k_grouped_gemm (opposite-spin contraction)"
+        kkey = "k_grouped_gemm_fp%d_%s" % (args.precision, args.workload)
     achieved = flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
-    kkey = "k_grouped_gemm_fp%d_%s" % (args.precision, args.workload)
     traffic, _ = profile_traffic(kkey)
     hbm_peak, hbm_src = measured_peaks()
     esz = 8 if args.precision == 64 else 4
@@ -235,7 +266,8 @@ def run_ours(args, wl, ws, rank, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.precision == 64 else "f32",
+        "dtype": ("f64 (tcgen05 bf16 exact slices, int64/f64 accumulation)" if tc else "f64")
+        if args.precision == 64 else "f32",
         "data": "synthetic (seeded integrals shaped like the paper's Be-in-a-box sets)",
         "config": {"workload": args.workload, "norb": wl["n"], "nalpha": wl["na"], "nbeta": wl["nb"],
                    "max_excitation": wl["kmax"], "ndet": ndet, "tau": tau, "nvec": 1,
@@ -244,12 +276,12 @@ def run_ours(args, wl, ws, rank, local):
         "gpu_launches": None,
         "e2e": {"value": round(e2e_val, 3), "unit": "GUpdates/s", "h2d_bytes_per_step": 8 * ndet,
                 "d2h_bytes_per_step": 8 * ndet, "matches_device_path": e2e_ok},
-        "roofline": {"bound": "alu", "achieved": round(achieved, 4) if achieved else None, "peak": peak,
+        "roofline": {"bound": bound, "achieved": round(achieved, 4) if achieved else None, "peak": peak,
                      "unit": "TFLOP/s", "frac": round(achieved / peak, 4) if achieved else None,
-                     "traffic": traffic, "kernel": "k_grouped_gemm (opposite-spin contraction)",
-                     "kernel_ms": round(gemm_ms, 4), "flops_per_launch": flops,
-                     "peak_source": "FP64 rate of GB300 (1.25 TFLOP/s; own probe measured 1.198)"
-                     if args.precision == 64 else "152 SM x 128 FFMA/clk x 2.07 GHz"},
+                     "traffic": traffic, "kernel": kname, "kernel_ms": round(gemm_ms, 4), "flops_per_launch": flops,
+                     "fp64_equivalent_tflops": round(st["opposite_gemm_flops"] / (gemm_ms * 1e-3) / 1e12, 3)
+                     if gemm_ms > 0 else None,
+                     "peak_source": peak_src},
         "hbm": {"compulsory_bytes_per_step": comp_bytes,
                 "achieved_gbs": round(comp_bytes / (ms * 1e-3) / 1e9, 2),
                 "peak_gbs": hbm_peak, "frac": round(comp_bytes / (ms * 1e-3) / 1e9 / hbm_peak, 5),
@@ -259,8 +291,8 @@ def run_ours(args, wl, ws, rank, local):
         "wall_s_timed": round(wall, 3),
         "init_s": round(init_s, 3),
     }
-    # kernel launches inside the timed region: lift, GEMM, fold, same-spin GEMM per sigma
-    line["gpu_launches"] = 4 * args.steps
+    # kernel launches of the library inside the timed region (counted by the library)
+    line["gpu_launches"] = st.get("kernel_launches")
     return line
 
 

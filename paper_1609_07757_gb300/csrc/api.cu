@@ -13,6 +13,7 @@
 namespace iscsi {
 
 static std::string g_error = "no error";
+long long g_launch_count = 0;
 static cudaStream_t g_stream = nullptr;
 static Options g_options;
 static std::map<int, std::unique_ptr<Context>> g_ctx;
@@ -232,6 +233,7 @@ iscsi_status iscsi_set_option(const char* key, double value) {
     o.phase_timing = value != 0;
     Context* ctx = current();
     if (ctx) ctx->ntimed = 0;  // restart the per-call record
+    g_launch_count = 0;
   } else {
     set_error("iscsi_set_option: unknown key " + k);
     return ISCSI_E_ARG;
@@ -268,12 +270,14 @@ iscsi_status iscsi_stats(char* json, int len) {
       "\"updates\": {\"onebody\": %.17g, \"samespin\": %.17g, \"opposite\": %.17g, \"total\": %.17g}, "
       "\"init_ms\": %.6f, \"timed_calls\": %d, \"phase_ms\": {\"lift\": %.6f, \"opposite_gemm\": %.6f, "
       "\"fold\": %.6f, \"samespin_gemm\": %.6f}, \"davidson_iters\": %d, \"davidson_ms\": %.6f, "
-      "\"opposite_gemm_flops\": %.17g, \"samespin_gemm_flops\": %.17g}",
+      "\"opposite_gemm_flops\": %.17g, \"samespin_gemm_flops\": %.17g, \"opposite_tc_bf16_flops\": %.17g, "
+      "\"fp64_tc\": %d, \"samespin_tc\": %d, \"kernel_launches\": %lld}",
       ctx->n, ctx->na, ctx->nb, ctx->kmax, ctx->tau, ctx->ndet, ctx->sp[0].count, ctx->sp[1].count,
       ctx->units_onebody_total, ctx->units_samespin_total, ctx->units_opposite_total, ctx->units_opposite,
       ctx->units_onebody, ctx->units_samespin, ctx->updates_onebody, ctx->updates_samespin,
       ctx->updates_opposite, upd, ctx->init_ms, ncalls, phase_ms[0], phase_ms[1], phase_ms[2], phase_ms[3],
-      ctx->last_davidson_iters, ctx->last_davidson_ms, ctx_gemm_flops(*ctx, 0), ctx_gemm_flops(*ctx, 1));
+      ctx->last_davidson_iters, ctx->last_davidson_ms, ctx_gemm_flops(*ctx, 0), ctx_gemm_flops(*ctx, 1),
+      ctx_gemm_flops(*ctx, 2), options().fp64_tc, options().samespin_tc, g_launch_count);
   std::strncpy(json, buf, len - 1);
   json[len - 1] = 0;
   return ISCSI_OK;

@@ -35,6 +35,10 @@ constexpr int kOk = 0, kErrArg = -1, kErrNoMem = -2, kErrCuda = -3, kErrNoConv =
               kErrNan = -6, kErrWait = -7;
 
 void set_error(const std::string& msg);
+
+// kernel launches of the sigma path since the last reset (iscsi_stats)
+extern long long g_launch_count;
+#define ISCSI_COUNT_LAUNCH() (++::iscsi::g_launch_count)
 const char* last_error();
 
 #define ISCSI_CUDA(...)                                                                         \
@@ -115,7 +119,18 @@ struct ProblemList {
   std::vector<Segment<T>> segs;
   int total_tiles = 0;
   DevBuf d_probs, d_segs;
+  // problems with at most kThinN columns run one warp per output row
+  std::vector<Problem<T>> thin;
+  DevBuf d_thin;
+  int thin_rows = 0;
+  // problems with at most kThinN rows run one thread per output column
+  std::vector<Problem<T>> mthin;
+  DevBuf d_mthin, d_part_off, d_part;
+  int mthin_cols = 0;
+  int mthin_chunks = 1;
+  long long mthin_part_stride = 0;
 };
+constexpr int kThinN = 16;
 
 // a tensor-core work list (problems + segments) kept on the device
 struct OzJob {
@@ -222,7 +237,8 @@ int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h
 int sigma_run(Context& ctx, const double* c, double* sigma, int nvec, int precision);
 int sigma_workspace(Context& ctx, int nvec, int precision);
 // algorithmic flops per sigma per vector of the opposite-spin GEMM (which = 0)
-// or of the same-spin GEMMs (which = 1): 2 x M x K x N summed over problems
+// or of the same-spin GEMMs (which = 1): 2 x M x K x N summed over problems;
+// which = 2: bf16 MMA flops of the tensor-core opposite-spin contraction
 double ctx_gemm_flops(const Context& ctx, int which);
 
 // sigma_tc.cu: tensor-core FP64 contractions

@@ -32,24 +32,58 @@
 
 namespace iscsi {
 
+// Slicing in integer arithmetic (GB300's FP64 units are slow): with |v| < 2^e,
+// N = round(v 2^(49-e)) is read off the FP64 bit pattern, then cut into
+// balanced base-128 digits, least significant first: N = sum_t a_t 2^(7(6-t)),
+// |a_t| <= 64 for t >= 1 and |a_0| <= 128, i.e. v 2^-e = 2^-7 sum_t a_t 2^-7t
+// up to the rounding of N (<= 2^-50).
+__device__ __forceinline__ void oz_digits(double v, int e, int (&a)[OZ_S]) {
+  long long bits = __double_as_longlong(v);
+  int E = (int)((bits >> 52) & 0x7FF);
+  long long N = 0;
+  if (E != 0) {  // zeros and subnormals give N = 0 (far below the slice resolution)
+    long long m = (bits & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+    int sh = (E - 1075) + 49 - e;  // v = m 2^(E-1075); N = m 2^sh, sh <= -4 when |v| < 2^e
+    if (sh >= 0) N = m << (sh > 10 ? 10 : sh);
+    else if (sh > -63) N = (m + (1ll << (-sh - 1))) >> (-sh);
+    if (bits < 0) N = -N;
+  }
+#pragma unroll
+  for (int t = OZ_S - 1; t >= 1; --t) {
+    int r = (int)(N & 127);
+    if (r >= 64) r -= 128;
+    a[t] = r;
+    N = (N - r) >> 7;
+  }
+  a[0] = (int)N;
+}
+
+__device__ __forceinline__ void oz_store_digits(const int (&a)[OZ_S], __nv_bfloat16* out, long long slice_stride) {
+  const float scale[OZ_S] = {1.0f, 0.0078125f, 6.103515625e-05f, 4.76837158203125e-07f, 3.7252902984619141e-09f,
+                             2.9103830456733704e-11f, 2.2737367544323206e-13f};  // 2^-7t, exact
+#pragma unroll
+  for (int s = 0; s < OZ_S; ++s) out[s * slice_stride] = __float2bfloat16_rn(__int2float_rn(a[s]) * scale[s]);
+}
+
+// exponent field of |x|: frexp exponent = field - 1022 for normal x (0 for zero)
+__device__ __forceinline__ int oz_exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
 // row exponent e with max_k |X(r,k)| * 2^-e < 1 (0 for an all-zero row);
 // X(r,k) = X[r*ld + k], or X[k*ld + r] when trans
 __global__ void k_oz_row_exp(const double* __restrict__ X, int rows, int cols, long long ld, int trans,
                              int* __restrict__ e) {
   int r = blockIdx.x;
-  double m = 0.0;
+  int m = 0;
   for (int k = threadIdx.x; k < cols; k += blockDim.x)
-    m = fmax(m, fabs(trans ? X[(long long)k * ld + r] : X[(long long)r * ld + k]));
-  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  __shared__ double sm[32];
+    m = max(m, oz_exp_field(trans ? X[(long long)k * ld + r] : X[(long long)r * ld + k]));
+  m = __reduce_max_sync(0xffffffffu, m);
+  __shared__ int sm[32];
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double x = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) x = fmax(x, sm[i]);
-    int ex = 0;
-    if (x > 0.0) frexp(x, &ex);  // x = f 2^ex, f in [0.5, 1)
-    e[r] = ex;
+    int x = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) x = max(x, sm[i]);
+    e[r] = x > 0 ? x - 1022 : 0;  // max |x| = f 2^e, f in [0.5, 1)
   }
 }
 
@@ -64,15 +98,14 @@ __global__ void k_oz_slice(const double* __restrict__ X, int rows, int cols, lon
   int r = (int)(t / ldo), k = (int)(t % ldo);
   int src = colmap ? colmap[k] : (k < cols ? k : -1);
   double x = 0.0;
-  if (r < rows && src >= 0)
-    x = ldexp(trans ? X[(long long)src * ld + r] : X[(long long)r * ld + src], -e[r]);
-#pragma unroll
-  for (int s = 0; s < OZ_S; ++s) {
-    double v = x * 128.0;
-    double a = rint(v);
-    x = v - a;  // exact
-    out[s * slice_stride + t] = __float2bfloat16_rn((float)ldexp(a, -OZ_BITS * s));
+  int ex = 0;
+  if (r < rows && src >= 0) {
+    x = trans ? X[(long long)src * ld + r] : X[(long long)r * ld + src];
+    ex = e[r];
   }
+  int a[OZ_S];
+  oz_digits(x, ex, a);
+  oz_store_digits(a, out + t, slice_stride);
 }
 
 // [rows x 16] bf16 slice tile, K-major, into core-matrix layout:
@@ -86,18 +119,22 @@ __device__ __forceinline__ void oz_load_unit(uint32_t sbase, const __nv_bfloat16
   tc::cp_async16(dst, src);
 }
 
-__device__ __forceinline__ void oz_load_stage(uint32_t sstage, const OzSeg& S, int m0, int n0, int k0) {
+// one K step (16) of all slices of both operands; a, b point at (row 0 of the
+// tile, k0) of slice 0
+__device__ __forceinline__ void oz_load_stage(uint32_t sstage, const __nv_bfloat16* a, long long a_slice, int lda,
+                                              const __nv_bfloat16* b, long long b_slice, int ldb) {
   // 84 units of 32 chunks: A 7 slices x 8 units, B 7 slices x 4 units
   int warp = threadIdx.x >> 5;
-  for (int u = warp; u < OZ_S * 12; u += OZ_THREADS / 32) {
+#pragma unroll
+  for (int i = 0; i < OZ_S * 12 / (OZ_THREADS / 32); ++i) {
+    int u = warp + i * (OZ_THREADS / 32);
     if (u < OZ_S * 8) {
-      int s = u / 8, unit = u % 8;
-      oz_load_unit(sstage + s * OZ_A_SLICE_BYTES, S.as + s * S.a_slice + (long long)m0 * S.lda + k0, S.lda, unit);
+      int s = u >> 3, unit = u & 7;
+      oz_load_unit(sstage + s * OZ_A_SLICE_BYTES, a + s * a_slice, lda, unit);
     } else {
       int v = u - OZ_S * 8;
-      int s = v / 4, unit = v % 4;
-      oz_load_unit(sstage + OZ_S * OZ_A_SLICE_BYTES + s * OZ_B_SLICE_BYTES,
-                   S.bs + s * S.b_slice + (long long)n0 * S.ldb + k0, S.ldb, unit);
+      int s = v >> 2, unit = v & 3;
+      oz_load_unit(sstage + OZ_S * OZ_A_SLICE_BYTES + s * OZ_B_SLICE_BYTES, b + s * b_slice, ldb, unit);
     }
   }
 }
@@ -162,15 +199,29 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const int row = warp * 32 + lane;
   const int gm = m0 + row;
 
-  auto seg_of = [&](int g) {
-    int s = 0;
-    while (s + 1 < nseg && g >= step0_s[s + 1]) ++s;
-    return s;
-  };
+  // register copy of the segment being loaded (loads advance in step order)
+  int ld_seg = -1, ld_end = 0, ld_begin = 0;
+  const __nv_bfloat16 *la = nullptr, *lb = nullptr;
+  long long las = 0, lbs = 0;
+  int llda = 0, lldb = 0;
   auto load_step = [&](int g, int stage) {
-    int s = seg_of(g);
-    oz_load_stage(s_stage0 + stage * OZ_STAGE_BYTES, seg_s[s], m0, n0, (g - step0_s[s]) * OZ_BK);
+    while (g >= ld_end) {
+      ++ld_seg;
+      ld_begin = step0_s[ld_seg];
+      ld_end = step0_s[ld_seg + 1];
+      const OzSeg& S = seg_s[ld_seg];
+      llda = S.lda;
+      lldb = S.ldb;
+      las = S.a_slice;
+      lbs = S.b_slice;
+      la = S.as + (long long)m0 * llda;
+      lb = S.bs + (long long)n0 * lldb;
+    }
+    int k0 = (g - ld_begin) * OZ_BK;
+    oz_load_stage(s_stage0 + stage * OZ_STAGE_BYTES, la + k0, las, llda, lb + k0, lbs, lldb);
   };
+  // segment of the step being computed
+  int c_seg = 0, c_begin = 0, c_end = nseg > 0 ? step0_s[1] : 0;
 
   for (int s = 0; s < OZ_STAGES; ++s) {
     if (s < total) load_step(s, s);
@@ -185,9 +236,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     else tc::cp_async_wait<OZ_STAGES - 2>();
     tc::fence_proxy_async();
     __syncthreads();
-    int sgi = seg_of(g);
-    int local = g - step0_s[sgi];
-    int seg_steps = step0_s[sgi + 1] - step0_s[sgi];
+    while (g >= c_end) {
+      ++c_seg;
+      c_begin = c_end;
+      c_end = step0_s[c_seg + 1];
+    }
+    const int sgi = c_seg;
+    int local = g - c_begin;
+    int seg_steps = c_end - c_begin;
     int kin = local % (OZ_CHUNK / OZ_BK);
     if (threadIdx.x == 0) {
       tc::fence_after_sync();

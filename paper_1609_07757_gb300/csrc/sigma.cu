@@ -129,6 +129,161 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   }
 }
 
+// Thin problems (N <= 16 columns, e.g. the single allowed beta string of the
+// highest-level CISD block): one warp per output row, lanes split K, the
+// per-column partial sums are reduced with shuffles.  The column count is a
+// template parameter so no FMA is spent on absent columns.
+template <typename T, int NB>
+__device__ __forceinline__ void thin_row_seg(T (&acc)[16], const T* __restrict__ Ap, const T* __restrict__ Bp,
+                                             int K, long long ldb, int lane) {
+  for (int k = lane; k < K; k += 32) {
+    T a = Ap[k];
+    const T* br = Bp + (long long)k * ldb;
+#pragma unroll
+    for (int n = 0; n < NB; ++n) acc[n] = fma(a, br[n], acc[n]);
+  }
+}
+
+template <typename T, int MB>
+__device__ __forceinline__ void mthin_col_seg(T (&acc)[16], const T* __restrict__ Ap, long long lda,
+                                              const T* __restrict__ Bp, long long ldb, int k0, int k1) {
+  for (int k = k0; k < k1; ++k) {
+    T b = Bp[(long long)k * ldb];
+#pragma unroll
+    for (int m = 0; m < MB; ++m) acc[m] = fma(Ap[(long long)m * lda + k], b, acc[m]);
+  }
+}
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_grouped_thin(const Problem<T>* __restrict__ probs, int nprobs, const Segment<T>* __restrict__ segs,
+                   const T* __restrict__ cbase, T* sbase, int total_rows) {
+  int item = blockIdx.x * 8 + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (item >= total_rows) return;
+  int lo = 0, hi = nprobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile_begin <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  const Problem<T> P = probs[lo];
+  int row = item - P.tile_begin;
+  auto resolve = [&](long long v, int src) -> const T* {
+    return src == kSrcC ? cbase + v : src == kSrcSigma ? sbase + v : reinterpret_cast<const T*>(v);
+  };
+  T acc[kThinN];
+#pragma unroll
+  for (int n = 0; n < kThinN; ++n) acc[n] = T(0);
+  for (int sg = 0; sg < P.seg_count; ++sg) {
+    const Segment<T> S = segs[P.seg_begin + sg];
+    const T* Ap = resolve(S.a, S.asrc) + (long long)row * S.lda;
+    const T* Bp = resolve(S.b, S.bsrc);
+    int bcols = min(S.bcols, P.N);
+    switch (bcols) {
+#define THIN_CASE(NB) \
+  case NB:            \
+    thin_row_seg<T, NB>(acc, Ap, Bp, S.K, S.ldb, lane); \
+    break;
+      THIN_CASE(1) THIN_CASE(2) THIN_CASE(3) THIN_CASE(4) THIN_CASE(5) THIN_CASE(6) THIN_CASE(7) THIN_CASE(8)
+      THIN_CASE(9) THIN_CASE(10) THIN_CASE(11) THIN_CASE(12) THIN_CASE(13) THIN_CASE(14) THIN_CASE(15)
+      THIN_CASE(16)
+#undef THIN_CASE
+      default:
+        break;
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < kThinN; ++n)
+    for (int o = 16; o; o >>= 1) acc[n] += __shfl_xor_sync(0xffffffffu, acc[n], o);
+  T* Cp = const_cast<T*>(resolve(P.c, P.csrc)) + (long long)row * P.ldc;
+#pragma unroll
+  for (int n = 0; n < kThinN; ++n)
+    if (lane == n && n < P.N) Cp[n] = P.accumulate ? Cp[n] + acc[n] : acc[n];
+}
+
+// Problems with at most kThinN rows (e.g. the reference row block): split K
+// into chunks of kMthinChunk over the concatenated segments; one thread per
+// (output column, K chunk) accumulates up to kThinN rows, partial sums go to
+// part[chunk][problem offset + m * N + n] and a second kernel adds them in
+// chunk order (deterministic).  tile_begin = first column item of the
+// problem, seg K ranges are taken in order.
+constexpr int kMthinChunk = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_grouped_mthin(const Problem<T>* __restrict__ probs, int nprobs, const Segment<T>* __restrict__ segs,
+                    const long long* __restrict__ part_off, const T* __restrict__ cbase, T* sbase, int total_cols,
+                    long long part_stride, T* __restrict__ part) {
+  int item = blockIdx.x * 256 + threadIdx.x;
+  if (item >= total_cols) return;
+  int lo = 0, hi = nprobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile_begin <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  const Problem<T> P = probs[lo];
+  int n = item - P.tile_begin;
+  long long k_lo = (long long)blockIdx.y * kMthinChunk, k_hi = k_lo + kMthinChunk;
+  auto resolve = [&](long long v, int src) -> const T* {
+    return src == kSrcC ? cbase + v : src == kSrcSigma ? sbase + v : reinterpret_cast<const T*>(v);
+  };
+  T acc[kThinN];
+#pragma unroll
+  for (int m = 0; m < kThinN; ++m) acc[m] = T(0);
+  long long kbase = 0;
+  for (int sg = 0; sg < P.seg_count && kbase < k_hi; ++sg) {
+    const Segment<T> S = segs[P.seg_begin + sg];
+    long long a0 = max(k_lo, kbase), a1 = min(k_hi, kbase + S.K);
+    if (a0 < a1 && n < min(S.bcols, P.N)) {
+      const T* Ap = resolve(S.a, S.asrc);
+      const T* Bp = resolve(S.b, S.bsrc) + n;
+      int k0 = (int)(a0 - kbase), k1 = (int)(a1 - kbase);
+      switch (P.M) {
+#define MTHIN_CASE(MB) \
+  case MB:             \
+    mthin_col_seg<T, MB>(acc, Ap, S.lda, Bp, S.ldb, k0, k1); \
+    break;
+        MTHIN_CASE(1) MTHIN_CASE(2) MTHIN_CASE(3) MTHIN_CASE(4) MTHIN_CASE(5) MTHIN_CASE(6) MTHIN_CASE(7)
+        MTHIN_CASE(8) MTHIN_CASE(9) MTHIN_CASE(10) MTHIN_CASE(11) MTHIN_CASE(12) MTHIN_CASE(13) MTHIN_CASE(14)
+        MTHIN_CASE(15) MTHIN_CASE(16)
+#undef MTHIN_CASE
+        default:
+          break;
+      }
+    }
+    kbase += S.K;
+  }
+  T* out = part + blockIdx.y * part_stride + part_off[lo];
+#pragma unroll
+  for (int m = 0; m < kThinN; ++m)
+    if (m < P.M) out[(long long)m * P.N + n] = acc[m];
+}
+
+template <typename T>
+__global__ void k_mthin_reduce(const Problem<T>* __restrict__ probs, int nprobs, const long long* __restrict__ part_off,
+                               T* sbase, const T* __restrict__ cbase, int total_cols, int nchunks,
+                               long long part_stride, const T* __restrict__ part) {
+  int item = blockIdx.x * 256 + threadIdx.x;
+  if (item >= total_cols) return;
+  int lo = 0, hi = nprobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile_begin <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  const Problem<T> P = probs[lo];
+  int n = item - P.tile_begin;
+  T* Cp = (P.csrc == kSrcC ? const_cast<T*>(cbase) + P.c : P.csrc == kSrcSigma ? sbase + P.c
+                                                                              : reinterpret_cast<T*>(P.c)) + n;
+  for (int m = 0; m < P.M; ++m) {
+    T acc = T(0);
+    for (int c = 0; c < nchunks; ++c) acc += part[c * part_stride + part_off[lo] + (long long)m * P.N + n];
+    T* dst = Cp + (long long)m * P.ldc;
+    *dst = P.accumulate ? *dst + acc : acc;
+  }
+}
+
 template <typename T>
 struct TileCfg;
 template <>
@@ -143,6 +298,52 @@ struct TileCfg<float> {
 template <typename T>
 static int upload_problems(ProblemList<T>& pl, cudaStream_t st) {
   using C = TileCfg<T>;
+  // split off the thin problems
+  pl.thin.clear();
+  pl.mthin.clear();
+  std::vector<Problem<T>> wide;
+  pl.thin_rows = 0;
+  pl.mthin_cols = 0;
+  std::vector<long long> part_off;
+  long long part_elems = 0;
+  int max_k = 0;
+  for (auto& p : pl.probs) {
+    if (p.M <= kThinN && p.N > kThinN && p.accumulate) {
+      Problem<T> q = p;
+      q.tile_begin = pl.mthin_cols;
+      pl.mthin_cols += q.N;
+      pl.mthin.push_back(q);
+      part_off.push_back(part_elems);
+      part_elems += (long long)q.M * q.N;
+      int k = 0;
+      for (int sg = 0; sg < q.seg_count; ++sg) k += pl.segs[q.seg_begin + sg].K;
+      max_k = std::max(max_k, k);
+    } else if (p.N <= kThinN) {
+      Problem<T> q = p;
+      q.tile_begin = pl.thin_rows;
+      pl.thin_rows += q.M;
+      pl.thin.push_back(q);
+    } else {
+      wide.push_back(p);
+    }
+  }
+  pl.probs.swap(wide);
+  if (!pl.mthin.empty()) {
+    ISCSI_TRY(pl.d_mthin.grow(sizeof(Problem<T>) * pl.mthin.size()));
+    ISCSI_CUDA(cudaMemcpyAsync(pl.d_mthin.p, pl.mthin.data(), sizeof(Problem<T>) * pl.mthin.size(),
+                               cudaMemcpyHostToDevice, st));
+    pl.mthin_chunks = std::max(1, (max_k + kMthinChunk - 1) / kMthinChunk);
+    pl.mthin_part_stride = part_elems;
+    ISCSI_TRY(pl.d_part_off.grow(sizeof(long long) * part_off.size()));
+    ISCSI_CUDA(cudaMemcpyAsync(pl.d_part_off.p, part_off.data(), sizeof(long long) * part_off.size(),
+                               cudaMemcpyHostToDevice, st));
+    ISCSI_TRY(pl.d_part.grow(sizeof(T) * part_elems * pl.mthin_chunks));
+  }
+  if (!pl.thin.empty()) {
+    ISCSI_TRY(pl.d_thin.grow(sizeof(Problem<T>) * pl.thin.size()));
+    ISCSI_CUDA(cudaMemcpyAsync(pl.d_thin.p, pl.thin.data(), sizeof(Problem<T>) * pl.thin.size(),
+                               cudaMemcpyHostToDevice, st));
+  }
   int tiles = 0;
   for (auto& p : pl.probs) {
     p.tile_begin = tiles;
@@ -150,11 +351,12 @@ static int upload_problems(ProblemList<T>& pl, cudaStream_t st) {
     tiles += ((p.M + C::BM - 1) / C::BM) * p.tiles_n;
   }
   pl.total_tiles = tiles;
-  if (pl.probs.empty()) return kOk;
-  ISCSI_TRY(pl.d_probs.grow(sizeof(Problem<T>) * pl.probs.size()));
+  if (pl.probs.empty() && pl.thin.empty() && pl.mthin.empty()) return kOk;
+  ISCSI_TRY(pl.d_probs.grow(sizeof(Problem<T>) * std::max<size_t>(1, pl.probs.size())));
   ISCSI_TRY(pl.d_segs.grow(sizeof(Segment<T>) * std::max<size_t>(1, pl.segs.size())));
-  ISCSI_CUDA(cudaMemcpyAsync(pl.d_probs.p, pl.probs.data(), sizeof(Problem<T>) * pl.probs.size(),
-                             cudaMemcpyHostToDevice, st));
+  if (!pl.probs.empty())
+    ISCSI_CUDA(cudaMemcpyAsync(pl.d_probs.p, pl.probs.data(), sizeof(Problem<T>) * pl.probs.size(),
+                               cudaMemcpyHostToDevice, st));
   if (!pl.segs.empty())
     ISCSI_CUDA(cudaMemcpyAsync(pl.d_segs.p, pl.segs.data(), sizeof(Segment<T>) * pl.segs.size(),
                                cudaMemcpyHostToDevice, st));
@@ -166,11 +368,28 @@ static int upload_problems(ProblemList<T>& pl, cudaStream_t st) {
 template <typename T>
 static int launch_grouped(const ProblemList<T>& pl, const T* cbase, T* sbase, cudaStream_t st) {
   using C = TileCfg<T>;
+  if (pl.mthin_cols > 0) {
+    dim3 grid((pl.mthin_cols + 255) / 256, pl.mthin_chunks);
+    k_grouped_mthin<T><<<grid, 256, 0, st>>>(pl.d_mthin.template as<Problem<T>>(), (int)pl.mthin.size(),
+                                             pl.d_segs.template as<Segment<T>>(), pl.d_part_off.template as<long long>(),
+                                             cbase, sbase, pl.mthin_cols, pl.mthin_part_stride,
+                                             pl.d_part.template as<T>()); ISCSI_COUNT_LAUNCH();
+    k_mthin_reduce<T><<<(pl.mthin_cols + 255) / 256, 256, 0, st>>>(
+        pl.d_mthin.template as<Problem<T>>(), (int)pl.mthin.size(), pl.d_part_off.template as<long long>(), sbase,
+        cbase, pl.mthin_cols, pl.mthin_chunks, pl.mthin_part_stride, pl.d_part.template as<T>()); ISCSI_COUNT_LAUNCH();
+    ISCSI_CUDA(cudaGetLastError());
+  }
+  if (pl.thin_rows > 0) {
+    k_grouped_thin<T><<<(pl.thin_rows + 7) / 8, 256, 0, st>>>(pl.d_thin.template as<Problem<T>>(),
+                                                              (int)pl.thin.size(), pl.d_segs.template as<Segment<T>>(),
+                                                              cbase, sbase, pl.thin_rows); ISCSI_COUNT_LAUNCH();
+    ISCSI_CUDA(cudaGetLastError());
+  }
   if (pl.total_tiles == 0) return kOk;
   constexpr int NT = (C::BM / C::TM) * (C::BN / C::TN);
   k_grouped_gemm<T, C::BM, C::BN, C::BK, C::TM, C::TN><<<pl.total_tiles, NT, 0, st>>>(
       pl.d_probs.template as<Problem<T>>(), (int)pl.probs.size(), pl.d_segs.template as<Segment<T>>(), cbase,
-      sbase);
+      sbase); ISCSI_COUNT_LAUNCH();
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
 }
@@ -374,6 +593,15 @@ static int build_problems(Context& ctx, int nvec, const T* G, const T* Ma, const
 
 double ctx_gemm_flops(const Context& ctx, int which) {
   double f = 0.0;
+  if (which == 2) {
+    // bf16 MMA flops the tensor-core opposite-spin contraction issues: 28 slice
+    // products (levels 0..6 of 7 slices) x 2 M N K, K rounded up to 16
+    if (!ctx.have_ab) return 0.0;
+    for (const ColClass& cc : ctx.cls)
+      if (cc.ncol > 0 && cc.mrows > 0)
+        f += 28.0 * 2.0 * cc.mrows * (double)((cc.krows + 15) / 16 * 16) * cc.ncol;
+    return f;
+  }
   if (which == 0) {
     if (!ctx.have_ab) return 0.0;
     for (const ColClass& cc : ctx.cls)
@@ -422,13 +650,13 @@ static int ensure_fp32_matrices(Context& ctx) {
   if (ctx.have_ab && !ctx.G32.p) {
     long long g2 = (long long)ctx.npairs * ctx.npairs;
     ISCSI_TRY(ctx.G32.alloc(sizeof(float) * g2));
-    k_convert<double, float><<<2048, 256, 0, st>>>(ctx.G64.as<double>(), ctx.G32.as<float>(), g2);
+    k_convert<double, float><<<2048, 256, 0, st>>>(ctx.G64.as<double>(), ctx.G32.as<float>(), g2); ISCSI_COUNT_LAUNCH();
   }
   for (int s = 0; s < 2; ++s) {
     if (!ctx.M64[s].p || ctx.M32[s].p) continue;
     long long m2 = (long long)ctx.sp[s].count * ctx.sp[s].count;
     ISCSI_TRY(ctx.M32[s].alloc(sizeof(float) * m2));
-    k_convert<double, float><<<2048, 256, 0, st>>>(ctx.M64[s].as<double>(), ctx.M32[s].as<float>(), m2);
+    k_convert<double, float><<<2048, 256, 0, st>>>(ctx.M64[s].as<double>(), ctx.M32[s].as<float>(), m2); ISCSI_COUNT_LAUNCH();
   }
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
@@ -472,7 +700,7 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
     k_fold<T><<<ctx.sp[0].count, 256, 0, st>>>(ct, nvec, ctx.n, ctx.na, ctx.nb, ctx.sp[1].nhole,
                                                ctx.sp[0].dec.as<int>(), ctx.sp[1].dec.as<int>(),
                                                ctx.hp_class.as<int8_t>(), ctx.hp_local.as<int>(),
-                                               ctx.pair_index.as<int>(), ctx.off.as<long long>(), ttw, ctx.ndet, sigma);
+                                               ctx.pair_index.as<int>(), ctx.off.as<long long>(), ttw, ctx.ndet, sigma); ISCSI_COUNT_LAUNCH();
     ISCSI_CUDA(cudaGetLastError());
     ISCSI_TRY(timing_event(ctx, call, 3, st));
   } else if (ctx.have_ab) {
@@ -482,7 +710,7 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
       k_lift_ct<T, TC><<<launch_blocks(tot, 256), 256, 0, st>>>(
           ct, nvec, ctx.n, ctx.sp[0].nhole, ctx.sp[1].nhole, ctx.pair_of.as<int>(), ctx.hp_inv.as<int>(),
           ctx.sp[0].lift.as<int>(), ctx.sp[1].lift.as<int>(), ctx.sp[0].level.as<int8_t>(), ctx.nballow.as<int>(),
-          ctx.off.as<long long>(), c_in, ctx.ndet, ctw);
+          ctx.off.as<long long>(), c_in, ctx.ndet, ctw); ISCSI_COUNT_LAUNCH();
       ISCSI_CUDA(cudaGetLastError());
     }
     ISCSI_TRY(timing_event(ctx, call, 1, st));
@@ -491,7 +719,7 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
     k_fold<T><<<ctx.sp[0].count, 256, 0, st>>>(ct, nvec, ctx.n, ctx.na, ctx.nb, ctx.sp[1].nhole,
                                                ctx.sp[0].dec.as<int>(), ctx.sp[1].dec.as<int>(),
                                                ctx.hp_class.as<int8_t>(), ctx.hp_local.as<int>(),
-                                               ctx.pair_index.as<int>(), ctx.off.as<long long>(), ttw, ctx.ndet, sigma);
+                                               ctx.pair_index.as<int>(), ctx.off.as<long long>(), ttw, ctx.ndet, sigma); ISCSI_COUNT_LAUNCH();
     ISCSI_CUDA(cudaGetLastError());
     ISCSI_TRY(timing_event(ctx, call, 3, st));
   } else {
@@ -522,11 +750,11 @@ int sigma_run(Context& ctx, const double* c, double* sigma, int nvec, int precis
   const float* Ma32 = ctx.na ? ctx.M32[0].as<float>() : nullptr;
   const float* Mb32 = ctx.nb ? (ctx.beta_alias ? ctx.M32[0].as<float>() : ctx.M32[1].as<float>()) : nullptr;
   long long cnt = ctx.ndet * nvec;
-  k_convert<double, float><<<std::min(launch_blocks(cnt, 256), 4096), 256, 0, st>>>(c, ctx.c32.as<float>(), cnt);
+  k_convert<double, float><<<std::min(launch_blocks(cnt, 256), 4096), 256, 0, st>>>(c, ctx.c32.as<float>(), cnt); ISCSI_COUNT_LAUNCH();
   ISCSI_TRY(sigma_impl<float, float>(ctx, ctx.c32.as<float>(), ctx.s32.as<float>(), ctx.c32.as<float>(),
                                      ctx.s32.as<float>(), nvec, ctx.pl_ab32, ctx.pl_ss32, ctx.pl_nvec32,
                                      ctx.G32.as<float>(), Ma32, Mb32));
-  k_convert<float, double><<<std::min(launch_blocks(cnt, 256), 4096), 256, 0, st>>>(ctx.s32.as<float>(), sigma, cnt);
+  k_convert<float, double><<<std::min(launch_blocks(cnt, 256), 4096), 256, 0, st>>>(ctx.s32.as<float>(), sigma, cnt); ISCSI_COUNT_LAUNCH();
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
 }
@@ -674,21 +902,21 @@ int sigma_noalloc_run(Context& ctx, const double* c, double* sigma) {
       k_lift_ct<double, double><<<launch_blocks(tot, 256), 256, 0, st>>>(
           ct, 1, ctx.n, ctx.sp[0].nhole, ctx.sp[1].nhole, ctx.pair_of.as<int>(), ctx.hp_inv.as<int>(),
           ctx.sp[0].lift.as<int>(), ctx.sp[1].lift.as<int>(), ctx.sp[0].level.as<int8_t>(), ctx.nballow.as<int>(),
-          ctx.off.as<long long>(), c, ctx.ndet, ctw);
+          ctx.off.as<long long>(), c, ctx.ndet, ctw); ISCSI_COUNT_LAUNCH();
     if (ab_tiles > 0)
       k_grouped_gemm<double, C::BM, C::BN, C::BK, C::TM, C::TN>
-          <<<ab_tiles, NT, 0, st>>>(dprobs, (int)ab.size(), dsegs, c, sigma);
+          <<<ab_tiles, NT, 0, st>>>(dprobs, (int)ab.size(), dsegs, c, sigma); ISCSI_COUNT_LAUNCH();
     k_fold<double><<<ctx.sp[0].count, 256, 0, st>>>(ct, 1, ctx.n, ctx.na, ctx.nb, ctx.sp[1].nhole,
                                                     ctx.sp[0].dec.as<int>(), ctx.sp[1].dec.as<int>(),
                                                     ctx.hp_class.as<int8_t>(), ctx.hp_local.as<int>(),
                                                     ctx.pair_index.as<int>(), ctx.off.as<long long>(), ttw, ctx.ndet,
-                                                    sigma);
+                                                    sigma); ISCSI_COUNT_LAUNCH();
   } else {
     ISCSI_CUDA(cudaMemsetAsync(sigma, 0, sizeof(double) * ctx.ndet, st));
   }
   if (ss_tiles > 0)
     k_grouped_gemm<double, C::BM, C::BN, C::BK, C::TM, C::TN>
-        <<<ss_tiles, NT, 0, st>>>(dprobs + ab.size(), (int)ss.size(), dsegs, c, sigma);
+        <<<ss_tiles, NT, 0, st>>>(dprobs + ab.size(), (int)ss.size(), dsegs, c, sigma); ISCSI_COUNT_LAUNCH();
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
 }

@@ -11,8 +11,8 @@
 // strings of level a, columns = the allowed beta prefix):
 //   sigma_a += sum_a' M_alpha[a, a'] C_a'   (A = M_alpha slices, B = C_a'^T)
 //            + C_a M_beta^T                 (A = C_a slices, B = M_beta slices)
-// as one multi-segment product per block; blocks too small for a 128 x 64
-// tile stay on the FP64 grouped GEMM of sigma.cu.
+// as one multi-segment product per block; blocks with at most 16 rows or
+// columns stay on the FP64 thin kernels of sigma.cu.
 // G's, M_alpha's and M_beta's slices are built once per context (first use).
 #include <algorithm>
 #include <climits>
@@ -80,8 +80,7 @@ __global__ void k_oz_col_exp(TcTable tt, int n, int nholeA, int nholeB, const in
   int col = (int)(local / C.kpad), k = (int)(local % C.kpad);
   double x = tc_gather(C, tt.nvec, col, k, n, nholeA, nholeB, pair_of, hp_inv, liftA, liftB, alevel, nballow, off,
                        c, ndet);
-  int e = INT_MIN;
-  if (x != 0.0) frexp(x, &e);
+  int e = x != 0.0 ? oz_exp_field(x) - 1022 : INT_MIN;  // frexp exponent of |x|
   // one atomic per (warp, column): lanes of the same column reduce together
   int key = (int)(C.exp_off + col);
   unsigned group = __match_any_sync(__activemask(), key);
@@ -114,16 +113,9 @@ __global__ void k_oz_lift_slice(TcTable tt, int n, int nholeA, int nholeB, const
   int col = (int)(local / C.kpad), k = (int)(local % C.kpad);
   double x = tc_gather(C, tt.nvec, col, k, n, nholeA, nholeB, pair_of, hp_inv, liftA, liftB, alevel, nballow, off,
                        c, ndet);
-  x = ldexp(x, -exps[C.exp_off + col]);
-  long long slice = (long long)C.npad * C.kpad;
-  __nv_bfloat16* out = bs + C.bs_off + (long long)col * C.kpad + k;
-#pragma unroll
-  for (int s = 0; s < OZ_S; ++s) {
-    double v = x * 128.0;
-    double a = rint(v);
-    x = v - a;
-    out[s * slice] = __float2bfloat16_rn((float)ldexp(a, -OZ_BITS * s));
-  }
+  int a[OZ_S];
+  oz_digits(x, exps[C.exp_off + col], a);
+  oz_store_digits(a, bs + C.bs_off + (long long)col * C.kpad + k, (long long)C.npad * C.kpad);
 }
 
 static int tc_attr() {
@@ -145,11 +137,11 @@ static int tc_err_buf(Context& ctx) {
 // slices of a row-major (or transposed) FP64 matrix with per-row exponents
 static int slice_matrix(const double* X, int rows, int cols, long long ld, int trans, const int* colmap, int ldo,
                         int rows_pad, int* exps, __nv_bfloat16* out, cudaStream_t st) {
-  if (rows > 0) k_oz_row_exp<<<rows, 256, 0, st>>>(X, rows, cols, ld, trans, exps);
+  if (rows > 0) k_oz_row_exp<<<rows, 256, 0, st>>>(X, rows, cols, ld, trans, exps); ISCSI_COUNT_LAUNCH();
   long long slice = (long long)rows_pad * ldo;
   if (slice > 0)
     k_oz_slice<<<launch_blocks(slice, 256), 256, 0, st>>>(X, rows, cols, ld, trans, colmap, exps, out, slice, ldo,
-                                                          rows_pad);
+                                                          rows_pad); ISCSI_COUNT_LAUNCH();
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
 }
@@ -185,7 +177,7 @@ static int upload_job(OzJob& job, cudaStream_t st) {
 static int launch_job(Context& ctx, const OzJob& job, double* tbase, cudaStream_t st) {
   if (job.tiles == 0) return kOk;
   k_oz_gemm<<<job.tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(job.d_probs.as<OzProblem>(), (int)job.probs.size(),
-                                                          job.d_segs.as<OzSeg>(), tbase, ctx.oz_err.as<int>());
+                                                          job.d_segs.as<OzSeg>(), tbase, ctx.oz_err.as<int>()); ISCSI_COUNT_LAUNCH();
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
 }
@@ -290,19 +282,19 @@ int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec) {
     job.nvec = nvec;
     job.tbase = ttw;
   }
-  k_oz_fill_int<<<launch_blocks(exp_elems, 256), 256, 0, st>>>(ctx.oz_bexp.as<int>(), exp_elems, INT_MIN);
+  k_oz_fill_int<<<launch_blocks(exp_elems, 256), 256, 0, st>>>(ctx.oz_bexp.as<int>(), exp_elems, INT_MIN); ISCSI_COUNT_LAUNCH();
   const SpinSpace& SA = ctx.sp[0];
   const SpinSpace& SB = ctx.sp[1];
   long long flat = tt.start[tt.nclass];
   k_oz_col_exp<<<launch_blocks(flat, 256), 256, 0, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_of.as<int>(),
                                                           ctx.hp_inv.as<int>(), SA.lift.as<int>(), SB.lift.as<int>(),
                                                           SA.level.as<int8_t>(), ctx.nballow.as<int>(),
-                                                          ctx.off.as<long long>(), c, ctx.ndet, ctx.oz_bexp.as<int>());
-  k_oz_fix_exp<<<launch_blocks(exp_elems, 256), 256, 0, st>>>(ctx.oz_bexp.as<int>(), exp_elems);
+                                                          ctx.off.as<long long>(), c, ctx.ndet, ctx.oz_bexp.as<int>()); ISCSI_COUNT_LAUNCH();
+  k_oz_fix_exp<<<launch_blocks(exp_elems, 256), 256, 0, st>>>(ctx.oz_bexp.as<int>(), exp_elems); ISCSI_COUNT_LAUNCH();
   k_oz_lift_slice<<<launch_blocks(flat, 256), 256, 0, st>>>(
       tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_of.as<int>(), ctx.hp_inv.as<int>(), SA.lift.as<int>(), SB.lift.as<int>(),
       SA.level.as<int8_t>(), ctx.nballow.as<int>(), ctx.off.as<long long>(), c, ctx.ndet, ctx.oz_bexp.as<int>(),
-      ctx.oz_bs.as<__nv_bfloat16>());
+      ctx.oz_bs.as<__nv_bfloat16>()); ISCSI_COUNT_LAUNCH();
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
 }
@@ -313,10 +305,13 @@ int opposite_tc_gemm(Context& ctx) { return launch_job(ctx, ctx.oz_ab, nullptr, 
 // same spin
 
 bool samespin_block_on_tc(const Context& ctx, int a) {
+  // blocks with more than 16 rows and 16 allowed beta strings fill enough of
+  // a 128 x 64 tile to beat the FP64 units; thinner ones stay on the FP64
+  // thin kernels of sigma.cu, which stream the wide operand once
   const SpinSpace& SA = ctx.sp[0];
   int rows = SA.level_start[a + 1] - SA.level_start[a];
   int nba = (int)ctx.nb_allowed_lvl[a];
-  return rows >= OZ_BM && nba >= OZ_BN;
+  return rows > kThinN && nba > kThinN;
 }
 
 bool samespin_tc_active(const Context& ctx) {
