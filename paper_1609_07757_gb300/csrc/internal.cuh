@@ -136,7 +136,8 @@ constexpr int kThinN = 16;
 struct OzJob {
   std::vector<OzProblem> probs;
   std::vector<OzSeg> segs;
-  DevBuf d_probs, d_segs;
+  std::vector<OzMaps> maps;  // one per segment
+  DevBuf d_probs, d_segs, d_maps;
   int tiles = 0;
   int nvec = -1;
   const void* tbase = nullptr;

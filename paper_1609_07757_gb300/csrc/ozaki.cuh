@@ -21,9 +21,11 @@
 //   weight makes that bias negligible over the whole K.  Relative error
 //   ~2^-48 of sum_k |x_k||y_k| (slice truncation, dropped levels, tail).
 //
-// Tile: 128 rows of A x 64 rows of B per CTA, K step 16 (one MMA), 3-stage
-// cp.async pipeline; one thread issues the 28 MMAs of a K step; 6 TMEM
-// accumulators of 64 columns (levels 0..4 and the tail).
+// Tile: 128 rows of A x 64 rows of B per CTA, K step 16, 4-stage TMA ring.
+// TMEM holds level L at columns 64L .. 64L+63 (L = 0..6), so the products
+// A_t x (B_0 .. B_{6-t}) of one A slice land on consecutive levels and go out
+// as one MMA of N = 64 (7 - t) columns (split at 256): 10 MMAs per K step
+// instead of 28, each A slice read from shared memory once or twice.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -108,48 +110,31 @@ __global__ void k_oz_slice(const double* __restrict__ X, int rows, int cols, lon
   oz_store_digits(a, out + t, slice_stride);
 }
 
-// [rows x 16] bf16 slice tile, K-major, into core-matrix layout:
-// offset(r, kc) = ((r/8)*2 + kc)*128 + (r%8)*16; LBO = 128 B, SBO = 256 B
-__device__ __forceinline__ void oz_load_unit(uint32_t sbase, const __nv_bfloat16* src_row0, int ld, int unit) {
-  int lane = threadIdx.x & 31;
-  int r = unit * 16 + (lane >> 4) * 8 + (lane & 7);
-  int kc = (lane >> 3) & 1;
-  const __nv_bfloat16* src = src_row0 + (long long)r * ld + kc * 8;
-  uint32_t dst = sbase + (uint32_t)(((r >> 3) * 2 + kc) * 128 + (r & 7) * 16);
-  tc::cp_async16(dst, src);
-}
-
-// one K step (16) of all slices of both operands; a, b point at (row 0 of the
-// tile, k0) of slice 0
-__device__ __forceinline__ void oz_load_stage(uint32_t sstage, const __nv_bfloat16* a, long long a_slice, int lda,
-                                              const __nv_bfloat16* b, long long b_slice, int ldb) {
-  // 84 units of 32 chunks: A 7 slices x 8 units, B 7 slices x 4 units
-  int warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < OZ_S * 12 / (OZ_THREADS / 32); ++i) {
-    int u = warp + i * (OZ_THREADS / 32);
-    if (u < OZ_S * 8) {
-      int s = u >> 3, unit = u & 7;
-      oz_load_unit(sstage + s * OZ_A_SLICE_BYTES, a + s * a_slice, lda, unit);
-    } else {
-      int v = u - OZ_S * 8;
-      int s = v >> 2, unit = v & 3;
-      oz_load_unit(sstage + OZ_S * OZ_A_SLICE_BYTES + s * OZ_B_SLICE_BYTES, b + s * b_slice, ldb, unit);
-    }
-  }
-}
-
+// Warp-specialised product kernel.  Per CTA one 128 x 64 output tile:
+//   warp 0     (one lane) loads K steps into a 4-stage ring: two TMA boxes
+//              (all slices of A, all slices of B) per step, completion as
+//              transaction bytes on full[stage],
+//   warp 1     (one lane) waits full[stage], issues the MMAs of the step,
+//              releases the stage through tcgen05.commit -> empty[stage] and,
+//              at the end of a K chunk, signals chunk_done,
+//   warps 2-5  drain the exact levels of each chunk from TMEM into int64
+//              sums held in registers (one output row, 64 columns per
+//              thread), finish each segment and release the accumulators
+//              (acc_free) for the next chunk.
+// Every wait is bounded; a wait that runs out sets abort (all roles stop),
+// the kernel waits (bounded) for its copies in flight, frees TMEM and
+// reports through err.
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    k_oz_gemm(const OzProblem* __restrict__ probs, int nprobs, const OzSeg* __restrict__ segs, double* tbase,
-              int* __restrict__ err) {
+    k_oz_gemm(const OzProblem* __restrict__ probs, int nprobs, const OzSeg* __restrict__ segs,
+              const OzMaps* __restrict__ maps, double* tbase, int* __restrict__ err) {
   extern __shared__ unsigned char oz_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
-  uint32_t s_stage0 = tc::smem_u32(smem);
-  long long* sums = reinterpret_cast<long long*>(smem + OZ_STAGES * OZ_STAGE_BYTES);  // [BN][BM]
-  __shared__ uint64_t mbar[OZ_STAGES];
+  const uint32_t s_stage0 = tc::smem_u32(smem);
+  __shared__ uint64_t full_b[OZ_STAGES], empty_b[OZ_STAGES], chunk_b, free_b, drain_b;
   __shared__ uint32_t tmem_s;
-  __shared__ int abort_s;
+  __shared__ volatile int abort_s;
   __shared__ OzSeg seg_s[OZ_MAX_SEGS];
+  __shared__ int segid_s[OZ_MAX_SEGS];
   __shared__ int step0_s[OZ_MAX_SEGS + 1];
   __shared__ int nseg_s;
 
@@ -162,19 +147,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   }
   const OzProblem P = probs[lo];
   double* const Tp = P.t_rel ? tbase + P.t : reinterpret_cast<double*>(P.t);
-  int tl = tile - P.tile_begin;
-  int m0 = (tl / P.tiles_n) * OZ_BM, n0 = (tl % P.tiles_n) * OZ_BN;
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tl = tile - P.tile_begin;
+  const int m0 = (tl / P.tiles_n) * OZ_BM, n0 = (tl % P.tiles_n) * OZ_BN;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int SPC = OZ_CHUNK / OZ_BK;  // steps per chunk
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < OZ_STAGES; ++s) tc::mbar_init(tc::smem_u32(&mbar[s]), 1);
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      tc::mbar_init(tc::smem_u32(&full_b[s]), 1);
+      tc::mbar_init(tc::smem_u32(&empty_b[s]), 1);
+    }
+    tc::mbar_init(tc::smem_u32(&chunk_b), 1);
+    tc::mbar_init(tc::smem_u32(&free_b), 128);
+    tc::mbar_init(tc::smem_u32(&drain_b), 1);
     abort_s = 0;
-    // the segments that reach this tile, and their first global K step
     int ns = 0, steps = 0;
     for (int g = 0; g < P.seg_count && ns < OZ_MAX_SEGS; ++g) {
       OzSeg sg = segs[P.seg_begin + g];
       if (n0 >= sg.nrows_b || sg.K <= 0) continue;
       seg_s[ns] = sg;
+      segid_s[ns] = P.seg_begin + g;
       step0_s[ns] = steps;
       steps += sg.K / OZ_BK;
       ++ns;
@@ -183,170 +175,211 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     nseg_s = ns;
     tc::fence_mbar_init();
   }
-  if (warp == 0) {
+  if (warp == 1) {
     tc::tmem_alloc(tc::smem_u32(&tmem_s), OZ_TMEM_COLS);
     tc::tmem_relinquish();
   }
-  for (int i = threadIdx.x; i < OZ_BM * OZ_BN; i += OZ_THREADS) sums[i] = 0;
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_s;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-  constexpr uint32_t idesc = tc::idesc_bf16_f32(OZ_BM, OZ_BN);
   const int nseg = nseg_s;
   const int total = step0_s[nseg];
-  const int row = warp * 32 + lane;
-  const int gm = m0 + row;
 
-  // register copy of the segment being loaded (loads advance in step order)
-  int ld_seg = -1, ld_end = 0, ld_begin = 0;
-  const __nv_bfloat16 *la = nullptr, *lb = nullptr;
-  long long las = 0, lbs = 0;
-  int llda = 0, lldb = 0;
-  auto load_step = [&](int g, int stage) {
-    while (g >= ld_end) {
-      ++ld_seg;
-      ld_begin = step0_s[ld_seg];
-      ld_end = step0_s[ld_seg + 1];
-      const OzSeg& S = seg_s[ld_seg];
-      llda = S.lda;
-      lldb = S.ldb;
-      las = S.a_slice;
-      lbs = S.b_slice;
-      la = S.as + (long long)m0 * llda;
-      lb = S.bs + (long long)n0 * lldb;
+  auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+    uint32_t a = tc::smem_u32(bar);
+    for (long long i = 0; i < OZ_SPIN; ++i) {
+      if (tc::mbar_try_wait(a, parity)) return true;
+      if ((i & 1023) == 1023 && abort_s) return false;
     }
-    int k0 = (g - ld_begin) * OZ_BK;
-    oz_load_stage(s_stage0 + stage * OZ_STAGE_BYTES, la + k0, las, llda, lb + k0, lbs, lldb);
+    abort_s = 1;
+    return false;
   };
-  // segment of the step being computed
-  int c_seg = 0, c_begin = 0, c_end = nseg > 0 ? step0_s[1] : 0;
 
-  for (int s = 0; s < OZ_STAGES; ++s) {
-    if (s < total) load_step(s, s);
-    tc::cp_async_commit();
-  }
-  bool aborted = false;
-  int done_segs = 0;
-  for (int g = 0; g < total; ++g) {
-    int st = g % OZ_STAGES;
-    // step g is commit group g (prologue: 0..S-1, then one group per g >= 1)
-    if (g == 0) tc::cp_async_wait<OZ_STAGES - 1>();
-    else tc::cp_async_wait<OZ_STAGES - 2>();
-    tc::fence_proxy_async();
-    __syncthreads();
-    while (g >= c_end) {
-      ++c_seg;
-      c_begin = c_end;
-      c_end = step0_s[c_seg + 1];
+  if (warp == 0) {
+    // ---------------- producer (TMA)
+    if (lane == 0) {
+      int seg = -1, seg_end = 0, seg_begin = 0;
+      const CUtensorMap *ma = nullptr, *mb = nullptr;
+      int ax = 0, ay = 0, bx = 0, by = 0;
+      int issued = 0;
+      for (int g = 0; g < total; ++g) {
+        const int st = g % OZ_STAGES;
+        if (g >= OZ_STAGES && !wait(&empty_b[st], ((g / OZ_STAGES) - 1) & 1)) break;
+        while (g >= seg_end) {
+          ++seg;
+          seg_begin = step0_s[seg];
+          seg_end = step0_s[seg + 1];
+          const OzSeg& S = seg_s[seg];
+          ma = &maps[segid_s[seg]].a;
+          mb = &maps[segid_s[seg]].b;
+          ax = S.a_k0;
+          ay = S.a_row0 + m0;
+          bx = S.b_k0;
+          by = S.b_row0 + n0;
+        }
+        const int k0 = (g - seg_begin) * OZ_BK;
+        const uint32_t fb = tc::smem_u32(&full_b[st]);
+        const uint32_t sa = s_stage0 + st * OZ_STAGE_BYTES;
+        tc::mbar_arrive_expect_tx(fb, OZ_STAGE_BYTES);
+        tc::tma_load_3d(sa, ma, ax + k0, ay, 0, fb);
+        tc::tma_load_3d(sa + OZ_S * OZ_A_SLICE_BYTES, mb, bx + k0, by, 0, fb);
+        issued = g + 1;
+      }
+      // copies still in flight (only after an abort) must land before the
+      // CTA's shared memory is released: wait for the last phase of each stage
+      for (int g = issued - OZ_STAGES > 0 ? issued - OZ_STAGES : 0; g < issued; ++g)
+        tc::mbar_wait_bounded(tc::smem_u32(&full_b[g % OZ_STAGES]), (g / OZ_STAGES) & 1, OZ_SPIN);
     }
-    const int sgi = c_seg;
-    int local = g - c_begin;
-    int seg_steps = c_end - c_begin;
-    int kin = local % (OZ_CHUNK / OZ_BK);
-    if (threadIdx.x == 0) {
-      tc::fence_after_sync();
-      uint32_t sa = s_stage0 + st * OZ_STAGE_BYTES;
-      uint32_t sb = sa + OZ_S * OZ_A_SLICE_BYTES;
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t N64 = tc::idesc_bf16_f32(OZ_BM, 64), N128 = tc::idesc_bf16_f32(OZ_BM, 128),
+                         N192 = tc::idesc_bf16_f32(OZ_BM, 192), N256 = tc::idesc_bf16_f32(OZ_BM, 256);
+      constexpr uint32_t TAIL = OZ_EXACT * OZ_BN;  // level 5 (level 6 follows at +64)
+      int seg = 0, seg_begin = 0, seg_end = nseg > 0 ? step0_s[1] : 0;
+      int chunk = 0;  // chunks completed so far
+      for (int g = 0; g < total; ++g) {
+        const int st = g % OZ_STAGES;
+        while (g >= seg_end) {
+          ++seg;
+          seg_begin = seg_end;
+          seg_end = step0_s[seg + 1];
+        }
+        const int local = g - seg_begin;
+        const int kin = local % SPC;
+        if (!wait(&full_b[st], (g / OZ_STAGES) & 1)) break;
+        tc::fence_after_sync();
+        const uint32_t sa = s_stage0 + st * OZ_STAGE_BYTES;
+        const uint32_t sb = sa + OZ_S * OZ_A_SLICE_BYTES;
+        auto A = [&](int t) { return tc::smem_desc_sw32(sa + t * OZ_A_SLICE_BYTES); };
+        auto B = [&](int u) { return tc::smem_desc_sw32(sb + u * OZ_B_SLICE_BYTES); };
+        const bool new_seg = local == 0;
+        const bool new_chunk = kin == 0;
+        if (!new_chunk) {
+          // A_t x (B_0 .. B_{6-t}) into levels t .. 6
+          tc::mma_bf16(tmem + 0, A(0), B(0), N256, 1u);
+          tc::mma_bf16(tmem + 256, A(0), B(4), N192, 1u);
+          tc::mma_bf16(tmem + 64, A(1), B(0), N256, 1u);
+          tc::mma_bf16(tmem + 320, A(1), B(4), N128, 1u);
+          tc::mma_bf16(tmem + 128, A(2), B(0), N256, 1u);
+          tc::mma_bf16(tmem + 384, A(2), B(4), N64, 1u);
+          tc::mma_bf16(tmem + 192, A(3), B(0), N256, 1u);
+          tc::mma_bf16(tmem + 256, A(4), B(0), N192, 1u);
+          tc::mma_bf16(tmem + 320, A(5), B(0), N128, 1u);
+          tc::mma_bf16(tmem + 384, A(6), B(0), N64, 1u);
+        } else {
+          // first step of a chunk: the tail levels (5, 6) run across the
+          // chunks of a segment and go first, unless a new segment starts
+          // and the epilogue still reads them; the exact levels restart
+          // once the epilogue has drained the previous chunk
+          if (new_seg && chunk > 0 && !wait(&free_b, (chunk - 1) & 1)) break;
 #pragma unroll
-      for (int L = 0; L < OZ_S; ++L) {
-        uint32_t acc_col = (uint32_t)((L < OZ_EXACT ? L : OZ_EXACT) * OZ_BN);
-#pragma unroll
-        for (int t = 0; t <= L; ++t) {
-          int u = L - t;
-          uint64_t ad = tc::smem_desc(sa + t * OZ_A_SLICE_BYTES, 128, 256);
-          uint64_t bd = tc::smem_desc(sb + u * OZ_B_SLICE_BYTES, 128, 256);
-          uint32_t accum;
-          if (L < OZ_EXACT) accum = (kin == 0 && t == 0) ? 0u : 1u;
-          else accum = (local == 0 && L == OZ_EXACT && t == 0) ? 0u : 1u;
-          tc::mma_bf16(tmem + acc_col, ad, bd, idesc, accum);
+          for (int t = 0; t < OZ_EXACT; ++t)
+            tc::mma_bf16(tmem + TAIL, A(t), B(OZ_EXACT - t), N128, (new_seg && t == 0) ? 0u : 1u);
+          tc::mma_bf16(tmem + TAIL, A(5), B(0), N128, 1u);
+          tc::mma_bf16(tmem + TAIL + 64, A(6), B(0), N64, 1u);
+          if (!new_seg && chunk > 0 && !wait(&free_b, (chunk - 1) & 1)) break;
+          tc::mma_bf16(tmem + 0, A(0), B(0), N256, 0u);
+          tc::mma_bf16(tmem + 256, A(0), B(4), N64, 0u);
+          tc::mma_bf16(tmem + 64, A(1), B(0), N256, 1u);
+          tc::mma_bf16(tmem + 128, A(2), B(0), N192, 1u);
+          tc::mma_bf16(tmem + 192, A(3), B(0), N128, 1u);
+          tc::mma_bf16(tmem + 256, A(4), B(0), N64, 1u);
+        }
+        tc::mma_commit(tc::smem_u32(&empty_b[st]));
+        if (kin == SPC - 1 || local == seg_end - seg_begin - 1) {
+          tc::mma_commit(tc::smem_u32(&chunk_b));
+          ++chunk;
         }
       }
-      tc::mma_commit(tc::smem_u32(&mbar[st]));
+      if (abort_s) {
+        // let MMAs already issued finish before TMEM is released (bounded)
+        tc::mma_commit(tc::smem_u32(&drain_b));
+        tc::mbar_wait_bounded(tc::smem_u32(&drain_b), 0, OZ_SPIN);
+      }
     }
-    // refill the stage of step g-1 once its MMAs completed
-    if (g >= 1 && g - 1 + OZ_STAGES < total) {
-      int ps = (g - 1) % OZ_STAGES;
-      if (!tc::mbar_wait_bounded(tc::smem_u32(&mbar[ps]), ((g - 1) / OZ_STAGES) & 1, OZ_SPIN)) abort_s = 1;
-      else load_step(g - 1 + OZ_STAGES, ps);
-    }
-    if (g >= 1) tc::cp_async_commit();
-    bool seg_end = (local == seg_steps - 1);
-    bool chunk_end = (kin == OZ_CHUNK / OZ_BK - 1) || seg_end;
-    if (chunk_end) {
-      // all MMAs so far done -> flush the exact levels into the int64 sums
-      if (!tc::mbar_wait_bounded(tc::smem_u32(&mbar[st]), (g / OZ_STAGES) & 1, OZ_SPIN)) abort_s = 1;
-      __syncthreads();  // abort_s is uniform below (tcgen05.ld is warp-collective)
-      if (!abort_s) {
+  } else {
+    // ---------------- epilogue: warps 2-5, TMEM lane quarter = warp % 4
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    const int gm = m0 + row;
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    long long sums[OZ_BN];
+#pragma unroll
+    for (int j = 0; j < OZ_BN; ++j) sums[j] = 0;
+    int chunk = 0, done_segs = 0;
+    for (int s = 0; s < nseg && !abort_s; ++s) {
+      const int steps = step0_s[s + 1] - step0_s[s];
+      const int nch = (steps + SPC - 1) / SPC;
+      const OzSeg& S = seg_s[s];
+      for (int ch = 0; ch < nch; ++ch, ++chunk) {
+        // warp-uniform decision: tcgen05.ld below is warp-collective
+        bool ok = wait(&chunk_b, chunk & 1);
+        if (!__all_sync(0xffffffffu, ok)) break;
         tc::fence_after_sync();
-        const OzSeg& S = seg_s[sgi];
-        int ea = (seg_end && gm < P.M) ? S.a_exp[gm] : 0;
-#pragma unroll 1
-        for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
-          uint32_t r0[16], r1[16], r2[16], r3[16], r4[16];
-          tc::tmem_ld16(tmem + lane_base + 0 * OZ_BN + c0, r0);
-          tc::tmem_ld16(tmem + lane_base + 1 * OZ_BN + c0, r1);
-          tc::tmem_ld16(tmem + lane_base + 2 * OZ_BN + c0, r2);
-          tc::tmem_ld16(tmem + lane_base + 3 * OZ_BN + c0, r3);
-          tc::tmem_ld16(tmem + lane_base + 4 * OZ_BN + c0, r4);
+#pragma unroll
+        for (int c0 = 0; c0 < OZ_BN; c0 += 8) {
+          uint32_t r0[8], r1[8], r2[8], r3[8], r4[8];
+          tc::tmem_ld8(tmem + lane_base + 0 * OZ_BN + c0, r0);
+          tc::tmem_ld8(tmem + lane_base + 1 * OZ_BN + c0, r1);
+          tc::tmem_ld8(tmem + lane_base + 2 * OZ_BN + c0, r2);
+          tc::tmem_ld8(tmem + lane_base + 3 * OZ_BN + c0, r3);
+          tc::tmem_ld8(tmem + lane_base + 4 * OZ_BN + c0, r4);
           tc::tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
+          for (int j = 0; j < 8; ++j) {
             // level L holds 2^-7L I_L exactly; recover the integers
             int i0 = __float2int_rn(__uint_as_float(r0[j]));
             int i1 = __float2int_rn(__uint_as_float(r1[j]) * 128.0f);
             int i2 = __float2int_rn(__uint_as_float(r2[j]) * 16384.0f);
             int i3 = __float2int_rn(__uint_as_float(r3[j]) * 2097152.0f);
             int i4 = __float2int_rn(__uint_as_float(r4[j]) * 268435456.0f);
-            long long v = ((long long)i0 << 28) + ((long long)i1 << 21) + ((long long)i2 << 14) +
-                          ((long long)i3 << 7) + (long long)i4;
-            sums[(c0 + j) * OZ_BM + row] += v;
+            sums[c0 + j] += ((long long)i0 << 28) + ((long long)i1 << 21) + ((long long)i2 << 14) +
+                            ((long long)i3 << 7) + (long long)i4;
           }
-          if (seg_end) {
-            // this segment's result: 2^(ea+eb-14) (S 2^-28 + tail), into T
-            uint32_t rt[16];
-            tc::tmem_ld16(tmem + lane_base + OZ_EXACT * OZ_BN + c0, rt);
+        }
+        if (ch == nch - 1) {
+          // this segment's result: 2^(ea+eb-14) (S 2^-28 + tail), into T
+          const int ea = gm < P.M ? S.a_exp[gm] : 0;
+#pragma unroll
+          for (int c0 = 0; c0 < OZ_BN; c0 += 8) {
+            uint32_t r5[8], r6[8];
+            tc::tmem_ld8(tmem + lane_base + OZ_EXACT * OZ_BN + c0, r5);
+            tc::tmem_ld8(tmem + lane_base + (OZ_EXACT + 1) * OZ_BN + c0, r6);
             tc::tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              int gn = n0 + c0 + j;
-              long long sv = sums[(c0 + j) * OZ_BM + row];
-              sums[(c0 + j) * OZ_BM + row] = 0;
+            for (int j = 0; j < 8; ++j) {
+              const int gn = n0 + c0 + j;
               if (gm < P.M && gn < P.N && gn < S.nrows_b) {
-                double v = (double)sv * 3.7252902984619141e-09 /* 2^-28 */ + (double)__uint_as_float(rt[j]);
+                double v = (double)sums[c0 + j] * 3.7252902984619141e-09 /* 2^-28 */ +
+                           ((double)__uint_as_float(r5[j]) + (double)__uint_as_float(r6[j]));
                 v = ldexp(v, ea + S.b_exp[gn] - 14);
                 double* dst = Tp + (long long)gm * P.ldt + gn;
                 *dst = (P.accumulate || done_segs > 0) ? *dst + v : v;
               }
+              sums[c0 + j] = 0;
             }
           }
+          ++done_segs;
         }
         tc::fence_before_sync();
+        tc::mbar_arrive(tc::smem_u32(&free_b));
       }
-      if (seg_end) ++done_segs;
     }
-    __syncthreads();
-    if (abort_s) {
-      aborted = true;
-      break;
-    }
-  }
-  tc::cp_async_wait<0>();
-  __syncthreads();
-  if (aborted || abort_s) {
-    if (threadIdx.x == 0) atomicExch(err, 1);
-  } else if (nseg == 0 && !P.accumulate) {
-    // no segment reaches this tile: its block of T is zero
-    if (gm < P.M)
+    if (nseg == 0 && !P.accumulate && gm < P.M) {
+      // no segment reaches this tile: its block of T is zero
       for (int j = 0; j < OZ_BN; ++j) {
-        int gn = n0 + j;
+        const int gn = n0 + j;
         if (gn < P.N) Tp[(long long)gm * P.ldt + gn] = 0.0;
       }
+    }
   }
+  __syncthreads();
+  if (abort_s && threadIdx.x == 0) atomicExch(err, 1);
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, OZ_TMEM_COLS);
   }

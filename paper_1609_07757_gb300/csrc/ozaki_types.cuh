@@ -1,6 +1,7 @@
 // ozaki_types.cuh -- constants and work-list records of the tensor-core
 // FP64-accurate contraction (kernels in ozaki.cuh).
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 namespace iscsi {
@@ -11,33 +12,38 @@ constexpr int OZ_EXACT = 5;        // levels flushed exactly per chunk
 constexpr int OZ_BM = 128;         // rows of A per tile
 constexpr int OZ_BN = 64;          // rows of B per tile
 constexpr int OZ_BK = 16;          // K per stage (one MMA)
-constexpr int OZ_STAGES = 3;
+constexpr int OZ_STAGES = 4;
 constexpr int OZ_CHUNK = 256;      // K per exact flush
-constexpr int OZ_THREADS = 128;
+constexpr int OZ_THREADS = 192;   // warp 0 loads (TMA), warp 1 issues MMAs, warps 2-5 drain TMEM
 constexpr int OZ_A_SLICE_BYTES = OZ_BM * OZ_BK * 2;   // 4096
 constexpr int OZ_B_SLICE_BYTES = OZ_BN * OZ_BK * 2;   // 2048
 constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_SLICE_BYTES + OZ_B_SLICE_BYTES);
-constexpr int OZ_SUM_BYTES = OZ_BM * OZ_BN * 8;
-constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + OZ_SUM_BYTES + 1024;
-constexpr int OZ_TMEM_COLS = 512;  // 6 x 64 used
+constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + 1024;
+constexpr int OZ_TMEM_COLS = 512;  // 7 levels x 64 columns used
 constexpr long long OZ_SPIN = 1ll << 24;
 
 constexpr int OZ_MAX_SEGS = 8;
 
-// One operand pair of a product: A[M][K] and B[N][K] (both K-major slices,
-// pointers at row 0 / k 0 of this problem).  Slices are zero padded so tile
-// loads need no bounds checks: A rows to the tile multiple of 128, B rows to
-// the multiple of 64, K to a multiple of 16.  Rows of B at or beyond nrows_b
-// contribute nothing (tiles wholly beyond are skipped).
+// One operand pair of a product: A[M][K] and B[N][K], both read through TMA
+// from K-major slice arrays [S][rows][ld] (bf16).  The segment's block starts
+// at (a_row0, a_k0) in A's array and (b_row0, b_k0) in B's; k offsets are
+// multiples of 16.  Slice arrays are zero padded so that tiles need no bounds
+// checks: A rows to the tile multiple of 128, B rows to the multiple of 64, K
+// to a multiple of 16.  Rows of B at or beyond nrows_b contribute nothing
+// (tiles wholly beyond are skipped).
 struct OzSeg {
-  const __nv_bfloat16* as;  // [S][*][lda]
-  const __nv_bfloat16* bs;  // [S][*][ldb]
-  long long a_slice, b_slice;  // elements between slices
-  const int* a_exp;         // row exponents of A (index = problem row)
-  const int* b_exp;         // row exponents of B (index = problem column)
-  int lda, ldb;             // row strides (elements)
-  int K;                    // multiple of 16
-  int nrows_b;              // valid rows of B
+  const int* a_exp;  // row exponents of A (index = problem row)
+  const int* b_exp;  // row exponents of B (index = problem column)
+  int a_row0, a_k0, b_row0, b_k0;
+  int K;             // multiple of 16
+  int nrows_b;       // valid rows of B
+};
+
+// TMA descriptors of a segment's two slice arrays: dims (ld, rows, S), box
+// (16, 128 or 64, S), 32-byte swizzle.  Kept in global memory beside the
+// segment list (one entry per segment).
+struct OzMaps {
+  CUtensorMap a, b;
 };
 
 // T[M][N] (FP64, ldt) (+)= sum over segments of A_seg B_seg^T; T is the

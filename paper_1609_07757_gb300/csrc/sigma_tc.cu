@@ -21,6 +21,7 @@
 
 #include "internal.cuh"
 #include "ozaki.cuh"
+#include "tma_map.h"
 
 namespace iscsi {
 
@@ -161,9 +162,44 @@ static int tc_prepare_g(Context& ctx) {
                       ctx.oz_gs.as<__nv_bfloat16>(), st);
 }
 
+// one slice array as TMA sees it
+struct SliceArray {
+  const __nv_bfloat16* base;
+  int ld;
+  long long rows, slice;
+};
+
+// segment of a job: block (a_row0, a_k0) of A times block (b_row0, b_k0) of B
+static int add_seg(OzJob& job, const SliceArray& A, int a_row0, int a_k0, const int* a_exp, const SliceArray& B,
+                   int b_row0, int b_k0, const int* b_exp, int K, int nrows_b) {
+  OzSeg sg;
+  sg.a_exp = a_exp;
+  sg.b_exp = b_exp;
+  sg.a_row0 = a_row0;
+  sg.a_k0 = a_k0;
+  sg.b_row0 = b_row0;
+  sg.b_k0 = b_k0;
+  sg.K = K;
+  sg.nrows_b = nrows_b;
+  OzMaps m;
+  std::memset(&m, 0, sizeof(m));
+  if (oz_encode_map(&m.a, A.base, A.ld, A.rows, OZ_S, A.slice, OZ_BM) ||
+      oz_encode_map(&m.b, B.base, B.ld, B.rows, OZ_S, B.slice, OZ_BN)) {
+    set_error("tensor-core sigma: TMA descriptor rejected");
+    return kErrCuda;
+  }
+  job.segs.push_back(sg);
+  job.maps.push_back(m);
+  return kOk;
+}
+
 static int upload_job(OzJob& job, cudaStream_t st) {
   ISCSI_TRY(job.d_probs.grow(sizeof(OzProblem) * std::max<size_t>(1, job.probs.size())));
   ISCSI_TRY(job.d_segs.grow(sizeof(OzSeg) * std::max<size_t>(1, job.segs.size())));
+  ISCSI_TRY(job.d_maps.grow(sizeof(OzMaps) * std::max<size_t>(1, job.maps.size())));
+  if (!job.maps.empty())
+    ISCSI_CUDA(cudaMemcpyAsync(job.d_maps.p, job.maps.data(), sizeof(OzMaps) * job.maps.size(),
+                               cudaMemcpyHostToDevice, st));
   if (!job.probs.empty())
     ISCSI_CUDA(cudaMemcpyAsync(job.d_probs.p, job.probs.data(), sizeof(OzProblem) * job.probs.size(),
                                cudaMemcpyHostToDevice, st));
@@ -177,7 +213,8 @@ static int upload_job(OzJob& job, cudaStream_t st) {
 static int launch_job(Context& ctx, const OzJob& job, double* tbase, cudaStream_t st) {
   if (job.tiles == 0) return kOk;
   k_oz_gemm<<<job.tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(job.d_probs.as<OzProblem>(), (int)job.probs.size(),
-                                                          job.d_segs.as<OzSeg>(), tbase, ctx.oz_err.as<int>()); ISCSI_COUNT_LAUNCH();
+                                                          job.d_segs.as<OzSeg>(), job.d_maps.as<OzMaps>(), tbase,
+                                                          ctx.oz_err.as<int>()); ISCSI_COUNT_LAUNCH();
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
 }
@@ -247,20 +284,12 @@ int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec) {
     OzJob& job = ctx.oz_ab;
     job.probs.clear();
     job.segs.clear();
+    job.maps.clear();
     long long t_off = 0;
+    const SliceArray GA{ctx.oz_gs.as<__nv_bfloat16>(), ctx.oz_kpad, ctx.oz_mpad, (long long)ctx.oz_mpad * ctx.oz_kpad};
     for (int i = 0; i < tt.nclass; ++i) {
       const TcClass& C = tt.c[i];
-      OzSeg sg;
-      sg.as = ctx.oz_gs.as<__nv_bfloat16>();
-      sg.bs = ctx.oz_bs.as<__nv_bfloat16>() + C.bs_off;
-      sg.a_slice = (long long)ctx.oz_mpad * ctx.oz_kpad;
-      sg.b_slice = (long long)C.npad * C.kpad;
-      sg.a_exp = ctx.oz_gexp.as<int>();
-      sg.b_exp = ctx.oz_bexp.as<int>() + C.exp_off;
-      sg.lda = ctx.oz_kpad;
-      sg.ldb = C.kpad;
-      sg.K = C.kpad;
-      sg.nrows_b = C.ncols;
+      const SliceArray CB{ctx.oz_bs.as<__nv_bfloat16>() + C.bs_off, C.kpad, C.npad, (long long)C.npad * C.kpad};
       OzProblem P;
       std::memset(&P, 0, sizeof(P));
       // T_c sits where the fold expects it: classes in order, mrows x ncols each
@@ -274,7 +303,8 @@ int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec) {
       P.seg_count = 1;
       P.accumulate = 0;
       t_off += (long long)mrows * C.ncols;
-      job.segs.push_back(sg);
+      ISCSI_TRY(add_seg(job, GA, 0, 0, ctx.oz_gexp.as<int>(), CB, 0, 0, ctx.oz_bexp.as<int>() + C.exp_off, C.kpad,
+                        C.ncols));
       job.probs.push_back(P);
     }
     job.tiles = add_tiles(job.probs);
@@ -433,6 +463,11 @@ int samespin_tc(Context& ctx, const double* c, double* sigma, int nvec) {
     OzJob& job = ctx.oz_ss;
     job.probs.clear();
     job.segs.clear();
+    job.maps.clear();
+    const SliceArray MA{ctx.oz_mas.as<__nv_bfloat16>(), ctx.oz_ma_ld, ctx.oz_ma_rows,
+                        (long long)ctx.oz_ma_rows * ctx.oz_ma_ld};
+    const SliceArray MB{ctx.oz_mbs.as<__nv_bfloat16>(), ctx.oz_mb_ld, ctx.oz_mb_rows,
+                        (long long)ctx.oz_mb_rows * ctx.oz_mb_ld};
     for (int v = 0; v < nvec; ++v)
       for (const SsBlock& b : blocks) {
         if (!samespin_block_on_tc(ctx, b.a)) continue;
@@ -448,33 +483,15 @@ int samespin_tc(Context& ctx, const double* c, double* sigma, int nvec) {
         if (ctx.na > 0 && ctx.oz_mas.p)
           for (const SsBlock& b2 : blocks) {
             if (std::abs(b.a - b2.a) > 2) continue;
-            OzSeg sg;
-            sg.as = ctx.oz_mas.as<__nv_bfloat16>() + (long long)b.start * ctx.oz_ma_ld + ctx.oz_kbase[b2.a];
-            sg.a_slice = (long long)ctx.oz_ma_rows * ctx.oz_ma_ld;
-            sg.a_exp = ctx.oz_maexp.as<int>() + b.start;
-            sg.lda = ctx.oz_ma_ld;
-            sg.bs = cs + v * elems1 + b2.bt_off;
-            sg.b_slice = (long long)b2.bt_rows * b2.bt_ld;
-            sg.b_exp = cx + v * exps1 + b2.bt_exp;
-            sg.ldb = b2.bt_ld;
-            sg.K = b2.bt_ld;
-            sg.nrows_b = std::min(b.nba, b2.nba);
-            job.segs.push_back(sg);
+            const SliceArray CT{cs + v * elems1 + b2.bt_off, b2.bt_ld, b2.bt_rows, (long long)b2.bt_rows * b2.bt_ld};
+            ISCSI_TRY(add_seg(job, MA, b.start, ctx.oz_kbase[b2.a], ctx.oz_maexp.as<int>() + b.start, CT, 0, 0,
+                              cx + v * exps1 + b2.bt_exp, b2.bt_ld, std::min(b.nba, b2.nba)));
             P.seg_count++;
           }
         if (ctx.nb > 0 && ctx.oz_mbs.p) {
-          OzSeg sg;
-          sg.as = cs + v * elems1 + b.ca_off;
-          sg.a_slice = (long long)b.ca_rows * b.ca_ld;
-          sg.a_exp = cx + v * exps1 + b.ca_exp;
-          sg.lda = b.ca_ld;
-          sg.bs = ctx.oz_mbs.as<__nv_bfloat16>();
-          sg.b_slice = (long long)ctx.oz_mb_rows * ctx.oz_mb_ld;
-          sg.b_exp = ctx.oz_mbexp.as<int>();
-          sg.ldb = ctx.oz_mb_ld;
-          sg.K = b.ca_ld;
-          sg.nrows_b = b.nba;
-          job.segs.push_back(sg);
+          const SliceArray CA{cs + v * elems1 + b.ca_off, b.ca_ld, b.ca_rows, (long long)b.ca_rows * b.ca_ld};
+          ISCSI_TRY(add_seg(job, CA, 0, 0, cx + v * exps1 + b.ca_exp, MB, 0, 0, ctx.oz_mbexp.as<int>(), b.ca_ld,
+                            b.nba));
           P.seg_count++;
         }
         if (P.seg_count > 0) job.probs.push_back(P);

@@ -1,6 +1,7 @@
 // tc_ptx.cuh -- inline-PTX wrappers for the Blackwell tensor-core path (sm_103a):
 // tcgen05 MMA with operands in shared memory and the accumulator in tensor
-// memory (TMEM), mbarrier completion tracking, cp.async staging.
+// memory (TMEM), mbarrier completion tracking, TMA tensor copies and cp.async
+// staging.
 #pragma once
 #include <cstdint>
 
@@ -21,6 +22,37 @@ TC_DEVI void cp_async_wait() {
 }
 // generic-proxy shared-memory writes become visible to the tensor core (async proxy)
 TC_DEVI void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// arrive on the mbarrier when all earlier cp.async of this thread completed
+// (the barrier's expected count includes this arrival)
+TC_DEVI void cp_async_mbar_arrive(uint32_t mbar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(mbar) : "memory");
+}
+TC_DEVI void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+TC_DEVI void mbar_arrive(uint32_t mbar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
+}
+
+// arrive (count 1) and add `bytes` to the transaction count the phase waits for
+TC_DEVI void mbar_arrive_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(mbar),
+               "r"(bytes)
+               : "memory");
+}
+
+// TMA: box of a 3-D tensor map at coordinates (x, y, z) into shared memory;
+// completion is signalled on mbar as transaction bytes.  x (innermost) must be
+// a multiple of 16 bytes' worth of elements.
+TC_DEVI void tma_load_3d(uint32_t dst, const void* map, int x, int y, int z, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(mbar)
+      : "memory");
+}
+TC_DEVI void prefetch_map(const void* map) {
+  asm volatile("prefetch.tensormap [%0];\n" ::"l"(map) : "memory");
+}
 
 TC_DEVI void mbar_init(uint32_t a, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
@@ -73,6 +105,11 @@ TC_DEVI void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
+TC_DEVI void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
 TC_DEVI void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
 // Shared-memory matrix descriptor (SM100 format), no swizzle, K-major canonical
@@ -83,6 +120,19 @@ TC_DEVI uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
   d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
   d |= (uint64_t)1 << 46;  // descriptor version for this architecture
+  return d;
+}
+
+// Shared-memory matrix descriptor, K-major with the 32-byte swizzle (the
+// layout TMA writes for a box whose rows are 32 bytes under
+// CU_TENSOR_MAP_SWIZZLE_32B): rows of 32 bytes, 8-row groups sbo = 256 bytes
+// apart; one MMA's K extent (16 bf16) is the whole swizzle width.
+TC_DEVI uint64_t smem_desc_sw32(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;             // leading byte offset: unused for this layout
+  d |= (uint64_t)(256 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)6 << 61;             // swizzle mode: 32 bytes
   return d;
 }
 
