@@ -10,8 +10,10 @@
 //   slice t is stored as the bf16 value a_t 2^-7t (exact: <= 8 significant bits);
 //   the product sum_k x_k y_k = 2^-14 sum_L 2^-7L I_L with
 //     I_L = sum_k sum_{t+u=L} a_t b_u  (integers);
-//   over a K chunk of 256 every |I_L| <= 256 (L+3) 2^12 <= 2^24, so the FP32
-//   tensor-memory accumulator of each level is exact;
+//   one k contributes at most 2 * 2^7 2^6 + (L-1) 2^12 = (L+3) 2^12 to I_L
+//   (4 * 2^12 for L = 0), so over a K chunk of 512 every |I_L| <= 7 * 2^21
+//   < 2^24 for L <= 4 and the FP32 tensor-memory accumulator of each of
+//   these levels holds it exactly;
 //   levels L = 0..4 are flushed after every chunk into an exact int64 running
 //   sum S = sum_L 2^7(4-L) I_L; levels 5..6 (weight <= 2^-35 of the leading
 //   one) accumulate in one FP32 tail over the whole K; levels >= 7 are dropped.
@@ -117,10 +119,11 @@ __global__ void k_oz_slice(const double* __restrict__ X, int rows, int cols, lon
 //   warp 1     (one lane) waits full[stage], issues the MMAs of the step,
 //              releases the stage through tcgen05.commit -> empty[stage] and,
 //              at the end of a K chunk, signals chunk_done,
-//   warps 2-5  drain the exact levels of each chunk from TMEM into int64
-//              sums held in registers (one output row, 64 columns per
-//              thread), finish each segment and release the accumulators
-//              (acc_free) for the next chunk.
+//   warps 2+   drain the exact levels of each chunk from TMEM into int64
+//              sums held in registers (one output row per thread; with 8
+//              epilogue warps, warps w and w+4 share TMEM lane quarter w % 4
+//              and take half of the columns each), finish each segment and
+//              release the accumulators (acc_free) for the next chunk.
 // Every wait is bounded; a wait that runs out sets abort (all roles stop),
 // the kernel waits (bounded) for its copies in flight, frees TMEM and
 // reports through err.
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       tc::mbar_init(tc::smem_u32(&empty_b[s]), 1);
     }
     tc::mbar_init(tc::smem_u32(&chunk_b), 1);
-    tc::mbar_init(tc::smem_u32(&free_b), 128);
+    tc::mbar_init(tc::smem_u32(&free_b), 32 * OZ_EPI_WARPS);
     tc::mbar_init(tc::smem_u32(&drain_b), 1);
     abort_s = 0;
     int ns = 0, steps = 0;
@@ -300,14 +303,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
     }
   } else {
-    // ---------------- epilogue: warps 2-5, TMEM lane quarter = warp % 4
+    // ---------------- epilogue: TMEM lane quarter = warp % 4
     const int quarter = warp & 3;
     const int row = quarter * 32 + lane;
     const int gm = m0 + row;
-    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-    long long sums[OZ_BN];
+    const int cbase = OZ_EPI_WARPS == 4 ? 0 : ((warp - 2) >> 2) * OZ_EPI_COLS;  // first column of this warp
+    const uint32_t lane_base = ((uint32_t)(quarter * 32) << 16) + (uint32_t)cbase;
+    long long sums[OZ_EPI_COLS];
 #pragma unroll
-    for (int j = 0; j < OZ_BN; ++j) sums[j] = 0;
+    for (int j = 0; j < OZ_EPI_COLS; ++j) sums[j] = 0;
     int chunk = 0, done_segs = 0;
     for (int s = 0; s < nseg && !abort_s; ++s) {
       const int steps = step0_s[s + 1] - step0_s[s];
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         if (!__all_sync(0xffffffffu, ok)) break;
         tc::fence_after_sync();
 #pragma unroll
-        for (int c0 = 0; c0 < OZ_BN; c0 += 8) {
+        for (int c0 = 0; c0 < OZ_EPI_COLS; c0 += 8) {
           uint32_t r0[8], r1[8], r2[8], r3[8], r4[8];
           tc::tmem_ld8(tmem + lane_base + 0 * OZ_BN + c0, r0);
           tc::tmem_ld8(tmem + lane_base + 1 * OZ_BN + c0, r1);
@@ -343,14 +347,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           // this segment's result: 2^(ea+eb-14) (S 2^-28 + tail), into T
           const int ea = gm < P.M ? S.a_exp[gm] : 0;
 #pragma unroll
-          for (int c0 = 0; c0 < OZ_BN; c0 += 8) {
+          for (int c0 = 0; c0 < OZ_EPI_COLS; c0 += 8) {
             uint32_t r5[8], r6[8];
             tc::tmem_ld8(tmem + lane_base + OZ_EXACT * OZ_BN + c0, r5);
             tc::tmem_ld8(tmem + lane_base + (OZ_EXACT + 1) * OZ_BN + c0, r6);
             tc::tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              const int gn = n0 + c0 + j;
+              const int gn = n0 + cbase + c0 + j;
               if (gm < P.M && gn < P.N && gn < S.nrows_b) {
                 double v = (double)sums[c0 + j] * 3.7252902984619141e-09 /* 2^-28 */ +
                            ((double)__uint_as_float(r5[j]) + (double)__uint_as_float(r6[j]));
@@ -369,8 +373,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
     if (nseg == 0 && !P.accumulate && gm < P.M) {
       // no segment reaches this tile: its block of T is zero
-      for (int j = 0; j < OZ_BN; ++j) {
-        const int gn = n0 + j;
+      for (int j = 0; j < OZ_EPI_COLS; ++j) {
+        const int gn = n0 + cbase + j;
         if (gn < P.N) Tp[(long long)gm * P.ldt + gn] = 0.0;
       }
     }

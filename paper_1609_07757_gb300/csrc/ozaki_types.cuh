@@ -13,8 +13,10 @@ constexpr int OZ_BM = 128;         // rows of A per tile
 constexpr int OZ_BN = 64;          // rows of B per tile
 constexpr int OZ_BK = 16;          // K per stage (one MMA)
 constexpr int OZ_STAGES = 4;
-constexpr int OZ_CHUNK = 256;      // K per exact flush
-constexpr int OZ_THREADS = 192;   // warp 0 loads (TMA), warp 1 issues MMAs, warps 2-5 drain TMEM
+constexpr int OZ_CHUNK = 512;      // K per exact flush
+constexpr int OZ_EPI_WARPS = 4;    // one per TMEM lane quarter (8 measured no faster)
+constexpr int OZ_EPI_COLS = OZ_BN / (OZ_EPI_WARPS / 4);
+constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;  // warp 0 loads (TMA), warp 1 issues MMAs, the rest drain TMEM
 constexpr int OZ_A_SLICE_BYTES = OZ_BM * OZ_BK * 2;   // 4096
 constexpr int OZ_B_SLICE_BYTES = OZ_BN * OZ_BK * 2;   // 2048
 constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_SLICE_BYTES + OZ_B_SLICE_BYTES);
