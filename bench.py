@@ -9,6 +9,11 @@ integral units and in-space determinant pairs (counted exactly at set-up).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload fci_n60] [--tau 1e-14] [--precision 64|32]
+                  [--mixed-workload fci_n100|none] [--mixed-roots 3]
+
+Beside the sigma line (rank 0, one GPU) it runs the precision form: FP32-mixed
+and plain FP64 Davidson for the lowest roots of --mixed-workload, with the
+energies' difference, iteration counts and the speedup ("mixed_precision").
 
 Under torchrun (N > 1) every rank runs an independent replica of the
 workload (the sigma step has no data-parallel exchange at one problem per
@@ -232,13 +237,19 @@ def run_ours(args, wl, ws, rank, local):
 
     # roofline of the dominant kernel (opposite-spin contraction)
     gemm_ms = st["phase_ms"]["opposite_gemm"] / max(1, st["timed_calls"])
-    tc = args.precision == 64 and st.get("fp64_tc", 0) == 1
-    if tc:
+    tc = st.get("fp64_tc" if args.precision == 64 else "fp32_tc", 0) == 1
+    if tc and args.precision == 64:
         # tensor-core kernel: bf16 MMA flops it issues (28 exact slice products)
         flops = st["opposite_tc_bf16_flops"]
         peak, peak_src = bf16_peak()
         bound, kname, kkey = "tensor", "k_oz_gemm (tcgen05, FP64-accurate opposite-spin contraction)", \
             "k_oz_gemm_%s" % args.workload
+    elif tc:
+        # FP32 form: 6 of the 9 products of three bf16 terms per operand
+        flops = st["opposite_tc_bf16_flops"] * 6.0 / 28.0
+        peak, peak_src = bf16_peak()
+        bound, kname, kkey = "tensor", "k_tc32_gemm (tcgen05, FP32-accurate opposite-spin contraction)", \
+            "k_tc32_gemm_%s" % args.workload
     else:
         flops = st["opposite_gemm_flops"]
         peak = FP64_PEAK_TFLOPS if args.precision == 64 else FP32_PEAK_TFLOPS
@@ -267,7 +278,7 @@ def run_ours(args, wl, ws, rank, local):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": ("f64 (tcgen05 bf16 exact slices, int64/f64 accumulation)" if tc else "f64")
-        if args.precision == 64 else "f32",
+        if args.precision == 64 else ("f32 (tcgen05, three bf16 terms, f32 accumulation)" if tc else "f32"),
         "data": "synthetic (seeded integrals shaped like the paper's Be-in-a-box sets)",
         "config": {"workload": args.workload, "norb": wl["n"], "nalpha": wl["na"], "nbeta": wl["nb"],
                    "max_excitation": wl["kmax"], "ndet": ndet, "tau": tau, "nvec": 1,
@@ -294,6 +305,52 @@ def run_ours(args, wl, ws, rank, local):
     # kernel launches of the library inside the timed region (counted by the library)
     line["gpu_launches"] = st.get("kernel_launches")
     return line
+
+
+def run_precision_form(name, nroots=3, tol=1e-8):
+    """FP32-mixed against plain FP64 Davidson on one workload: lowest roots, time,
+    iterations (FP32 phase), and |dE| between the two.  Each precision first runs
+    one untimed sigma so that one-time operand preparation is not timed."""
+    import numpy as np
+    import torch
+
+    from paper_1609_07757_gb300 import _lib as L
+    from paper_1609_07757_gb300.synthetic import make_integrals, unit_vector
+
+    wl = WORKLOADS[name]
+    h1, eri = make_integrals(wl["n"], wl["seed"], ell=wl["ell"], nchol=wl["nchol"], box=wl["box"])
+    L.iscsi_init(wl["n"], wl["na"], wl["nb"], wl["kmax"], h1, eri, wl["tau"])
+    ndet = L.iscsi_ndet()
+    c = torch.tensor(unit_vector(ndet, 5), dtype=torch.float64, device="cuda")
+    s = torch.empty_like(c)
+    out = {"workload": name, "ndet": ndet, "nroots": nroots, "tol": tol}
+    res = {}
+    for prec in (64, 32):
+        L.iscsi_set_option("precision", prec)
+        L.iscsi_sigma(c, s, 1)
+        torch.cuda.synchronize()
+        vecs = torch.zeros((nroots, ndet), dtype=torch.float64, device="cuda")
+        t0 = time.time()
+        st, e = L.iscsi_davidson(nroots, tol, vecs)
+        wall = time.time() - t0
+        stt = L.iscsi_stats()
+        # FP64 residual of the returned vectors (one FP64 sigma)
+        L.iscsi_set_option("precision", 64)
+        w = torch.empty_like(vecs)
+        L.iscsi_sigma(vecs, w, nroots)
+        torch.cuda.synchronize()
+        et = torch.tensor(np.asarray(e), dtype=torch.float64, device="cuda")[:, None]
+        rnorm = torch.linalg.norm(w - et * vecs, dim=1).cpu().numpy()
+        res[prec] = {"status": int(st), "energies": [float(x) for x in e], "iters": stt["davidson_iters"],
+                     "fp32_iters": stt.get("davidson_fp32_iters", 0), "ms": round(stt["davidson_ms"], 3),
+                     "wall_s": round(wall, 3), "residual_norms": [float("%.3e" % r) for r in rnorm]}
+    L.iscsi_set_option("precision", 64)
+    L.iscsi_finalize()
+    de = max(abs(a - b) for a, b in zip(res[32]["energies"], res[64]["energies"]))
+    out.update({"fp64": res[64], "mixed": res[32], "max_abs_dE_mixed_vs_fp64": float("%.3e" % de),
+                "within_1e-9": de <= 1e-9,
+                "speedup_mixed_vs_fp64": round(res[64]["ms"] / res[32]["ms"], 3) if res[32]["ms"] > 0 else None})
+    return out
 
 
 def cpu_baseline(wl, tau, target_s=15.0, steps=1):
@@ -366,6 +423,9 @@ def main():
     ap.add_argument("--tau", type=float, default=None)
     ap.add_argument("--precision", type=int, default=64, choices=[32, 64])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mixed-workload", default="fci_n100", choices=sorted(WORKLOADS) + ["none"],
+                    help="workload of the FP32-mixed vs FP64 Davidson comparison added to the line")
+    ap.add_argument("--mixed-roots", type=int, default=3)
     ap.add_argument("--updates", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     ws, rank, local = dist_env()
@@ -393,6 +453,9 @@ def main():
             print(json.dumps(line))
         return
     line = run_ours(args, wl, ws, rank, local)
+    if rank == 0 and ws == 1 and args.mixed_workload != "none":
+        # the precision form: FP32-mixed vs FP64 Davidson, |dE| and speedup (untimed by the contract)
+        line["mixed_precision"] = run_precision_form(args.mixed_workload, args.mixed_roots)
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
             tau = args.tau if args.tau is not None else wl["tau"]

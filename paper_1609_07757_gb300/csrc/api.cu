@@ -229,6 +229,8 @@ iscsi_status iscsi_set_option(const char* key, double value) {
     o.fp64_tc = value != 0;
   } else if (k == "samespin_tc") {
     o.samespin_tc = value != 0;
+  } else if (k == "fp32_tc") {
+    o.fp32_tc = value != 0;
   } else if (k == "phase_timing") {
     o.phase_timing = value != 0;
     Context* ctx = current();
@@ -271,13 +273,15 @@ iscsi_status iscsi_stats(char* json, int len) {
       "\"init_ms\": %.6f, \"timed_calls\": %d, \"phase_ms\": {\"lift\": %.6f, \"opposite_gemm\": %.6f, "
       "\"fold\": %.6f, \"samespin_gemm\": %.6f}, \"davidson_iters\": %d, \"davidson_ms\": %.6f, "
       "\"opposite_gemm_flops\": %.17g, \"samespin_gemm_flops\": %.17g, \"opposite_tc_bf16_flops\": %.17g, "
-      "\"fp64_tc\": %d, \"samespin_tc\": %d, \"kernel_launches\": %lld}",
+      "\"fp64_tc\": %d, \"samespin_tc\": %d, \"fp32_tc\": %d, \"davidson_fp32_iters\": %d, "
+      "\"kernel_launches\": %lld}",
       ctx->n, ctx->na, ctx->nb, ctx->kmax, ctx->tau, ctx->ndet, ctx->sp[0].count, ctx->sp[1].count,
       ctx->units_onebody_total, ctx->units_samespin_total, ctx->units_opposite_total, ctx->units_opposite,
       ctx->units_onebody, ctx->units_samespin, ctx->updates_onebody, ctx->updates_samespin,
       ctx->updates_opposite, upd, ctx->init_ms, ncalls, phase_ms[0], phase_ms[1], phase_ms[2], phase_ms[3],
       ctx->last_davidson_iters, ctx->last_davidson_ms, ctx_gemm_flops(*ctx, 0), ctx_gemm_flops(*ctx, 1),
-      ctx_gemm_flops(*ctx, 2), options().fp64_tc, options().samespin_tc, g_launch_count);
+      ctx_gemm_flops(*ctx, 2), options().fp64_tc, options().samespin_tc, options().fp32_tc,
+      ctx->last_davidson_fp32_iters, g_launch_count);
   std::strncpy(json, buf, len - 1);
   json[len - 1] = 0;
   return ISCSI_OK;

@@ -340,6 +340,7 @@ int davidson_run(Context& ctx, int nroots, double tol, double* energies, double*
   }
 
   bool mixed = (opt.precision == 32);
+  ctx.last_davidson_fp32_iters = 0;
   int prec = mixed ? 32 : 64;
   int m = k;
   ISCSI_TRY(sigma_run(ctx, V, W, k, prec));
@@ -414,6 +415,7 @@ int davidson_run(Context& ctx, int nroots, double tol, double* energies, double*
         ISCSI_TRY(normalise(V + (size_t)j * N, 1, nrm));
       }
       prec = 64;
+      ctx.last_davidson_fp32_iters = iter;
       m = k;
       ISCSI_TRY(sigma_run(ctx, V, W, k, prec));
       ISCSI_TRY(update_S(0, m));

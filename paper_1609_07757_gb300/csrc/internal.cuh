@@ -194,6 +194,12 @@ struct Context {
   long long oz_cs_elems = 0;
   bool oz_m_ready = false;
   int pl_ss_tc = -1;  // same-spin routing the FP64 grouped-GEMM list was built for
+  // FP32 form of the tensor-core contractions (three bf16 terms per element)
+  OzJob t3_ab, t3_ss;
+  DevBuf t3_gs, t3_bs, t3_mas, t3_mbs, t3_cs;
+  long long t3_bs_elems = 0, t3_cs_elems = 0;
+  bool t3_m_ready = false;
+  int pl_ss_tc32 = -1;  // same-spin routing the FP32 grouped-GEMM list was built for
   // statistics
   double updates_onebody = 0, updates_samespin = 0, updates_opposite = 0;
   long long units_onebody = 0, units_samespin = 0, units_opposite = 0;
@@ -206,6 +212,7 @@ struct Context {
   std::vector<cudaEvent_t> tev;  // [kMaxTimed][kPhases + 1]
   int ntimed = 0;
   int last_davidson_iters = 0;
+  int last_davidson_fp32_iters = 0;  // iterations of the FP32 phase (mixed precision)
   double last_davidson_ms = 0;
   // Davidson buffers
   DevBuf dv_V, dv_W, dv_tmp, dv_small;
@@ -225,6 +232,7 @@ struct Options {
   int phase_timing = 0;
   int fp64_tc = 1;      // FP64 opposite-spin contraction on the tensor cores (exact bf16 slices)
   int samespin_tc = 1;  // same for the same-spin blocks large enough for a 128 x 64 tile
+  int fp32_tc = 1;      // FP32 form: contractions on the tensor cores (three bf16 terms, FP32 accumulation)
 };
 
 Options& options();
@@ -248,6 +256,10 @@ int opposite_tc_gemm(Context& ctx);                                             
 bool samespin_block_on_tc(const Context& ctx, int a);
 bool samespin_tc_active(const Context& ctx);
 int samespin_tc(Context& ctx, const double* c, double* sigma, int nvec);           // sigma += same-spin
+int opposite_tc32_operands(Context& ctx, const float* c, float* ttw, int nvec);   // FP32 form
+int opposite_tc32_gemm(Context& ctx);
+bool samespin_tc32_active(const Context& ctx);
+int samespin_tc32(Context& ctx, const float* c, float* sigma, int nvec);
 int tc_check(Context& ctx);
 
 // allocation-free single-vector FP64 sigma on a static device array (sigma.cu)

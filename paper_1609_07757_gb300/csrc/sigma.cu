@@ -541,7 +541,8 @@ static int build_problems(Context& ctx, int nvec, const T* G, const T* Ma, const
       int rows = SA.level_start[a + 1] - SA.level_start[a];
       int nba = (int)ctx.nb_allowed_lvl[a];
       if (rows == 0 || nba == 0) continue;
-      if (std::is_same<T, double>::value && ctx.pl_ss_tc == 1 && samespin_block_on_tc(ctx, a)) continue;
+      const int routed = std::is_same<T, double>::value ? ctx.pl_ss_tc : ctx.pl_ss_tc32;
+      if (routed == 1 && samespin_block_on_tc(ctx, a)) continue;
       long long obase = ctx.off_h[SA.level_start[a]];
       Problem<T> p;
       p.c = (long long)v * ctx.ndet + obase;
@@ -678,9 +679,11 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
   T* ctw = ctx.ct.as<T>();
   T* ttw = ctx.tt.as<T>();
   // problem lists depend on nvec, the workspaces and the same-spin routing, not on the vectors
-  int ss_tc = (std::is_same<T, double>::value && samespin_tc_active(ctx)) ? 1 : 0;
-  if (std::is_same<T, double>::value && ctx.pl_ss_tc != ss_tc) {
-    ctx.pl_ss_tc = ss_tc;
+  constexpr bool f64 = std::is_same<T, double>::value;
+  int ss_tc = (f64 ? samespin_tc_active(ctx) : samespin_tc32_active(ctx)) ? 1 : 0;
+  int& routed = f64 ? ctx.pl_ss_tc : ctx.pl_ss_tc32;
+  if (routed != ss_tc) {
+    routed = ss_tc;
     pl_nvec = 0;
   }
   if (pl_nvec != nvec) {
@@ -689,13 +692,19 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
   }
   int call = ctx.ntimed;
   ISCSI_TRY(timing_event(ctx, call, 0, st));
-  bool tc_path = std::is_same<T, double>::value && options().fp64_tc;
+  bool tc_path = f64 ? options().fp64_tc : options().fp32_tc;
   if (ctx.have_ab && tc_path) {
-    // FP64 opposite-spin contraction on the tensor cores (lift + slice, GEMM)
+    // opposite-spin contraction on the tensor cores (lift + slice, GEMM)
     ClassTable ct = class_table(ctx, nvec);
-    ISCSI_TRY(opposite_tc_operands(ctx, reinterpret_cast<const double*>(c_in), reinterpret_cast<double*>(ttw), nvec));
-    ISCSI_TRY(timing_event(ctx, call, 1, st));
-    ISCSI_TRY(opposite_tc_gemm(ctx));
+    if (f64) {
+      ISCSI_TRY(opposite_tc_operands(ctx, reinterpret_cast<const double*>(c_in), reinterpret_cast<double*>(ttw), nvec));
+      ISCSI_TRY(timing_event(ctx, call, 1, st));
+      ISCSI_TRY(opposite_tc_gemm(ctx));
+    } else {
+      ISCSI_TRY(opposite_tc32_operands(ctx, reinterpret_cast<const float*>(c_in), reinterpret_cast<float*>(ttw), nvec));
+      ISCSI_TRY(timing_event(ctx, call, 1, st));
+      ISCSI_TRY(opposite_tc32_gemm(ctx));
+    }
     ISCSI_TRY(timing_event(ctx, call, 2, st));
     k_fold<T><<<ctx.sp[0].count, 256, 0, st>>>(ct, nvec, ctx.n, ctx.na, ctx.nb, ctx.sp[1].nhole,
                                                ctx.sp[0].dec.as<int>(), ctx.sp[1].dec.as<int>(),
@@ -729,8 +738,10 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
     ISCSI_TRY(timing_event(ctx, call, 3, st));
   }
   ISCSI_TRY(launch_grouped<T>(ss, c, sigma, st));
-  if (ss_tc)
+  if (ss_tc && f64)
     ISCSI_TRY(samespin_tc(ctx, reinterpret_cast<const double*>(c), reinterpret_cast<double*>(sigma), nvec));
+  else if (ss_tc)
+    ISCSI_TRY(samespin_tc32(ctx, reinterpret_cast<const float*>(c), reinterpret_cast<float*>(sigma), nvec));
   ISCSI_TRY(timing_event(ctx, call, 4, st));
   if (options().phase_timing && call < Context::kMaxTimed) ctx.ntimed++;
   (void)s_out;

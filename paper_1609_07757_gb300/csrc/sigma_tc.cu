@@ -14,6 +14,10 @@
 // as one multi-segment product per block; blocks with at most 16 rows or
 // columns stay on the FP64 thin kernels of sigma.cu.
 // G's, M_alpha's and M_beta's slices are built once per context (first use).
+//
+// The FP32 form (tc32.cuh) runs the same two contractions with three bf16
+// terms per element and FP32 accumulation (k_tc32_gemm): no exponents, no
+// exact levels; its operands come from the FP32 copy of the CI vector.
 #include <algorithm>
 #include <climits>
 #include <cstring>
@@ -21,6 +25,7 @@
 
 #include "internal.cuh"
 #include "ozaki.cuh"
+#include "tc32.cuh"
 #include "tma_map.h"
 
 namespace iscsi {
@@ -46,23 +51,23 @@ struct TcTable {
 
 static inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-__device__ __forceinline__ double tc_gather(const TcClass& C, int nvec, int col, int k, int n, int nholeA,
-                                            int nholeB, const int* __restrict__ pair_of,
-                                            const int* __restrict__ hp_inv, const int* __restrict__ liftA,
-                                            const int* __restrict__ liftB, const int8_t* __restrict__ alevel,
-                                            const int* __restrict__ nballow, const long long* __restrict__ off,
-                                            const double* __restrict__ c, long long ndet) {
-  if (k >= C.krows) return 0.0;
+template <typename V>
+__device__ __forceinline__ V tc_gather(const TcClass& C, int nvec, int col, int k, int n, int nholeA, int nholeB,
+                                       const int* __restrict__ pair_of, const int* __restrict__ hp_inv,
+                                       const int* __restrict__ liftA, const int* __restrict__ liftB,
+                                       const int8_t* __restrict__ alevel, const int* __restrict__ nballow,
+                                       const long long* __restrict__ off, const V* __restrict__ c, long long ndet) {
+  if (k >= C.krows) return (V)0;
   int hp = col / nvec, v = col % nvec;
   int xy = hp_inv[C.hp_start + hp];
   int X = xy / nholeB, Y = xy % nholeB;
   int qs = pair_of[k];
   int q = qs / n, s = qs % n;
   int ea = liftA[q * nholeA + X], eb = liftB[s * nholeB + Y];
-  if (ea < 0 || eb < 0) return 0.0;
+  if (ea < 0 || eb < 0) return (V)0;
   int Ap = ea >> 1, Bp = eb >> 1;
-  if (Bp >= nballow[alevel[Ap]]) return 0.0;
-  double x = c[(long long)v * ndet + off[Ap] + Bp];
+  if (Bp >= nballow[alevel[Ap]]) return (V)0;
+  V x = c[(long long)v * ndet + off[Ap] + Bp];
   return ((ea ^ eb) & 1) ? -x : x;
 }
 
@@ -79,8 +84,8 @@ __global__ void k_oz_col_exp(TcTable tt, int n, int nholeA, int nholeB, const in
   const TcClass& C = tt.c[cl];
   long long local = t - tt.start[cl];
   int col = (int)(local / C.kpad), k = (int)(local % C.kpad);
-  double x = tc_gather(C, tt.nvec, col, k, n, nholeA, nholeB, pair_of, hp_inv, liftA, liftB, alevel, nballow, off,
-                       c, ndet);
+  double x = tc_gather<double>(C, tt.nvec, col, k, n, nholeA, nholeB, pair_of, hp_inv, liftA, liftB, alevel,
+                               nballow, off, c, ndet);
   int e = x != 0.0 ? oz_exp_field(x) - 1022 : INT_MIN;  // frexp exponent of |x|
   // one atomic per (warp, column): lanes of the same column reduce together
   int key = (int)(C.exp_off + col);
@@ -112,17 +117,36 @@ __global__ void k_oz_lift_slice(TcTable tt, int n, int nholeA, int nholeB, const
   const TcClass& C = tt.c[cl];
   long long local = t - tt.start[cl];
   int col = (int)(local / C.kpad), k = (int)(local % C.kpad);
-  double x = tc_gather(C, tt.nvec, col, k, n, nholeA, nholeB, pair_of, hp_inv, liftA, liftB, alevel, nballow, off,
-                       c, ndet);
+  double x = tc_gather<double>(C, tt.nvec, col, k, n, nholeA, nholeB, pair_of, hp_inv, liftA, liftB, alevel,
+                               nballow, off, c, ndet);
   int a[OZ_S];
   oz_digits(x, exps[C.exp_off + col], a);
   oz_store_digits(a, bs + C.bs_off + (long long)col * C.kpad + k, (long long)C.npad * C.kpad);
+}
+
+// FP32 form: Ct^T gathered from the FP32 vector and split into three bf16 terms
+__global__ void k_t3_lift(TcTable tt, int n, int nholeA, int nholeB, const int* __restrict__ pair_of,
+                          const int* __restrict__ hp_inv, const int* __restrict__ liftA, const int* __restrict__ liftB,
+                          const int8_t* __restrict__ alevel, const int* __restrict__ nballow,
+                          const long long* __restrict__ off, const float* __restrict__ c, long long ndet,
+                          __nv_bfloat16* __restrict__ bs) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= tt.start[tt.nclass]) return;
+  int cl = 0;
+  while (t >= tt.start[cl + 1]) ++cl;
+  const TcClass& C = tt.c[cl];
+  long long local = t - tt.start[cl];
+  int col = (int)(local / C.kpad), k = (int)(local % C.kpad);
+  float x = tc_gather<float>(C, tt.nvec, col, k, n, nholeA, nholeB, pair_of, hp_inv, liftA, liftB, alevel, nballow,
+                             off, c, ndet);
+  t3_store_terms<float>(x, bs + C.bs_off + (long long)col * C.kpad + k, (long long)C.npad * C.kpad);
 }
 
 static int tc_attr() {
   static bool done = false;
   if (!done) {
     ISCSI_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES));
+    ISCSI_CUDA(cudaFuncSetAttribute(k_tc32_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, T3_SMEM_BYTES));
     done = true;
   }
   return kOk;
@@ -171,7 +195,7 @@ struct SliceArray {
 
 // segment of a job: block (a_row0, a_k0) of A times block (b_row0, b_k0) of B
 static int add_seg(OzJob& job, const SliceArray& A, int a_row0, int a_k0, const int* a_exp, const SliceArray& B,
-                   int b_row0, int b_k0, const int* b_exp, int K, int nrows_b) {
+                   int b_row0, int b_k0, const int* b_exp, int K, int nrows_b, int nslice = OZ_S) {
   OzSeg sg;
   sg.a_exp = a_exp;
   sg.b_exp = b_exp;
@@ -183,8 +207,8 @@ static int add_seg(OzJob& job, const SliceArray& A, int a_row0, int a_k0, const 
   sg.nrows_b = nrows_b;
   OzMaps m;
   std::memset(&m, 0, sizeof(m));
-  if (oz_encode_map(&m.a, A.base, A.ld, A.rows, OZ_S, A.slice, OZ_BM) ||
-      oz_encode_map(&m.b, B.base, B.ld, B.rows, OZ_S, B.slice, OZ_BN)) {
+  if (oz_encode_map(&m.a, A.base, A.ld, A.rows, nslice, A.slice, OZ_BM) ||
+      oz_encode_map(&m.b, B.base, B.ld, B.rows, nslice, B.slice, OZ_BN)) {
     set_error("tensor-core sigma: TMA descriptor rejected");
     return kErrCuda;
   }
@@ -232,7 +256,7 @@ static int add_tiles(std::vector<OzProblem>& probs) {
 // ---------------------------------------------------------------------------
 // opposite spin
 
-static TcTable ab_table(const Context& ctx, int nvec, long long* bs_elems, long long* exp_elems) {
+static TcTable ab_table(const Context& ctx, int nvec, long long* bs_elems, long long* exp_elems, int nslice = OZ_S) {
   TcTable tt;
   std::memset(&tt, 0, sizeof(tt));
   tt.nvec = nvec;
@@ -253,7 +277,7 @@ static TcTable ab_table(const Context& ctx, int nvec, long long* bs_elems, long 
     tt.start[tt.nclass] = flat;
     tt.c[tt.nclass++] = C;
     flat += C.tot;
-    bs += (long long)OZ_S * C.npad * C.kpad;
+    bs += (long long)nslice * C.npad * C.kpad;
     ex += C.ncols;
   }
   tt.start[tt.nclass] = flat;
@@ -405,7 +429,7 @@ struct SsBlock {
   int bt_rows, bt_ld, ca_rows, ca_ld;
 };
 
-static std::vector<SsBlock> ss_blocks(const Context& ctx, long long* elems, long long* exps) {
+static std::vector<SsBlock> ss_blocks(const Context& ctx, long long* elems, long long* exps, int nslice = OZ_S) {
   std::vector<SsBlock> out;
   const SpinSpace& SA = ctx.sp[0];
   long long e = 0, x = 0;
@@ -421,14 +445,14 @@ static std::vector<SsBlock> ss_blocks(const Context& ctx, long long* elems, long
     b.bt_rows = round_up(b.nba, OZ_BN);
     b.bt_ld = round_up(b.rows, OZ_BK);
     b.bt_off = e;
-    e += (long long)OZ_S * b.bt_rows * b.bt_ld;
+    e += (long long)nslice * b.bt_rows * b.bt_ld;
     b.bt_exp = x;
     x += b.bt_rows;
     // C_a (beta part operand): rows = alpha strings of the block, K = beta strings
     b.ca_rows = round_up(b.rows, OZ_BM);
     b.ca_ld = round_up(b.nba, OZ_BK);
     b.ca_off = e;
-    e += (long long)OZ_S * b.ca_rows * b.ca_ld;
+    e += (long long)nslice * b.ca_rows * b.ca_ld;
     b.ca_exp = x;
     x += b.ca_rows;
     out.push_back(b);
@@ -517,6 +541,214 @@ int samespin_tc(Context& ctx, const double* c, double* sigma, int nvec) {
     }
   (void)SB;
   return launch_job(ctx, ctx.oz_ss, sigma, st);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 form: three bf16 terms per element, FP32 accumulation (tc32.cuh)
+
+template <typename V>
+static int t3_slice_matrix(const V* X, int rows, int cols, long long ld, int trans, const int* colmap, int ldo,
+                           int rows_pad, __nv_bfloat16* out, cudaStream_t st) {
+  long long slice = (long long)rows_pad * ldo;
+  if (slice > 0) {
+    k_t3_slice<V><<<launch_blocks(slice, 256), 256, 0, st>>>(X, rows, cols, ld, trans, colmap, out, slice, ldo,
+                                                             rows_pad); ISCSI_COUNT_LAUNCH();
+  }
+  ISCSI_CUDA(cudaGetLastError());
+  return kOk;
+}
+
+static int t3_launch(Context& ctx, const OzJob& job, float* tbase, cudaStream_t st) {
+  if (job.tiles == 0) return kOk;
+  k_tc32_gemm<<<job.tiles, T3_THREADS, T3_SMEM_BYTES, st>>>(job.d_probs.as<OzProblem>(), (int)job.probs.size(),
+                                                            job.d_segs.as<OzSeg>(), job.d_maps.as<OzMaps>(), tbase,
+                                                            ctx.oz_err.as<int>()); ISCSI_COUNT_LAUNCH();
+  ISCSI_CUDA(cudaGetLastError());
+  return kOk;
+}
+
+static int t3_prepare_g(Context& ctx) {
+  if (ctx.t3_gs.p) return kOk;
+  ISCSI_TRY(tc_attr());
+  ISCSI_TRY(tc_err_buf(ctx));
+  int np = ctx.npairs;
+  ctx.oz_mpad = round_up(np, OZ_BM);
+  ctx.oz_kpad = round_up(np, OZ_BK);
+  long long slice = (long long)ctx.oz_mpad * ctx.oz_kpad;
+  ISCSI_TRY(ctx.t3_gs.alloc(sizeof(__nv_bfloat16) * slice * T3_S));
+  return t3_slice_matrix<double>(ctx.G64.as<double>(), np, np, np, 0, nullptr, ctx.oz_kpad, ctx.oz_mpad,
+                                 ctx.t3_gs.as<__nv_bfloat16>(), stream());
+}
+
+int opposite_tc32_operands(Context& ctx, const float* c, float* ttw, int nvec) {
+  cudaStream_t st = stream();
+  ISCSI_TRY(t3_prepare_g(ctx));
+  long long bs_elems = 0, exp_elems = 0;
+  TcTable tt = ab_table(ctx, nvec, &bs_elems, &exp_elems, T3_S);
+  if (tt.nclass == 0) return kOk;
+  bool rebuild = ctx.t3_ab.nvec != nvec || ctx.t3_ab.tbase != (const void*)ttw;
+  if (ctx.t3_bs_elems < bs_elems) {
+    ISCSI_TRY(ctx.t3_bs.alloc(sizeof(__nv_bfloat16) * bs_elems));
+    ctx.t3_bs_elems = bs_elems;
+    rebuild = true;
+  }
+  if (rebuild) {
+    ISCSI_CUDA(cudaMemsetAsync(ctx.t3_bs.p, 0, sizeof(__nv_bfloat16) * ctx.t3_bs_elems, st));
+    OzJob& job = ctx.t3_ab;
+    job.probs.clear();
+    job.segs.clear();
+    job.maps.clear();
+    long long t_off = 0;
+    const SliceArray GA{ctx.t3_gs.as<__nv_bfloat16>(), ctx.oz_kpad, ctx.oz_mpad, (long long)ctx.oz_mpad * ctx.oz_kpad};
+    for (int i = 0; i < tt.nclass; ++i) {
+      const TcClass& C = tt.c[i];
+      const SliceArray CB{ctx.t3_bs.as<__nv_bfloat16>() + C.bs_off, C.kpad, C.npad, (long long)C.npad * C.kpad};
+      OzProblem P;
+      std::memset(&P, 0, sizeof(P));
+      P.t = (long long)reinterpret_cast<uintptr_t>(ttw + t_off);
+      P.ldt = C.ncols;
+      P.M = C.mrows;
+      P.N = C.ncols;
+      P.seg_begin = (int)job.segs.size();
+      P.seg_count = 1;
+      t_off += (long long)C.mrows * C.ncols;
+      ISCSI_TRY(add_seg(job, GA, 0, 0, nullptr, CB, 0, 0, nullptr, C.kpad, C.ncols, T3_S));
+      job.probs.push_back(P);
+    }
+    job.tiles = add_tiles(job.probs);
+    ISCSI_TRY(upload_job(job, st));
+    job.nvec = nvec;
+    job.tbase = ttw;
+  }
+  const SpinSpace& SA = ctx.sp[0];
+  const SpinSpace& SB = ctx.sp[1];
+  long long flat = tt.start[tt.nclass];
+  k_t3_lift<<<launch_blocks(flat, 256), 256, 0, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_of.as<int>(),
+                                                       ctx.hp_inv.as<int>(), SA.lift.as<int>(), SB.lift.as<int>(),
+                                                       SA.level.as<int8_t>(), ctx.nballow.as<int>(),
+                                                       ctx.off.as<long long>(), c, ctx.ndet,
+                                                       ctx.t3_bs.as<__nv_bfloat16>()); ISCSI_COUNT_LAUNCH();
+  ISCSI_CUDA(cudaGetLastError());
+  return kOk;
+}
+
+int opposite_tc32_gemm(Context& ctx) { return t3_launch(ctx, ctx.t3_ab, nullptr, stream()); }
+
+bool samespin_tc32_active(const Context& ctx) {
+  if (!options().fp32_tc || !options().samespin_tc) return false;
+  for (int a = 0; a <= ctx.sp[0].maxlevel; ++a)
+    if (samespin_block_on_tc(ctx, a)) return true;
+  return false;
+}
+
+static int t3_prepare_m(Context& ctx) {
+  if (ctx.t3_m_ready) return kOk;
+  cudaStream_t st = stream();
+  ISCSI_TRY(tc_attr());
+  ISCSI_TRY(tc_err_buf(ctx));
+  const SpinSpace& SA = ctx.sp[0];
+  const SpinSpace& SB = ctx.sp[1];
+  int nl = SA.maxlevel + 1;
+  // the same level-padded column layout as the FP64 slices
+  ctx.oz_kbase.assign(nl + 1, 0);
+  for (int a = 0; a < nl; ++a) ctx.oz_kbase[a + 1] = ctx.oz_kbase[a] + round_up(SA.level_start[a + 1] - SA.level_start[a], OZ_BK);
+  if (ctx.na > 0 && ctx.M64[0].p) {
+    int kcols = ctx.oz_kbase[nl];
+    std::vector<int> colmap(kcols, -1);
+    for (int a = 0; a < nl; ++a)
+      for (int i = SA.level_start[a]; i < SA.level_start[a + 1]; ++i) colmap[ctx.oz_kbase[a] + i - SA.level_start[a]] = i;
+    DevBuf dmap;
+    ISCSI_TRY(dmap.alloc(sizeof(int) * kcols));
+    ISCSI_CUDA(cudaMemcpyAsync(dmap.p, colmap.data(), sizeof(int) * kcols, cudaMemcpyHostToDevice, st));
+    ctx.oz_ma_rows = SA.count + OZ_BM;
+    ctx.oz_ma_ld = kcols;
+    ISCSI_TRY(ctx.t3_mas.alloc(sizeof(__nv_bfloat16) * T3_S * (size_t)ctx.oz_ma_rows * kcols));
+    ISCSI_TRY(t3_slice_matrix<double>(ctx.M64[0].as<double>(), SA.count, SA.count, SA.count, 0, dmap.as<int>(), kcols,
+                                      ctx.oz_ma_rows, ctx.t3_mas.as<__nv_bfloat16>(), st));
+    ISCSI_CUDA(cudaStreamSynchronize(st));  // colmap lives until here
+  }
+  if (ctx.nb > 0) {
+    const double* Mb = ctx.beta_alias ? ctx.M64[0].as<double>() : ctx.M64[1].as<double>();
+    int trans = ctx.beta_alias ? 0 : 1;
+    ctx.oz_mb_rows = round_up(SB.count, OZ_BN);
+    ctx.oz_mb_ld = round_up(SB.count, OZ_BK);
+    ISCSI_TRY(ctx.t3_mbs.alloc(sizeof(__nv_bfloat16) * T3_S * (size_t)ctx.oz_mb_rows * ctx.oz_mb_ld));
+    ISCSI_TRY(t3_slice_matrix<double>(Mb, SB.count, SB.count, SB.count, trans, nullptr, ctx.oz_mb_ld, ctx.oz_mb_rows,
+                                      ctx.t3_mbs.as<__nv_bfloat16>(), st));
+  }
+  ctx.t3_m_ready = true;
+  return kOk;
+}
+
+int samespin_tc32(Context& ctx, const float* c, float* sigma, int nvec) {
+  cudaStream_t st = stream();
+  ISCSI_TRY(t3_prepare_m(ctx));
+  long long elems1 = 0, exps1 = 0;
+  std::vector<SsBlock> blocks = ss_blocks(ctx, &elems1, &exps1, T3_S);
+  long long elems = elems1 * nvec;
+  bool rebuild = ctx.t3_ss.nvec != nvec;
+  if (ctx.t3_cs_elems < elems) {
+    ISCSI_TRY(ctx.t3_cs.alloc(sizeof(__nv_bfloat16) * elems));
+    ctx.t3_cs_elems = elems;
+    rebuild = true;
+  }
+  __nv_bfloat16* cs = ctx.t3_cs.as<__nv_bfloat16>();
+  if (rebuild) {
+    ISCSI_CUDA(cudaMemsetAsync(ctx.t3_cs.p, 0, sizeof(__nv_bfloat16) * ctx.t3_cs_elems, st));
+    OzJob& job = ctx.t3_ss;
+    job.probs.clear();
+    job.segs.clear();
+    job.maps.clear();
+    const SliceArray MA{ctx.t3_mas.as<__nv_bfloat16>(), ctx.oz_ma_ld, ctx.oz_ma_rows,
+                        (long long)ctx.oz_ma_rows * ctx.oz_ma_ld};
+    const SliceArray MB{ctx.t3_mbs.as<__nv_bfloat16>(), ctx.oz_mb_ld, ctx.oz_mb_rows,
+                        (long long)ctx.oz_mb_rows * ctx.oz_mb_ld};
+    for (int v = 0; v < nvec; ++v)
+      for (const SsBlock& b : blocks) {
+        if (!samespin_block_on_tc(ctx, b.a)) continue;
+        OzProblem P;
+        std::memset(&P, 0, sizeof(P));
+        P.t = (long long)v * ctx.ndet + b.obase;
+        P.t_rel = 1;
+        P.ldt = b.nba;
+        P.M = b.rows;
+        P.N = b.nba;
+        P.seg_begin = (int)job.segs.size();
+        P.accumulate = 1;
+        if (ctx.na > 0 && ctx.t3_mas.p)
+          for (const SsBlock& b2 : blocks) {
+            if (std::abs(b.a - b2.a) > 2) continue;
+            const SliceArray CT{cs + v * elems1 + b2.bt_off, b2.bt_ld, b2.bt_rows, (long long)b2.bt_rows * b2.bt_ld};
+            ISCSI_TRY(add_seg(job, MA, b.start, ctx.oz_kbase[b2.a], nullptr, CT, 0, 0, nullptr, b2.bt_ld,
+                              std::min(b.nba, b2.nba), T3_S));
+            P.seg_count++;
+          }
+        if (ctx.nb > 0 && ctx.t3_mbs.p) {
+          const SliceArray CA{cs + v * elems1 + b.ca_off, b.ca_ld, b.ca_rows, (long long)b.ca_rows * b.ca_ld};
+          ISCSI_TRY(add_seg(job, CA, 0, 0, nullptr, MB, 0, 0, nullptr, b.ca_ld, b.nba, T3_S));
+          P.seg_count++;
+        }
+        if (P.seg_count > 0) job.probs.push_back(P);
+      }
+    job.tiles = add_tiles(job.probs);
+    ISCSI_TRY(upload_job(job, st));
+    job.nvec = nvec;
+  }
+  for (int v = 0; v < nvec; ++v)
+    for (const SsBlock& b : blocks) {
+      bool used = samespin_block_on_tc(ctx, b.a);
+      for (const SsBlock& b2 : blocks)
+        if (std::abs(b.a - b2.a) <= 2 && samespin_block_on_tc(ctx, b2.a)) used = true;
+      if (!used) continue;
+      const float* X = c + (long long)v * ctx.ndet + b.obase;  // [rows][nba]
+      if (ctx.na > 0)
+        ISCSI_TRY(t3_slice_matrix<float>(X, b.nba, b.rows, b.nba, 1, nullptr, b.bt_ld, b.bt_rows,
+                                         cs + v * elems1 + b.bt_off, st));
+      if (ctx.nb > 0 && samespin_block_on_tc(ctx, b.a))
+        ISCSI_TRY(t3_slice_matrix<float>(X, b.rows, b.nba, b.nba, 0, nullptr, b.ca_ld, b.ca_rows,
+                                         cs + v * elems1 + b.ca_off, st));
+    }
+  return t3_launch(ctx, ctx.t3_ss, sigma, st);
 }
 
 // status of the bounded waits of the tensor-core kernels (synchronises)

@@ -32,6 +32,7 @@ def _fresh_library():
     L.iscsi_set_option("class_mask_lo", 4294967295)
     L.iscsi_set_option("class_mask_hi", 1023)
     L.iscsi_set_option("precision", 64)
+    L.iscsi_set_option("fp32_tc", 1)
     L.iscsi_set_stream(torch.cuda.current_stream())
     yield
     torch.cuda.synchronize()
@@ -39,6 +40,7 @@ def _fresh_library():
     L.iscsi_set_option("class_mask_lo", 4294967295)
     L.iscsi_set_option("class_mask_hi", 1023)
     L.iscsi_set_option("precision", 64)
+    L.iscsi_set_option("fp32_tc", 1)
 
 
 def gpu_sigma(C, nvec=1, precision=64):
@@ -284,3 +286,28 @@ def test_samespin_tensor_core_blocks(n, k, tau):
         assert_close(s_tc[v], s_nat[v], REL64)
         ref = o.sigma_rows(C[v], rows)
         assert np.abs(s_tc[v][rows] - ref).max() <= REL64 * np.abs(s_nat[v]).max()
+
+
+@pytest.mark.parametrize("n,na,nb,k,tau", [(10, 2, 2, 4, 1e-14), (11, 2, 2, 2, 1e-6), (7, 3, 2, 3, 0.0),
+                                           (9, 1, 2, 9, 1e-10), (24, 2, 2, 3, 1e-12), (30, 2, 2, 2, 1e-10)])
+def test_fp32_tensor_core_and_native_paths(n, na, nb, k, tau):
+    # FP32 form: three bf16 terms per element on the tensor cores (default) and
+    # the FP32 FFMA kernels both stay within the FP32 bound of the oracle
+    h1, eri = make_integrals(n, 1300 + n, ell=4.0, nchol=12)
+    L.iscsi_init(n, na, nb, k, h1, eri, tau)
+    nd = L.iscsi_ndet()
+    C = np.stack([unit_vector(nd, 80 + v) for v in range(2)])
+    s64 = gpu_sigma(C, nvec=2).reshape(2, -1)
+    L.iscsi_set_option("fp32_tc", 1)
+    s_tc = gpu_sigma(C, nvec=2, precision=32).reshape(2, -1)
+    L.iscsi_set_option("fp32_tc", 0)
+    s_nat = gpu_sigma(C, nvec=2, precision=32).reshape(2, -1)
+    L.iscsi_set_option("fp32_tc", 1)
+    o = Oracle(n, na, nb, k, tau, h1, eri)
+    rows = np.random.default_rng(2).choice(nd, size=min(nd, 400), replace=False)
+    for v in range(2):
+        ref = o.sigma_rows(C[v], rows)
+        assert np.abs(s64[v][rows] - ref).max() <= REL64 * np.abs(s64[v]).max()
+        for s in (s_tc[v], s_nat[v]):
+            assert np.linalg.norm(s - s64[v]) <= REL32 * np.linalg.norm(s64[v])
+            assert np.abs(s[rows] - ref).max() <= REL32 * np.abs(s64[v]).max()
