@@ -202,12 +202,20 @@ ISCSI_API iscsi_status iscsi_set_stream(void* stream);
  *   "switch_tol"       mixed precision: residual at which FP64 sigma starts (default 1e-5;
  *                      the switch also happens when the FP32 residual stalls)
  *   "guess_from_vecs"  1: iscsi_davidson starts from `vecs` (default 0)
- *   "use_graph"        1: capture one Davidson iteration as a CUDA graph (default 1)
+ *   "use_graph"        1 (default): one Davidson iteration is captured as a
+ *                      CUDA graph on first use and replayed; 0: direct launches
+ *   "olsen"            1 (default): Olsen's correction in the Davidson
+ *                      preconditioner; 0: plain diagonal preconditioner
  *   "fp64_tc"          1 (default): with precision 64, the opposite-spin
  *                      contraction runs on the bf16 tensor cores with FP64
  *                      accuracy (operands cut into exact 7-bit slices, exact
  *                      integer accumulation of the leading levels; relative
  *                      error ~1e-14 of sum |g||c|); 0: native FP64 FMA
+ *   "samespin_tc"      1 (default): the same for the same-spin level blocks
+ *                      with more than 16 rows and 16 allowed beta strings
+ *   "fp32_tc"          1 (default): with precision 32, both contractions run
+ *                      on the tensor cores with three bf16 terms per element
+ *                      and FP32 accumulation; 0: FP32 FMA kernels
  *   "phase_timing"     1: record per-phase CUDA events of every sigma call
  *                      (reported by iscsi_stats; the record restarts when set)
  * Errors: ISCSI_E_ARG for an unknown key or a value out of range.
@@ -218,8 +226,12 @@ ISCSI_API iscsi_status iscsi_set_option(const char* key, double value);
  * Statistics of the current context as one JSON object (NUL-terminated,
  * truncated to len bytes): sizes, surviving units per group, updates per
  * sigma (one update = one sigma_I += sign * unit * c_J, counted over
- * surviving units and in-space determinant pairs), last sigma time.
- * Errors: ISCSI_E_NOINIT, ISCSI_E_ARG.
+ * surviving units and in-space determinant pairs), last sigma time, and of
+ * the last iscsi_davidson: iterations, those of the FP32 phase, whether a
+ * captured graph was replayed, time, and the largest residual norm per
+ * iteration ("davidson_rmax", up to 400 values).
+ * Errors: ISCSI_E_NOINIT, ISCSI_E_ARG (also when len is too small; the
+ * truncated text is still written).
  */
 ISCSI_API iscsi_status iscsi_stats(char* json, int len);
 

@@ -175,7 +175,7 @@ def iscsi_set_option(key, value):
 
 def iscsi_stats():
     import json
-    buf = ctypes.create_string_buffer(8192)
+    buf = ctypes.create_string_buffer(65536)
     _check(load().iscsi_stats(buf, len(buf)))
     return json.loads(buf.value.decode())
 

@@ -225,6 +225,8 @@ iscsi_status iscsi_set_option(const char* key, double value) {
     o.guess_from_vecs = value != 0;
   } else if (k == "use_graph") {
     o.use_graph = value != 0;
+  } else if (k == "olsen") {
+    o.olsen = value != 0;
   } else if (k == "fp64_tc") {
     o.fp64_tc = value != 0;
   } else if (k == "samespin_tc") {
@@ -274,16 +276,31 @@ iscsi_status iscsi_stats(char* json, int len) {
       "\"fold\": %.6f, \"samespin_gemm\": %.6f}, \"davidson_iters\": %d, \"davidson_ms\": %.6f, "
       "\"opposite_gemm_flops\": %.17g, \"samespin_gemm_flops\": %.17g, \"opposite_tc_bf16_flops\": %.17g, "
       "\"fp64_tc\": %d, \"samespin_tc\": %d, \"fp32_tc\": %d, \"davidson_fp32_iters\": %d, "
-      "\"kernel_launches\": %lld}",
+      "\"davidson_graph\": %d, \"kernel_launches\": %lld}",
       ctx->n, ctx->na, ctx->nb, ctx->kmax, ctx->tau, ctx->ndet, ctx->sp[0].count, ctx->sp[1].count,
       ctx->units_onebody_total, ctx->units_samespin_total, ctx->units_opposite_total, ctx->units_opposite,
       ctx->units_onebody, ctx->units_samespin, ctx->updates_onebody, ctx->updates_samespin,
       ctx->updates_opposite, upd, ctx->init_ms, ncalls, phase_ms[0], phase_ms[1], phase_ms[2], phase_ms[3],
       ctx->last_davidson_iters, ctx->last_davidson_ms, ctx_gemm_flops(*ctx, 0), ctx_gemm_flops(*ctx, 1),
       ctx_gemm_flops(*ctx, 2), options().fp64_tc, options().samespin_tc, options().fp32_tc,
-      ctx->last_davidson_fp32_iters, g_launch_count);
-  std::strncpy(json, buf, len - 1);
+      ctx->last_davidson_fp32_iters, ctx->last_davidson_graph, g_launch_count);
+  // largest residual norm per Davidson iteration of the last run (up to 400)
+  std::string out(buf);
+  out.pop_back();  // closing brace
+  out += ", \"davidson_rmax\": [";
+  const size_t nh = std::min<size_t>(ctx->last_davidson_rhist.size(), 400);
+  for (size_t i = 0; i < nh; ++i) {
+    char v[32];
+    std::snprintf(v, sizeof(v), i ? ", %.3e" : "%.3e", ctx->last_davidson_rhist[i]);
+    out += v;
+  }
+  out += "]}";
+  std::strncpy(json, out.c_str(), len - 1);
   json[len - 1] = 0;
+  if (out.size() >= (size_t)len) {
+    set_error("iscsi_stats: buffer too small");
+    return ISCSI_E_ARG;
+  }
   return ISCSI_OK;
 }
 

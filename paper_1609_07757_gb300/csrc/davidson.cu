@@ -1,160 +1,656 @@
-// davidson.cu -- lowest eigenpairs of H_tau (Eq. hcec) by a Davidson iteration
-// around the sigma step (Eq. sigma).  The paper names Davidson as the usual
-// optimisation step that follows sigma; its own runs used imaginary-time
-// propagation instead (Sec. "Basis and calculation set up").
+// davidson.cu -- lowest eigenpairs of H_tau (Eq. hcec) by a device-resident
+// Davidson iteration around the sigma step (Eq. sigma).  The paper names
+// Davidson as the usual optimisation step that follows sigma; its own runs
+// used imaginary-time propagation instead (Sec. "Basis and calculation set up").
 //
-// Vectors (subspace basis V, images W = H V, Ritz vectors, residuals) live on
-// the device in FP64.  Projections, Rayleigh-Ritz, residual norms and the
-// Gram-Schmidt orthonormalisation are FP64.  With the mixed-precision option
-// the sigma steps run in FP32 until every residual norm is below switch_tol;
-// then the basis is collapsed to the current Ritz vectors, their images are
-// recomputed with the FP64 sigma, and the iteration finishes in FP64, so the
-// returned energies are Rayleigh quotients of the FP64 operator.
+// Everything lives on the device: the basis V, its images W = H V, the Ritz
+// vectors X and residuals R, the subspace matrix S = V^T W, its eigen-
+// decomposition and a small control block (DavCtl) holding the basis size,
+// Ritz values, residual norms and flags.  Every kernel reads the basis size
+// from the control block, so one iteration is a fixed launch sequence:
+//
+//   restart      thick restart to the lowest nkeep Ritz pairs when the next
+//                expansion would overflow the basis (flag set by check)
+//   precondition t_j = (r_j - eps_j x_j) / (theta_j - diag) (Olsen's correction,
+//                option), zero for converged roots
+//   orthogonalise block Gram-Schmidt against V (a second pass only where the
+//                first removed more than 30% of a column), then two passes of
+//                Cholesky QR within the block; directions that keep no more
+//                than 1e-8 of their norm are dropped
+//   sigma        W_new = H T (the FP64 or FP32 sigma path)
+//   append       T, W_new join V, W; the new rows and columns of S
+//   eig          one-CTA parallel Jacobi on S (Brent-Luk round-robin order)
+//   ritz         X = V Y, R = W Y - X diag(theta), |R_j|
+//   check        convergence (all |R_j| <= tol and |d theta| <= etol),
+//                restart decision
+//
+// which is captured once as a CUDA graph and replayed each iteration; the host
+// reads the control block back (one small copy) to decide whether to stop.
+// Projections, Rayleigh-Ritz, residual norms and the orthonormalisation are
+// FP64.  With the mixed-precision option the sigma steps run in FP32 until
+// every residual norm is below switch_tol (or stops improving near the FP32
+// floor); then the basis is collapsed to the lowest 2k Ritz vectors, their
+// images are recomputed with the FP64 sigma, and the iteration finishes in
+// FP64, so the returned energies are Rayleigh quotients of the FP64 operator.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "internal.cuh"
 
 namespace iscsi {
 
-constexpr int kDotTile = 8;
-constexpr int kDotThreads = 256;
+constexpr int kMaxRoots = 32;
+constexpr int kVecThreads = 256;
+constexpr int kVecBlocks = 4 * 152;  // streaming kernels: 4 blocks per SM
+constexpr int kDotT = 8;             // tall-skinny dot products: 8 x 8 vectors per block
 
-// partial[b][i*nw + j] = sum over this block's slice of V_i[e] * W_j[e]
-__global__ void k_dots(const double* __restrict__ V, int nv, const double* __restrict__ W, int nw, long long N,
-                       double* __restrict__ partial, int npair_tiles_j) {
-  int ti = blockIdx.y / npair_tiles_j, tj = blockIdx.y % npair_tiles_j;
-  int i0 = ti * kDotTile, j0 = tj * kDotTile;
-  double acc[kDotTile][kDotTile];
+struct DavCtl {
+  int m;        // basis size
+  int k;        // roots
+  int maxsub;   // basis capacity
+  int iter;     // completed checks
+  int restart;  // 1: thick restart at the start of the next expansion
+  int nkeep;    // Ritz pairs kept by that restart
+  int added;    // vectors appended by the last expansion
+  int status;   // kStatus* bits
+  double tol, etol, rmax, dmax;
+  int reorth;    // 1: the block needs a second Gram-Schmidt pass
+  int olsen;    // 1: Olsen's correction in the preconditioner
+  double theta[kMaxRoots], theta_prev[kMaxRoots], rnorm[kMaxRoots], nrm0[kMaxRoots], eps[kMaxRoots];
+  int active[kMaxRoots];
+};
+enum { kStatusConverged = 1, kStatusNonFinite = 2, kStatusNoDirection = 4 };
+
+__device__ __forceinline__ double dav_den(double th, double d) {
+  double den = th - d;
+  if (fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
+  return den;
+}
+
+__device__ __forceinline__ double block_sum(double x, double* red) {
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;  // valid in thread 0
+}
+
+// partial[b][i][j] = sum over block b's elements of A_i[e] B_j[e], for
+// i < na = (na_dev ? *na_dev : 0) + na_add and j < nb; rows_cap bounds na.
+// Each block takes kDotT rows of A and NB columns of B (NB = nb when nb <= 8,
+// so no FMA is spent on absent columns: GB300's FP64 rate, not HBM, bounds
+// these products).
+template <int NB>
+__global__ void __launch_bounds__(kVecThreads) k_tsdots(const double* __restrict__ A, const int* __restrict__ na_dev,
+                                                        int na_add, const double* __restrict__ B, int nb, long long N,
+                                                        double* __restrict__ partial, int rows_cap,
+                                                        const int* __restrict__ gate) {
+  if (gate && !*gate) return;
+  const int na = (na_dev ? *na_dev : 0) + na_add;
+  const int tiles_b = (nb + NB - 1) / NB;
+  const int i0 = (blockIdx.y / tiles_b) * kDotT, j0 = (blockIdx.y % tiles_b) * NB;
+  if (i0 >= na) return;
+  const int ra = min(kDotT, na - i0);
+  double acc[kDotT][NB];
 #pragma unroll
-  for (int a = 0; a < kDotTile; ++a)
+  for (int a = 0; a < kDotT; ++a)
 #pragma unroll
-    for (int b = 0; b < kDotTile; ++b) acc[a][b] = 0.0;
-  long long stride = (long long)gridDim.x * blockDim.x;
+    for (int b = 0; b < NB; ++b) acc[a][b] = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
-    double v[kDotTile], w[kDotTile];
+    double vb[NB];
 #pragma unroll
-    for (int a = 0; a < kDotTile; ++a) v[a] = (i0 + a < nv) ? V[(long long)(i0 + a) * N + e] : 0.0;
+    for (int b = 0; b < NB; ++b) vb[b] = (j0 + b < nb) ? B[(long long)(j0 + b) * N + e] : 0.0;
 #pragma unroll
-    for (int b = 0; b < kDotTile; ++b) w[b] = (j0 + b < nw) ? W[(long long)(j0 + b) * N + e] : 0.0;
+    for (int a = 0; a < kDotT; ++a)
+      if (a < ra) {
+        const double va = A[(long long)(i0 + a) * N + e];
 #pragma unroll
-    for (int a = 0; a < kDotTile; ++a)
-#pragma unroll
-      for (int b = 0; b < kDotTile; ++b) acc[a][b] = fma(v[a], w[b], acc[a][b]);
+        for (int b = 0; b < NB; ++b) acc[a][b] = fma(va, vb[b], acc[a][b]);
+      }
   }
-  __shared__ double red[kDotThreads / 32][kDotTile * kDotTile];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ double red[kVecThreads / 32][kDotT * NB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int a = 0; a < kDotTile; ++a)
+  for (int a = 0; a < kDotT; ++a)
 #pragma unroll
-    for (int b = 0; b < kDotTile; ++b) {
+    for (int b = 0; b < NB; ++b) {
       double x = acc[a][b];
       for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) red[warp][a * kDotTile + b] = x;
+      if (lane == 0) red[warp][a * NB + b] = x;
     }
   __syncthreads();
-  if (threadIdx.x < kDotTile * kDotTile) {
+  if (threadIdx.x < kDotT * NB) {
     double x = 0.0;
-    for (int w_ = 0; w_ < kDotThreads / 32; ++w_) x += red[w_][threadIdx.x];
-    int a = threadIdx.x / kDotTile, b = threadIdx.x % kDotTile;
-    if (i0 + a < nv && j0 + b < nw) partial[(long long)blockIdx.x * nv * nw + (i0 + a) * nw + (j0 + b)] = x;
+    for (int w = 0; w < kVecThreads / 32; ++w) x += red[w][threadIdx.x];
+    const int a = threadIdx.x / NB, b = threadIdx.x % NB;
+    if (a < ra && j0 + b < nb) partial[((long long)blockIdx.x * rows_cap + i0 + a) * nb + j0 + b] = x;
   }
 }
 
-__global__ void k_reduce_partials(const double* __restrict__ partial, int nparts, int count, double* __restrict__ out) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= count) return;
+// C[i][j] = sum over blocks of partial[b][i][j] (nothing when gate points at 0)
+__global__ void k_tsreduce(const double* __restrict__ partial, int parts, const int* __restrict__ na_dev, int na_add,
+                           int nb, int rows_cap, double* __restrict__ C, const int* __restrict__ gate) {
+  if (gate && !*gate) return;
+  const int na = (na_dev ? *na_dev : 0) + na_add;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= na * nb) return;
   double x = 0.0;
-  for (int p = 0; p < nparts; ++p) x += partial[(long long)p * count + t];
-  out[t] = x;
+  for (int p = 0; p < parts; ++p) x += partial[(long long)p * rows_cap * nb + t];
+  C[t] = x;
 }
 
-// X_j = sum_i V_i Y[i][j] (j < k); if W != nullptr: R_j = sum_i W_i Y[i][j] - theta_j X_j
-// Y is m x k row-major (ld = k).  k <= 32.
-__global__ void k_ritz(const double* __restrict__ V, const double* __restrict__ W, int m, const double* __restrict__ Y,
-                       int k, const double* __restrict__ theta, long long N, double* __restrict__ X,
-                       double* __restrict__ R) {
-  extern __shared__ double sY[];
-  for (int t = threadIdx.x; t < m * k; t += blockDim.x) sY[t] = Y[t];
+// X_j = sum_i V_i Y[i][j], R_j = sum_i W_i Y[i][j] - theta_j X_j for j in
+// [j0, j0 + KC) (j < k); partial[b][j] = block b's part of |R_j|^2
+template <int KC>
+__global__ void __launch_bounds__(kVecThreads) k_dav_ritz(const double* __restrict__ V, const double* __restrict__ W,
+                                                          const DavCtl* __restrict__ ctl, const double* __restrict__ Y,
+                                                          int ldy, int j0, long long N, double* __restrict__ X,
+                                                          double* __restrict__ R, double* __restrict__ partial) {
+  extern __shared__ double sY[];  // [m][KC]
+  __shared__ double red[kVecThreads / 32];
+  const int m = ctl->m, k = ctl->k;
+  const int cnt = min(KC, k - j0);
+  if (cnt <= 0) return;
+  for (int t = threadIdx.x; t < m * KC; t += blockDim.x) sY[t] = (t % KC < cnt) ? Y[(t / KC) * ldy + j0 + t % KC] : 0.0;
+  double th[KC];
+#pragma unroll
+  for (int j = 0; j < KC; ++j) th[j] = j < cnt ? ctl->theta[j0 + j] : 0.0;
   __syncthreads();
-  long long stride = (long long)gridDim.x * blockDim.x;
+  double rr[KC];
+#pragma unroll
+  for (int j = 0; j < KC; ++j) rr[j] = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
-    double x[32], r[32];
-    for (int j = 0; j < k; ++j) x[j] = r[j] = 0.0;
+    double x[KC], r[KC];
+#pragma unroll
+    for (int j = 0; j < KC; ++j) x[j] = r[j] = 0.0;
     for (int i = 0; i < m; ++i) {
-      double v = V[(long long)i * N + e];
-      double w = W ? W[(long long)i * N + e] : 0.0;
-      for (int j = 0; j < k; ++j) {
-        x[j] = fma(v, sY[i * k + j], x[j]);
-        if (W) r[j] = fma(w, sY[i * k + j], r[j]);
+      const double v = V[(long long)i * N + e], w = W[(long long)i * N + e];
+#pragma unroll
+      for (int j = 0; j < KC; ++j) {
+        x[j] = fma(v, sY[i * KC + j], x[j]);
+        r[j] = fma(w, sY[i * KC + j], r[j]);
       }
     }
-    for (int j = 0; j < k; ++j) {
-      X[(long long)j * N + e] = x[j];
-      if (W) R[(long long)j * N + e] = r[j] - theta[j] * x[j];
-    }
+#pragma unroll
+    for (int j = 0; j < KC; ++j)
+      if (j < cnt) {
+        const double rv = r[j] - th[j] * x[j];
+        X[(long long)(j0 + j) * N + e] = x[j];
+        R[(long long)(j0 + j) * N + e] = rv;
+        rr[j] = fma(rv, rv, rr[j]);
+      }
+  }
+#pragma unroll
+  for (int j = 0; j < KC; ++j) {
+    const double t = block_sum(rr[j], red);
+    if (threadIdx.x == 0 && j < cnt) partial[(long long)blockIdx.x * k + j0 + j] = t;
   }
 }
 
-// out_j = sum_i V_i Y[i][j0 + j] for j < cnt <= 32 (Y is m x ldy row-major)
-__global__ void k_lincomb(const double* __restrict__ V, int m, const double* __restrict__ Y, int ldy, int j0, int cnt,
-                          long long N, double* __restrict__ out) {
+// out_j = sum_{i<m} V_i Y[i][j0 + j] for j < min(KC, nkeep - j0); only when a
+// restart is pending
+template <int KC>
+__global__ void __launch_bounds__(kVecThreads) k_dav_restart_lincomb(const double* __restrict__ V,
+                                                                     const DavCtl* __restrict__ ctl,
+                                                                     const double* __restrict__ Y, int ldy, int j0,
+                                                                     long long N, double* __restrict__ out) {
   extern __shared__ double sYc[];
-  for (int t = threadIdx.x; t < m * cnt; t += blockDim.x) sYc[t] = Y[(t / cnt) * ldy + j0 + (t % cnt)];
+  if (!ctl->restart) return;
+  const int m = ctl->m;
+  const int cnt = min(KC, ctl->nkeep - j0);
+  if (cnt <= 0) return;
+  for (int t = threadIdx.x; t < m * KC; t += blockDim.x) sYc[t] = (t % KC < cnt) ? Y[(t / KC) * ldy + j0 + t % KC] : 0.0;
   __syncthreads();
-  long long stride = (long long)gridDim.x * blockDim.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
-    double acc[32];
-    for (int j = 0; j < cnt; ++j) acc[j] = 0.0;
+    double acc[KC];
+#pragma unroll
+    for (int j = 0; j < KC; ++j) acc[j] = 0.0;
     for (int i = 0; i < m; ++i) {
-      double v = V[(long long)i * N + e];
-      for (int j = 0; j < cnt; ++j) acc[j] = fma(v, sYc[i * cnt + j], acc[j]);
+      const double v = V[(long long)i * N + e];
+#pragma unroll
+      for (int j = 0; j < KC; ++j) acc[j] = fma(v, sYc[i * KC + j], acc[j]);
     }
-    for (int j = 0; j < cnt; ++j) out[(long long)j * N + e] = acc[j];
+#pragma unroll
+    for (int j = 0; j < KC; ++j)
+      if (j < cnt) out[(long long)(j0 + j) * N + e] = acc[j];
   }
 }
 
-// T_j -= sum_i V_i C[i][j] for j < k (C is m x k row-major), then nothing else
-__global__ void k_project_out(const double* __restrict__ V, int m, const double* __restrict__ C, int k, long long N,
-                              double* __restrict__ T) {
-  extern __shared__ double sC[];
-  for (int t = threadIdx.x; t < m * k; t += blockDim.x) sC[t] = C[t];
+// dst[0 : nkeep N] = src[...] when a restart is pending
+__global__ void k_dav_restart_copy(double* __restrict__ dst, const double* __restrict__ src,
+                                   const DavCtl* __restrict__ ctl, long long N) {
+  if (!ctl->restart) return;
+  const long long total = (long long)ctl->nkeep * N;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += stride) dst[t] = src[t];
+}
+
+// after a restart the basis is the Ritz basis: S = diag(theta_0 .. theta_{nkeep-1})
+__global__ void k_dav_restart_S(DavCtl* __restrict__ ctl, double* __restrict__ S, int lds,
+                                const double* __restrict__ theta_all) {
+  if (!ctl->restart) return;
+  const int m = ctl->m, nk = ctl->nkeep;
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    const int i = t / m, j = t % m;
+    S[(long long)i * lds + j] = (i == j && i < nk) ? theta_all[i] : 0.0;
+  }
   __syncthreads();
-  long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
-    double acc[32];
-    for (int j = 0; j < k; ++j) acc[j] = 0.0;
-    for (int i = 0; i < m; ++i) {
-      double v = V[(long long)i * N + e];
-      for (int j = 0; j < k; ++j) acc[j] = fma(v, sC[i * k + j], acc[j]);
-    }
-    for (int j = 0; j < k; ++j) T[(long long)j * N + e] -= acc[j];
+  if (threadIdx.x == 0) {
+    ctl->m = nk;
+    ctl->restart = 0;
   }
 }
 
-// t_j[e] = r_j[e] / (theta_j - d[e]), with the denominator kept away from zero
-__global__ void k_precondition(const double* __restrict__ R, const double* __restrict__ diag,
-                               const double* __restrict__ theta, int k, long long N, double* __restrict__ T) {
-  long long stride = (long long)gridDim.x * blockDim.x;
+// t_j = (r_j - eps_j x_j) / (theta_j - d) with the denominator kept away from
+// zero (eps_j = 0 without Olsen's correction); zero for roots already
+// converged (no new direction)
+__global__ void __launch_bounds__(kVecThreads) k_dav_precond(const double* __restrict__ R,
+                                                             const double* __restrict__ X,
+                                                             const double* __restrict__ diag,
+                                                             const DavCtl* __restrict__ ctl, long long N,
+                                                             double* __restrict__ T) {
+  __shared__ double th[kMaxRoots], ep[kMaxRoots];
+  __shared__ int on[kMaxRoots];
+  const int k = ctl->k;
+  if (threadIdx.x < k) {
+    th[threadIdx.x] = ctl->theta[threadIdx.x];
+    ep[threadIdx.x] = ctl->olsen ? ctl->eps[threadIdx.x] : 0.0;
+    on[threadIdx.x] = ctl->rnorm[threadIdx.x] > 0.1 * ctl->tol;
+  }
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
-    double d = diag[e];
+    const double d = diag[e];
     for (int j = 0; j < k; ++j) {
-      double den = theta[j] - d;
-      if (fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
-      T[(long long)j * N + e] = R[(long long)j * N + e] / den;
+      const double r = R[(long long)j * N + e] - (ep[j] != 0.0 ? ep[j] * X[(long long)j * N + e] : 0.0);
+      T[(long long)j * N + e] = on[j] ? r / dav_den(th[j], d) : 0.0;
     }
   }
 }
 
-__global__ void k_scale_vecs(double* __restrict__ T, const double* __restrict__ f, int k, long long N) {
-  long long stride = (long long)gridDim.x * blockDim.x;
+// norms of the corrections before projection (G = T^T T) and the directions
+// that take part in this expansion
+__global__ void k_dav_set_nrm0(DavCtl* __restrict__ ctl, const double* __restrict__ G) {
+  const int k = ctl->k, j = threadIdx.x;
+  if (j < k) {
+    const double g = G[j * k + j];
+    ctl->nrm0[j] = sqrt(fmax(g, 0.0));
+    ctl->active[j] = g > 0.0 && isfinite(g);
+  }
+}
+
+// T_j -= sum_{i<m} V_i C[i][j] for all j < k (k <= KC); nothing when gate points at 0
+template <int KC>
+__global__ void __launch_bounds__(kVecThreads) k_dav_project(const double* __restrict__ V,
+                                                             const DavCtl* __restrict__ ctl,
+                                                             const double* __restrict__ C, long long N,
+                                                             double* __restrict__ T, const int* __restrict__ gate) {
+  extern __shared__ double sC[];  // [m][KC]
+  if (gate && !*gate) return;
+  const int m = ctl->m, k = ctl->k;
+  for (int t = threadIdx.x; t < m * KC; t += blockDim.x) sC[t] = (t % KC < k) ? C[(t / KC) * k + t % KC] : 0.0;
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
+    double acc[KC];
+#pragma unroll
+    for (int j = 0; j < KC; ++j) acc[j] = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double v = V[(long long)i * N + e];
+#pragma unroll
+      for (int j = 0; j < KC; ++j) acc[j] = fma(v, sC[i * KC + j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < KC; ++j)
+      if (j < k) T[(long long)j * N + e] -= acc[j];
+  }
+}
+
+// Second Gram-Schmidt pass only where the first removed more than 30% of a
+// column's norm (the criterion of Daniel, Gragg, Kaufman and Stewart, Math.
+// Comp. 30 (1976) 772); otherwise one pass already leaves the block orthogonal
+// to the basis to working precision.
+__global__ void k_dav_reorth(DavCtl* __restrict__ ctl, const double* __restrict__ G) {
+  if (threadIdx.x != 0) return;
+  const int k = ctl->k;
+  int re = 0;
+  for (int j = 0; j < k; ++j)
+    if (ctl->active[j] && sqrt(fmax(G[j * k + j], 0.0)) < 0.7 * ctl->nrm0[j]) re = 1;
+  ctl->reorth = re;
+}
+
+// Olsen's correction (Olsen, Jorgensen and Simons, Chem. Phys. Lett. 169
+// (1990) 463): t_j = M_j^-1 (r_j - eps_j x_j) with M_j = diag(theta_j - H_ii)
+// and eps_j = (x_j . M_j^-1 r_j) / (x_j . M_j^-1 x_j), so that t_j is
+// orthogonal to x_j in the M_j metric.  partial[b][2j], [2j+1]: block b's
+// parts of the two products.
+__global__ void __launch_bounds__(kVecThreads) k_dav_olsen_dots(const double* __restrict__ R,
+                                                                const double* __restrict__ X,
+                                                                const double* __restrict__ diag,
+                                                                const DavCtl* __restrict__ ctl, long long N,
+                                                                double* __restrict__ partial) {
+  __shared__ double red[kVecThreads / 32];
+  if (!ctl->olsen) return;
+  const int k = ctl->k;
+  for (int j = 0; j < k; ++j) {
+    const double th = ctl->theta[j];
+    double a = 0.0, b = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
+      const double x = X[(long long)j * N + e], inv = 1.0 / dav_den(th, diag[e]);
+      a = fma(x * inv, R[(long long)j * N + e], a);
+      b = fma(x * inv, x, b);
+    }
+    a = block_sum(a, red);
+    b = block_sum(b, red);
+    if (threadIdx.x == 0) {
+      partial[(long long)blockIdx.x * 2 * k + 2 * j] = a;
+      partial[(long long)blockIdx.x * 2 * k + 2 * j + 1] = b;
+    }
+  }
+}
+
+__global__ void k_dav_olsen_eps(DavCtl* __restrict__ ctl, const double* __restrict__ partial, int parts) {
+  const int k = ctl->k, j = threadIdx.x;
+  if (j >= k) return;
+  if (!ctl->olsen) {
+    ctl->eps[j] = 0.0;
+    return;
+  }
+  double a = 0.0, b = 0.0;
+  for (int p = 0; p < parts; ++p) {
+    a += partial[(long long)p * 2 * k + 2 * j];
+    b += partial[(long long)p * 2 * k + 2 * j + 1];
+  }
+  ctl->eps[j] = (b != 0.0 && isfinite(a / b)) ? a / b : 0.0;
+}
+
+// Cholesky QR of the correction block from G = T^T T: upper R with R^T R = G
+// over the active columns, Rinv = R^-1 (zero rows/columns for dropped ones).
+// A column is dropped when its remaining norm is at most 1e-8 times its norm
+// before projection (first pass) or times its current norm (second pass).
+__global__ void k_dav_cholqr(DavCtl* __restrict__ ctl, const double* __restrict__ G, double* __restrict__ Rinv,
+                             int first_pass) {
+  __shared__ double Rm[kMaxRoots][kMaxRoots], Ri[kMaxRoots][kMaxRoots];
+  if (threadIdx.x != 0) return;
+  const int k = ctl->k;
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) Rm[i][j] = Ri[i][j] = 0.0;
+  for (int j = 0; j < k; ++j) {
+    if (!ctl->active[j]) continue;
+    double d = G[j * k + j];
+    for (int i = 0; i < j; ++i) d -= Rm[i][j] * Rm[i][j];
+    const double ref = first_pass ? ctl->nrm0[j] : sqrt(fmax(G[j * k + j], 0.0));
+    if (!(d > 0.0) || sqrt(d) <= 1e-8 * ref) {
+      ctl->active[j] = 0;
+      continue;
+    }
+    Rm[j][j] = sqrt(d);
+    for (int l = j + 1; l < k; ++l) {
+      if (!ctl->active[l]) continue;
+      double x = G[j * k + l];
+      for (int i = 0; i < j; ++i) x -= Rm[i][j] * Rm[i][l];
+      Rm[j][l] = x / Rm[j][j];
+    }
+  }
+  // inverse of the upper-triangular R on the active columns
+  for (int j = 0; j < k; ++j) {
+    if (!ctl->active[j]) continue;
+    Ri[j][j] = 1.0 / Rm[j][j];
+    for (int i = j - 1; i >= 0; --i) {
+      if (!ctl->active[i]) continue;
+      double x = 0.0;
+      for (int l = i + 1; l <= j; ++l) x += Rm[i][l] * Ri[l][j];
+      Ri[i][j] = -x / Rm[i][i];
+    }
+  }
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) Rinv[i * k + j] = Ri[i][j];
+}
+
+// T <- T Rinv (in place, all k <= KC columns per element)
+template <int KC>
+__global__ void __launch_bounds__(kVecThreads) k_dav_transform(double* __restrict__ T,
+                                                               const double* __restrict__ Rinv,
+                                                               const DavCtl* __restrict__ ctl, long long N) {
+  __shared__ double sR[KC * KC];
+  const int k = ctl->k;
+  for (int t = threadIdx.x; t < KC * KC; t += blockDim.x) {
+    const int i = t / KC, j = t % KC;
+    sR[t] = (i < k && j < k) ? Rinv[i * k + j] : 0.0;
+  }
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
+    double t[KC];
+#pragma unroll
+    for (int j = 0; j < KC; ++j) t[j] = j < k ? T[(long long)j * N + e] : 0.0;
+#pragma unroll
+    for (int j = 0; j < KC; ++j)
+      if (j < k) {
+        double x = 0.0;
+#pragma unroll
+        for (int i = 0; i <= j; ++i) x = fma(t[i], sR[i * KC + j], x);
+        T[(long long)j * N + e] = x;
+      }
+  }
+}
+
+// the active columns of T and W_new join the basis at positions m, m+1, ...
+__global__ void __launch_bounds__(kVecThreads) k_dav_append_vec(double* __restrict__ V, double* __restrict__ W,
+                                                                const double* __restrict__ T,
+                                                                const double* __restrict__ Wn,
+                                                                const DavCtl* __restrict__ ctl, long long N) {
+  __shared__ int slot[kMaxRoots];
+  const int k = ctl->k, m = ctl->m;
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int j = 0; j < k; ++j) slot[j] = ctl->active[j] ? s++ : -1;
+  }
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride)
-    for (int j = 0; j < k; ++j) T[(long long)j * N + e] *= f[j];
+    for (int j = 0; j < k; ++j)
+      if (slot[j] >= 0) {
+        V[(long long)(m + slot[j]) * N + e] = T[(long long)j * N + e];
+        W[(long long)(m + slot[j]) * N + e] = Wn[(long long)j * N + e];
+      }
+}
+
+// new rows/columns of S from C1 = V[0:m]^T W_new and C2 = T^T W_new; m grows
+__global__ void k_dav_append_S(DavCtl* __restrict__ ctl, double* __restrict__ S, int lds,
+                               const double* __restrict__ C1, const double* __restrict__ C2) {
+  __shared__ int slot[kMaxRoots];
+  __shared__ int added;
+  const int k = ctl->k, m = ctl->m;
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int j = 0; j < k; ++j) slot[j] = ctl->active[j] ? s++ : -1;
+    added = s;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < m * k; t += blockDim.x) {
+    const int i = t / k, j = t % k;
+    if (slot[j] < 0) continue;
+    const int p = m + slot[j];
+    S[(long long)i * lds + p] = S[(long long)p * lds + i] = C1[i * k + j];
+  }
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int j = t / k, l = t % k;
+    if (slot[j] < 0 || slot[l] < 0) continue;
+    S[(long long)(m + slot[j]) * lds + (m + slot[l])] = 0.5 * (C2[j * k + l] + C2[l * k + j]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl->m = m + added;
+    ctl->added = added;
+    if (added == 0) ctl->status |= kStatusNoDirection;
+  }
+}
+
+// S[0:cnt][0:cnt] from C = V[0:cnt]^T W[0:cnt] (symmetrised); the basis is
+// those cnt vectors
+__global__ void k_dav_init_S(DavCtl* __restrict__ ctl, double* __restrict__ S, int lds, const double* __restrict__ C,
+                             int cnt) {
+  for (int t = threadIdx.x; t < cnt * cnt; t += blockDim.x) {
+    const int i = t / cnt, j = t % cnt;
+    S[(long long)i * lds + j] = 0.5 * (C[i * cnt + j] + C[j * cnt + i]);
+  }
+  if (threadIdx.x == 0) {
+    ctl->m = cnt;
+    ctl->restart = 0;
+  }
+}
+
+// request a restart to the lowest nkeep Ritz pairs (used when the precision changes)
+__global__ void k_dav_request_restart(DavCtl* __restrict__ ctl, int nkeep) {
+  if (threadIdx.x == 0) {
+    ctl->restart = 1;
+    ctl->nkeep = nkeep;
+    ctl->status = 0;
+  }
+}
+
+// Symmetric eigen-decomposition of S[0:m][0:m] by cyclic Jacobi rotations
+// (Golub & Van Loan, "Matrix Computations", Sec. 8.5) in the parallel
+// round-robin order of Brent and Luk: each round rotates m/2 disjoint (p, q)
+// pairs at once.  A, Q are m x m work arrays (shared or global memory).
+// Eigenvalues ascending into theta_all, eigenvector j into column j of Y;
+// ctl->theta gets the lowest k.
+__global__ void __launch_bounds__(256) k_dav_eigh(DavCtl* __restrict__ ctl, const double* __restrict__ S, int lds,
+                                                  double* gA, double* gQ, double* __restrict__ Y, int ldy,
+                                                  double* __restrict__ theta_all, int use_smem) {
+  extern __shared__ double dyn[];
+  __shared__ double cs[192], sn[192];
+  __shared__ int pp[192], qq[192];
+  __shared__ double red[8];
+  __shared__ int stop;
+  const int m = ctl->m;
+  double* A = use_smem ? dyn : gA;
+  double* Q = use_smem ? dyn + m * m : gQ;
+  const int me = m + (m & 1);
+  const int npair = me / 2;
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    const int i = t / m, j = t % m;
+    A[t] = S[(long long)i * lds + j];
+    Q[t] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 60 && m > 1; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      const double x = A[t] * A[t];
+      tot += x;
+      if (t / m != t % m) off += x;
+    }
+    off = block_sum(off, red);
+    tot = block_sum(tot, red);
+    if (threadIdx.x == 0) stop = !(off > 1e-30 * tot) || off == 0.0;
+    __syncthreads();
+    if (stop) break;
+    for (int r = 0; r < me - 1; ++r) {
+      for (int i = threadIdx.x; i < npair; i += blockDim.x) {
+        const int a = i == 0 ? 0 : ((i - 1 + r) % (me - 1)) + 1;
+        const int b = ((me - 2 - i + r) % (me - 1)) + 1;
+        const int p = min(a, b), q = max(a, b);
+        double c = 1.0, s = 0.0;
+        if (q < m) {
+          const double apq = A[p * m + q];
+          if (fabs(apq) >= 1e-300) {
+            const double tau = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+            const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        }
+        pp[i] = p;
+        qq[i] = q;
+        cs[i] = c;
+        sn[i] = s;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < npair * m; t += blockDim.x) {  // rows p, q
+        const int i = t / m, col = t % m;
+        const int p = pp[i], q = qq[i];
+        if (q >= m || sn[i] == 0.0) continue;
+        const double c = cs[i], s = sn[i];
+        const double apk = A[p * m + col], aqk = A[q * m + col];
+        A[p * m + col] = c * apk - s * aqk;
+        A[q * m + col] = s * apk + c * aqk;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < npair * m; t += blockDim.x) {  // columns p, q and Q
+        const int i = t / m, row = t % m;
+        const int p = pp[i], q = qq[i];
+        if (q >= m || sn[i] == 0.0) continue;
+        const double c = cs[i], s = sn[i];
+        const double akp = A[row * m + p], akq = A[row * m + q];
+        A[row * m + p] = c * akp - s * akq;
+        A[row * m + q] = s * akp + c * akq;
+        const double ykp = Q[row * m + p], ykq = Q[row * m + q];
+        Q[row * m + p] = c * ykp - s * ykq;
+        Q[row * m + q] = s * ykp + c * ykq;
+      }
+      __syncthreads();
+    }
+  }
+  // ascending order: rank of each eigenvalue (ties by index)
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double li = A[i * m + i];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      const double lj = A[j * m + j];
+      rank += (lj < li) || (lj == li && j < i);
+    }
+    theta_all[rank] = li;
+    for (int row = 0; row < m; ++row) Y[(long long)row * ldy + rank] = Q[row * m + i];
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < ctl->k && j < m; j += blockDim.x) ctl->theta[j] = theta_all[j];
+}
+
+// residual norms, convergence and the restart decision
+__global__ void k_dav_check(DavCtl* __restrict__ ctl, const double* __restrict__ partial, int parts) {
+  const int k = ctl->k, j = threadIdx.x;
+  if (j < k) {
+    double x = 0.0;
+    for (int p = 0; p < parts; ++p) x += partial[(long long)p * k + j];
+    ctl->rnorm[j] = sqrt(fmax(x, 0.0));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double rmax = 0.0, dmax = 0.0;
+    bool finite = true;
+    for (int i = 0; i < k; ++i) {
+      rmax = fmax(rmax, ctl->rnorm[i]);
+      dmax = fmax(dmax, fabs(ctl->theta[i] - ctl->theta_prev[i]));
+      if (!isfinite(ctl->theta[i]) || !isfinite(ctl->rnorm[i])) finite = false;
+      ctl->theta_prev[i] = ctl->theta[i];
+    }
+    ctl->rmax = rmax;
+    ctl->dmax = dmax;
+    ctl->iter += 1;
+    if (!finite) ctl->status |= kStatusNonFinite;
+    if (finite && ctl->iter > 1 && rmax <= ctl->tol && dmax <= ctl->etol) ctl->status |= kStatusConverged;
+    const int m = ctl->m;
+    if (m + k > ctl->maxsub) {
+      ctl->restart = 1;
+      ctl->nkeep = max(k, min(m - k, ctl->maxsub / 2));
+    }
+  }
 }
 
 __global__ void k_unit_vectors(double* __restrict__ V, const long long* __restrict__ idx, int k, long long N) {
-  long long stride = (long long)gridDim.x * blockDim.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride)
     for (int j = 0; j < k; ++j) V[(long long)j * N + e] = (e == idx[j]) ? 1.0 : 0.0;
 }
@@ -162,321 +658,427 @@ __global__ void k_unit_vectors(double* __restrict__ V, const long long* __restri
 // ---------------------------------------------------------------------------
 // host side
 
-// Symmetric eigen-decomposition by cyclic Jacobi rotations (Golub & Van Loan,
-// "Matrix Computations", Sec. 8.5).  A (n x n, row-major) is overwritten; the
-// eigenvalues come back ascending with eigenvector columns in Y (row-major).
-static void jacobi_eigh(std::vector<double> A, int n, std::vector<double>& w, std::vector<double>& Y) {
-  Y.assign((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) Y[(size_t)i * n + i] = 1.0;
-  auto at = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        double x = at(i, j) * at(i, j);
-        tot += x;
-        if (i != j) off += x;
-      }
-    if (off <= 1e-30 * tot || off == 0.0) break;
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        double apq = at(p, q);
-        if (std::fabs(apq) < 1e-300) continue;
-        double app = at(p, p), aqq = at(q, q);
-        double tau = (aqq - app) / (2.0 * apq);
-        double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
-        double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
-        for (int k = 0; k < n; ++k) {  // A <- J^T A J
-          double akp = at(k, p), akq = at(k, q);
-          at(k, p) = c * akp - s * akq;
-          at(k, q) = s * akp + c * akq;
-        }
-        for (int k = 0; k < n; ++k) {
-          double apk = at(p, k), aqk = at(q, k);
-          at(p, k) = c * apk - s * aqk;
-          at(q, k) = s * apk + c * aqk;
-        }
-        for (int k = 0; k < n; ++k) {
-          double ykp = Y[(size_t)k * n + p], ykq = Y[(size_t)k * n + q];
-          Y[(size_t)k * n + p] = c * ykp - s * ykq;
-          Y[(size_t)k * n + q] = s * ykp + c * ykq;
-        }
-      }
-  }
-  std::vector<int> order(n);
-  for (int i = 0; i < n; ++i) order[i] = i;
-  std::sort(order.begin(), order.end(), [&](int a, int b) { return at(a, a) < at(b, b); });
-  w.resize(n);
-  std::vector<double> Ys((size_t)n * n);
-  for (int jj = 0; jj < n; ++jj) {
-    w[jj] = at(order[jj], order[jj]);
-    for (int i = 0; i < n; ++i) Ys[(size_t)i * n + jj] = Y[(size_t)i * n + order[jj]];
-  }
-  Y.swap(Ys);
-}
+namespace {
 
-struct DavWork {
+int kc_for(int k) { return k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32; }
+
+struct Dav {
   Context& ctx;
   long long N;
+  int k, maxsub, kc, parts, rows_cap, eig_smem;
   cudaStream_t st;
-  DevBuf partial, small_d, small_d2;
-  int blocks;
-  explicit DavWork(Context& c) : ctx(c), N(c.ndet), st(stream()) {
-    blocks = (int)std::min<long long>(4 * 152, (N + kDotThreads - 1) / kDotThreads);
-    if (blocks < 1) blocks = 1;
+  DevBuf ctl_d, S, Y, thetas, eigA, eigQ, partial, C1, C2, G, Rinv, rr_part;
+  double *V = nullptr, *W = nullptr, *X = nullptr, *R = nullptr, *T = nullptr, *Wn = nullptr, *tmp = nullptr;
+  DavCtl* ctl = nullptr;
+
+  Dav(Context& c, int k_, int maxsub_) : ctx(c), N(c.ndet), k(k_), maxsub(maxsub_), st(stream()) {
+    kc = kc_for(k);
+    parts = kVecBlocks;
+    rows_cap = maxsub + k;
+    const int eb = 2 * maxsub * maxsub * (int)sizeof(double);
+    eig_smem = eb <= 160 * 1024 ? eb : 0;
   }
-  // host out[i*nw + j] = V_i . W_j
-  int dots(const double* V, int nv, const double* W, int nw, std::vector<double>& out) {
-    int tj = (nw + kDotTile - 1) / kDotTile, ti = (nv + kDotTile - 1) / kDotTile;
-    int parts = std::min(blocks, 152);
-    ISCSI_TRY(partial.grow(sizeof(double) * (size_t)parts * nv * nw));
-    ISCSI_TRY(small_d.grow(sizeof(double) * (size_t)nv * nw));
-    dim3 grid(parts, ti * tj);
-    k_dots<<<grid, kDotThreads, 0, st>>>(V, nv, W, nw, N, partial.as<double>(), tj);
-    k_reduce_partials<<<launch_blocks((long long)nv * nw, 128), 128, 0, st>>>(partial.as<double>(), parts, nv * nw,
-                                                                             small_d.as<double>());
-    ISCSI_CUDA(cudaGetLastError());
-    out.resize((size_t)nv * nw);
-    ISCSI_CUDA(cudaMemcpyAsync(out.data(), small_d.p, sizeof(double) * nv * nw, cudaMemcpyDeviceToHost, st));
-    ISCSI_CUDA(cudaStreamSynchronize(st));
-    return kOk;
+
+  int setup() {
+    ISCSI_TRY(ctx.dv_V.grow(sizeof(double) * (size_t)maxsub * N));
+    ISCSI_TRY(ctx.dv_W.grow(sizeof(double) * (size_t)maxsub * N));
+    // X, R, T, W_new and the restart buffer
+    const size_t nk = std::max(k, maxsub / 2);
+    ISCSI_TRY(ctx.dv_tmp.grow(sizeof(double) * ((size_t)4 * k + nk) * N));
+    V = ctx.dv_V.as<double>();
+    W = ctx.dv_W.as<double>();
+    X = ctx.dv_tmp.as<double>();
+    R = X + (size_t)k * N;
+    T = R + (size_t)k * N;
+    Wn = T + (size_t)k * N;
+    tmp = Wn + (size_t)k * N;
+    ISCSI_TRY(ctl_d.alloc(sizeof(DavCtl)));
+    ctl = ctl_d.as<DavCtl>();
+    ISCSI_TRY(S.alloc(sizeof(double) * (size_t)maxsub * maxsub));
+    ISCSI_TRY(Y.alloc(sizeof(double) * (size_t)maxsub * maxsub));
+    ISCSI_TRY(thetas.alloc(sizeof(double) * maxsub));
+    ISCSI_TRY(eigA.alloc(sizeof(double) * (size_t)maxsub * maxsub));
+    ISCSI_TRY(eigQ.alloc(sizeof(double) * (size_t)maxsub * maxsub));
+    ISCSI_TRY(partial.alloc(sizeof(double) * (size_t)parts * rows_cap * 2 * k));
+    ISCSI_TRY(C1.alloc(sizeof(double) * (size_t)rows_cap * 2 * k));
+    ISCSI_TRY(C2.alloc(sizeof(double) * (size_t)k * k));
+    ISCSI_TRY(G.alloc(sizeof(double) * (size_t)k * k));
+    ISCSI_TRY(Rinv.alloc(sizeof(double) * (size_t)k * k));
+    ISCSI_TRY(rr_part.alloc(sizeof(double) * (size_t)parts * 2 * k));
+    ISCSI_CUDA(cudaMemsetAsync(S.p, 0, sizeof(double) * (size_t)maxsub * maxsub, st));
+    return attributes();
   }
-  int upload(const std::vector<double>& h, DevBuf& d) {
-    ISCSI_TRY(d.grow(sizeof(double) * std::max<size_t>(1, h.size())));
-    ISCSI_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, st));
-    return kOk;
-  }
-  // T_j -= V (V^T T_j), applied twice; T has k vectors
-  int orthogonalise(const double* V, int m, double* T, int k) {
-    if (m == 0) return kOk;
-    for (int pass = 0; pass < 2; ++pass) {
-      std::vector<double> C;
-      ISCSI_TRY(dots(V, m, T, k, C));  // C[i*k + j] = V_i . T_j
-      ISCSI_TRY(upload(C, small_d2));
-      k_project_out<<<blocks, 256, sizeof(double) * m * k, st>>>(V, m, small_d2.as<double>(), k, N, T);
-      ISCSI_CUDA(cudaGetLastError());
-      ISCSI_CUDA(cudaStreamSynchronize(st));  // C must stay alive until the copy is consumed
+
+  int attributes() {
+    const int lim = 200 * 1024;
+    if ((long long)sizeof(double) * maxsub * kc > lim) {
+      set_error("iscsi_davidson: subspace too large for the shared-memory staging");
+      return kErrArg;
     }
+#define ISCSI_DAV_ATTR(KC)                                                                                 \
+  ISCSI_CUDA(cudaFuncSetAttribute(k_dav_ritz<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));    \
+  ISCSI_CUDA(cudaFuncSetAttribute(k_dav_project<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)); \
+  ISCSI_CUDA(cudaFuncSetAttribute(k_dav_restart_lincomb<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    ISCSI_DAV_ATTR(4)
+    ISCSI_DAV_ATTR(8)
+    ISCSI_DAV_ATTR(16)
+    ISCSI_DAV_ATTR(32)
+#undef ISCSI_DAV_ATTR
+    if (eig_smem) ISCSI_CUDA(cudaFuncSetAttribute(k_dav_eigh, cudaFuncAttributeMaxDynamicSharedMemorySize, eig_smem));
+    return kOk;
+  }
+
+  template <int NB>
+  void dots_t(const double* A, const int* na_dev, int na_add, const double* B, int nb, const int* gate) {
+    const int tiles = ((rows_cap + kDotT - 1) / kDotT) * ((nb + NB - 1) / NB);
+    k_tsdots<NB><<<dim3(parts, tiles), kVecThreads, 0, st>>>(A, na_dev, na_add, B, nb, N, partial.as<double>(),
+                                                             rows_cap, gate); ISCSI_COUNT_LAUNCH();
+  }
+  // C[i][j] = A_i . B_j for i < (na_dev ? *na_dev : 0) + na_add, j < nb; when
+  // gate is given, only if *gate != 0 at run time
+  void dots(const double* A, const int* na_dev, int na_add, const double* B, int nb, double* C,
+            const int* gate = nullptr) {
+    switch (nb) {
+      case 1: dots_t<1>(A, na_dev, na_add, B, nb, gate); break;
+      case 2: dots_t<2>(A, na_dev, na_add, B, nb, gate); break;
+      case 3: dots_t<3>(A, na_dev, na_add, B, nb, gate); break;
+      case 4: dots_t<4>(A, na_dev, na_add, B, nb, gate); break;
+      case 5: dots_t<5>(A, na_dev, na_add, B, nb, gate); break;
+      case 6: dots_t<6>(A, na_dev, na_add, B, nb, gate); break;
+      case 7: dots_t<7>(A, na_dev, na_add, B, nb, gate); break;
+      default: dots_t<8>(A, na_dev, na_add, B, nb, gate); break;
+    }
+    k_tsreduce<<<(rows_cap * nb + 127) / 128, 128, 0, st>>>(partial.as<double>(), parts, na_dev, na_add, nb, rows_cap,
+                                                            C, gate); ISCSI_COUNT_LAUNCH();
+  }
+
+  template <int KC>
+  void ritz_t() {
+    const size_t sm = sizeof(double) * (size_t)maxsub * KC;
+    for (int j0 = 0; j0 < k; j0 += KC) {
+      k_dav_ritz<KC><<<parts, kVecThreads, sm, st>>>(V, W, ctl, Y.as<double>(), maxsub, j0, N, X, R,
+                                                     rr_part.as<double>()); ISCSI_COUNT_LAUNCH();
+    }
+  }
+  template <int KC>
+  void project_t(const double* C, const int* gate) {
+    k_dav_project<KC><<<parts, kVecThreads, sizeof(double) * (size_t)maxsub * KC, st>>>(V, ctl, C, N, T, gate); ISCSI_COUNT_LAUNCH();
+  }
+  template <int KC>
+  void transform_t() {
+    k_dav_transform<KC><<<parts, kVecThreads, 0, st>>>(T, Rinv.as<double>(), ctl, N); ISCSI_COUNT_LAUNCH();
+  }
+  template <int KC>
+  void restart_t() {
+    const size_t sm = sizeof(double) * (size_t)maxsub * KC;
+    const int nk = std::max(k, maxsub / 2);
+    for (int pass = 0; pass < 2; ++pass) {
+      double* src = pass == 0 ? V : W;
+      for (int j0 = 0; j0 < nk; j0 += KC) {
+        k_dav_restart_lincomb<KC><<<parts, kVecThreads, sm, st>>>(src, ctl, Y.as<double>(), maxsub, j0, N, tmp); ISCSI_COUNT_LAUNCH();
+      }
+      k_dav_restart_copy<<<parts, kVecThreads, 0, st>>>(src, tmp, ctl, N); ISCSI_COUNT_LAUNCH();
+    }
+    k_dav_restart_S<<<1, 256, 0, st>>>(ctl, S.as<double>(), maxsub, thetas.as<double>()); ISCSI_COUNT_LAUNCH();
+  }
+  void ritz() {
+    switch (kc) {
+      case 4: ritz_t<4>(); break;
+      case 8: ritz_t<8>(); break;
+      case 16: ritz_t<16>(); break;
+      default: ritz_t<32>(); break;
+    }
+  }
+  void transform() {
+    switch (kc) {
+      case 4: transform_t<4>(); break;
+      case 8: transform_t<8>(); break;
+      case 16: transform_t<16>(); break;
+      default: transform_t<32>(); break;
+    }
+  }
+  void restart() {
+    switch (kc) {
+      case 4: restart_t<4>(); break;
+      case 8: restart_t<8>(); break;
+      case 16: restart_t<16>(); break;
+      default: restart_t<32>(); break;
+    }
+  }
+  void project(const double* C, const int* gate = nullptr) {
+    switch (kc) {
+      case 4: project_t<4>(C, gate); break;
+      case 8: project_t<8>(C, gate); break;
+      case 16: project_t<16>(C, gate); break;
+      default: project_t<32>(C, gate); break;
+    }
+  }
+
+  // eigen-decomposition of S, Ritz vectors and residuals, convergence check
+  int evaluate() {
+    k_dav_eigh<<<1, 256, eig_smem, st>>>(ctl, S.as<double>(), maxsub, eigA.as<double>(), eigQ.as<double>(),
+                                         Y.as<double>(), maxsub, thetas.as<double>(), eig_smem ? 1 : 0); ISCSI_COUNT_LAUNCH();
+    ritz();
+    k_dav_check<<<1, 32, 0, st>>>(ctl, rr_part.as<double>(), parts); ISCSI_COUNT_LAUNCH();
+    ISCSI_CUDA(cudaGetLastError());
+    return kOk;
+  }
+
+  // orthonormalise the k columns of T against V[0:m] and among themselves
+  int orthonormalise_block(bool set_norms) {
+    if (set_norms) {
+      dots(T, nullptr, k, T, k, G.as<double>());
+      k_dav_set_nrm0<<<1, 32, 0, st>>>(ctl, G.as<double>()); ISCSI_COUNT_LAUNCH();
+    }
+    // Gram-Schmidt against the basis; the second pass runs only when needed
+    dots(V, &ctl->m, 0, T, k, C1.as<double>());
+    project(C1.as<double>());
+    dots(T, nullptr, k, T, k, G.as<double>());
+    k_dav_reorth<<<1, 32, 0, st>>>(ctl, G.as<double>()); ISCSI_COUNT_LAUNCH();
+    dots(V, &ctl->m, 0, T, k, C1.as<double>(), &ctl->reorth);
+    project(C1.as<double>(), &ctl->reorth);
+    dots(T, nullptr, k, T, k, G.as<double>(), &ctl->reorth);
+    // Cholesky QR within the block, twice
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass) dots(T, nullptr, k, T, k, G.as<double>());
+      k_dav_cholqr<<<1, 32, 0, st>>>(ctl, G.as<double>(), Rinv.as<double>(), pass == 0 ? 1 : 0); ISCSI_COUNT_LAUNCH();
+      transform();
+    }
+    ISCSI_CUDA(cudaGetLastError());
+    return kOk;
+  }
+
+  // one iteration after an evaluation: expand the basis, evaluate again
+  int iteration(int prec) {
+    // Olsen's epsilon from the Ritz vectors of the last evaluation (X is
+    // overwritten by a restart below only through V, not X)
+    k_dav_olsen_dots<<<parts, kVecThreads, 0, st>>>(R, X, ctx.diag.as<double>(), ctl, N, rr_part.as<double>()); ISCSI_COUNT_LAUNCH();
+    k_dav_olsen_eps<<<1, 32, 0, st>>>(ctl, rr_part.as<double>(), parts); ISCSI_COUNT_LAUNCH();
+    restart();
+    k_dav_precond<<<parts, kVecThreads, 0, st>>>(R, X, ctx.diag.as<double>(), ctl, N, T); ISCSI_COUNT_LAUNCH();
+    ISCSI_TRY(orthonormalise_block(true));
+    ISCSI_TRY(sigma_run(ctx, T, Wn, k, prec));
+    dots(V, &ctl->m, 0, Wn, k, C1.as<double>());
+    dots(T, nullptr, k, Wn, k, C2.as<double>());
+    k_dav_append_vec<<<parts, kVecThreads, 0, st>>>(V, W, T, Wn, ctl, N); ISCSI_COUNT_LAUNCH();
+    k_dav_append_S<<<1, 256, 0, st>>>(ctl, S.as<double>(), maxsub, C1.as<double>(), C2.as<double>()); ISCSI_COUNT_LAUNCH();
+    return evaluate();
+  }
+
+  // basis = the cnt orthonormal columns at V (cnt a multiple of k); W = H V in
+  // sigma calls of k vectors each (the call shape the captured iteration
+  // uses); S; evaluate
+  int start_from_basis(int prec, int cnt) {
+    for (int j0 = 0; j0 < cnt; j0 += k)
+      ISCSI_TRY(sigma_run(ctx, V + (size_t)j0 * N, W + (size_t)j0 * N, k, prec));
+    dots(V, nullptr, cnt, W, cnt, C1.as<double>());
+    k_dav_init_S<<<1, 256, 0, st>>>(ctl, S.as<double>(), maxsub, C1.as<double>(), cnt); ISCSI_COUNT_LAUNCH();
+    return evaluate();
+  }
+
+  // keep the lowest cnt Ritz vectors of the current basis and rebuild their
+  // images with the given precision (the switch from FP32 to FP64 sigma)
+  int collapse(int prec, int cnt) {
+    k_dav_request_restart<<<1, 32, 0, st>>>(ctl, cnt); ISCSI_COUNT_LAUNCH();
+    switch (kc) {
+      case 4: restart_v<4>(); break;
+      case 8: restart_v<8>(); break;
+      case 16: restart_v<16>(); break;
+      default: restart_v<32>(); break;
+    }
+    return start_from_basis(prec, cnt);
+  }
+  template <int KC>
+  void restart_v() {
+    const size_t sm = sizeof(double) * (size_t)maxsub * KC;
+    for (int j0 = 0; j0 < 2 * k; j0 += KC) {
+      k_dav_restart_lincomb<KC><<<parts, kVecThreads, sm, st>>>(V, ctl, Y.as<double>(), maxsub, j0, N, tmp); ISCSI_COUNT_LAUNCH();
+    }
+    k_dav_restart_copy<<<parts, kVecThreads, 0, st>>>(V, tmp, ctl, N); ISCSI_COUNT_LAUNCH();
+  }
+
+  int read_ctl(DavCtl& h) {
+    ISCSI_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(DavCtl), cudaMemcpyDeviceToHost, st));
+    ISCSI_CUDA(cudaStreamSynchronize(st));
     return kOk;
   }
 };
 
-int davidson_run(Context& ctx, int nroots, double tol, double* energies, double* vecs) {
+// kernel nodes of a captured graph (counted per replay in the launch statistics)
+long long graph_kernels(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+  long long c = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++c;
+  }
+  return c;
+}
+
+struct IterGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t x = nullptr;
+  long long kernels = 0;
+  bool failed = false;
+  IterGraph() = default;
+  IterGraph(const IterGraph&) = delete;
+  IterGraph& operator=(const IterGraph&) = delete;
+  ~IterGraph() {
+    if (x) cudaGraphExecDestroy(x);
+    if (g) cudaGraphDestroy(g);
+  }
+};
+
+}  // namespace
+
+static int davidson_body(Context& ctx, int nroots, double tol, double* energies, double* vecs) {
   const Options& opt = options();
-  long long N = ctx.ndet;
-  int k = nroots;
-  int maxsub = (int)std::min<long long>(N, (long long)std::max(2, opt.max_subspace) * k);
-  // the Ritz kernels stage the m x k coefficient block in 48 KB of shared memory
-  maxsub = std::min(maxsub, 6144 / k);
-  if (maxsub < 2 * k && N > k) maxsub = std::min<long long>(N, 2 * k);
-  if (maxsub < k) maxsub = k;
-  if (k > 32) {
+  const long long N = ctx.ndet;
+  const int k = nroots;
+  if (k > kMaxRoots) {
     set_error("iscsi_davidson: at most 32 roots");
     return kErrArg;
   }
-  DavWork dw(ctx);
-  cudaStream_t st = dw.st;
-  ISCSI_TRY(ctx.dv_V.grow(sizeof(double) * (size_t)maxsub * N));
-  ISCSI_TRY(ctx.dv_W.grow(sizeof(double) * (size_t)maxsub * N));
-  ISCSI_TRY(ctx.dv_tmp.grow(sizeof(double) * (size_t)2 * k * N));  // X and R
-  DevBuf dT, dth, dY, dscale, dYall, restart;
-  ISCSI_TRY(dT.alloc(sizeof(double) * (size_t)k * N));
-  ISCSI_TRY(restart.alloc(sizeof(double) * (size_t)std::max(k, maxsub / 2) * N));
-  double* V = ctx.dv_V.as<double>();
-  double* W = ctx.dv_W.as<double>();
-  double* X = ctx.dv_tmp.as<double>();
-  double* R = X + (size_t)k * N;
-  double* T = dT.as<double>();
+  int maxsub = (int)std::min<long long>(N, (long long)std::max(2, opt.max_subspace) * k);
+  maxsub = std::min(maxsub, 384);
+  if (maxsub < 2 * k && N > k) maxsub = (int)std::min<long long>(N, 2 * k);
+  if (maxsub < k) maxsub = k;
+  Dav d(ctx, k, maxsub);
+  cudaStream_t st = d.st;
+  ISCSI_TRY(d.setup());
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
 
-  // --- initial guesses
+  DavCtl h;
+  std::memset(&h, 0, sizeof(h));
+  h.k = k;
+  h.maxsub = maxsub;
+  h.tol = tol;
+  h.etol = opt.etol;
+  h.olsen = opt.olsen ? 1 : 0;
+  ISCSI_CUDA(cudaMemcpyAsync(d.ctl, &h, sizeof(DavCtl), cudaMemcpyHostToDevice, st));
+
+  // --- start vectors: the caller's (orthonormalised) or the k lowest diagonal entries
   if (vecs && opt.guess_from_vecs) {
-    ISCSI_CUDA(cudaMemcpyAsync(V, vecs, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, st));
+    ISCSI_CUDA(cudaMemcpyAsync(d.T, vecs, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, st));
+    ISCSI_TRY(d.orthonormalise_block(true));  // the basis is still empty (m = 0)
+    ISCSI_TRY(d.read_ctl(h));
+    for (int j = 0; j < k; ++j)
+      if (!h.active[j]) {
+        set_error("iscsi_davidson: start vectors are linearly dependent");
+        return kErrArg;
+      }
+    ISCSI_CUDA(cudaMemcpyAsync(d.V, d.T, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, st));
   } else {
-    std::vector<double> d(N);
-    ISCSI_CUDA(cudaMemcpyAsync(d.data(), ctx.diag.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    std::vector<double> dg(N);
+    ISCSI_CUDA(cudaMemcpyAsync(dg.data(), ctx.diag.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
     ISCSI_CUDA(cudaStreamSynchronize(st));
     std::vector<long long> idx(N);
     for (long long i = 0; i < N; ++i) idx[i] = i;
     std::partial_sort(idx.begin(), idx.begin() + k, idx.end(),
-                      [&](long long a, long long b) { return d[a] < d[b] || (d[a] == d[b] && a < b); });
+                      [&](long long a, long long b) { return dg[a] < dg[b] || (dg[a] == dg[b] && a < b); });
     idx.resize(k);
     DevBuf didx;
     ISCSI_TRY(didx.alloc(sizeof(long long) * k));
     ISCSI_CUDA(cudaMemcpyAsync(didx.p, idx.data(), sizeof(long long) * k, cudaMemcpyHostToDevice, st));
-    k_unit_vectors<<<dw.blocks, 256, 0, st>>>(V, didx.as<long long>(), k, N);
+    k_unit_vectors<<<kVecBlocks, kVecThreads, 0, st>>>(d.V, didx.as<long long>(), k, N); ISCSI_COUNT_LAUNCH();
     ISCSI_CUDA(cudaGetLastError());
     ISCSI_CUDA(cudaStreamSynchronize(st));
-  }
-  // orthonormalise the start block (Gram-Schmidt, one vector at a time)
-  auto normalise = [&](double* vv, int cnt, std::vector<double>& norms) -> int {
-    std::vector<double> g;
-    ISCSI_TRY(dw.dots(vv, cnt, vv, cnt, g));
-    norms.resize(cnt);
-    std::vector<double> f(cnt);
-    for (int j = 0; j < cnt; ++j) {
-      norms[j] = std::sqrt(std::max(0.0, g[(size_t)j * cnt + j]));
-      f[j] = norms[j] > 0 ? 1.0 / norms[j] : 0.0;
-    }
-    ISCSI_TRY(dw.upload(f, dscale));
-    k_scale_vecs<<<dw.blocks, 256, 0, st>>>(vv, dscale.as<double>(), cnt, N);
-    ISCSI_CUDA(cudaGetLastError());
-    ISCSI_CUDA(cudaStreamSynchronize(st));
-    return kOk;
-  };
-  {
-    std::vector<double> nrm;
-    for (int j = 0; j < k; ++j) {
-      ISCSI_TRY(dw.orthogonalise(V, j, V + (size_t)j * N, 1));
-      ISCSI_TRY(normalise(V + (size_t)j * N, 1, nrm));
-      if (nrm[0] < 1e-12) {
-        set_error("iscsi_davidson: start vectors are linearly dependent");
-        return kErrArg;
-      }
-    }
   }
 
-  bool mixed = (opt.precision == 32);
+  const bool mixed = (opt.precision == 32);
   ctx.last_davidson_fp32_iters = 0;
+  ctx.last_davidson_graph = 0;
   int prec = mixed ? 32 : 64;
-  int m = k;
-  ISCSI_TRY(sigma_run(ctx, V, W, k, prec));
-  std::vector<double> S((size_t)maxsub * maxsub, 0.0);
-  auto update_S = [&](int from, int to) -> int {
-    // blk[i][j - from] = V_i . W_j for i < to, from <= j < to
-    std::vector<double> blk;
-    ISCSI_TRY(dw.dots(V, to, W + (size_t)from * N, to - from, blk));
-    int w_ = to - from;
-    for (int i = 0; i < from; ++i)
-      for (int j = from; j < to; ++j) S[(size_t)i * maxsub + j] = S[(size_t)j * maxsub + i] = blk[(size_t)i * w_ + (j - from)];
-    // inside the new block the two products V_i.W_j and V_j.W_i are averaged
-    for (int i = from; i < to; ++i)
-      for (int j = i; j < to; ++j) {
-        double x = 0.5 * (blk[(size_t)i * w_ + (j - from)] + blk[(size_t)j * w_ + (i - from)]);
-        S[(size_t)i * maxsub + j] = S[(size_t)j * maxsub + i] = x;
-      }
-    return kOk;
-  };
-  ISCSI_TRY(update_S(0, m));
+  ISCSI_TRY(d.start_from_basis(prec, k));
 
-  std::vector<double> theta_prev(k, 0.0), theta(k, 0.0), rnorm(k, 0.0);
+  IterGraph graphs[2];  // [0]: FP64 sigma, [1]: FP32 sigma
+  auto run_iteration = [&](int p) -> int {
+    IterGraph& G = graphs[p == 32 ? 1 : 0];
+    if (opt.use_graph && !G.x && !G.failed) {
+      // capture one iteration; on any failure fall back to direct launches
+      long long before = g_launch_count;
+      ctx.capturing = true;
+      cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+      int rc = ce == cudaSuccess ? d.iteration(p) : kErrCuda;
+      cudaGraph_t g = nullptr;
+      cudaError_t ee = ce == cudaSuccess ? cudaStreamEndCapture(st, &g) : ce;
+      ctx.capturing = false;
+      g_launch_count = before;
+      if (ce == cudaSuccess && rc == kOk && ee == cudaSuccess && g &&
+          cudaGraphInstantiate(&G.x, g, 0) == cudaSuccess) {
+        G.g = g;
+        G.kernels = graph_kernels(g);
+      } else {
+        if (g) cudaGraphDestroy(g);
+        G.x = nullptr;
+        G.failed = true;
+        cudaGetLastError();
+      }
+    }
+    if (G.x) {
+      ISCSI_CUDA(cudaGraphLaunch(G.x, st));
+      g_launch_count += G.kernels;
+      ctx.last_davidson_graph = 1;
+      return kOk;
+    }
+    return d.iteration(p);
+  };
+
   double best_r = 1e300;
   int best_it = 0;
   int status = kErrNoConv;
   int iter = 0;
+  ctx.last_davidson_rhist.clear();
   for (iter = 1; iter <= opt.maxiter; ++iter) {
-    // Rayleigh-Ritz in the subspace
-    std::vector<double> Sm((size_t)m * m);
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) Sm[(size_t)i * m + j] = S[(size_t)i * maxsub + j];
-    std::vector<double> w, Y;
-    jacobi_eigh(Sm, m, w, Y);
-    std::vector<double> Yk((size_t)m * k);
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < k; ++j) Yk[(size_t)i * k + j] = Y[(size_t)i * m + j];
-    for (int j = 0; j < k; ++j) theta[j] = w[j];
-    ISCSI_TRY(dw.upload(Yk, dY));
-    ISCSI_TRY(dw.upload(theta, dth));
-    k_ritz<<<dw.blocks, 256, sizeof(double) * m * k, st>>>(V, W, m, dY.as<double>(), k, dth.as<double>(), N, X, R);
-    ISCSI_CUDA(cudaGetLastError());
-    std::vector<double> rr;
-    ISCSI_TRY(dw.dots(R, k, R, k, rr));
-    double rmax = 0.0, dmax = 0.0;
-    bool finite = true;
-    for (int j = 0; j < k; ++j) {
-      rnorm[j] = std::sqrt(std::max(0.0, rr[(size_t)j * k + j]));
-      rmax = std::max(rmax, rnorm[j]);
-      dmax = std::max(dmax, std::fabs(theta[j] - theta_prev[j]));
-      if (!std::isfinite(theta[j]) || !std::isfinite(rnorm[j])) finite = false;
-    }
-    if (!finite) {
+    ISCSI_TRY(d.read_ctl(h));
+    ctx.last_davidson_rhist.push_back(h.rmax);
+    if (h.status & kStatusNonFinite) {
       set_error("iscsi_davidson: NaN or Inf in the subspace");
       status = kErrNan;
       break;
     }
-    bool fp32_phase = mixed && prec == 32;
-    // the FP32 phase ends at switch_tol or when its residual stops improving
-    // (the FP32 rounding floor): best residual not improved by 10% in 8 iterations
-    if (fp32_phase) {
-      if (rmax < 0.9 * best_r) {
-        best_r = rmax;
-        best_it = iter;
-      }
-    }
-    if (fp32_phase && (rmax <= opt.switch_tol || iter - best_it >= 8)) {
-      // collapse to the Ritz vectors and recompute their images in FP64
-      ISCSI_CUDA(cudaMemcpyAsync(V, X, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, st));
-      std::vector<double> nrm;
-      for (int j = 0; j < k; ++j) {
-        ISCSI_TRY(dw.orthogonalise(V, j, V + (size_t)j * N, 1));
-        ISCSI_TRY(normalise(V + (size_t)j * N, 1, nrm));
-      }
-      prec = 64;
-      ctx.last_davidson_fp32_iters = iter;
-      m = k;
-      ISCSI_TRY(sigma_run(ctx, V, W, k, prec));
-      ISCSI_TRY(update_S(0, m));
-      theta_prev = theta;
-      continue;
-    }
-    if (!fp32_phase && iter > 1 && rmax <= tol && dmax <= opt.etol) {
+    const bool fp32_phase = mixed && prec == 32;
+    if (!fp32_phase && (h.status & kStatusConverged)) {
       status = kOk;
       break;
     }
-    theta_prev = theta;
-    // thick restart when the basis is full: keep the lowest nkeep Ritz pairs
-    if (m + k > maxsub) {
-      int nkeep = std::max(k, std::min(m - k, maxsub / 2));
-      std::vector<double> Yall((size_t)m * nkeep);
-      for (int i = 0; i < m; ++i)
-        for (int j = 0; j < nkeep; ++j) Yall[(size_t)i * nkeep + j] = Y[(size_t)i * m + j];
-      ISCSI_TRY(dw.upload(Yall, dYall));
-      for (int pass = 0; pass < 2; ++pass) {
-        double* src = pass == 0 ? V : W;
-        for (int j0 = 0; j0 < nkeep; j0 += 32) {
-          int cnt = std::min(32, nkeep - j0);
-          k_lincomb<<<dw.blocks, 256, sizeof(double) * m * cnt, st>>>(src, m, dYall.as<double>(), nkeep, j0, cnt, N,
-                                                                     restart.as<double>() + (size_t)j0 * N);
-        }
-        ISCSI_CUDA(cudaGetLastError());
-        ISCSI_CUDA(cudaMemcpyAsync(src, restart.p, sizeof(double) * nkeep * N, cudaMemcpyDeviceToDevice, st));
-      }
-      std::fill(S.begin(), S.end(), 0.0);
-      for (int j = 0; j < nkeep; ++j) S[(size_t)j * maxsub + j] = w[j];
-      m = nkeep;
-      ISCSI_CUDA(cudaStreamSynchronize(st));
-    }
-    // corrections from the unconverged residuals
-    k_precondition<<<dw.blocks, 256, 0, st>>>(R, ctx.diag.as<double>(), dth.as<double>(), k, N, T);
-    ISCSI_CUDA(cudaGetLastError());
-    int added = 0;
-    std::vector<double> nrm0, nrm;
-    for (int j = 0; j < k; ++j) {
-      if (rnorm[j] <= tol * 0.1) continue;  // converged root: no new direction
-      double* tj = T + (size_t)j * N;
-      double* dst = V + (size_t)(m + added) * N;
-      ISCSI_CUDA(cudaMemcpyAsync(dst, tj, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-      ISCSI_TRY(normalise(dst, 1, nrm0));
-      if (nrm0[0] == 0.0) continue;
-      ISCSI_TRY(dw.orthogonalise(V, m + added, dst, 1));
-      ISCSI_TRY(normalise(dst, 1, nrm));
-      if (nrm[0] < 1e-8) continue;  // no new direction
-      ++added;
-    }
-    if (added == 0) {
+    if (!fp32_phase && (h.status & kStatusNoDirection)) {
       // the subspace cannot grow: report what we have
-      status = (rmax <= tol) ? kOk : kErrNoConv;
+      status = (h.rmax <= tol) ? kOk : kErrNoConv;
       break;
     }
-    ISCSI_TRY(sigma_run(ctx, V + (size_t)m * N, W + (size_t)m * N, added, prec));
-    ISCSI_TRY(update_S(m, m + added));
-    m += added;
+    if (fp32_phase) {
+      // the FP32 phase ends at switch_tol, or when its residual stops
+      // improving near the FP32 rounding floor (best residual within 1e3 of
+      // switch_tol and not improved by 10% in 8 iterations; early plateaus of
+      // the iteration itself do not count)
+      if (h.rmax < 0.9 * best_r) {
+        best_r = h.rmax;
+        best_it = iter;
+      }
+      const bool stalled = iter - best_it >= 8 && best_r <= 1e3 * opt.switch_tol;
+      if (h.rmax <= opt.switch_tol || stalled || (h.status & kStatusNoDirection)) {
+        // keep the lowest Ritz vectors (2k when the basis holds them) and
+        // recompute their images with the FP64 sigma
+        const int keep = h.m >= 2 * k ? 2 * k : k;
+        prec = 64;
+        ctx.last_davidson_fp32_iters = iter;
+        ISCSI_TRY(d.collapse(prec, keep));
+        continue;
+      }
+    }
+    ISCSI_TRY(run_iteration(prec));
   }
-  for (int j = 0; j < k; ++j) energies[j] = theta[j];
-  if (vecs) ISCSI_CUDA(cudaMemcpyAsync(vecs, X, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, st));
+  ISCSI_TRY(d.read_ctl(h));
+  if (status == kErrNoConv && prec == 64 && (h.status & kStatusConverged)) status = kOk;
+  for (int j = 0; j < k; ++j) energies[j] = h.theta[j];
+  if (vecs) ISCSI_CUDA(cudaMemcpyAsync(vecs, d.X, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, st));
   cudaEventRecord(e1, st);
   ISCSI_CUDA(cudaStreamSynchronize(st));
   float ms = 0;
@@ -484,9 +1086,35 @@ int davidson_run(Context& ctx, int nroots, double tol, double* energies, double*
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ctx.last_davidson_ms = ms;
-  ctx.last_davidson_iters = iter;
+  ctx.last_davidson_iters = h.iter;
   if (status == kErrNoConv) set_error("iscsi_davidson: no convergence within maxiter");
   return status;
+}
+
+// The iteration runs on a stream of its own (the legacy default stream, which
+// callers often use, cannot be captured into a graph), ordered after the
+// caller's stream on entry and before it on exit.
+int davidson_run(Context& ctx, int nroots, double tol, double* energies, double* vecs) {
+  cudaStream_t user = stream();
+  cudaStream_t ds = nullptr;
+  cudaEvent_t ev = nullptr;
+  ISCSI_CUDA(cudaStreamCreateWithFlags(&ds, cudaStreamNonBlocking));
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaStreamDestroy(ds);
+    set_error("iscsi_davidson: cudaEventCreate failed");
+    return kErrCuda;
+  }
+  cudaEventRecord(ev, user);
+  cudaStreamWaitEvent(ds, ev, 0);
+  set_stream(ds);
+  int rc = davidson_body(ctx, nroots, tol, energies, vecs);
+  cudaEventRecord(ev, ds);
+  cudaStreamWaitEvent(user, ev, 0);
+  set_stream(user);
+  cudaStreamSynchronize(ds);
+  cudaStreamDestroy(ds);
+  cudaEventDestroy(ev);
+  return rc;
 }
 
 }  // namespace iscsi

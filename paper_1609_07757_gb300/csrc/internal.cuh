@@ -213,9 +213,12 @@ struct Context {
   int ntimed = 0;
   int last_davidson_iters = 0;
   int last_davidson_fp32_iters = 0;  // iterations of the FP32 phase (mixed precision)
+  std::vector<double> last_davidson_rhist;  // largest residual norm per iteration
   double last_davidson_ms = 0;
   // Davidson buffers
   DevBuf dv_V, dv_W, dv_tmp, dv_small;
+  bool capturing = false;  // a CUDA graph capture of a Davidson iteration is in progress
+  int last_davidson_graph = 0;  // 1: the last Davidson run replayed captured iterations
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   ~Context();
 };
@@ -229,6 +232,7 @@ struct Options {
   double switch_tol = 1e-5;
   int guess_from_vecs = 0;
   int use_graph = 1;
+  int olsen = 1;        // Olsen's correction in the Davidson preconditioner
   int phase_timing = 0;
   int fp64_tc = 1;      // FP64 opposite-spin contraction on the tensor cores (exact bf16 slices)
   int samespin_tc = 1;  // same for the same-spin blocks large enough for a 128 x 64 tile

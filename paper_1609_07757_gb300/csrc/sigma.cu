@@ -664,7 +664,7 @@ static int ensure_fp32_matrices(Context& ctx) {
 }
 
 static int timing_event(Context& ctx, int call, int phase, cudaStream_t st) {
-  if (!options().phase_timing || call >= Context::kMaxTimed) return kOk;
+  if (!options().phase_timing || ctx.capturing || call >= Context::kMaxTimed) return kOk;
   size_t idx = (size_t)call * (Context::kPhases + 1) + phase;
   if (ctx.tev.size() <= idx) ctx.tev.resize((size_t)Context::kMaxTimed * (Context::kPhases + 1), nullptr);
   if (!ctx.tev[idx]) ISCSI_CUDA(cudaEventCreate(&ctx.tev[idx]));
@@ -743,7 +743,7 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
   else if (ss_tc)
     ISCSI_TRY(samespin_tc32(ctx, reinterpret_cast<const float*>(c), reinterpret_cast<float*>(sigma), nvec));
   ISCSI_TRY(timing_event(ctx, call, 4, st));
-  if (options().phase_timing && call < Context::kMaxTimed) ctx.ntimed++;
+  if (options().phase_timing && !ctx.capturing && call < Context::kMaxTimed) ctx.ntimed++;
   (void)s_out;
   return kOk;
 }

@@ -311,3 +311,67 @@ def test_fp32_tensor_core_and_native_paths(n, na, nb, k, tau):
         for s in (s_tc[v], s_nat[v]):
             assert np.linalg.norm(s - s64[v]) <= REL32 * np.linalg.norm(s64[v])
             assert np.abs(s[rows] - ref).max() <= REL32 * np.abs(s64[v]).max()
+
+
+def _stats():
+    return L.iscsi_stats()
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_davidson_graph_and_direct_launches_agree(use_graph):
+    # one Davidson iteration is replayed from a captured CUDA graph (default)
+    # or launched directly; both reach the dense eigenvalues, and small
+    # subspaces force thick restarts
+    n, tau = 10, 1e-14
+    h1, eri = make_integrals(n, 5, ell=3.0, nchol=20)
+    o = Oracle(n, 2, 2, 4, tau, h1, eri)
+    w = np.linalg.eigvalsh(o.dense_h())
+    L.iscsi_init(n, 2, 2, 4, h1, eri, tau)
+    L.iscsi_set_option("use_graph", use_graph)
+    L.iscsi_set_option("max_subspace", 4)
+    try:
+        st, e = L.iscsi_davidson(4, 1e-8)
+        s = _stats()
+    finally:
+        L.iscsi_set_option("use_graph", 1)
+        L.iscsi_set_option("max_subspace", 12)
+    assert st == 0
+    assert np.abs(e - w[:4]).max() <= 1e-10
+    assert s["davidson_graph"] == use_graph
+    assert s["davidson_iters"] > 4
+
+
+def test_davidson_many_roots_and_start_vectors():
+    # 12 roots of a truncated space; a second run started from the first run's
+    # vectors converges in a few iterations to the same energies
+    n, k, tau = 12, 2, 1e-12
+    h1, eri = make_integrals(n, 710, ell=3.0, nchol=12)
+    o = Oracle(n, 2, 2, k, tau, h1, eri)
+    w = np.linalg.eigvalsh(o.dense_h())
+    L.iscsi_init(n, 2, 2, k, h1, eri, tau)
+    vecs = torch.zeros((12, o.ndet), dtype=torch.float64, device="cuda")
+    st, e = L.iscsi_davidson(12, 1e-8, vecs)
+    assert st == 0
+    assert np.abs(e - w[:12]).max() <= 1e-10
+    it1 = _stats()["davidson_iters"]
+    L.iscsi_set_option("guess_from_vecs", 1)
+    try:
+        st2, e2 = L.iscsi_davidson(12, 1e-8, vecs)
+    finally:
+        L.iscsi_set_option("guess_from_vecs", 0)
+    assert st2 == 0
+    assert np.abs(e2 - w[:12]).max() <= 1e-10
+    assert _stats()["davidson_iters"] < it1
+
+
+def test_davidson_whole_space():
+    # fewer determinants than the subspace can hold: the basis reaches the
+    # whole space and the iteration stops with the exact spectrum
+    n = 4
+    h1, eri = make_integrals(n, 720)
+    o = Oracle(n, 1, 1, 2, 0.0, h1, eri)
+    w = np.linalg.eigvalsh(o.dense_h())
+    L.iscsi_init(n, 1, 1, 2, h1, eri, 0.0)
+    st, e = L.iscsi_davidson(3, 1e-9)
+    assert st == 0
+    assert np.abs(e - w[:3]).max() <= 1e-10
