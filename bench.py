@@ -51,6 +51,8 @@ WORKLOADS = {
     "cisdt_n50": dict(n=50, na=2, nb=2, kmax=3, ell=5.0, nchol=20, box=True, seed=2000, tau=1e-14),
     "cisdt_n150": dict(n=150, na=2, nb=2, kmax=3, ell=5.0, nchol=20, box=True, seed=2000, tau=1e-14),
     "cisdt_n200": dict(n=200, na=2, nb=2, kmax=3, ell=5.0, nchol=20, box=True, seed=2000, tau=1e-14),
+    # the batching form's block Davidson (16 roots, FP32-mixed)
+    "cisdt_n120": dict(n=120, na=2, nb=2, kmax=3, ell=5.0, nchol=20, box=True, seed=4500, tau=1e-14),
 }
 
 
@@ -353,6 +355,81 @@ def run_precision_form(name, nroots=3, tol=1e-8):
     return out
 
 
+def run_batching(count=64, reps=5, tau=1e-14, nroots=1):
+    """The batching form: `count` independent full-CI instances (2 alpha + 2 beta
+    electrons, orbital counts uniform on [20, 80], each with its own seeded
+    integrals of the 10-orbital workload's generator).  sigma for all of them
+    one context at a time (one iscsi_sigma per instance) against one
+    iscsi_batch_sigma call (merged contractions, replayed CUDA graph), FP64 and
+    FP32; then the lowest root of every instance by Davidson, one at a time."""
+    import torch
+
+    from paper_1609_07757_gb300 import _lib as L
+    from paper_1609_07757_gb300.synthetic import make_integrals, multi_instance_sizes, unit_vector
+
+    sizes = [int(x) for x in multi_instance_sizes(count)]
+    hs, cs, ss, upd, ndets = [], [], [], 0.0, 0
+    t0 = time.time()
+    for i, n in enumerate(sizes):
+        h1, eri = make_integrals(n, 4000 + i, ell=3.0, nchol=20)
+        L.iscsi_init(n, 2, 2, 4, h1, eri, tau)
+        hs.append(L.iscsi_ctx_current())
+        nd = L.iscsi_ndet()
+        ndets += nd
+        upd += L.iscsi_updates_per_sigma()
+        c = torch.tensor(unit_vector(nd, 7 + i), dtype=torch.float64, device="cuda")
+        cs.append(c)
+        ss.append(torch.empty_like(c))
+    init_s = time.time() - t0
+    out = {"instances": count, "orbitals": [min(sizes), max(sizes)], "mean_ndet": ndets / count,
+           "updates_per_round": upd, "init_s": round(init_s, 2)}
+    for prec in (64, 32):
+        L.iscsi_set_option("precision", prec)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+        def single():
+            for h, c, s in zip(hs, cs, ss):
+                L.iscsi_ctx_use(h)
+                L.iscsi_sigma(c, s, 1)
+
+        def batched():
+            L.iscsi_batch_sigma(hs, cs, ss, 1)
+
+        res = {}
+        for name, fn in (("one_at_a_time", single), ("batched", batched)):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            w0 = time.time()
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            wall = (time.time() - w0) / reps
+            ms = e0.elapsed_time(e1) / reps
+            res[name] = {"ms_per_round": round(ms, 3), "host_wall_ms_per_round": round(wall * 1e3, 3),
+                         "instances_per_s": round(count / (ms * 1e-3), 1),
+                         "sigma_per_s": round(count / (ms * 1e-3), 1),
+                         "GUpdates_per_s": round(upd / (ms * 1e-3) / 1e9, 1)}
+        res["speedup"] = round(res["one_at_a_time"]["ms_per_round"] / res["batched"]["ms_per_round"], 3)
+        out["fp%d" % prec] = res
+    L.iscsi_set_option("precision", 64)
+    # the lowest root of every instance, one Davidson per instance (FP64, device-resident)
+    t0 = time.time()
+    iters = 0
+    for h in hs:
+        L.iscsi_ctx_use(h)
+        st, e = L.iscsi_davidson(nroots, 1e-8)
+        iters += L.iscsi_stats()["davidson_iters"]
+    torch.cuda.synchronize()
+    dt = time.time() - t0
+    out["davidson_fp64_one_at_a_time"] = {"roots_per_instance": nroots, "wall_s": round(dt, 2),
+                                          "instances_per_s": round(count / dt, 2), "iterations": iters}
+    L.iscsi_finalize()
+    return out
+
+
 def cpu_baseline(wl, tau, target_s=15.0, steps=1):
     """The oracle, as it stands, on a bounded sample of rows of the same workload."""
     import numpy as np
@@ -426,6 +503,8 @@ def main():
     ap.add_argument("--mixed-workload", default="fci_n100", choices=sorted(WORKLOADS) + ["none"],
                     help="workload of the FP32-mixed vs FP64 Davidson comparison added to the line")
     ap.add_argument("--mixed-roots", type=int, default=3)
+    ap.add_argument("--batching", type=int, default=0, metavar="COUNT",
+                    help="add the batching form: COUNT full-CI instances, batched vs one at a time")
     ap.add_argument("--updates", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     ws, rank, local = dist_env()
@@ -456,6 +535,8 @@ def main():
     if rank == 0 and ws == 1 and args.mixed_workload != "none":
         # the precision form: FP32-mixed vs FP64 Davidson, |dE| and speedup (untimed by the contract)
         line["mixed_precision"] = run_precision_form(args.mixed_workload, args.mixed_roots)
+    if rank == 0 and ws == 1 and args.batching > 0:
+        line["batching"] = run_batching(args.batching)
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
             tau = args.tau if args.tau is not None else wl["tau"]

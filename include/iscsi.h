@@ -245,6 +245,30 @@ ISCSI_API const char* iscsi_last_error(void);
 ISCSI_API void iscsi_finalize(void);
 
 /*
+ * Batching form: sigma_i = H_tau(context i) c_i for count independent
+ * contexts (many problems of uneven size, e.g. full CI in different orbital
+ * counts) in one call.  The paper treats one problem at a time; this entry
+ * point has no counterpart there.  handles: host [count] distinct context
+ * handles (iscsi_ctx_current); cs, sigmas: host [count] arrays of device
+ * pointers, each FP64 [nvec][ndet_i] vector-major as in iscsi_sigma (the
+ * caller owns them).  The precision option applies to all.  The tensor-core
+ * contractions of all contexts run as one launch each; from the second call
+ * with the same handles, pointers, nvec and precision the whole batch is
+ * replayed from one captured CUDA graph (option "use_graph").  Asynchronous
+ * on the library stream; the current context is unchanged.  A bounded
+ * device wait that runs out in a merged launch is reported by
+ * iscsi_batch_check.
+ * Errors: ISCSI_E_ARG (count or nvec < 1, NULL array or vector, unknown or
+ * repeated handle), ISCSI_E_NOMEM, ISCSI_E_CUDA.
+ */
+ISCSI_API iscsi_status iscsi_batch_sigma(const int* handles, const void* const* cs, void* const* sigmas, int count,
+                                         int nvec);
+
+/* Synchronises and returns ISCSI_E_WAIT if a bounded device wait of the last
+   batch's merged launches ran out, else ISCSI_OK. */
+ISCSI_API iscsi_status iscsi_batch_check(void);
+
+/*
  * Several contexts (batching).  iscsi_init creates a context and makes it
  * current; iscsi_ctx_current returns its handle (> 0), iscsi_ctx_use makes
  * another one current, iscsi_ctx_destroy frees one.

@@ -65,6 +65,8 @@ def load(build_if_missing=True):
         "iscsi_ctx_current": (c_int, []),
         "iscsi_ctx_use": (c_int, [c_int]),
         "iscsi_ctx_destroy": (c_int, [c_int]),
+        "iscsi_batch_sigma": (c_int, [vp, vp, vp, c_int, c_int]),
+        "iscsi_batch_check": (c_int, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -118,6 +120,21 @@ def iscsi_init(norb, nalpha, nbeta, max_excitation, h1, eri, tau):
 
 def iscsi_sigma(c, sigma, nvec=1):
     return _check(load().iscsi_sigma(_dev(c), _dev(sigma), int(nvec)))
+
+
+def iscsi_batch_sigma(handles, cs, sigmas, nvec=1):
+    """sigma_i = H(context handles[i]) c_i for all i in one call (device tensors)."""
+    n = len(handles)
+    if len(cs) != n or len(sigmas) != n:
+        raise ValueError("handles, cs and sigmas differ in length")
+    h = (ctypes.c_int * n)(*[int(x) for x in handles])
+    c = (ctypes.c_void_p * n)(*[_dev(x) for x in cs])
+    s = (ctypes.c_void_p * n)(*[_dev(x) for x in sigmas])
+    return _check(load().iscsi_batch_sigma(h, c, s, n, int(nvec)))
+
+
+def iscsi_batch_check():
+    return _check(load().iscsi_batch_check())
 
 
 def iscsi_sigma_noalloc(c, sigma):

@@ -313,9 +313,38 @@ double iscsi_updates_per_sigma(void) {
 const char* iscsi_last_error(void) { return last_error(); }
 
 void iscsi_finalize(void) {
+  batch_reset();
   g_ctx.clear();
   g_current = 0;
 }
+
+iscsi_status iscsi_batch_sigma(const int* handles, const void* const* cs, void* const* sigmas, int count, int nvec) {
+  if (count < 1 || nvec < 1 || !handles || !cs || !sigmas) {
+    set_error("iscsi_batch_sigma: invalid argument");
+    return ISCSI_E_ARG;
+  }
+  std::vector<Context*> ctxs(count);
+  std::vector<const double*> c(count);
+  std::vector<double*> s(count);
+  for (int i = 0; i < count; ++i) {
+    auto it = g_ctx.find(handles[i]);
+    if (it == g_ctx.end() || !cs[i] || !sigmas[i]) {
+      set_error("iscsi_batch_sigma: unknown handle or NULL vector at position " + std::to_string(i));
+      return ISCSI_E_ARG;
+    }
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) {
+        set_error("iscsi_batch_sigma: a context appears twice");
+        return ISCSI_E_ARG;
+      }
+    ctxs[i] = it->second.get();
+    c[i] = static_cast<const double*>(cs[i]);
+    s[i] = static_cast<double*>(sigmas[i]);
+  }
+  return batch_sigma(ctxs, c, s, nvec, options().precision == 32 ? 32 : 64);
+}
+
+iscsi_status iscsi_batch_check(void) { return batch_check(); }
 
 int iscsi_ctx_current(void) { return current() ? g_current : 0; }
 
@@ -334,6 +363,7 @@ iscsi_status iscsi_ctx_destroy(int handle) {
     set_error("iscsi_ctx_destroy: unknown handle");
     return ISCSI_E_ARG;
   }
+  batch_reset();  // a cached batch may refer to this context
   g_ctx.erase(it);
   if (g_current == handle) g_current = 0;
   return ISCSI_OK;

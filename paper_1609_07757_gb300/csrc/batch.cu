@@ -1,0 +1,243 @@
+// batch.cu -- the sigma step for many independent contexts at once (the
+// batching form: many instances of uneven orbital counts in one pass).
+//
+// Each phase of the sigma step runs for every context in turn, except the two
+// tensor-core contractions: the opposite-spin products of all contexts form
+// one problem list and run as one k_oz_gemm (or k_tc32_gemm) launch, and so do
+// the same-spin level-block products.  Problems keep their per-context
+// output addressing through a table of output bases (OzProblem::tb).  From the
+// second call with the same contexts, vectors, vector count and precision,
+// the whole sequence is replayed from one captured CUDA graph, so a batch of
+// any size costs one launch on the host.
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace iscsi {
+
+namespace {
+
+struct MergedJob {
+  std::vector<OzProblem> probs;
+  std::vector<OzSeg> segs;
+  std::vector<OzMaps> maps;
+  DevBuf d_probs, d_segs, d_maps, d_tbases;
+  std::vector<const OzJob*> src;
+  std::vector<long long> ver;
+  std::vector<void*> tbases;
+  int tiles = 0;
+};
+
+// one problem list over the given jobs; rebuilt only when a job changed
+int merge_jobs(MergedJob& mj, const std::vector<const OzJob*>& jobs, const std::vector<void*>& tbases,
+               cudaStream_t st) {
+  bool same = mj.src == jobs && mj.tbases == tbases;
+  for (size_t i = 0; same && i < jobs.size(); ++i) same = mj.ver[i] == jobs[i]->version;
+  if (same) return kOk;
+  mj.probs.clear();
+  mj.segs.clear();
+  mj.maps.clear();
+  mj.tiles = 0;
+  for (size_t i = 0; i < jobs.size(); ++i) {
+    const OzJob& J = *jobs[i];
+    const int seg0 = (int)mj.segs.size();
+    for (OzProblem P : J.probs) {
+      P.seg_begin += seg0;
+      P.tile_begin += mj.tiles;
+      P.tb = (int)i;
+      mj.probs.push_back(P);
+    }
+    mj.segs.insert(mj.segs.end(), J.segs.begin(), J.segs.end());
+    mj.maps.insert(mj.maps.end(), J.maps.begin(), J.maps.end());
+    mj.tiles += J.tiles;
+  }
+  ISCSI_TRY(mj.d_probs.grow(sizeof(OzProblem) * std::max<size_t>(1, mj.probs.size())));
+  ISCSI_TRY(mj.d_segs.grow(sizeof(OzSeg) * std::max<size_t>(1, mj.segs.size())));
+  ISCSI_TRY(mj.d_maps.grow(sizeof(OzMaps) * std::max<size_t>(1, mj.maps.size())));
+  ISCSI_TRY(mj.d_tbases.grow(sizeof(void*) * std::max<size_t>(1, tbases.size())));
+  if (!mj.probs.empty())
+    ISCSI_CUDA(cudaMemcpyAsync(mj.d_probs.p, mj.probs.data(), sizeof(OzProblem) * mj.probs.size(),
+                               cudaMemcpyHostToDevice, st));
+  if (!mj.segs.empty())
+    ISCSI_CUDA(cudaMemcpyAsync(mj.d_segs.p, mj.segs.data(), sizeof(OzSeg) * mj.segs.size(), cudaMemcpyHostToDevice,
+                               st));
+  if (!mj.maps.empty())
+    ISCSI_CUDA(cudaMemcpyAsync(mj.d_maps.p, mj.maps.data(), sizeof(OzMaps) * mj.maps.size(), cudaMemcpyHostToDevice,
+                               st));
+  if (!tbases.empty())
+    ISCSI_CUDA(cudaMemcpyAsync(mj.d_tbases.p, tbases.data(), sizeof(void*) * tbases.size(), cudaMemcpyHostToDevice,
+                               st));
+  ISCSI_CUDA(cudaStreamSynchronize(st));  // the host vectors may change after this call
+  mj.src = jobs;
+  mj.tbases = tbases;
+  mj.ver.resize(jobs.size());
+  for (size_t i = 0; i < jobs.size(); ++i) mj.ver[i] = jobs[i]->version;
+  return kOk;
+}
+
+int launch_merged(const MergedJob& mj, int prec, int* err, cudaStream_t st) {
+  if (mj.tiles == 0) return kOk;
+  return launch_tc_problems(mj.d_probs.as<OzProblem>(), (int)mj.probs.size(), mj.d_segs.as<OzSeg>(),
+                            mj.d_maps.as<OzMaps>(), mj.d_tbases.as<void*>(), mj.tiles, prec, err, st);
+}
+
+struct BatchState {
+  std::vector<Context*> ctxs;
+  std::vector<const double*> cs;
+  std::vector<double*> ss;
+  int nvec = 0, prec = 0;
+  MergedJob ab, sst;
+  DevBuf err;
+  cudaStream_t bs = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t x = nullptr;
+  long long kernels = 0;
+  bool failed = false;
+  int calls = 0;
+  BatchState() = default;
+  BatchState(const BatchState&) = delete;
+  BatchState& operator=(const BatchState&) = delete;
+  ~BatchState() {
+    if (bs) cudaStreamSynchronize(bs);
+    if (x) cudaGraphExecDestroy(x);
+    if (g) cudaGraphDestroy(g);
+    if (ev) cudaEventDestroy(ev);
+    if (bs) cudaStreamDestroy(bs);
+  }
+};
+
+std::unique_ptr<BatchState> g_batch;
+
+// the whole batch, launch by launch (also what a capture records)
+int batch_sequence(BatchState& B) {
+  cudaStream_t st = stream();
+  const int n = (int)B.ctxs.size();
+  const bool tc = B.prec == 64 ? options().fp64_tc : options().fp32_tc;
+  for (int i = 0; i < n; ++i) ISCSI_TRY(sigma_run(*B.ctxs[i], B.cs[i], B.ss[i], B.nvec, B.prec, kPhPre));
+  if (tc) {
+    std::vector<const OzJob*> jobs;
+    std::vector<void*> tb;
+    for (int i = 0; i < n; ++i)
+      if (B.ctxs[i]->have_ab) {
+        jobs.push_back(B.prec == 64 ? &B.ctxs[i]->oz_ab : &B.ctxs[i]->t3_ab);
+        tb.push_back(nullptr);  // absolute output pointers (the context's T workspace)
+      }
+    ISCSI_TRY(merge_jobs(B.ab, jobs, tb, st));
+    ISCSI_TRY(launch_merged(B.ab, B.prec, B.err.as<int>(), st));
+  } else {
+    for (int i = 0; i < n; ++i) ISCSI_TRY(sigma_run(*B.ctxs[i], B.cs[i], B.ss[i], B.nvec, B.prec, kPhAbGemm));
+  }
+  for (int i = 0; i < n; ++i) ISCSI_TRY(sigma_run(*B.ctxs[i], B.cs[i], B.ss[i], B.nvec, B.prec, kPhMid));
+  {
+    std::vector<const OzJob*> jobs;
+    std::vector<void*> tb;
+    for (int i = 0; i < n; ++i) {
+      Context& c = *B.ctxs[i];
+      const bool on = B.prec == 64 ? samespin_tc_active(c) : samespin_tc32_active(c);
+      if (!on) continue;
+      jobs.push_back(B.prec == 64 ? &c.oz_ss : &c.t3_ss);
+      tb.push_back(B.prec == 64 ? static_cast<void*>(B.ss[i]) : static_cast<void*>(c.s32.as<float>()));
+    }
+    ISCSI_TRY(merge_jobs(B.sst, jobs, tb, st));
+    ISCSI_TRY(launch_merged(B.sst, B.prec, B.err.as<int>(), st));
+  }
+  for (int i = 0; i < n; ++i) ISCSI_TRY(sigma_run(*B.ctxs[i], B.cs[i], B.ss[i], B.nvec, B.prec, kPhPost));
+  return kOk;
+}
+
+long long graph_kernel_nodes(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+  long long c = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++c;
+  }
+  return c;
+}
+
+int batch_run(BatchState& B) {
+  if (B.x) {
+    ISCSI_CUDA(cudaGraphLaunch(B.x, B.bs));
+    g_launch_count += B.kernels;
+    return kOk;
+  }
+  if (B.calls == 0 || !options().use_graph || B.failed) return batch_sequence(B);
+  // second call with this batch: capture it, then replay
+  long long before = g_launch_count;
+  for (Context* c : B.ctxs) c->capturing = true;
+  cudaError_t ce = cudaStreamBeginCapture(B.bs, cudaStreamCaptureModeThreadLocal);
+  int rc = ce == cudaSuccess ? batch_sequence(B) : kErrCuda;
+  cudaGraph_t g = nullptr;
+  cudaError_t ee = ce == cudaSuccess ? cudaStreamEndCapture(B.bs, &g) : ce;
+  for (Context* c : B.ctxs) c->capturing = false;
+  g_launch_count = before;
+  if (ce == cudaSuccess && rc == kOk && ee == cudaSuccess && g && cudaGraphInstantiate(&B.x, g, 0) == cudaSuccess) {
+    B.g = g;
+    B.kernels = graph_kernel_nodes(g);
+    ISCSI_CUDA(cudaGraphLaunch(B.x, B.bs));
+    g_launch_count += B.kernels;
+    return kOk;
+  }
+  if (g) cudaGraphDestroy(g);
+  B.x = nullptr;
+  B.failed = true;
+  cudaGetLastError();
+  return batch_sequence(B);
+}
+
+}  // namespace
+
+void batch_reset() { g_batch.reset(); }
+
+int batch_sigma(const std::vector<Context*>& ctxs, const std::vector<const double*>& cs,
+                const std::vector<double*>& ss, int nvec, int prec) {
+  if (!g_batch || g_batch->ctxs != ctxs || g_batch->cs != cs || g_batch->ss != ss || g_batch->nvec != nvec ||
+      g_batch->prec != prec) {
+    g_batch.reset(new BatchState());
+    BatchState& B = *g_batch;
+    B.ctxs = ctxs;
+    B.cs = cs;
+    B.ss = ss;
+    B.nvec = nvec;
+    B.prec = prec;
+    ISCSI_TRY(B.err.alloc(sizeof(int)));
+    ISCSI_CUDA(cudaMemset(B.err.p, 0, sizeof(int)));
+    ISCSI_CUDA(cudaStreamCreateWithFlags(&B.bs, cudaStreamNonBlocking));
+    ISCSI_CUDA(cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming));
+  }
+  BatchState& B = *g_batch;
+  // run on the batch's own (capturable) stream, ordered after and before the caller's
+  cudaStream_t user = stream();
+  ISCSI_CUDA(cudaEventRecord(B.ev, user));
+  ISCSI_CUDA(cudaStreamWaitEvent(B.bs, B.ev, 0));
+  set_stream(B.bs);
+  int rc = batch_run(B);
+  set_stream(user);
+  ++B.calls;
+  ISCSI_CUDA(cudaEventRecord(B.ev, B.bs));
+  ISCSI_CUDA(cudaStreamWaitEvent(user, B.ev, 0));
+  return rc;
+}
+
+// status of the bounded waits of the merged launches (synchronises)
+int batch_check() {
+  if (!g_batch || !g_batch->err.p) return kOk;
+  int h = 0;
+  ISCSI_CUDA(cudaMemcpy(&h, g_batch->err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    set_error("batched sigma: a bounded device wait ran out");
+    return kErrWait;
+  }
+  return kOk;
+}
+
+bool batch_graph_active() { return g_batch && g_batch->x; }
+
+}  // namespace iscsi

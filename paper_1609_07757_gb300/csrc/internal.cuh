@@ -141,6 +141,7 @@ struct OzJob {
   int tiles = 0;
   int nvec = -1;
   const void* tbase = nullptr;
+  long long version = 0;  // bumped at every rebuild (launches over several contexts re-merge)
 };
 
 struct ColClass {       // column level class c = level(X) + level(Y)
@@ -247,7 +248,10 @@ void set_stream(cudaStream_t s);
 int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h1, const double* eri, double tau);
 
 // sigma.cu
-int sigma_run(Context& ctx, const double* c, double* sigma, int nvec, int precision);
+// phases of one sigma step (a batch over several contexts runs each phase for
+// all contexts, with the two contractions merged into one launch each)
+enum { kPhPre = 1, kPhAbGemm = 2, kPhMid = 4, kPhSsGemm = 8, kPhPost = 16, kPhAll = 31 };
+int sigma_run(Context& ctx, const double* c, double* sigma, int nvec, int precision, int phases = kPhAll);
 int sigma_workspace(Context& ctx, int nvec, int precision);
 // algorithmic flops per sigma per vector of the opposite-spin GEMM (which = 0)
 // or of the same-spin GEMMs (which = 1): 2 x M x K x N summed over problems;
@@ -259,11 +263,15 @@ int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec); 
 int opposite_tc_gemm(Context& ctx);                                                // T = G Ct
 bool samespin_block_on_tc(const Context& ctx, int a);
 bool samespin_tc_active(const Context& ctx);
-int samespin_tc(Context& ctx, const double* c, double* sigma, int nvec);           // sigma += same-spin
+int samespin_tc_operands(Context& ctx, const double* c, double* sigma, int nvec);  // slices of C, job
+int samespin_tc_gemm(Context& ctx, double* sigma);                                 // sigma += same-spin
 int opposite_tc32_operands(Context& ctx, const float* c, float* ttw, int nvec);   // FP32 form
 int opposite_tc32_gemm(Context& ctx);
 bool samespin_tc32_active(const Context& ctx);
-int samespin_tc32(Context& ctx, const float* c, float* sigma, int nvec);
+int samespin_tc32_operands(Context& ctx, const float* c, float* sigma, int nvec);
+int samespin_tc32_gemm(Context& ctx, float* sigma);
+int launch_tc_problems(const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
+                       void* const* tbases, int tiles, int prec, int* err, cudaStream_t st);
 int tc_check(Context& ctx);
 
 // allocation-free single-vector FP64 sigma on a static device array (sigma.cu)
@@ -273,6 +281,13 @@ size_t noalloc_scratch_bytes();
 
 // davidson.cu
 int davidson_run(Context& ctx, int nroots, double tol, double* energies, double* vecs);
+
+// batch.cu
+int batch_sigma(const std::vector<Context*>& ctxs, const std::vector<const double*>& cs,
+                const std::vector<double*>& ss, int nvec, int prec);
+int batch_check();
+void batch_reset();
+bool batch_graph_active();
 
 // small helpers shared by the .cu files
 long long binom_ll(int n, int k);

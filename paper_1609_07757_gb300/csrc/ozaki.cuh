@@ -129,7 +129,8 @@ __global__ void k_oz_slice(const double* __restrict__ X, int rows, int cols, lon
 // reports through err.
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_oz_gemm(const OzProblem* __restrict__ probs, int nprobs, const OzSeg* __restrict__ segs,
-              const OzMaps* __restrict__ maps, double* tbase, int* __restrict__ err) {
+              const OzMaps* __restrict__ maps, double* tbase, double* const* __restrict__ tbases,
+              int* __restrict__ err) {
   extern __shared__ unsigned char oz_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t s_stage0 = tc::smem_u32(smem);
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     else hi = mid - 1;
   }
   const OzProblem P = probs[lo];
-  double* const Tp = P.t_rel ? tbase + P.t : reinterpret_cast<double*>(P.t);
+  double* const Tp = P.t_rel ? (tbases ? tbases[P.tb] : tbase) + P.t : reinterpret_cast<double*>(P.t);
   const int tl = tile - P.tile_begin;
   const int m0 = (tl / P.tiles_n) * OZ_BM, n0 = (tl % P.tiles_n) * OZ_BN;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

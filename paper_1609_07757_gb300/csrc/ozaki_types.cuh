@@ -49,11 +49,13 @@ struct OzMaps {
 };
 
 // T[M][N] (FP64, ldt) (+)= sum over segments of A_seg B_seg^T; T is the
-// device pointer t, or tbase + t when t_rel (so problem lists survive new
-// output vectors)
+// device pointer t, or base + t when t_rel, base being the launch's tbase
+// argument or, in a launch over several contexts, tbases[tb] (so problem
+// lists survive new output vectors)
 struct OzProblem {
   long long t;
   int t_rel;
+  int tb;
   long long ldt;
   int M, N;
   int seg_begin, seg_count;

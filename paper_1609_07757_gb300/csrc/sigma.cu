@@ -674,98 +674,112 @@ static int timing_event(Context& ctx, int call, int phase, cudaStream_t st) {
 
 template <typename T, typename TC>
 static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sigma, int nvec, ProblemList<T>& ab,
-                      ProblemList<T>& ss, int& pl_nvec, const T* G, const T* Ma, const T* Mb) {
+                      ProblemList<T>& ss, int& pl_nvec, const T* G, const T* Ma, const T* Mb, int phases) {
   cudaStream_t st = stream();
   T* ctw = ctx.ct.as<T>();
   T* ttw = ctx.tt.as<T>();
-  // problem lists depend on nvec, the workspaces and the same-spin routing, not on the vectors
   constexpr bool f64 = std::is_same<T, double>::value;
-  int ss_tc = (f64 ? samespin_tc_active(ctx) : samespin_tc32_active(ctx)) ? 1 : 0;
-  int& routed = f64 ? ctx.pl_ss_tc : ctx.pl_ss_tc32;
-  if (routed != ss_tc) {
-    routed = ss_tc;
-    pl_nvec = 0;
-  }
-  if (pl_nvec != nvec) {
-    ISCSI_TRY(build_problems<T>(ctx, nvec, G, Ma, Mb, ctw, ttw, ab, ss));
-    pl_nvec = nvec;
-  }
-  int call = ctx.ntimed;
-  ISCSI_TRY(timing_event(ctx, call, 0, st));
-  bool tc_path = f64 ? options().fp64_tc : options().fp32_tc;
-  if (ctx.have_ab && tc_path) {
-    // opposite-spin contraction on the tensor cores (lift + slice, GEMM)
-    ClassTable ct = class_table(ctx, nvec);
-    if (f64) {
-      ISCSI_TRY(opposite_tc_operands(ctx, reinterpret_cast<const double*>(c_in), reinterpret_cast<double*>(ttw), nvec));
-      ISCSI_TRY(timing_event(ctx, call, 1, st));
-      ISCSI_TRY(opposite_tc_gemm(ctx));
-    } else {
-      ISCSI_TRY(opposite_tc32_operands(ctx, reinterpret_cast<const float*>(c_in), reinterpret_cast<float*>(ttw), nvec));
-      ISCSI_TRY(timing_event(ctx, call, 1, st));
-      ISCSI_TRY(opposite_tc32_gemm(ctx));
+  const int ss_tc = (f64 ? samespin_tc_active(ctx) : samespin_tc32_active(ctx)) ? 1 : 0;
+  const bool tc_path = f64 ? options().fp64_tc : options().fp32_tc;
+  // per-phase events only when the whole step runs in this call
+  const bool timed = phases == kPhAll;
+  const int call = ctx.ntimed;
+  auto ev = [&](int ph) { return timed ? timing_event(ctx, call, ph, st) : kOk; };
+  if (phases & kPhPre) {
+    // problem lists depend on nvec, the workspaces and the same-spin routing, not on the vectors
+    int& routed = f64 ? ctx.pl_ss_tc : ctx.pl_ss_tc32;
+    if (routed != ss_tc) {
+      routed = ss_tc;
+      pl_nvec = 0;
     }
-    ISCSI_TRY(timing_event(ctx, call, 2, st));
-    k_fold<T><<<ctx.sp[0].count, 256, 0, st>>>(ct, nvec, ctx.n, ctx.na, ctx.nb, ctx.sp[1].nhole,
-                                               ctx.sp[0].dec.as<int>(), ctx.sp[1].dec.as<int>(),
-                                               ctx.hp_class.as<int8_t>(), ctx.hp_local.as<int>(),
-                                               ctx.pair_index.as<int>(), ctx.off.as<long long>(), ttw, ctx.ndet, sigma); ISCSI_COUNT_LAUNCH();
-    ISCSI_CUDA(cudaGetLastError());
-    ISCSI_TRY(timing_event(ctx, call, 3, st));
-  } else if (ctx.have_ab) {
-    ClassTable ct = class_table(ctx, nvec);
-    long long tot = ct.start[ct.nclass];
-    if (tot > 0) {
-      k_lift_ct<T, TC><<<launch_blocks(tot, 256), 256, 0, st>>>(
-          ct, nvec, ctx.n, ctx.sp[0].nhole, ctx.sp[1].nhole, ctx.pair_of.as<int>(), ctx.hp_inv.as<int>(),
-          ctx.sp[0].lift.as<int>(), ctx.sp[1].lift.as<int>(), ctx.sp[0].level.as<int8_t>(), ctx.nballow.as<int>(),
-          ctx.off.as<long long>(), c_in, ctx.ndet, ctw); ISCSI_COUNT_LAUNCH();
+    if (pl_nvec != nvec) {
+      ISCSI_TRY(build_problems<T>(ctx, nvec, G, Ma, Mb, ctw, ttw, ab, ss));
+      pl_nvec = nvec;
+    }
+    ISCSI_TRY(ev(0));
+    if (ctx.have_ab && tc_path) {
+      // opposite-spin operands for the tensor cores (lift + slice)
+      if (f64)
+        ISCSI_TRY(opposite_tc_operands(ctx, reinterpret_cast<const double*>(c_in), reinterpret_cast<double*>(ttw),
+                                       nvec));
+      else
+        ISCSI_TRY(opposite_tc32_operands(ctx, reinterpret_cast<const float*>(c_in), reinterpret_cast<float*>(ttw),
+                                         nvec));
+    } else if (ctx.have_ab) {
+      ClassTable ct = class_table(ctx, nvec);
+      long long tot = ct.start[ct.nclass];
+      if (tot > 0) {
+        k_lift_ct<T, TC><<<launch_blocks(tot, 256), 256, 0, st>>>(
+            ct, nvec, ctx.n, ctx.sp[0].nhole, ctx.sp[1].nhole, ctx.pair_of.as<int>(), ctx.hp_inv.as<int>(),
+            ctx.sp[0].lift.as<int>(), ctx.sp[1].lift.as<int>(), ctx.sp[0].level.as<int8_t>(), ctx.nballow.as<int>(),
+            ctx.off.as<long long>(), c_in, ctx.ndet, ctw); ISCSI_COUNT_LAUNCH();
+        ISCSI_CUDA(cudaGetLastError());
+      }
+    } else {
+      ISCSI_CUDA(cudaMemsetAsync(sigma, 0, sizeof(T) * ctx.ndet * nvec, st));
+    }
+    ISCSI_TRY(ev(1));
+  }
+  if (phases & kPhAbGemm) {
+    if (ctx.have_ab && tc_path)
+      ISCSI_TRY(f64 ? opposite_tc_gemm(ctx) : opposite_tc32_gemm(ctx));
+    else if (ctx.have_ab)
+      ISCSI_TRY(launch_grouped<T>(ab, c, sigma, st));
+    ISCSI_TRY(ev(2));
+  }
+  if (phases & kPhMid) {
+    if (ctx.have_ab) {
+      ClassTable ct = class_table(ctx, nvec);
+      k_fold<T><<<ctx.sp[0].count, 256, 0, st>>>(ct, nvec, ctx.n, ctx.na, ctx.nb, ctx.sp[1].nhole,
+                                                 ctx.sp[0].dec.as<int>(), ctx.sp[1].dec.as<int>(),
+                                                 ctx.hp_class.as<int8_t>(), ctx.hp_local.as<int>(),
+                                                 ctx.pair_index.as<int>(), ctx.off.as<long long>(), ttw, ctx.ndet,
+                                                 sigma); ISCSI_COUNT_LAUNCH();
       ISCSI_CUDA(cudaGetLastError());
     }
-    ISCSI_TRY(timing_event(ctx, call, 1, st));
-    ISCSI_TRY(launch_grouped<T>(ab, c, sigma, st));
-    ISCSI_TRY(timing_event(ctx, call, 2, st));
-    k_fold<T><<<ctx.sp[0].count, 256, 0, st>>>(ct, nvec, ctx.n, ctx.na, ctx.nb, ctx.sp[1].nhole,
-                                               ctx.sp[0].dec.as<int>(), ctx.sp[1].dec.as<int>(),
-                                               ctx.hp_class.as<int8_t>(), ctx.hp_local.as<int>(),
-                                               ctx.pair_index.as<int>(), ctx.off.as<long long>(), ttw, ctx.ndet, sigma); ISCSI_COUNT_LAUNCH();
-    ISCSI_CUDA(cudaGetLastError());
-    ISCSI_TRY(timing_event(ctx, call, 3, st));
-  } else {
-    ISCSI_CUDA(cudaMemsetAsync(sigma, 0, sizeof(T) * ctx.ndet * nvec, st));
-    ISCSI_TRY(timing_event(ctx, call, 1, st));
-    ISCSI_TRY(timing_event(ctx, call, 2, st));
-    ISCSI_TRY(timing_event(ctx, call, 3, st));
+    ISCSI_TRY(ev(3));
+    ISCSI_TRY(launch_grouped<T>(ss, c, sigma, st));
+    if (ss_tc && f64)
+      ISCSI_TRY(samespin_tc_operands(ctx, reinterpret_cast<const double*>(c), reinterpret_cast<double*>(sigma), nvec));
+    else if (ss_tc)
+      ISCSI_TRY(samespin_tc32_operands(ctx, reinterpret_cast<const float*>(c), reinterpret_cast<float*>(sigma), nvec));
   }
-  ISCSI_TRY(launch_grouped<T>(ss, c, sigma, st));
-  if (ss_tc && f64)
-    ISCSI_TRY(samespin_tc(ctx, reinterpret_cast<const double*>(c), reinterpret_cast<double*>(sigma), nvec));
-  else if (ss_tc)
-    ISCSI_TRY(samespin_tc32(ctx, reinterpret_cast<const float*>(c), reinterpret_cast<float*>(sigma), nvec));
-  ISCSI_TRY(timing_event(ctx, call, 4, st));
-  if (options().phase_timing && !ctx.capturing && call < Context::kMaxTimed) ctx.ntimed++;
+  if (phases & kPhSsGemm) {
+    if (ss_tc && f64)
+      ISCSI_TRY(samespin_tc_gemm(ctx, reinterpret_cast<double*>(sigma)));
+    else if (ss_tc)
+      ISCSI_TRY(samespin_tc32_gemm(ctx, reinterpret_cast<float*>(sigma)));
+  }
+  if (phases & kPhPost) {
+    ISCSI_TRY(ev(4));
+    if (timed && options().phase_timing && !ctx.capturing && call < Context::kMaxTimed) ctx.ntimed++;
+  }
   (void)s_out;
   return kOk;
 }
 
-int sigma_run(Context& ctx, const double* c, double* sigma, int nvec, int precision) {
+int sigma_run(Context& ctx, const double* c, double* sigma, int nvec, int precision, int phases) {
   cudaStream_t st = stream();
-  ISCSI_TRY(sigma_workspace(ctx, nvec, precision));
+  if (phases & kPhPre) ISCSI_TRY(sigma_workspace(ctx, nvec, precision));
   const double* Ma = ctx.na ? ctx.M64[0].as<double>() : nullptr;
   const double* Mb = ctx.nb ? (ctx.beta_alias ? ctx.M64[0].as<double>() : ctx.M64[1].as<double>()) : nullptr;
   if (precision == 64) {
     return sigma_impl<double, double>(ctx, c, sigma, c, sigma, nvec, ctx.pl_ab64, ctx.pl_ss64, ctx.pl_nvec64,
-                                      ctx.G64.as<double>(), Ma, Mb);
+                                      ctx.G64.as<double>(), Ma, Mb, phases);
   }
-  ISCSI_TRY(ensure_fp32_matrices(ctx));
+  if (phases & kPhPre) ISCSI_TRY(ensure_fp32_matrices(ctx));
   const float* Ma32 = ctx.na ? ctx.M32[0].as<float>() : nullptr;
   const float* Mb32 = ctx.nb ? (ctx.beta_alias ? ctx.M32[0].as<float>() : ctx.M32[1].as<float>()) : nullptr;
   long long cnt = ctx.ndet * nvec;
-  k_convert<double, float><<<std::min(launch_blocks(cnt, 256), 4096), 256, 0, st>>>(c, ctx.c32.as<float>(), cnt); ISCSI_COUNT_LAUNCH();
+  if (phases & kPhPre) {
+    k_convert<double, float><<<std::min(launch_blocks(cnt, 256), 4096), 256, 0, st>>>(c, ctx.c32.as<float>(), cnt); ISCSI_COUNT_LAUNCH();
+  }
   ISCSI_TRY(sigma_impl<float, float>(ctx, ctx.c32.as<float>(), ctx.s32.as<float>(), ctx.c32.as<float>(),
                                      ctx.s32.as<float>(), nvec, ctx.pl_ab32, ctx.pl_ss32, ctx.pl_nvec32,
-                                     ctx.G32.as<float>(), Ma32, Mb32));
-  k_convert<float, double><<<std::min(launch_blocks(cnt, 256), 4096), 256, 0, st>>>(ctx.s32.as<float>(), sigma, cnt); ISCSI_COUNT_LAUNCH();
+                                     ctx.G32.as<float>(), Ma32, Mb32, phases));
+  if (phases & kPhPost) {
+    k_convert<float, double><<<std::min(launch_blocks(cnt, 256), 4096), 256, 0, st>>>(ctx.s32.as<float>(), sigma, cnt); ISCSI_COUNT_LAUNCH();
+  }
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
 }

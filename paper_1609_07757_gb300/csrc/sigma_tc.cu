@@ -218,6 +218,7 @@ static int add_seg(OzJob& job, const SliceArray& A, int a_row0, int a_k0, const 
 }
 
 static int upload_job(OzJob& job, cudaStream_t st) {
+  ++job.version;
   ISCSI_TRY(job.d_probs.grow(sizeof(OzProblem) * std::max<size_t>(1, job.probs.size())));
   ISCSI_TRY(job.d_segs.grow(sizeof(OzSeg) * std::max<size_t>(1, job.segs.size())));
   ISCSI_TRY(job.d_maps.grow(sizeof(OzMaps) * std::max<size_t>(1, job.maps.size())));
@@ -238,7 +239,7 @@ static int launch_job(Context& ctx, const OzJob& job, double* tbase, cudaStream_
   if (job.tiles == 0) return kOk;
   k_oz_gemm<<<job.tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(job.d_probs.as<OzProblem>(), (int)job.probs.size(),
                                                           job.d_segs.as<OzSeg>(), job.d_maps.as<OzMaps>(), tbase,
-                                                          ctx.oz_err.as<int>()); ISCSI_COUNT_LAUNCH();
+                                                          nullptr, ctx.oz_err.as<int>()); ISCSI_COUNT_LAUNCH();
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
 }
@@ -462,7 +463,7 @@ static std::vector<SsBlock> ss_blocks(const Context& ctx, long long* elems, long
   return out;
 }
 
-int samespin_tc(Context& ctx, const double* c, double* sigma, int nvec) {
+int samespin_tc_operands(Context& ctx, const double* c, double* sigma, int nvec) {
   cudaStream_t st = stream();
   ISCSI_TRY(tc_prepare_m(ctx));
   long long elems1 = 0, exps1 = 0;
@@ -540,8 +541,11 @@ int samespin_tc(Context& ctx, const double* c, double* sigma, int nvec) {
                                cs + v * elems1 + b.ca_off, st));
     }
   (void)SB;
-  return launch_job(ctx, ctx.oz_ss, sigma, st);
+  (void)sigma;
+  return kOk;
 }
+
+int samespin_tc_gemm(Context& ctx, double* sigma) { return launch_job(ctx, ctx.oz_ss, sigma, stream()); }
 
 // ---------------------------------------------------------------------------
 // FP32 form: three bf16 terms per element, FP32 accumulation (tc32.cuh)
@@ -562,7 +566,7 @@ static int t3_launch(Context& ctx, const OzJob& job, float* tbase, cudaStream_t 
   if (job.tiles == 0) return kOk;
   k_tc32_gemm<<<job.tiles, T3_THREADS, T3_SMEM_BYTES, st>>>(job.d_probs.as<OzProblem>(), (int)job.probs.size(),
                                                             job.d_segs.as<OzSeg>(), job.d_maps.as<OzMaps>(), tbase,
-                                                            ctx.oz_err.as<int>()); ISCSI_COUNT_LAUNCH();
+                                                            nullptr, ctx.oz_err.as<int>()); ISCSI_COUNT_LAUNCH();
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
 }
@@ -680,7 +684,7 @@ static int t3_prepare_m(Context& ctx) {
   return kOk;
 }
 
-int samespin_tc32(Context& ctx, const float* c, float* sigma, int nvec) {
+int samespin_tc32_operands(Context& ctx, const float* c, float* sigma, int nvec) {
   cudaStream_t st = stream();
   ISCSI_TRY(t3_prepare_m(ctx));
   long long elems1 = 0, exps1 = 0;
@@ -748,7 +752,27 @@ int samespin_tc32(Context& ctx, const float* c, float* sigma, int nvec) {
         ISCSI_TRY(t3_slice_matrix<float>(X, b.rows, b.nba, b.nba, 0, nullptr, b.ca_ld, b.ca_rows,
                                          cs + v * elems1 + b.ca_off, st));
     }
-  return t3_launch(ctx, ctx.t3_ss, sigma, st);
+  (void)sigma;
+  return kOk;
+}
+
+int samespin_tc32_gemm(Context& ctx, float* sigma) { return t3_launch(ctx, ctx.t3_ss, sigma, stream()); }
+
+// one launch of the FP64-accurate (prec 64) or FP32-form (prec 32) contraction
+// over a device problem list whose relative outputs use the base table tbases
+int launch_tc_problems(const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
+                       void* const* tbases, int tiles, int prec, int* err, cudaStream_t st) {
+  if (tiles == 0) return kOk;
+  ISCSI_TRY(tc_attr());
+  if (prec == 64) {
+    k_oz_gemm<<<tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(probs, nprobs, segs, maps, nullptr,
+                                                       reinterpret_cast<double* const*>(tbases), err); ISCSI_COUNT_LAUNCH();
+  } else {
+    k_tc32_gemm<<<tiles, T3_THREADS, T3_SMEM_BYTES, st>>>(probs, nprobs, segs, maps, nullptr,
+                                                         reinterpret_cast<float* const*>(tbases), err); ISCSI_COUNT_LAUNCH();
+  }
+  ISCSI_CUDA(cudaGetLastError());
+  return kOk;
 }
 
 // status of the bounded waits of the tensor-core kernels (synchronises)

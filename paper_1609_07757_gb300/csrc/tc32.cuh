@@ -71,7 +71,8 @@ __global__ void k_t3_slice(const V* __restrict__ X, int rows, int cols, long lon
 // waits (bounded) for its copies in flight, frees TMEM and reports via err.
 __global__ void __launch_bounds__(T3_THREADS, 1)
     k_tc32_gemm(const OzProblem* __restrict__ probs, int nprobs, const OzSeg* __restrict__ segs,
-                const OzMaps* __restrict__ maps, float* tbase, int* __restrict__ err) {
+                const OzMaps* __restrict__ maps, float* tbase, float* const* __restrict__ tbases,
+                int* __restrict__ err) {
   extern __shared__ unsigned char t3_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)t3_smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t s_stage0 = tc::smem_u32(smem);
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     else hi = mid - 1;
   }
   const OzProblem P = probs[lo];
-  float* const Tp = P.t_rel ? tbase + P.t : reinterpret_cast<float*>(P.t);
+  float* const Tp = P.t_rel ? (tbases ? tbases[P.tb] : tbase) + P.t : reinterpret_cast<float*>(P.t);
   const int tl = tile - P.tile_begin;
   const int m0 = (tl / P.tiles_n) * T3_BM, n0 = (tl % P.tiles_n) * T3_BN;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

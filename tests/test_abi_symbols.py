@@ -39,6 +39,8 @@ def test_calls_without_context_fail_cleanly():
     assert lib.iscsi_set_option(b"no_such_key", 1.0) == _lib.ISCSI_E_ARG
     assert lib.iscsi_set_option(b"precision", 16.0) == _lib.ISCSI_E_ARG
     assert b"precision" in lib.iscsi_last_error()
+    assert lib.iscsi_batch_sigma(None, None, None, 0, 1) == _lib.ISCSI_E_ARG
+    assert b"iscsi_batch_sigma" in lib.iscsi_last_error()
 
 
 def test_init_rejects_bad_arguments_before_touching_the_gpu():
