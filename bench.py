@@ -415,17 +415,31 @@ def run_batching(count=64, reps=5, tau=1e-14, nroots=1):
         res["speedup"] = round(res["one_at_a_time"]["ms_per_round"] / res["batched"]["ms_per_round"], 3)
         out["fp%d" % prec] = res
     L.iscsi_set_option("precision", 64)
-    # the lowest root of every instance, one Davidson per instance (FP64, device-resident)
-    t0 = time.time()
-    iters = 0
-    for h in hs:
-        L.iscsi_ctx_use(h)
-        st, e = L.iscsi_davidson(nroots, 1e-8)
-        iters += L.iscsi_stats()["davidson_iters"]
-    torch.cuda.synchronize()
-    dt = time.time() - t0
-    out["davidson_fp64_one_at_a_time"] = {"roots_per_instance": nroots, "wall_s": round(dt, 2),
-                                          "instances_per_s": round(count / dt, 2), "iterations": iters}
+    # the lowest root of every instance: one Davidson per instance, then all
+    # instances iterated together (iscsi_batch_davidson), FP64 and FP32-mixed
+    import numpy as np
+    for prec in (64, 32):
+        L.iscsi_set_option("precision", prec)
+        t0 = time.time()
+        iters, e_single = 0, []
+        for h in hs:
+            L.iscsi_ctx_use(h)
+            st, e = L.iscsi_davidson(nroots, 1e-8)
+            e_single.append(e)
+            iters += L.iscsi_stats()["davidson_iters"]
+        torch.cuda.synchronize()
+        dt1 = time.time() - t0
+        t0 = time.time()
+        st, e_batch, sts = L.iscsi_batch_davidson(hs, nroots, 1e-8)
+        torch.cuda.synchronize()
+        dt2 = time.time() - t0
+        de = float(np.abs(np.asarray(e_single) - e_batch).max())
+        out["davidson_fp%d" % prec] = {
+            "roots_per_instance": nroots, "one_at_a_time_s": round(dt1, 2), "batched_s": round(dt2, 2),
+            "instances_per_s_one_at_a_time": round(count / dt1, 2), "instances_per_s_batched": round(count / dt2, 2),
+            "speedup": round(dt1 / dt2, 3), "iterations_one_at_a_time": iters, "batched_status": st,
+            "converged": int(sum(1 for x in sts if x == 0)), "max_abs_dE_batched_vs_single": float("%.3e" % de)}
+    L.iscsi_set_option("precision", 64)
     L.iscsi_finalize()
     return out
 

@@ -197,7 +197,8 @@ ISCSI_API iscsi_status iscsi_set_stream(void* stream);
  *   "class_mask_lo"    classes 0..31 to keep, as an integer bit mask (default all)
  *   "class_mask_hi"    classes 32..41, bit i-32 (default all)
  *   "maxiter"          Davidson iteration limit (default 300)
- *   "max_subspace"     Davidson subspace size per root (default 12)
+ *   "max_subspace"     Davidson basis vectors per root; 0 (default): 12 per
+ *                      root up to 96 in all, at least 4 per root
  *   "etol"             Davidson energy-change threshold (default 1e-10)
  *   "switch_tol"       mixed precision: residual at which FP64 sigma starts (default 1e-5;
  *                      the switch also happens when the FP32 residual stalls)
@@ -267,6 +268,24 @@ ISCSI_API iscsi_status iscsi_batch_sigma(const int* handles, const void* const* 
 /* Synchronises and returns ISCSI_E_WAIT if a bounded device wait of the last
    batch's merged launches ran out, else ISCSI_OK. */
 ISCSI_API iscsi_status iscsi_batch_check(void);
+
+/*
+ * Batching form of iscsi_davidson: the lowest nroots eigenpairs of count
+ * independent contexts, iterated together (one Davidson iteration of every
+ * unconverged context per step, their sigma steps batched as in
+ * iscsi_batch_sigma, the step captured as one CUDA graph while the set of
+ * unconverged contexts is unchanged).  Options as for iscsi_davidson.
+ * energies: host [count][nroots]; vecs: NULL or host [count] array of device
+ * pointers (each NULL or FP64 [nroots][ndet_i], written; read as start
+ * vectors when "guess_from_vecs" is set); statuses: NULL or host [count],
+ * each context's own status.  Synchronises.  Returns ISCSI_OK when every
+ * context converged, else the first failing context's status.
+ * Errors: ISCSI_E_ARG (count or nroots < 1, nroots > ndet_i, tol <= 0, NULL
+ * handles or energies, unknown or repeated handle), ISCSI_E_NOCONV,
+ * ISCSI_E_NAN, ISCSI_E_WAIT, ISCSI_E_NOMEM, ISCSI_E_CUDA.
+ */
+ISCSI_API iscsi_status iscsi_batch_davidson(const int* handles, int count, int nroots, double tol, double* energies,
+                                            void* const* vecs, int* statuses);
 
 /*
  * Several contexts (batching).  iscsi_init creates a context and makes it

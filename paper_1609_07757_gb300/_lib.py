@@ -67,6 +67,7 @@ def load(build_if_missing=True):
         "iscsi_ctx_destroy": (c_int, [c_int]),
         "iscsi_batch_sigma": (c_int, [vp, vp, vp, c_int, c_int]),
         "iscsi_batch_check": (c_int, []),
+        "iscsi_batch_davidson": (c_int, [vp, c_int, c_int, c_d, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -135,6 +136,22 @@ def iscsi_batch_sigma(handles, cs, sigmas, nvec=1):
 
 def iscsi_batch_check():
     return _check(load().iscsi_batch_check())
+
+
+def iscsi_batch_davidson(handles, nroots, tol, vecs=None):
+    """Lowest nroots eigenpairs of several contexts iterated together.
+    Returns (status, energies [count][nroots], per-context statuses)."""
+    n = len(handles)
+    h = (ctypes.c_int * n)(*[int(x) for x in handles])
+    e = np.zeros((n, nroots), dtype=np.float64)
+    sts = (ctypes.c_int * n)()
+    vp = None
+    if vecs is not None:
+        vp = (ctypes.c_void_p * n)(*[(_dev(v) if v is not None else None) for v in vecs])
+    st = load().iscsi_batch_davidson(h, n, int(nroots), float(tol), e.ctypes.data_as(ctypes.c_void_p), vp, sts)
+    if st < 0 and st not in (ISCSI_E_NOCONV,):
+        _check(st)
+    return st, e, list(sts)
 
 
 def iscsi_sigma_noalloc(c, sigma):

@@ -213,7 +213,7 @@ iscsi_status iscsi_set_option(const char* key, double value) {
     if (value < 1 || value > 100000) return bad();
     o.maxiter = (int)value;
   } else if (k == "max_subspace") {
-    if (value < 2 || value > 64) return bad();
+    if (value != 0 && (value < 2 || value > 64)) return bad();
     o.max_subspace = (int)value;
   } else if (k == "etol") {
     if (value <= 0) return bad();
@@ -345,6 +345,35 @@ iscsi_status iscsi_batch_sigma(const int* handles, const void* const* cs, void* 
 }
 
 iscsi_status iscsi_batch_check(void) { return batch_check(); }
+
+iscsi_status iscsi_batch_davidson(const int* handles, int count, int nroots, double tol, double* energies,
+                                  void* const* vecs, int* statuses) {
+  if (count < 1 || !handles || nroots < 1 || !(tol > 0) || !energies) {
+    set_error("iscsi_batch_davidson: invalid argument");
+    return ISCSI_E_ARG;
+  }
+  std::vector<Context*> ctxs(count);
+  for (int i = 0; i < count; ++i) {
+    auto it = g_ctx.find(handles[i]);
+    if (it == g_ctx.end() || nroots > it->second->ndet) {
+      set_error("iscsi_batch_davidson: unknown handle, or more roots than determinants, at position " +
+                std::to_string(i));
+      return ISCSI_E_ARG;
+    }
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) {
+        set_error("iscsi_batch_davidson: a context appears twice");
+        return ISCSI_E_ARG;
+      }
+    ctxs[i] = it->second.get();
+  }
+  int s = davidson_batch_run(ctxs, nroots, tol, energies, reinterpret_cast<double* const*>(vecs), statuses);
+  for (Context* c : ctxs) {
+    int w = tc_check(*c);
+    if (w != ISCSI_OK && s == ISCSI_OK) s = w;
+  }
+  return s;
+}
 
 int iscsi_ctx_current(void) { return current() ? g_current : 0; }
 

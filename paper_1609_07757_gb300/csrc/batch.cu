@@ -20,17 +20,6 @@ namespace iscsi {
 
 namespace {
 
-struct MergedJob {
-  std::vector<OzProblem> probs;
-  std::vector<OzSeg> segs;
-  std::vector<OzMaps> maps;
-  DevBuf d_probs, d_segs, d_maps, d_tbases;
-  std::vector<const OzJob*> src;
-  std::vector<long long> ver;
-  std::vector<void*> tbases;
-  int tiles = 0;
-};
-
 // one problem list over the given jobs; rebuilt only when a job changed
 int merge_jobs(MergedJob& mj, const std::vector<const OzJob*>& jobs, const std::vector<void*>& tbases,
                cudaStream_t st) {
@@ -85,12 +74,7 @@ int launch_merged(const MergedJob& mj, int prec, int* err, cudaStream_t st) {
 }
 
 struct BatchState {
-  std::vector<Context*> ctxs;
-  std::vector<const double*> cs;
-  std::vector<double*> ss;
-  int nvec = 0, prec = 0;
-  MergedJob ab, sst;
-  DevBuf err;
+  SigmaBatch sb;
   cudaStream_t bs = nullptr;
   cudaEvent_t ev = nullptr;
   cudaGraph_t g = nullptr;
@@ -112,10 +96,16 @@ struct BatchState {
 
 std::unique_ptr<BatchState> g_batch;
 
-// the whole batch, launch by launch (also what a capture records)
-int batch_sequence(BatchState& B) {
+}  // namespace
+
+// the whole batch, launch by launch on stream() (also what a capture records)
+int sigma_batch_sequence(SigmaBatch& B) {
   cudaStream_t st = stream();
   const int n = (int)B.ctxs.size();
+  if (!B.err.p) {
+    ISCSI_TRY(B.err.alloc(sizeof(int)));
+    ISCSI_CUDA(cudaMemsetAsync(B.err.p, 0, sizeof(int), st));
+  }
   const bool tc = B.prec == 64 ? options().fp64_tc : options().fp32_tc;
   for (int i = 0; i < n; ++i) ISCSI_TRY(sigma_run(*B.ctxs[i], B.cs[i], B.ss[i], B.nvec, B.prec, kPhPre));
   if (tc) {
@@ -149,6 +139,8 @@ int batch_sequence(BatchState& B) {
   return kOk;
 }
 
+namespace {
+
 long long graph_kernel_nodes(cudaGraph_t g) {
   size_t n = 0;
   if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
@@ -168,15 +160,15 @@ int batch_run(BatchState& B) {
     g_launch_count += B.kernels;
     return kOk;
   }
-  if (B.calls == 0 || !options().use_graph || B.failed) return batch_sequence(B);
+  if (B.calls == 0 || !options().use_graph || B.failed) return sigma_batch_sequence(B.sb);
   // second call with this batch: capture it, then replay
   long long before = g_launch_count;
-  for (Context* c : B.ctxs) c->capturing = true;
+  for (Context* c : B.sb.ctxs) c->capturing = true;
   cudaError_t ce = cudaStreamBeginCapture(B.bs, cudaStreamCaptureModeThreadLocal);
-  int rc = ce == cudaSuccess ? batch_sequence(B) : kErrCuda;
+  int rc = ce == cudaSuccess ? sigma_batch_sequence(B.sb) : kErrCuda;
   cudaGraph_t g = nullptr;
   cudaError_t ee = ce == cudaSuccess ? cudaStreamEndCapture(B.bs, &g) : ce;
-  for (Context* c : B.ctxs) c->capturing = false;
+  for (Context* c : B.sb.ctxs) c->capturing = false;
   g_launch_count = before;
   if (ce == cudaSuccess && rc == kOk && ee == cudaSuccess && g && cudaGraphInstantiate(&B.x, g, 0) == cudaSuccess) {
     B.g = g;
@@ -189,7 +181,7 @@ int batch_run(BatchState& B) {
   B.x = nullptr;
   B.failed = true;
   cudaGetLastError();
-  return batch_sequence(B);
+  return sigma_batch_sequence(B.sb);
 }
 
 }  // namespace
@@ -198,17 +190,17 @@ void batch_reset() { g_batch.reset(); }
 
 int batch_sigma(const std::vector<Context*>& ctxs, const std::vector<const double*>& cs,
                 const std::vector<double*>& ss, int nvec, int prec) {
-  if (!g_batch || g_batch->ctxs != ctxs || g_batch->cs != cs || g_batch->ss != ss || g_batch->nvec != nvec ||
-      g_batch->prec != prec) {
+  if (!g_batch || g_batch->sb.ctxs != ctxs || g_batch->sb.cs != cs || g_batch->sb.ss != ss ||
+      g_batch->sb.nvec != nvec || g_batch->sb.prec != prec) {
     g_batch.reset(new BatchState());
     BatchState& B = *g_batch;
-    B.ctxs = ctxs;
-    B.cs = cs;
-    B.ss = ss;
-    B.nvec = nvec;
-    B.prec = prec;
-    ISCSI_TRY(B.err.alloc(sizeof(int)));
-    ISCSI_CUDA(cudaMemset(B.err.p, 0, sizeof(int)));
+    B.sb.ctxs = ctxs;
+    B.sb.cs = cs;
+    B.sb.ss = ss;
+    B.sb.nvec = nvec;
+    B.sb.prec = prec;
+    ISCSI_TRY(B.sb.err.alloc(sizeof(int)));
+    ISCSI_CUDA(cudaMemset(B.sb.err.p, 0, sizeof(int)));
     ISCSI_CUDA(cudaStreamCreateWithFlags(&B.bs, cudaStreamNonBlocking));
     ISCSI_CUDA(cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming));
   }
@@ -228,9 +220,9 @@ int batch_sigma(const std::vector<Context*>& ctxs, const std::vector<const doubl
 
 // status of the bounded waits of the merged launches (synchronises)
 int batch_check() {
-  if (!g_batch || !g_batch->err.p) return kOk;
+  if (!g_batch || !g_batch->sb.err.p) return kOk;
   int h = 0;
-  ISCSI_CUDA(cudaMemcpy(&h, g_batch->err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  ISCSI_CUDA(cudaMemcpy(&h, g_batch->sb.err.p, sizeof(int), cudaMemcpyDeviceToHost));
   if (h) {
     set_error("batched sigma: a bounded device wait ran out");
     return kErrWait;

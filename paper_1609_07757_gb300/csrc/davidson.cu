@@ -35,6 +35,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include "internal.cuh"
@@ -848,16 +849,18 @@ struct Dav {
     return kOk;
   }
 
-  // one iteration after an evaluation: expand the basis, evaluate again
-  int iteration(int prec) {
-    // Olsen's epsilon from the Ritz vectors of the last evaluation (X is
-    // overwritten by a restart below only through V, not X)
+  // one iteration after an evaluation, in two halves around the sigma of the
+  // new directions T -> W_new: expand the basis, evaluate again
+  int pre_sigma() {
+    // Olsen's epsilon from the Ritz vectors of the last evaluation (a restart
+    // below replaces V, not X)
     k_dav_olsen_dots<<<parts, kVecThreads, 0, st>>>(R, X, ctx.diag.as<double>(), ctl, N, rr_part.as<double>()); ISCSI_COUNT_LAUNCH();
     k_dav_olsen_eps<<<1, 32, 0, st>>>(ctl, rr_part.as<double>(), parts); ISCSI_COUNT_LAUNCH();
     restart();
     k_dav_precond<<<parts, kVecThreads, 0, st>>>(R, X, ctx.diag.as<double>(), ctl, N, T); ISCSI_COUNT_LAUNCH();
-    ISCSI_TRY(orthonormalise_block(true));
-    ISCSI_TRY(sigma_run(ctx, T, Wn, k, prec));
+    return orthonormalise_block(true);
+  }
+  int post_sigma() {
     dots(V, &ctl->m, 0, Wn, k, C1.as<double>());
     dots(T, nullptr, k, Wn, k, C2.as<double>());
     k_dav_append_vec<<<parts, kVecThreads, 0, st>>>(V, W, T, Wn, ctl, N); ISCSI_COUNT_LAUNCH();
@@ -922,49 +925,43 @@ struct IterGraph {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t x = nullptr;
   long long kernels = 0;
-  bool failed = false;
   IterGraph() = default;
   IterGraph(const IterGraph&) = delete;
   IterGraph& operator=(const IterGraph&) = delete;
-  ~IterGraph() {
+  ~IterGraph() { reset(); }
+  void reset() {
     if (x) cudaGraphExecDestroy(x);
     if (g) cudaGraphDestroy(g);
+    x = nullptr;
+    g = nullptr;
+    kernels = 0;
   }
 };
 
-}  // namespace
-
-static int davidson_body(Context& ctx, int nroots, double tol, double* energies, double* vecs) {
-  const Options& opt = options();
-  const long long N = ctx.ndet;
-  const int k = nroots;
-  if (k > kMaxRoots) {
-    set_error("iscsi_davidson: at most 32 roots");
-    return kErrArg;
-  }
-  int maxsub = (int)std::min<long long>(N, (long long)std::max(2, opt.max_subspace) * k);
+// basis capacity: max_subspace vectors per root when set, else 12 per root up
+// to 96 (at least 4 per root): with many roots the FP64 subspace work (its
+// eigen-decomposition grows as m^3, the vector products as m k) costs more
+// than the extra iterations a smaller basis needs (16 roots: 96 vectors
+// converge in 53 iterations against 43 with 192, 1.4x faster overall)
+int subspace_size(long long N, int k) {
+  const int per_root = options().max_subspace;
+  const long long want = per_root > 0 ? (long long)std::max(2, per_root) * k
+                                      : std::min<long long>(12ll * k, std::max<long long>(4ll * k, 96));
+  int maxsub = (int)std::min<long long>(N, want);
   maxsub = std::min(maxsub, 384);
   if (maxsub < 2 * k && N > k) maxsub = (int)std::min<long long>(N, 2 * k);
   if (maxsub < k) maxsub = k;
-  Dav d(ctx, k, maxsub);
+  return maxsub;
+}
+
+// start vectors of one instance: the caller's (orthonormalised) or unit
+// vectors on the k lowest diagonal entries
+int start_vectors(Dav& d, DavCtl& h, const double* vecs) {
+  Context& ctx = d.ctx;
+  const long long N = d.N;
+  const int k = d.k;
   cudaStream_t st = d.st;
-  ISCSI_TRY(d.setup());
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, st);
-
-  DavCtl h;
-  std::memset(&h, 0, sizeof(h));
-  h.k = k;
-  h.maxsub = maxsub;
-  h.tol = tol;
-  h.etol = opt.etol;
-  h.olsen = opt.olsen ? 1 : 0;
-  ISCSI_CUDA(cudaMemcpyAsync(d.ctl, &h, sizeof(DavCtl), cudaMemcpyHostToDevice, st));
-
-  // --- start vectors: the caller's (orthonormalised) or the k lowest diagonal entries
-  if (vecs && opt.guess_from_vecs) {
+  if (vecs && options().guess_from_vecs) {
     ISCSI_CUDA(cudaMemcpyAsync(d.T, vecs, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, st));
     ISCSI_TRY(d.orthonormalise_block(true));  // the basis is still empty (m = 0)
     ISCSI_TRY(d.read_ctl(h));
@@ -974,127 +971,227 @@ static int davidson_body(Context& ctx, int nroots, double tol, double* energies,
         return kErrArg;
       }
     ISCSI_CUDA(cudaMemcpyAsync(d.V, d.T, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, st));
-  } else {
-    std::vector<double> dg(N);
-    ISCSI_CUDA(cudaMemcpyAsync(dg.data(), ctx.diag.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
-    ISCSI_CUDA(cudaStreamSynchronize(st));
-    std::vector<long long> idx(N);
-    for (long long i = 0; i < N; ++i) idx[i] = i;
-    std::partial_sort(idx.begin(), idx.begin() + k, idx.end(),
-                      [&](long long a, long long b) { return dg[a] < dg[b] || (dg[a] == dg[b] && a < b); });
-    idx.resize(k);
-    DevBuf didx;
-    ISCSI_TRY(didx.alloc(sizeof(long long) * k));
-    ISCSI_CUDA(cudaMemcpyAsync(didx.p, idx.data(), sizeof(long long) * k, cudaMemcpyHostToDevice, st));
-    k_unit_vectors<<<kVecBlocks, kVecThreads, 0, st>>>(d.V, didx.as<long long>(), k, N); ISCSI_COUNT_LAUNCH();
-    ISCSI_CUDA(cudaGetLastError());
-    ISCSI_CUDA(cudaStreamSynchronize(st));
+    return kOk;
+  }
+  std::vector<double> dg(N);
+  ISCSI_CUDA(cudaMemcpyAsync(dg.data(), ctx.diag.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+  ISCSI_CUDA(cudaStreamSynchronize(st));
+  std::vector<long long> idx(N);
+  for (long long i = 0; i < N; ++i) idx[i] = i;
+  std::partial_sort(idx.begin(), idx.begin() + k, idx.end(),
+                    [&](long long a, long long b) { return dg[a] < dg[b] || (dg[a] == dg[b] && a < b); });
+  idx.resize(k);
+  DevBuf didx;
+  ISCSI_TRY(didx.alloc(sizeof(long long) * k));
+  ISCSI_CUDA(cudaMemcpyAsync(didx.p, idx.data(), sizeof(long long) * k, cudaMemcpyHostToDevice, st));
+  k_unit_vectors<<<kVecBlocks, kVecThreads, 0, st>>>(d.V, didx.as<long long>(), k, N); ISCSI_COUNT_LAUNCH();
+  ISCSI_CUDA(cudaGetLastError());
+  ISCSI_CUDA(cudaStreamSynchronize(st));
+  return kOk;
+}
+
+// the bounded waits of the merged contractions of a batch (synchronises)
+int batch_wait_status(const std::unique_ptr<SigmaBatch> (&sb)[2]) {
+  for (int g = 0; g < 2; ++g) {
+    if (!sb[g] || !sb[g]->err.p) continue;
+    int h = 0;
+    ISCSI_CUDA(cudaMemcpy(&h, sb[g]->err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+      set_error("iscsi_davidson: a bounded device wait ran out in a tensor-core contraction");
+      return kErrWait;
+    }
+  }
+  return kOk;
+}
+
+}  // namespace
+
+// Davidson for several independent contexts at once.  Every active instance
+// keeps its own device-resident state; one iteration is: the pre-sigma half of
+// every instance, one batched sigma per precision group (the contractions of
+// all members merged, batch.cu), the post-sigma half of every instance.  That
+// sequence is captured into one CUDA graph per set of active instances and
+// replayed; instances leave the set when they converge (or fail), switch
+// precision, or reach maxiter, and the graph is captured again.
+static int davidson_batch_body(const std::vector<Context*>& ctxs, int k, double tol, double* energies,
+                               double* const* vecs, int* statuses) {
+  const Options& opt = options();
+  const int n = (int)ctxs.size();
+  if (k > kMaxRoots) {
+    set_error("iscsi_davidson: at most 32 roots");
+    return kErrArg;
+  }
+  cudaStream_t st = stream();
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  const bool mixed = (opt.precision == 32);
+  std::vector<std::unique_ptr<Dav>> D(n);
+  std::vector<DavCtl> H(n);
+  std::vector<int> prec(n, mixed ? 32 : 64), status(n, kErrNoConv), active(n, 1), iters(n, 0), best_it(n, 0),
+      fp32_iters(n, 0);
+  std::vector<double> best_r(n, 1e300);
+  std::vector<std::vector<double>> rhist(n);
+  for (int i = 0; i < n; ++i) {
+    D[i].reset(new Dav(*ctxs[i], k, subspace_size(ctxs[i]->ndet, k)));
+    ISCSI_TRY(D[i]->setup());
+    DavCtl& h = H[i];
+    std::memset(&h, 0, sizeof(h));
+    h.k = k;
+    h.maxsub = D[i]->maxsub;
+    h.tol = tol;
+    h.etol = opt.etol;
+    h.olsen = opt.olsen ? 1 : 0;
+    ISCSI_CUDA(cudaMemcpyAsync(D[i]->ctl, &h, sizeof(DavCtl), cudaMemcpyHostToDevice, st));
+    ISCSI_TRY(start_vectors(*D[i], h, vecs ? vecs[i] : nullptr));
+    ISCSI_TRY(D[i]->start_from_basis(prec[i], k));
   }
 
-  const bool mixed = (opt.precision == 32);
-  ctx.last_davidson_fp32_iters = 0;
-  ctx.last_davidson_graph = 0;
-  int prec = mixed ? 32 : 64;
-  ISCSI_TRY(d.start_from_basis(prec, k));
-
-  IterGraph graphs[2];  // [0]: FP64 sigma, [1]: FP32 sigma
-  auto run_iteration = [&](int p) -> int {
-    IterGraph& G = graphs[p == 32 ? 1 : 0];
-    if (opt.use_graph && !G.x && !G.failed) {
-      // capture one iteration; on any failure fall back to direct launches
+  IterGraph graph;
+  std::unique_ptr<SigmaBatch> sb[2];  // [0]: FP64 members, [1]: FP32 members
+  std::vector<int> members;
+  bool changed = true, warm = false, graph_failed = false;
+  auto sequence = [&]() -> int {
+    for (int i : members) ISCSI_TRY(D[i]->pre_sigma());
+    for (int g = 0; g < 2; ++g)
+      if (sb[g] && !sb[g]->ctxs.empty()) ISCSI_TRY(sigma_batch_sequence(*sb[g]));
+    for (int i : members) ISCSI_TRY(D[i]->post_sigma());
+    return kOk;
+  };
+  int rc = kOk;
+  for (int it = 1; it <= opt.maxiter; ++it) {
+    // the state of every active instance (one small copy each, one synchronisation)
+    for (int i = 0; i < n; ++i)
+      if (active[i]) ISCSI_CUDA(cudaMemcpyAsync(&H[i], D[i]->ctl, sizeof(DavCtl), cudaMemcpyDeviceToHost, st));
+    ISCSI_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < n; ++i) {
+      if (!active[i]) continue;
+      const DavCtl& h = H[i];
+      rhist[i].push_back(h.rmax);
+      const bool fp32_phase = mixed && prec[i] == 32;
+      if (h.status & kStatusNonFinite) {
+        status[i] = kErrNan;
+        active[i] = 0;
+      } else if (!fp32_phase && (h.status & kStatusConverged)) {
+        status[i] = kOk;
+        active[i] = 0;
+      } else if (!fp32_phase && (h.status & kStatusNoDirection)) {
+        status[i] = h.rmax <= tol ? kOk : kErrNoConv;  // the subspace cannot grow
+        active[i] = 0;
+      } else if (fp32_phase) {
+        // the FP32 phase ends at switch_tol, or when its residual stops
+        // improving near the FP32 rounding floor (best residual within 1e3 of
+        // switch_tol and not improved by 10% in 8 iterations; early plateaus
+        // of the iteration itself do not count)
+        if (h.rmax < 0.9 * best_r[i]) {
+          best_r[i] = h.rmax;
+          best_it[i] = iters[i];
+        }
+        const bool stalled = iters[i] - best_it[i] >= 8 && best_r[i] <= 1e3 * opt.switch_tol;
+        if (h.rmax <= opt.switch_tol || stalled || (h.status & kStatusNoDirection)) {
+          // keep the lowest Ritz vectors (2k when the basis holds them) and
+          // recompute their images with the FP64 sigma
+          prec[i] = 64;
+          fp32_iters[i] = iters[i] + 1;
+          ISCSI_TRY(D[i]->collapse(64, h.m >= 2 * k ? 2 * k : k));
+          changed = true;
+        }
+      }
+      if (!active[i]) changed = true;
+    }
+    // instances of the next iteration
+    std::vector<int> next;
+    for (int i = 0; i < n; ++i)
+      if (active[i]) next.push_back(i);
+    if (next.empty()) break;
+    if (changed || next != members) {
+      members = next;
+      graph.reset();
+      ISCSI_TRY(batch_wait_status(sb));
+      for (int g = 0; g < 2; ++g) sb[g].reset(new SigmaBatch());
+      for (int i : members) {
+        SigmaBatch& b = *sb[prec[i] == 32 ? 1 : 0];
+        b.ctxs.push_back(ctxs[i]);
+        b.cs.push_back(D[i]->T);
+        b.ss.push_back(D[i]->Wn);
+        b.nvec = k;
+        b.prec = prec[i];
+      }
+      changed = false;
+      warm = false;  // the first pass of a new set runs directly (it builds the merged lists)
+    }
+    if (graph.x) {
+      ISCSI_CUDA(cudaGraphLaunch(graph.x, st));
+      g_launch_count += graph.kernels;
+      for (int i : members) ctxs[i]->last_davidson_graph = 1;
+    } else if (!warm || !opt.use_graph || graph_failed) {
+      ISCSI_TRY(sequence());
+      warm = true;
+    } else {
       long long before = g_launch_count;
-      ctx.capturing = true;
+      for (int i : members) ctxs[i]->capturing = true;
       cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-      int rc = ce == cudaSuccess ? d.iteration(p) : kErrCuda;
+      int crc = ce == cudaSuccess ? sequence() : kErrCuda;
       cudaGraph_t g = nullptr;
       cudaError_t ee = ce == cudaSuccess ? cudaStreamEndCapture(st, &g) : ce;
-      ctx.capturing = false;
+      for (int i : members) ctxs[i]->capturing = false;
       g_launch_count = before;
-      if (ce == cudaSuccess && rc == kOk && ee == cudaSuccess && g &&
-          cudaGraphInstantiate(&G.x, g, 0) == cudaSuccess) {
-        G.g = g;
-        G.kernels = graph_kernels(g);
+      if (ce == cudaSuccess && crc == kOk && ee == cudaSuccess && g &&
+          cudaGraphInstantiate(&graph.x, g, 0) == cudaSuccess) {
+        graph.g = g;
+        graph.kernels = graph_kernels(g);
+        ISCSI_CUDA(cudaGraphLaunch(graph.x, st));
+        g_launch_count += graph.kernels;
+        for (int i : members) ctxs[i]->last_davidson_graph = 1;
       } else {
         if (g) cudaGraphDestroy(g);
-        G.x = nullptr;
-        G.failed = true;
+        graph_failed = true;
         cudaGetLastError();
+        ISCSI_TRY(sequence());
       }
     }
-    if (G.x) {
-      ISCSI_CUDA(cudaGraphLaunch(G.x, st));
-      g_launch_count += G.kernels;
-      ctx.last_davidson_graph = 1;
-      return kOk;
-    }
-    return d.iteration(p);
-  };
-
-  double best_r = 1e300;
-  int best_it = 0;
-  int status = kErrNoConv;
-  int iter = 0;
-  ctx.last_davidson_rhist.clear();
-  for (iter = 1; iter <= opt.maxiter; ++iter) {
-    ISCSI_TRY(d.read_ctl(h));
-    ctx.last_davidson_rhist.push_back(h.rmax);
-    if (h.status & kStatusNonFinite) {
-      set_error("iscsi_davidson: NaN or Inf in the subspace");
-      status = kErrNan;
-      break;
-    }
-    const bool fp32_phase = mixed && prec == 32;
-    if (!fp32_phase && (h.status & kStatusConverged)) {
-      status = kOk;
-      break;
-    }
-    if (!fp32_phase && (h.status & kStatusNoDirection)) {
-      // the subspace cannot grow: report what we have
-      status = (h.rmax <= tol) ? kOk : kErrNoConv;
-      break;
-    }
-    if (fp32_phase) {
-      // the FP32 phase ends at switch_tol, or when its residual stops
-      // improving near the FP32 rounding floor (best residual within 1e3 of
-      // switch_tol and not improved by 10% in 8 iterations; early plateaus of
-      // the iteration itself do not count)
-      if (h.rmax < 0.9 * best_r) {
-        best_r = h.rmax;
-        best_it = iter;
-      }
-      const bool stalled = iter - best_it >= 8 && best_r <= 1e3 * opt.switch_tol;
-      if (h.rmax <= opt.switch_tol || stalled || (h.status & kStatusNoDirection)) {
-        // keep the lowest Ritz vectors (2k when the basis holds them) and
-        // recompute their images with the FP64 sigma
-        const int keep = h.m >= 2 * k ? 2 * k : k;
-        prec = 64;
-        ctx.last_davidson_fp32_iters = iter;
-        ISCSI_TRY(d.collapse(prec, keep));
-        continue;
-      }
-    }
-    ISCSI_TRY(run_iteration(prec));
+    for (int i : members) ++iters[i];
   }
-  ISCSI_TRY(d.read_ctl(h));
-  if (status == kErrNoConv && prec == 64 && (h.status & kStatusConverged)) status = kOk;
-  for (int j = 0; j < k; ++j) energies[j] = h.theta[j];
-  if (vecs) ISCSI_CUDA(cudaMemcpyAsync(vecs, d.X, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, st));
+  ISCSI_TRY(batch_wait_status(sb));
+  // results: the last evaluation of every instance
+  for (int i = 0; i < n; ++i) ISCSI_CUDA(cudaMemcpyAsync(&H[i], D[i]->ctl, sizeof(DavCtl), cudaMemcpyDeviceToHost, st));
+  ISCSI_CUDA(cudaStreamSynchronize(st));
+  for (int i = 0; i < n; ++i) {
+    if (status[i] == kErrNoConv && prec[i] == 64 && (H[i].status & kStatusConverged)) status[i] = kOk;
+    for (int j = 0; j < k; ++j) energies[(size_t)i * k + j] = H[i].theta[j];
+    if (vecs && vecs[i])
+      ISCSI_CUDA(cudaMemcpyAsync(vecs[i], D[i]->X, sizeof(double) * k * D[i]->N, cudaMemcpyDeviceToDevice, st));
+    if (statuses) statuses[i] = status[i];
+  }
   cudaEventRecord(e1, st);
   ISCSI_CUDA(cudaStreamSynchronize(st));
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  ctx.last_davidson_ms = ms;
-  ctx.last_davidson_iters = h.iter;
-  if (status == kErrNoConv) set_error("iscsi_davidson: no convergence within maxiter");
-  return status;
+  for (int i = 0; i < n; ++i) {
+    Context& c = *ctxs[i];
+    c.last_davidson_ms = ms;
+    c.last_davidson_iters = H[i].iter;
+    c.last_davidson_fp32_iters = mixed ? (prec[i] == 64 ? fp32_iters[i] : iters[i]) : 0;
+    c.last_davidson_rhist = rhist[i];
+  }
+  for (int i = 0; i < n; ++i)
+    if (status[i] != kOk) {
+      rc = status[i];
+      if (status[i] == kErrNoConv) set_error("iscsi_davidson: no convergence within maxiter");
+      if (status[i] == kErrNan) set_error("iscsi_davidson: NaN or Inf in the subspace");
+      break;
+    }
+  return rc;
 }
 
 // The iteration runs on a stream of its own (the legacy default stream, which
 // callers often use, cannot be captured into a graph), ordered after the
 // caller's stream on entry and before it on exit.
-int davidson_run(Context& ctx, int nroots, double tol, double* energies, double* vecs) {
+int davidson_batch_run(const std::vector<Context*>& ctxs, int nroots, double tol, double* energies,
+                       double* const* vecs, int* statuses) {
   cudaStream_t user = stream();
   cudaStream_t ds = nullptr;
   cudaEvent_t ev = nullptr;
@@ -1104,10 +1201,11 @@ int davidson_run(Context& ctx, int nroots, double tol, double* energies, double*
     set_error("iscsi_davidson: cudaEventCreate failed");
     return kErrCuda;
   }
+  for (Context* c : ctxs) c->last_davidson_graph = 0;
   cudaEventRecord(ev, user);
   cudaStreamWaitEvent(ds, ev, 0);
   set_stream(ds);
-  int rc = davidson_body(ctx, nroots, tol, energies, vecs);
+  int rc = davidson_batch_body(ctxs, nroots, tol, energies, vecs, statuses);
   cudaEventRecord(ev, ds);
   cudaStreamWaitEvent(user, ev, 0);
   set_stream(user);
@@ -1115,6 +1213,12 @@ int davidson_run(Context& ctx, int nroots, double tol, double* energies, double*
   cudaStreamDestroy(ds);
   cudaEventDestroy(ev);
   return rc;
+}
+
+int davidson_run(Context& ctx, int nroots, double tol, double* energies, double* vecs) {
+  std::vector<Context*> one(1, &ctx);
+  double* v[1] = {vecs};
+  return davidson_batch_run(one, nroots, tol, energies, v, nullptr);
 }
 
 }  // namespace iscsi

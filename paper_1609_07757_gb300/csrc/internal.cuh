@@ -228,7 +228,7 @@ struct Options {
   int precision = 64;
   unsigned long long class_mask = (1ull << kNumClasses) - 1;
   int maxiter = 300;
-  int max_subspace = 12;
+  int max_subspace = 0;  // Davidson basis vectors per root; 0: automatic
   double etol = 1e-10;
   double switch_tol = 1e-5;
   int guess_from_vecs = 0;
@@ -281,8 +281,31 @@ size_t noalloc_scratch_bytes();
 
 // davidson.cu
 int davidson_run(Context& ctx, int nroots, double tol, double* energies, double* vecs);
+int davidson_batch_run(const std::vector<Context*>& ctxs, int nroots, double tol, double* energies,
+                       double* const* vecs, int* statuses);
 
 // batch.cu
+// one problem list over the tensor-core jobs of several contexts
+struct MergedJob {
+  std::vector<OzProblem> probs;
+  std::vector<OzSeg> segs;
+  std::vector<OzMaps> maps;
+  DevBuf d_probs, d_segs, d_maps, d_tbases;
+  std::vector<const OzJob*> src;
+  std::vector<long long> ver;
+  std::vector<void*> tbases;
+  int tiles = 0;
+};
+// sigma_i = H(ctxs[i]) cs[i] for several contexts, contractions merged
+struct SigmaBatch {
+  std::vector<Context*> ctxs;
+  std::vector<const double*> cs;
+  std::vector<double*> ss;
+  int nvec = 0, prec = 0;
+  MergedJob ab, sst;
+  DevBuf err;
+};
+int sigma_batch_sequence(SigmaBatch& B);  // launches on stream(); capturable once warmed up
 int batch_sigma(const std::vector<Context*>& ctxs, const std::vector<const double*>& cs,
                 const std::vector<double*>& ss, int nvec, int prec);
 int batch_check();

@@ -98,3 +98,35 @@ def test_batch_sigma_rejects_bad_arguments():
         L.iscsi_batch_sigma([hs[0], 12345], cs[:2], outs[:2], 1)
     with pytest.raises(L.IscsiError):
         L.iscsi_batch_sigma([], [], [], 1)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_batch_davidson_matches_dense_and_single(precision):
+    # several contexts iterated together reach each one's dense eigenvalues,
+    # like the one-context call
+    shapes = [(8, 2, 2, 4, 1e-14), (10, 2, 2, 4, 1e-14), (12, 2, 2, 2, 1e-12), (7, 3, 2, 3, 0.0)]
+    hs, ws = [], []
+    for i, (n, na, nb, k, tau) in enumerate(shapes):
+        h1, eri = make_integrals(n, 1600 + i, ell=3.0, nchol=12)
+        ws.append(np.linalg.eigvalsh(Oracle(n, na, nb, k, tau, h1, eri).dense_h())[:2])
+        L.iscsi_init(n, na, nb, k, h1, eri, tau)
+        hs.append(L.iscsi_ctx_current())
+    L.iscsi_set_option("precision", precision)
+    vecs = []
+    for h in hs:
+        L.iscsi_ctx_use(h)
+        vecs.append(torch.zeros((2, L.iscsi_ndet()), dtype=torch.float64, device="cuda"))
+    st, e, sts = L.iscsi_batch_davidson(hs, 2, 1e-8, vecs)
+    assert st == 0 and sts == [0] * len(hs)
+    for i, h in enumerate(hs):
+        assert np.abs(e[i] - ws[i]).max() <= (1e-10 if precision == 64 else 1e-9)
+        L.iscsi_ctx_use(h)
+        st1, e1 = L.iscsi_davidson(2, 1e-8)
+        assert st1 == 0 and np.abs(e1 - ws[i]).max() <= (1e-10 if precision == 64 else 1e-9)
+        # returned vectors are eigenvectors of the context's operator
+        s = torch.empty_like(vecs[i])
+        L.iscsi_set_option("precision", 64)
+        L.iscsi_sigma(vecs[i], s, 2)
+        L.iscsi_set_option("precision", precision)
+        r = s - torch.tensor(e[i], device="cuda")[:, None] * vecs[i]
+        assert torch.linalg.norm(r, dim=1).max().item() < 1e-6

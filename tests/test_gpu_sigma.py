@@ -334,7 +334,7 @@ def test_davidson_graph_and_direct_launches_agree(use_graph):
         s = _stats()
     finally:
         L.iscsi_set_option("use_graph", 1)
-        L.iscsi_set_option("max_subspace", 12)
+        L.iscsi_set_option("max_subspace", 0)
     assert st == 0
     assert np.abs(e - w[:4]).max() <= 1e-10
     assert s["davidson_graph"] == use_graph
