@@ -98,7 +98,64 @@ std::unique_ptr<BatchState> g_batch;
 
 }  // namespace
 
-// the whole batch, launch by launch on stream() (also what a capture records)
+StreamPool::~StreamPool() {
+  for (cudaEvent_t e : done) cudaEventDestroy(e);
+  if (start) cudaEventDestroy(start);
+  for (cudaStream_t x : s) {
+    cudaStreamSynchronize(x);
+    cudaStreamDestroy(x);
+  }
+}
+
+int StreamPool::init(int n) {
+  if ((int)s.size() >= n) return kOk;
+  if (!start) ISCSI_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  while ((int)s.size() < n) {
+    cudaStream_t x;
+    cudaEvent_t e;
+    ISCSI_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+    ISCSI_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    s.push_back(x);
+    done.push_back(e);
+  }
+  return kOk;
+}
+
+int StreamPool::fork(cudaStream_t main) {
+  ISCSI_CUDA(cudaEventRecord(start, main));
+  for (cudaStream_t x : s) ISCSI_CUDA(cudaStreamWaitEvent(x, start, 0));
+  return kOk;
+}
+
+int StreamPool::join(cudaStream_t main) {
+  for (size_t i = 0; i < s.size(); ++i) {
+    ISCSI_CUDA(cudaEventRecord(done[i], s[i]));
+    ISCSI_CUDA(cudaStreamWaitEvent(main, done[i], 0));
+  }
+  return kOk;
+}
+
+namespace {
+
+// one phase of every context, each on a pool stream (concurrent chains)
+int phase_all(SigmaBatch& B, int phase) {
+  cudaStream_t main = stream();
+  ISCSI_TRY(B.pool.fork(main));
+  int rc = kOk;
+  for (size_t i = 0; i < B.ctxs.size() && rc == kOk; ++i) {
+    set_stream(B.pool.at((int)i));
+    rc = sigma_run(*B.ctxs[i], B.cs[i], B.ss[i], B.nvec, B.prec, phase);
+  }
+  set_stream(main);
+  ISCSI_TRY(rc);
+  return B.pool.join(main);
+}
+
+}  // namespace
+
+// the whole batch, launch by launch on stream() (also what a capture records):
+// the per-context phases run on concurrent pool streams, the merged
+// contractions on the main stream between them
 int sigma_batch_sequence(SigmaBatch& B) {
   cudaStream_t st = stream();
   const int n = (int)B.ctxs.size();
@@ -106,8 +163,9 @@ int sigma_batch_sequence(SigmaBatch& B) {
     ISCSI_TRY(B.err.alloc(sizeof(int)));
     ISCSI_CUDA(cudaMemsetAsync(B.err.p, 0, sizeof(int), st));
   }
+  ISCSI_TRY(B.pool.init(std::min(n, 16)));
   const bool tc = B.prec == 64 ? options().fp64_tc : options().fp32_tc;
-  for (int i = 0; i < n; ++i) ISCSI_TRY(sigma_run(*B.ctxs[i], B.cs[i], B.ss[i], B.nvec, B.prec, kPhPre));
+  ISCSI_TRY(phase_all(B, kPhPre));
   if (tc) {
     std::vector<const OzJob*> jobs;
     std::vector<void*> tb;
@@ -119,9 +177,9 @@ int sigma_batch_sequence(SigmaBatch& B) {
     ISCSI_TRY(merge_jobs(B.ab, jobs, tb, st));
     ISCSI_TRY(launch_merged(B.ab, B.prec, B.err.as<int>(), st));
   } else {
-    for (int i = 0; i < n; ++i) ISCSI_TRY(sigma_run(*B.ctxs[i], B.cs[i], B.ss[i], B.nvec, B.prec, kPhAbGemm));
+    ISCSI_TRY(phase_all(B, kPhAbGemm));
   }
-  for (int i = 0; i < n; ++i) ISCSI_TRY(sigma_run(*B.ctxs[i], B.cs[i], B.ss[i], B.nvec, B.prec, kPhMid));
+  ISCSI_TRY(phase_all(B, kPhMid));
   {
     std::vector<const OzJob*> jobs;
     std::vector<void*> tb;
@@ -135,7 +193,7 @@ int sigma_batch_sequence(SigmaBatch& B) {
     ISCSI_TRY(merge_jobs(B.sst, jobs, tb, st));
     ISCSI_TRY(launch_merged(B.sst, B.prec, B.err.as<int>(), st));
   }
-  for (int i = 0; i < n; ++i) ISCSI_TRY(sigma_run(*B.ctxs[i], B.cs[i], B.ss[i], B.nvec, B.prec, kPhPost));
+  ISCSI_TRY(phase_all(B, kPhPost));
   return kOk;
 }
 

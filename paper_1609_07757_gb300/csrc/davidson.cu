@@ -1052,12 +1052,26 @@ static int davidson_batch_body(const std::vector<Context*>& ctxs, int k, double 
   std::unique_ptr<SigmaBatch> sb[2];  // [0]: FP64 members, [1]: FP32 members
   std::vector<int> members;
   bool changed = true, warm = false, graph_failed = false;
+  // the halves of every instance run on concurrent pool streams
+  StreamPool dpool;
+  ISCSI_TRY(dpool.init(std::min(n, 16)));
+  auto halves = [&](bool pre) -> int {
+    ISCSI_TRY(dpool.fork(st));
+    int rc2 = kOk;
+    for (size_t j = 0; j < members.size() && rc2 == kOk; ++j) {
+      Dav& d = *D[members[j]];
+      d.st = dpool.at((int)j);
+      rc2 = pre ? d.pre_sigma() : d.post_sigma();
+      d.st = st;
+    }
+    ISCSI_TRY(rc2);
+    return dpool.join(st);
+  };
   auto sequence = [&]() -> int {
-    for (int i : members) ISCSI_TRY(D[i]->pre_sigma());
+    ISCSI_TRY(halves(true));
     for (int g = 0; g < 2; ++g)
       if (sb[g] && !sb[g]->ctxs.empty()) ISCSI_TRY(sigma_batch_sequence(*sb[g]));
-    for (int i : members) ISCSI_TRY(D[i]->post_sigma());
-    return kOk;
+    return halves(false);
   };
   int rc = kOk;
   for (int it = 1; it <= opt.maxiter; ++it) {

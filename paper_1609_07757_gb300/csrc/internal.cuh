@@ -285,6 +285,24 @@ int davidson_batch_run(const std::vector<Context*>& ctxs, int nroots, double tol
                        double* const* vecs, int* statuses);
 
 // batch.cu
+// Streams for the independent per-context work of a batch: fork() makes every
+// pool stream wait for the main stream, join() makes the main stream wait for
+// all of them.  Captured into a graph, the per-context chains become parallel
+// branches that the GPU runs concurrently.
+struct StreamPool {
+  std::vector<cudaStream_t> s;
+  std::vector<cudaEvent_t> done;
+  cudaEvent_t start = nullptr;
+  StreamPool() = default;
+  StreamPool(const StreamPool&) = delete;
+  StreamPool& operator=(const StreamPool&) = delete;
+  ~StreamPool();
+  int init(int n);
+  int fork(cudaStream_t main);
+  int join(cudaStream_t main);
+  cudaStream_t at(int i) const { return s[i % s.size()]; }
+};
+
 // one problem list over the tensor-core jobs of several contexts
 struct MergedJob {
   std::vector<OzProblem> probs;
@@ -304,6 +322,7 @@ struct SigmaBatch {
   int nvec = 0, prec = 0;
   MergedJob ab, sst;
   DevBuf err;
+  StreamPool pool;
 };
 int sigma_batch_sequence(SigmaBatch& B);  // launches on stream(); capturable once warmed up
 int batch_sigma(const std::vector<Context*>& ctxs, const std::vector<const double*>& cs,
