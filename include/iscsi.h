@@ -217,6 +217,13 @@ ISCSI_API iscsi_status iscsi_set_stream(void* stream);
  *   "fp32_tc"          1 (default): with precision 32, both contractions run
  *                      on the tensor cores with three bf16 terms per element
  *                      and FP32 accumulation; 0: FP32 FMA kernels
+ *   "autotune"         1 (default): before the first sigma of a context for a
+ *                      given precision and vector count, time the candidate
+ *                      kernel routings (opposite-spin contraction on the
+ *                      tensor cores or the FMA kernels; same-spin level-block
+ *                      threshold 16/64/256/none) that a flop model puts within
+ *                      3x of the best, and keep the fastest (iscsi_stats
+ *                      "route_fp64" / "route_fp32"); 0: the defaults
  *   "phase_timing"     1: record per-phase CUDA events of every sigma call
  *                      (reported by iscsi_stats; the record restarts when set)
  * Errors: ISCSI_E_ARG for an unknown key or a value out of range.

@@ -233,6 +233,8 @@ iscsi_status iscsi_set_option(const char* key, double value) {
     o.samespin_tc = value != 0;
   } else if (k == "fp32_tc") {
     o.fp32_tc = value != 0;
+  } else if (k == "autotune") {
+    o.autotune = value != 0;
   } else if (k == "phase_timing") {
     o.phase_timing = value != 0;
     Context* ctx = current();
@@ -294,7 +296,23 @@ iscsi_status iscsi_stats(char* json, int len) {
     std::snprintf(v, sizeof(v), i ? ", %.3e" : "%.3e", ctx->last_davidson_rhist[i]);
     out += v;
   }
-  out += "]}";
+  out += "]";
+  // the autotuner's routing per precision and its trials (ab_tc, ss_min or -1 =
+  // none on the tensor cores, predicted ms, measured ms or -1 = pruned)
+  for (int p = 0; p < 2; ++p) {
+    const Context::Route& R = ctx->route[p];
+    char v[160];
+    std::snprintf(v, sizeof(v), ", \"route_fp%d\": {\"ab_tc\": %d, \"ss_min\": %d, \"tuned_nvec\": %d, \"trials\": [",
+                  p == 0 ? 64 : 32, R.ab_tc, R.ss_min >= (1 << 30) ? -1 : R.ss_min, R.tuned_nvec);
+    out += v;
+    for (size_t i = 0; i + 3 < R.trials.size(); i += 4) {
+      std::snprintf(v, sizeof(v), "%s[%d, %d, %.4g, %.4g]", i ? ", " : "", (int)R.trials[i], (int)R.trials[i + 1],
+                    R.trials[i + 2], R.trials[i + 3]);
+      out += v;
+    }
+    out += "]}";
+  }
+  out += "}";
   std::strncpy(json, out.c_str(), len - 1);
   json[len - 1] = 0;
   if (out.size() >= (size_t)len) {

@@ -137,12 +137,15 @@ int StreamPool::join(cudaStream_t main) {
 
 namespace {
 
-// one phase of every context, each on a pool stream (concurrent chains)
-int phase_all(SigmaBatch& B, int phase) {
+// one phase of every context, each on a pool stream (concurrent chains);
+// skip_tc: only the contexts whose opposite-spin contraction is not on the
+// tensor cores (those run in the merged launch)
+int phase_all(SigmaBatch& B, int phase, bool skip_tc = false) {
   cudaStream_t main = stream();
   ISCSI_TRY(B.pool.fork(main));
   int rc = kOk;
   for (size_t i = 0; i < B.ctxs.size() && rc == kOk; ++i) {
+    if (skip_tc && ab_on_tc(*B.ctxs[i], B.prec)) continue;
     set_stream(B.pool.at((int)i));
     rc = sigma_run(*B.ctxs[i], B.cs[i], B.ss[i], B.nvec, B.prec, phase);
   }
@@ -164,20 +167,22 @@ int sigma_batch_sequence(SigmaBatch& B) {
     ISCSI_CUDA(cudaMemsetAsync(B.err.p, 0, sizeof(int), st));
   }
   ISCSI_TRY(B.pool.init(std::min(n, 16)));
-  const bool tc = B.prec == 64 ? options().fp64_tc : options().fp32_tc;
+  // each context's routing is tuned by plain sigma calls before it joins a batch
+  for (int i = 0; i < n; ++i)
+    if (!B.ctxs[i]->capturing) ISCSI_TRY(sigma_autotune(*B.ctxs[i], B.cs[i], B.ss[i], B.nvec, B.prec));
   ISCSI_TRY(phase_all(B, kPhPre));
-  if (tc) {
+  {
+    // opposite spin: the tensor-core contexts in one launch, the others on their own
     std::vector<const OzJob*> jobs;
     std::vector<void*> tb;
     for (int i = 0; i < n; ++i)
-      if (B.ctxs[i]->have_ab) {
+      if (B.ctxs[i]->have_ab && ab_on_tc(*B.ctxs[i], B.prec)) {
         jobs.push_back(B.prec == 64 ? &B.ctxs[i]->oz_ab : &B.ctxs[i]->t3_ab);
         tb.push_back(nullptr);  // absolute output pointers (the context's T workspace)
       }
     ISCSI_TRY(merge_jobs(B.ab, jobs, tb, st));
     ISCSI_TRY(launch_merged(B.ab, B.prec, B.err.as<int>(), st));
-  } else {
-    ISCSI_TRY(phase_all(B, kPhAbGemm));
+    ISCSI_TRY(phase_all(B, kPhAbGemm, /*skip_tc=*/true));
   }
   ISCSI_TRY(phase_all(B, kPhMid));
   {

@@ -194,6 +194,15 @@ struct Context {
   int oz_ma_rows = 0, oz_ma_ld = 0, oz_mb_rows = 0, oz_mb_ld = 0;
   long long oz_cs_elems = 0;
   bool oz_m_ready = false;
+  // kernel routing per precision ([0] FP64, [1] FP32), chosen by the autotuner
+  struct Route {
+    int ab_tc = 1;           // opposite-spin contraction on the tensor cores (else FMA kernels)
+    int ss_min = kThinN;     // same-spin level blocks with more rows and allowed beta strings
+                             // than this run on the tensor cores (else FMA kernels)
+    int tuned_nvec = 0;      // vector count the autotuner ran for (0: not yet)
+    std::vector<double> trials;  // (ab_tc, ss_min, predicted ms, measured ms) per candidate
+  } route[2];
+  long long pl_route_key = -1, pl_route_key32 = -1;  // routing the grouped-GEMM lists were built for
   int pl_ss_tc = -1;  // same-spin routing the FP64 grouped-GEMM list was built for
   // FP32 form of the tensor-core contractions (three bf16 terms per element)
   OzJob t3_ab, t3_ss;
@@ -238,6 +247,7 @@ struct Options {
   int fp64_tc = 1;      // FP64 opposite-spin contraction on the tensor cores (exact bf16 slices)
   int samespin_tc = 1;  // same for the same-spin blocks large enough for a 128 x 64 tile
   int fp32_tc = 1;      // FP32 form: contractions on the tensor cores (three bf16 terms, FP32 accumulation)
+  int autotune = 1;     // time the routing candidates at the first sigma of each vector count
 };
 
 Options& options();
@@ -261,8 +271,10 @@ double ctx_gemm_flops(const Context& ctx, int which);
 // sigma_tc.cu: tensor-core FP64 contractions
 int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec);  // slices of Ct
 int opposite_tc_gemm(Context& ctx);                                                // T = G Ct
-bool samespin_block_on_tc(const Context& ctx, int a);
+bool samespin_block_on_tc(const Context& ctx, int a, int prec);
 bool samespin_tc_active(const Context& ctx);
+bool ab_on_tc(const Context& ctx, int prec);
+int sigma_autotune(Context& ctx, const double* c, double* sigma, int nvec, int prec);
 int samespin_tc_operands(Context& ctx, const double* c, double* sigma, int nvec);  // slices of C, job
 int samespin_tc_gemm(Context& ctx, double* sigma);                                 // sigma += same-spin
 int opposite_tc32_operands(Context& ctx, const float* c, float* ttw, int nvec);   // FP32 form

@@ -542,7 +542,7 @@ static int build_problems(Context& ctx, int nvec, const T* G, const T* Ma, const
       int nba = (int)ctx.nb_allowed_lvl[a];
       if (rows == 0 || nba == 0) continue;
       const int routed = std::is_same<T, double>::value ? ctx.pl_ss_tc : ctx.pl_ss_tc32;
-      if (routed == 1 && samespin_block_on_tc(ctx, a)) continue;
+      if (routed == 1 && samespin_block_on_tc(ctx, a, std::is_same<T, double>::value ? 64 : 32)) continue;
       long long obase = ctx.off_h[SA.level_start[a]];
       Problem<T> p;
       p.c = (long long)v * ctx.ndet + obase;
@@ -680,17 +680,23 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
   T* ttw = ctx.tt.as<T>();
   constexpr bool f64 = std::is_same<T, double>::value;
   const int ss_tc = (f64 ? samespin_tc_active(ctx) : samespin_tc32_active(ctx)) ? 1 : 0;
-  const bool tc_path = f64 ? options().fp64_tc : options().fp32_tc;
+  const bool tc_path = ab_on_tc(ctx, f64 ? 64 : 32);
   // per-phase events only when the whole step runs in this call
   const bool timed = phases == kPhAll;
   const int call = ctx.ntimed;
   auto ev = [&](int ph) { return timed ? timing_event(ctx, call, ph, st) : kOk; };
   if (phases & kPhPre) {
     // problem lists depend on nvec, the workspaces and the same-spin routing, not on the vectors
+    // a new routing (autotuner) rebuilds the FMA lists and the same-spin tensor-core job
     int& routed = f64 ? ctx.pl_ss_tc : ctx.pl_ss_tc32;
-    if (routed != ss_tc) {
+    long long& rkey = f64 ? ctx.pl_route_key : ctx.pl_route_key32;
+    const Context::Route& R = ctx.route[f64 ? 0 : 1];
+    const long long key = ((long long)R.ss_min << 2) | (R.ab_tc << 1) | ss_tc;
+    if (routed != ss_tc || rkey != key) {
       routed = ss_tc;
+      rkey = key;
       pl_nvec = 0;
+      (f64 ? ctx.oz_ss : ctx.t3_ss).nvec = -1;
     }
     if (pl_nvec != nvec) {
       ISCSI_TRY(build_problems<T>(ctx, nvec, G, Ma, Mb, ctw, ttw, ab, ss));
@@ -760,6 +766,7 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
 
 int sigma_run(Context& ctx, const double* c, double* sigma, int nvec, int precision, int phases) {
   cudaStream_t st = stream();
+  if (phases == kPhAll) ISCSI_TRY(sigma_autotune(ctx, c, sigma, nvec, precision));
   if (phases & kPhPre) ISCSI_TRY(sigma_workspace(ctx, nvec, precision));
   const double* Ma = ctx.na ? ctx.M64[0].as<double>() : nullptr;
   const double* Mb = ctx.nb ? (ctx.beta_alias ? ctx.M64[0].as<double>() : ctx.M64[1].as<double>()) : nullptr;
@@ -781,6 +788,124 @@ int sigma_run(Context& ctx, const double* c, double* sigma, int nvec, int precis
     k_convert<float, double><<<std::min(launch_blocks(cnt, 256), 4096), 256, 0, st>>>(ctx.s32.as<float>(), sigma, cnt); ISCSI_COUNT_LAUNCH();
   }
   ISCSI_CUDA(cudaGetLastError());
+  return kOk;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: the kernel routing of a context (which products run on the
+// tensor cores, which on the FMA kernels) for one precision and vector count.
+// Candidates: the opposite-spin contraction on the tensor cores or not, and
+// the same-spin block threshold (16, 64, 256, or none on the tensor cores).
+// A model from the flop counts and the kernels' measured rates (tensor-core
+// FP64-accurate contraction ~1.1 PFLOP/s of bf16 products, FP32 form ~0.6,
+// FP64 FMA ~1.1 TFLOP/s, FP32 FMA ~24 TFLOP/s) keeps the candidates within 3x
+// of the best prediction; each of those is timed on the caller's vector (one
+// untimed sigma to build its lists, one timed with CUDA events) and the
+// fastest is kept.  Runs once per context, precision and vector count, before
+// the first sigma (never during a graph capture).
+
+namespace {
+
+double block_rows(const Context& ctx, int a) {
+  return ctx.sp[0].level_start[a + 1] - ctx.sp[0].level_start[a];
+}
+
+// predicted ms of one sigma under a routing (contractions only)
+double route_model_ms(const Context& ctx, int prec, int ab_tc, int ss_min, int nvec) {
+  const bool f64 = prec == 64;
+  const double tc_rate = f64 ? 1.1e15 / 28.0 : 0.6e15 / 6.0;  // useful flops/s on the tensor cores
+  const double fma_rate = f64 ? 1.1e12 : 2.4e13;
+  double t = 0.0;
+  const double fab = ctx_gemm_flops(ctx, 0) * nvec;
+  t += fab / (ab_tc ? tc_rate : fma_rate);
+  const SpinSpace& SA = ctx.sp[0];
+  for (int a = 0; a <= SA.maxlevel; ++a) {
+    double rows = block_rows(ctx, a), nba = (double)ctx.nb_allowed_lvl[a];
+    if (rows == 0 || nba == 0) continue;
+    double f = 0.0;
+    if (ctx.na > 0 && ctx.M64[0].p)
+      for (int a2 = 0; a2 <= SA.maxlevel; ++a2) {
+        double rows2 = block_rows(ctx, a2), nba2 = (double)ctx.nb_allowed_lvl[a2];
+        if (rows2 == 0 || nba2 == 0 || std::abs(a - a2) > 2) continue;
+        f += 2.0 * rows * rows2 * std::min(nba, nba2);
+      }
+    if (ctx.nb > 0) f += 2.0 * rows * nba * nba;
+    const bool on = rows > ss_min && nba > ss_min;
+    t += f * nvec / (on ? tc_rate : fma_rate);
+  }
+  return t * 1e3;
+}
+
+}  // namespace
+
+int sigma_autotune(Context& ctx, const double* c, double* sigma, int nvec, int prec) {
+  Context::Route& R = ctx.route[prec == 32 ? 1 : 0];
+  if (!options().autotune || ctx.capturing || R.tuned_nvec == nvec) return kOk;
+  R.tuned_nvec = nvec;  // also stops the trial sigma calls below from tuning again
+  const bool tc_ok = prec == 32 ? options().fp32_tc : options().fp64_tc;
+  const bool ss_ok = tc_ok && options().samespin_tc;
+  struct Cand {
+    int ab, ss;
+    double pred, ms;
+  };
+  std::vector<Cand> cands;
+  const int thr[4] = {kThinN, 64, 256, 1 << 30};
+  for (int ab = tc_ok ? 1 : 0; ab >= 0; --ab)
+    for (int i = 0; i < (ss_ok ? 4 : 1); ++i) {
+      const int ss = ss_ok ? thr[i] : (1 << 30);
+      // thresholds that route the same blocks are the same candidate
+      bool dup = false;
+      for (const Cand& q : cands) {
+        if (q.ab != ab) continue;
+        bool same = true;
+        for (int a = 0; a <= ctx.sp[0].maxlevel && same; ++a) {
+          double rows = block_rows(ctx, a), nba = (double)ctx.nb_allowed_lvl[a];
+          same = (rows > q.ss && nba > q.ss) == (rows > ss && nba > ss);
+        }
+        if (same) dup = true;
+      }
+      if (!dup) cands.push_back({ab, ss, route_model_ms(ctx, prec, ab, ss, nvec), -1.0});
+    }
+  double best_pred = 1e300;
+  for (const Cand& q : cands) best_pred = std::min(best_pred, q.pred);
+  std::vector<Cand> keep;
+  for (const Cand& q : cands)
+    if (q.pred <= 3.0 * best_pred) keep.push_back(q);
+  R.trials.clear();
+  if (keep.size() > 1 && best_pred > 0.05) {  // below ~50 us a sigma is launch-bound: nothing to learn
+    cudaStream_t st = stream();
+    cudaEvent_t e0, e1;
+    ISCSI_CUDA(cudaEventCreate(&e0));
+    ISCSI_CUDA(cudaEventCreate(&e1));
+    for (Cand& q : keep) {
+      R.ab_tc = q.ab;
+      R.ss_min = q.ss;
+      ISCSI_TRY(sigma_run(ctx, c, sigma, nvec, prec));  // builds this routing's lists
+      ISCSI_CUDA(cudaEventRecord(e0, st));
+      ISCSI_TRY(sigma_run(ctx, c, sigma, nvec, prec));
+      ISCSI_CUDA(cudaEventRecord(e1, st));
+      ISCSI_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      ISCSI_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      q.ms = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  const Cand* best = &keep[0];
+  for (const Cand& q : keep)
+    if ((q.ms >= 0 ? q.ms : q.pred) < (best->ms >= 0 ? best->ms : best->pred)) best = &q;
+  R.ab_tc = best->ab;
+  R.ss_min = best->ss;
+  for (const Cand& q : cands) {
+    R.trials.push_back(q.ab);
+    R.trials.push_back(q.ss >= (1 << 30) ? -1 : q.ss);
+    R.trials.push_back(q.pred);
+    double ms = -1.0;
+    for (const Cand& k2 : keep)
+      if (k2.ab == q.ab && k2.ss == q.ss) ms = k2.ms;
+    R.trials.push_back(ms);
+  }
   return kOk;
 }
 

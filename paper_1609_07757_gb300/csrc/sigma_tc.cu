@@ -359,20 +359,26 @@ int opposite_tc_gemm(Context& ctx) { return launch_job(ctx, ctx.oz_ab, nullptr, 
 // ---------------------------------------------------------------------------
 // same spin
 
-bool samespin_block_on_tc(const Context& ctx, int a) {
-  // blocks with more than 16 rows and 16 allowed beta strings fill enough of
-  // a 128 x 64 tile to beat the FP64 units; thinner ones stay on the FP64
-  // thin kernels of sigma.cu, which stream the wide operand once
+// Same-spin level block a goes to the tensor cores when it has more rows and
+// allowed beta strings than the context's threshold for this precision (set
+// by the autotuner; the default 16 keeps the thinnest blocks on the FMA thin
+// kernels of sigma.cu, which stream the wide operand once).
+bool samespin_block_on_tc(const Context& ctx, int a, int prec) {
   const SpinSpace& SA = ctx.sp[0];
   int rows = SA.level_start[a + 1] - SA.level_start[a];
   int nba = (int)ctx.nb_allowed_lvl[a];
-  return rows > kThinN && nba > kThinN;
+  const int thr = ctx.route[prec == 32 ? 1 : 0].ss_min;
+  return rows > thr && nba > thr;
+}
+
+bool ab_on_tc(const Context& ctx, int prec) {
+  return (prec == 32 ? options().fp32_tc : options().fp64_tc) && ctx.route[prec == 32 ? 1 : 0].ab_tc;
 }
 
 bool samespin_tc_active(const Context& ctx) {
   if (!options().fp64_tc || !options().samespin_tc) return false;
   for (int a = 0; a <= ctx.sp[0].maxlevel; ++a)
-    if (samespin_block_on_tc(ctx, a)) return true;
+    if (samespin_block_on_tc(ctx, a, 64)) return true;
   return false;
 }
 
@@ -495,7 +501,7 @@ int samespin_tc_operands(Context& ctx, const double* c, double* sigma, int nvec)
                         (long long)ctx.oz_mb_rows * ctx.oz_mb_ld};
     for (int v = 0; v < nvec; ++v)
       for (const SsBlock& b : blocks) {
-        if (!samespin_block_on_tc(ctx, b.a)) continue;
+        if (!samespin_block_on_tc(ctx, b.a, 64)) continue;
         OzProblem P;
         std::memset(&P, 0, sizeof(P));
         P.t = (long long)v * ctx.ndet + b.obase;
@@ -528,15 +534,15 @@ int samespin_tc_operands(Context& ctx, const double* c, double* sigma, int nvec)
   // slice this call's C blocks (only the blocks some tensor-core problem reads)
   for (int v = 0; v < nvec; ++v)
     for (const SsBlock& b : blocks) {
-      bool used = samespin_block_on_tc(ctx, b.a);
+      bool used = samespin_block_on_tc(ctx, b.a, 64);
       for (const SsBlock& b2 : blocks)
-        if (std::abs(b.a - b2.a) <= 2 && samespin_block_on_tc(ctx, b2.a)) used = true;
+        if (std::abs(b.a - b2.a) <= 2 && samespin_block_on_tc(ctx, b2.a, 64)) used = true;
       if (!used) continue;
       const double* X = c + (long long)v * ctx.ndet + b.obase;  // [rows][nba]
       if (ctx.na > 0)
         ISCSI_TRY(slice_matrix(X, b.nba, b.rows, b.nba, 1, nullptr, b.bt_ld, b.bt_rows, cx + v * exps1 + b.bt_exp,
                                cs + v * elems1 + b.bt_off, st));
-      if (ctx.nb > 0 && samespin_block_on_tc(ctx, b.a))
+      if (ctx.nb > 0 && samespin_block_on_tc(ctx, b.a, 64))
         ISCSI_TRY(slice_matrix(X, b.rows, b.nba, b.nba, 0, nullptr, b.ca_ld, b.ca_rows, cx + v * exps1 + b.ca_exp,
                                cs + v * elems1 + b.ca_off, st));
     }
@@ -641,7 +647,7 @@ int opposite_tc32_gemm(Context& ctx) { return t3_launch(ctx, ctx.t3_ab, nullptr,
 bool samespin_tc32_active(const Context& ctx) {
   if (!options().fp32_tc || !options().samespin_tc) return false;
   for (int a = 0; a <= ctx.sp[0].maxlevel; ++a)
-    if (samespin_block_on_tc(ctx, a)) return true;
+    if (samespin_block_on_tc(ctx, a, 32)) return true;
   return false;
 }
 
@@ -709,7 +715,7 @@ int samespin_tc32_operands(Context& ctx, const float* c, float* sigma, int nvec)
                         (long long)ctx.oz_mb_rows * ctx.oz_mb_ld};
     for (int v = 0; v < nvec; ++v)
       for (const SsBlock& b : blocks) {
-        if (!samespin_block_on_tc(ctx, b.a)) continue;
+        if (!samespin_block_on_tc(ctx, b.a, 32)) continue;
         OzProblem P;
         std::memset(&P, 0, sizeof(P));
         P.t = (long long)v * ctx.ndet + b.obase;
@@ -740,15 +746,15 @@ int samespin_tc32_operands(Context& ctx, const float* c, float* sigma, int nvec)
   }
   for (int v = 0; v < nvec; ++v)
     for (const SsBlock& b : blocks) {
-      bool used = samespin_block_on_tc(ctx, b.a);
+      bool used = samespin_block_on_tc(ctx, b.a, 32);
       for (const SsBlock& b2 : blocks)
-        if (std::abs(b.a - b2.a) <= 2 && samespin_block_on_tc(ctx, b2.a)) used = true;
+        if (std::abs(b.a - b2.a) <= 2 && samespin_block_on_tc(ctx, b2.a, 32)) used = true;
       if (!used) continue;
       const float* X = c + (long long)v * ctx.ndet + b.obase;  // [rows][nba]
       if (ctx.na > 0)
         ISCSI_TRY(t3_slice_matrix<float>(X, b.nba, b.rows, b.nba, 1, nullptr, b.bt_ld, b.bt_rows,
                                          cs + v * elems1 + b.bt_off, st));
-      if (ctx.nb > 0 && samespin_block_on_tc(ctx, b.a))
+      if (ctx.nb > 0 && samespin_block_on_tc(ctx, b.a, 32))
         ISCSI_TRY(t3_slice_matrix<float>(X, b.rows, b.nba, b.nba, 0, nullptr, b.ca_ld, b.ca_rows,
                                          cs + v * elems1 + b.ca_off, st));
     }

@@ -33,6 +33,8 @@ def _fresh_library():
     L.iscsi_set_option("class_mask_hi", 1023)
     L.iscsi_set_option("precision", 64)
     L.iscsi_set_option("fp32_tc", 1)
+    # the parity tests below exercise the default routing; the autotuner has its own test
+    L.iscsi_set_option("autotune", 0)
     L.iscsi_set_stream(torch.cuda.current_stream())
     yield
     torch.cuda.synchronize()
@@ -41,6 +43,7 @@ def _fresh_library():
     L.iscsi_set_option("class_mask_hi", 1023)
     L.iscsi_set_option("precision", 64)
     L.iscsi_set_option("fp32_tc", 1)
+    L.iscsi_set_option("autotune", 1)
 
 
 def gpu_sigma(C, nvec=1, precision=64):
@@ -375,3 +378,31 @@ def test_davidson_whole_space():
     st, e = L.iscsi_davidson(3, 1e-9)
     assert st == 0
     assert np.abs(e - w[:3]).max() <= 1e-10
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_autotune_picks_a_timed_routing_with_the_same_sigma(precision):
+    # full CI in 40 orbitals: large enough for the autotuner to time its
+    # candidates; the routing it keeps is the fastest it measured and gives the
+    # same sigma as the default routing
+    n, tau = 40, 1e-12
+    h1, eri = make_integrals(n, 1400, ell=4.0, nchol=16)
+    L.iscsi_init(n, 2, 2, 4, h1, eri, tau)
+    nd = L.iscsi_ndet()
+    C = np.stack([unit_vector(nd, 95 + v) for v in range(2)])
+    s_def = gpu_sigma(C, nvec=2, precision=precision).reshape(2, -1)
+    assert L.iscsi_stats()["route_fp%d" % precision]["tuned_nvec"] == 0
+    L.iscsi_set_option("autotune", 1)
+    try:
+        s_tun = gpu_sigma(C, nvec=2, precision=precision).reshape(2, -1)
+        r = L.iscsi_stats()["route_fp%d" % precision]
+    finally:
+        L.iscsi_set_option("autotune", 0)
+    assert r["tuned_nvec"] == 2 and r["trials"]
+    chosen = [t for t in r["trials"] if t[0] == r["ab_tc"] and t[1] == r["ss_min"]]
+    assert len(chosen) == 1
+    measured = [t[3] for t in r["trials"] if t[3] >= 0]
+    assert len(measured) >= 2 and chosen[0][3] == min(measured)
+    rel = REL64 if precision == 64 else REL32
+    for v in range(2):
+        assert np.linalg.norm(s_tun[v] - s_def[v]) <= rel * np.linalg.norm(s_def[v])
