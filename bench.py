@@ -115,6 +115,65 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class NvmlClockSampler:
+    """SM clock and clock-event (throttle) reasons read through NVML (the
+    driver's libnvidia-ml, via ctypes) every ~2 ms in a thread during the timed
+    region, so that even a region of tens of milliseconds gets many samples.
+    Falls back to the nvidia-smi sampler when NVML cannot be loaded."""
+
+    # NVML clock-event reason bits (nvml.h): software power cap, hardware
+    # slowdown, software thermal slowdown, hardware thermal slowdown
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, index):
+        import ctypes
+        self.ct = ctypes
+        self.fallback = None
+        self.samples, self.reasons, self.smax = [], set(), None
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit failed")
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h)) != 0:
+                raise OSError("no NVML device %d" % index)
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(mx)) == 0:
+                self.smax = float(mx.value)
+            self.lib, self.h = lib, h
+            fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+            self.reason_fn = fn or lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        except (OSError, AttributeError):
+            self.fallback = ClockSampler(index)
+
+    def _poll(self):
+        ct = self.ct
+        mhz, rs = ct.c_uint(), ct.c_ulonglong()
+        while not self.stop_flag:
+            if self.lib.nvmlDeviceGetClockInfo(self.h, ct.c_int(1), ct.byref(mhz)) == 0:
+                self.samples.append(float(mhz.value))
+            if self.reason_fn(self.h, ct.byref(rs)) == 0:
+                for nm, bit in self.BITS.items():
+                    if rs.value & bit:
+                        self.reasons.add(nm)
+            time.sleep(0.002)
+
+    def start(self):
+        if self.fallback:
+            return self.fallback.start()
+        self.stop_flag = False
+        self.thread = threading.Thread(target=self._poll, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.fallback:
+            return self.fallback.stop()
+        self.stop_flag = True
+        self.thread.join(timeout=5)
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None, "sm_max_mhz": self.smax,
+                "reasons": sorted(self.reasons), "samples": len(self.samples), "source": "nvml"}
+
+
 def _peaks_file():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -196,7 +255,7 @@ def run_ours(args, wl, ws, rank, local):
     # device-timed region: K sigma steps, L2 flushed between them
     L.iscsi_set_option("phase_timing", 1)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
+    clocks = NvmlClockSampler(local)
     clocks.start()
     barrier()
     wall0 = time.time()
