@@ -142,6 +142,7 @@ struct OzJob {
   int nvec = -1;
   const void* tbase = nullptr;
   long long version = 0;  // bumped at every rebuild (launches over several contexts re-merge)
+  int cl = 1;             // CTAs per cluster of its launches (2: A tiles multicast to CTA pairs)
 };
 
 struct ColClass {       // column level class c = level(X) + level(Y)
@@ -199,8 +200,9 @@ struct Context {
     int ab_tc = 1;           // opposite-spin contraction on the tensor cores (else FMA kernels)
     int ss_min = kThinN;     // same-spin level blocks with more rows and allowed beta strings
                              // than this run on the tensor cores (else FMA kernels)
+    int cl = 1;              // CTAs per cluster of the opposite-spin tensor-core launch (1 or 2)
     int tuned_nvec = 0;      // vector count the autotuner ran for (0: not yet)
-    std::vector<double> trials;  // (ab_tc, ss_min, predicted ms, measured ms) per candidate
+    std::vector<double> trials;  // (ab_tc, ss_min, cl, predicted ms, measured ms) per candidate
   } route[2];
   long long pl_route_key = -1, pl_route_key32 = -1;  // routing the grouped-GEMM lists were built for
   int pl_ss_tc = -1;  // same-spin routing the FP64 grouped-GEMM list was built for
@@ -248,6 +250,8 @@ struct Options {
   int samespin_tc = 1;  // same for the same-spin blocks large enough for a 128 x 64 tile
   int fp32_tc = 1;      // FP32 form: contractions on the tensor cores (three bf16 terms, FP32 accumulation)
   int autotune = 1;     // time the routing candidates at the first sigma of each vector count
+  int tc_cluster = 1;   // opposite-spin contraction in two-CTA clusters (A tiles multicast):
+                        // 0 never, 1 when the autotuner measures it faster, 2 always
 };
 
 Options& options();
@@ -283,7 +287,7 @@ bool samespin_tc32_active(const Context& ctx);
 int samespin_tc32_operands(Context& ctx, const float* c, float* sigma, int nvec);
 int samespin_tc32_gemm(Context& ctx, float* sigma);
 int launch_tc_problems(const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
-                       void* const* tbases, int tiles, int prec, int* err, cudaStream_t st);
+                       void* const* tbases, int tiles, int prec, int cl, int* err, cudaStream_t st);
 int tc_check(Context& ctx);
 
 // allocation-free single-vector FP64 sigma on a static device array (sigma.cu)
@@ -325,6 +329,7 @@ struct MergedJob {
   std::vector<long long> ver;
   std::vector<void*> tbases;
   int tiles = 0;
+  int cl = 1;
 };
 // sigma_i = H(ctxs[i]) cs[i] for several contexts, contractions merged
 struct SigmaBatch {
@@ -332,7 +337,7 @@ struct SigmaBatch {
   std::vector<const double*> cs;
   std::vector<double*> ss;
   int nvec = 0, prec = 0;
-  MergedJob ab, sst;
+  MergedJob ab[2], sst;  // ab[cl - 1]: the opposite-spin jobs launched in clusters of cl CTAs
   DevBuf err;
   StreamPool pool;
 };

@@ -42,10 +42,11 @@ struct OzSeg {
 };
 
 // TMA descriptors of a segment's two slice arrays: dims (ld, rows, S), box
-// (16, 128 or 64, S), 32-byte swizzle.  Kept in global memory beside the
-// segment list (one entry per segment).
+// (16, 128 or 64, S), 32-byte swizzle; ah: A's array in boxes of (16, 64, 1).
+// Kept in global memory beside the segment list (one entry per segment).
 struct OzMaps {
   CUtensorMap a, b;
+  CUtensorMap ah;  // A in boxes of 16 x 64 rows x 1 slice (half tiles, two-CTA clusters)
 };
 
 // T[M][N] (FP64, ldt) (+)= sum over segments of A_seg B_seg^T; T is the

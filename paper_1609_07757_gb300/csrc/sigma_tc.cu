@@ -145,8 +145,10 @@ __global__ void k_t3_lift(TcTable tt, int n, int nholeA, int nholeB, const int* 
 static int tc_attr() {
   static bool done = false;
   if (!done) {
-    ISCSI_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES));
-    ISCSI_CUDA(cudaFuncSetAttribute(k_tc32_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, T3_SMEM_BYTES));
+    ISCSI_CUDA(cudaFuncSetAttribute(k_oz_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES));
+    ISCSI_CUDA(cudaFuncSetAttribute(k_oz_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES));
+    ISCSI_CUDA(cudaFuncSetAttribute(k_tc32_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, T3_SMEM_BYTES));
+    ISCSI_CUDA(cudaFuncSetAttribute(k_tc32_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, T3_SMEM_BYTES));
     done = true;
   }
   return kOk;
@@ -208,7 +210,8 @@ static int add_seg(OzJob& job, const SliceArray& A, int a_row0, int a_k0, const 
   OzMaps m;
   std::memset(&m, 0, sizeof(m));
   if (oz_encode_map(&m.a, A.base, A.ld, A.rows, nslice, A.slice, OZ_BM) ||
-      oz_encode_map(&m.b, B.base, B.ld, B.rows, nslice, B.slice, OZ_BN)) {
+      oz_encode_map(&m.b, B.base, B.ld, B.rows, nslice, B.slice, OZ_BN) ||
+      oz_encode_map(&m.ah, A.base, A.ld, A.rows, nslice, A.slice, OZ_BM / 2, 1)) {
     set_error("tensor-core sigma: TMA descriptor rejected");
     return kErrCuda;
   }
@@ -235,19 +238,44 @@ static int upload_job(OzJob& job, cudaStream_t st) {
   return kOk;
 }
 
-static int launch_job(Context& ctx, const OzJob& job, double* tbase, cudaStream_t st) {
-  if (job.tiles == 0) return kOk;
-  k_oz_gemm<<<job.tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(job.d_probs.as<OzProblem>(), (int)job.probs.size(),
-                                                          job.d_segs.as<OzSeg>(), job.d_maps.as<OzMaps>(), tbase,
-                                                          nullptr, ctx.oz_err.as<int>()); ISCSI_COUNT_LAUNCH();
+// k_oz_gemm over a problem list; cl = 2 launches clusters of two CTAs (the
+// list's column-tile counts must then be even, add_tiles(probs, 2))
+static int launch_oz(int cl, int tiles, const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
+                     double* tbase, double* const* tbases, int* err, cudaStream_t st) {
+  if (tiles == 0) return kOk;
+  if (cl == 2) {
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(tiles, 1, 1);
+    cfg.blockDim = dim3(OZ_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = OZ_SMEM_BYTES;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ISCSI_CUDA(cudaLaunchKernelEx(&cfg, k_oz_gemm<2>, probs, nprobs, segs, maps, tbase, tbases, err)); ISCSI_COUNT_LAUNCH();
+  } else {
+    k_oz_gemm<1><<<tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(probs, nprobs, segs, maps, tbase, tbases, err); ISCSI_COUNT_LAUNCH();
+  }
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
 }
 
-static int add_tiles(std::vector<OzProblem>& probs) {
+static int launch_job(Context& ctx, const OzJob& job, double* tbase, cudaStream_t st) {
+  return launch_oz(job.cl, job.tiles, job.d_probs.as<OzProblem>(), (int)job.probs.size(), job.d_segs.as<OzSeg>(),
+                   job.d_maps.as<OzMaps>(), tbase, nullptr, ctx.oz_err.as<int>(), st);
+}
+
+// tile numbering of a problem list; with cl = 2 every problem gets an even
+// number of column tiles (a cluster's two CTAs share a row block)
+static int add_tiles(std::vector<OzProblem>& probs, int cl = 1) {
   int tiles = 0;
   for (auto& p : probs) {
-    p.tiles_n = round_up(p.N, OZ_BN) / OZ_BN;
+    p.tiles_n = round_up(round_up(p.N, OZ_BN) / OZ_BN, cl);
     p.tile_begin = tiles;
     tiles += (round_up(p.M, OZ_BM) / OZ_BM) * p.tiles_n;
   }
@@ -293,7 +321,8 @@ int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec) {
   long long bs_elems = 0, exp_elems = 0;
   TcTable tt = ab_table(ctx, nvec, &bs_elems, &exp_elems);
   if (tt.nclass == 0) return kOk;
-  bool rebuild = ctx.oz_ab.nvec != nvec || ctx.oz_ab.tbase != (const void*)ttw;
+  const int cl = options().tc_cluster == 2 || (options().tc_cluster == 1 && ctx.route[0].cl == 2) ? 2 : 1;
+  bool rebuild = ctx.oz_ab.nvec != nvec || ctx.oz_ab.tbase != (const void*)ttw || ctx.oz_ab.cl != cl;
   if (ctx.oz_bs_elems < bs_elems) {
     ISCSI_TRY(ctx.oz_bs.alloc(sizeof(__nv_bfloat16) * bs_elems));
     ctx.oz_bs_elems = bs_elems;
@@ -332,7 +361,8 @@ int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec) {
                         C.ncols));
       job.probs.push_back(P);
     }
-    job.tiles = add_tiles(job.probs);
+    job.cl = cl;
+    job.tiles = add_tiles(job.probs, cl);
     ISCSI_TRY(upload_job(job, st));
     job.nvec = nvec;
     job.tbase = ttw;
@@ -568,13 +598,35 @@ static int t3_slice_matrix(const V* X, int rows, int cols, long long ld, int tra
   return kOk;
 }
 
-static int t3_launch(Context& ctx, const OzJob& job, float* tbase, cudaStream_t st) {
-  if (job.tiles == 0) return kOk;
-  k_tc32_gemm<<<job.tiles, T3_THREADS, T3_SMEM_BYTES, st>>>(job.d_probs.as<OzProblem>(), (int)job.probs.size(),
-                                                            job.d_segs.as<OzSeg>(), job.d_maps.as<OzMaps>(), tbase,
-                                                            nullptr, ctx.oz_err.as<int>()); ISCSI_COUNT_LAUNCH();
+// k_tc32_gemm over a problem list, in two-CTA clusters when cl = 2
+static int launch_t3(int cl, int tiles, const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
+                     float* tbase, float* const* tbases, int* err, cudaStream_t st) {
+  if (tiles == 0) return kOk;
+  if (cl == 2) {
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(tiles, 1, 1);
+    cfg.blockDim = dim3(T3_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = T3_SMEM_BYTES;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ISCSI_CUDA(cudaLaunchKernelEx(&cfg, k_tc32_gemm<2>, probs, nprobs, segs, maps, tbase, tbases, err)); ISCSI_COUNT_LAUNCH();
+  } else {
+    k_tc32_gemm<1><<<tiles, T3_THREADS, T3_SMEM_BYTES, st>>>(probs, nprobs, segs, maps, tbase, tbases, err); ISCSI_COUNT_LAUNCH();
+  }
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
+}
+
+static int t3_launch(Context& ctx, const OzJob& job, float* tbase, cudaStream_t st) {
+  return launch_t3(job.cl, job.tiles, job.d_probs.as<OzProblem>(), (int)job.probs.size(), job.d_segs.as<OzSeg>(),
+                   job.d_maps.as<OzMaps>(), tbase, nullptr, ctx.oz_err.as<int>(), st);
 }
 
 static int t3_prepare_g(Context& ctx) {
@@ -596,7 +648,8 @@ int opposite_tc32_operands(Context& ctx, const float* c, float* ttw, int nvec) {
   long long bs_elems = 0, exp_elems = 0;
   TcTable tt = ab_table(ctx, nvec, &bs_elems, &exp_elems, T3_S);
   if (tt.nclass == 0) return kOk;
-  bool rebuild = ctx.t3_ab.nvec != nvec || ctx.t3_ab.tbase != (const void*)ttw;
+  const int cl = options().tc_cluster == 2 || (options().tc_cluster == 1 && ctx.route[1].cl == 2) ? 2 : 1;
+  bool rebuild = ctx.t3_ab.nvec != nvec || ctx.t3_ab.tbase != (const void*)ttw || ctx.t3_ab.cl != cl;
   if (ctx.t3_bs_elems < bs_elems) {
     ISCSI_TRY(ctx.t3_bs.alloc(sizeof(__nv_bfloat16) * bs_elems));
     ctx.t3_bs_elems = bs_elems;
@@ -625,7 +678,8 @@ int opposite_tc32_operands(Context& ctx, const float* c, float* ttw, int nvec) {
       ISCSI_TRY(add_seg(job, GA, 0, 0, nullptr, CB, 0, 0, nullptr, C.kpad, C.ncols, T3_S));
       job.probs.push_back(P);
     }
-    job.tiles = add_tiles(job.probs);
+    job.cl = cl;
+    job.tiles = add_tiles(job.probs, cl);
     ISCSI_TRY(upload_job(job, st));
     job.nvec = nvec;
     job.tbase = ttw;
@@ -767,18 +821,14 @@ int samespin_tc32_gemm(Context& ctx, float* sigma) { return t3_launch(ctx, ctx.t
 // one launch of the FP64-accurate (prec 64) or FP32-form (prec 32) contraction
 // over a device problem list whose relative outputs use the base table tbases
 int launch_tc_problems(const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
-                       void* const* tbases, int tiles, int prec, int* err, cudaStream_t st) {
+                       void* const* tbases, int tiles, int prec, int cl, int* err, cudaStream_t st) {
   if (tiles == 0) return kOk;
   ISCSI_TRY(tc_attr());
   if (prec == 64) {
-    k_oz_gemm<<<tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(probs, nprobs, segs, maps, nullptr,
-                                                       reinterpret_cast<double* const*>(tbases), err); ISCSI_COUNT_LAUNCH();
+    return launch_oz(cl, tiles, probs, nprobs, segs, maps, nullptr, reinterpret_cast<double* const*>(tbases), err, st);
   } else {
-    k_tc32_gemm<<<tiles, T3_THREADS, T3_SMEM_BYTES, st>>>(probs, nprobs, segs, maps, nullptr,
-                                                         reinterpret_cast<float* const*>(tbases), err); ISCSI_COUNT_LAUNCH();
+    return launch_t3(cl, tiles, probs, nprobs, segs, maps, nullptr, reinterpret_cast<float* const*>(tbases), err, st);
   }
-  ISCSI_CUDA(cudaGetLastError());
-  return kOk;
 }
 
 // status of the bounded waits of the tensor-core kernels (synchronises)

@@ -67,12 +67,16 @@ __global__ void k_t3_slice(const V* __restrict__ X, int rows, int cols, long lon
 }
 
 // Per CTA one 128 x 64 tile of T (FP32, ldt), over all segments of its
-// problem.  Every wait is bounded; a wait that runs out sets abort, the CTA
-// waits (bounded) for its copies in flight, frees TMEM and reports via err.
+// problem.  With CL = 2, clusters of two CTAs on adjacent column tiles of one
+// row block share the A operand by multicast, as in k_oz_gemm (ozaki.cuh).
+// Every wait is bounded; a wait that runs out sets abort, the CTA waits
+// (bounded) for its copies in flight, frees TMEM and reports via err.
+template <int CL>
 __global__ void __launch_bounds__(T3_THREADS, 1)
     k_tc32_gemm(const OzProblem* __restrict__ probs, int nprobs, const OzSeg* __restrict__ segs,
                 const OzMaps* __restrict__ maps, float* tbase, float* const* __restrict__ tbases,
                 int* __restrict__ err) {
+  static_assert(CL == 1 || CL == 2, "clusters of one or two CTAs");
   extern __shared__ unsigned char t3_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)t3_smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t s_stage0 = tc::smem_u32(smem);
@@ -95,13 +99,14 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   float* const Tp = P.t_rel ? (tbases ? tbases[P.tb] : tbase) + P.t : reinterpret_cast<float*>(P.t);
   const int tl = tile - P.tile_begin;
   const int m0 = (tl / P.tiles_n) * T3_BM, n0 = (tl % P.tiles_n) * T3_BN;
+  const int n0_pair = ((tl % P.tiles_n) & ~(CL - 1)) * T3_BN;  // first column of the cluster
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int SPC = T3_CHUNK_STEPS;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < T3_STAGES; ++s) {
       tc::mbar_init(tc::smem_u32(&full_b[s]), 1);
-      tc::mbar_init(tc::smem_u32(&empty_b[s]), 1);
+      tc::mbar_init(tc::smem_u32(&empty_b[s]), CL);
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(tc::smem_u32(&chunk_b[b]), 1);
@@ -112,7 +117,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     int ns = 0, steps = 0;
     for (int g = 0; g < P.seg_count && ns < OZ_MAX_SEGS; ++g) {
       OzSeg sg = segs[P.seg_begin + g];
-      if (n0 >= sg.nrows_b || sg.K <= 0) continue;
+      if (n0_pair >= sg.nrows_b || sg.K <= 0) continue;
       seg_s[ns] = sg;
       segid_s[ns] = P.seg_begin + g;
       step0_s[ns] = steps;
@@ -129,6 +134,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   }
   tc::fence_before_sync();
   __syncthreads();
+  if (CL == 2) tc::cluster_sync();  // the partner's barriers exist before any multicast
   tc::fence_after_sync();
   const uint32_t tmem = tmem_s;
   const int nseg = nseg_s;
@@ -149,9 +155,10 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     // ---------------- producer (TMA): all terms of A and of B per K step
     if (lane == 0) {
       int seg = -1, seg_end = 0, seg_begin = 0;
-      const CUtensorMap *ma = nullptr, *mb = nullptr;
+      const CUtensorMap *ma = nullptr, *mah = nullptr, *mb = nullptr;
       int ax = 0, ay = 0, bx = 0, by = 0;
       int issued = 0;
+      const int rank = CL == 2 ? (int)tc::cluster_rank() : 0;
       for (int g = 0; g < total; ++g) {
         const int st = g % T3_STAGES;
         if (g >= T3_STAGES && !wait(&empty_b[st], ((g / T3_STAGES) - 1) & 1)) break;
@@ -161,6 +168,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
           seg_end = step0_s[seg + 1];
           const OzSeg& S = seg_s[seg];
           ma = &maps[segid_s[seg]].a;
+          mah = &maps[segid_s[seg]].ah;
           mb = &maps[segid_s[seg]].b;
           ax = S.a_k0;
           ay = S.a_row0 + m0;
@@ -171,7 +179,15 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         const uint32_t fb = tc::smem_u32(&full_b[st]);
         const uint32_t sa = s_stage0 + st * T3_STAGE_BYTES;
         tc::mbar_arrive_expect_tx(fb, T3_STAGE_BYTES);
-        tc::tma_load_3d(sa, ma, ax + k0, ay, 0, fb);
+        if (CL == 1) {
+          tc::tma_load_3d(sa, ma, ax + k0, ay, 0, fb);
+        } else {
+          // this CTA's half of the rows of each A term, to both CTAs
+#pragma unroll
+          for (int t = 0; t < T3_S; ++t)
+            tc::tma_load_3d_mc(sa + t * T3_A_SLICE_BYTES + rank * (T3_A_SLICE_BYTES / 2), mah, ax + k0,
+                               ay + rank * (T3_BM / 2), t, fb, (uint16_t)0x3);
+        }
         tc::tma_load_3d(sa + T3_S * T3_A_SLICE_BYTES, mb, bx + k0, by, 0, fb);
         issued = g + 1;
       }
@@ -197,7 +213,10 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         tc::mma_bf16(D, tc::smem_desc_sw32(sa), tc::smem_desc_sw32(sb), N192, kin == 0 ? 0u : 1u);
         tc::mma_bf16(D + 64, tc::smem_desc_sw32(sa + T3_A_SLICE_BYTES), tc::smem_desc_sw32(sb), N128, 1u);
         tc::mma_bf16(D + 128, tc::smem_desc_sw32(sa + 2 * T3_A_SLICE_BYTES), tc::smem_desc_sw32(sb), N64, 1u);
-        tc::mma_commit(tc::smem_u32(&empty_b[st]));
+        if (CL == 2)
+          tc::mma_commit_mc(tc::smem_u32(&empty_b[st]), (uint16_t)0x3);  // both CTAs read this stage
+        else
+          tc::mma_commit(tc::smem_u32(&empty_b[st]));
         if (kin == SPC - 1 || g == total - 1) tc::mma_commit(tc::smem_u32(&chunk_b[b]));
       }
       if (abort_s) {
@@ -258,6 +277,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, T3_TMEM_COLS);
   }
+  // no CTA leaves while its partner's copies or MMA commits may still reach it
+  if (CL == 2) tc::cluster_sync();
 }
 
 }  // namespace iscsi

@@ -8,12 +8,13 @@
 namespace iscsi {
 
 // Descriptor of a K-major slice array [nslice][rows][ld] (bf16, slice_elems
-// elements between slices) read in boxes of 16 (K) x box_rows x nslice with
-// the 32-byte swizzle, the layout smem_desc_sw32 describes to the MMA.
-// base must be 16-byte aligned and ld a multiple of 16.  Returns 0 on
-// success, -1 when the driver entry point is missing or rejects the shape.
+// elements between slices) read in boxes of 16 (K) x box_rows x box_slices
+// (default: all slices) with the 32-byte swizzle, the layout smem_desc_sw32
+// describes to the MMA.  base must be 16-byte aligned and ld a multiple of 16.
+// Returns 0 on success, -1 when the driver entry point is missing or rejects
+// the shape.
 inline int oz_encode_map(CUtensorMap* map, const void* base, int ld, long long rows, int nslice,
-                         long long slice_elems, int box_rows) {
+                         long long slice_elems, int box_rows, int box_slices = 0) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -26,7 +27,7 @@ inline int oz_encode_map(CUtensorMap* map, const void* base, int ld, long long r
   }
   cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)rows, (cuuint64_t)nslice};
   cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)slice_elems * 2};
-  cuuint32_t box[3] = {16, (cuuint32_t)box_rows, (cuuint32_t)nslice};
+  cuuint32_t box[3] = {16, (cuuint32_t)box_rows, (cuuint32_t)(box_slices > 0 ? box_slices : nslice)};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
