@@ -503,6 +503,56 @@ def run_batching(count=64, reps=5, tau=1e-14, nroots=1):
     return out
 
 
+def run_sweep(steps=5, warmup=3):
+    """The box-size sweep: CISD and CISDT, 2 alpha + 2 beta electrons in 50, 100,
+    150 and 200 orbitals (integrals decaying with the box), tau = 1e-14, FP64.
+    sigma time per orbital count and the exponent of a least-squares fit
+    t ~ n^p over the four sizes."""
+    import math
+
+    import torch
+
+    from paper_1609_07757_gb300 import _lib as L
+    from paper_1609_07757_gb300.synthetic import make_integrals, unit_vector
+
+    out = {}
+    for k, name in ((2, "cisd"), (3, "cisdt")):
+        rows = []
+        for n in (50, 100, 150, 200):
+            wl = WORKLOADS["%s_n%d" % (name, n)]
+            h1, eri = make_integrals(wl["n"], wl["seed"], ell=wl["ell"], nchol=wl["nchol"], box=wl["box"])
+            L.iscsi_init(wl["n"], wl["na"], wl["nb"], wl["kmax"], h1, eri, wl["tau"])
+            nd = L.iscsi_ndet()
+            c = torch.tensor(unit_vector(nd, 11), dtype=torch.float64, device="cuda")
+            sg = torch.empty_like(c)
+            for _ in range(warmup):
+                L.iscsi_sigma(c, sg, 1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(steps):
+                L.iscsi_sigma(c, sg, 1)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            st = L.iscsi_stats()
+            upd = L.iscsi_updates_per_sigma()
+            kept = st["units_kept_opposite"] / max(1, st["units_total"]["opposite"])
+            rows.append({"norb": n, "ndet": nd, "sigma_ms": round(ms, 3), "GUpdates_per_s": round(upd / ms / 1e6, 1),
+                         "updates": upd, "opposite_units_kept": round(kept, 4)})
+            L.iscsi_finalize()
+        xs = [math.log(r["norb"]) for r in rows]
+        ys = [math.log(r["sigma_ms"]) for r in rows]
+        yu = [math.log(r["updates"]) for r in rows]
+        mx = sum(xs) / len(xs)
+
+        def slope(y):
+            my = sum(y) / len(y)
+            return sum((a - mx) * (b - my) for a, b in zip(xs, y)) / sum((a - mx) ** 2 for a in xs)
+        out[name] = {"points": rows, "time_exponent": round(slope(ys), 3), "updates_exponent": round(slope(yu), 3)}
+    return out
+
+
 def cpu_baseline(wl, tau, target_s=15.0, steps=1):
     """The oracle, as it stands, on a bounded sample of rows of the same workload."""
     import numpy as np
@@ -578,6 +628,8 @@ def main():
     ap.add_argument("--mixed-roots", type=int, default=3)
     ap.add_argument("--batching", type=int, default=0, metavar="COUNT",
                     help="add the batching form: COUNT full-CI instances, batched vs one at a time")
+    ap.add_argument("--sweep", action="store_true",
+                    help="add the CISD/CISDT box-size sweep (n = 50..200) with its fitted scaling exponents")
     ap.add_argument("--updates", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     ws, rank, local = dist_env()
@@ -610,6 +662,8 @@ def main():
         line["mixed_precision"] = run_precision_form(args.mixed_workload, args.mixed_roots)
     if rank == 0 and ws == 1 and args.batching > 0:
         line["batching"] = run_batching(args.batching)
+    if rank == 0 and ws == 1 and args.sweep:
+        line["box_sweep"] = run_sweep()
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
             tau = args.tau if args.tau is not None else wl["tau"]
