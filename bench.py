@@ -232,6 +232,8 @@ def run_ours(args, wl, ws, rank, local):
     h1, eri = make_integrals(wl["n"], wl["seed"], ell=wl["ell"], nchol=wl["nchol"], box=wl["box"])
     stream = torch.cuda.current_stream()
     L.iscsi_set_stream(stream)
+    L.iscsi_set_option("autotune", args.autotune)
+    L.iscsi_set_option("tc_cluster", args.tc_cluster)
     t0 = time.time()
     L.iscsi_init(wl["n"], wl["na"], wl["nb"], wl["kmax"], h1, eri, tau)
     init_s = time.time() - t0
@@ -299,18 +301,21 @@ def run_ours(args, wl, ws, rank, local):
     # roofline of the dominant kernel (opposite-spin contraction)
     gemm_ms = st["phase_ms"]["opposite_gemm"] / max(1, st["timed_calls"])
     tc = st.get("fp64_tc" if args.precision == 64 else "fp32_tc", 0) == 1
+    route = st.get("route_fp%d" % args.precision, {})
+    cl = route.get("cl", 1) if args.tc_cluster == 1 else (2 if args.tc_cluster == 2 else 1)
+    tc = tc and route.get("ab_tc", 1) == 1
     if tc and args.precision == 64:
         # tensor-core kernel: bf16 MMA flops it issues (28 exact slice products)
         flops = st["opposite_tc_bf16_flops"]
         peak, peak_src = bf16_peak()
-        bound, kname, kkey = "tensor", "k_oz_gemm (tcgen05, FP64-accurate opposite-spin contraction)", \
-            "k_oz_gemm_%s" % args.workload
+        bound, kname, kkey = "tensor", "k_oz_gemm<%d> (tcgen05, FP64-accurate opposite-spin contraction, " \
+            "clusters of %d CTA)" % (cl, cl), "k_oz_gemm_cl%d_%s" % (cl, args.workload)
     elif tc:
         # FP32 form: 6 of the 9 products of three bf16 terms per operand
         flops = st["opposite_tc_bf16_flops"] * 6.0 / 28.0
         peak, peak_src = bf16_peak()
-        bound, kname, kkey = "tensor", "k_tc32_gemm (tcgen05, FP32-accurate opposite-spin contraction)", \
-            "k_tc32_gemm_%s" % args.workload
+        bound, kname, kkey = "tensor", "k_tc32_gemm<%d> (tcgen05, FP32-accurate opposite-spin contraction, " \
+            "clusters of %d CTA)" % (cl, cl), "k_tc32_gemm_cl%d_%s" % (cl, args.workload)
     else:
         flops = st["opposite_gemm_flops"]
         peak = FP64_PEAK_TFLOPS if args.precision == 64 else FP32_PEAK_TFLOPS
@@ -628,6 +633,10 @@ def main():
     ap.add_argument("--mixed-roots", type=int, default=3)
     ap.add_argument("--batching", type=int, default=0, metavar="COUNT",
                     help="add the batching form: COUNT full-CI instances, batched vs one at a time")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="library option autotune (kernel routing timed at the first sigma)")
+    ap.add_argument("--tc-cluster", type=int, default=1, choices=[0, 1, 2],
+                    help="library option tc_cluster (0 never, 1 tuned, 2 always two-CTA clusters)")
     ap.add_argument("--sweep", action="store_true",
                     help="add the CISD/CISDT box-size sweep (n = 50..200) with its fitted scaling exponents")
     ap.add_argument("--updates", type=float, default=None, help=argparse.SUPPRESS)
