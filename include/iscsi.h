@@ -200,8 +200,10 @@ ISCSI_API iscsi_status iscsi_set_stream(void* stream);
  *   "max_subspace"     Davidson basis vectors per root; 0 (default): 12 per
  *                      root up to 96 in all, at least 4 per root
  *   "etol"             Davidson energy-change threshold (default 1e-10)
- *   "switch_tol"       mixed precision: residual at which FP64 sigma starts (default 1e-5;
- *                      the switch also happens when the FP32 residual stalls)
+ *   "switch_tol"       mixed precision: residual at which FP64 sigma starts (default 1e-6;
+ *                      the switch also happens when the FP32 residual stalls near its floor)
+ *   "block_extra"      Davidson iterates the wanted roots and this many more (default 0;
+ *                      convergence is judged on the wanted roots)
  *   "guess_from_vecs"  1: iscsi_davidson starts from `vecs` (default 0)
  *   "use_graph"        1 (default): one Davidson iteration is captured as a
  *                      CUDA graph on first use and replayed; 0: direct launches

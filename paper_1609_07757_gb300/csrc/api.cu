@@ -227,6 +227,9 @@ iscsi_status iscsi_set_option(const char* key, double value) {
     o.use_graph = value != 0;
   } else if (k == "olsen") {
     o.olsen = value != 0;
+  } else if (k == "block_extra") {
+    if (value < 0 || value > 31) return bad();
+    o.block_extra = (int)value;
   } else if (k == "fp64_tc") {
     o.fp64_tc = value != 0;
   } else if (k == "samespin_tc") {

@@ -49,7 +49,8 @@ constexpr int kDotT = 8;             // tall-skinny dot products: 8 x 8 vectors 
 
 struct DavCtl {
   int m;        // basis size
-  int k;        // roots
+  int k;        // block: roots iterated
+  int kw;       // roots wanted (the first kw of the block decide convergence)
   int maxsub;   // basis capacity
   int iter;     // completed checks
   int restart;  // 1: thick restart at the start of the next expansion
@@ -632,8 +633,10 @@ __global__ void k_dav_check(DavCtl* __restrict__ ctl, const double* __restrict__
     double rmax = 0.0, dmax = 0.0;
     bool finite = true;
     for (int i = 0; i < k; ++i) {
-      rmax = fmax(rmax, ctl->rnorm[i]);
-      dmax = fmax(dmax, fabs(ctl->theta[i] - ctl->theta_prev[i]));
+      if (i < ctl->kw) {
+        rmax = fmax(rmax, ctl->rnorm[i]);
+        dmax = fmax(dmax, fabs(ctl->theta[i] - ctl->theta_prev[i]));
+      }
       if (!isfinite(ctl->theta[i]) || !isfinite(ctl->rnorm[i])) finite = false;
       ctl->theta_prev[i] = ctl->theta[i];
     }
@@ -1013,14 +1016,21 @@ int batch_wait_status(const std::unique_ptr<SigmaBatch> (&sb)[2]) {
 // sequence is captured into one CUDA graph per set of active instances and
 // replayed; instances leave the set when they converge (or fail), switch
 // precision, or reach maxiter, and the graph is captured again.
-static int davidson_batch_body(const std::vector<Context*>& ctxs, int k, double tol, double* energies,
+static int davidson_batch_body(const std::vector<Context*>& ctxs, int kw, double tol, double* energies,
                                double* const* vecs, int* statuses) {
   const Options& opt = options();
   const int n = (int)ctxs.size();
-  if (k > kMaxRoots) {
+  if (kw > kMaxRoots) {
     set_error("iscsi_davidson: at most 32 roots");
     return kErrArg;
   }
+  // the block: the wanted roots and block_extra more (they widen the
+  // expansion; convergence is judged on the wanted roots only)
+  long long ndet_min = ctxs[0]->ndet;
+  for (const Context* c : ctxs) ndet_min = std::min(ndet_min, c->ndet);
+  // (the caller's start vectors fill a block of the wanted roots only)
+  const int extra = vecs && opt.guess_from_vecs ? 0 : std::max(0, opt.block_extra);
+  const int k = (int)std::min<long long>(std::min(kMaxRoots, kw + extra), ndet_min);
   cudaStream_t st = stream();
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -1039,6 +1049,7 @@ static int davidson_batch_body(const std::vector<Context*>& ctxs, int k, double 
     DavCtl& h = H[i];
     std::memset(&h, 0, sizeof(h));
     h.k = k;
+    h.kw = kw;
     h.maxsub = D[i]->maxsub;
     h.tol = tol;
     h.etol = opt.etol;
@@ -1173,9 +1184,9 @@ static int davidson_batch_body(const std::vector<Context*>& ctxs, int k, double 
   ISCSI_CUDA(cudaStreamSynchronize(st));
   for (int i = 0; i < n; ++i) {
     if (status[i] == kErrNoConv && prec[i] == 64 && (H[i].status & kStatusConverged)) status[i] = kOk;
-    for (int j = 0; j < k; ++j) energies[(size_t)i * k + j] = H[i].theta[j];
+    for (int j = 0; j < kw; ++j) energies[(size_t)i * kw + j] = H[i].theta[j];
     if (vecs && vecs[i])
-      ISCSI_CUDA(cudaMemcpyAsync(vecs[i], D[i]->X, sizeof(double) * k * D[i]->N, cudaMemcpyDeviceToDevice, st));
+      ISCSI_CUDA(cudaMemcpyAsync(vecs[i], D[i]->X, sizeof(double) * kw * D[i]->N, cudaMemcpyDeviceToDevice, st));
     if (statuses) statuses[i] = status[i];
   }
   cudaEventRecord(e1, st);

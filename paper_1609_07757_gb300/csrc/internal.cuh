@@ -241,10 +241,11 @@ struct Options {
   int maxiter = 300;
   int max_subspace = 0;  // Davidson basis vectors per root; 0: automatic
   double etol = 1e-10;
-  double switch_tol = 1e-5;
+  double switch_tol = 1e-6;  // mixed precision: FP32 sigma until every residual is below this
   int guess_from_vecs = 0;
   int use_graph = 1;
   int olsen = 1;        // Olsen's correction in the Davidson preconditioner
+  int block_extra = 0;  // Davidson block: the wanted roots and this many more
   int phase_timing = 0;
   int fp64_tc = 1;      // FP64 opposite-spin contraction on the tensor cores (exact bf16 slices)
   int samespin_tc = 1;  // same for the same-spin blocks large enough for a 128 x 64 tile

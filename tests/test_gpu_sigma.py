@@ -434,3 +434,20 @@ def test_two_cta_clusters_give_identical_sigma(precision):
     s = outs[1].reshape(3, -1)
     for v in range(3):
         assert np.abs(s[v][rows] - o.sigma_rows(C[v], rows)).max() <= rel * np.abs(s[v]).max()
+
+
+def test_davidson_extra_block_vectors():
+    # iterating two more roots than wanted still returns the wanted ones
+    n, tau = 10, 1e-14
+    h1, eri = make_integrals(n, 6, ell=3.0, nchol=20)
+    w = np.linalg.eigvalsh(Oracle(n, 2, 2, 4, tau, h1, eri).dense_h())
+    L.iscsi_init(n, 2, 2, 4, h1, eri, tau)
+    vecs = torch.zeros((2, L.iscsi_ndet()), dtype=torch.float64, device="cuda")
+    L.iscsi_set_option("block_extra", 2)
+    try:
+        st, e = L.iscsi_davidson(2, 1e-8, vecs)
+    finally:
+        L.iscsi_set_option("block_extra", 0)
+    assert st == 0 and e.shape == (2,)
+    assert np.abs(e - w[:2]).max() <= 1e-10
+    assert torch.abs(torch.linalg.norm(vecs, dim=1) - 1).max().item() < 1e-12
