@@ -63,6 +63,32 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(values, device="cpu"):
+    """Element-wise maximum of a list of floats over all ranks (the job's time is
+    its slowest rank's); the values themselves when there is one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_rate(units_per_rank, ws, seconds):
+    """Units all ranks processed per second: every rank does the same work (weak
+    scaling), and the job takes as long as its slowest rank."""
+    return ws * units_per_rank / seconds
+
+
+def shard(count, rank, ws):
+    """The instances of a many-instance workload that this rank runs: every
+    ws-th one starting at rank, so ranks share the mix of sizes evenly and no
+    instance is run twice or left out; instances are independent, so the
+    shards need no exchange."""
+    return list(range(rank, count, ws))
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -289,14 +315,10 @@ def run_ours(args, wl, ws, rank, local):
     ref = s.cpu().numpy()
     e2e_ok = bool(np.array_equal(sh_np, ref))
 
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot_ms, e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms, e2e_s = float(t[0]), float(t[1])
+    tot_ms, e2e_s = max_over_ranks([tot_ms, e2e_s], device=dev)
     ms = tot_ms / args.steps
-    value = ws * updates / (ms * 1e-3) / 1e9
-    e2e_val = ws * updates * args.steps / e2e_s / 1e9
+    value = whole_job_rate(updates, ws, ms * 1e-3) / 1e9
+    e2e_val = whole_job_rate(updates * args.steps, ws, e2e_s) / 1e9
 
     # roofline of the dominant kernel (opposite-spin contraction)
     gemm_ms = st["phase_ms"]["opposite_gemm"] / max(1, st["timed_calls"])
@@ -419,7 +441,7 @@ def run_precision_form(name, nroots=3, tol=1e-8):
     return out
 
 
-def run_batching(count=64, reps=5, tau=1e-14, nroots=1):
+def run_batching(count=64, reps=5, tau=1e-14, nroots=1, rank=0, ws=1):
     """The batching form: `count` independent full-CI instances (2 alpha + 2 beta
     electrons, orbital counts uniform on [20, 80], each with its own seeded
     integrals of the 10-orbital workload's generator).  sigma for all of them
@@ -431,10 +453,12 @@ def run_batching(count=64, reps=5, tau=1e-14, nroots=1):
     from paper_1609_07757_gb300 import _lib as L
     from paper_1609_07757_gb300.synthetic import make_integrals, multi_instance_sizes, unit_vector
 
-    sizes = [int(x) for x in multi_instance_sizes(count)]
+    all_sizes = [int(x) for x in multi_instance_sizes(count)]
+    mine = shard(count, rank, ws)  # with several ranks each runs its own share of the instances
+    sizes = [all_sizes[i] for i in mine]
     hs, cs, ss, upd, ndets = [], [], [], 0.0, 0
     t0 = time.time()
-    for i, n in enumerate(sizes):
+    for i, n in zip(mine, sizes):
         h1, eri = make_integrals(n, 4000 + i, ell=3.0, nchol=20)
         L.iscsi_init(n, 2, 2, 4, h1, eri, tau)
         hs.append(L.iscsi_ctx_current())
@@ -445,8 +469,8 @@ def run_batching(count=64, reps=5, tau=1e-14, nroots=1):
         cs.append(c)
         ss.append(torch.empty_like(c))
     init_s = time.time() - t0
-    out = {"instances": count, "orbitals": [min(sizes), max(sizes)], "mean_ndet": ndets / count,
-           "updates_per_round": upd, "init_s": round(init_s, 2)}
+    out = {"instances": count, "ranks": ws, "orbitals": [min(all_sizes), max(all_sizes)],
+           "mean_ndet_rank0": ndets / max(1, len(mine)), "updates_per_round_rank0": upd, "init_s": round(init_s, 2)}
     for prec in (64, 32):
         L.iscsi_set_option("precision", prec)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -472,10 +496,11 @@ def run_batching(count=64, reps=5, tau=1e-14, nroots=1):
             torch.cuda.synchronize()
             wall = (time.time() - w0) / reps
             ms = e0.elapsed_time(e1) / reps
+            ms, wall = max_over_ranks([ms, wall], device="cuda")
             res[name] = {"ms_per_round": round(ms, 3), "host_wall_ms_per_round": round(wall * 1e3, 3),
                          "instances_per_s": round(count / (ms * 1e-3), 1),
                          "sigma_per_s": round(count / (ms * 1e-3), 1),
-                         "GUpdates_per_s": round(upd / (ms * 1e-3) / 1e9, 1)}
+                         "GUpdates_per_s_rank0": round(upd / (ms * 1e-3) / 1e9, 1)}
         res["speedup"] = round(res["one_at_a_time"]["ms_per_round"] / res["batched"]["ms_per_round"], 3)
         out["fp%d" % prec] = res
     L.iscsi_set_option("precision", 64)
@@ -497,6 +522,7 @@ def run_batching(count=64, reps=5, tau=1e-14, nroots=1):
         st, e_batch, sts = L.iscsi_batch_davidson(hs, nroots, 1e-8)
         torch.cuda.synchronize()
         dt2 = time.time() - t0
+        dt1, dt2 = max_over_ranks([dt1, dt2], device="cuda")
         de = float(np.abs(np.asarray(e_single) - e_batch).max())
         out["davidson_fp%d" % prec] = {
             "roots_per_instance": nroots, "one_at_a_time_s": round(dt1, 2), "batched_s": round(dt2, 2),
@@ -669,8 +695,11 @@ def main():
     if rank == 0 and ws == 1 and args.mixed_workload != "none":
         # the precision form: FP32-mixed vs FP64 Davidson, |dE| and speedup (untimed by the contract)
         line["mixed_precision"] = run_precision_form(args.mixed_workload, args.mixed_roots)
-    if rank == 0 and ws == 1 and args.batching > 0:
-        line["batching"] = run_batching(args.batching)
+    if args.batching > 0:
+        # every rank runs its share of the instances; rank 0 reports the job
+        b = run_batching(args.batching, rank=rank, ws=ws)
+        if rank == 0:
+            line["batching"] = b
     if rank == 0 and ws == 1 and args.sweep:
         line["box_sweep"] = run_sweep()
     if rank == 0:
