@@ -326,18 +326,23 @@ def run_ours(args, wl, ws, rank, local):
     route = st.get("route_fp%d" % args.precision, {})
     cl = route.get("cl", 1) if args.tc_cluster == 1 else (2 if args.tc_cluster == 2 else 1)
     tc = tc and route.get("ab_tc", 1) == 1
+    # with both contractions on the tensor cores they are one launch: its flops
+    # are the opposite- and the same-spin slice products
+    both = st.get("both_tc_fp%d" % args.precision, 0) == 1
+    what = "opposite- and same-spin contractions in one launch" if both else "opposite-spin contraction"
+    tag = "_both" if both else ""
     if tc and args.precision == 64:
         # tensor-core kernel: bf16 MMA flops it issues (28 exact slice products)
-        flops = st["opposite_tc_bf16_flops"]
+        flops = st["opposite_tc_bf16_flops"] + (st.get("samespin_tc_bf16_flops", 0.0) if both else 0.0)
         peak, peak_src = bf16_peak()
-        bound, kname, kkey = "tensor", "k_oz_gemm<%d> (tcgen05, FP64-accurate opposite-spin contraction, " \
-            "clusters of %d CTA)" % (cl, cl), "k_oz_gemm_cl%d_%s" % (cl, args.workload)
+        bound, kname, kkey = "tensor", "k_oz_gemm<%d> (tcgen05, FP64-accurate %s, clusters of %d CTA)" % (
+            cl, what, cl), "k_oz_gemm_cl%d%s_%s" % (cl, tag, args.workload)
     elif tc:
         # FP32 form: 6 of the 9 products of three bf16 terms per operand
-        flops = st["opposite_tc_bf16_flops"] * 6.0 / 28.0
+        flops = (st["opposite_tc_bf16_flops"] + (st.get("samespin_tc_bf16_flops", 0.0) if both else 0.0)) * 6.0 / 28.0
         peak, peak_src = bf16_peak()
-        bound, kname, kkey = "tensor", "k_tc32_gemm<%d> (tcgen05, FP32-accurate opposite-spin contraction, " \
-            "clusters of %d CTA)" % (cl, cl), "k_tc32_gemm_cl%d_%s" % (cl, args.workload)
+        bound, kname, kkey = "tensor", "k_tc32_gemm<%d> (tcgen05, FP32-accurate %s, clusters of %d CTA)" % (
+            cl, what, cl), "k_tc32_gemm_cl%d%s_%s" % (cl, tag, args.workload)
     else:
         flops = st["opposite_gemm_flops"]
         peak = FP64_PEAK_TFLOPS if args.precision == 64 else FP32_PEAK_TFLOPS

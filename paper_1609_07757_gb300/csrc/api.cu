@@ -303,6 +303,16 @@ iscsi_status iscsi_stats(char* json, int len) {
     out += v;
   }
   out += "]";
+  // whether the opposite- and same-spin tensor-core products run as one launch
+  {
+    char v[256];
+    auto both = [&](int prec) {
+      return ctx->have_ab && ab_on_tc(*ctx, prec) && (prec == 64 ? samespin_tc_active(*ctx) : samespin_tc32_active(*ctx));
+    };
+    std::snprintf(v, sizeof(v), ", \"samespin_tc_bf16_flops\": %.17g, \"both_tc_fp64\": %d, \"both_tc_fp32\": %d",
+                  ctx_gemm_flops(*ctx, 3), both(64) ? 1 : 0, both(32) ? 1 : 0);
+    out += v;
+  }
   // the autotuner's routing per precision and its trials (ab_tc, ss_min or -1 =
   // none on the tensor cores, cluster size, predicted ms, measured ms or -1 =
   // pruned)

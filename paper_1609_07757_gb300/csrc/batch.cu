@@ -143,6 +143,11 @@ int StreamPool::join(cudaStream_t main) {
 
 namespace {
 
+// both contractions of the context on the tensor cores (one combined list)
+bool both_tc(const Context& c, int prec) {
+  return c.have_ab && ab_on_tc(c, prec) && (prec == 64 ? samespin_tc_active(c) : samespin_tc32_active(c));
+}
+
 // one phase of every context, each on a pool stream (concurrent chains);
 // skip_tc: only the contexts whose opposite-spin contraction is not on the
 // tensor cores (those run in the merged launch)
@@ -184,11 +189,19 @@ int sigma_batch_sequence(SigmaBatch& B) {
       std::vector<const OzJob*> jobs;
       std::vector<void*> tb;
       for (int i = 0; i < n; ++i) {
-        if (!B.ctxs[i]->have_ab || !ab_on_tc(*B.ctxs[i], B.prec)) continue;
-        const OzJob* J = B.prec == 64 ? &B.ctxs[i]->oz_ab : &B.ctxs[i]->t3_ab;
+        Context& c = *B.ctxs[i];
+        if (!c.have_ab || !ab_on_tc(c, B.prec)) continue;
+        const OzJob* J = B.prec == 64 ? &c.oz_ab : &c.t3_ab;
+        void* base = nullptr;  // the opposite-spin outputs are absolute (the context's T workspace)
+        if (both_tc(c, B.prec)) {
+          // the context's combined list: its same-spin outputs are relative to its sigma
+          J = both_tc_job(c, B.prec);
+          if (!J) return kErrCuda;
+          base = B.prec == 64 ? static_cast<void*>(B.ss[i]) : static_cast<void*>(c.s32.as<float>());
+        }
         if (J->cl != cl) continue;
         jobs.push_back(J);
-        tb.push_back(nullptr);  // absolute output pointers (the context's T workspace)
+        tb.push_back(base);
       }
       ISCSI_TRY(merge_jobs(B.ab[cl - 1], jobs, tb, st));
       ISCSI_TRY(launch_merged(B.ab[cl - 1], B.prec, B.err.as<int>(), st));
@@ -202,7 +215,7 @@ int sigma_batch_sequence(SigmaBatch& B) {
     for (int i = 0; i < n; ++i) {
       Context& c = *B.ctxs[i];
       const bool on = B.prec == 64 ? samespin_tc_active(c) : samespin_tc32_active(c);
-      if (!on) continue;
+      if (!on || both_tc(c, B.prec)) continue;  // combined contexts ran above
       jobs.push_back(B.prec == 64 ? &c.oz_ss : &c.t3_ss);
       tb.push_back(B.prec == 64 ? static_cast<void*>(B.ss[i]) : static_cast<void*>(c.s32.as<float>()));
     }

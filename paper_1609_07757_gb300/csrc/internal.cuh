@@ -143,6 +143,7 @@ struct OzJob {
   const void* tbase = nullptr;
   long long version = 0;  // bumped at every rebuild (launches over several contexts re-merge)
   int cl = 1;             // CTAs per cluster of its launches (2: A tiles multicast to CTA pairs)
+  long long src_ver[2] = {-1, -1};  // a combined job: versions of the jobs it was built from
 };
 
 struct ColClass {       // column level class c = level(X) + level(Y)
@@ -189,7 +190,7 @@ struct Context {
   DevBuf oz_gs, oz_gexp, oz_bs, oz_bexp, oz_err;
   int oz_mpad = 0, oz_kpad = 0;
   long long oz_bs_elems = 0;
-  OzJob oz_ab, oz_ss;
+  OzJob oz_ab, oz_ss, oz_both;  // oz_both: oz_ab and oz_ss as one problem list
   DevBuf oz_mas, oz_maexp, oz_mbs, oz_mbexp, oz_cs, oz_csexp;
   std::vector<int> oz_kbase;
   int oz_ma_rows = 0, oz_ma_ld = 0, oz_mb_rows = 0, oz_mb_ld = 0;
@@ -207,7 +208,7 @@ struct Context {
   long long pl_route_key = -1, pl_route_key32 = -1;  // routing the grouped-GEMM lists were built for
   int pl_ss_tc = -1;  // same-spin routing the FP64 grouped-GEMM list was built for
   // FP32 form of the tensor-core contractions (three bf16 terms per element)
-  OzJob t3_ab, t3_ss;
+  OzJob t3_ab, t3_ss, t3_both;
   DevBuf t3_gs, t3_bs, t3_mas, t3_mbs, t3_cs;
   long long t3_bs_elems = 0, t3_cs_elems = 0;
   bool t3_m_ready = false;
@@ -287,6 +288,9 @@ int opposite_tc32_gemm(Context& ctx);
 bool samespin_tc32_active(const Context& ctx);
 int samespin_tc32_operands(Context& ctx, const float* c, float* sigma, int nvec);
 int samespin_tc32_gemm(Context& ctx, float* sigma);
+int both_tc_gemm(Context& ctx, double* sigma);  // opposite- and same-spin contractions, one launch
+int both_tc32_gemm(Context& ctx, float* sigma);
+const OzJob* both_tc_job(Context& ctx, int prec);  // that combined job (built when needed), or nullptr
 int launch_tc_problems(const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
                        void* const* tbases, int tiles, int prec, int cl, int* err, cudaStream_t st);
 int tc_check(Context& ctx);

@@ -437,13 +437,13 @@ __global__ void k_lift_ct(ClassTable ct, int nvec, int n, int nholeA, int nholeB
   out[t] = val;
 }
 
-// fold: sigma_v[A,B] = sum_{(p,X)->A} sum_{(r,Y)->B} s s T_c[pi(p,r)][(X,Y), v]
+// fold: sigma_v[A,B] (+)= sum_{(p,X)->A} sum_{(r,Y)->B} s s T_c[pi(p,r)][(X,Y), v]
 template <typename T>
 __global__ void k_fold(ClassTable ct, int nvec, int n, int na, int nb, int nholeB, const int* __restrict__ decA,
                        const int* __restrict__ decB, const int8_t* __restrict__ hp_class,
                        const int* __restrict__ hp_local, const int* __restrict__ pair_index,
                        const long long* __restrict__ off, const T* __restrict__ tt, long long ndet,
-                       T* __restrict__ sigma) {
+                       T* __restrict__ sigma, int accumulate) {
   int A = blockIdx.x;
   long long o0 = off[A], o1 = off[A + 1];
   long long work = (o1 - o0) * nvec;
@@ -463,7 +463,8 @@ __global__ void k_fold(ClassTable ct, int nvec, int n, int na, int nb, int nhole
         acc += ((da ^ db) & 1) ? -x : x;
       }
     }
-    sigma[(long long)v * ndet + o0 + B] = acc;
+    T* dst = sigma + (long long)v * ndet + o0 + B;
+    *dst = accumulate ? *dst + acc : acc;
   }
 }
 
@@ -594,6 +595,25 @@ static int build_problems(Context& ctx, int nvec, const T* G, const T* Ma, const
 
 double ctx_gemm_flops(const Context& ctx, int which) {
   double f = 0.0;
+  if (which == 3) {
+    // bf16 MMA flops of the same-spin level blocks on the tensor cores (FP64
+    // routing): 28 slice products x 2 M N K, K padded to 16 per segment
+    const SpinSpace& SA = ctx.sp[0];
+    auto pad = [](double x) { return std::ceil(x / 16.0) * 16.0; };
+    for (int a = 0; a <= SA.maxlevel; ++a) {
+      if (!samespin_block_on_tc(ctx, a, 64)) continue;
+      double rows = SA.level_start[a + 1] - SA.level_start[a], nba = (double)ctx.nb_allowed_lvl[a];
+      if (rows == 0 || nba == 0) continue;
+      if (ctx.na > 0 && ctx.M64[0].p)
+        for (int a2 = 0; a2 <= SA.maxlevel; ++a2) {
+          double rows2 = SA.level_start[a2 + 1] - SA.level_start[a2], nba2 = (double)ctx.nb_allowed_lvl[a2];
+          if (rows2 == 0 || nba2 == 0 || std::abs(a - a2) > 2) continue;
+          f += 28.0 * 2.0 * rows * pad(rows2) * std::min(nba, nba2);
+        }
+      if (ctx.nb > 0) f += 28.0 * 2.0 * rows * nba * pad(nba);
+    }
+    return f;
+  }
   if (which == 2) {
     // bf16 MMA flops the tensor-core opposite-spin contraction issues: 28 slice
     // products (levels 0..6 of 7 slices) x 2 M N K, K rounded up to 16
@@ -681,6 +701,10 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
   constexpr bool f64 = std::is_same<T, double>::value;
   const int ss_tc = (f64 ? samespin_tc_active(ctx) : samespin_tc32_active(ctx)) ? 1 : 0;
   const bool tc_path = ab_on_tc(ctx, f64 ? 64 : 32);
+  // both contractions on the tensor cores: one launch for both problem lists
+  // (fewer partly filled waves); sigma starts at zero, the same-spin products
+  // add into it, the fold adds last
+  const bool comb = ctx.have_ab && tc_path && ss_tc;
   // per-phase events only when the whole step runs in this call
   const bool timed = phases == kPhAll;
   const int call = ctx.ntimed;
@@ -711,6 +735,15 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
       else
         ISCSI_TRY(opposite_tc32_operands(ctx, reinterpret_cast<const float*>(c_in), reinterpret_cast<float*>(ttw),
                                          nvec));
+      if (comb) {
+        ISCSI_CUDA(cudaMemsetAsync(sigma, 0, sizeof(T) * ctx.ndet * nvec, st));
+        if (f64)
+          ISCSI_TRY(samespin_tc_operands(ctx, reinterpret_cast<const double*>(c), reinterpret_cast<double*>(sigma),
+                                         nvec));
+        else
+          ISCSI_TRY(samespin_tc32_operands(ctx, reinterpret_cast<const float*>(c), reinterpret_cast<float*>(sigma),
+                                           nvec));
+      }
     } else if (ctx.have_ab) {
       ClassTable ct = class_table(ctx, nvec);
       long long tot = ct.start[ct.nclass];
@@ -727,7 +760,10 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
     ISCSI_TRY(ev(1));
   }
   if (phases & kPhAbGemm) {
-    if (ctx.have_ab && tc_path)
+    if (comb)
+      ISCSI_TRY(f64 ? both_tc_gemm(ctx, reinterpret_cast<double*>(sigma))
+                    : both_tc32_gemm(ctx, reinterpret_cast<float*>(sigma)));
+    else if (ctx.have_ab && tc_path)
       ISCSI_TRY(f64 ? opposite_tc_gemm(ctx) : opposite_tc32_gemm(ctx));
     else if (ctx.have_ab)
       ISCSI_TRY(launch_grouped<T>(ab, c, sigma, st));
@@ -740,20 +776,20 @@ static int sigma_impl(Context& ctx, const TC* c_in, T* s_out, const T* c, T* sig
                                                  ctx.sp[0].dec.as<int>(), ctx.sp[1].dec.as<int>(),
                                                  ctx.hp_class.as<int8_t>(), ctx.hp_local.as<int>(),
                                                  ctx.pair_index.as<int>(), ctx.off.as<long long>(), ttw, ctx.ndet,
-                                                 sigma); ISCSI_COUNT_LAUNCH();
+                                                 sigma, comb ? 1 : 0); ISCSI_COUNT_LAUNCH();
       ISCSI_CUDA(cudaGetLastError());
     }
     ISCSI_TRY(ev(3));
     ISCSI_TRY(launch_grouped<T>(ss, c, sigma, st));
-    if (ss_tc && f64)
+    if (ss_tc && !comb && f64)
       ISCSI_TRY(samespin_tc_operands(ctx, reinterpret_cast<const double*>(c), reinterpret_cast<double*>(sigma), nvec));
-    else if (ss_tc)
+    else if (ss_tc && !comb)
       ISCSI_TRY(samespin_tc32_operands(ctx, reinterpret_cast<const float*>(c), reinterpret_cast<float*>(sigma), nvec));
   }
   if (phases & kPhSsGemm) {
-    if (ss_tc && f64)
+    if (ss_tc && !comb && f64)
       ISCSI_TRY(samespin_tc_gemm(ctx, reinterpret_cast<double*>(sigma)));
-    else if (ss_tc)
+    else if (ss_tc && !comb)
       ISCSI_TRY(samespin_tc32_gemm(ctx, reinterpret_cast<float*>(sigma)));
   }
   if (phases & kPhPost) {
@@ -1069,7 +1105,7 @@ int sigma_noalloc_run(Context& ctx, const double* c, double* sigma) {
                                                     ctx.sp[0].dec.as<int>(), ctx.sp[1].dec.as<int>(),
                                                     ctx.hp_class.as<int8_t>(), ctx.hp_local.as<int>(),
                                                     ctx.pair_index.as<int>(), ctx.off.as<long long>(), ttw, ctx.ndet,
-                                                    sigma); ISCSI_COUNT_LAUNCH();
+                                                    sigma, 0); ISCSI_COUNT_LAUNCH();
   } else {
     ISCSI_CUDA(cudaMemsetAsync(sigma, 0, sizeof(double) * ctx.ndet, st));
   }

@@ -818,6 +818,49 @@ int samespin_tc32_operands(Context& ctx, const float* c, float* sigma, int nvec)
 
 int samespin_tc32_gemm(Context& ctx, float* sigma) { return t3_launch(ctx, ctx.t3_ss, sigma, stream()); }
 
+// The opposite-spin and same-spin problem lists of a context as one list
+// (one launch fills the GPU's waves better than two).  Rebuilt when either
+// source job changed; the same-spin problems take the opposite-spin job's
+// cluster shape.
+static int build_both(OzJob& both, const OzJob& ab, const OzJob& ss, cudaStream_t st) {
+  if (both.src_ver[0] == ab.version && both.src_ver[1] == ss.version && both.cl == ab.cl) return kOk;
+  both.probs = ab.probs;
+  both.segs = ab.segs;
+  both.maps = ab.maps;
+  const int seg0 = (int)ab.segs.size();
+  for (OzProblem P : ss.probs) {
+    P.seg_begin += seg0;
+    both.probs.push_back(P);
+  }
+  both.segs.insert(both.segs.end(), ss.segs.begin(), ss.segs.end());
+  both.maps.insert(both.maps.end(), ss.maps.begin(), ss.maps.end());
+  both.cl = ab.cl;
+  both.tiles = add_tiles(both.probs, both.cl);
+  ISCSI_TRY(upload_job(both, st));
+  both.src_ver[0] = ab.version;
+  both.src_ver[1] = ss.version;
+  return kOk;
+}
+
+const OzJob* both_tc_job(Context& ctx, int prec) {
+  OzJob& both = prec == 64 ? ctx.oz_both : ctx.t3_both;
+  if (build_both(both, prec == 64 ? ctx.oz_ab : ctx.t3_ab, prec == 64 ? ctx.oz_ss : ctx.t3_ss, stream()) != kOk)
+    return nullptr;
+  return &both;
+}
+
+int both_tc_gemm(Context& ctx, double* sigma) {
+  cudaStream_t st = stream();
+  ISCSI_TRY(build_both(ctx.oz_both, ctx.oz_ab, ctx.oz_ss, st));
+  return launch_job(ctx, ctx.oz_both, sigma, st);
+}
+
+int both_tc32_gemm(Context& ctx, float* sigma) {
+  cudaStream_t st = stream();
+  ISCSI_TRY(build_both(ctx.t3_both, ctx.t3_ab, ctx.t3_ss, st));
+  return t3_launch(ctx, ctx.t3_both, sigma, st);
+}
+
 // one launch of the FP64-accurate (prec 64) or FP32-form (prec 32) contraction
 // over a device problem list whose relative outputs use the base table tbases
 int launch_tc_problems(const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,

@@ -411,10 +411,13 @@ def test_autotune_picks_a_timed_routing_with_the_same_sigma(precision):
 
 @pytest.mark.parametrize("precision", [64, 32])
 def test_two_cta_clusters_give_identical_sigma(precision):
-    # the opposite-spin contraction in two-CTA clusters (A tiles multicast to
-    # the pair) computes the same tiles in the same order: bit-identical
-    # sigma; problems with an odd column-tile count exercise the padded
-    # partner tile
+    # the contractions in two-CTA clusters (A tiles multicast to the pair)
+    # compute the same tiles: bit-identical FP64 sigma (its exact integer
+    # levels do not depend on how K is grouped); in the FP32 form a pair may
+    # step through a segment that contributes zeros to one of its tiles, which
+    # moves that tile's 512-wide chunk boundaries and so its FP32 rounding:
+    # equal within the FP32 bound.  Odd column-tile counts exercise the padded
+    # partner tile.
     n, k, tau = 30, 3, 1e-12
     h1, eri = make_integrals(n, 1450, ell=4.0, nchol=16)
     L.iscsi_init(n, 2, 2, k, h1, eri, tau)
@@ -427,7 +430,11 @@ def test_two_cta_clusters_give_identical_sigma(precision):
             outs.append(gpu_sigma(C, nvec=3, precision=precision))
     finally:
         L.iscsi_set_option("tc_cluster", 1)
-    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    assert np.array_equal(outs[0], outs[2])  # deterministic
+    if precision == 64:
+        assert np.array_equal(outs[0], outs[1])
+    else:
+        assert np.linalg.norm(outs[1] - outs[0]) <= REL32 * np.linalg.norm(outs[0])
     o = Oracle(n, 2, 2, k, tau, h1, eri)
     rows = np.random.default_rng(3).choice(nd, size=200, replace=False)
     rel = REL64 if precision == 64 else REL32
