@@ -10,7 +10,8 @@ Contents
     (Eq. ci_hierarchy truncated at total excitation level k), the screened
     Hamiltonian of Eq. index_re (screening of Eq. sigma_split, applied per
     integral unit as in the screened loops of Sec. "Second part"), sigma by
-    two independent traversals and dense H.
+    two independent traversals and dense H; the density matrices of Eqs. d1
+    and d2 by explicit operator application.
   * ``jordan_wigner`` -- a third, independent route: the Fock-space matrix of
     the unrestricted Hamiltonian of Eq. ham for tiny orbital counts.
 
@@ -53,6 +54,8 @@ def _load():
         lib.ora_hij.restype = ctypes.c_double
         lib.ora_hij.argtypes = [vp, i64, i64, u64]
         lib.ora_max_threads.restype = ctypes.c_int
+        lib.ora_density.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int]
+        lib.ora_density_elems.argtypes = [vp, dp, dp, ip, i64, dp, ctypes.c_int]
         lib.ora_apply.restype = ctypes.c_int
         lib.ora_apply.argtypes = [ctypes.c_int, ip, ip, ctypes.c_int, ip, ip, ip]
         _lib = lib
@@ -152,6 +155,38 @@ class Oracle:
 
     def hij(self, i, j, mask=ALL_CLASSES):
         return float(_load().ora_hij(self._h, i, j, ctypes.c_uint64(mask)))
+
+    def density(self, bra, ket=None, two_body=True, nthreads=0):
+        """One- and two-body density matrices of Eqs. d1 and d2, spin-resolved.
+
+        Returns (d1 [2, n, n], d2 [3, n, n, n, n] or None):
+          d1[s, p, q]       = <bra| a+_ps a_qs |ket>                 (s = alpha, beta)
+          d2[b, p, q, r, t] = <bra| a+_ps a+_ru a_tu a_qs |ket>      ((s,u) = aa, ab, bb)
+        by applying each operator string to every determinant of the space.
+        ket defaults to bra.  Cost ~ ndet * n^2 (4 n^2 determinant look-ups
+        per determinant and block): small spaces only.
+        """
+        bra = np.ascontiguousarray(bra, dtype=np.float64)
+        ket = bra if ket is None else np.ascontiguousarray(ket, dtype=np.float64)
+        assert bra.shape == (self.ndet,) and ket.shape == (self.ndet,)
+        n = self.n
+        d1 = np.zeros((2, n, n))
+        d2 = np.zeros((3, n, n, n, n)) if two_body else None
+        _load().ora_density(self._h, _ptr(bra), _ptr(ket), _ptr(d1), None if d2 is None else _ptr(d2), int(nthreads))
+        return d1, d2
+
+    def density_elems(self, bra, ket, spec, nthreads=0):
+        """Single density-matrix elements, each a sum over the whole space.
+
+        spec: int array [m, 5] of (block, p, q, r, t): block 0..2 selects
+        d2[block, p, q, r, t], block 3 / 4 selects d1[0 / 1, p, q].
+        """
+        bra = np.ascontiguousarray(bra, dtype=np.float64)
+        ket = bra if ket is None else np.ascontiguousarray(ket, dtype=np.float64)
+        spec = np.ascontiguousarray(spec, dtype=np.int32).reshape(-1, 5)
+        out = np.zeros(spec.shape[0])
+        _load().ora_density_elems(self._h, _ptr(bra), _ptr(ket), _ptr(spec), spec.shape[0], _ptr(out), int(nthreads))
+        return out
 
     def eigh(self, mask=ALL_CLASSES):
         """All eigenvalues / eigenvectors of the dense H_tau (LAPACK via numpy)."""

@@ -22,7 +22,10 @@
  *       ora_sigma_terms : every surviving term applied to every determinant
  *                         (the distributive form of Eq. sigma_int), and
  *       ora_sigma_rows  : row-wise, H_IJ assembled from the terms that can
- *                         connect J to I (Slater-Condon selection), any n.
+ *                         connect J to I (Slater-Condon selection), any n;
+ *   - the one- and two-body density matrices of Eqs. d1 and d2 (Sec.
+ *     "Density matrices"), spin-resolved, by explicit operator application
+ *     (ora_density for all elements, ora_density_elems for single ones).
  *
  * Conventions (fixed by this library's interface, not by the paper):
  *   - strings are sorted by (excitation level, colex rank of the ascending
@@ -700,6 +703,154 @@ void ora_sigma_rows(void *p, const double *c, const int64_t *rows, int64_t nrows
 #endif
 #pragma omp parallel for schedule(dynamic, 8)
   for (int64_t k = 0; k < nrows; ++k) out[k] = sigma_row(o, c, rows[k], mask);
+}
+
+/* ------------------------------------------------------------------ */
+/* density matrices (Sec. "Density matrices", Eqs. d1 and d2)           */
+/*                                                                      */
+/* Spin-resolved blocks, from the definitions by explicit operator      */
+/* application on every determinant of the space (no string tables, no  */
+/* excitation classes):                                                 */
+/*   D1[s][p][q]     = <bra| a+_{p s} a_{q s} |ket>,     s = alpha, beta   */
+/*   D2[b][p][q][r][t] = <bra| a+_{p s} a+_{r u} a_{t u} a_{q s} |ket>     */
+/*     with (s, u) = (alpha, alpha), (alpha, beta), (beta, beta) for       */
+/*     b = 0, 1, 2; flat index ((p n + q) n + r) n + t.                   */
+/* The spin-summed D2 of Eq. d2 is D2[0] + D2[2] + D2[1] + D2[1] with     */
+/* (p,q) and (r,t) swapped.                                             */
+
+static const int dm_spin1[3] = {0, 0, 1}, dm_spin2[3] = {0, 1, 1};
+
+/* accumulates ket_J's contributions into d1 [2 n n] and d2 [3 n^4] (d2 may be NULL) */
+static void density_from_det(const Oracle *o, const double *bra, double kJ, const Det *dJ, double *d1, double *d2) {
+  int n = o->n;
+  for (int sp = 0; sp < 2; ++sp)
+    for (int q = 0; q < n; ++q) {
+      Det d0 = *dJ;
+      int s1 = op_apply(&d0, 0, sp * n + q);
+      if (!s1) continue;
+      for (int p = 0; p < n; ++p) {
+        Det d = d0;
+        int s2 = op_apply(&d, 1, sp * n + p);
+        if (!s2) continue;
+        int64_t I = det_lookup(o, &d);
+        if (I >= 0) d1[(sp * n + p) * n + q] += bra[I] * (double)(s1 * s2) * kJ;
+      }
+    }
+  if (!d2) return;
+  int64_t n2 = (int64_t)n * n, n4 = n2 * n2;
+  for (int b = 0; b < 3; ++b) {
+    int so1 = dm_spin1[b] * n, so2 = dm_spin2[b] * n;
+    for (int q = 0; q < n; ++q)
+      for (int t = 0; t < n; ++t) {
+        Det d0 = *dJ; /* a_{q s} acts first, then a_{t u} */
+        int s1 = op_apply(&d0, 0, so1 + q);
+        if (!s1) continue;
+        int s2 = op_apply(&d0, 0, so2 + t);
+        if (!s2) continue;
+        for (int r = 0; r < n; ++r) {
+          Det d1r = d0;
+          int s3 = op_apply(&d1r, 1, so2 + r);
+          if (!s3) continue;
+          for (int p = 0; p < n; ++p) {
+            Det d = d1r;
+            int s4 = op_apply(&d, 1, so1 + p);
+            if (!s4) continue;
+            int64_t I = det_lookup(o, &d);
+            if (I < 0) continue;
+            d2[b * n4 + ((int64_t)p * n + q) * n2 + (int64_t)r * n + t] += bra[I] * (double)(s1 * s2 * s3 * s4) * kJ;
+          }
+        }
+      }
+  }
+}
+
+/* all blocks of D1 and (if d2) D2 for the pair (bra, ket); both [ndet] */
+void ora_density(void *ptr, const double *bra, const double *ket, double *d1, double *d2, int nthreads) {
+  Oracle *o = (Oracle *)ptr;
+  int n = o->n;
+  int64_t n1 = 2 * (int64_t)n * n, n4 = (int64_t)n * n * n * n, n2tot = d2 ? 3 * n4 : 0;
+  memset(d1, 0, sizeof(double) * (size_t)n1);
+  if (d2) memset(d2, 0, sizeof(double) * (size_t)n2tot);
+  int nt = 1;
+#ifdef _OPENMP
+  nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+  /* private accumulators: at most ~2 GB in total */
+  int64_t per = (n1 + n2tot) * (int64_t)sizeof(double);
+  while (nt > 1 && per * nt > ((int64_t)2 << 30)) --nt;
+#else
+  (void)nthreads;
+#endif
+  double *acc = (double *)calloc((size_t)nt * (size_t)(n1 + n2tot), sizeof(double));
+  if (!acc) return;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 16)
+#endif
+  for (int64_t J = 0; J < o->ndet; ++J) {
+    if (ket[J] == 0.0) continue;
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    double *a1 = acc + (size_t)tid * (size_t)(n1 + n2tot);
+    Det dJ;
+    det_of_index(o, J, &dJ);
+    density_from_det(o, bra, ket[J], &dJ, a1, d2 ? a1 + n1 : NULL);
+  }
+  for (int t = 0; t < nt; ++t) {
+    double *a1 = acc + (size_t)t * (size_t)(n1 + n2tot);
+    for (int64_t i = 0; i < n1; ++i) d1[i] += a1[i];
+    for (int64_t i = 0; i < n2tot; ++i) d2[i] += a1[n1 + i];
+  }
+  free(acc);
+}
+
+/* single elements, each summed over every determinant J of the space:
+   spec[5k..5k+4] = (block, p, q, r, t); block 0..2 are the D2 blocks
+   (aa, ab, bb), block 3 / 4 the alpha / beta D1 (r, t ignored) */
+void ora_density_elems(void *ptr, const double *bra, const double *ket, const int *spec, int64_t m, double *out,
+                       int nthreads) {
+  Oracle *o = (Oracle *)ptr;
+  int n = o->n;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t k = 0; k < m; ++k) {
+    const int *sp = spec + 5 * k;
+    OpString op;
+    if (sp[0] >= 3) {
+      int s = (sp[0] - 3) * n;
+      op.nops = 2;
+      op.create[0] = 1;
+      op.so[0] = s + sp[1];
+      op.create[1] = 0;
+      op.so[1] = s + sp[2];
+    } else {
+      int s1 = dm_spin1[sp[0]] * n, s2 = dm_spin2[sp[0]] * n;
+      op.nops = 4;
+      op.create[0] = 1;
+      op.so[0] = s1 + sp[1];
+      op.create[1] = 1;
+      op.so[1] = s2 + sp[3];
+      op.create[2] = 0;
+      op.so[2] = s2 + sp[4];
+      op.create[3] = 0;
+      op.so[3] = s1 + sp[2];
+    }
+    double acc = 0.0;
+    for (int64_t J = 0; J < o->ndet; ++J) {
+      if (ket[J] == 0.0) continue;
+      Det d;
+      det_of_index(o, J, &d);
+      int sg = opstring_apply(&op, &d);
+      if (!sg) continue;
+      int64_t I = det_lookup(o, &d);
+      if (I >= 0) acc += bra[I] * (double)sg * ket[J];
+    }
+    out[k] = acc;
+  }
 }
 
 int ora_max_threads(void) {

@@ -81,3 +81,38 @@ def projected(h1, eri_full, n, dets):
     nm = 2 * n
     idx = [_basis_index(list(A) + [n + b for b in B], nm) for A, B in dets]
     return H[idx, :][:, idx].toarray()
+
+
+def density(n, dets, bra, ket):
+    """Spin-resolved density matrices (Eqs. d1 and d2) through Fock-space matrices.
+
+    dets: the determinant list (alpha orbitals, beta orbitals) that bra and
+    ket are expanded in.  Returns (d1 [2, n, n], d2 [3, n, n, n, n]) with
+      d1[s, p, q]       = <bra| a+_ps a_qs |ket>,
+      d2[b, p, q, r, t] = <bra| a+_ps a+_ru a_tu a_qs |ket>,  (s,u) = aa, ab, bb,
+    computed as inner products of the Fock vectors a_ru a_ps |bra> and
+    a_tu a_qs |ket> (the adjoint of a+_ps a+_ru is a_ru a_ps).
+    """
+    nm = 2 * n
+    a = _annihilators(nm)
+    dim = 1 << nm
+    fb = np.zeros(dim)
+    fk = np.zeros(dim)
+    for (A, B), x, y in zip(dets, bra, ket):
+        i = _basis_index(list(A) + [n + b for b in B], nm)
+        fb[i] = x
+        fk[i] = y
+    d1 = np.zeros((2, n, n))
+    for s in range(2):
+        vb = [a[s * n + p] @ fb for p in range(n)]
+        vk = [a[s * n + q] @ fk for q in range(n)]
+        for p in range(n):
+            for q in range(n):
+                d1[s, p, q] = vb[p] @ vk[q]
+    d2 = np.zeros((3, n, n, n, n))
+    for b, (s, u) in enumerate(((0, 0), (0, 1), (1, 1))):
+        # X[p, r] = a_ru a_ps |bra>, Y[q, t] = a_tu a_qs |ket>
+        X = np.array([[a[u * n + r] @ (a[s * n + p] @ fb) for r in range(n)] for p in range(n)])
+        Y = np.array([[a[u * n + t] @ (a[s * n + q] @ fk) for t in range(n)] for q in range(n)])
+        d2[b] = np.einsum("prk,qtk->pqrt", X, Y)
+    return d1, d2
