@@ -539,6 +539,87 @@ def run_batching(count=64, reps=5, tau=1e-14, nroots=1, rank=0, ws=1):
     return out
 
 
+def run_density(name, steps=10, warmup=3, with_cpu=True, tau=None):
+    """One- and two-body density matrices (Eqs. d1, d2) of a unit vector on a
+    workload: device ms per call (L2 flushed between calls), the contraction's
+    launch time and tensor-core rate, and the oracle's element-wise route on a
+    bounded sample of elements, scaled to the whole tensor."""
+    import numpy as np
+    import torch
+
+    from paper_1609_07757_gb300 import _lib as L
+    from paper_1609_07757_gb300.synthetic import make_integrals, unit_vector
+
+    wl = WORKLOADS[name]
+    tau = wl["tau"] if tau is None else tau
+    h1, eri = make_integrals(wl["n"], wl["seed"], ell=wl["ell"], nchol=wl["nchol"], box=wl["box"])
+    stream = torch.cuda.current_stream()
+    L.iscsi_set_stream(stream)
+    L.iscsi_init(wl["n"], wl["na"], wl["nb"], wl["kmax"], h1, eri, tau)
+    n, ndet = wl["n"], L.iscsi_ndet()
+    c = torch.tensor(unit_vector(ndet, 23), dtype=torch.float64, device="cuda")
+    d1 = torch.empty((2, n, n), dtype=torch.float64, device="cuda")
+    d2 = torch.empty((3, n, n, n, n), dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(max(3, warmup)):
+        L.iscsi_density(c, None, d1, d2)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    gemm = []
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        L.iscsi_density(c, None, d1, d2)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    # the contraction's own launch time, read after further untimed calls
+    for _ in range(3):
+        flush.zero_()
+        L.iscsi_density(c, None, d1, d2)
+        gemm.append(L.iscsi_stats()["density_gemm_ms"])
+    st = L.iscsi_stats()
+    bf16, fp64 = st["density_bf16_flops"][0], st["density_fp64_flops"][0]
+    gemm_ms = float(np.mean(gemm))
+    peak, peak_src = bf16_peak()
+    # invariants of a unit vector: traces of the blocks
+    na, nb = wl["na"], wl["nb"]
+    tr = [float(torch.einsum("pprr->", d2[b])) for b in range(3)]
+    checks = {"trace_aa": tr[0], "trace_ab": tr[1], "trace_bb": tr[2],
+              "expected": [na * (na - 1), na * nb, nb * (nb - 1)],
+              "max_trace_err": max(abs(tr[0] - na * (na - 1)), abs(tr[1] - na * nb), abs(tr[2] - nb * (nb - 1)))}
+    out = {"workload": name, "ndet": ndet, "ms_per_call": round(ms, 4), "contraction_ms": round(gemm_ms, 4),
+           "contraction_bf16_flops": bf16, "contraction_fp64_flops": fp64,
+           "roofline": {"bound": "tensor", "achieved": round(bf16 / (gemm_ms * 1e-3) / 1e12, 4), "peak": peak,
+                        "unit": "TFLOP/s", "frac": round(bf16 / (gemm_ms * 1e-3) / 1e12 / peak, 4),
+                        "traffic": profile_traffic("k_oz_gemm_density_%s" % name)[0],
+                        "kernel": "k_oz_gemm<1> (tcgen05, FP64-accurate Gram products of lifted vectors, ket = bra)",
+                        "peak_source": peak_src},
+           "fp64_equivalent_tflops": round(fp64 / (gemm_ms * 1e-3) / 1e12, 3),
+           "output_bytes": 8 * (2 * n * n + 3 * n ** 4), "l2": "flushed between calls", "checks": checks}
+    L.iscsi_finalize()
+    if with_cpu:
+        # the oracle's element-wise route (every element a pass over all determinants)
+        # on a sample of elements, scaled to the 3 n^4 + 2 n^2 elements
+        from oracle import Oracle, max_threads
+        o = Oracle(wl["n"], na, nb, wl["kmax"], tau, h1, eri)
+        cc = unit_vector(ndet, 23)
+        rng = np.random.default_rng(1)
+        m = 2 * max_threads()
+        spec = np.column_stack([rng.integers(0, 3, m)] + [rng.integers(0, n, m) for _ in range(4)])
+        t0 = time.time()
+        vals = o.density_elems(cc, None, spec)
+        dt = time.time() - t0
+        full_s = dt / m * (3 * n ** 4 + 2 * n * n)
+        out["cpu_baseline"] = {"value": round(full_s * 1e3, 1), "unit": "ms per density call (extrapolated)",
+                               "cores": max_threads(), "kind": "oracle",
+                               "sample": "%d random d2 elements by the oracle's element-wise route (%.1f s), "
+                                         "scaled to all %d elements" % (m, dt, 3 * n ** 4 + 2 * n * n)}
+        out["sample_check"] = {"elements": m, "max_abs_diff": float(np.abs(
+            d2.cpu().numpy()[spec[:, 0], spec[:, 1], spec[:, 2], spec[:, 3], spec[:, 4]] - vals).max())}
+    return out
+
+
 def run_sweep(steps=5, warmup=3):
     """The box-size sweep: CISD and CISDT, 2 alpha + 2 beta electrons in 50, 100,
     150 and 200 orbitals (integrals decaying with the box), tau = 1e-14, FP64.
@@ -668,6 +749,8 @@ def main():
                     help="library option autotune (kernel routing timed at the first sigma)")
     ap.add_argument("--tc-cluster", type=int, default=1, choices=[0, 1, 2],
                     help="library option tc_cluster (0 never, 1 tuned, 2 always two-CTA clusters)")
+    ap.add_argument("--density-workload", default="fci_n60", choices=sorted(WORKLOADS) + ["none"],
+                    help="one- and two-body density matrices on this workload (none: skip)")
     ap.add_argument("--sweep", action="store_true",
                     help="add the CISD/CISDT box-size sweep (n = 50..200) with its fitted scaling exponents")
     ap.add_argument("--updates", type=float, default=None, help=argparse.SUPPRESS)
@@ -707,6 +790,8 @@ def main():
             line["batching"] = b
     if rank == 0 and ws == 1 and args.sweep:
         line["box_sweep"] = run_sweep()
+    if rank == 0 and ws == 1 and args.density_workload != "none":
+        line["density_matrices"] = run_density(args.density_workload, with_cpu=not args.no_cpu_baseline)
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
             tau = args.tau if args.tau is not None else wl["tau"]

@@ -145,6 +145,43 @@ ISCSI_API iscsi_status iscsi_sigma_noalloc(const void* c, void* sigma);
 ISCSI_API iscsi_status iscsi_sigma_host(const double* c, double* sigma, int nvec);
 
 /*
+ * One- and two-body (transition) density matrices of Eqs. d1 and d2 (Sec.
+ * "Density matrices"), spin-resolved, for the current context's space:
+ *   d1[s][p][q]       = <bra| a+_{p s} a_{q s} |ket>,  s = 0 alpha, 1 beta;
+ *   d2[b][p][q][r][t] = <bra| a+_{p s} a+_{r u} a_{t u} a_{q s} |ket>,
+ *                       (s, u) = (alpha, alpha), (alpha, beta), (beta, beta)
+ *                       for b = 0, 1, 2; flat index ((p n + q) n + r) n + t
+ *                       inside each block.
+ * The spin-summed matrices of Eqs. d1 and d2 are d1[0] + d1[1] and
+ * d2[0] + d2[2] + d2[1] + d2[1] with (p,q) and (r,t) exchanged; with these
+ * blocks <bra|H|ket> (tau = 0) = sum h_pq (d1[0] + d1[1])_pq
+ * + 1/2 sum g_pqrt (d2[0] + d2[2])_pqrt + sum g_pqrt d2[1]_pqrt.
+ *   bra  device, FP64 [ndet].
+ *   ket  device, FP64 [ndet], or NULL (or bra) for the state densities of
+ *        bra; then the symmetric half of the contraction is computed.
+ *   d1   device, FP64 [2][n][n], or NULL;  d2: device, FP64 [3][n^4], or NULL
+ *        (at least one of them); overwritten.
+ * The two-body blocks are FP64-accurate products of lifted vectors on the
+ * tensor cores (exact bf16 slices); the first call with d2 builds the string
+ * tables and work lists and synchronises; later calls are asynchronous on the
+ * library stream.  Workspace: about 14 bytes per element of the lifted
+ * vectors (n^2 rows x the hole-pair count for the alpha-beta block) plus the
+ * pair-indexed results (n^4 doubles); a ket different from bra adds its own
+ * slices.  A bounded device wait that runs out is reported by the next
+ * synchronising call.
+ * Errors: ISCSI_E_NOINIT, ISCSI_E_ARG (bra NULL, both outputs NULL), ISCSI_E_NOMEM,
+ * ISCSI_E_CUDA.
+ */
+ISCSI_API iscsi_status iscsi_density(const void* bra, const void* ket, void* d1, void* d2);
+
+/*
+ * Same as iscsi_density with HOST buffers (bra, ket [ndet]; d1 [2 n n]; d2
+ * [3 n^4]): copies in, computes, copies out, synchronises and reports a
+ * device wait that ran out (ISCSI_E_WAIT).
+ */
+ISCSI_API iscsi_status iscsi_density_host(const double* bra, const double* ket, double* d1, double* d2);
+
+/*
  * Lowest nroots eigenpairs of H_tau by a Davidson iteration on the device
  * (diagonal preconditioner, FP64 orthonormalisation, Rayleigh-Ritz and
  * residuals).  Converged when every root has residual 2-norm <= tol and its

@@ -51,6 +51,8 @@ def load(build_if_missing=True):
         "iscsi_sigma_host": (c_int, [vp, vp, c_int]),
         "iscsi_sigma_noalloc": (c_int, [vp, vp]),
         "iscsi_davidson": (c_int, [c_int, c_d, vp, vp]),
+        "iscsi_density": (c_int, [vp, vp, vp, vp]),
+        "iscsi_density_host": (c_int, [vp, vp, vp, vp]),
         "iscsi_ndet": (c_ll, []),
         "iscsi_nstrings": (c_ll, [c_int]),
         "iscsi_get_strings": (c_int, [c_int, vp, vp]),
@@ -165,6 +167,26 @@ def iscsi_sigma_host(c, sigma, nvec=1):
         raise ValueError("sigma must be a C-contiguous float64 numpy array")
     cc, cp = _host_f64(c)
     return _check(load().iscsi_sigma_host(cp, sigma.ctypes.data_as(ctypes.c_void_p), int(nvec)))
+
+
+def iscsi_density(bra, ket, d1, d2):
+    """Spin-resolved density matrices of Eqs. d1, d2 on the device.
+    bra, ket: device FP64 [ndet] (ket None: ket = bra); d1: device FP64
+    [2, n, n] or None; d2: device FP64 [3, n, n, n, n] or None."""
+    return _check(load().iscsi_density(_dev(bra), _dev(ket), _dev(d1), _dev(d2)))
+
+
+def iscsi_density_host(bra, ket, d1, d2):
+    """Host form: bra, ket numpy float64 [ndet] (ket may be None); d1 / d2
+    C-contiguous float64 numpy outputs of 2 n^2 / 3 n^4 elements, or None."""
+    for o in (d1, d2):
+        if o is not None and not (isinstance(o, np.ndarray) and o.dtype == np.float64 and o.flags.c_contiguous):
+            raise ValueError("outputs must be C-contiguous float64 numpy arrays")
+    bb, bp = _host_f64(bra)
+    kk, kp = _host_f64(ket) if ket is not None else (None, None)
+    p1 = d1.ctypes.data_as(ctypes.c_void_p) if d1 is not None else None
+    p2 = d2.ctypes.data_as(ctypes.c_void_p) if d2 is not None else None
+    return _check(load().iscsi_density_host(bp, kp, p1, p2))
 
 
 def iscsi_davidson(nroots, tol, vecs=None):

@@ -106,6 +106,41 @@ iscsi_status iscsi_sigma_host(const double* c, double* sigma, int nvec) {
   return tc_check(*ctx);
 }
 
+iscsi_status iscsi_density(const void* bra, const void* ket, void* d1, void* d2) {
+  NEED_CTX(ctx);
+  if (!bra || (!d1 && !d2)) {
+    set_error("iscsi_density: bra is NULL or both outputs are NULL");
+    return ISCSI_E_ARG;
+  }
+  return density_run(*ctx, static_cast<const double*>(bra), static_cast<const double*>(ket),
+                     static_cast<double*>(d1), static_cast<double*>(d2));
+}
+
+iscsi_status iscsi_density_host(const double* bra, const double* ket, double* d1, double* d2) {
+  NEED_CTX(ctx);
+  if (!bra || (!d1 && !d2)) {
+    set_error("iscsi_density_host: bra is NULL or both outputs are NULL");
+    return ISCSI_E_ARG;
+  }
+  cudaStream_t st = stream();
+  const size_t vb = sizeof(double) * (size_t)ctx->ndet;
+  const size_t n2 = (size_t)ctx->n * ctx->n, b1 = sizeof(double) * 2 * n2, b2 = sizeof(double) * 3 * n2 * n2;
+  DevBuf db, dk, o1, o2;
+  ISCSI_TRY(db.alloc(vb));
+  ISCSI_CUDA(cudaMemcpyAsync(db.p, bra, vb, cudaMemcpyHostToDevice, st));
+  if (ket && ket != bra) {
+    ISCSI_TRY(dk.alloc(vb));
+    ISCSI_CUDA(cudaMemcpyAsync(dk.p, ket, vb, cudaMemcpyHostToDevice, st));
+  }
+  if (d1) ISCSI_TRY(o1.alloc(b1));
+  if (d2) ISCSI_TRY(o2.alloc(b2));
+  ISCSI_TRY(density_run(*ctx, db.as<double>(), dk.p ? dk.as<double>() : nullptr, o1.as<double>(), o2.as<double>()));
+  if (d1) ISCSI_CUDA(cudaMemcpyAsync(d1, o1.p, b1, cudaMemcpyDeviceToHost, st));
+  if (d2) ISCSI_CUDA(cudaMemcpyAsync(d2, o2.p, b2, cudaMemcpyDeviceToHost, st));
+  ISCSI_CUDA(cudaStreamSynchronize(st));
+  return tc_check(*ctx);
+}
+
 iscsi_status iscsi_davidson(int nroots, double tol, double* energies, void* vecs) {
   NEED_CTX(ctx);
   if (nroots < 1 || nroots > ctx->ndet || !(tol > 0) || !energies) {
@@ -305,12 +340,20 @@ iscsi_status iscsi_stats(char* json, int len) {
   out += "]";
   // whether the opposite- and same-spin tensor-core products run as one launch
   {
-    char v[256];
+    char v[512];
     auto both = [&](int prec) {
       return ctx->have_ab && ab_on_tc(*ctx, prec) && (prec == 64 ? samespin_tc_active(*ctx) : samespin_tc32_active(*ctx));
     };
     std::snprintf(v, sizeof(v), ", \"samespin_tc_bf16_flops\": %.17g, \"both_tc_fp64\": %d, \"both_tc_fp32\": %d",
                   ctx_gemm_flops(*ctx, 3), both(64) ? 1 : 0, both(32) ? 1 : 0);
+    out += v;
+    // the density matrices' contraction (after the first iscsi_density call with d2):
+    // bf16 MMA flops and 2 M N K of one launch, ket = bra and general
+    std::snprintf(v, sizeof(v),
+                  ", \"density_bf16_flops\": [%.17g, %.17g], \"density_fp64_flops\": [%.17g, %.17g], "
+                  "\"density_gemm_ms\": %.6g",
+                  density_flops(*ctx, 1, 0), density_flops(*ctx, 0, 0), density_flops(*ctx, 1, 1),
+                  density_flops(*ctx, 0, 1), density_gemm_ms(*ctx));
     out += v;
   }
   // the autotuner's routing per precision and its trials (ab_tc, ss_min or -1 =

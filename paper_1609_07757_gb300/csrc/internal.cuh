@@ -132,6 +132,13 @@ struct ProblemList {
 };
 constexpr int kThinN = 16;
 
+// one bf16 slice array [OZ_S][rows][ld] as TMA sees it
+struct SliceArray {
+  const __nv_bfloat16* base;
+  int ld;
+  long long rows, slice;
+};
+
 // a tensor-core work list (problems + segments) kept on the device
 struct OzJob {
   std::vector<OzProblem> probs;
@@ -145,6 +152,8 @@ struct OzJob {
   int cl = 1;             // CTAs per cluster of its launches (2: A tiles multicast to CTA pairs)
   long long src_ver[2] = {-1, -1};  // a combined job: versions of the jobs it was built from
 };
+
+struct DensityPlan;     // density.cu
 
 struct ColClass {       // column level class c = level(X) + level(Y)
   int level = 0;
@@ -233,6 +242,8 @@ struct Context {
   bool capturing = false;  // a CUDA graph capture of a Davidson iteration is in progress
   int last_davidson_graph = 0;  // 1: the last Davidson run replayed captured iterations
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // density matrices (density.cu): string tables, workspaces and work lists, built at first use
+  DensityPlan* dm = nullptr;
   ~Context();
 };
 
@@ -294,6 +305,20 @@ const OzJob* both_tc_job(Context& ctx, int prec);  // that combined job (built w
 int launch_tc_problems(const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
                        void* const* tbases, int tiles, int prec, int cl, int* err, cudaStream_t st);
 int tc_check(Context& ctx);
+// jobs assembled elsewhere: append a segment (K from column 0 of both arrays),
+// number the tiles and upload (cl CTAs per cluster), launch k_oz_gemm
+int oz_job_add_seg(OzJob& job, const SliceArray& A, int a_row0, const int* a_exp, const SliceArray& B, int b_row0,
+                   const int* b_exp, int K, int nrows_b);
+int oz_job_upload(OzJob& job, int cl, cudaStream_t st);
+int oz_job_launch(Context& ctx, const OzJob& job, cudaStream_t st);
+
+// density.cu: one- and two-body density matrices (Eqs. d1, d2)
+int density_run(Context& ctx, const double* bra, const double* ket, double* d1, double* d2);
+void density_release(Context& ctx);
+// flops of one launch of the density contraction (sym: ket = bra); which 0:
+// bf16 MMA flops, 1: 2 M N K of the computed regions; 0 before the first call
+double density_flops(const Context& ctx, int sym, int which);
+double density_gemm_ms(Context& ctx);  // duration of the last contraction launch (synchronises), 0 if none
 
 // allocation-free single-vector FP64 sigma on a static device array (sigma.cu)
 int sigma_noalloc_run(Context& ctx, const double* c, double* sigma);

@@ -56,6 +56,7 @@ void DevBuf::release() {
 }
 
 Context::~Context() {
+  density_release(*this);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
 }
@@ -689,13 +690,16 @@ int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h
     ISCSI_CUDA(cudaStreamSynchronize(st));
   }
 
-  // --- hole strings and lift / dec tables (opposite-spin part)
+  // --- hole strings and lift / dec tables of each spin with electrons (the
+  // opposite-spin sigma part and the density matrices use them; they do not
+  // depend on the integrals)
   ctx.have_ab = (na > 0 && nb > 0 && eri != nullptr);
   std::vector<int> hole_lcount[2];
-  if (ctx.have_ab) {
+  {
     DevBuf hole_orbs[2], hole_level[2], hole_pos[2];
     for (int s = 0; s < 2; ++s) {
       SpinSpace& S = ctx.sp[s];
+      if (S.ne == 0) continue;
       ISCSI_TRY(enumerate_strings(n, S.ne - 1, S.ne, hole_orbs[s], hole_level[s], hole_pos[s], hole_lcount[s], st));
       S.nhole = (int)binom_ll(n, S.ne - 1);
       if (S.nhole >= (1 << 22)) {
@@ -719,7 +723,8 @@ int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h
       ISCSI_CUDA(cudaGetLastError());
       ISCSI_CUDA(cudaStreamSynchronize(st));
     }
-
+  }
+  if (na > 0 && nb > 0) {
     // pair ordering pi(p, r): sorted by (level(p) + level(r), p, r)
     ctx.npairs = n * n;
     std::vector<int> pair_of(ctx.npairs), pair_index(ctx.npairs);
@@ -782,7 +787,8 @@ int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h
       if (cc.ncol > 0 && rows > 0) ctx.ct_elems += (size_t)rows * cc.ncol;
       ctx.cls.push_back(cc);
     }
-
+  }
+  if (ctx.have_ab) {
     // opposite-spin updates per surviving unit, by (alpha pair kind, beta pair kind)
     double w[6][6];
     const int qv_of[6] = {0, 0, 1, 0, 1, 1}, pv_of[6] = {0, 0, 0, 1, 1, 1};

@@ -188,13 +188,6 @@ static int tc_prepare_g(Context& ctx) {
                       ctx.oz_gs.as<__nv_bfloat16>(), st);
 }
 
-// one slice array as TMA sees it
-struct SliceArray {
-  const __nv_bfloat16* base;
-  int ld;
-  long long rows, slice;
-};
-
 // segment of a job: block (a_row0, a_k0) of A times block (b_row0, b_k0) of B
 static int add_seg(OzJob& job, const SliceArray& A, int a_row0, int a_k0, const int* a_exp, const SliceArray& B,
                    int b_row0, int b_k0, const int* b_exp, int K, int nrows_b, int nslice = OZ_S) {
@@ -872,6 +865,25 @@ int launch_tc_problems(const OzProblem* probs, int nprobs, const OzSeg* segs, co
   } else {
     return launch_t3(cl, tiles, probs, nprobs, segs, maps, nullptr, reinterpret_cast<float* const*>(tbases), err, st);
   }
+}
+
+// tensor-core jobs built by other parts of the library (density.cu): segments
+// whose K starts at column 0 of both slice arrays
+int oz_job_add_seg(OzJob& job, const SliceArray& A, int a_row0, const int* a_exp, const SliceArray& B, int b_row0,
+                   const int* b_exp, int K, int nrows_b) {
+  return add_seg(job, A, a_row0, 0, a_exp, B, b_row0, 0, b_exp, K, nrows_b);
+}
+
+int oz_job_upload(OzJob& job, int cl, cudaStream_t st) {
+  job.cl = cl;
+  job.tiles = add_tiles(job.probs, cl);
+  return upload_job(job, st);
+}
+
+int oz_job_launch(Context& ctx, const OzJob& job, cudaStream_t st) {
+  ISCSI_TRY(tc_attr());
+  ISCSI_TRY(tc_err_buf(ctx));
+  return launch_job(ctx, job, nullptr, st);
 }
 
 // status of the bounded waits of the tensor-core kernels (synchronises)
