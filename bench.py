@@ -238,10 +238,13 @@ def profile_traffic(kernel_key):
     ent = d.get(kernel_key)
     if not ent:
         return None, None
-    src = os.path.join(ROOT, ent["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] if os.path.exists(src) else None
-    if h != ent.get("source_sha256_16"):
-        return None, ent
+    # every source the launch depends on (the kernel, and the code that builds
+    # its work list) must be unchanged since the capture
+    for src_rel, want in ent.get("sources", {ent.get("source"): ent.get("source_sha256_16")}).items():
+        src = os.path.join(ROOT, src_rel or "")
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] if src_rel and os.path.exists(src) else None
+        if h != want:
+            return None, ent
     return float(ent["dram_bytes_per_launch"]), ent
 
 
@@ -751,6 +754,8 @@ def main():
                     help="library option tc_cluster (0 never, 1 tuned, 2 always two-CTA clusters)")
     ap.add_argument("--density-workload", default="fci_n60", choices=sorted(WORKLOADS) + ["none"],
                     help="one- and two-body density matrices on this workload (none: skip)")
+    ap.add_argument("--density-only", action="store_true",
+                    help="run only the density-matrix leg and print its object")
     ap.add_argument("--sweep", action="store_true",
                     help="add the CISD/CISDT box-size sweep (n = 50..200) with its fitted scaling exponents")
     ap.add_argument("--updates", type=float, default=None, help=argparse.SUPPRESS)
@@ -778,6 +783,13 @@ def main():
         line = run_reference(args, wl, ws, rank)
         if rank == 0 and line:
             print(json.dumps(line))
+        return
+    if args.density_only:
+        # the density-matrix leg alone (profiling its contraction)
+        if rank == 0:
+            print(json.dumps({"density_matrices": run_density(args.density_workload, steps=args.steps,
+                                                              warmup=args.warmup,
+                                                              with_cpu=not args.no_cpu_baseline)}))
         return
     line = run_ours(args, wl, ws, rank, local)
     if rank == 0 and ws == 1 and args.mixed_workload != "none":

@@ -226,6 +226,19 @@ static int plan_build(Context& ctx) {
   }
   if (ctx.na >= 2) ISCSI_TRY(build_samespin(ctx, P, 0, P.blk[1]));
   if (ctx.nb >= 2) ISCSI_TRY(build_samespin(ctx, P, 1, P.blk[2]));
+  // consecutive classes that reach the same rows are one part (their columns
+  // are adjacent in the column lists): one longer K instead of several segments
+  for (int b = 0; b < 3; ++b) {
+    std::vector<DmPart> merged;
+    for (const DmPart& pt : P.blk[b].parts) {
+      if (!merged.empty() && merged.back().rows == pt.rows &&
+          merged.back().col_start + merged.back().ncol == pt.col_start)
+        merged.back().ncol += pt.ncol;
+      else
+        merged.push_back(pt);
+    }
+    P.blk[b].parts = merged;
+  }
   // workspace layout
   size_t sl = 0, q = 0, ex = 0;
   for (int b = 0; b < 3; ++b) {
@@ -305,43 +318,55 @@ __device__ __forceinline__ double dm_value(const DmGather& g, int col, int row, 
   return neg ? -x : x;
 }
 
-// row exponent e with max |L[row][:]| 2^-e < 1 (0 for an all-zero row), one block per row
-__global__ void __launch_bounds__(256) k_dm_row_exp(DmGather g, int col_start, int ncol, const double* __restrict__ c,
-                                                    int* __restrict__ e) {
+// One block per row of L (rows_pad rows, ld columns): gathers the row once
+// (held in registers, kDmRowRegs values per thread, or re-gathered beyond
+// that), takes the row exponent e with max |L[row][:]| 2^-e < 1 (0 for an
+// all-zero row, and for the padding rows) and writes the row's slices
+// out[s][row][k], zero padded.
+constexpr int kDmRowRegs = 16;
+__global__ void __launch_bounds__(256) k_dm_lift_slice(DmGather g, int col_start, int ncol, int rows, int ld,
+                                                       int rows_pad, const double* __restrict__ c,
+                                                       int* __restrict__ e, __nv_bfloat16* __restrict__ out) {
   const int r = blockIdx.x;
+  const long long total = (long long)rows_pad * ld;
+  double v[kDmRowRegs];
   int m = 0;
-  for (int k = threadIdx.x; k < ncol; k += blockDim.x) {
-    double v = dm_value(g, col_start + k, r, c);
-    m = max(m, oz_exp_field(v));
+#pragma unroll
+  for (int i = 0; i < kDmRowRegs; ++i) {
+    const int k = threadIdx.x + i * blockDim.x;
+    v[i] = (r < rows && k < ncol) ? dm_value(g, col_start + k, r, c) : 0.0;
+    m = max(m, oz_exp_field(v[i]));
   }
+  for (int k = threadIdx.x + kDmRowRegs * blockDim.x; k < ncol; k += blockDim.x)
+    if (r < rows) m = max(m, oz_exp_field(dm_value(g, col_start + k, r, c)));
   m = __reduce_max_sync(0xffffffffu, m);
   __shared__ int sm[8];
+  __shared__ int ex_s;
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
     int x = 0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) x = max(x, sm[i]);
-    e[r] = x > 0 ? x - 1022 : 0;
+    ex_s = x > 0 ? x - 1022 : 0;
+    if (r < rows) e[r] = ex_s;
   }
-}
-
-// slices out[s][row][k] of L (rows_pad x ld, zero padded)
-__global__ void __launch_bounds__(256) k_dm_slice(DmGather g, int col_start, int ncol, int rows, int ld, int rows_pad,
-                                                  const double* __restrict__ c, const int* __restrict__ e,
-                                                  __nv_bfloat16* __restrict__ out) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long total = (long long)rows_pad * ld;
-  if (t >= total) return;
-  const int r = (int)(t / ld), k = (int)(t - (long long)r * ld);
-  double x = 0.0;
-  int ex = 0;
-  if (r < rows && k < ncol) {
-    x = dm_value(g, col_start + k, r, c);
-    ex = e[r];
-  }
+  __syncthreads();
+  const int ex = ex_s;
+  __nv_bfloat16* row = out + (long long)r * ld;
   int a[OZ_S];
-  oz_digits(x, ex, a);
-  oz_store_digits(a, out + t, total);
+#pragma unroll
+  for (int i = 0; i < kDmRowRegs; ++i) {
+    const int k = threadIdx.x + i * blockDim.x;
+    if (k < ld) {
+      oz_digits(v[i], ex, a);
+      oz_store_digits(a, row + k, total);
+    }
+  }
+  for (int k = threadIdx.x + kDmRowRegs * blockDim.x; k < ld; k += blockDim.x) {
+    const double x = (r < rows && k < ncol) ? dm_value(g, col_start + k, r, c) : 0.0;
+    oz_digits(x, ex, a);
+    oz_store_digits(a, row + k, total);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -491,10 +516,8 @@ static int cut_operands(Context& ctx, const double* v, __nv_bfloat16* sl, int* e
     for (size_t i = 0; i < B.parts.size(); ++i) {
       const DmPart& pt = B.parts[i];
       int* e = ex + B.exp_off + i * B.R128;
-      k_dm_row_exp<<<pt.rows, 256, 0, st>>>(g, pt.col_start, pt.ncol, v, e); ISCSI_COUNT_LAUNCH();
-      long long tot = (long long)pt.rows_pad * pt.ld;
-      k_dm_slice<<<launch_blocks(tot, 256), 256, 0, st>>>(g, pt.col_start, pt.ncol, pt.rows, pt.ld, pt.rows_pad, v,
-                                                          e, sl + pt.sl_off); ISCSI_COUNT_LAUNCH();
+      k_dm_lift_slice<<<pt.rows_pad, 256, 0, st>>>(g, pt.col_start, pt.ncol, pt.rows, pt.ld, pt.rows_pad, v, e,
+                                                   sl + pt.sl_off); ISCSI_COUNT_LAUNCH();
     }
   }
   ISCSI_CUDA(cudaGetLastError());
