@@ -623,6 +623,65 @@ def run_density(name, steps=10, warmup=3, with_cpu=True, tau=None):
     return out
 
 
+def dipole_like(n):
+    """A position-like one-body coupling (orbitals on a line), for the propagation leg."""
+    import numpy as np
+    v = np.diag(np.arange(n) - (n - 1) / 2.0) / n
+    return v + 0.05 * (np.eye(n, k=1) + np.eye(n, k=-1))
+
+
+def run_propagation(name, nsteps=4, dt=0.02, krylov=12, with_cpu=True):
+    """Real-time propagation under H(t) = H_tau + f(t) V (Eq. ham with h(t) =
+    h + f(t) v, v dipole-like, f(t) = 0.05 sin(0.8 t)) by the short-iterative
+    Lanczos propagator: ms per step (one warm-up step first), the sigma work
+    per step, norm and energy drift, the Krylov error indicator."""
+    import numpy as np
+    import torch
+
+    from paper_1609_07757_gb300 import _lib as L
+    from paper_1609_07757_gb300.synthetic import make_integrals, unit_vector
+
+    wl = WORKLOADS[name]
+    n = wl["n"]
+    h1, eri = make_integrals(n, wl["seed"], ell=wl["ell"], nchol=wl["nchol"], box=wl["box"])
+    stream = torch.cuda.current_stream()
+    L.iscsi_set_stream(stream)
+    L.iscsi_init(n, wl["na"], wl["nb"], wl["kmax"], dipole_like(n), None, wl["tau"])
+    hv = L.iscsi_ctx_current()
+    L.iscsi_init(n, wl["na"], wl["nb"], wl["kmax"], h1, eri, wl["tau"])
+    ndet, updates = L.iscsi_ndet(), L.iscsi_updates_per_sigma()
+    c = torch.zeros((2, ndet), dtype=torch.float64, device="cuda")
+    c[0] = torch.tensor(unit_vector(ndet, 29), dtype=torch.float64, device="cuda")
+    field = 0.05 * np.sin(0.8 * dt * (np.arange(nsteps + 1) + 0.5))
+    L.iscsi_propagate(c, 1, dt, field[:1], hv, krylov)  # warm-up step (work lists, routing)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    diag = L.iscsi_propagate(c, nsteps, dt, field[1:], hv, krylov)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / nsteps
+    norm = float(torch.linalg.norm(c))
+    L.iscsi_finalize()
+    sig = 2 * krylov  # sigma applications of H per step (complex vectors: nvec = 2)
+    out = {"workload": name, "ndet": ndet, "steps": nsteps, "dt": dt, "krylov": krylov, "ms_per_step": round(ms, 3),
+           "sigma_vectors_per_step": {"H": sig, "V": sig},
+           "effective_gupdates_per_s": round(sig * updates / (ms * 1e-3) / 1e9, 1),
+           "norm_drift": abs(norm - 1.0), "max_error_indicator": float(diag[:, 0].max()),
+           "energy_per_step": [round(float(x), 10) for x in diag[:, 1]],
+           "field": "0.05 sin(0.8 t), position-like one-body coupling"}
+    if with_cpu:
+        # the oracle's row-wise sigma on a bounded sample, scaled to the sigma work of one step
+        o, nrow, times, cores = cpu_baseline(wl, wl["tau"], target_s=8.0, steps=1)
+        sigma_s = times[0] * o.ndet / nrow
+        out["cpu_baseline"] = {"value": round(sig * sigma_s * 1e3, 1), "unit": "ms per step (extrapolated)",
+                               "cores": cores, "kind": "oracle",
+                               "sample": "row-wise oracle sigma on %d of %d rows (%.1f s), scaled to %d sigma "
+                                         "vectors of H per step (the V products not counted)" % (
+                                             nrow, o.ndet, times[0], sig)}
+    return out
+
+
 def run_sweep(steps=5, warmup=3):
     """The box-size sweep: CISD and CISDT, 2 alpha + 2 beta electrons in 50, 100,
     150 and 200 orbitals (integrals decaying with the box), tau = 1e-14, FP64.
@@ -754,6 +813,8 @@ def main():
                     help="library option tc_cluster (0 never, 1 tuned, 2 always two-CTA clusters)")
     ap.add_argument("--density-workload", default="fci_n60", choices=sorted(WORKLOADS) + ["none"],
                     help="one- and two-body density matrices on this workload (none: skip)")
+    ap.add_argument("--propagation-workload", default="fci_n60", choices=sorted(WORKLOADS) + ["none"],
+                    help="real-time propagation under a field on this workload (none: skip)")
     ap.add_argument("--density-only", action="store_true",
                     help="run only the density-matrix leg and print its object")
     ap.add_argument("--sweep", action="store_true",
@@ -804,6 +865,8 @@ def main():
         line["box_sweep"] = run_sweep()
     if rank == 0 and ws == 1 and args.density_workload != "none":
         line["density_matrices"] = run_density(args.density_workload, with_cpu=not args.no_cpu_baseline)
+    if rank == 0 and ws == 1 and args.propagation_workload != "none":
+        line["propagation"] = run_propagation(args.propagation_workload, with_cpu=not args.no_cpu_baseline)
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
             tau = args.tau if args.tau is not None else wl["tau"]

@@ -182,6 +182,38 @@ ISCSI_API iscsi_status iscsi_density(const void* bra, const void* ket, void* d1,
 ISCSI_API iscsi_status iscsi_density_host(const double* bra, const double* ket, double* d1, double* d2);
 
 /*
+ * Time propagation of a CI vector under H(t) = H_tau + f(t) V (Eq. ham with a
+ * time-dependent one-body part h(t) = h + f(t) v; the two-body part constant)
+ * by the short-iterative Lanczos propagator (the paper's SIAL): per step of
+ * length dt, with the field held at its sample f_k, a Krylov space of krylov
+ * vectors of H_tau + f_k V from the current vector, the exponential of its
+ * tridiagonal matrix, and the combination.  The basis is kept orthogonal by
+ * two Gram-Schmidt passes; the small eigenproblem runs on the host.
+ *   c         device, FP64, updated in place: real time [2][ndet] (real part,
+ *             then imaginary part), c <- exp(-i H_k dt) c per step; imaginary
+ *             time [ndet], c <- exp(-H_k dt) c / |exp(-H_k dt) c| (the paper's
+ *             ground-state runs).
+ *   nsteps    >= 1;  dt: finite, != 0 (> 0 in imaginary time; < 0 propagates
+ *             backwards in real time).
+ *   field     host [nsteps] samples f_k (for a smooth field, its value at the
+ *             step's midpoint), or NULL for f = 0.
+ *   coupling  handle of a context created with iscsi_init(norb, nalpha, nbeta,
+ *             max_excitation, v, NULL, tau) on the same space (its sigma is V c),
+ *             or 0 when field is NULL.
+ *   krylov    Krylov dimension, 2..64 (12 is typical).
+ *   imaginary 0: real time, 1: imaginary time.
+ *   diag      host [2 * nsteps] or NULL: per step the error indicator
+ *             |c| beta_m |e_m^T exp(.) e_1| of the Krylov approximation and
+ *             <c|H_k|c> / <c|c> at the step's start.
+ * Sigma runs in the "precision" option's arithmetic.  Synchronises (twice per
+ * step).  Errors: ISCSI_E_NOINIT, ISCSI_E_ARG (arguments, a coupling on another
+ * space, a field without a coupling), ISCSI_E_NAN, ISCSI_E_NOMEM, ISCSI_E_CUDA,
+ * ISCSI_E_WAIT.
+ */
+ISCSI_API iscsi_status iscsi_propagate(void* c, int nsteps, double dt, const double* field, int coupling, int krylov,
+                                       int imaginary, double* diag);
+
+/*
  * Lowest nroots eigenpairs of H_tau by a Davidson iteration on the device
  * (diagonal preconditioner, FP64 orthonormalisation, Rayleigh-Ritz and
  * residuals).  Converged when every root has residual 2-norm <= tol and its

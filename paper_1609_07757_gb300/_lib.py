@@ -52,6 +52,7 @@ def load(build_if_missing=True):
         "iscsi_sigma_noalloc": (c_int, [vp, vp]),
         "iscsi_davidson": (c_int, [c_int, c_d, vp, vp]),
         "iscsi_density": (c_int, [vp, vp, vp, vp]),
+        "iscsi_propagate": (c_int, [vp, c_int, c_d, vp, c_int, c_int, c_int, vp]),
         "iscsi_density_host": (c_int, [vp, vp, vp, vp]),
         "iscsi_ndet": (c_ll, []),
         "iscsi_nstrings": (c_ll, [c_int]),
@@ -187,6 +188,21 @@ def iscsi_density_host(bra, ket, d1, d2):
     p1 = d1.ctypes.data_as(ctypes.c_void_p) if d1 is not None else None
     p2 = d2.ctypes.data_as(ctypes.c_void_p) if d2 is not None else None
     return _check(load().iscsi_density_host(bp, kp, p1, p2))
+
+
+def iscsi_propagate(c, nsteps, dt, field=None, coupling=0, krylov=12, imaginary=False):
+    """Propagate c (device FP64: [2, ndet] real time, [ndet] imaginary time) in
+    place; returns the per-step diagnostics [nsteps, 2] (error indicator, energy)."""
+    diag = np.zeros((nsteps, 2))
+    fp = None
+    if field is not None:
+        fa = np.ascontiguousarray(field, dtype=np.float64)
+        if fa.shape != (nsteps,):
+            raise ValueError("field must have nsteps samples")
+        fp = fa.ctypes.data_as(ctypes.c_void_p)
+    _check(load().iscsi_propagate(_dev(c), int(nsteps), float(dt), fp, int(coupling), int(krylov),
+                                  1 if imaginary else 0, diag.ctypes.data_as(ctypes.c_void_p)))
+    return diag
 
 
 def iscsi_davidson(nroots, tol, vecs=None):

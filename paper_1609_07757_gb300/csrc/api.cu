@@ -141,6 +141,42 @@ iscsi_status iscsi_density_host(const double* bra, const double* ket, double* d1
   return tc_check(*ctx);
 }
 
+iscsi_status iscsi_propagate(void* c, int nsteps, double dt, const double* field, int coupling, int krylov,
+                             int imaginary, double* diag) {
+  NEED_CTX(ctx);
+  if (!c || nsteps < 1 || !std::isfinite(dt) || dt == 0.0 || krylov < 2 || krylov > kPrMaxKrylov ||
+      (imaginary != 0 && imaginary != 1) || (imaginary && dt < 0.0)) {
+    set_error("iscsi_propagate: invalid argument (c != NULL, nsteps >= 1, finite dt != 0 (> 0 in imaginary "
+              "time), 2 <= krylov <= 64, imaginary 0 or 1)");
+    return ISCSI_E_ARG;
+  }
+  Context* cpl = nullptr;
+  if (coupling) {
+    auto it = g_ctx.find(coupling);
+    if (it == g_ctx.end() || it->second.get() == ctx) {
+      set_error("iscsi_propagate: unknown coupling handle, or the current context itself");
+      return ISCSI_E_ARG;
+    }
+    cpl = it->second.get();
+    if (cpl->n != ctx->n || cpl->na != ctx->na || cpl->nb != ctx->nb || cpl->kmax != ctx->kmax ||
+        cpl->ndet != ctx->ndet) {
+      set_error("iscsi_propagate: the coupling context is on a different determinant space");
+      return ISCSI_E_ARG;
+    }
+  }
+  if (field && !cpl) {
+    set_error("iscsi_propagate: a field needs a coupling context");
+    return ISCSI_E_ARG;
+  }
+  if (field)
+    for (int k = 0; k < nsteps; ++k)
+      if (!std::isfinite(field[k])) {
+        set_error("iscsi_propagate: non-finite field sample");
+        return ISCSI_E_ARG;
+      }
+  return propagate_run(*ctx, cpl, static_cast<double*>(c), nsteps, dt, field, krylov, imaginary, diag);
+}
+
 iscsi_status iscsi_davidson(int nroots, double tol, double* energies, void* vecs) {
   NEED_CTX(ctx);
   if (nroots < 1 || nroots > ctx->ndet || !(tol > 0) || !energies) {

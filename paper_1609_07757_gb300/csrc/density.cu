@@ -378,25 +378,42 @@ struct DmResult {
   int bnd[kDmMaxBnd];
 };
 
-// Q[x][y]; with sym, entries outside the computed part are read transposed
-__device__ __forceinline__ double dm_read(const DmResult& Q, int sym, int x, int y) {
-  if (x >= Q.R || y >= Q.R) return 0.0;
-  if (sym) {
-    int i = 0, j = 0;
-    while (i + 1 < Q.nreg && x >= Q.bnd[i + 1]) ++i;
-    while (j + 1 < Q.nreg && y >= Q.bnd[j + 1]) ++j;
-    bool done = i < j || (i == j && y >= Q.bnd[i] + ((x - Q.bnd[i]) / OZ_BM) * OZ_BM);
-    if (!done) {
-      int t = x;
-      x = y;
-      y = t;
-    }
+// whether entry (x, y) of a ket = bra result is computed by the contraction:
+// regions i < j, or the same region right of the 128-row block's first row
+__device__ __forceinline__ bool dm_computed(const DmResult& Q, int x, int y) {
+  int i = 0, j = 0;
+  while (i + 1 < Q.nreg && x >= Q.bnd[i + 1]) ++i;
+  while (j + 1 < Q.nreg && y >= Q.bnd[j + 1]) ++j;
+  return i < j || (i == j && y >= Q.bnd[i] + ((x - Q.bnd[i]) / OZ_BM) * OZ_BM);
+}
+
+// ket = bra: every entry that was not computed is copied from its transpose,
+// 32 x 32 tiles through shared memory (reads and writes coalesced).  Tiles
+// wholly above the diagonal are all computed (x < y lies in the computed part).
+__global__ void __launch_bounds__(256) k_dm_mirror(DmResult Q, double* __restrict__ q) {
+  __shared__ double tile[32][33];
+  const int x0 = blockIdx.y * 32, y0 = blockIdx.x * 32;  // destination rows x, columns y
+  if (x0 + 31 < y0) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int i = ty; i < 32; i += 8) {  // source rows y0 + i, columns x0 + tx
+    const int ys = y0 + i, xs = x0 + tx;
+    tile[i][tx] = (ys < Q.R && xs < Q.R) ? q[(long long)ys * Q.R + xs] : 0.0;
   }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {  // destination row x0 + i, column y0 + tx
+    const int x = x0 + i, y = y0 + tx;
+    if (x < Q.R && y < Q.R && !dm_computed(Q, x, y)) q[(long long)x * Q.R + y] = tile[tx][i];
+  }
+}
+
+// Q[x][y] (0 outside the rows any class reaches)
+__device__ __forceinline__ double dm_read(const DmResult& Q, int x, int y) {
+  if (x >= Q.R || y >= Q.R) return 0.0;
   return Q.q[(long long)x * Q.R + y];
 }
 
 struct DmExpand {
-  int n, na, nb, sym;
+  int n, na, nb;
   DmResult blk[3];        // in d2's block order: aa, ab, bb
   const int* pair_index;  // ab: (p, r) -> row
   const int* pp_row[2];   // aa / bb: {u < v} -> row
@@ -407,7 +424,7 @@ __device__ __forceinline__ double dm_samespin(const DmExpand& E, int b, int p, i
   if (p == r || q == t) return 0.0;
   const int* pr = E.pp_row[b == 0 ? 0 : 1];
   int x = pr[min(p, r) * E.n + max(p, r)], y = pr[min(q, t) * E.n + max(q, t)];
-  double v = dm_read(E.blk[b], E.sym, x, y);
+  double v = dm_read(E.blk[b], x, y);
   return ((p < r) == (q < t)) ? v : -v;
 }
 
@@ -421,7 +438,7 @@ __global__ void __launch_bounds__(256) k_dm_expand(DmExpand E, double* __restric
     double v = 0.0;
     if (b == 1) {
       if (E.na > 0 && E.nb > 0)
-        v = dm_read(E.blk[1], E.sym, E.pair_index[p * E.n + r], E.pair_index[q * E.n + t]);
+        v = dm_read(E.blk[1], E.pair_index[p * E.n + r], E.pair_index[q * E.n + t]);
     } else if ((b == 0 ? E.na : E.nb) >= 2) {
       v = dm_samespin(E, b, p, q, r, t);
     }
@@ -597,7 +614,6 @@ int density_run(Context& ctx, const double* bra, const double* ket, double* d1, 
   E.n = n;
   E.na = ctx.na;
   E.nb = ctx.nb;
-  E.sym = sym ? 1 : 0;
   E.pair_index = ctx.pair_index.as<int>();
   if (d2) {
     ISCSI_TRY(plan_build(ctx));
@@ -631,6 +647,13 @@ int density_run(Context& ctx, const double* bra, const double* ket, double* d1, 
     }
     E.pp_row[0] = P.pp_row[0].as<int>();
     E.pp_row[1] = P.pp_row[1].as<int>();
+    if (sym)
+      for (int b = 0; b < 3; ++b) {
+        const DmResult& R = E.blk[b];
+        if (R.R == 0) continue;
+        dim3 grid((R.R + 31) / 32, (R.R + 31) / 32);
+        k_dm_mirror<<<grid, 256, 0, st>>>(R, const_cast<double*>(R.q)); ISCSI_COUNT_LAUNCH();
+      }
     long long tot = 3ll * n * n * n * n;
     int blocks = (int)std::min<long long>((tot + 255) / 256, 152ll * 16);
     k_dm_expand<<<blocks, 256, 0, st>>>(E, d2); ISCSI_COUNT_LAUNCH();

@@ -244,6 +244,8 @@ struct Context {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // density matrices (density.cu): string tables, workspaces and work lists, built at first use
   DensityPlan* dm = nullptr;
+  // time propagation (propagate.cu): Krylov basis and sigma buffers, partial sums, control block
+  DevBuf pr_ws, pr_part, pr_ctl;
   ~Context();
 };
 
@@ -324,6 +326,13 @@ double density_gemm_ms(Context& ctx);  // duration of the last contraction launc
 int sigma_noalloc_run(Context& ctx, const double* c, double* sigma);
 size_t noalloc_bytes_needed(const Context& ctx);
 size_t noalloc_scratch_bytes();
+
+// propagate.cu: steps of the short-iterative Lanczos propagator of H_tau + f_k V
+// (cpl: the context of V, or nullptr); c device [2][ndet] (real time) or
+// [ndet] (imaginary time); diag: host [2 * nsteps] or nullptr
+constexpr int kPrMaxKrylov = 64;
+int propagate_run(Context& ctx, Context* cpl, double* c, int nsteps, double dt, const double* field, int m,
+                  int imaginary, double* diag);
 
 // davidson.cu
 int davidson_run(Context& ctx, int nroots, double tol, double* energies, double* vecs);
