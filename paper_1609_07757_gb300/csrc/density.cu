@@ -428,21 +428,21 @@ __device__ __forceinline__ double dm_samespin(const DmExpand& E, int b, int p, i
   return ((p < r) == (q < t)) ? v : -v;
 }
 
+// one block per (p, q) and d2 block b: writes d2[b][p][q][r][t] for all (r, t),
+// consecutive threads on consecutive t (coalesced stores; the pair-indexed
+// reads are mostly consecutive within a level group)
 __global__ void __launch_bounds__(256) k_dm_expand(DmExpand E, double* __restrict__ d2) {
-  const long long n = E.n, n2 = n * n, n4 = n2 * n2;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3 * n4;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(i / n4);
-    long long w = i - b * n4;
-    const int p = (int)(w / (n2 * n)), q = (int)((w / n2) % n), r = (int)((w / n) % n), t = (int)(w % n);
+  const int n = E.n, p = blockIdx.x / n, q = blockIdx.x - (blockIdx.x / n) * n, b = blockIdx.y;
+  const long long n2 = (long long)n * n;
+  double* __restrict__ out = d2 + (long long)b * n2 * n2 + (long long)blockIdx.x * n2;
+  const bool ab = b == 1 && E.na > 0 && E.nb > 0;
+  const bool ss = b != 1 && (b == 0 ? E.na : E.nb) >= 2;
+  for (int rt = threadIdx.x; rt < n * n; rt += blockDim.x) {
+    const int r = rt / n, t = rt - (rt / n) * n;
     double v = 0.0;
-    if (b == 1) {
-      if (E.na > 0 && E.nb > 0)
-        v = dm_read(E.blk[1], E.pair_index[p * E.n + r], E.pair_index[q * E.n + t]);
-    } else if ((b == 0 ? E.na : E.nb) >= 2) {
-      v = dm_samespin(E, b, p, q, r, t);
-    }
-    d2[i] = v;
+    if (ab) v = dm_read(E.blk[1], E.pair_index[p * n + r], E.pair_index[q * n + t]);
+    else if (ss) v = dm_samespin(E, b, p, q, r, t);
+    out[rt] = v;
   }
 }
 
@@ -654,9 +654,7 @@ int density_run(Context& ctx, const double* bra, const double* ket, double* d1, 
         dim3 grid((R.R + 31) / 32, (R.R + 31) / 32);
         k_dm_mirror<<<grid, 256, 0, st>>>(R, const_cast<double*>(R.q)); ISCSI_COUNT_LAUNCH();
       }
-    long long tot = 3ll * n * n * n * n;
-    int blocks = (int)std::min<long long>((tot + 255) / 256, 152ll * 16);
-    k_dm_expand<<<blocks, 256, 0, st>>>(E, d2); ISCSI_COUNT_LAUNCH();
+    k_dm_expand<<<dim3(n * n, 3), 256, 0, st>>>(E, d2); ISCSI_COUNT_LAUNCH();
     ISCSI_CUDA(cudaGetLastError());
   }
   if (d1) {

@@ -184,6 +184,8 @@ struct Context {
   bool have_ab = false;
   // same-spin parts
   DevBuf M64[2], M32[2];                  // [count x count] per spin (beta aliases alpha when equal)
+  DevBuf M64base[2];                      // M64 without a per-step one-body term (propagation)
+  double m_shift = 0.0;                   // the factor f of that term now in M64
   bool beta_alias = false;
   DevBuf diag;                            // FP64 [ndet]
   // workspaces
@@ -307,6 +309,9 @@ const OzJob* both_tc_job(Context& ctx, int prec);  // that combined job (built w
 int launch_tc_problems(const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
                        void* const* tbases, int tiles, int prec, int cl, int* err, cudaStream_t st);
 int tc_check(Context& ctx);
+int samespin_matrices_changed(Context& ctx);  // re-cut the same-spin operand slices in place
+// M <- M_base + f M_v (cpl: the context of v); f = 0 restores (sigma.cu)
+int onebody_shift(Context& ctx, const Context& cpl, double f);
 // jobs assembled elsewhere: append a segment (K from column 0 of both arrays),
 // number the tiles and upload (cl CTAs per cluster), launch k_oz_gemm
 int oz_job_add_seg(OzJob& job, const SliceArray& A, int a_row0, const int* a_exp, const SliceArray& B, int b_row0,

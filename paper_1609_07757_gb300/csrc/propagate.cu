@@ -7,10 +7,11 @@
 //   tridiagonal T (alpha_j = <q_j|H_k q_j>, beta_j = |residual_j|),
 //   c <- |c| Q exp(-i T dt) e_1        (real time; c complex)
 //   c <- Q exp(-T dt) e_1 / |...|       (imaginary time; c real, normalised).
-// Every sigma is the library's (H_tau c from the current context, V c from a
+// Every sigma is the library's: the one-body term f_k V enters the context's
+// string matrices for the step (M <- M_base + f_k M_v, with M_v those of a
 // second context built with h1 = v and no two-electron integrals on the same
-// space); a complex vector is stored as [re; im] and its sigma is one call with
-// nvec = 2.  The basis is kept orthogonal by two classical Gram-Schmidt passes
+// space; restored at the end), so a Krylov vector costs one sigma of H_k; a
+// complex vector is stored as [re; im] and its sigma is one call with nvec = 2.  The basis is kept orthogonal by two classical Gram-Schmidt passes
 // against all earlier vectors (inner products by two-pass deterministic
 // reductions).  The m x m eigenproblem of T runs on the host (Jacobi) after
 // one synchronisation per step.
@@ -133,14 +134,6 @@ __global__ void __launch_bounds__(kPrThreads) k_pr_scale(const double* __restric
     dst[i] = src[i] * inv;
 }
 
-// w += f v
-__global__ void __launch_bounds__(kPrThreads) k_pr_axpy(double* __restrict__ w, const double* __restrict__ v, double f,
-                                                        long long count) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
-       i += (long long)gridDim.x * blockDim.x)
-    w[i] += f * v[i];
-}
-
 // c = sum_j y_j q_j  (complex y for nc = 2)
 __global__ void __launch_bounds__(kPrThreads) k_pr_combine(const double* __restrict__ Q, long long qstride, int m,
                                                            double* __restrict__ c, int nc, long long ndet,
@@ -211,21 +204,20 @@ static void jacobi_eigh(std::vector<double>& A, int m, std::vector<double>& w, s
 
 static int pr_blocks(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 8)); }
 
-int propagate_run(Context& ctx, Context* cpl, double* c, int nsteps, double dt, const double* field, int m,
-                  int imaginary, double* diag) {
+static int propagate_steps(Context& ctx, Context* cpl, double* c, int nsteps, double dt, const double* field, int m,
+                           int imaginary, double* diag) {
   cudaStream_t st = stream();
   const int nc = imaginary ? 1 : 2;
   const long long N = ctx.ndet, qs = (long long)nc * N;
   const int prec = options().precision;
-  // workspace: basis [m + 1][nc][N], sigma [nc][N], coupling sigma [nc][N], partial sums, control
-  const size_t need = sizeof(double) * ((size_t)(m + 1) * qs + 2 * (size_t)qs);
+  // workspace: basis [m + 1][nc][N], sigma [nc][N], partial sums, control
+  const size_t need = sizeof(double) * ((size_t)(m + 1) * qs + (size_t)qs);
   if (ctx.pr_ws.bytes < need) ISCSI_TRY(ctx.pr_ws.grow(need));
   if (ctx.pr_part.bytes < sizeof(double) * 2 * kPrBlocks * (m + 1))
     ISCSI_TRY(ctx.pr_part.grow(sizeof(double) * 2 * kPrBlocks * (m + 1)));
   if (!ctx.pr_ctl.p) ISCSI_TRY(ctx.pr_ctl.alloc(sizeof(PrCtl)));
   double* Q = ctx.pr_ws.as<double>();
   double* W = Q + (size_t)(m + 1) * qs;
-  double* Wv = W + qs;
   double* part = ctx.pr_part.as<double>();
   PrCtl* ctl = ctx.pr_ctl.as<PrCtl>();
   const int gb = pr_blocks(N);
@@ -233,6 +225,7 @@ int propagate_run(Context& ctx, Context* cpl, double* c, int nsteps, double dt, 
   std::vector<double> T, w, S;
   for (int step = 0; step < nsteps; ++step) {
     const double f = field ? field[step] : 0.0;
+    if (cpl) ISCSI_TRY(onebody_shift(ctx, *cpl, f));
     ISCSI_CUDA(cudaMemsetAsync(ctl, 0, sizeof(PrCtl), st));
     // q_0 = c / |c|
     k_pr_dots<<<kPrBlocks, kPrThreads, 0, st>>>(c, 0, 1, c, nc, N, part); ISCSI_COUNT_LAUNCH();
@@ -241,10 +234,6 @@ int propagate_run(Context& ctx, Context* cpl, double* c, int nsteps, double dt, 
     for (int j = 0; j < m; ++j) {
       double* qj = Q + (size_t)j * qs;
       ISCSI_TRY(sigma_run(ctx, qj, W, nc, prec));
-      if (cpl && f != 0.0) {
-        ISCSI_TRY(sigma_run(*cpl, qj, Wv, nc, prec));
-        k_pr_axpy<<<pr_blocks(qs), kPrThreads, 0, st>>>(W, Wv, f, qs); ISCSI_COUNT_LAUNCH();
-      }
       for (int pass = 0; pass < 2; ++pass) {
         k_pr_dots<<<kPrBlocks, kPrThreads, 0, st>>>(Q, qs, j + 1, W, nc, N, part); ISCSI_COUNT_LAUNCH();
         k_pr_sum<<<1, 2 * (j + 1), 0, st>>>(part, kPrBlocks, j + 1, 0, j, ctl); ISCSI_COUNT_LAUNCH();
@@ -309,9 +298,15 @@ int propagate_run(Context& ctx, Context* cpl, double* c, int nsteps, double dt, 
     ISCSI_CUDA(cudaGetLastError());
     ISCSI_CUDA(cudaStreamSynchronize(st));  // 'up' is read by the copy
   }
-  int w8 = tc_check(ctx);
-  if (w8 != kOk) return w8;
-  return cpl ? tc_check(*cpl) : kOk;
+  return tc_check(ctx);
+}
+
+int propagate_run(Context& ctx, Context* cpl, double* c, int nsteps, double dt, const double* field, int m,
+                  int imaginary, double* diag) {
+  int s = propagate_steps(ctx, cpl, c, nsteps, dt, field, m, imaginary, diag);
+  // the context's string matrices lose the step's one-body term, also after an error
+  int r = cpl ? onebody_shift(ctx, *cpl, 0.0) : kOk;
+  return s != kOk ? s : r;
 }
 
 }  // namespace iscsi

@@ -666,6 +666,42 @@ int sigma_workspace(Context& ctx, int nvec, int precision) {
   return kOk;
 }
 
+// M = M_base + f M_v, elementwise
+__global__ void k_shift_m(const double* __restrict__ base, const double* __restrict__ mv, double f,
+                          double* __restrict__ out, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    out[i] = base[i] + f * mv[i];
+}
+
+// A per-step one-body term (Eq. ham with h(t) = h + f v): the string matrices
+// of the one-body and same-spin units become M_base + f M_v, with M_v those of
+// the context cpl (h1 = v, no two-electron part, the same space); the FP32
+// copies and the tensor-core slices follow.  f = 0 restores M_base exactly.
+int onebody_shift(Context& ctx, const Context& cpl, double f) {
+  if (f == ctx.m_shift) return kOk;
+  cudaStream_t st = stream();
+  for (int s = 0; s < 2; ++s) {
+    if (!ctx.M64[s].p) continue;
+    if (!cpl.M64[s].p) {
+      set_error("one-body shift: the coupling context has no matching string matrix");
+      return kErrArg;
+    }
+    const long long m2 = (long long)ctx.sp[s].count * ctx.sp[s].count;
+    if (!ctx.M64base[s].p) {
+      ISCSI_TRY(ctx.M64base[s].alloc(sizeof(double) * m2));
+      ISCSI_CUDA(cudaMemcpyAsync(ctx.M64base[s].p, ctx.M64[s].p, sizeof(double) * m2, cudaMemcpyDeviceToDevice, st));
+    }
+    k_shift_m<<<launch_blocks(m2, 256), 256, 0, st>>>(ctx.M64base[s].as<double>(), cpl.M64[s].as<double>(), f,
+                                                      ctx.M64[s].as<double>(), m2); ISCSI_COUNT_LAUNCH();
+    if (ctx.M32[s].p) {
+      k_convert<double, float><<<2048, 256, 0, st>>>(ctx.M64[s].as<double>(), ctx.M32[s].as<float>(), m2); ISCSI_COUNT_LAUNCH();
+    }
+  }
+  ISCSI_CUDA(cudaGetLastError());
+  ctx.m_shift = f;
+  return samespin_matrices_changed(ctx);
+}
+
 static int ensure_fp32_matrices(Context& ctx) {
   cudaStream_t st = stream();
   if (ctx.have_ab && !ctx.G32.p) {

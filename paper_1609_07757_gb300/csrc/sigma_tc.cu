@@ -405,8 +405,10 @@ bool samespin_tc_active(const Context& ctx) {
   return false;
 }
 
-static int tc_prepare_m(Context& ctx) {
-  if (ctx.oz_m_ready) return kOk;
+// cut_only: the matrices changed in place (a per-step one-body term); cut them
+// again into the existing buffers, so the work lists keep their pointers
+static int tc_prepare_m(Context& ctx, bool cut_only = false) {
+  if (ctx.oz_m_ready && !cut_only) return kOk;
   cudaStream_t st = stream();
   ISCSI_TRY(tc_attr());
   ISCSI_TRY(tc_err_buf(ctx));
@@ -427,9 +429,11 @@ static int tc_prepare_m(Context& ctx) {
     ISCSI_CUDA(cudaMemcpyAsync(dmap.p, colmap.data(), sizeof(int) * kcols, cudaMemcpyHostToDevice, st));
     ctx.oz_ma_rows = SA.count + OZ_BM;
     ctx.oz_ma_ld = kcols;
-    ISCSI_TRY(ctx.oz_mas.alloc(sizeof(__nv_bfloat16) * OZ_S * (size_t)ctx.oz_ma_rows * kcols));
-    ISCSI_TRY(ctx.oz_maexp.alloc(sizeof(int) * ctx.oz_ma_rows));
-    ISCSI_CUDA(cudaMemsetAsync(ctx.oz_maexp.p, 0, sizeof(int) * ctx.oz_ma_rows, st));
+    if (!cut_only) {
+      ISCSI_TRY(ctx.oz_mas.alloc(sizeof(__nv_bfloat16) * OZ_S * (size_t)ctx.oz_ma_rows * kcols));
+      ISCSI_TRY(ctx.oz_maexp.alloc(sizeof(int) * ctx.oz_ma_rows));
+      ISCSI_CUDA(cudaMemsetAsync(ctx.oz_maexp.p, 0, sizeof(int) * ctx.oz_ma_rows, st));
+    }
     ISCSI_TRY(slice_matrix(ctx.M64[0].as<double>(), SA.count, SA.count, SA.count, 0, dmap.as<int>(), kcols,
                            ctx.oz_ma_rows, ctx.oz_maexp.as<int>(), ctx.oz_mas.as<__nv_bfloat16>(), st));
     ISCSI_CUDA(cudaStreamSynchronize(st));  // colmap lives until here
@@ -441,8 +445,10 @@ static int tc_prepare_m(Context& ctx) {
     int trans = ctx.beta_alias ? 0 : 1;
     ctx.oz_mb_rows = round_up(SB.count, OZ_BN);
     ctx.oz_mb_ld = round_up(SB.count, OZ_BK);
-    ISCSI_TRY(ctx.oz_mbs.alloc(sizeof(__nv_bfloat16) * OZ_S * (size_t)ctx.oz_mb_rows * ctx.oz_mb_ld));
-    ISCSI_TRY(ctx.oz_mbexp.alloc(sizeof(int) * ctx.oz_mb_rows));
+    if (!cut_only) {
+      ISCSI_TRY(ctx.oz_mbs.alloc(sizeof(__nv_bfloat16) * OZ_S * (size_t)ctx.oz_mb_rows * ctx.oz_mb_ld));
+      ISCSI_TRY(ctx.oz_mbexp.alloc(sizeof(int) * ctx.oz_mb_rows));
+    }
     ISCSI_TRY(slice_matrix(Mb, SB.count, SB.count, SB.count, trans, nullptr, ctx.oz_mb_ld, ctx.oz_mb_rows,
                            ctx.oz_mbexp.as<int>(), ctx.oz_mbs.as<__nv_bfloat16>(), st));
   }
@@ -698,8 +704,8 @@ bool samespin_tc32_active(const Context& ctx) {
   return false;
 }
 
-static int t3_prepare_m(Context& ctx) {
-  if (ctx.t3_m_ready) return kOk;
+static int t3_prepare_m(Context& ctx, bool cut_only = false) {
+  if (ctx.t3_m_ready && !cut_only) return kOk;
   cudaStream_t st = stream();
   ISCSI_TRY(tc_attr());
   ISCSI_TRY(tc_err_buf(ctx));
@@ -719,7 +725,7 @@ static int t3_prepare_m(Context& ctx) {
     ISCSI_CUDA(cudaMemcpyAsync(dmap.p, colmap.data(), sizeof(int) * kcols, cudaMemcpyHostToDevice, st));
     ctx.oz_ma_rows = SA.count + OZ_BM;
     ctx.oz_ma_ld = kcols;
-    ISCSI_TRY(ctx.t3_mas.alloc(sizeof(__nv_bfloat16) * T3_S * (size_t)ctx.oz_ma_rows * kcols));
+    if (!cut_only) ISCSI_TRY(ctx.t3_mas.alloc(sizeof(__nv_bfloat16) * T3_S * (size_t)ctx.oz_ma_rows * kcols));
     ISCSI_TRY(t3_slice_matrix<double>(ctx.M64[0].as<double>(), SA.count, SA.count, SA.count, 0, dmap.as<int>(), kcols,
                                       ctx.oz_ma_rows, ctx.t3_mas.as<__nv_bfloat16>(), st));
     ISCSI_CUDA(cudaStreamSynchronize(st));  // colmap lives until here
@@ -729,7 +735,7 @@ static int t3_prepare_m(Context& ctx) {
     int trans = ctx.beta_alias ? 0 : 1;
     ctx.oz_mb_rows = round_up(SB.count, OZ_BN);
     ctx.oz_mb_ld = round_up(SB.count, OZ_BK);
-    ISCSI_TRY(ctx.t3_mbs.alloc(sizeof(__nv_bfloat16) * T3_S * (size_t)ctx.oz_mb_rows * ctx.oz_mb_ld));
+    if (!cut_only) ISCSI_TRY(ctx.t3_mbs.alloc(sizeof(__nv_bfloat16) * T3_S * (size_t)ctx.oz_mb_rows * ctx.oz_mb_ld));
     ISCSI_TRY(t3_slice_matrix<double>(Mb, SB.count, SB.count, SB.count, trans, nullptr, ctx.oz_mb_ld, ctx.oz_mb_rows,
                                       ctx.t3_mbs.as<__nv_bfloat16>(), st));
   }
@@ -865,6 +871,13 @@ int launch_tc_problems(const OzProblem* probs, int nprobs, const OzSeg* segs, co
   } else {
     return launch_t3(cl, tiles, probs, nprobs, segs, maps, nullptr, reinterpret_cast<float* const*>(tbases), err, st);
   }
+}
+
+// the same-spin string matrices changed in place: cut the slices prepared so far again
+int samespin_matrices_changed(Context& ctx) {
+  if (ctx.oz_m_ready) ISCSI_TRY(tc_prepare_m(ctx, true));
+  if (ctx.t3_m_ready) ISCSI_TRY(t3_prepare_m(ctx, true));
+  return kOk;
 }
 
 // tensor-core jobs built by other parts of the library (density.cu): segments

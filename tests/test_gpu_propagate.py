@@ -142,3 +142,18 @@ def test_argument_checks():
     L.iscsi_ctx_use(hh)
     with pytest.raises(Exception):
         L.iscsi_propagate(x, 2, 0.1, np.zeros(2), other, 8)  # coupling on another space
+
+
+def test_context_is_restored_after_a_field():
+    """The one-body term enters the context's string matrices only during the call."""
+    hh, hv, H, V, o = make_pair(8, 2, 2, 3)
+    c = torch.as_tensor(unit_vector(o.ndet, 3), dtype=torch.float64, device="cuda")
+    s0 = torch.empty_like(c)
+    L.iscsi_sigma(c, s0, 1)
+    x = torch.zeros((2, o.ndet), dtype=torch.float64, device="cuda")
+    x[0] = c
+    L.iscsi_propagate(x, 3, 0.05, np.array([0.3, -0.2, 0.1]), hv, 8)
+    s1 = torch.empty_like(c)
+    L.iscsi_sigma(c, s1, 1)
+    torch.cuda.synchronize()
+    assert torch.equal(s0, s1)
