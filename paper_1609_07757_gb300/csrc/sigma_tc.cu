@@ -2,10 +2,10 @@
 // (tcgen05), with FP64 accuracy from exact bf16 slices (ozaki.cuh).
 //
 // Opposite spin, per sigma call and column level class c:
-//   k_oz_col_exp    : exponent of the largest |Ct| in each column (X,Y,v)
-//   k_oz_lift_slice : Ct^T[(X,Y,v)][(q,s)] = s s c[X u q, Y u s], gathered
-//                     through the contraction/addition tables and cut into 7
-//                     bf16 slices (the B operand, K-major)
+//   k_oz_lift_row   : per column (X,Y,v), Ct^T[(X,Y,v)][(q,s)] = s s c[X u q, Y u s]
+//                     gathered once through the contraction/addition tables,
+//                     the column's exponent, and its 7 exact bf16 slices (the
+//                     B operand, K-major)
 //   k_oz_gemm       : T_c = G[:M_c, :K_c] Ct_c for all classes, one launch
 // Same spin, per excitation-level block a of the CI vector (rows = alpha
 // strings of level a, columns = the allowed beta prefix):
@@ -47,6 +47,7 @@ struct TcTable {
   int nvec;
   TcClass c[2 * kMaxElec];
   long long start[2 * kMaxElec + 1];  // flattened (col, k) element offsets
+  int col_start[2 * kMaxElec + 1];    // first column of each class over all classes
 };
 
 static inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -71,57 +72,97 @@ __device__ __forceinline__ V tc_gather(const TcClass& C, int nvec, int col, int 
   return ((ea ^ eb) & 1) ? -x : x;
 }
 
-// exponent (frexp) of max |Ct| per column, by atomicMax; exps start at INT_MIN
-__global__ void k_oz_col_exp(TcTable tt, int n, int nholeA, int nholeB, const int* __restrict__ pair_of,
-                             const int* __restrict__ hp_inv, const int* __restrict__ liftA,
-                             const int* __restrict__ liftB, const int8_t* __restrict__ alevel,
-                             const int* __restrict__ nballow, const long long* __restrict__ off,
-                             const double* __restrict__ c, long long ndet, int* __restrict__ exps) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= tt.start[tt.nclass]) return;
+// One block per column (X, Y, v) of Ct^T over all classes.  The column's lift
+// entries for every orbital (a+_q |X> and a+_s |Y>: target string and sign,
+// and the target alpha string's offset and allowed beta count) are staged in
+// shared memory first, so an element (q, s) costs the pair table and c.  The
+// K values are gathered once (kOzRowRegs per thread in registers; a longer K
+// is gathered again beyond that), the column's exponent (frexp of the largest
+// |x|, 0 for an all-zero column) is taken and its exact slices written.
+constexpr int kOzRowRegs = 24;
+struct OzLiftCol {
+  int a[kMaxOrb], b[kMaxOrb], lim[kMaxOrb];
+  long long off[kMaxOrb];
+};
+
+__device__ __forceinline__ double oz_lift_value(const OzLiftCol& L, const TcClass& C, int k, int n,
+                                                const int* __restrict__ pair_of, const double* __restrict__ cv) {
+  if (k >= C.krows) return 0.0;
+  const int qs = pair_of[k];
+  const int q = qs / n, s = qs - (qs / n) * n;
+  const int ea = L.a[q], eb = L.b[s];
+  if (ea < 0 || eb < 0) return 0.0;
+  const int Bp = eb >> 1;
+  if (Bp >= L.lim[q]) return 0.0;
+  const double x = cv[L.off[q] + Bp];
+  return ((ea ^ eb) & 1) ? -x : x;
+}
+
+__global__ void __launch_bounds__(256) k_oz_lift_row(TcTable tt, int n, int nholeA, int nholeB,
+                                                     const int* __restrict__ pair_of, const int* __restrict__ hp_inv,
+                                                     const int* __restrict__ liftA, const int* __restrict__ liftB,
+                                                     const int8_t* __restrict__ alevel,
+                                                     const int* __restrict__ nballow, const long long* __restrict__ off,
+                                                     const double* __restrict__ c, long long ndet,
+                                                     int* __restrict__ exps, __nv_bfloat16* __restrict__ bs) {
+  __shared__ OzLiftCol L;
+  __shared__ int sm[8];
+  __shared__ int ex_s;
   int cl = 0;
-  while (t >= tt.start[cl + 1]) ++cl;
+  while ((int)blockIdx.x >= tt.col_start[cl + 1]) ++cl;
   const TcClass& C = tt.c[cl];
-  long long local = t - tt.start[cl];
-  int col = (int)(local / C.kpad), k = (int)(local % C.kpad);
-  double x = tc_gather<double>(C, tt.nvec, col, k, n, nholeA, nholeB, pair_of, hp_inv, liftA, liftB, alevel,
-                               nballow, off, c, ndet);
-  int e = x != 0.0 ? oz_exp_field(x) - 1022 : INT_MIN;  // frexp exponent of |x|
-  // one atomic per (warp, column): lanes of the same column reduce together
-  int key = (int)(C.exp_off + col);
-  unsigned group = __match_any_sync(__activemask(), key);
-  int m = __reduce_max_sync(group, e);
-  if ((int)(threadIdx.x & 31) == __ffs(group) - 1 && m != INT_MIN) atomicMax(&exps[key], m);
-}
-
-__global__ void k_oz_fill_int(int* __restrict__ p, long long count, int value) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t < count) p[t] = value;
-}
-
-__global__ void k_oz_fix_exp(int* __restrict__ exps, long long count) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t < count && exps[t] == INT_MIN) exps[t] = 0;
-}
-
-__global__ void k_oz_lift_slice(TcTable tt, int n, int nholeA, int nholeB, const int* __restrict__ pair_of,
-                                const int* __restrict__ hp_inv, const int* __restrict__ liftA,
-                                const int* __restrict__ liftB, const int8_t* __restrict__ alevel,
-                                const int* __restrict__ nballow, const long long* __restrict__ off,
-                                const double* __restrict__ c, long long ndet, const int* __restrict__ exps,
-                                __nv_bfloat16* __restrict__ bs) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= tt.start[tt.nclass]) return;
-  int cl = 0;
-  while (t >= tt.start[cl + 1]) ++cl;
-  const TcClass& C = tt.c[cl];
-  long long local = t - tt.start[cl];
-  int col = (int)(local / C.kpad), k = (int)(local % C.kpad);
-  double x = tc_gather<double>(C, tt.nvec, col, k, n, nholeA, nholeB, pair_of, hp_inv, liftA, liftB, alevel,
-                               nballow, off, c, ndet);
+  const int col = (int)blockIdx.x - tt.col_start[cl];
+  const int hp = col / tt.nvec, vv = col - hp * tt.nvec;
+  const int xy = hp_inv[C.hp_start + hp];
+  const int X = xy / nholeB, Y = xy - (xy / nholeB) * nholeB;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int ea = liftA[q * nholeA + X];
+    L.a[q] = ea;
+    L.b[q] = liftB[q * nholeB + Y];
+    if (ea >= 0) {
+      const int A = ea >> 1;
+      L.off[q] = off[A];
+      L.lim[q] = nballow[alevel[A]];
+    }
+  }
+  __syncthreads();
+  const double* cv = c + (long long)vv * ndet;
+  double v[kOzRowRegs];
+  int m = 0;
+#pragma unroll
+  for (int i = 0; i < kOzRowRegs; ++i) {
+    const int k = threadIdx.x + i * blockDim.x;
+    v[i] = k < C.kpad ? oz_lift_value(L, C, k, n, pair_of, cv) : 0.0;
+    m = max(m, oz_exp_field(v[i]));
+  }
+  for (int k = threadIdx.x + kOzRowRegs * blockDim.x; k < C.kpad; k += blockDim.x)
+    m = max(m, oz_exp_field(oz_lift_value(L, C, k, n, pair_of, cv)));
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int x = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) x = max(x, sm[i]);
+    ex_s = x > 0 ? x - 1022 : 0;
+    exps[C.exp_off + col] = ex_s;
+  }
+  __syncthreads();
+  const int ex = ex_s;
+  __nv_bfloat16* row = bs + C.bs_off + (long long)col * C.kpad;
+  const long long stride = (long long)C.npad * C.kpad;
   int a[OZ_S];
-  oz_digits(x, exps[C.exp_off + col], a);
-  oz_store_digits(a, bs + C.bs_off + (long long)col * C.kpad + k, (long long)C.npad * C.kpad);
+#pragma unroll
+  for (int i = 0; i < kOzRowRegs; ++i) {
+    const int k = threadIdx.x + i * blockDim.x;
+    if (k < C.kpad) {
+      oz_digits(v[i], ex, a);
+      oz_store_digits(a, row + k, stride);
+    }
+  }
+  for (int k = threadIdx.x + kOzRowRegs * blockDim.x; k < C.kpad; k += blockDim.x) {
+    oz_digits(oz_lift_value(L, C, k, n, pair_of, cv), ex, a);
+    oz_store_digits(a, row + k, stride);
+  }
 }
 
 // FP32 form: Ct^T gathered from the FP32 vector and split into three bf16 terms
@@ -297,6 +338,7 @@ static TcTable ab_table(const Context& ctx, int nvec, long long* bs_elems, long 
     C.exp_off = ex;
     C.tot = (long long)C.ncols * C.kpad;
     tt.start[tt.nclass] = flat;
+    tt.col_start[tt.nclass + 1] = tt.col_start[tt.nclass] + C.ncols;
     tt.c[tt.nclass++] = C;
     flat += C.tot;
     bs += (long long)nslice * C.npad * C.kpad;
@@ -360,19 +402,15 @@ int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec) {
     job.nvec = nvec;
     job.tbase = ttw;
   }
-  k_oz_fill_int<<<launch_blocks(exp_elems, 256), 256, 0, st>>>(ctx.oz_bexp.as<int>(), exp_elems, INT_MIN); ISCSI_COUNT_LAUNCH();
   const SpinSpace& SA = ctx.sp[0];
   const SpinSpace& SB = ctx.sp[1];
-  long long flat = tt.start[tt.nclass];
-  k_oz_col_exp<<<launch_blocks(flat, 256), 256, 0, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_of.as<int>(),
-                                                          ctx.hp_inv.as<int>(), SA.lift.as<int>(), SB.lift.as<int>(),
-                                                          SA.level.as<int8_t>(), ctx.nballow.as<int>(),
-                                                          ctx.off.as<long long>(), c, ctx.ndet, ctx.oz_bexp.as<int>()); ISCSI_COUNT_LAUNCH();
-  k_oz_fix_exp<<<launch_blocks(exp_elems, 256), 256, 0, st>>>(ctx.oz_bexp.as<int>(), exp_elems); ISCSI_COUNT_LAUNCH();
-  k_oz_lift_slice<<<launch_blocks(flat, 256), 256, 0, st>>>(
-      tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_of.as<int>(), ctx.hp_inv.as<int>(), SA.lift.as<int>(), SB.lift.as<int>(),
-      SA.level.as<int8_t>(), ctx.nballow.as<int>(), ctx.off.as<long long>(), c, ctx.ndet, ctx.oz_bexp.as<int>(),
-      ctx.oz_bs.as<__nv_bfloat16>()); ISCSI_COUNT_LAUNCH();
+  const int ncol_all = tt.col_start[tt.nclass];
+  if (ncol_all > 0) {
+    k_oz_lift_row<<<ncol_all, 256, 0, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_of.as<int>(), ctx.hp_inv.as<int>(),
+                                            SA.lift.as<int>(), SB.lift.as<int>(), SA.level.as<int8_t>(),
+                                            ctx.nballow.as<int>(), ctx.off.as<long long>(), c, ctx.ndet,
+                                            ctx.oz_bexp.as<int>(), ctx.oz_bs.as<__nv_bfloat16>()); ISCSI_COUNT_LAUNCH();
+  }
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
 }
