@@ -52,25 +52,6 @@ struct TcTable {
 
 static inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-template <typename V>
-__device__ __forceinline__ V tc_gather(const TcClass& C, int nvec, int col, int k, int n, int nholeA, int nholeB,
-                                       const int* __restrict__ pair_of, const int* __restrict__ hp_inv,
-                                       const int* __restrict__ liftA, const int* __restrict__ liftB,
-                                       const int8_t* __restrict__ alevel, const int* __restrict__ nballow,
-                                       const long long* __restrict__ off, const V* __restrict__ c, long long ndet) {
-  if (k >= C.krows) return (V)0;
-  int hp = col / nvec, v = col % nvec;
-  int xy = hp_inv[C.hp_start + hp];
-  int X = xy / nholeB, Y = xy % nholeB;
-  int qs = pair_of[k];
-  int q = qs / n, s = qs % n;
-  int ea = liftA[q * nholeA + X], eb = liftB[s * nholeB + Y];
-  if (ea < 0 || eb < 0) return (V)0;
-  int Ap = ea >> 1, Bp = eb >> 1;
-  if (Bp >= nballow[alevel[Ap]]) return (V)0;
-  V x = c[(long long)v * ndet + off[Ap] + Bp];
-  return ((ea ^ eb) & 1) ? -x : x;
-}
 
 // One block per column (X, Y, v) of Ct^T over all classes.  The column's lift
 // entries for every orbital (a+_q |X> and a+_s |Y>: target string and sign,
@@ -85,34 +66,32 @@ struct OzLiftCol {
   long long off[kMaxOrb];
 };
 
-__device__ __forceinline__ double oz_lift_value(const OzLiftCol& L, const TcClass& C, int k, int n,
-                                                const int* __restrict__ pair_of, const double* __restrict__ cv) {
-  if (k >= C.krows) return 0.0;
+template <typename V>
+__device__ __forceinline__ V oz_lift_value(const OzLiftCol& L, const TcClass& C, int k, int n,
+                                           const int* __restrict__ pair_of, const V* __restrict__ cv) {
+  if (k >= C.krows) return (V)0;
   const int qs = pair_of[k];
   const int q = qs / n, s = qs - (qs / n) * n;
   const int ea = L.a[q], eb = L.b[s];
-  if (ea < 0 || eb < 0) return 0.0;
+  if (ea < 0 || eb < 0) return (V)0;
   const int Bp = eb >> 1;
-  if (Bp >= L.lim[q]) return 0.0;
-  const double x = cv[L.off[q] + Bp];
+  if (Bp >= L.lim[q]) return (V)0;
+  const V x = cv[L.off[q] + Bp];
   return ((ea ^ eb) & 1) ? -x : x;
 }
 
-__global__ void __launch_bounds__(256) k_oz_lift_row(TcTable tt, int n, int nholeA, int nholeB,
-                                                     const int* __restrict__ pair_of, const int* __restrict__ hp_inv,
-                                                     const int* __restrict__ liftA, const int* __restrict__ liftB,
-                                                     const int8_t* __restrict__ alevel,
-                                                     const int* __restrict__ nballow, const long long* __restrict__ off,
-                                                     const double* __restrict__ c, long long ndet,
-                                                     int* __restrict__ exps, __nv_bfloat16* __restrict__ bs) {
-  __shared__ OzLiftCol L;
-  __shared__ int sm[8];
-  __shared__ int ex_s;
+// the column (X, Y, v) of block blockIdx.x: class, local column, staged lift entries
+__device__ __forceinline__ int oz_stage_column(const TcTable& tt, int n, int nholeA, int nholeB,
+                                               const int* __restrict__ hp_inv, const int* __restrict__ liftA,
+                                               const int* __restrict__ liftB, const int8_t* __restrict__ alevel,
+                                               const int* __restrict__ nballow, const long long* __restrict__ off,
+                                               OzLiftCol& L, int& col, int& vv) {
   int cl = 0;
   while ((int)blockIdx.x >= tt.col_start[cl + 1]) ++cl;
   const TcClass& C = tt.c[cl];
-  const int col = (int)blockIdx.x - tt.col_start[cl];
-  const int hp = col / tt.nvec, vv = col - hp * tt.nvec;
+  col = (int)blockIdx.x - tt.col_start[cl];
+  const int hp = col / tt.nvec;
+  vv = col - hp * tt.nvec;
   const int xy = hp_inv[C.hp_start + hp];
   const int X = xy / nholeB, Y = xy - (xy / nholeB) * nholeB;
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
@@ -126,17 +105,32 @@ __global__ void __launch_bounds__(256) k_oz_lift_row(TcTable tt, int n, int nhol
     }
   }
   __syncthreads();
+  return cl;
+}
+
+__global__ void __launch_bounds__(256) k_oz_lift_row(TcTable tt, int n, int nholeA, int nholeB,
+                                                     const int* __restrict__ pair_of, const int* __restrict__ hp_inv,
+                                                     const int* __restrict__ liftA, const int* __restrict__ liftB,
+                                                     const int8_t* __restrict__ alevel,
+                                                     const int* __restrict__ nballow, const long long* __restrict__ off,
+                                                     const double* __restrict__ c, long long ndet,
+                                                     int* __restrict__ exps, __nv_bfloat16* __restrict__ bs) {
+  __shared__ OzLiftCol L;
+  __shared__ int sm[8];
+  __shared__ int ex_s;
+  int col, vv;
+  const TcClass& C = tt.c[oz_stage_column(tt, n, nholeA, nholeB, hp_inv, liftA, liftB, alevel, nballow, off, L, col, vv)];
   const double* cv = c + (long long)vv * ndet;
   double v[kOzRowRegs];
   int m = 0;
 #pragma unroll
   for (int i = 0; i < kOzRowRegs; ++i) {
     const int k = threadIdx.x + i * blockDim.x;
-    v[i] = k < C.kpad ? oz_lift_value(L, C, k, n, pair_of, cv) : 0.0;
+    v[i] = k < C.kpad ? oz_lift_value<double>(L, C, k, n, pair_of, cv) : 0.0;
     m = max(m, oz_exp_field(v[i]));
   }
   for (int k = threadIdx.x + kOzRowRegs * blockDim.x; k < C.kpad; k += blockDim.x)
-    m = max(m, oz_exp_field(oz_lift_value(L, C, k, n, pair_of, cv)));
+    m = max(m, oz_exp_field(oz_lift_value<double>(L, C, k, n, pair_of, cv)));
   m = __reduce_max_sync(0xffffffffu, m);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
   __syncthreads();
@@ -160,27 +154,27 @@ __global__ void __launch_bounds__(256) k_oz_lift_row(TcTable tt, int n, int nhol
     }
   }
   for (int k = threadIdx.x + kOzRowRegs * blockDim.x; k < C.kpad; k += blockDim.x) {
-    oz_digits(oz_lift_value(L, C, k, n, pair_of, cv), ex, a);
+    oz_digits(oz_lift_value<double>(L, C, k, n, pair_of, cv), ex, a);
     oz_store_digits(a, row + k, stride);
   }
 }
 
-// FP32 form: Ct^T gathered from the FP32 vector and split into three bf16 terms
-__global__ void k_t3_lift(TcTable tt, int n, int nholeA, int nholeB, const int* __restrict__ pair_of,
-                          const int* __restrict__ hp_inv, const int* __restrict__ liftA, const int* __restrict__ liftB,
-                          const int8_t* __restrict__ alevel, const int* __restrict__ nballow,
-                          const long long* __restrict__ off, const float* __restrict__ c, long long ndet,
-                          __nv_bfloat16* __restrict__ bs) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= tt.start[tt.nclass]) return;
-  int cl = 0;
-  while (t >= tt.start[cl + 1]) ++cl;
-  const TcClass& C = tt.c[cl];
-  long long local = t - tt.start[cl];
-  int col = (int)(local / C.kpad), k = (int)(local % C.kpad);
-  float x = tc_gather<float>(C, tt.nvec, col, k, n, nholeA, nholeB, pair_of, hp_inv, liftA, liftB, alevel, nballow,
-                             off, c, ndet);
-  t3_store_terms<float>(x, bs + C.bs_off + (long long)col * C.kpad + k, (long long)C.npad * C.kpad);
+// FP32 form: Ct^T gathered from the FP32 vector and split into three bf16
+// terms, one block per column with its lift entries staged as above
+__global__ void __launch_bounds__(256) k_t3_lift(TcTable tt, int n, int nholeA, int nholeB,
+                                                 const int* __restrict__ pair_of, const int* __restrict__ hp_inv,
+                                                 const int* __restrict__ liftA, const int* __restrict__ liftB,
+                                                 const int8_t* __restrict__ alevel, const int* __restrict__ nballow,
+                                                 const long long* __restrict__ off, const float* __restrict__ c,
+                                                 long long ndet, __nv_bfloat16* __restrict__ bs) {
+  __shared__ OzLiftCol L;
+  int col, vv;
+  const TcClass& C = tt.c[oz_stage_column(tt, n, nholeA, nholeB, hp_inv, liftA, liftB, alevel, nballow, off, L, col, vv)];
+  const float* cv = c + (long long)vv * ndet;
+  __nv_bfloat16* row = bs + C.bs_off + (long long)col * C.kpad;
+  const long long stride = (long long)C.npad * C.kpad;
+  for (int k = threadIdx.x; k < C.kpad; k += blockDim.x)
+    t3_store_terms<float>(oz_lift_value<float>(L, C, k, n, pair_of, cv), row + k, stride);
 }
 
 static int tc_attr() {
@@ -723,8 +717,8 @@ int opposite_tc32_operands(Context& ctx, const float* c, float* ttw, int nvec) {
   }
   const SpinSpace& SA = ctx.sp[0];
   const SpinSpace& SB = ctx.sp[1];
-  long long flat = tt.start[tt.nclass];
-  k_t3_lift<<<launch_blocks(flat, 256), 256, 0, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_of.as<int>(),
+  if (tt.col_start[tt.nclass] > 0)
+  k_t3_lift<<<tt.col_start[tt.nclass], 256, 0, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_of.as<int>(),
                                                        ctx.hp_inv.as<int>(), SA.lift.as<int>(), SB.lift.as<int>(),
                                                        SA.level.as<int8_t>(), ctx.nballow.as<int>(),
                                                        ctx.off.as<long long>(), c, ctx.ndet,
