@@ -609,10 +609,14 @@ def run_density(name, steps=10, warmup=3, with_cpu=True, tau=None):
         cc = unit_vector(ndet, 23)
         rng = np.random.default_rng(1)
         m = 2 * max_threads()
-        spec = np.column_stack([rng.integers(0, 3, m)] + [rng.integers(0, n, m) for _ in range(4)])
-        t0 = time.time()
-        vals = o.density_elems(cc, None, spec)
-        dt = time.time() - t0
+        for _ in range(2):  # calibrate on a few elements, then aim at ~10 s
+            spec = np.column_stack([rng.integers(0, 3, m)] + [rng.integers(0, n, m) for _ in range(4)])
+            t0 = time.time()
+            vals = o.density_elems(cc, None, spec)
+            dt = time.time() - t0
+            if dt >= 3.0:
+                break
+            m = int(min(3 * n ** 4, max(m, m * 10.0 / max(dt, 1e-3))))
         full_s = dt / m * (3 * n ** 4 + 2 * n * n)
         out["cpu_baseline"] = {"value": round(full_s * 1e3, 1), "unit": "ms per density call (extrapolated)",
                                "cores": max_threads(), "kind": "oracle",
@@ -744,12 +748,14 @@ def cpu_baseline(wl, tau, target_s=15.0, steps=1):
     c = unit_vector(o.ndet, 17)
     rng = np.random.default_rng(5)
     cores = oracle.max_threads()
-    # calibrate the sample size on a few rows
-    rows = rng.choice(o.ndet, size=min(o.ndet, 4 * cores), replace=False)
-    t0 = time.time()
-    o.sigma_rows(c, rows)
-    per_row = max((time.time() - t0) / len(rows), 1e-7)
-    nrow = int(min(o.ndet, max(len(rows), target_s / per_row)))
+    # calibrate the sample size on a few rows, then on a sample a tenth of the target
+    nrow = min(o.ndet, 4 * cores)
+    for target in (0.1 * target_s, target_s):
+        rows = rng.choice(o.ndet, size=nrow, replace=False)
+        t0 = time.time()
+        o.sigma_rows(c, rows)
+        per_row = max((time.time() - t0) / len(rows), 1e-7)
+        nrow = int(min(o.ndet, max(len(rows), target / per_row)))
     times = []
     for _ in range(steps):
         rows = rng.choice(o.ndet, size=nrow, replace=False)
