@@ -666,6 +666,7 @@ def run_propagation(name, nsteps=4, dt=0.02, krylov=12, with_cpu=True):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / nsteps
     norm = float(torch.linalg.norm(c))
+    route = L.iscsi_stats().get("route_fp64")
     L.iscsi_finalize()
     sig = 2 * krylov  # sigma vectors of H_k per step (complex vectors: nvec = 2; f_k V folded into H's matrices)
     out = {"workload": name, "ndet": ndet, "steps": nsteps, "dt": dt, "krylov": krylov, "ms_per_step": round(ms, 3),
@@ -673,7 +674,7 @@ def run_propagation(name, nsteps=4, dt=0.02, krylov=12, with_cpu=True):
            "effective_gupdates_per_s": round(sig * updates / (ms * 1e-3) / 1e9, 1),
            "norm_drift": abs(norm - 1.0), "max_error_indicator": float(diag[:, 0].max()),
            "energy_per_step": [round(float(x), 10) for x in diag[:, 1]],
-           "field": "0.05 sin(0.8 t), position-like one-body coupling"}
+           "field": "0.05 sin(0.8 t), position-like one-body coupling", "route_fp64": route}
     if with_cpu:
         # the oracle's row-wise sigma on a bounded sample, scaled to the sigma work of one step
         o, nrow, times, cores = cpu_baseline(wl, wl["tau"], target_s=8.0, steps=1)
@@ -853,6 +854,10 @@ def main():
         if rank == 0 and line:
             print(json.dumps(line))
         return
+    if args.propagation_only or args.density_only:
+        from paper_1609_07757_gb300 import _lib as L
+        L.iscsi_set_option("autotune", args.autotune)
+        L.iscsi_set_option("tc_cluster", args.tc_cluster)
     if args.propagation_only:
         # the propagation leg alone (profiling its launches)
         if rank == 0:

@@ -80,15 +80,18 @@ struct PrCtl {
   double y[kPrMaxKrylov][2];   // combination coefficients of the step's result
 };
 
-// sums the partial products in block order; mode 0: h[k] = sum (a Gram-Schmidt
-// pass; alpha[j] += Re h[j] with j = nk - 1); mode 1: beta[j] = sqrt(sum_re);
-// mode 2: beta0 = sqrt(sum_re)
+// sums the partial products, one warp per (k, re/im) with a fixed reduction
+// order (lane l takes blocks l, l + 32, ..., then a shuffle tree);
+// mode 0: h[k] = sum (a Gram-Schmidt pass; alpha[j] += Re h[j] with j = nk - 1);
+// mode 1: beta[j] = sqrt(sum_re); mode 2: beta0 = sqrt(sum_re)
 __global__ void k_pr_sum(const double* __restrict__ part, int parts, int nk, int mode, int j, PrCtl* __restrict__ ctl) {
-  const int t = threadIdx.x;
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (t >= 2 * nk) return;
   const int k = t >> 1, c = t & 1;
   double s = 0.0;
-  for (int b = 0; b < parts; ++b) s += part[((long long)b * nk + k) * 2 + c];
+  for (int b = lane; b < parts; b += 32) s += part[((long long)b * nk + k) * 2 + c];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane != 0) return;
   if (mode == 0) {
     ctl->h[k][c] = s;
     if (k == nk - 1 && c == 0) ctl->alpha[j] += s;
@@ -229,18 +232,18 @@ static int propagate_steps(Context& ctx, Context* cpl, double* c, int nsteps, do
     ISCSI_CUDA(cudaMemsetAsync(ctl, 0, sizeof(PrCtl), st));
     // q_0 = c / |c|
     k_pr_dots<<<kPrBlocks, kPrThreads, 0, st>>>(c, 0, 1, c, nc, N, part); ISCSI_COUNT_LAUNCH();
-    k_pr_sum<<<1, 2, 0, st>>>(part, kPrBlocks, 1, 2, 0, ctl); ISCSI_COUNT_LAUNCH();
+    k_pr_sum<<<1, 64, 0, st>>>(part, kPrBlocks, 1, 2, 0, ctl); ISCSI_COUNT_LAUNCH();
     k_pr_scale<<<pr_blocks(qs), kPrThreads, 0, st>>>(c, Q, qs, ctl, -1); ISCSI_COUNT_LAUNCH();
     for (int j = 0; j < m; ++j) {
       double* qj = Q + (size_t)j * qs;
       ISCSI_TRY(sigma_run(ctx, qj, W, nc, prec));
       for (int pass = 0; pass < 2; ++pass) {
         k_pr_dots<<<kPrBlocks, kPrThreads, 0, st>>>(Q, qs, j + 1, W, nc, N, part); ISCSI_COUNT_LAUNCH();
-        k_pr_sum<<<1, 2 * (j + 1), 0, st>>>(part, kPrBlocks, j + 1, 0, j, ctl); ISCSI_COUNT_LAUNCH();
+        k_pr_sum<<<(2 * (j + 1) + 7) / 8, 256, 0, st>>>(part, kPrBlocks, j + 1, 0, j, ctl); ISCSI_COUNT_LAUNCH();
         k_pr_update<<<gb, kPrThreads, 0, st>>>(Q, qs, j + 1, W, nc, N, ctl); ISCSI_COUNT_LAUNCH();
       }
       k_pr_dots<<<kPrBlocks, kPrThreads, 0, st>>>(W, 0, 1, W, nc, N, part); ISCSI_COUNT_LAUNCH();
-      k_pr_sum<<<1, 2, 0, st>>>(part, kPrBlocks, 1, 1, j, ctl); ISCSI_COUNT_LAUNCH();
+      k_pr_sum<<<1, 64, 0, st>>>(part, kPrBlocks, 1, 1, j, ctl); ISCSI_COUNT_LAUNCH();
       if (j + 1 < m) {
         k_pr_scale<<<pr_blocks(qs), kPrThreads, 0, st>>>(W, Q + (size_t)(j + 1) * qs, qs, ctl, j); ISCSI_COUNT_LAUNCH();
       }

@@ -58,3 +58,71 @@ def test_fullsize_sampled_rows(name):
     scale = np.abs(s).max()
     err = np.abs(s[rows] - ref).max()
     assert err <= 1e-12 * scale, (err, scale)
+
+
+def test_fullsize_density_matrices():
+    """Full CI n = 60 (the benchmark's density workload): sampled elements of d1
+    and d2 against the oracle's element-wise route, the traces of a unit vector,
+    and <c|H|c> from the densities against c . sigma."""
+    n, k, ell, nchol, box, seed, tau, nd = FULL["fci_n60_tau1e-14"]
+    h1, eri = make_integrals(n, seed, ell=ell, nchol=nchol, box=box)
+    L.iscsi_init(n, 2, 2, k, h1, eri, 0.0)
+    c = unit_vector(nd, 23)
+    ct = torch.tensor(c, dtype=torch.float64, device="cuda")
+    d1 = torch.empty((2, n, n), dtype=torch.float64, device="cuda")
+    d2 = torch.empty((3, n, n, n, n), dtype=torch.float64, device="cuda")
+    L.iscsi_density(ct, None, d1, d2)
+    st = torch.empty_like(ct)
+    L.iscsi_sigma(ct, st, 1)
+    torch.cuda.synchronize()
+    for b, want in ((0, 2.0), (1, 4.0), (2, 2.0)):
+        assert abs(float(torch.einsum("pprr->", d2[b])) - want) <= 1e-12
+    from oracle import jordan_wigner as jw
+    g = torch.as_tensor(jw.unpack_eri(eri, n), device="cuda")
+    h = torch.as_tensor(h1, device="cuda")
+    e_dm = float((h * (d1[0] + d1[1])).sum() + 0.5 * (g * (d2[0] + d2[2])).sum() + (g * d2[1]).sum())
+    e_sig = float(torch.dot(ct, st))
+    assert abs(e_dm - e_sig) <= 1e-10 * max(1.0, abs(e_sig))
+    o = Oracle(n, 2, 2, k, 0.0, h1, eri)
+    rng = np.random.default_rng(4)
+    m = 48
+    spec = np.column_stack([rng.integers(0, 5, m)] + [rng.integers(0, n, m) for _ in range(4)])
+    spec[:8, 1:] = [[0, 0, 1, 1], [0, 1, 1, 0], [1, 0, 0, 1], [2, 2, 0, 0], [0, 2, 1, 3], [5, 5, 7, 7],
+                    [59, 58, 57, 56], [1, 1, 59, 59]]  # some elements the reference occupies
+    ref = o.density_elems(c, None, spec)
+    g1, g2 = d1.cpu().numpy(), d2.cpu().numpy()
+    got = np.array([g2[b, p, q, r, t] if b < 3 else g1[b - 3, p, q] for b, p, q, r, t in spec])
+    scale = max(np.abs(g2).max(), np.abs(g1).max())
+    assert np.abs(got - ref).max() <= 1e-12 * scale
+
+
+def test_fullsize_propagation():
+    """Full CI n = 60, one real-time step with a field: unitary (norm kept), the
+    step's energy is <c|H + f V|c>, and Krylov dimensions 12 and 16 agree within
+    the error indicator of the smaller one."""
+    n, k, ell, nchol, box, seed, tau, nd = FULL["fci_n60_tau1e-14"]
+    h1, eri = make_integrals(n, seed, ell=ell, nchol=nchol, box=box)
+    v = np.diag(np.arange(n) - (n - 1) / 2.0) / n + 0.05 * (np.eye(n, k=1) + np.eye(n, k=-1))
+    L.iscsi_init(n, 2, 2, k, v, None, tau)
+    hv = L.iscsi_ctx_current()
+    c0 = torch.tensor(unit_vector(nd, 29), dtype=torch.float64, device="cuda")
+    s0 = torch.empty_like(c0)
+    L.iscsi_sigma(c0, s0, 1)
+    ev = float(torch.dot(c0, s0))  # <c|V|c>
+    L.iscsi_init(n, 2, 2, k, h1, eri, tau)
+    L.iscsi_sigma(c0, s0, 1)
+    f = 0.05
+    e0 = float(torch.dot(c0, s0)) + f * ev  # <c|H + f V|c>
+    out, ind = [], []
+    for m in (12, 16):
+        x = torch.zeros((2, nd), dtype=torch.float64, device="cuda")
+        x[0] = c0
+        diag = L.iscsi_propagate(x, 1, 0.02, np.array([f]), hv, m)
+        torch.cuda.synchronize()
+        assert abs(float(torch.linalg.norm(x)) - 1.0) <= 1e-12
+        assert abs(diag[0, 1] - e0) <= 1e-11 * max(1.0, abs(e0))
+        out.append(x)
+        ind.append(diag[0, 0])
+    # the Krylov error indicator of the smaller space bounds the difference (with margin)
+    assert float(torch.linalg.norm(out[0] - out[1])) <= 10.0 * ind[0] + 1e-13
+    assert ind[0] <= 1e-10 and ind[1] <= 1e-13
