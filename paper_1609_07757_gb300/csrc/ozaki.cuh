@@ -23,7 +23,7 @@
 //   weight makes that bias negligible over the whole K.  Relative error
 //   ~2^-48 of sum_k |x_k||y_k| (slice truncation, dropped levels, tail).
 //
-// Tile: 128 rows of A x 64 rows of B per CTA, K step 16, 4-stage TMA ring.
+// Tile: 128 rows of A x 64 rows of B per CTA, K step 16, OZ_STAGES-deep TMA ring.
 // TMEM holds level L at columns 64L .. 64L+63 (L = 0..6), so the products
 // A_t x (B_0 .. B_{6-t}) of one A slice land on consecutive levels and go out
 // as one MMA of N = 64 (7 - t) columns (split at 256): 10 MMAs per K step
@@ -78,7 +78,7 @@ __global__ void k_oz_slice(const double* __restrict__ X, int rows, int cols, lon
 }
 
 // Warp-specialised product kernel.  Per CTA one 128 x 64 output tile:
-//   warp 0     (one lane) loads K steps into a 4-stage ring: two TMA boxes
+//   warp 0     (one lane) loads K steps into an OZ_STAGES-deep ring: two TMA boxes
 //              (all slices of A, all slices of B) per step, completion as
 //              transaction bytes on full[stage],
 //   warp 1     (one lane) waits full[stage], issues the MMAs of the step,
