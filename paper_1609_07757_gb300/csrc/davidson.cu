@@ -83,6 +83,55 @@ __device__ __forceinline__ double block_sum(double x, double* red) {
   return t;  // valid in thread 0
 }
 
+// ---------------------------------------------------------------------------
+// FP64-accurate products on the FP32 units.  GB300 issues FP64 at about 1/64
+// of its FP32 rate, so the tall-skinny products of the iteration (projections,
+// Ritz vectors, restarts) are formed in double-float arithmetic: each double
+// is split exactly into a float pair (hi = its leading 24 significant bits,
+// lo = the rest rounded, 2^-48 relative), a product is the exact product of the
+// high parts (fmaf gives its rounding error) plus the cross terms in FP32, and
+// a sum is a float pair renormalised after every term by Knuth's error-free
+// two-sum (about 3e-14 of sum |x y| over a thread's few hundred terms, which
+// FP64 sums of the same length match).  Magnitudes below 2^-126 (the float
+// range) are flushed to zero, far below the iteration's tolerances for the
+// unit-norm basis and its images.  Reductions across threads stay FP64.
+struct Df {
+  float s, c;
+};
+
+__device__ __forceinline__ void df_split(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  const unsigned int sgn = (unsigned int)(b >> 63) << 31;
+  const int eh = E - 1023 + 127;
+  if (eh < 1 || eh > 254) {
+    hi = 0.0f;
+    lo = 0.0f;
+    return;
+  }
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  hi = __uint_as_float(sgn | ((unsigned int)eh << 23) | (unsigned int)(m >> 29));
+  const int el = E - 1075 + 127;  // the low 29 bits L are worth L 2^(E - 1075)
+  const float l = el >= 1 ? __fmul_rn(__int2float_rn((int)(m & 0x1FFFFFFFull)), __uint_as_float((unsigned int)el << 23))
+                          : 0.0f;
+  lo = sgn ? -l : l;
+}
+
+__device__ __forceinline__ void df_fma(Df& a, float xh, float xl, float yh, float yl) {
+  const float p = __fmul_rn(xh, yh);
+  const float e = __fmaf_rn(xh, yh, -p);                 // xh yh - p, exact
+  const float cr = __fmaf_rn(xh, yl, __fmul_rn(xl, yh));  // cross terms
+  const float s = __fadd_rn(a.s, p);                     // two-sum of a.s and p
+  const float bb = __fsub_rn(s, a.s);
+  const float t = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  const float c = __fadd_rn(a.c, __fadd_rn(t, __fadd_rn(e, cr)));
+  const float s2 = __fadd_rn(s, c);                      // renormalise
+  a.c = __fsub_rn(c, __fsub_rn(s2, s));
+  a.s = s2;
+}
+
+__device__ __forceinline__ double df_value(const Df& a) { return (double)a.s + (double)a.c; }
+
 // partial[b][i][j] = sum over block b's elements of A_i[e] B_j[e], for
 // i < na = (na_dev ? *na_dev : 0) + na_add and j < nb; rows_cap bounds na.
 // Each block takes kDotT rows of A and NB columns of B (NB = nb when nb <= 8,
@@ -99,22 +148,23 @@ __global__ void __launch_bounds__(kVecThreads) k_tsdots(const double* __restrict
   const int i0 = (blockIdx.y / tiles_b) * kDotT, j0 = (blockIdx.y % tiles_b) * NB;
   if (i0 >= na) return;
   const int ra = min(kDotT, na - i0);
-  double acc[kDotT][NB];
+  Df acc[kDotT][NB];
 #pragma unroll
   for (int a = 0; a < kDotT; ++a)
 #pragma unroll
-    for (int b = 0; b < NB; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < NB; ++b) acc[a][b] = Df{0.0f, 0.0f};
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
-    double vb[NB];
+    float bh[NB], bl[NB];
 #pragma unroll
-    for (int b = 0; b < NB; ++b) vb[b] = (j0 + b < nb) ? B[(long long)(j0 + b) * N + e] : 0.0;
+    for (int b = 0; b < NB; ++b) df_split((j0 + b < nb) ? B[(long long)(j0 + b) * N + e] : 0.0, bh[b], bl[b]);
 #pragma unroll
     for (int a = 0; a < kDotT; ++a)
       if (a < ra) {
-        const double va = A[(long long)(i0 + a) * N + e];
+        float ah, al;
+        df_split(A[(long long)(i0 + a) * N + e], ah, al);
 #pragma unroll
-        for (int b = 0; b < NB; ++b) acc[a][b] = fma(va, vb[b], acc[a][b]);
+        for (int b = 0; b < NB; ++b) df_fma(acc[a][b], ah, al, bh[b], bl[b]);
       }
   }
   __shared__ double red[kVecThreads / 32][kDotT * NB];
@@ -123,7 +173,7 @@ __global__ void __launch_bounds__(kVecThreads) k_tsdots(const double* __restrict
   for (int a = 0; a < kDotT; ++a)
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-      double x = acc[a][b];
+      double x = df_value(acc[a][b]);
       for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
       if (lane == 0) red[warp][a * NB + b] = x;
     }
@@ -155,12 +205,15 @@ __global__ void __launch_bounds__(kVecThreads) k_dav_ritz(const double* __restri
                                                           const DavCtl* __restrict__ ctl, const double* __restrict__ Y,
                                                           int ldy, int j0, long long N, double* __restrict__ X,
                                                           double* __restrict__ R, double* __restrict__ partial) {
-  extern __shared__ double sY[];  // [m][KC]
+  extern __shared__ float sYf[];  // [2][m][KC]: Y split into float pairs
   __shared__ double red[kVecThreads / 32];
   const int m = ctl->m, k = ctl->k;
   const int cnt = min(KC, k - j0);
   if (cnt <= 0) return;
-  for (int t = threadIdx.x; t < m * KC; t += blockDim.x) sY[t] = (t % KC < cnt) ? Y[(t / KC) * ldy + j0 + t % KC] : 0.0;
+  float* sYh = sYf;
+  float* sYl = sYf + m * KC;
+  for (int t = threadIdx.x; t < m * KC; t += blockDim.x)
+    df_split((t % KC < cnt) ? Y[(t / KC) * ldy + j0 + t % KC] : 0.0, sYh[t], sYl[t]);
   double th[KC];
 #pragma unroll
   for (int j = 0; j < KC; ++j) th[j] = j < cnt ? ctl->theta[j0 + j] : 0.0;
@@ -170,22 +223,25 @@ __global__ void __launch_bounds__(kVecThreads) k_dav_ritz(const double* __restri
   for (int j = 0; j < KC; ++j) rr[j] = 0.0;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
-    double x[KC], r[KC];
+    Df x[KC], r[KC];
 #pragma unroll
-    for (int j = 0; j < KC; ++j) x[j] = r[j] = 0.0;
+    for (int j = 0; j < KC; ++j) x[j] = r[j] = Df{0.0f, 0.0f};
     for (int i = 0; i < m; ++i) {
-      const double v = V[(long long)i * N + e], w = W[(long long)i * N + e];
+      float vh, vl, wh, wl;
+      df_split(V[(long long)i * N + e], vh, vl);
+      df_split(W[(long long)i * N + e], wh, wl);
 #pragma unroll
       for (int j = 0; j < KC; ++j) {
-        x[j] = fma(v, sY[i * KC + j], x[j]);
-        r[j] = fma(w, sY[i * KC + j], r[j]);
+        df_fma(x[j], vh, vl, sYh[i * KC + j], sYl[i * KC + j]);
+        df_fma(r[j], wh, wl, sYh[i * KC + j], sYl[i * KC + j]);
       }
     }
 #pragma unroll
     for (int j = 0; j < KC; ++j)
       if (j < cnt) {
-        const double rv = r[j] - th[j] * x[j];
-        X[(long long)(j0 + j) * N + e] = x[j];
+        const double xv = df_value(x[j]);
+        const double rv = df_value(r[j]) - th[j] * xv;
+        X[(long long)(j0 + j) * N + e] = xv;
         R[(long long)(j0 + j) * N + e] = rv;
         rr[j] = fma(rv, rv, rr[j]);
       }
@@ -204,26 +260,30 @@ __global__ void __launch_bounds__(kVecThreads) k_dav_restart_lincomb(const doubl
                                                                      const DavCtl* __restrict__ ctl,
                                                                      const double* __restrict__ Y, int ldy, int j0,
                                                                      long long N, double* __restrict__ out) {
-  extern __shared__ double sYc[];
+  extern __shared__ float sYcf[];  // [2][m][KC]
   if (!ctl->restart) return;
   const int m = ctl->m;
   const int cnt = min(KC, ctl->nkeep - j0);
   if (cnt <= 0) return;
-  for (int t = threadIdx.x; t < m * KC; t += blockDim.x) sYc[t] = (t % KC < cnt) ? Y[(t / KC) * ldy + j0 + t % KC] : 0.0;
+  float* sYh = sYcf;
+  float* sYl = sYcf + m * KC;
+  for (int t = threadIdx.x; t < m * KC; t += blockDim.x)
+    df_split((t % KC < cnt) ? Y[(t / KC) * ldy + j0 + t % KC] : 0.0, sYh[t], sYl[t]);
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
-    double acc[KC];
+    Df acc[KC];
 #pragma unroll
-    for (int j = 0; j < KC; ++j) acc[j] = 0.0;
+    for (int j = 0; j < KC; ++j) acc[j] = Df{0.0f, 0.0f};
     for (int i = 0; i < m; ++i) {
-      const double v = V[(long long)i * N + e];
+      float vh, vl;
+      df_split(V[(long long)i * N + e], vh, vl);
 #pragma unroll
-      for (int j = 0; j < KC; ++j) acc[j] = fma(v, sYc[i * KC + j], acc[j]);
+      for (int j = 0; j < KC; ++j) df_fma(acc[j], vh, vl, sYh[i * KC + j], sYl[i * KC + j]);
     }
 #pragma unroll
     for (int j = 0; j < KC; ++j)
-      if (j < cnt) out[(long long)(j0 + j) * N + e] = acc[j];
+      if (j < cnt) out[(long long)(j0 + j) * N + e] = df_value(acc[j]);
   }
 }
 
@@ -296,24 +356,28 @@ __global__ void __launch_bounds__(kVecThreads) k_dav_project(const double* __res
                                                              const DavCtl* __restrict__ ctl,
                                                              const double* __restrict__ C, long long N,
                                                              double* __restrict__ T, const int* __restrict__ gate) {
-  extern __shared__ double sC[];  // [m][KC]
+  extern __shared__ float sCf[];  // [2][m][KC]
   if (gate && !*gate) return;
   const int m = ctl->m, k = ctl->k;
-  for (int t = threadIdx.x; t < m * KC; t += blockDim.x) sC[t] = (t % KC < k) ? C[(t / KC) * k + t % KC] : 0.0;
+  float* sCh = sCf;
+  float* sCl = sCf + m * KC;
+  for (int t = threadIdx.x; t < m * KC; t += blockDim.x)
+    df_split((t % KC < k) ? C[(t / KC) * k + t % KC] : 0.0, sCh[t], sCl[t]);
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
-    double acc[KC];
+    Df acc[KC];
 #pragma unroll
-    for (int j = 0; j < KC; ++j) acc[j] = 0.0;
+    for (int j = 0; j < KC; ++j) acc[j] = Df{0.0f, 0.0f};
     for (int i = 0; i < m; ++i) {
-      const double v = V[(long long)i * N + e];
+      float vh, vl;
+      df_split(V[(long long)i * N + e], vh, vl);
 #pragma unroll
-      for (int j = 0; j < KC; ++j) acc[j] = fma(v, sC[i * KC + j], acc[j]);
+      for (int j = 0; j < KC; ++j) df_fma(acc[j], vh, vl, sCh[i * KC + j], sCl[i * KC + j]);
     }
 #pragma unroll
     for (int j = 0; j < KC; ++j)
-      if (j < k) T[(long long)j * N + e] -= acc[j];
+      if (j < k) T[(long long)j * N + e] -= df_value(acc[j]);
   }
 }
 
@@ -664,7 +728,9 @@ __global__ void k_unit_vectors(double* __restrict__ V, const long long* __restri
 
 namespace {
 
-int kc_for(int k) { return k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32; }
+// column block of the lincomb kernels: k itself up to 8 (no work on absent
+// columns), else 16 or 32
+int kc_for(int k) { return k <= 8 ? std::max(k, 1) : k <= 16 ? 16 : 32; }
 
 struct Dav {
   Context& ctx;
@@ -787,7 +853,13 @@ struct Dav {
   }
   void ritz() {
     switch (kc) {
+      case 1: ritz_t<1>(); break;
+      case 2: ritz_t<2>(); break;
+      case 3: ritz_t<3>(); break;
       case 4: ritz_t<4>(); break;
+      case 5: ritz_t<5>(); break;
+      case 6: ritz_t<6>(); break;
+      case 7: ritz_t<7>(); break;
       case 8: ritz_t<8>(); break;
       case 16: ritz_t<16>(); break;
       default: ritz_t<32>(); break;
@@ -795,7 +867,13 @@ struct Dav {
   }
   void transform() {
     switch (kc) {
+      case 1: transform_t<1>(); break;
+      case 2: transform_t<2>(); break;
+      case 3: transform_t<3>(); break;
       case 4: transform_t<4>(); break;
+      case 5: transform_t<5>(); break;
+      case 6: transform_t<6>(); break;
+      case 7: transform_t<7>(); break;
       case 8: transform_t<8>(); break;
       case 16: transform_t<16>(); break;
       default: transform_t<32>(); break;
@@ -803,7 +881,13 @@ struct Dav {
   }
   void restart() {
     switch (kc) {
+      case 1: restart_t<1>(); break;
+      case 2: restart_t<2>(); break;
+      case 3: restart_t<3>(); break;
       case 4: restart_t<4>(); break;
+      case 5: restart_t<5>(); break;
+      case 6: restart_t<6>(); break;
+      case 7: restart_t<7>(); break;
       case 8: restart_t<8>(); break;
       case 16: restart_t<16>(); break;
       default: restart_t<32>(); break;
@@ -811,7 +895,13 @@ struct Dav {
   }
   void project(const double* C, const int* gate = nullptr) {
     switch (kc) {
+      case 1: project_t<1>(C, gate); break;
+      case 2: project_t<2>(C, gate); break;
+      case 3: project_t<3>(C, gate); break;
       case 4: project_t<4>(C, gate); break;
+      case 5: project_t<5>(C, gate); break;
+      case 6: project_t<6>(C, gate); break;
+      case 7: project_t<7>(C, gate); break;
       case 8: project_t<8>(C, gate); break;
       case 16: project_t<16>(C, gate); break;
       default: project_t<32>(C, gate); break;
@@ -887,7 +977,13 @@ struct Dav {
   int collapse(int prec, int cnt) {
     k_dav_request_restart<<<1, 32, 0, st>>>(ctl, cnt); ISCSI_COUNT_LAUNCH();
     switch (kc) {
+      case 1: restart_v<1>(); break;
+      case 2: restart_v<2>(); break;
+      case 3: restart_v<3>(); break;
       case 4: restart_v<4>(); break;
+      case 5: restart_v<5>(); break;
+      case 6: restart_v<6>(); break;
+      case 7: restart_v<7>(); break;
       case 8: restart_v<8>(); break;
       case 16: restart_v<16>(); break;
       default: restart_v<32>(); break;
