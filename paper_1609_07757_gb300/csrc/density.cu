@@ -22,8 +22,8 @@
 // diagonal region, the tiles right of each 128-row block's start) are computed.
 // An expansion kernel writes the n^4 tensors from the pair-indexed results.
 // d1 comes from d2's partial trace when d2 is computed for that spin (sum_r
-// d2_ss[p,q,r,r] = (N_s - 1) d1_s[p,q]), else from a direct kernel over the
-// one-hole strings.
+// d2_ss[p,q,r,r] = (N_s - 1) d1_s[p,q], summed by the expansion kernel), else
+// from a direct kernel over the one-hole strings.
 #include <algorithm>
 #include <climits>
 #include <cstring>
@@ -323,22 +323,63 @@ __device__ __forceinline__ double dm_value(const DmGather& g, int col, int row, 
 // that), takes the row exponent e with max |L[row][:]| 2^-e < 1 (0 for an
 // all-zero row, and for the padding rows) and writes the row's slices
 // out[s][row][k], zero padded.
+// With STAGED (the alpha-beta block with at most kDmStage hole strings per
+// spin) the row's lift entries -- a+_q |X> and a+_t |Y> for every X and Y,
+// with the target alpha string's offset and allowed beta count -- are staged
+// in shared memory first, so an element costs the hole-pair table and c.
 constexpr int kDmRowRegs = 16;
+constexpr int kDmStage = 256;
+struct DmStageRow {
+  int a[kDmStage], b[kDmStage], lim[kDmStage];
+  long long off[kDmStage];
+};
+
+template <bool STAGED>
+__device__ __forceinline__ double dm_row_value(const DmGather& g, const DmStageRow& S, int col, int row,
+                                               const double* __restrict__ c) {
+  if (!STAGED) return dm_value(g, col, row, c);
+  const int xy = g.hp_inv[col];
+  const int X = xy / g.nholeB, Y = xy - (xy / g.nholeB) * g.nholeB;
+  const int ea = S.a[X], eb = S.b[Y];
+  if (ea < 0 || eb < 0) return 0.0;
+  const int B = eb >> 1;
+  if (B >= S.lim[X]) return 0.0;
+  const double x = c[S.off[X] + B];
+  return ((ea ^ eb) & 1) ? -x : x;
+}
+
+template <bool STAGED>
 __global__ void __launch_bounds__(256) k_dm_lift_slice(DmGather g, int col_start, int ncol, int rows, int ld,
                                                        int rows_pad, const double* __restrict__ c,
                                                        int* __restrict__ e, __nv_bfloat16* __restrict__ out) {
   const int r = blockIdx.x;
   const long long total = (long long)rows_pad * ld;
+  __shared__ DmStageRow S;
+  if (STAGED && r < rows) {
+    const int qt = g.pair_of[r];
+    const int q = qt / g.n, t = qt - (qt / g.n) * g.n;
+    for (int X = threadIdx.x; X < g.nholeA; X += blockDim.x) {
+      const int ea = g.liftA[q * g.nholeA + X];
+      S.a[X] = ea;
+      if (ea >= 0) {
+        const int A = ea >> 1;
+        S.off[X] = g.off[A];
+        S.lim[X] = g.nballow[g.alevel[A]];
+      }
+    }
+    for (int Y = threadIdx.x; Y < g.nholeB; Y += blockDim.x) S.b[Y] = g.liftB[t * g.nholeB + Y];
+  }
+  __syncthreads();
   double v[kDmRowRegs];
   int m = 0;
 #pragma unroll
   for (int i = 0; i < kDmRowRegs; ++i) {
     const int k = threadIdx.x + i * blockDim.x;
-    v[i] = (r < rows && k < ncol) ? dm_value(g, col_start + k, r, c) : 0.0;
+    v[i] = (r < rows && k < ncol) ? dm_row_value<STAGED>(g, S, col_start + k, r, c) : 0.0;
     m = max(m, oz_exp_field(v[i]));
   }
   for (int k = threadIdx.x + kDmRowRegs * blockDim.x; k < ncol; k += blockDim.x)
-    if (r < rows) m = max(m, oz_exp_field(dm_value(g, col_start + k, r, c)));
+    if (r < rows) m = max(m, oz_exp_field(dm_row_value<STAGED>(g, S, col_start + k, r, c)));
   m = __reduce_max_sync(0xffffffffu, m);
   __shared__ int sm[8];
   __shared__ int ex_s;
@@ -363,7 +404,7 @@ __global__ void __launch_bounds__(256) k_dm_lift_slice(DmGather g, int col_start
     }
   }
   for (int k = threadIdx.x + kDmRowRegs * blockDim.x; k < ld; k += blockDim.x) {
-    const double x = (r < rows && k < ncol) ? dm_value(g, col_start + k, r, c) : 0.0;
+    const double x = (r < rows && k < ncol) ? dm_row_value<STAGED>(g, S, col_start + k, r, c) : 0.0;
     oz_digits(x, ex, a);
     oz_store_digits(a, row + k, total);
   }
@@ -431,31 +472,34 @@ __device__ __forceinline__ double dm_samespin(const DmExpand& E, int b, int p, i
 // one block per (p, q) and d2 block b: writes d2[b][p][q][r][t] for all (r, t),
 // consecutive threads on consecutive t (coalesced stores; the pair-indexed
 // reads are mostly consecutive within a level group)
-__global__ void __launch_bounds__(256) k_dm_expand(DmExpand E, double* __restrict__ d2) {
+// A same-spin block's (p, q) block also yields d1_s[p][q] = sum_r d2_ss[p,q,r,r]
+// / (N_s - 1) (written when d1 is given and N_s >= 2).
+__global__ void __launch_bounds__(256) k_dm_expand(DmExpand E, double* __restrict__ d2, double* __restrict__ d1) {
   const int n = E.n, p = blockIdx.x / n, q = blockIdx.x - (blockIdx.x / n) * n, b = blockIdx.y;
   const long long n2 = (long long)n * n;
   double* __restrict__ out = d2 + (long long)b * n2 * n2 + (long long)blockIdx.x * n2;
   const bool ab = b == 1 && E.na > 0 && E.nb > 0;
   const bool ss = b != 1 && (b == 0 ? E.na : E.nb) >= 2;
+  double tr = 0.0;
   for (int rt = threadIdx.x; rt < n * n; rt += blockDim.x) {
     const int r = rt / n, t = rt - (rt / n) * n;
     double v = 0.0;
     if (ab) v = dm_read(E.blk[1], E.pair_index[p * n + r], E.pair_index[q * n + t]);
     else if (ss) v = dm_samespin(E, b, p, q, r, t);
     out[rt] = v;
+    if (r == t) tr += v;
   }
-}
-
-// d1_s[p][q] = sum_r d2_ss[p,q,r,r] / (N_s - 1), for the spins with N_s >= 2
-__global__ void k_dm_gamma_trace(DmExpand E, int spin, double* __restrict__ d1) {
-  const int n = E.n;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n * n) return;
-  int p = i / n, q = i % n;
-  const int b = spin == 0 ? 0 : 2;
-  double acc = 0.0;
-  for (int r = 0; r < n; ++r) acc += dm_samespin(E, b, p, q, r, r);
-  d1[spin * n * n + i] = acc / (double)((spin == 0 ? E.na : E.nb) - 1);
+  if (!ss || !d1) return;
+  __shared__ double red[8];
+  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tr;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+    const int spin = b == 0 ? 0 : 1;
+    d1[(long long)spin * n2 + blockIdx.x] = sum / (double)((spin == 0 ? E.na : E.nb) - 1);
+  }
 }
 
 // d1_s[p][q] = sum_X s(p,X) s(q,X) sum_O bra[X u p, O] ket[X u q, O] over the
@@ -533,8 +577,13 @@ static int cut_operands(Context& ctx, const double* v, __nv_bfloat16* sl, int* e
     for (size_t i = 0; i < B.parts.size(); ++i) {
       const DmPart& pt = B.parts[i];
       int* e = ex + B.exp_off + i * B.R128;
-      k_dm_lift_slice<<<pt.rows_pad, 256, 0, st>>>(g, pt.col_start, pt.ncol, pt.rows, pt.ld, pt.rows_pad, v, e,
-                                                   sl + pt.sl_off); ISCSI_COUNT_LAUNCH();
+      if (b == 0 && g.nholeA <= kDmStage && g.nholeB <= kDmStage)
+        k_dm_lift_slice<true><<<pt.rows_pad, 256, 0, st>>>(g, pt.col_start, pt.ncol, pt.rows, pt.ld, pt.rows_pad, v,
+                                                           e, sl + pt.sl_off);
+      else
+        k_dm_lift_slice<false><<<pt.rows_pad, 256, 0, st>>>(g, pt.col_start, pt.ncol, pt.rows, pt.ld, pt.rows_pad,
+                                                            v, e, sl + pt.sl_off);
+      ISCSI_COUNT_LAUNCH();
     }
   }
   ISCSI_CUDA(cudaGetLastError());
@@ -654,14 +703,14 @@ int density_run(Context& ctx, const double* bra, const double* ket, double* d1, 
         dim3 grid((R.R + 31) / 32, (R.R + 31) / 32);
         k_dm_mirror<<<grid, 256, 0, st>>>(R, const_cast<double*>(R.q)); ISCSI_COUNT_LAUNCH();
       }
-    k_dm_expand<<<dim3(n * n, 3), 256, 0, st>>>(E, d2); ISCSI_COUNT_LAUNCH();
+    k_dm_expand<<<dim3(n * n, 3), 256, 0, st>>>(E, d2, d1); ISCSI_COUNT_LAUNCH();
     ISCSI_CUDA(cudaGetLastError());
   }
   if (d1) {
     for (int s = 0; s < 2; ++s) {
       const int ne = s == 0 ? ctx.na : ctx.nb;
       if (d2 && ne >= 2) {
-        k_dm_gamma_trace<<<launch_blocks((long long)n * n, 128), 128, 0, st>>>(E, s, d1); ISCSI_COUNT_LAUNCH();
+        // written by the expansion
       } else if (ne == 0) {
         ISCSI_CUDA(cudaMemsetAsync(d1 + (size_t)s * n * n, 0, sizeof(double) * n * n, st));
       } else {
