@@ -27,6 +27,7 @@ constexpr int OZ_TMEM_COLS = 512;  // 7 levels x 64 columns used
 constexpr long long OZ_SPIN = 1ll << 24;
 
 constexpr int OZ_MAX_SEGS = 8;
+constexpr int OZ_BW_ROWS = 128;    // rows of B per 128-column tile; B arrays are padded to this
 
 // One operand pair of a product: A[M][K] and B[N][K], both read through TMA
 // from K-major slice arrays [S][rows][ld] (bf16).  The segment's block starts
@@ -49,6 +50,7 @@ struct OzSeg {
 struct OzMaps {
   CUtensorMap a, b;
   CUtensorMap ah;  // A in boxes of 16 x 64 rows x 1 slice (half tiles, two-CTA clusters)
+  CUtensorMap bw;  // B in boxes of 16 x OZ_BW_ROWS rows x all slices (128-column tiles, tc32w.cuh)
 };
 
 // T[M][N] (FP64, ldt) (+)= sum over segments of A_seg B_seg^T; T is the

@@ -26,6 +26,7 @@
 #include "internal.cuh"
 #include "ozaki.cuh"
 #include "tc32.cuh"
+#include "tc32w.cuh"
 #include "tma_map.h"
 
 namespace iscsi {
@@ -184,6 +185,8 @@ static int tc_attr() {
     ISCSI_CUDA(cudaFuncSetAttribute(k_oz_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES));
     ISCSI_CUDA(cudaFuncSetAttribute(k_tc32_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, T3_SMEM_BYTES));
     ISCSI_CUDA(cudaFuncSetAttribute(k_tc32_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, T3_SMEM_BYTES));
+    ISCSI_CUDA(cudaFuncSetAttribute(k_tc32w_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, T3W_SMEM_BYTES));
+    ISCSI_CUDA(cudaFuncSetAttribute(k_tc32w_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, T3W_SMEM_BYTES));
     done = true;
   }
   return kOk;
@@ -239,7 +242,8 @@ static int add_seg(OzJob& job, const SliceArray& A, int a_row0, int a_k0, const 
   std::memset(&m, 0, sizeof(m));
   if (oz_encode_map(&m.a, A.base, A.ld, A.rows, nslice, A.slice, OZ_BM) ||
       oz_encode_map(&m.b, B.base, B.ld, B.rows, nslice, B.slice, OZ_BN) ||
-      oz_encode_map(&m.ah, A.base, A.ld, A.rows, nslice, A.slice, OZ_BM / 2, 1)) {
+      oz_encode_map(&m.ah, A.base, A.ld, A.rows, nslice, A.slice, OZ_BM / 2, 1) ||
+      oz_encode_map(&m.bw, B.base, B.ld, B.rows, nslice, B.slice, OZ_BW_ROWS)) {
     set_error("tensor-core sigma: TMA descriptor rejected");
     return kErrCuda;
   }
@@ -300,10 +304,10 @@ static int launch_job(Context& ctx, const OzJob& job, double* tbase, cudaStream_
 
 // tile numbering of a problem list; with cl = 2 every problem gets an even
 // number of column tiles (a cluster's two CTAs share a row block)
-static int add_tiles(std::vector<OzProblem>& probs, int cl = 1) {
+static int add_tiles(std::vector<OzProblem>& probs, int cl = 1, int bn = OZ_BN) {
   int tiles = 0;
   for (auto& p : probs) {
-    p.tiles_n = round_up(round_up(p.N, OZ_BN) / OZ_BN, cl);
+    p.tiles_n = round_up(round_up(p.N, bn) / bn, cl);
     p.tile_begin = tiles;
     tiles += (round_up(p.M, OZ_BM) / OZ_BM) * p.tiles_n;
   }
@@ -326,7 +330,7 @@ static TcTable ab_table(const Context& ctx, int nvec, long long* bs_elems, long 
     C.ncols = cc.ncol * nvec;
     C.krows = cc.krows;
     C.kpad = round_up(cc.krows, OZ_BK);
-    C.npad = round_up(C.ncols, OZ_BN);
+    C.npad = round_up(C.ncols, OZ_BW_ROWS);
     C.hp_start = ctx.hp_class_start[cl];
     C.bs_off = bs;
     C.exp_off = ex;
@@ -475,7 +479,7 @@ static int tc_prepare_m(Context& ctx, bool cut_only = false) {
     // (or the symmetric alpha matrix when shared)
     const double* Mb = ctx.beta_alias ? ctx.M64[0].as<double>() : ctx.M64[1].as<double>();
     int trans = ctx.beta_alias ? 0 : 1;
-    ctx.oz_mb_rows = round_up(SB.count, OZ_BN);
+    ctx.oz_mb_rows = round_up(SB.count, OZ_BW_ROWS);
     ctx.oz_mb_ld = round_up(SB.count, OZ_BK);
     if (!cut_only) {
       ISCSI_TRY(ctx.oz_mbs.alloc(sizeof(__nv_bfloat16) * OZ_S * (size_t)ctx.oz_mb_rows * ctx.oz_mb_ld));
@@ -510,7 +514,7 @@ static std::vector<SsBlock> ss_blocks(const Context& ctx, long long* elems, long
     if (b.rows == 0 || b.nba == 0) continue;
     b.obase = ctx.off_h[b.start];
     // C_a^T (alpha part operand): rows = beta strings, K = alpha strings of the block
-    b.bt_rows = round_up(b.nba, OZ_BN);
+    b.bt_rows = round_up(b.nba, OZ_BW_ROWS);
     b.bt_ld = round_up(b.rows, OZ_BK);
     b.bt_off = e;
     e += (long long)nslice * b.bt_rows * b.bt_ld;
@@ -637,8 +641,8 @@ static int launch_t3(int cl, int tiles, const OzProblem* probs, int nprobs, cons
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3(tiles, 1, 1);
-    cfg.blockDim = dim3(T3_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = T3_SMEM_BYTES;
+    cfg.blockDim = dim3(T3W_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = T3W_SMEM_BYTES;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -647,9 +651,9 @@ static int launch_t3(int cl, int tiles, const OzProblem* probs, int nprobs, cons
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    ISCSI_CUDA(cudaLaunchKernelEx(&cfg, k_tc32_gemm<2>, probs, nprobs, segs, maps, tbase, tbases, err)); ISCSI_COUNT_LAUNCH();
+    ISCSI_CUDA(cudaLaunchKernelEx(&cfg, k_tc32w_gemm<2>, probs, nprobs, segs, maps, tbase, tbases, err)); ISCSI_COUNT_LAUNCH();
   } else {
-    k_tc32_gemm<1><<<tiles, T3_THREADS, T3_SMEM_BYTES, st>>>(probs, nprobs, segs, maps, tbase, tbases, err); ISCSI_COUNT_LAUNCH();
+    k_tc32w_gemm<1><<<tiles, T3W_THREADS, T3W_SMEM_BYTES, st>>>(probs, nprobs, segs, maps, tbase, tbases, err); ISCSI_COUNT_LAUNCH();
   }
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
@@ -710,7 +714,7 @@ int opposite_tc32_operands(Context& ctx, const float* c, float* ttw, int nvec) {
       job.probs.push_back(P);
     }
     job.cl = cl;
-    job.tiles = add_tiles(job.probs, cl);
+    job.tiles = add_tiles(job.probs, cl, T3W_BN);
     ISCSI_TRY(upload_job(job, st));
     job.nvec = nvec;
     job.tbase = ttw;
@@ -765,7 +769,7 @@ static int t3_prepare_m(Context& ctx, bool cut_only = false) {
   if (ctx.nb > 0) {
     const double* Mb = ctx.beta_alias ? ctx.M64[0].as<double>() : ctx.M64[1].as<double>();
     int trans = ctx.beta_alias ? 0 : 1;
-    ctx.oz_mb_rows = round_up(SB.count, OZ_BN);
+    ctx.oz_mb_rows = round_up(SB.count, OZ_BW_ROWS);
     ctx.oz_mb_ld = round_up(SB.count, OZ_BK);
     if (!cut_only) ISCSI_TRY(ctx.t3_mbs.alloc(sizeof(__nv_bfloat16) * T3_S * (size_t)ctx.oz_mb_rows * ctx.oz_mb_ld));
     ISCSI_TRY(t3_slice_matrix<double>(Mb, SB.count, SB.count, SB.count, trans, nullptr, ctx.oz_mb_ld, ctx.oz_mb_rows,
@@ -825,7 +829,7 @@ int samespin_tc32_operands(Context& ctx, const float* c, float* sigma, int nvec)
         }
         if (P.seg_count > 0) job.probs.push_back(P);
       }
-    job.tiles = add_tiles(job.probs);
+    job.tiles = add_tiles(job.probs, 1, T3W_BN);
     ISCSI_TRY(upload_job(job, st));
     job.nvec = nvec;
   }
@@ -853,7 +857,7 @@ int samespin_tc32_gemm(Context& ctx, float* sigma) { return t3_launch(ctx, ctx.t
 // (one launch fills the GPU's waves better than two).  Rebuilt when either
 // source job changed; the same-spin problems take the opposite-spin job's
 // cluster shape.
-static int build_both(OzJob& both, const OzJob& ab, const OzJob& ss, cudaStream_t st) {
+static int build_both(OzJob& both, const OzJob& ab, const OzJob& ss, int bn, cudaStream_t st) {
   if (both.src_ver[0] == ab.version && both.src_ver[1] == ss.version && both.cl == ab.cl) return kOk;
   both.probs = ab.probs;
   both.segs = ab.segs;
@@ -866,7 +870,7 @@ static int build_both(OzJob& both, const OzJob& ab, const OzJob& ss, cudaStream_
   both.segs.insert(both.segs.end(), ss.segs.begin(), ss.segs.end());
   both.maps.insert(both.maps.end(), ss.maps.begin(), ss.maps.end());
   both.cl = ab.cl;
-  both.tiles = add_tiles(both.probs, both.cl);
+  both.tiles = add_tiles(both.probs, both.cl, bn);
   ISCSI_TRY(upload_job(both, st));
   both.src_ver[0] = ab.version;
   both.src_ver[1] = ss.version;
@@ -875,20 +879,21 @@ static int build_both(OzJob& both, const OzJob& ab, const OzJob& ss, cudaStream_
 
 const OzJob* both_tc_job(Context& ctx, int prec) {
   OzJob& both = prec == 64 ? ctx.oz_both : ctx.t3_both;
-  if (build_both(both, prec == 64 ? ctx.oz_ab : ctx.t3_ab, prec == 64 ? ctx.oz_ss : ctx.t3_ss, stream()) != kOk)
+  if (build_both(both, prec == 64 ? ctx.oz_ab : ctx.t3_ab, prec == 64 ? ctx.oz_ss : ctx.t3_ss,
+                 prec == 64 ? OZ_BN : T3W_BN, stream()) != kOk)
     return nullptr;
   return &both;
 }
 
 int both_tc_gemm(Context& ctx, double* sigma) {
   cudaStream_t st = stream();
-  ISCSI_TRY(build_both(ctx.oz_both, ctx.oz_ab, ctx.oz_ss, st));
+  ISCSI_TRY(build_both(ctx.oz_both, ctx.oz_ab, ctx.oz_ss, OZ_BN, st));
   return launch_job(ctx, ctx.oz_both, sigma, st);
 }
 
 int both_tc32_gemm(Context& ctx, float* sigma) {
   cudaStream_t st = stream();
-  ISCSI_TRY(build_both(ctx.t3_both, ctx.t3_ab, ctx.t3_ss, st));
+  ISCSI_TRY(build_both(ctx.t3_both, ctx.t3_ab, ctx.t3_ss, T3W_BN, st));
   return t3_launch(ctx, ctx.t3_both, sigma, st);
 }
 
