@@ -344,8 +344,8 @@ def run_ours(args, wl, ws, rank, local):
         # FP32 form: 6 of the 9 products of three bf16 terms per operand
         flops = (st["opposite_tc_bf16_flops"] + (st.get("samespin_tc_bf16_flops", 0.0) if both else 0.0)) * 6.0 / 28.0
         peak, peak_src = bf16_peak()
-        bound, kname, kkey = "tensor", "k_tc32_gemm<%d> (tcgen05, FP32-accurate %s, clusters of %d CTA)" % (
-            cl, what, cl), "k_tc32_gemm_cl%d%s_%s" % (cl, tag, args.workload)
+        bound, kname, kkey = "tensor", "k_tc32w_gemm<%d> (tcgen05, FP32-accurate %s, 128 x 128 tiles, " \
+            "clusters of %d CTA)" % (cl, what, cl), "k_tc32w_gemm_cl%d%s_%s" % (cl, tag, args.workload)
     else:
         flops = st["opposite_gemm_flops"]
         peak = FP64_PEAK_TFLOPS if args.precision == 64 else FP32_PEAK_TFLOPS
