@@ -3,7 +3,7 @@
 //
 // Each phase of the sigma step runs for every context in turn, except the two
 // tensor-core contractions: the opposite-spin products of all contexts form
-// one problem list and run as one k_oz_gemm (or k_tc32_gemm) launch, and so do
+// one problem list and run as one k_oz_gemm (or k_tc32w_gemm) launch, and so do
 // the same-spin level-block products.  Problems keep their per-context
 // output addressing through a table of output bases (OzProblem::tb).  From the
 // second call with the same contexts, vectors, vector count and precision,

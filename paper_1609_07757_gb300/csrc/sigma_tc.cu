@@ -16,7 +16,7 @@
 // G's, M_alpha's and M_beta's slices are built once per context (first use).
 //
 // The FP32 form (tc32.cuh) runs the same two contractions with three bf16
-// terms per element and FP32 accumulation (k_tc32_gemm): no exponents, no
+// terms per element and FP32 accumulation (k_tc32w_gemm): no exponents, no
 // exact levels; its operands come from the FP32 copy of the CI vector.
 #include <algorithm>
 #include <climits>
@@ -183,8 +183,6 @@ static int tc_attr() {
   if (!done) {
     ISCSI_CUDA(cudaFuncSetAttribute(k_oz_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES));
     ISCSI_CUDA(cudaFuncSetAttribute(k_oz_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES));
-    ISCSI_CUDA(cudaFuncSetAttribute(k_tc32_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, T3_SMEM_BYTES));
-    ISCSI_CUDA(cudaFuncSetAttribute(k_tc32_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, T3_SMEM_BYTES));
     ISCSI_CUDA(cudaFuncSetAttribute(k_tc32w_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, T3W_SMEM_BYTES));
     ISCSI_CUDA(cudaFuncSetAttribute(k_tc32w_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, T3W_SMEM_BYTES));
     done = true;
@@ -633,7 +631,7 @@ static int t3_slice_matrix(const V* X, int rows, int cols, long long ld, int tra
   return kOk;
 }
 
-// k_tc32_gemm over a problem list, in two-CTA clusters when cl = 2
+// k_tc32w_gemm over a problem list, in two-CTA clusters when cl = 2
 static int launch_t3(int cl, int tiles, const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
                      float* tbase, float* const* tbases, int* err, cudaStream_t st) {
   if (tiles == 0) return kOk;

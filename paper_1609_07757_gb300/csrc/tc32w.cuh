@@ -1,22 +1,26 @@
-// tc32w.cuh -- the FP32-form contraction (tc32.cuh) on 128 x 128 output
-// tiles, for half the operand traffic per product.
+// tc32w.cuh -- the FP32-form contraction T = A * B^T on the bf16 tensor
+// cores, 128 x 128 output tiles (arithmetic in tc32.cuh): three bf16 terms
+// per element, the six term pairs of order t + u <= 2, FP32 accumulation in
+// tensor memory over K chunks of 512 and round-to-nearest FP32 sums across
+// chunks in registers.
 //
-// Same arithmetic as k_tc32_gemm: three bf16 terms per element, the six term
-// pairs of order t + u <= 2, FP32 accumulation in tensor memory over K chunks
-// of 512 and round-to-nearest FP32 sums across chunks in registers.  The
-// 64-column tiles of k_tc32_gemm stream 18 KB of operands per 16-deep K step
-// for 0.79 M products, which leaves that kernel bound by the L2-to-SM traffic;
-// here a K step brings 24 KB for 1.57 M products.  To fit two accumulator
+// A 64-column tile streams 18 KB of operands per 16-deep K step for 0.79 M
+// products, which leaves the product bound by the L2-to-SM traffic; a
+// 128-column tile brings 24 KB for 1.57 M products.  To fit two accumulator
 // buffers of a 128-column tile into the 512 TMEM columns, the orders share
 // accumulators: order 0 (A_0 B_0) has its own 128 columns, orders 1 and 2
 // (five pairs, each at most 2^-8 of order 0) sum into a second 128; a buffer
-// is 256 columns, buffer b at 256 b.  Per K step: one MMA of N = 128 into the
+// is 256 columns, buffer b at 256 b, and the MMAs of chunk c + 1 run while
+// the epilogue drains chunk c.  Per K step: one MMA of N = 128 into the
 // order-0 columns and five into the others.
 //
-// Work split as in k_tc32_gemm: warp 0 loads (TMA; B in 128-row boxes), warp 1
-// issues the MMAs, warps 2-9 drain (two per TMEM lane quarter, 64 columns
-// each).  Problems, segments and tensor maps are the shared records (ozaki_types.cuh);
-// tiles are numbered with 128-column tiles (add_tiles with bn = 128).
+// Warp 0 loads (TMA; A in 128-row boxes, or two 64-row halves multicast to a
+// cluster pair; B in 128-row boxes), warp 1 issues the MMAs, warps 2-9 drain
+// (two per TMEM lane quarter, 64 columns each).  Problems, segments and
+// tensor maps are the shared records (ozaki_types.cuh); tiles are numbered
+// with 128-column tiles (add_tiles with bn = 128).  Every wait is bounded; a
+// wait that runs out sets abort, the CTA waits (bounded) for its copies in
+// flight, frees TMEM and reports through err.
 #pragma once
 #include <cuda_bf16.h>
 
