@@ -140,7 +140,10 @@ ISCSI_API iscsi_status iscsi_sigma_noalloc(const void* c, void* sigma);
 
 /*
  * Same as iscsi_sigma with HOST buffers: copies c to the device, computes,
- * copies sigma back and synchronises.  c, sigma: host, [nvec][ndet] FP64.
+ * copies sigma back and synchronises.  c, sigma: host, [nvec][ndet] FP64
+ * (page-locked memory gives the fastest copies).  The device staging buffers
+ * (2 nvec ndet doubles) stay with the context for later calls until it is
+ * destroyed.
  */
 ISCSI_API iscsi_status iscsi_sigma_host(const double* c, double* sigma, int nvec);
 
@@ -177,7 +180,8 @@ ISCSI_API iscsi_status iscsi_density(const void* bra, const void* ket, void* d1,
 /*
  * Same as iscsi_density with HOST buffers (bra, ket [ndet]; d1 [2 n n]; d2
  * [3 n^4]): copies in, computes, copies out, synchronises and reports a
- * device wait that ran out (ISCSI_E_WAIT).
+ * device wait that ran out (ISCSI_E_WAIT).  Its device staging buffers stay
+ * with the context for later calls until it is destroyed.
  */
 ISCSI_API iscsi_status iscsi_density_host(const double* bra, const double* ket, double* d1, double* d2);
 

@@ -96,9 +96,11 @@ iscsi_status iscsi_sigma_host(const double* c, double* sigma, int nvec) {
   }
   cudaStream_t st = stream();
   size_t bytes = sizeof(double) * (size_t)ctx->ndet * nvec;
-  DevBuf dc, ds;
-  ISCSI_TRY(dc.alloc(bytes));
-  ISCSI_TRY(ds.alloc(bytes));
+  // staging buffers kept by the context (no allocation on repeated calls)
+  DevBuf& dc = ctx->host_io[0];
+  DevBuf& ds = ctx->host_io[1];
+  ISCSI_TRY(dc.grow(bytes));
+  ISCSI_TRY(ds.grow(bytes));
   ISCSI_CUDA(cudaMemcpyAsync(dc.p, c, bytes, cudaMemcpyHostToDevice, st));
   ISCSI_TRY(sigma_run(*ctx, dc.as<double>(), ds.as<double>(), nvec, options().precision));
   ISCSI_CUDA(cudaMemcpyAsync(sigma, ds.p, bytes, cudaMemcpyDeviceToHost, st));
@@ -125,16 +127,22 @@ iscsi_status iscsi_density_host(const double* bra, const double* ket, double* d1
   cudaStream_t st = stream();
   const size_t vb = sizeof(double) * (size_t)ctx->ndet;
   const size_t n2 = (size_t)ctx->n * ctx->n, b1 = sizeof(double) * 2 * n2, b2 = sizeof(double) * 3 * n2 * n2;
-  DevBuf db, dk, o1, o2;
-  ISCSI_TRY(db.alloc(vb));
+  // staging buffers kept by the context (no allocation on repeated calls)
+  DevBuf& db = ctx->host_io[0];
+  DevBuf& dk = ctx->host_io[1];
+  DevBuf& o1 = ctx->host_io[2];
+  DevBuf& o2 = ctx->host_io[3];
+  const bool has_ket = ket && ket != bra;
+  ISCSI_TRY(db.grow(vb));
   ISCSI_CUDA(cudaMemcpyAsync(db.p, bra, vb, cudaMemcpyHostToDevice, st));
-  if (ket && ket != bra) {
-    ISCSI_TRY(dk.alloc(vb));
+  if (has_ket) {
+    ISCSI_TRY(dk.grow(vb));
     ISCSI_CUDA(cudaMemcpyAsync(dk.p, ket, vb, cudaMemcpyHostToDevice, st));
   }
-  if (d1) ISCSI_TRY(o1.alloc(b1));
-  if (d2) ISCSI_TRY(o2.alloc(b2));
-  ISCSI_TRY(density_run(*ctx, db.as<double>(), dk.p ? dk.as<double>() : nullptr, o1.as<double>(), o2.as<double>()));
+  if (d1) ISCSI_TRY(o1.grow(b1));
+  if (d2) ISCSI_TRY(o2.grow(b2));
+  ISCSI_TRY(density_run(*ctx, db.as<double>(), has_ket ? dk.as<double>() : nullptr, d1 ? o1.as<double>() : nullptr,
+                        d2 ? o2.as<double>() : nullptr));
   if (d1) ISCSI_CUDA(cudaMemcpyAsync(d1, o1.p, b1, cudaMemcpyDeviceToHost, st));
   if (d2) ISCSI_CUDA(cudaMemcpyAsync(d2, o2.p, b2, cudaMemcpyDeviceToHost, st));
   ISCSI_CUDA(cudaStreamSynchronize(st));

@@ -248,6 +248,8 @@ struct Context {
   DensityPlan* dm = nullptr;
   // time propagation (propagate.cu): Krylov basis and sigma buffers, partial sums, control block
   DevBuf pr_ws, pr_part, pr_ctl;
+  // device staging of the host-buffer entry points (iscsi_sigma_host, iscsi_density_host)
+  DevBuf host_io[4];
   ~Context();
 };
 
