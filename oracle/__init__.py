@@ -14,6 +14,10 @@ Contents
     and d2 by explicit operator application.
   * ``jordan_wigner`` -- a third, independent route: the Fock-space matrix of
     the unrestricted Hamiltonian of Eq. ham for tiny orbital counts.
+  * ``propagate`` -- exact piecewise-constant propagators of H + f(t) V.
+  * ``gas`` -- GAS restrictions (Sec. "Generalized Active Space"): the kept
+    determinants under accumulated subspace occupation limits, and the
+    Hamiltonian restricted to them.
 
 Parity status of each function is stated in its docstring; every function
 here is pinned by tests/test_oracle_*.py (paper table, paper sign examples,
