@@ -221,6 +221,42 @@ ISCSI_API iscsi_status iscsi_propagate(void* c, int nsteps, double dt, const dou
                                        int imaginary, double* diag);
 
 /*
+ * Generalised-active-space restriction of the current context's determinant
+ * space (Sec. "Generalized Active Space"; the paper's use: at most one
+ * electron in a continuum subspace).  The orbitals are split into nspace
+ * ordered subspaces, subspace j holding the next sizes[j] orbitals; a
+ * determinant of the truncated space is kept iff for every j
+ *     cmin[j] <= electrons (alpha + beta) in subspaces 0..j <= cmax[j].
+ * The CI problem becomes P H_tau P, P the projector onto the kept
+ * determinants, on the unchanged index range (length ndet, canonical order):
+ *   iscsi_sigma, iscsi_sigma_host  sigma = P H_tau P c (zero outside);
+ *   iscsi_davidson, iscsi_batch_davidson  eigenpairs of P H_tau P on the kept
+ *             determinants (start vectors projected; nroots <= kept count);
+ *   iscsi_propagate  c is projected first, then propagated under P H(t) P.
+ * iscsi_sigma_noalloc and iscsi_batch_sigma refuse a restricted context
+ * (ISCSI_E_ARG).  Density matrices and the diagonal are unaffected.  The
+ * enclosing truncated space is what is computed on: the restriction selects
+ * determinants, it does not make sigma cheaper.
+ *   nspace    1..8, or 0 to remove the restriction (the other pointers unused).
+ *   sizes     host [nspace], each >= 1, summing to norb.
+ *   cmin, cmax host [nspace], 0 <= cmin[j] <= cmax[j] <= nalpha + nbeta.
+ *   ndet_gas  host, out (may be NULL): the number of kept determinants (may
+ *             be 0).
+ * Synchronises.  The mask costs one byte per determinant of device memory.
+ * Errors: ISCSI_E_NOINIT, ISCSI_E_ARG, ISCSI_E_NOMEM, ISCSI_E_CUDA.
+ */
+ISCSI_API iscsi_status iscsi_set_gas(int nspace, const int* sizes, const int* cmin, const int* cmax,
+                                     long long* ndet_gas);
+
+/*
+ * The current context's determinant mask: mask device, uint8 [ndet], 1 for a
+ * kept determinant, 0 otherwise (all 1 without a GAS restriction).
+ * Asynchronous on the library stream.  Errors: ISCSI_E_NOINIT, ISCSI_E_ARG
+ * (NULL), ISCSI_E_CUDA.
+ */
+ISCSI_API iscsi_status iscsi_gas_mask(void* mask);
+
+/*
  * Lowest nroots eigenpairs of H_tau by a Davidson iteration on the device
  * (diagonal preconditioner, FP64 orthonormalisation, Rayleigh-Ritz and
  * residuals).  Converged when every root has residual 2-norm <= tol and its

@@ -54,6 +54,8 @@ def load(build_if_missing=True):
         "iscsi_density": (c_int, [vp, vp, vp, vp]),
         "iscsi_propagate": (c_int, [vp, c_int, c_d, vp, c_int, c_int, c_int, vp]),
         "iscsi_density_host": (c_int, [vp, vp, vp, vp]),
+        "iscsi_set_gas": (c_int, [c_int, vp, vp, vp, vp]),
+        "iscsi_gas_mask": (c_int, [vp]),
         "iscsi_ndet": (c_ll, []),
         "iscsi_nstrings": (c_ll, [c_int]),
         "iscsi_get_strings": (c_int, [c_int, vp, vp]),
@@ -203,6 +205,27 @@ def iscsi_propagate(c, nsteps, dt, field=None, coupling=0, krylov=12, imaginary=
     _check(load().iscsi_propagate(_dev(c), int(nsteps), float(dt), fp, int(coupling), int(krylov),
                                   1 if imaginary else 0, diag.ctypes.data_as(ctypes.c_void_p)))
     return diag
+
+
+def iscsi_set_gas(sizes=(), cmin=(), cmax=()):
+    """GAS restriction of the current context (empty sizes: none); returns the
+    number of kept determinants."""
+    n = len(sizes)
+    if len(cmin) != n or len(cmax) != n:
+        raise ValueError("one (cmin, cmax) pair per subspace")
+    arrs = [np.ascontiguousarray(x, dtype=np.int32) for x in (sizes, cmin, cmax)]
+    ptrs = [a.ctypes.data_as(ctypes.c_void_p) if n else None for a in arrs]
+    kept = ctypes.c_longlong(0)
+    _check(load().iscsi_set_gas(n, ptrs[0], ptrs[1], ptrs[2], ctypes.byref(kept)))
+    return int(kept.value)
+
+
+def iscsi_gas_mask(mask):
+    """Copy the determinant mask into mask (a contiguous uint8 CUDA tensor of ndet elements)."""
+    import torch
+    if not (mask.is_cuda and mask.dtype == torch.uint8 and mask.is_contiguous() and mask.numel() == iscsi_ndet()):
+        raise ValueError("expected a contiguous uint8 CUDA tensor of ndet elements")
+    _check(load().iscsi_gas_mask(mask.data_ptr()))
 
 
 def iscsi_davidson(nroots, tol, vecs=None):

@@ -76,13 +76,23 @@ iscsi_status iscsi_sigma(const void* c, void* sigma, int nvec) {
     set_error("iscsi_sigma: NULL pointer or nvec < 1");
     return ISCSI_E_ARG;
   }
-  return sigma_run(*ctx, static_cast<const double*>(c), static_cast<double*>(sigma), nvec, options().precision);
+  const double* cin = static_cast<const double*>(c);
+  if (ctx->gas_nspace) {  // sigma = P H P c: the projected input in a context buffer
+    ISCSI_TRY(ctx->gas_in.grow(sizeof(double) * (size_t)ctx->ndet * nvec));
+    ISCSI_TRY(gas_project(*ctx, cin, ctx->gas_in.as<double>(), nvec, stream()));
+    cin = ctx->gas_in.as<double>();
+  }
+  return sigma_run(*ctx, cin, static_cast<double*>(sigma), nvec, options().precision);
 }
 
 iscsi_status iscsi_sigma_noalloc(const void* c, void* sigma) {
   NEED_CTX(ctx);
   if (!c || !sigma) {
     set_error("iscsi_sigma_noalloc: NULL pointer");
+    return ISCSI_E_ARG;
+  }
+  if (ctx->gas_nspace) {
+    set_error("iscsi_sigma_noalloc: not with a GAS restriction; use iscsi_sigma");
     return ISCSI_E_ARG;
   }
   return sigma_noalloc_run(*ctx, static_cast<const double*>(c), static_cast<double*>(sigma));
@@ -102,6 +112,7 @@ iscsi_status iscsi_sigma_host(const double* c, double* sigma, int nvec) {
   ISCSI_TRY(dc.grow(bytes));
   ISCSI_TRY(ds.grow(bytes));
   ISCSI_CUDA(cudaMemcpyAsync(dc.p, c, bytes, cudaMemcpyHostToDevice, st));
+  if (ctx->gas_nspace) ISCSI_TRY(gas_project(*ctx, dc.as<double>(), dc.as<double>(), nvec, st));
   ISCSI_TRY(sigma_run(*ctx, dc.as<double>(), ds.as<double>(), nvec, options().precision));
   ISCSI_CUDA(cudaMemcpyAsync(sigma, ds.p, bytes, cudaMemcpyDeviceToHost, st));
   ISCSI_CUDA(cudaStreamSynchronize(st));
@@ -182,13 +193,37 @@ iscsi_status iscsi_propagate(void* c, int nsteps, double dt, const double* field
         set_error("iscsi_propagate: non-finite field sample");
         return ISCSI_E_ARG;
       }
+  // a GAS restriction: the start vector is projected onto the kept determinants
+  if (ctx->gas_nspace)
+    ISCSI_TRY(gas_project(*ctx, static_cast<double*>(c), static_cast<double*>(c), imaginary ? 1 : 2, stream()));
   return propagate_run(*ctx, cpl, static_cast<double*>(c), nsteps, dt, field, krylov, imaginary, diag);
+}
+
+iscsi_status iscsi_set_gas(int nspace, const int* sizes, const int* cmin, const int* cmax, long long* ndet_gas) {
+  NEED_CTX(ctx);
+  ISCSI_TRY(gas_set(*ctx, nspace, sizes, cmin, cmax));
+  if (ndet_gas) *ndet_gas = ctx->gas_ndet;
+  return ISCSI_OK;
+}
+
+iscsi_status iscsi_gas_mask(void* mask) {
+  NEED_CTX(ctx);
+  if (!mask) {
+    set_error("iscsi_gas_mask: NULL pointer");
+    return ISCSI_E_ARG;
+  }
+  cudaStream_t st = stream();
+  if (ctx->gas_nspace)
+    ISCSI_CUDA(cudaMemcpyAsync(mask, ctx->gas_mask.p, ctx->ndet, cudaMemcpyDeviceToDevice, st));
+  else
+    ISCSI_CUDA(cudaMemsetAsync(mask, 1, ctx->ndet, st));
+  return ISCSI_OK;
 }
 
 iscsi_status iscsi_davidson(int nroots, double tol, double* energies, void* vecs) {
   NEED_CTX(ctx);
-  if (nroots < 1 || nroots > ctx->ndet || !(tol > 0) || !energies) {
-    set_error("iscsi_davidson: invalid argument");
+  if (nroots < 1 || nroots > ctx->gas_ndet || !(tol > 0) || !energies) {
+    set_error("iscsi_davidson: invalid argument (1 <= nroots <= determinants of the space, tol > 0, energies)");
     return ISCSI_E_ARG;
   }
   int s = davidson_run(*ctx, nroots, tol, energies, static_cast<double*>(vecs));
@@ -391,6 +426,9 @@ iscsi_status iscsi_stats(char* json, int len) {
     std::snprintf(v, sizeof(v), ", \"samespin_tc_bf16_flops\": %.17g, \"both_tc_fp64\": %d, \"both_tc_fp32\": %d",
                   ctx_gemm_flops(*ctx, 3), both(64) ? 1 : 0, both(32) ? 1 : 0);
     out += v;
+    // GAS restriction: subspaces (0: none) and kept determinants
+    std::snprintf(v, sizeof(v), ", \"gas_subspaces\": %d, \"gas_ndet\": %lld", ctx->gas_nspace, ctx->gas_ndet);
+    out += v;
     // the density matrices' contraction (after the first iscsi_density call with d2):
     // bf16 MMA flops and 2 M N K of one launch, ket = bra and general
     std::snprintf(v, sizeof(v),
@@ -460,6 +498,11 @@ iscsi_status iscsi_batch_sigma(const int* handles, const void* const* cs, void* 
         set_error("iscsi_batch_sigma: a context appears twice");
         return ISCSI_E_ARG;
       }
+    if (it->second->gas_nspace) {
+      set_error("iscsi_batch_sigma: the context at position " + std::to_string(i) +
+                " has a GAS restriction; use iscsi_sigma");
+      return ISCSI_E_ARG;
+    }
     ctxs[i] = it->second.get();
     c[i] = static_cast<const double*>(cs[i]);
     s[i] = static_cast<double*>(sigmas[i]);
@@ -478,7 +521,7 @@ iscsi_status iscsi_batch_davidson(const int* handles, int count, int nroots, dou
   std::vector<Context*> ctxs(count);
   for (int i = 0; i < count; ++i) {
     auto it = g_ctx.find(handles[i]);
-    if (it == g_ctx.end() || nroots > it->second->ndet) {
+    if (it == g_ctx.end() || nroots > it->second->gas_ndet) {
       set_error("iscsi_batch_davidson: unknown handle, or more roots than determinants, at position " +
                 std::to_string(i));
       return ISCSI_E_ARG;

@@ -1062,6 +1062,7 @@ int start_vectors(Dav& d, DavCtl& h, const double* vecs) {
   cudaStream_t st = d.st;
   if (vecs && options().guess_from_vecs) {
     ISCSI_CUDA(cudaMemcpyAsync(d.T, vecs, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, st));
+    if (ctx.gas_nspace) ISCSI_TRY(gas_project(ctx, d.T, d.T, k, st));  // onto the GAS space
     ISCSI_TRY(d.orthonormalise_block(true));  // the basis is still empty (m = 0)
     ISCSI_TRY(d.read_ctl(h));
     for (int j = 0; j < k; ++j)
@@ -1075,8 +1076,15 @@ int start_vectors(Dav& d, DavCtl& h, const double* vecs) {
   std::vector<double> dg(N);
   ISCSI_CUDA(cudaMemcpyAsync(dg.data(), ctx.diag.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
   ISCSI_CUDA(cudaStreamSynchronize(st));
-  std::vector<long long> idx(N);
-  for (long long i = 0; i < N; ++i) idx[i] = i;
+  // the candidates: every determinant, or the kept ones under a GAS restriction
+  std::vector<long long> idx;
+  idx.reserve(ctx.gas_ndet);
+  for (long long i = 0; i < N; ++i)
+    if (!ctx.gas_nspace || ctx.gas_mask_h[i]) idx.push_back(i);
+  if ((long long)idx.size() < k) {
+    set_error("iscsi_davidson: fewer determinants in the space than vectors in the block");
+    return kErrArg;
+  }
   std::partial_sort(idx.begin(), idx.begin() + k, idx.end(),
                     [&](long long a, long long b) { return dg[a] < dg[b] || (dg[a] == dg[b] && a < b); });
   idx.resize(k);
@@ -1122,8 +1130,8 @@ static int davidson_batch_body(const std::vector<Context*>& ctxs, int kw, double
   }
   // the block: the wanted roots and block_extra more (they widen the
   // expansion; convergence is judged on the wanted roots only)
-  long long ndet_min = ctxs[0]->ndet;
-  for (const Context* c : ctxs) ndet_min = std::min(ndet_min, c->ndet);
+  long long ndet_min = ctxs[0]->gas_ndet;
+  for (const Context* c : ctxs) ndet_min = std::min(ndet_min, c->gas_ndet);
   // (the caller's start vectors fill a block of the wanted roots only)
   const int extra = vecs && opt.guess_from_vecs ? 0 : std::max(0, opt.block_extra);
   const int k = (int)std::min<long long>(std::min(kMaxRoots, kw + extra), ndet_min);
@@ -1140,7 +1148,7 @@ static int davidson_batch_body(const std::vector<Context*>& ctxs, int kw, double
   std::vector<double> best_r(n, 1e300);
   std::vector<std::vector<double>> rhist(n);
   for (int i = 0; i < n; ++i) {
-    D[i].reset(new Dav(*ctxs[i], k, subspace_size(ctxs[i]->ndet, k)));
+    D[i].reset(new Dav(*ctxs[i], k, subspace_size(ctxs[i]->gas_ndet, k)));  // basis <= dimension of the space
     ISCSI_TRY(D[i]->setup());
     DavCtl& h = H[i];
     std::memset(&h, 0, sizeof(h));

@@ -250,6 +250,12 @@ struct Context {
   DevBuf pr_ws, pr_part, pr_ctl;
   // device staging of the host-buffer entry points (iscsi_sigma_host, iscsi_density_host)
   DevBuf host_io[4];
+  // GAS restriction (gas.cu): 0 subspaces = none; which determinants are kept
+  int gas_nspace = 0;
+  long long gas_ndet = 0;
+  DevBuf gas_mask;                  // uint8 [ndet], 1 = kept
+  std::vector<uint8_t> gas_mask_h;  // host copy (start vectors of the Davidson method)
+  DevBuf gas_in;                    // projected copy of a caller's vectors
   ~Context();
 };
 
@@ -272,6 +278,12 @@ struct Options {
   int tc_cluster = 1;   // opposite-spin contraction in two-CTA clusters (A tiles multicast):
                         // 0 never, 1 when the autotuner measures it faster, 2 always
 };
+
+// gas.cu: GAS restriction (P H P, P the projector onto the kept determinants)
+constexpr int kGasMaxSpaces = 8;
+int gas_set(Context& ctx, int nspace, const int* sizes, const int* cmin, const int* cmax);
+// dst = P src for nvec vectors (a copy when there is no restriction; src == dst allowed)
+int gas_project(const Context& ctx, const double* src, double* dst, int nvec, cudaStream_t st);
 
 Options& options();
 cudaStream_t stream();

@@ -624,6 +624,7 @@ int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h
     acc += (long long)(SA.level_start[l + 1] - SA.level_start[l]) * ctx.nb_allowed_lvl[l];
   }
   ctx.ndet = acc;
+  ctx.gas_ndet = acc;
   if (ctx.ndet <= 0) {
     set_error("empty determinant space");
     return kErrArg;

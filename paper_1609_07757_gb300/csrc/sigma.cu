@@ -843,8 +843,11 @@ int sigma_run(Context& ctx, const double* c, double* sigma, int nvec, int precis
   const double* Ma = ctx.na ? ctx.M64[0].as<double>() : nullptr;
   const double* Mb = ctx.nb ? (ctx.beta_alias ? ctx.M64[0].as<double>() : ctx.M64[1].as<double>()) : nullptr;
   if (precision == 64) {
-    return sigma_impl<double, double>(ctx, c, sigma, c, sigma, nvec, ctx.pl_ab64, ctx.pl_ss64, ctx.pl_nvec64,
-                                      ctx.G64.as<double>(), Ma, Mb, phases);
+    ISCSI_TRY(sigma_impl<double, double>(ctx, c, sigma, c, sigma, nvec, ctx.pl_ab64, ctx.pl_ss64, ctx.pl_nvec64,
+                                         ctx.G64.as<double>(), Ma, Mb, phases));
+    // a GAS restriction: sigma = P H c (zero outside the kept determinants)
+    if ((phases & kPhPost) && ctx.gas_nspace) ISCSI_TRY(gas_project(ctx, sigma, sigma, nvec, st));
+    return kOk;
   }
   if (phases & kPhPre) ISCSI_TRY(ensure_fp32_matrices(ctx));
   const float* Ma32 = ctx.na ? ctx.M32[0].as<float>() : nullptr;
@@ -858,6 +861,7 @@ int sigma_run(Context& ctx, const double* c, double* sigma, int nvec, int precis
                                      ctx.G32.as<float>(), Ma32, Mb32, phases));
   if (phases & kPhPost) {
     k_convert<float, double><<<std::min(launch_blocks(cnt, 256), 4096), 256, 0, st>>>(ctx.s32.as<float>(), sigma, cnt); ISCSI_COUNT_LAUNCH();
+    if (ctx.gas_nspace) ISCSI_TRY(gas_project(ctx, sigma, sigma, nvec, st));
   }
   ISCSI_CUDA(cudaGetLastError());
   return kOk;

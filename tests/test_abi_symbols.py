@@ -37,6 +37,8 @@ def test_calls_without_context_fail_cleanly():
     assert lib.iscsi_ctx_current() == 0
     assert lib.iscsi_sigma(None, None, 1) == _lib.ISCSI_E_NOINIT
     assert lib.iscsi_density(None, None, None, None) == _lib.ISCSI_E_NOINIT
+    assert lib.iscsi_set_gas(0, None, None, None, None) == _lib.ISCSI_E_NOINIT
+    assert lib.iscsi_gas_mask(None) == _lib.ISCSI_E_NOINIT
     assert lib.iscsi_set_option(b"no_such_key", 1.0) == _lib.ISCSI_E_ARG
     assert lib.iscsi_set_option(b"precision", 16.0) == _lib.ISCSI_E_ARG
     assert b"precision" in lib.iscsi_last_error()

@@ -126,3 +126,36 @@ def test_fullsize_propagation():
     # the Krylov error indicator of the smaller space bounds the difference (with margin)
     assert float(torch.linalg.norm(out[0] - out[1])) <= 10.0 * ind[0] + 1e-13
     assert ind[0] <= 1e-10 and ind[1] <= 1e-13
+
+
+def test_fullsize_gas_restriction():
+    """Full CI n = 60 with the paper's three-subspace restriction (2 occupied,
+    18 bound, 40 continuum orbitals, at most one electron in the continuum):
+    the whole mask bit-exact, sampled rows of P H P c against the oracle."""
+    from oracle import gas
+    n, k, ell, nchol, box, seed, tau, nd = FULL["fci_n60_tau1e-14"]
+    sizes, cmin, cmax = (2, 18, 40), (0, 3, 4), (4, 4, 4)
+    h1, eri = make_integrals(n, seed, ell=ell, nchol=nchol, box=box)
+    L.iscsi_init(n, 2, 2, k, h1, eri, tau)
+    kept = L.iscsi_set_gas(sizes, cmin, cmax)
+    m = torch.empty(nd, dtype=torch.uint8, device="cuda")
+    L.iscsi_gas_mask(m)
+    c = unit_vector(nd, 19)
+    ct = torch.tensor(c, dtype=torch.float64, device="cuda")
+    st = torch.empty_like(ct)
+    L.iscsi_sigma(ct, st, 1)
+    torch.cuda.synchronize()
+    s = st.cpu().numpy()
+    gmask = m.cpu().numpy().astype(bool)
+    L.iscsi_finalize()
+    o = Oracle(n, 2, 2, k, tau, h1, eri)
+    keep = gas.mask(o, sizes, cmin, cmax)
+    assert kept == int(keep.sum()) and np.array_equal(gmask, keep)
+    assert not np.any(s[~keep])
+    rng = np.random.default_rng(5)
+    idx = np.flatnonzero(keep)
+    rows = np.unique(np.concatenate([idx[:2], idx[-2:], rng.choice(idx, size=400, replace=False)]))
+    ref = o.sigma_rows(c * keep, rows)
+    scale = np.abs(s).max()
+    err = np.abs(s[rows] - ref).max()
+    assert err <= 1e-12 * scale, (err, scale)
