@@ -699,6 +699,112 @@ def run_propagation(name, nsteps=4, dt=0.02, krylov=12, with_cpu=True):
     return out
 
 
+# the paper's GAS use (Sec. "Generalized Active Space"): occupied, bound and
+# continuum orbitals with at most one electron in the continuum
+GAS_SPLIT = {"fci_n60": ((2, 18, 40), (0, 3, 4), (4, 4, 4))}
+
+
+def run_gas(name, steps=10, warmup=3, with_cpu=True):
+    """Sigma and the ground state under a GAS restriction (P H P, at most one
+    electron in the continuum subspace): ms per sigma with and without the
+    restriction (L2 flushed), the projection overhead against its HBM bound,
+    a Davidson ground state on the restricted space against the unrestricted
+    one, sampled rows against the oracle."""
+    import numpy as np
+    import torch
+
+    from paper_1609_07757_gb300 import _lib as L
+    from paper_1609_07757_gb300.synthetic import make_integrals, unit_vector
+
+    wl = WORKLOADS[name]
+    sizes, cmin, cmax = GAS_SPLIT[name]
+    n = wl["n"]
+    h1, eri = make_integrals(n, wl["seed"], ell=wl["ell"], nchol=wl["nchol"], box=wl["box"])
+    stream = torch.cuda.current_stream()
+    L.iscsi_set_stream(stream)
+    L.iscsi_init(n, wl["na"], wl["nb"], wl["kmax"], h1, eri, wl["tau"])
+    ndet = L.iscsi_ndet()
+    c = torch.tensor(unit_vector(ndet, 31), dtype=torch.float64, device="cuda")
+    s = torch.empty_like(c)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed():
+        for _ in range(max(3, warmup)):
+            L.iscsi_sigma(c, s, 1)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            L.iscsi_sigma(c, s, 1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    ms_plain = timed()
+    st, e_full = L.iscsi_davidson(1, 1e-8)
+    kept = L.iscsi_set_gas(sizes, cmin, cmax)
+    ms_gas = timed()
+    s_host = s.cpu().numpy()
+    t0 = time.time()
+    st2, e_gas = L.iscsi_davidson(1, 1e-8)
+    dav_s = time.time() - t0
+    iters = L.iscsi_stats()["davidson_iters"]
+    L.iscsi_finalize()
+    # the same restriction as a GAS context: the level split at the continuum
+    # (levels count continuum electrons, at most one) gives the GAS space itself
+    L.iscsi_init_gas(n, wl["na"], wl["nb"], sizes, cmin, cmax, h1, eri, wl["tau"])
+    st_ctx = L.iscsi_stats()
+    ndet_ctx = L.iscsi_ndet()
+    c = torch.tensor(unit_vector(ndet_ctx, 31), dtype=torch.float64, device="cuda")
+    s = torch.empty_like(c)
+    ms_ctx = timed()
+    upd_ctx = L.iscsi_updates_per_sigma()
+    t0 = time.time()
+    st3, e_ctx = L.iscsi_davidson(1, 1e-8)
+    dav_ctx_s = time.time() - t0
+    iters_ctx = L.iscsi_stats()["davidson_iters"]
+    L.iscsi_finalize()
+    proj_bytes = 2 * ndet * (1 + 8 + 8)  # mask + read + write, input and output
+    hbm, hbm_src = measured_peaks()
+    out = {"workload": name, "subspaces": {"sizes": list(sizes), "cmin": list(cmin), "cmax": list(cmax),
+                                           "meaning": "2 occupied, 18 bound, 40 continuum orbitals; at most one "
+                                                      "electron in the continuum"},
+           "ndet": ndet, "ndet_gas": kept, "ms_per_sigma": round(ms_gas, 4), "ms_per_sigma_unrestricted":
+               round(ms_plain, 4), "projection_overhead_ms": round(ms_gas - ms_plain, 4),
+           "projection_hbm_bound_ms": round(proj_bytes / (hbm * 1e9) * 1e3, 4),
+           "projection_bytes": proj_bytes, "hbm_peak_gbs": hbm, "peak_source": hbm_src,
+           "davidson": {"status": st2, "energy_gas": float(e_gas[0]), "energy_unrestricted": float(e_full[0]),
+                        "iterations": iters, "seconds": round(dav_s, 3)},
+           "gas_context": {"ndet": ndet_ctx, "level_split": st_ctx["level_split"],
+                           "max_excitation": st_ctx["max_excitation"], "mask": st_ctx["gas_subspaces"] > 0,
+                           "ms_per_sigma": round(ms_ctx, 4), "gupdates_per_s": round(upd_ctx / (ms_ctx * 1e-3) / 1e9, 1),
+                           "speedup_vs_projected": round(ms_gas / ms_ctx, 2),
+                           "davidson": {"status": st3, "energy": float(e_ctx[0]), "iterations": iters_ctx,
+                                        "seconds": round(dav_ctx_s, 3),
+                                        "abs_dE_vs_projected": abs(float(e_ctx[0]) - float(e_gas[0]))}},
+           "l2": "flushed between calls",
+           "note": "projected: sigma on the enclosing full-CI space with the mask; gas_context: iscsi_init_gas, "
+                   "whose level split makes the GAS space the computed space"}
+    if with_cpu:
+        from oracle import Oracle, gas, max_threads
+        o = Oracle(n, wl["na"], wl["nb"], wl["kmax"], wl["tau"], h1, eri)
+        keep = gas.mask(o, sizes, cmin, cmax)
+        cc = unit_vector(ndet, 31) * keep
+        rows = np.random.default_rng(2).choice(np.flatnonzero(keep), size=64, replace=False)
+        t0 = time.time()
+        ref = o.sigma_rows(cc, rows)
+        dt = time.time() - t0
+        out["sample_check"] = {"rows": len(rows), "max_abs_diff": float(np.abs(s_host[rows] - ref).max()),
+                               "scale": float(np.abs(s_host).max()),
+                               "mask_equal": bool(kept == int(keep.sum()))}
+        out["cpu_baseline"] = {"value": round(dt / len(rows) * kept * 1e3, 1), "unit": "ms per sigma (extrapolated)",
+                               "cores": max_threads(), "kind": "oracle",
+                               "sample": "row-wise oracle sigma on %d kept rows (%.2f s), scaled to the %d kept "
+                                         "rows" % (len(rows), dt, kept)}
+    return out
+
+
 def run_sweep(steps=5, warmup=3):
     """The box-size sweep: CISD and CISDT, 2 alpha + 2 beta electrons in 50, 100,
     150 and 200 orbitals (integrals decaying with the box), tau = 1e-14, FP64.
@@ -834,6 +940,9 @@ def main():
                     help="one- and two-body density matrices on this workload (none: skip)")
     ap.add_argument("--propagation-workload", default="fci_n60", choices=sorted(WORKLOADS) + ["none"],
                     help="real-time propagation under a field on this workload (none: skip)")
+    ap.add_argument("--gas-workload", default="fci_n60", choices=sorted(GAS_SPLIT) + ["none"],
+                    help="sigma and ground state under a GAS restriction on this workload (none: skip)")
+    ap.add_argument("--gas-only", action="store_true", help="run only the GAS leg and print its object")
     ap.add_argument("--propagation-only", action="store_true",
                     help="run only the propagation leg (--steps steps) and print its object")
     ap.add_argument("--density-only", action="store_true",
@@ -866,7 +975,7 @@ def main():
         if rank == 0 and line:
             print(json.dumps(line))
         return
-    if args.propagation_only or args.density_only:
+    if args.propagation_only or args.density_only or args.gas_only:
         from paper_1609_07757_gb300 import _lib as L
         L.iscsi_set_option("autotune", args.autotune)
         L.iscsi_set_option("tc_cluster", args.tc_cluster)
@@ -875,6 +984,11 @@ def main():
         if rank == 0:
             print(json.dumps({"propagation": run_propagation(args.propagation_workload, nsteps=args.steps,
                                                              with_cpu=not args.no_cpu_baseline)}))
+        return
+    if args.gas_only:
+        if rank == 0:
+            print(json.dumps({"gas": run_gas(args.gas_workload, steps=args.steps, warmup=args.warmup,
+                                             with_cpu=not args.no_cpu_baseline)}))
         return
     if args.density_only:
         # the density-matrix leg alone (profiling its contraction)
@@ -898,6 +1012,8 @@ def main():
         line["density_matrices"] = run_density(args.density_workload, with_cpu=not args.no_cpu_baseline)
     if rank == 0 and ws == 1 and args.propagation_workload != "none":
         line["propagation"] = run_propagation(args.propagation_workload, with_cpu=not args.no_cpu_baseline)
+    if rank == 0 and ws == 1 and args.gas_workload != "none":
+        line["gas"] = run_gas(args.gas_workload, with_cpu=not args.no_cpu_baseline)
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
             tau = args.tau if args.tau is not None else wl["tau"]

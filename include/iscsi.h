@@ -102,6 +102,29 @@ ISCSI_API iscsi_status iscsi_init(int norb, int nalpha, int nbeta, int max_excit
                         double tau);
 
 /*
+ * Create a context on a GAS space (Sec. "Generalized Active Space"): the
+ * determinants of nalpha / nbeta electrons in norb orbitals whose accumulated
+ * subspace occupations satisfy the limits (sizes, cmin, cmax as in
+ * iscsi_set_gas; no excitation-level truncation beyond them), and make it
+ * current.  The library computes on an enclosing truncated space and masks the
+ * rest: of full CI and, for each subspace boundary j < nspace - 1, the space
+ * of determinants with at most N - cmin[j] electrons (N = nalpha + nbeta)
+ * outside the first sizes[0] + ... + sizes[j] orbitals (a level truncation
+ * with those orbitals as the inner ones), it takes the smallest; the limits
+ * it does not enforce are applied as by iscsi_set_gas.  With one lower limit
+ * doing all the restricting (the paper's "at most one electron in the
+ * continuum") no mask remains and sigma costs what the GAS space costs.
+ * iscsi_ndet is the enclosing space's dimension; iscsi_stats gives "gas_ndet"
+ * (the GAS dimension) and "level_split" (the inner orbitals per spin); strings
+ * are sorted by the level of that split (electrons outside the inner orbitals),
+ * determinants by it as in iscsi_init.  h1, eri, tau as in iscsi_init.
+ * Errors: ISCSI_E_ARG (limits of iscsi_init and iscsi_set_gas), ISCSI_E_NOMEM,
+ * ISCSI_E_CUDA.  On error no context is created.
+ */
+ISCSI_API iscsi_status iscsi_init_gas(int norb, int nalpha, int nbeta, int nspace, const int* sizes, const int* cmin,
+                                      const int* cmax, const double* h1, const double* eri, double tau);
+
+/*
  * sigma = H_tau c for nvec vectors (Eq. sigma, screened as Eq. sigma_split).
  *   c      device, FP64, [nvec][ndet] (vector-major, ndet contiguous).
  *   sigma  device, FP64, [nvec][ndet]; overwritten; must not overlap c.

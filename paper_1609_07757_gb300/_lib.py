@@ -55,6 +55,7 @@ def load(build_if_missing=True):
         "iscsi_propagate": (c_int, [vp, c_int, c_d, vp, c_int, c_int, c_int, vp]),
         "iscsi_density_host": (c_int, [vp, vp, vp, vp]),
         "iscsi_set_gas": (c_int, [c_int, vp, vp, vp, vp]),
+        "iscsi_init_gas": (c_int, [c_int, c_int, c_int, c_int, vp, vp, vp, vp, vp, c_d]),
         "iscsi_gas_mask": (c_int, [vp]),
         "iscsi_ndet": (c_ll, []),
         "iscsi_nstrings": (c_ll, [c_int]),
@@ -218,6 +219,20 @@ def iscsi_set_gas(sizes=(), cmin=(), cmax=()):
     kept = ctypes.c_longlong(0)
     _check(load().iscsi_set_gas(n, ptrs[0], ptrs[1], ptrs[2], ctypes.byref(kept)))
     return int(kept.value)
+
+
+def iscsi_init_gas(norb, nalpha, nbeta, sizes, cmin, cmax, h1, eri, tau):
+    """A new current context on the GAS space of the accumulated limits (see iscsi_init_gas)."""
+    n = len(sizes)
+    if len(cmin) != n or len(cmax) != n or n == 0:
+        raise ValueError("one (cmin, cmax) pair per subspace, at least one subspace")
+    arrs = [np.ascontiguousarray(x, dtype=np.int32) for x in (sizes, cmin, cmax)]
+    h, hp = _host_f64(h1)
+    ep = None
+    if eri is not None:
+        e, ep = _host_f64(eri)
+    return _check(load().iscsi_init_gas(norb, nalpha, nbeta, n, *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs],
+                                        hp, ep, float(tau)))
 
 
 def iscsi_gas_mask(mask):

@@ -44,8 +44,18 @@ using namespace iscsi;
 
 extern "C" {
 
-iscsi_status iscsi_init(int norb, int nalpha, int nbeta, int max_excitation, const double* h1, const double* eri,
-                        double tau) {
+}  // extern "C"
+
+// a new current context; ninner < 0: excitation levels, else levels count the
+// electrons outside the first ninner orbitals.  gas: a GAS spec applied before
+// the context is registered (nullptr: none)
+struct GasSpec {
+  int nspace;
+  const int *sizes, *cmin, *cmax;
+};
+
+static iscsi_status init_context(int norb, int nalpha, int nbeta, int max_excitation, const double* h1,
+                                 const double* eri, double tau, int ninner, const GasSpec* gas) {
   if (norb < 1 || norb > kMaxOrb || nalpha < 0 || nbeta < 0 || nalpha > norb || nbeta > norb ||
       nalpha > kMaxElec || nbeta > kMaxElec || max_excitation < 0 || !h1 || !(tau >= 0.0) || std::isinf(tau)) {
     set_error("iscsi_init: invalid argument (limits: 1<=norb<=256, 0<=n_sigma<=min(norb,16), "
@@ -59,7 +69,12 @@ iscsi_status iscsi_init(int norb, int nalpha, int nbeta, int max_excitation, con
     return ISCSI_E_ARG;
   }
   auto ctx = std::make_unique<Context>();
-  int s = context_build(*ctx, norb, nalpha, nbeta, max_excitation, h1, eri, tau);
+  int s = context_build(*ctx, norb, nalpha, nbeta, max_excitation, h1, eri, tau, ninner);
+  if (s == kOk && gas) {
+    s = gas_set(*ctx, gas->nspace, gas->sizes, gas->cmin, gas->cmax);
+    // the level truncation alone gives the GAS space: no projection needed
+    if (s == kOk && ctx->gas_ndet == ctx->ndet) s = gas_set(*ctx, 0, nullptr, nullptr, nullptr);
+  }
   if (s != kOk) {
     cudaGetLastError();
     return s;
@@ -68,6 +83,62 @@ iscsi_status iscsi_init(int norb, int nalpha, int nbeta, int max_excitation, con
   g_ctx[h] = std::move(ctx);
   g_current = h;
   return ISCSI_OK;
+}
+
+// determinants with at most kmax electrons (alpha + beta) outside the first e orbitals
+static double split_dim(int n, int na, int nb, int e, int kmax) {
+  auto cnt = [&](int ne, int l) { return (double)binom_ll(e, ne - l) * (double)binom_ll(n - e, l); };
+  double tot = 0.0;
+  for (int la = 0; la <= na; ++la)
+    for (int lb = 0; lb <= nb && la + lb <= kmax; ++lb) tot += cnt(na, la) * cnt(nb, lb);
+  return tot;
+}
+
+extern "C" {
+
+iscsi_status iscsi_init(int norb, int nalpha, int nbeta, int max_excitation, const double* h1, const double* eri,
+                        double tau) {
+  return init_context(norb, nalpha, nbeta, max_excitation, h1, eri, tau, -1, nullptr);
+}
+
+iscsi_status iscsi_init_gas(int norb, int nalpha, int nbeta, int nspace, const int* sizes, const int* cmin,
+                            const int* cmax, const double* h1, const double* eri, double tau) {
+  const int N = nalpha + nbeta;
+  if (norb < 1 || norb > kMaxOrb || nalpha < 0 || nbeta < 0 || nspace < 1 || nspace > kGasMaxSpaces || !sizes ||
+      !cmin || !cmax) {
+    set_error("iscsi_init_gas: invalid argument (1 to 8 subspaces with sizes and limits)");
+    return ISCSI_E_ARG;
+  }
+  int edge = 0;
+  for (int j = 0; j < nspace; ++j) {
+    if (sizes[j] < 1 || cmin[j] < 0 || cmax[j] < cmin[j] || cmax[j] > N) {
+      set_error("iscsi_init_gas: subspace sizes >= 1 and limits 0 <= cmin <= cmax <= electrons");
+      return ISCSI_E_ARG;
+    }
+    edge += sizes[j];
+  }
+  if (edge != norb) {
+    set_error("iscsi_init_gas: subspace sizes must add up to the orbital count");
+    return ISCSI_E_ARG;
+  }
+  // the enclosing space: full CI, or the level truncation of one accumulated
+  // lower limit (at least cmin[j] electrons in the first e_j orbitals), the
+  // smallest of them
+  int best_inner = -1, best_k = N;
+  double best = split_dim(norb, nalpha, nbeta, 0, N);  // every string at level ne: full CI
+  edge = 0;
+  for (int j = 0; j + 1 < nspace; ++j) {
+    edge += sizes[j];
+    const int k = N - cmin[j];
+    const double d = split_dim(norb, nalpha, nbeta, edge, k);
+    if (d < best) {
+      best = d;
+      best_inner = edge;
+      best_k = k;
+    }
+  }
+  const GasSpec spec{nspace, sizes, cmin, cmax};
+  return init_context(norb, nalpha, nbeta, best_k, h1, eri, tau, best_inner, &spec);
 }
 
 iscsi_status iscsi_sigma(const void* c, void* sigma, int nvec) {
@@ -278,7 +349,7 @@ long long iscsi_det_index(const int* alpha_orbitals, const int* beta_orbitals) {
       int o = lists[s] ? lists[s][i] : -1;
       if (o < 0 || o >= ctx->n || (i > 0 && o <= lists[s][i - 1])) return -1;
       rank += binom_ll(o, i + 1);
-      lvl[s] += (o >= S.ne);
+      lvl[s] += (o >= S.nocc);
     }
     int p = 0;
     if (cudaMemcpy(&p, S.pos.as<int>() + rank, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
@@ -427,7 +498,8 @@ iscsi_status iscsi_stats(char* json, int len) {
                   ctx_gemm_flops(*ctx, 3), both(64) ? 1 : 0, both(32) ? 1 : 0);
     out += v;
     // GAS restriction: subspaces (0: none) and kept determinants
-    std::snprintf(v, sizeof(v), ", \"gas_subspaces\": %d, \"gas_ndet\": %lld", ctx->gas_nspace, ctx->gas_ndet);
+    std::snprintf(v, sizeof(v), ", \"gas_subspaces\": %d, \"gas_ndet\": %lld, \"level_split\": [%d, %d]",
+                  ctx->gas_nspace, ctx->gas_ndet, ctx->sp[0].nocc, ctx->sp[1].nocc);
     out += v;
     // the density matrices' contraction (after the first iscsi_density call with d2):
     // bf16 MMA flops and 2 M N K of one launch, ket = bra and general

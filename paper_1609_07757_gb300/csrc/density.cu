@@ -98,7 +98,7 @@ static int host_colex(const int* o, int ne) {
 // electrons removed, the two-hole lift <Z| a_v a_u |A>, and the column list
 // (Z, string of the other spin) grouped by level class
 static int build_samespin(Context& ctx, DensityPlan& P, int s, DmBlock& B) {
-  const int n = ctx.n, ne = ctx.sp[s].ne, o = 1 - s;
+  const int n = ctx.n, ne = ctx.sp[s].ne, nocc = ctx.sp[s].nocc, o = 1 - s;
   const SpinSpace& SO = ctx.sp[o];
   std::vector<int> pos(ctx.sp[s].count);
   ISCSI_CUDA(cudaMemcpy(pos.data(), ctx.sp[s].pos.p, sizeof(int) * pos.size(), cudaMemcpyDeviceToHost));
@@ -107,12 +107,12 @@ static int build_samespin(Context& ctx, DensityPlan& P, int s, DmBlock& B) {
   for (int lev = 0; lev <= 2; ++lev)
     for (int u = 0; u < n; ++u)
       for (int v = u + 1; v < n; ++v)
-        if ((u >= ne) + (v >= ne) == lev) pairs.push_back({u, v});
+        if ((u >= nocc) + (v >= nocc) == lev) pairs.push_back({u, v});
   const int npp = (int)pairs.size();
   std::vector<int> pp_row(n * n, -1), pair_lev(npp);
   for (int i = 0; i < npp; ++i) {
     pp_row[pairs[i].first * n + pairs[i].second] = i;
-    pair_lev[i] = (pairs[i].first >= ne) + (pairs[i].second >= ne);
+    pair_lev[i] = (pairs[i].first >= nocc) + (pairs[i].second >= nocc);
   }
   // strings Z of ne - 2 electrons (lexicographic), with their levels
   std::vector<std::vector<int>> Z;
@@ -137,7 +137,7 @@ static int build_samespin(Context& ctx, DensityPlan& P, int s, DmBlock& B) {
   std::vector<int> zlev(nz), lift2((size_t)npp * nz, -1);
   for (int z = 0; z < nz; ++z) {
     int l = 0;
-    for (int x : Z[z]) l += (x >= ne);
+    for (int x : Z[z]) l += (x >= nocc);
     zlev[z] = l;
     for (int i = 0; i < npp; ++i) {
       int u = pairs[i].first, v = pairs[i].second;

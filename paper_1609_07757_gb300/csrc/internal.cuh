@@ -75,6 +75,8 @@ struct DevBuf {
 
 struct SpinSpace {
   int ne = 0;
+  int nocc = 0;        // a string's level counts its electrons at orbitals >= nocc (nocc = ne: the
+                       // excitation level of Eq. ci_hierarchy; else a two-subspace GAS split)
   int count = 0;       // C(n, ne)
   int maxlevel = 0;
   std::vector<int> level_start;   // first sorted index of each level, size maxlevel+2
@@ -290,7 +292,10 @@ cudaStream_t stream();
 void set_stream(cudaStream_t s);
 
 // setup.cu
-int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h1, const double* eri, double tau);
+// ninner < 0: levels are excitation levels (nocc = ne per spin); else every spin's level counts
+// its electrons outside the first ninner orbitals
+int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h1, const double* eri, double tau,
+                  int ninner = -1);
 
 // sigma.cu
 // phases of one sigma step (a batch over several contexts runs each phase for

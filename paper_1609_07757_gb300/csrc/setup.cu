@@ -338,8 +338,11 @@ __device__ __forceinline__ int pair_kind(int p, int q, int ne) {
 }
 
 // G[m][k] = g_pqrs for m = pi(p,r), k = pi(q,s) if the unit survives, else 0
-__global__ void k_build_g(const double* eri, long long npair, int n, int na, int nb, int npairs, const int* pair_of,
-                          double tau, unsigned long long mask, double* G, double* upd, unsigned long long* nunits) {
+// (class labels use the reference's occupied orbitals na, nb; the update
+// weights the level split oa, ob)
+__global__ void k_build_g(const double* eri, long long npair, int n, int na, int nb, int oa, int ob, int npairs,
+                          const int* pair_of, double tau, unsigned long long mask, double* G, double* upd,
+                          unsigned long long* nunits) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   double my_upd = 0.0;
   unsigned long long my_units = 0;
@@ -351,7 +354,7 @@ __global__ void k_build_g(const double* eri, long long npair, int n, int na, int
     bool keep = fabs(g) > tau && class_on(mask, class_ab(p >= na, q >= na, r >= nb, s >= nb));
     G[t] = keep ? g : 0.0;
     if (keep) {
-      my_upd = c_w_ab[pair_kind(p, q, na)][pair_kind(r, s, nb)];
+      my_upd = c_w_ab[pair_kind(p, q, oa)][pair_kind(r, s, ob)];
       my_units = 1;
     }
   }
@@ -563,19 +566,21 @@ static void host_binom_table() {
   done = true;
 }
 
-// number of (k)-subsets of the orbitals outside {p,q} with the given level,
-// for the six (p,q) kinds of pair_kind (O/V membership and p == q)
-static double hole_count(int n, int ne, int kind, int lvl) {
-  // orbitals removed from O and from V by {p,q}
+// number of (ne-1)-subsets of the orbitals outside {p,q} with the given
+// level, for the six (p,q) kinds of pair_kind (inner / outer membership, the
+// first nocc orbitals being the inner ones, and p == q)
+static double hole_count(int n, int ne, int nocc, int kind, int lvl) {
+  // orbitals removed from the inner and the outer orbitals by {p,q}
   static const int rmO[6] = {1, 2, 1, 1, 0, 0};
   static const int rmV[6] = {0, 0, 1, 1, 1, 2};
   int k = ne - 1;
-  int o = ne - rmO[kind], v = (n - ne) - rmV[kind];
+  int o = nocc - rmO[kind], v = (n - nocc) - rmV[kind];
   if (o < 0 || v < 0 || k < 0) return 0.0;
   return (double)binom_ll(o, k - lvl) * (double)binom_ll(v, lvl);
 }
 
-int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h1, const double* eri, double tau) {
+int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h1, const double* eri, double tau,
+                  int ninner) {
   cudaStream_t st = stream();
   host_binom_table();
   ISCSI_CUDA(cudaGetLastError());
@@ -595,7 +600,8 @@ int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h
   for (int s = 0; s < 2; ++s) {
     SpinSpace& S = ctx.sp[s];
     S.ne = nel[s];
-    ISCSI_TRY(enumerate_strings(n, S.ne, S.ne, S.orbs, S.level, S.pos, lcount[s], st));
+    S.nocc = ninner < 0 ? S.ne : ninner;
+    ISCSI_TRY(enumerate_strings(n, S.ne, S.nocc, S.orbs, S.level, S.pos, lcount[s], st));
     S.count = (int)binom_ll(n, S.ne);
     S.maxlevel = 0;
     for (int l = 0; l < (int)lcount[s].size(); ++l)
@@ -701,7 +707,7 @@ int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h
     for (int s = 0; s < 2; ++s) {
       SpinSpace& S = ctx.sp[s];
       if (S.ne == 0) continue;
-      ISCSI_TRY(enumerate_strings(n, S.ne - 1, S.ne, hole_orbs[s], hole_level[s], hole_pos[s], hole_lcount[s], st));
+      ISCSI_TRY(enumerate_strings(n, S.ne - 1, S.nocc, hole_orbs[s], hole_level[s], hole_pos[s], hole_lcount[s], st));
       S.nhole = (int)binom_ll(n, S.ne - 1);
       if (S.nhole >= (1 << 22)) {
         set_error("hole-string space too large (>= 2^22)");
@@ -736,7 +742,7 @@ int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h
         ctx.pair_level_start[lvl] = m;
         for (int p = 0; p < n; ++p)
           for (int r = 0; r < n; ++r)
-            if ((p >= na) + (r >= nb) == lvl) {
+            if ((p >= ctx.sp[0].nocc) + (r >= ctx.sp[1].nocc) == lvl) {
               pair_of[m] = p * n + r;
               pair_index[p * n + r] = m;
               ++m;
@@ -800,7 +806,8 @@ int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h
           for (int ly = 0; ly <= nb - 1; ++ly) {
             int src = lx + qv_of[ka] + ly + qv_of[kb];
             int dst = lx + pv_of[ka] + ly + pv_of[kb];
-            if (src <= kmax && dst <= kmax) tot += hole_count(n, na, ka, lx) * hole_count(n, nb, kb, ly);
+            if (src <= kmax && dst <= kmax)
+              tot += hole_count(n, na, ctx.sp[0].nocc, ka, lx) * hole_count(n, nb, ctx.sp[1].nocc, kb, ly);
           }
         w[ka][kb] = tot;
       }
@@ -808,7 +815,8 @@ int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h
 
     long long g2 = (long long)ctx.npairs * ctx.npairs;
     ISCSI_TRY(ctx.G64.alloc(sizeof(double) * g2));
-    k_build_g<<<launch_blocks(g2, 256), 256, 0, st>>>(d_eri.as<double>(), npair, n, na, nb, ctx.npairs,
+    k_build_g<<<launch_blocks(g2, 256), 256, 0, st>>>(d_eri.as<double>(), npair, n, na, nb, ctx.sp[0].nocc,
+                                                      ctx.sp[1].nocc, ctx.npairs,
                                                       ctx.pair_of.as<int>(), tau, cm, ctx.G64.as<double>(),
                                                       d_upd.as<double>() + 4, d_units.as<unsigned long long>() + 4);
     ISCSI_CUDA(cudaGetLastError());

@@ -275,3 +275,160 @@ def test_several_tiles_continuum_restriction():
     assert L.iscsi_set_gas(sizes, cmin, cmax) == int(keep.sum())
     c = unit_vector(o.ndet, 4)
     assert_close(gpu_sigma(c), gas.sigma(o, c, keep))
+
+
+# ---------------------------------------------------------------------------
+# contexts created on a GAS space (iscsi_init_gas): the enclosing space is a
+# level truncation of another inner/outer orbital split, with its own
+# determinant order; every GPU index is mapped to the full-CI oracle's index.
+
+def gpu_to_oracle_index(o):
+    """oracle index of every determinant of the current context, in its order."""
+    na, nb = o.na, o.nb
+    ga, la = L.iscsi_get_strings(0, na)
+    gb, lb = L.iscsi_get_strings(1, nb)
+    oa, _ = o.strings(0)
+    ob, _ = o.strings(1)
+    off = o.offsets()
+    posa = {tuple(int(x) for x in r): i for i, r in enumerate(oa)}
+    posb = {tuple(int(x) for x in r): i for i, r in enumerate(ob)}
+    pa = np.array([posa[tuple(int(x) for x in r)] for r in ga])
+    pb = np.array([posb[tuple(int(x) for x in r)] for r in gb])
+    kmax = L.iscsi_stats()["max_excitation"]
+    assert np.all(np.diff(lb) >= 0)  # beta strings sorted by level: allowed ones are a prefix
+    parts = []
+    for a in range(len(ga)):
+        nba = int(np.searchsorted(lb, kmax - la[a], side="right"))
+        parts.append(off[pa[a]] + pb[:nba])
+    idx = np.concatenate(parts) if parts else np.zeros(0, dtype=np.int64)
+    assert len(idx) == L.iscsi_ndet() and len(np.unique(idx)) == len(idx)
+    return idx
+
+
+def _split_dim(n, na, nb, e, k):
+    from math import comb
+    cnt = lambda ne, l: comb(e, ne - l) * comb(n - e, l) if 0 <= ne - l <= e else 0
+    return sum(cnt(na, la) * cnt(nb, lb) for la in range(na + 1) for lb in range(nb + 1) if la + lb <= k)
+
+
+SPLIT_CASES = [  # n, na, nb, sizes, cmin, cmax, expected (level split, kmax) or None for full CI
+    (10, 2, 2, (2, 3, 5), (0, 3, 4), (4, 4, 4), (5, 1)),          # at most one electron in the continuum
+    (10, 2, 2, (2, 3, 5), (2, 3, 4), (4, 4, 4), (2, 2)),          # and at most two out of the occupied: split there, mask
+    (9, 3, 2, (4, 5), (3, 5), (5, 5), (4, 2)),
+    (9, 2, 1, (3, 6), (2, 3), (3, 3), (3, 1)),
+    (8, 2, 2, (2, 2, 4), (0, 0, 4), (4, 3, 4), None),            # only an upper limit restricts: full CI + mask
+    (8, 3, 0, (4, 4), (2, 3), (3, 3), (4, 1)),                     # no beta electrons
+    (8, 2, 2, (4, 4), (4, 4), (4, 4), (4, 0)),                     # CAS(4): every electron inner
+]
+
+
+@pytest.mark.parametrize("n,na,nb,sizes,cmin,cmax,split", SPLIT_CASES)
+def test_gas_context_sigma_matches_oracle(n, na, nb, sizes, cmin, cmax, split):
+    h1, eri = make_integrals(n, 90 + n, ell=3.0, nchol=8)
+    L.iscsi_init_gas(n, na, nb, sizes, cmin, cmax, h1, eri, 0.0)
+    st = L.iscsi_stats()
+    o = Oracle(n, na, nb, 99, 0.0, h1, eri)  # full CI
+    keep = gas.mask(o, sizes, cmin, cmax)
+    assert st["gas_ndet"] == int(keep.sum())
+    if split is None:
+        assert L.iscsi_ndet() == o.ndet
+    else:
+        e, k = split
+        assert st["level_split"] == [e, e] and st["max_excitation"] == k
+        assert L.iscsi_ndet() == _split_dim(n, na, nb, e, k)
+    idx = gpu_to_oracle_index(o)
+    assert set(np.flatnonzero(keep)) <= set(idx.tolist())  # the GAS space lies in the enclosing one
+    c_or = unit_vector(o.ndet, 11) * keep
+    c_or /= np.linalg.norm(c_or)
+    s = gpu_sigma(c_or[idx])
+    assert_close(s, gas.sigma(o, c_or, keep)[idx])
+    # the determinant mask in the context's own order
+    assert np.array_equal(gpu_mask(L.iscsi_ndet()), keep[idx])
+
+
+@pytest.mark.parametrize("n,na,nb,sizes,cmin,cmax,nroots", [
+    (10, 2, 2, (2, 3, 5), (0, 3, 4), (4, 4, 4), 3),
+    (10, 2, 2, (2, 3, 5), (2, 3, 4), (4, 4, 4), 2),
+    (9, 3, 2, (4, 5), (3, 5), (5, 5), 2),
+])
+def test_gas_context_davidson_matches_restricted_spectrum(n, na, nb, sizes, cmin, cmax, nroots):
+    h1, eri = make_integrals(n, 95 + n, ell=3.0, nchol=8)
+    L.iscsi_init_gas(n, na, nb, sizes, cmin, cmax, h1, eri, 0.0)
+    o = Oracle(n, na, nb, 99, 0.0, h1, eri)
+    keep = gas.mask(o, sizes, cmin, cmax)
+    w = np.linalg.eigvalsh(gas.dense(o, keep))
+    st, e = L.iscsi_davidson(nroots, 1e-8)
+    assert st == 0 and np.abs(e - w[:nroots]).max() <= 1e-10
+
+
+@pytest.mark.parametrize("n,na,nb,sizes,cmin,cmax", [
+    (10, 2, 2, (2, 3, 5), (0, 3, 4), (4, 4, 4)),
+    (9, 3, 2, (4, 5), (3, 5), (5, 5)),
+    (8, 3, 3, (5, 3), (4, 6), (6, 6)),
+])
+def test_gas_context_density_matches_oracle(n, na, nb, sizes, cmin, cmax):
+    """The density matrices' lift tables follow the context's level split."""
+    h1, eri = make_integrals(n, 97 + n, ell=3.0, nchol=8)
+    L.iscsi_init_gas(n, na, nb, sizes, cmin, cmax, h1, eri, 0.0)
+    o = Oracle(n, na, nb, 99, 0.0, h1, eri)
+    keep = gas.mask(o, sizes, cmin, cmax)
+    idx = gpu_to_oracle_index(o)
+    bra = unit_vector(o.ndet, 12) * keep
+    ket = unit_vector(o.ndet, 13) * keep
+    r1, r2 = o.density(bra, ket)
+    d1 = torch.empty((2, n, n), dtype=torch.float64, device="cuda")
+    d2 = torch.empty((3, n, n, n, n), dtype=torch.float64, device="cuda")
+    L.iscsi_density(_dev(bra[idx]), _dev(ket[idx]), d1, d2)
+    torch.cuda.synchronize()
+    for got, ref in ((d1.cpu().numpy(), r1), (d2.cpu().numpy(), r2)):
+        assert np.abs(got - ref).max() <= 1e-12 * max(np.abs(ref).max(), 1e-300)
+
+
+def test_gas_context_propagation_matches_oracle():
+    n, na, nb = 9, 2, 2
+    sizes, cmin, cmax = (2, 3, 4), (0, 3, 4), (4, 4, 4)
+    h1, eri = make_integrals(n, 99, ell=3.0, nchol=8)
+    L.iscsi_init_gas(n, na, nb, sizes, cmin, cmax, h1, eri, 0.0)
+    o = Oracle(n, na, nb, 99, 0.0, h1, eri)
+    keep = gas.mask(o, sizes, cmin, cmax)
+    idx = gpu_to_oracle_index(o)
+    c = unit_vector(o.ndet, 6) * keep
+    c /= np.linalg.norm(c)
+    x = _dev(np.stack([c[idx], np.zeros(len(idx))]))
+    L.iscsi_propagate(x, 6, 0.05, None, 0, 16, False)
+    torch.cuda.synchronize()
+    y = x.cpu().numpy()
+    got = y[0] + 1j * y[1]
+    ref = propagate(gas.dense(o, keep), None, c[keep], 0.05, np.zeros(6))
+    full = np.zeros(o.ndet, dtype=np.complex128)
+    full[keep] = ref
+    assert np.linalg.norm(got - full[idx]) <= 1e-11
+
+
+def test_gas_context_refusals():
+    h1, eri = make_integrals(6, 1, ell=3.0, nchol=8)
+    for sizes, cmin, cmax in [((3, 2), (0, 4), (4, 4)), ((3, 3), (3, 4), (2, 4)), ((3, 3), (0, 4), (4, 5))]:
+        with pytest.raises(L.IscsiError):
+            L.iscsi_init_gas(6, 2, 2, sizes, cmin, cmax, h1, eri, 0.0)
+    assert L.iscsi_ctx_current() == 0
+
+
+def test_gas_context_full_size_continuum():
+    """Full CI n = 60 restricted to at most one electron in the 40 continuum
+    orbitals (2 occupied, 18 bound): the split alone gives the GAS space
+    (340,100 determinants, no mask); sampled rows against the full-CI oracle."""
+    n, sizes, cmin, cmax = 60, (2, 18, 40), (0, 3, 4), (4, 4, 4)
+    h1, eri = make_integrals(n, 1000, ell=4.0, nchol=60)
+    L.iscsi_init_gas(n, 2, 2, sizes, cmin, cmax, h1, eri, 1e-14)
+    st = L.iscsi_stats()
+    assert L.iscsi_ndet() == 340100 and st["gas_ndet"] == 340100 and st["gas_subspaces"] == 0
+    assert st["level_split"] == [20, 20] and st["max_excitation"] == 1
+    o = Oracle(n, 2, 2, 99, 1e-14, h1, eri)
+    idx = gpu_to_oracle_index(o)
+    c = unit_vector(len(idx), 8)
+    s = gpu_sigma(c)
+    c_or = np.zeros(o.ndet)
+    c_or[idx] = c
+    rows = np.random.default_rng(4).choice(len(idx), size=300, replace=False)
+    ref = o.sigma_rows(c_or, idx[rows])
+    assert np.abs(s[rows] - ref).max() <= 1e-12 * np.abs(s).max()
