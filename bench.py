@@ -699,12 +699,36 @@ def run_propagation(name, nsteps=4, dt=0.02, krylov=12, with_cpu=True):
     return out
 
 
+def context_strings(L, na, nb):
+    """(alpha orbitals, alpha levels, beta orbitals, beta levels, max level sum) of the current context."""
+    ga, la = L.iscsi_get_strings(0, na)
+    gb, lb = L.iscsi_get_strings(1, nb)
+    return ga, la, gb, lb, L.iscsi_stats()["max_excitation"]
+
+
+def index_map_to_oracle(o, strings):
+    """The oracle's index of every determinant of a context (its order: alpha
+    strings in turn, each with the prefix of level-sorted beta strings its level
+    allows); strings from context_strings, o a full-CI oracle."""
+    import numpy as np
+    ga, la, gb, lb, kmax = strings
+    oa, _ = o.strings(0)
+    ob, _ = o.strings(1)
+    off = o.offsets()
+    posa = {tuple(int(x) for x in r): i for i, r in enumerate(oa)}
+    posb = {tuple(int(x) for x in r): i for i, r in enumerate(ob)}
+    pa = np.array([posa[tuple(int(x) for x in r)] for r in ga])
+    pb = np.array([posb[tuple(int(x) for x in r)] for r in gb])
+    nba = np.searchsorted(lb, kmax - la, side="right")
+    return np.concatenate([off[pa[a]] + pb[:nba[a]] for a in range(len(ga))])
+
+
 # the paper's GAS use (Sec. "Generalized Active Space"): occupied, bound and
 # continuum orbitals with at most one electron in the continuum
 GAS_SPLIT = {"fci_n60": ((2, 18, 40), (0, 3, 4), (4, 4, 4))}
 
 
-def run_gas(name, steps=10, warmup=3, with_cpu=True):
+def run_gas(name, steps=10, warmup=3, with_cpu=True, projected=True):
     """Sigma and the ground state under a GAS restriction (P H P, at most one
     electron in the continuum subspace): ms per sigma with and without the
     restriction (L2 flushed), the projection overhead against its HBM bound,
@@ -741,15 +765,27 @@ def run_gas(name, steps=10, warmup=3, with_cpu=True):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in ev) / steps
 
-    ms_plain = timed()
-    st, e_full = L.iscsi_davidson(1, 1e-8)
-    kept = L.iscsi_set_gas(sizes, cmin, cmax)
-    ms_gas = timed()
-    s_host = s.cpu().numpy()
-    t0 = time.time()
-    st2, e_gas = L.iscsi_davidson(1, 1e-8)
-    dav_s = time.time() - t0
-    iters = L.iscsi_stats()["davidson_iters"]
+    out = {"workload": name, "subspaces": {"sizes": list(sizes), "cmin": list(cmin), "cmax": list(cmax),
+                                           "meaning": "2 occupied, 18 bound, 40 continuum orbitals; at most one "
+                                                      "electron in the continuum"}}
+    if projected:
+        ms_plain = timed()
+        st, e_full = L.iscsi_davidson(1, 1e-8)
+        kept = L.iscsi_set_gas(sizes, cmin, cmax)
+        ms_gas = timed()
+        t0 = time.time()
+        st2, e_gas = L.iscsi_davidson(1, 1e-8)
+        dav_s = time.time() - t0
+        iters = L.iscsi_stats()["davidson_iters"]
+        hbm, hbm_src = measured_peaks()
+        proj_bytes = 2 * ndet * (1 + 8 + 8)  # mask + read + write, input and output
+        out["projected"] = {
+            "ndet": ndet, "ndet_gas": kept, "ms_per_sigma": round(ms_gas, 4),
+            "ms_per_sigma_unrestricted": round(ms_plain, 4), "projection_overhead_ms": round(ms_gas - ms_plain, 4),
+            "projection_hbm_bound_ms": round(proj_bytes / (hbm * 1e9) * 1e3, 4), "projection_bytes": proj_bytes,
+            "hbm_peak_gbs": hbm, "peak_source": hbm_src,
+            "davidson": {"status": st2, "energy_gas": float(e_gas[0]), "energy_unrestricted": float(e_full[0]),
+                         "iterations": iters, "seconds": round(dav_s, 3)}}
     L.iscsi_finalize()
     # the same restriction as a GAS context: the level split at the continuum
     # (levels count continuum electrons, at most one) gives the GAS space itself
@@ -758,50 +794,74 @@ def run_gas(name, steps=10, warmup=3, with_cpu=True):
     ndet_ctx = L.iscsi_ndet()
     c = torch.tensor(unit_vector(ndet_ctx, 31), dtype=torch.float64, device="cuda")
     s = torch.empty_like(c)
+    L.iscsi_set_option("phase_timing", 1)
     ms_ctx = timed()
+    st_t = L.iscsi_stats()
+    L.iscsi_set_option("phase_timing", 0)
     upd_ctx = L.iscsi_updates_per_sigma()
+    s_ctx = s.cpu().numpy()
     t0 = time.time()
     st3, e_ctx = L.iscsi_davidson(1, 1e-8)
     dav_ctx_s = time.time() - t0
     iters_ctx = L.iscsi_stats()["davidson_iters"]
+    strings = context_strings(L, wl["na"], wl["nb"])
     L.iscsi_finalize()
-    proj_bytes = 2 * ndet * (1 + 8 + 8)  # mask + read + write, input and output
-    hbm, hbm_src = measured_peaks()
-    out = {"workload": name, "subspaces": {"sizes": list(sizes), "cmin": list(cmin), "cmax": list(cmax),
-                                           "meaning": "2 occupied, 18 bound, 40 continuum orbitals; at most one "
-                                                      "electron in the continuum"},
-           "ndet": ndet, "ndet_gas": kept, "ms_per_sigma": round(ms_gas, 4), "ms_per_sigma_unrestricted":
-               round(ms_plain, 4), "projection_overhead_ms": round(ms_gas - ms_plain, 4),
-           "projection_hbm_bound_ms": round(proj_bytes / (hbm * 1e9) * 1e3, 4),
-           "projection_bytes": proj_bytes, "hbm_peak_gbs": hbm, "peak_source": hbm_src,
-           "davidson": {"status": st2, "energy_gas": float(e_gas[0]), "energy_unrestricted": float(e_full[0]),
-                        "iterations": iters, "seconds": round(dav_s, 3)},
+    # the dominant kernel of the GAS context's sigma, timed live (phase events)
+    gemm_ms = st_t["phase_ms"]["opposite_gemm"] / max(1, st_t["timed_calls"])
+    both = st_t.get("both_tc_fp64", 0) == 1
+    route = st_t.get("route_fp64", {})
+    if st_t.get("fp64_tc", 0) == 1 and route.get("ab_tc", 1) == 1 and gemm_ms > 0:
+        flops = st_t["opposite_tc_bf16_flops"] + (st_t.get("samespin_tc_bf16_flops", 0.0) if both else 0.0)
+        peak, peak_src = bf16_peak()
+        cl = route.get("cl", 1)
+        ach = flops / (gemm_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": round(ach, 4), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(ach / peak, 4),
+                "traffic": profile_traffic("k_oz_gemm_cl%d%s_gas_%s" % (cl, "_both" if both else "", name))[0],
+                "kernel": "k_oz_gemm<%d> (tcgen05, FP64-accurate, %s)" % (
+                    cl, "opposite- and same-spin contractions in one launch" if both else "opposite-spin"),
+                "kernel_ms": round(gemm_ms, 4), "flops_per_launch": flops, "peak_source": peak_src}
+    else:
+        roof = {"bound": None, "note": "opposite-spin contraction not on the tensor cores", "route": route}
+    out.update({
            "gas_context": {"ndet": ndet_ctx, "level_split": st_ctx["level_split"],
                            "max_excitation": st_ctx["max_excitation"], "mask": st_ctx["gas_subspaces"] > 0,
                            "ms_per_sigma": round(ms_ctx, 4), "gupdates_per_s": round(upd_ctx / (ms_ctx * 1e-3) / 1e9, 1),
-                           "speedup_vs_projected": round(ms_gas / ms_ctx, 2),
+                           "speedup_vs_projected": round(ms_gas / ms_ctx, 2) if projected else None,
+                           "roofline": roof, "route_fp64": route,
                            "davidson": {"status": st3, "energy": float(e_ctx[0]), "iterations": iters_ctx,
                                         "seconds": round(dav_ctx_s, 3),
-                                        "abs_dE_vs_projected": abs(float(e_ctx[0]) - float(e_gas[0]))}},
+                                        "abs_dE_vs_projected": abs(float(e_ctx[0]) - float(e_gas[0]))
+                                        if projected else None}},
            "l2": "flushed between calls",
            "note": "projected: sigma on the enclosing full-CI space with the mask; gas_context: iscsi_init_gas, "
-                   "whose level split makes the GAS space the computed space"}
+                   "whose level split makes the GAS space the computed space"})
     if with_cpu:
+        # the full-CI oracle on sampled rows of the GAS space (the GAS context's
+        # vector mapped to full-CI indices), calibrated to ~5 s, scaled to all rows
         from oracle import Oracle, gas, max_threads
-        o = Oracle(n, wl["na"], wl["nb"], wl["kmax"], wl["tau"], h1, eri)
+        o = Oracle(n, wl["na"], wl["nb"], 99, wl["tau"], h1, eri)
         keep = gas.mask(o, sizes, cmin, cmax)
-        cc = unit_vector(ndet, 31) * keep
-        rows = np.random.default_rng(2).choice(np.flatnonzero(keep), size=64, replace=False)
-        t0 = time.time()
-        ref = o.sigma_rows(cc, rows)
-        dt = time.time() - t0
-        out["sample_check"] = {"rows": len(rows), "max_abs_diff": float(np.abs(s_host[rows] - ref).max()),
-                               "scale": float(np.abs(s_host).max()),
-                               "mask_equal": bool(kept == int(keep.sum()))}
-        out["cpu_baseline"] = {"value": round(dt / len(rows) * kept * 1e3, 1), "unit": "ms per sigma (extrapolated)",
-                               "cores": max_threads(), "kind": "oracle",
-                               "sample": "row-wise oracle sigma on %d kept rows (%.2f s), scaled to the %d kept "
-                                         "rows" % (len(rows), dt, kept)}
+        idx = index_map_to_oracle(o, strings)
+        c_or = np.zeros(o.ndet)
+        c_or[idx] = unit_vector(len(idx), 31)
+        rng = np.random.default_rng(2)
+        m = 64
+        for _ in range(3):
+            rows = rng.choice(len(idx), size=min(m, len(idx)), replace=False)
+            t0 = time.time()
+            ref = o.sigma_rows(c_or, idx[rows])
+            dt = time.time() - t0
+            if dt >= 2.5 or m >= len(idx):
+                break
+            m = int(min(len(idx), m * 5.0 / max(dt, 1e-3)))
+        out["sample_check"] = {"rows": len(rows), "max_abs_diff": float(np.abs(s_ctx[rows] - ref).max()),
+                               "scale": float(np.abs(s_ctx).max()),
+                               "gas_ndet_equal": bool(int(keep.sum()) == len(idx))}
+        out["cpu_baseline"] = {"value": round(dt / len(rows) * len(idx) * 1e3, 1),
+                               "unit": "ms per sigma (extrapolated)", "cores": max_threads(), "kind": "oracle",
+                               "sample": "row-wise full-CI oracle sigma on %d GAS rows (%.2f s), scaled to the %d "
+                                         "GAS rows" % (len(rows), dt, len(idx))}
     return out
 
 
@@ -943,6 +1003,8 @@ def main():
     ap.add_argument("--gas-workload", default="fci_n60", choices=sorted(GAS_SPLIT) + ["none"],
                     help="sigma and ground state under a GAS restriction on this workload (none: skip)")
     ap.add_argument("--gas-only", action="store_true", help="run only the GAS leg and print its object")
+    ap.add_argument("--gas-context-only", action="store_true",
+                    help="with --gas-only: only the GAS context (iscsi_init_gas), not the projected form")
     ap.add_argument("--propagation-only", action="store_true",
                     help="run only the propagation leg (--steps steps) and print its object")
     ap.add_argument("--density-only", action="store_true",
@@ -988,7 +1050,8 @@ def main():
     if args.gas_only:
         if rank == 0:
             print(json.dumps({"gas": run_gas(args.gas_workload, steps=args.steps, warmup=args.warmup,
-                                             with_cpu=not args.no_cpu_baseline)}))
+                                             with_cpu=not args.no_cpu_baseline,
+                                             projected=not args.gas_context_only)}))
         return
     if args.density_only:
         # the density-matrix leg alone (profiling its contraction)
