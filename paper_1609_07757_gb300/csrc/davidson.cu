@@ -186,16 +186,28 @@ __global__ void __launch_bounds__(kVecThreads) k_tsdots(const double* __restrict
   }
 }
 
-// C[i][j] = sum over blocks of partial[b][i][j] (nothing when gate points at 0)
+// x[0] + x[stride] + ... + x[(parts - 1) stride] by one warp in a fixed order
+// (lane l sums l, l + 32, ...; then a butterfly whose two operands are the same
+// on both lanes of every exchange, so every lane returns the same value, and
+// every run the same)
+__device__ __forceinline__ double warp_sum_strided(const double* __restrict__ x, long long stride, int parts,
+                                                   int lane) {
+  double s = 0.0;
+  for (int p = lane; p < parts; p += 32) s += x[(long long)p * stride];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// C[i][j] = sum over blocks of partial[b][i][j], one warp per element
+// (nothing when gate points at 0)
 __global__ void k_tsreduce(const double* __restrict__ partial, int parts, const int* __restrict__ na_dev, int na_add,
                            int nb, int rows_cap, double* __restrict__ C, const int* __restrict__ gate) {
   if (gate && !*gate) return;
   const int na = (na_dev ? *na_dev : 0) + na_add;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= na * nb) return;
-  double x = 0.0;
-  for (int p = 0; p < parts; ++p) x += partial[(long long)p * rows_cap * nb + t];
-  C[t] = x;
+  const int t = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (t >= na * nb) return;  // whole warps
+  const double x = warp_sum_strided(partial + t, (long long)rows_cap * nb, parts, lane);
+  if (lane == 0) C[t] = x;
 }
 
 // X_j = sum_i V_i Y[i][j], R_j = sum_i W_i Y[i][j] - theta_j X_j for j in
@@ -425,19 +437,17 @@ __global__ void __launch_bounds__(kVecThreads) k_dav_olsen_dots(const double* __
   }
 }
 
+// one warp per root (kMaxRoots warps)
 __global__ void k_dav_olsen_eps(DavCtl* __restrict__ ctl, const double* __restrict__ partial, int parts) {
-  const int k = ctl->k, j = threadIdx.x;
+  const int k = ctl->k, j = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (j >= k) return;
   if (!ctl->olsen) {
-    ctl->eps[j] = 0.0;
+    if (lane == 0) ctl->eps[j] = 0.0;
     return;
   }
-  double a = 0.0, b = 0.0;
-  for (int p = 0; p < parts; ++p) {
-    a += partial[(long long)p * 2 * k + 2 * j];
-    b += partial[(long long)p * 2 * k + 2 * j + 1];
-  }
-  ctl->eps[j] = (b != 0.0 && isfinite(a / b)) ? a / b : 0.0;
+  const double a = warp_sum_strided(partial + 2 * j, 2ll * k, parts, lane);
+  const double b = warp_sum_strided(partial + 2 * j + 1, 2ll * k, parts, lane);
+  if (lane == 0) ctl->eps[j] = (b != 0.0 && isfinite(a / b)) ? a / b : 0.0;
 }
 
 // Cholesky QR of the correction block from G = T^T T: upper R with R^T R = G
@@ -685,12 +695,12 @@ __global__ void __launch_bounds__(256) k_dav_eigh(DavCtl* __restrict__ ctl, cons
 }
 
 // residual norms, convergence and the restart decision
+// (one warp per root for the residual norms: kMaxRoots warps)
 __global__ void k_dav_check(DavCtl* __restrict__ ctl, const double* __restrict__ partial, int parts) {
-  const int k = ctl->k, j = threadIdx.x;
+  const int k = ctl->k, j = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (j < k) {
-    double x = 0.0;
-    for (int p = 0; p < parts; ++p) x += partial[(long long)p * k + j];
-    ctl->rnorm[j] = sqrt(fmax(x, 0.0));
+    const double x = warp_sum_strided(partial + j, k, parts, lane);
+    if (lane == 0) ctl->rnorm[j] = sqrt(fmax(x, 0.0));
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -818,7 +828,7 @@ struct Dav {
       case 7: dots_t<7>(A, na_dev, na_add, B, nb, gate); break;
       default: dots_t<8>(A, na_dev, na_add, B, nb, gate); break;
     }
-    k_tsreduce<<<(rows_cap * nb + 127) / 128, 128, 0, st>>>(partial.as<double>(), parts, na_dev, na_add, nb, rows_cap,
+    k_tsreduce<<<(rows_cap * nb + 7) / 8, 256, 0, st>>>(partial.as<double>(), parts, na_dev, na_add, nb, rows_cap,
                                                             C, gate); ISCSI_COUNT_LAUNCH();
   }
 
@@ -913,7 +923,7 @@ struct Dav {
     k_dav_eigh<<<1, 256, eig_smem, st>>>(ctl, S.as<double>(), maxsub, eigA.as<double>(), eigQ.as<double>(),
                                          Y.as<double>(), maxsub, thetas.as<double>(), eig_smem ? 1 : 0); ISCSI_COUNT_LAUNCH();
     ritz();
-    k_dav_check<<<1, 32, 0, st>>>(ctl, rr_part.as<double>(), parts); ISCSI_COUNT_LAUNCH();
+    k_dav_check<<<1, 32 * kMaxRoots, 0, st>>>(ctl, rr_part.as<double>(), parts); ISCSI_COUNT_LAUNCH();
     ISCSI_CUDA(cudaGetLastError());
     return kOk;
   }
@@ -948,7 +958,7 @@ struct Dav {
     // Olsen's epsilon from the Ritz vectors of the last evaluation (a restart
     // below replaces V, not X)
     k_dav_olsen_dots<<<parts, kVecThreads, 0, st>>>(R, X, ctx.diag.as<double>(), ctl, N, rr_part.as<double>()); ISCSI_COUNT_LAUNCH();
-    k_dav_olsen_eps<<<1, 32, 0, st>>>(ctl, rr_part.as<double>(), parts); ISCSI_COUNT_LAUNCH();
+    k_dav_olsen_eps<<<1, 32 * kMaxRoots, 0, st>>>(ctl, rr_part.as<double>(), parts); ISCSI_COUNT_LAUNCH();
     restart();
     k_dav_precond<<<parts, kVecThreads, 0, st>>>(R, X, ctx.diag.as<double>(), ctl, N, T); ISCSI_COUNT_LAUNCH();
     return orthonormalise_block(true);
