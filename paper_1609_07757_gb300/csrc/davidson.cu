@@ -753,7 +753,10 @@ struct Dav {
 
   Dav(Context& c, int k_, int maxsub_) : ctx(c), N(c.ndet), k(k_), maxsub(maxsub_), st(stream()) {
     kc = kc_for(k);
-    parts = kVecBlocks;
+    // blocks of the streaming kernels: 1 to 4 per SM, about 8 or more elements
+    // per thread (fewer block partials to reduce on small spaces)
+    const long long per_wave = 152ll * kVecThreads * 8;
+    parts = 152 * (int)std::min<long long>(kVecBlocks / 152, std::max<long long>(1, (N + per_wave - 1) / per_wave));
     rows_cap = maxsub + k;
     const int eb = 2 * maxsub * maxsub * (int)sizeof(double);
     eig_smem = eb <= 160 * 1024 ? eb : 0;
