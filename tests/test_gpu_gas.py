@@ -319,6 +319,8 @@ SPLIT_CASES = [  # n, na, nb, sizes, cmin, cmax, expected (level split, kmax) or
     (8, 2, 2, (2, 2, 4), (0, 0, 4), (4, 3, 4), None),            # only an upper limit restricts: full CI + mask
     (8, 3, 0, (4, 4), (2, 3), (3, 3), (4, 1)),                     # no beta electrons
     (8, 2, 2, (4, 4), (4, 4), (4, 4), (4, 0)),                     # CAS(4): every electron inner
+    (8, 2, 2, (1, 7), (1, 4), (2, 4), (1, 3)),                     # fewer inner orbitals than electrons:
+    (7, 3, 2, (2, 5), (3, 5), (4, 5), (2, 2)),                     # no string at level 0
 ]
 
 
@@ -365,6 +367,7 @@ def test_gas_context_davidson_matches_restricted_spectrum(n, na, nb, sizes, cmin
     (10, 2, 2, (2, 3, 5), (0, 3, 4), (4, 4, 4)),
     (9, 3, 2, (4, 5), (3, 5), (5, 5)),
     (8, 3, 3, (5, 3), (4, 6), (6, 6)),
+    (7, 3, 2, (2, 5), (3, 5), (5, 5)),  # alpha strings without a level-0 string
 ])
 def test_gas_context_density_matches_oracle(n, na, nb, sizes, cmin, cmax):
     """The density matrices' lift tables follow the context's level split."""
