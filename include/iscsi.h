@@ -156,8 +156,9 @@ ISCSI_API iscsi_status iscsi_sigma(const void* c, void* sigma, int nvec);
  * device looks up the array's device address (cudaGetSymbolAddress); make that
  * first call before any stream capture.  All calls share the array: calls
  * whose work overlaps on the GPU race and must be serialised by the caller.
- * Asynchronous on the library stream.  Errors: ISCSI_E_NOINIT, ISCSI_E_ARG,
- * ISCSI_E_CUDA.
+ * Asynchronous on the library stream.  A context with a determinant mask
+ * (iscsi_set_gas) is refused with ISCSI_E_ARG.  Errors: ISCSI_E_NOINIT,
+ * ISCSI_E_ARG, ISCSI_E_CUDA.
  */
 ISCSI_API iscsi_status iscsi_sigma_noalloc(const void* c, void* sigma);
 
@@ -304,15 +305,20 @@ ISCSI_API long long iscsi_nstrings(int spin);
 /*
  * Copy the sorted strings of one spin to the host.
  *   orbitals  host, [count][n_sigma] ints, ascending orbital list per string.
- *   levels    host, [count] ints (excitation level).  Either may be NULL.
+ *   levels    host, [count] ints: the level the strings are sorted by -- the
+ *             excitation level (electrons outside the first n_sigma orbitals),
+ *             or, in a context from iscsi_init_gas, the electrons outside its
+ *             inner orbitals (iscsi_stats "level_split").  Either may be NULL.
  * Synchronises.  Errors: ISCSI_E_NOINIT, ISCSI_E_ARG.
  */
 ISCSI_API iscsi_status iscsi_get_strings(int spin, int* orbitals, int* levels);
 
 /*
  * Determinant index of (alpha orbitals, beta orbitals), each an ascending host
- * list of nalpha / nbeta orbitals; -1 if outside the truncated space or
- * invalid, -5 (ISCSI_E_NOINIT) without a context.
+ * list of nalpha / nbeta orbitals; -1 if outside the truncated space (for a
+ * context from iscsi_init_gas: its enclosing space) or invalid, -5
+ * (ISCSI_E_NOINIT) without a context.  A determinant the GAS mask excludes
+ * still has an index (its sigma entries are zero).
  */
 ISCSI_API long long iscsi_det_index(const int* alpha_orbitals, const int* beta_orbitals);
 
