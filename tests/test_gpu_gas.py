@@ -435,3 +435,43 @@ def test_gas_context_full_size_continuum():
     rows = np.random.default_rng(4).choice(len(idx), size=300, replace=False)
     ref = o.sigma_rows(c_or, idx[rows])
     assert np.abs(s[rows] - ref).max() <= 1e-12 * np.abs(s).max()
+
+
+def test_gas_context_fp32_mixed_and_batch():
+    """A GAS context (split, no mask) through the FP32 form, the FP32-mixed
+    Davidson and iscsi_batch_sigma next to an ordinary context."""
+    n, na, nb = 10, 2, 2
+    sizes, cmin, cmax = (2, 3, 5), (0, 3, 4), (4, 4, 4)
+    h1, eri = make_integrals(n, 77, ell=3.0, nchol=8)
+    L.iscsi_init_gas(n, na, nb, sizes, cmin, cmax, h1, eri, 0.0)
+    g = L.iscsi_ctx_current()
+    assert L.iscsi_stats()["gas_subspaces"] == 0  # the split carries the restriction
+    o = Oracle(n, na, nb, 99, 0.0, h1, eri)
+    keep = gas.mask(o, sizes, cmin, cmax)
+    idx = gpu_to_oracle_index(o)
+    c_or = unit_vector(o.ndet, 14) * keep
+    ref = gas.sigma(o, c_or, keep)[idx]
+    # FP32 form
+    L.iscsi_set_option("precision", 32)
+    s32 = gpu_sigma(c_or[idx])
+    L.iscsi_set_option("precision", 64)
+    assert np.linalg.norm(s32 - ref) <= 2e-5 * np.linalg.norm(ref)
+    # FP32-mixed Davidson
+    w = np.linalg.eigvalsh(gas.dense(o, keep))[:2]
+    L.iscsi_set_option("precision", 32)
+    try:
+        st, e = L.iscsi_davidson(2, 1e-8)
+    finally:
+        L.iscsi_set_option("precision", 64)
+    assert st == 0 and np.abs(e - w).max() <= 1e-9
+    # batched sigma with an ordinary context
+    L.iscsi_init(8, 2, 2, 4, *make_integrals(8, 78, ell=3.0, nchol=8), 0.0)
+    b = L.iscsi_ctx_current()
+    ob = Oracle(8, 2, 2, 4, 0.0, *make_integrals(8, 78, ell=3.0, nchol=8))
+    cb = unit_vector(ob.ndet, 15)
+    xg, xb = _dev(c_or[idx]), _dev(cb)
+    sg, sb = torch.empty_like(xg), torch.empty_like(xb)
+    L.iscsi_batch_sigma([g, b], [xg, xb], [sg, sb])
+    torch.cuda.synchronize()
+    assert_close(sg.cpu().numpy(), ref)
+    assert_close(sb.cpu().numpy(), ob.sigma(cb))
