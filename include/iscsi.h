@@ -226,8 +226,9 @@ ISCSI_API iscsi_status iscsi_density_host(const double* bra, const double* ket, 
  *   field     host [nsteps] samples f_k (for a smooth field, its value at the
  *             step's midpoint), or NULL for f = 0.
  *   coupling  handle of a context created with iscsi_init(norb, nalpha, nbeta,
- *             max_excitation, v, NULL, tau) on the same space, or 0 when field
- *             is NULL.  For each step its string matrices, scaled by f_k, are
+ *             max_excitation, v, NULL, tau) on the same space (for a context
+ *             from iscsi_init_gas: iscsi_init_gas with the same limits and v,
+ *             NULL), or 0 when field is NULL.  For each step its string matrices, scaled by f_k, are
  *             added to the current context's (the one-body classes become
  *             per-step), so a Krylov vector costs one sigma; the current
  *             context is restored exactly when the call returns.

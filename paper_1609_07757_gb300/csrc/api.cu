@@ -249,7 +249,7 @@ iscsi_status iscsi_propagate(void* c, int nsteps, double dt, const double* field
     }
     cpl = it->second.get();
     if (cpl->n != ctx->n || cpl->na != ctx->na || cpl->nb != ctx->nb || cpl->kmax != ctx->kmax ||
-        cpl->ndet != ctx->ndet) {
+        cpl->ndet != ctx->ndet || cpl->sp[0].nocc != ctx->sp[0].nocc || cpl->sp[1].nocc != ctx->sp[1].nocc) {
       set_error("iscsi_propagate: the coupling context is on a different determinant space");
       return ISCSI_E_ARG;
     }

@@ -475,3 +475,30 @@ def test_gas_context_fp32_mixed_and_batch():
     torch.cuda.synchronize()
     assert_close(sg.cpu().numpy(), ref)
     assert_close(sb.cpu().numpy(), ob.sigma(cb))
+
+
+def test_gas_context_propagation_with_field():
+    """Real time under H + f(t) V on a GAS context; V's context comes from
+    iscsi_init_gas with the same limits (the same determinant order)."""
+    n, na, nb = 9, 2, 2
+    sizes, cmin, cmax = (2, 3, 4), (0, 3, 4), (4, 4, 4)
+    h1, eri = make_integrals(n, 98, ell=3.0, nchol=8)
+    v = np.diag(np.arange(n) - (n - 1) / 2.0) / n + 0.05 * (np.eye(n, k=1) + np.eye(n, k=-1))
+    L.iscsi_init_gas(n, na, nb, sizes, cmin, cmax, v, None, 0.0)
+    hv = L.iscsi_ctx_current()
+    L.iscsi_init_gas(n, na, nb, sizes, cmin, cmax, h1, eri, 0.0)
+    o = Oracle(n, na, nb, 99, 0.0, h1, eri)
+    ov = Oracle(n, na, nb, 99, 0.0, v, None)
+    keep = gas.mask(o, sizes, cmin, cmax)
+    idx = gpu_to_oracle_index(o)
+    c = unit_vector(o.ndet, 16) * keep
+    c /= np.linalg.norm(c)
+    field = 0.3 * np.sin(0.5 * np.arange(8))
+    x = _dev(np.stack([c[idx], np.zeros(len(idx))]))
+    L.iscsi_propagate(x, 8, 0.05, field, hv, 16, False)
+    torch.cuda.synchronize()
+    y = x.cpu().numpy()
+    ref = propagate(gas.dense(o, keep), gas.dense(ov, keep), c[keep], 0.05, field)
+    full = np.zeros(o.ndet, dtype=np.complex128)
+    full[keep] = ref
+    assert np.linalg.norm(y[0] + 1j * y[1] - full[idx]) <= 1e-11
