@@ -6,12 +6,16 @@
 // sizes[j] orbitals.  A determinant is kept iff for every j the electrons
 // (alpha + beta) in subspaces 0..j number between cmin[j] and cmax[j] (the
 // accumulated form of the occupation limits).  The restricted CI problem is
-// P H P with P the projector onto the kept determinants: the determinant space
-// and its addressing stay those of the excitation-level truncation, sigma is
-// computed on that space and its entries outside the GAS space are set to
-// zero, and so are the input's (public sigma calls) or the start vectors'
-// (Davidson, propagation).  The restriction therefore costs what the enclosing
-// truncated space costs plus two streaming passes.
+// P H P with P the projector onto the kept determinants.  One lower limit can
+// be carried by the context's own addressing: a context built on a level split
+// after e orbitals (levels = electrons outside them, at most N - cmin) holds
+// exactly the determinants with at least cmin electrons inside (iscsi_init_gas
+// picks the most restrictive such limit, setup.cu builds the strings with it).
+// The limits the addressing does not carry are a mask, applied here: sigma is
+// computed on the context's space and its entries outside the GAS space are
+// set to zero, and so are the input's (public sigma calls) or the start
+// vectors' (Davidson, propagation); a mask costs what the context's space
+// costs plus two streaming passes.
 //
 // Device data: per string its electron count in each subspace, one byte each,
 // packed into a 64-bit word (at most 8 subspaces; at most 16 electrons per
