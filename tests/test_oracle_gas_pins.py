@@ -163,3 +163,47 @@ def test_limits_validated():
     with pytest.raises(ValueError):
         gas.mask(o, (2, 2), (0, 4), (4, 4))
     assert gas.mask(o, (2, 3), (0, 0), (4, 4)).all()
+
+
+def test_random_specs_match_brute_force():
+    """60 seeded random subspace splits and limits (2-4 subspaces, any electron
+    counts, level truncations included; half of them with limits within one of
+    a random determinant's accumulated counts, so that the kept set is rarely
+    empty or everything): the oracle's kept set equals the brute-force
+    enumeration, and its size the closed-form count at full CI."""
+    rng = np.random.default_rng(2024)
+    for trial in range(60):
+        n = int(rng.integers(4, 8))
+        na, nb = int(rng.integers(0, 4)), int(rng.integers(0, 4))
+        na, nb = min(na, n), min(nb, n)
+        if na + nb == 0:
+            na = 1
+        N = na + nb
+        ns = int(rng.integers(2, 5))
+        cuts = np.sort(rng.choice(np.arange(1, n), size=min(ns - 1, n - 1), replace=False))
+        sizes = tuple(int(x) for x in np.diff(np.concatenate([[0], cuts, [n]])))
+        cmin, cmax = [], []
+        if trial % 2:
+            occ = np.zeros(n, dtype=int)
+            occ[rng.choice(n, size=na, replace=False)] += 1
+            occ[rng.choice(n, size=nb, replace=False)] += 1
+            acc = np.cumsum([occ[a:b].sum() for a, b in zip(np.cumsum((0,) + sizes[:-1]), np.cumsum(sizes))])
+            for j in range(len(sizes)):
+                cmin.append(max(0, int(acc[j]) - int(rng.integers(0, 2))))
+                cmax.append(min(N, int(acc[j]) + int(rng.integers(0, 2))))
+        else:
+            for j in range(len(sizes)):
+                lo, hi = sorted(int(x) for x in rng.integers(0, N + 1, size=2))
+                cmin.append(lo)
+                cmax.append(hi)
+        cmin[-1] = min(cmin[-1], N)
+        cmax[-1] = N  # the last accumulated count is N: keep the space non-trivially reachable
+        kmax = int(rng.integers(0, N + 1))
+        h1, e = _rand_ints(n, 1)
+        o = Oracle(n, na, nb, kmax, 0.0, h1, e)
+        keep = gas.mask(o, sizes, cmin, cmax)
+        dets = _brute_force_dets(n, na, nb, kmax, sizes, cmin, cmax)
+        idx = sorted(o.det_index(A, B) for A, B in dets)
+        assert idx == np.flatnonzero(keep).tolist(), (n, na, nb, kmax, sizes, cmin, cmax)
+        if kmax >= N:
+            assert int(keep.sum()) == _closed_form_count(na, nb, sizes, cmin, cmax)
