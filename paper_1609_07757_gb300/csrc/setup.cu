@@ -8,6 +8,7 @@
 // applied here, once per integral unit: a dropped unit is a structural zero of
 // the matrices below, which is exactly the same as never applying its term.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -16,10 +17,16 @@
 
 namespace iscsi {
 
+// C(n, k); LLONG_MAX when it does not fit (every partial product r is itself
+// the binomial C(n - k + i, i), so the division is exact)
 long long binom_ll(int n, int k) {
   if (k < 0 || n < 0 || k > n) return 0;
+  if (k > n - k) k = n - k;
   long long r = 1;
-  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  for (int i = 1; i <= k; ++i) {
+    if (r > LLONG_MAX / (n - k + i)) return LLONG_MAX;
+    r = r * (n - k + i) / i;
+  }
   return r;
 }
 

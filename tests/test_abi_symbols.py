@@ -55,3 +55,22 @@ def test_init_rejects_bad_arguments_before_touching_the_gpu():
     assert lib.iscsi_init(2, 3, 1, 2, h, None, 0.0) == _lib.ISCSI_E_ARG
     assert lib.iscsi_init(2, 1, 1, 2, None, None, 0.0) == _lib.ISCSI_E_ARG
     assert lib.iscsi_init(2, 1, 1, 2, h, None, float("nan")) == _lib.ISCSI_E_ARG
+    # C(256, 16) ~ 1e25 strings: rejected by the string-space limit, not by an overflow
+    assert lib.iscsi_init(256, 16, 16, 2, h, None, 0.0) == _lib.ISCSI_E_ARG
+    assert b"string space" in lib.iscsi_last_error()
+
+
+def test_init_gas_rejects_bad_limits_before_touching_the_gpu():
+    lib = _lib.load()
+    h = (ctypes.c_double * 4)()
+    arr = lambda *v: (ctypes.c_int * len(v))(*v)
+    # sizes not adding up to norb, cmin > cmax, cmax above the electrons, an empty subspace, 9 subspaces
+    for sizes, cmin, cmax in [((1, 2), (0, 2), (2, 2)), ((1, 1), (2, 2), (1, 2)), ((1, 1), (0, 2), (2, 3)),
+                              ((0, 2), (0, 2), (2, 2))]:
+        assert lib.iscsi_init_gas(2, 1, 1, 2, arr(*sizes), arr(*cmin), arr(*cmax), h, None, 0.0) == _lib.ISCSI_E_ARG
+    nine = arr(*([1] * 9))
+    assert lib.iscsi_init_gas(9, 1, 1, 9, nine, arr(*([0] * 9)), arr(*([2] * 9)), h, None, 0.0) == _lib.ISCSI_E_ARG
+    # a string space far too large (the enclosing space is chosen first, with saturated counts)
+    big = arr(128, 128)
+    assert lib.iscsi_init_gas(256, 16, 16, 2, big, arr(0, 32), arr(32, 32), h, None, 0.0) == _lib.ISCSI_E_ARG
+    assert lib.iscsi_ctx_current() == 0
