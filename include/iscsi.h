@@ -26,7 +26,17 @@
  *     max_excitation; its index is off[A] + B, where B runs over the beta
  *     strings of level <= max_excitation - level(A) (a prefix of the sorted
  *     list) -- alpha-major, the CI-vector blocking of Fig. cisdt;
- *   - |A,B> = prod_{p in A ascending} a+_pa prod_{q in B ascending} a+_qb |vac>.
+ *   - |A,B> = prod_{p in A ascending} a+_pa prod_{q in B ascending} a+_qb |vac>;
+ *   - a context created with iscsi_init_gas counts levels against its own
+ *     inner orbitals instead of the reference's (Sec. "Generalized Active
+ *     Space"), with the same sorting and blocking; the class ids keep the
+ *     reference's O / V.
+ *
+ * Beyond sigma and the Davidson solver: spin-resolved one- and two-body
+ * (transition) density matrices (iscsi_density), time propagation under a
+ * time-dependent one-body term (iscsi_propagate), GAS restrictions
+ * (iscsi_init_gas, iscsi_set_gas), and many independent contexts at once
+ * (iscsi_batch_sigma, iscsi_batch_davidson).
  *
  * Class ids (bit i of a class mask):
  *   0..3   H^{1,1}, H^{1,0}, H^{0,1}, H^{0,0} _{1,0,1}   (one-body alpha)
