@@ -262,7 +262,6 @@ def run_ours(args, wl, ws, rank, local):
     stream = torch.cuda.current_stream()
     L.iscsi_set_stream(stream)
     L.iscsi_set_option("autotune", args.autotune)
-    L.iscsi_set_option("tc_cluster", args.tc_cluster)
     t0 = time.time()
     L.iscsi_init(wl["n"], wl["na"], wl["nb"], wl["kmax"], h1, eri, tau)
     init_s = time.time() - t0
@@ -327,7 +326,6 @@ def run_ours(args, wl, ws, rank, local):
     gemm_ms = st["phase_ms"]["opposite_gemm"] / max(1, st["timed_calls"])
     tc = st.get("fp64_tc" if args.precision == 64 else "fp32_tc", 0) == 1
     route = st.get("route_fp%d" % args.precision, {})
-    cl = route.get("cl", 1) if args.tc_cluster == 1 else (2 if args.tc_cluster == 2 else 1)
     tc = tc and route.get("ab_tc", 1) == 1
     # with both contractions on the tensor cores they are one launch: its flops
     # are the opposite- and the same-spin slice products
@@ -338,14 +336,14 @@ def run_ours(args, wl, ws, rank, local):
         # tensor-core kernel: bf16 MMA flops it issues (28 exact slice products)
         flops = st["opposite_tc_bf16_flops"] + (st.get("samespin_tc_bf16_flops", 0.0) if both else 0.0)
         peak, peak_src = bf16_peak()
-        bound, kname, kkey = "tensor", "k_oz_gemm<%d> (tcgen05, FP64-accurate %s, clusters of %d CTA)" % (
-            cl, what, cl), "k_oz_gemm_cl%d%s_%s" % (cl, tag, args.workload)
+        bound, kname, kkey = "tensor", "k_oz_gemm (tcgen05, FP64-accurate %s)" % what, \
+            "k_oz_gemm%s_%s" % (tag, args.workload)
     elif tc:
         # FP32 form: 6 of the 9 products of three bf16 terms per operand
         flops = (st["opposite_tc_bf16_flops"] + (st.get("samespin_tc_bf16_flops", 0.0) if both else 0.0)) * 6.0 / 28.0
         peak, peak_src = bf16_peak()
-        bound, kname, kkey = "tensor", "k_tc32w_gemm<%d> (tcgen05, FP32-accurate %s, 128 x 128 tiles, " \
-            "clusters of %d CTA)" % (cl, what, cl), "k_tc32w_gemm_cl%d%s_%s" % (cl, tag, args.workload)
+        bound, kname, kkey = "tensor", "k_tc32w_gemm (tcgen05, FP32-accurate %s, 128 x 128 tiles)" % what, \
+            "k_tc32w_gemm%s_%s" % (tag, args.workload)
     else:
         flops = st["opposite_gemm_flops"]
         peak = FP64_PEAK_TFLOPS if args.precision == 64 else FP32_PEAK_TFLOPS
@@ -813,13 +811,12 @@ def run_gas(name, steps=10, warmup=3, with_cpu=True, projected=True):
     if st_t.get("fp64_tc", 0) == 1 and route.get("ab_tc", 1) == 1 and gemm_ms > 0:
         flops = st_t["opposite_tc_bf16_flops"] + (st_t.get("samespin_tc_bf16_flops", 0.0) if both else 0.0)
         peak, peak_src = bf16_peak()
-        cl = route.get("cl", 1)
         ach = flops / (gemm_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": round(ach, 4), "peak": peak, "unit": "TFLOP/s",
                 "frac": round(ach / peak, 4),
-                "traffic": profile_traffic("k_oz_gemm_cl%d%s_gas_%s" % (cl, "_both" if both else "", name))[0],
-                "kernel": "k_oz_gemm<%d> (tcgen05, FP64-accurate, %s)" % (
-                    cl, "opposite- and same-spin contractions in one launch" if both else "opposite-spin"),
+                "traffic": profile_traffic("k_oz_gemm%s_gas_%s" % ("_both" if both else "", name))[0],
+                "kernel": "k_oz_gemm (tcgen05, FP64-accurate, %s)" % (
+                    "opposite- and same-spin contractions in one launch" if both else "opposite-spin"),
                 "kernel_ms": round(gemm_ms, 4), "flops_per_launch": flops, "peak_source": peak_src}
     else:
         roof = {"bound": None, "note": "opposite-spin contraction not on the tensor cores", "route": route}
@@ -994,8 +991,6 @@ def main():
                     help="add the batching form: COUNT full-CI instances, batched vs one at a time")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="library option autotune (kernel routing timed at the first sigma)")
-    ap.add_argument("--tc-cluster", type=int, default=1, choices=[0, 1, 2],
-                    help="library option tc_cluster (0 never, 1 tuned, 2 always two-CTA clusters)")
     ap.add_argument("--density-workload", default="fci_n60", choices=sorted(WORKLOADS) + ["none"],
                     help="one- and two-body density matrices on this workload (none: skip)")
     ap.add_argument("--propagation-workload", default="fci_n60", choices=sorted(WORKLOADS) + ["none"],
@@ -1040,7 +1035,6 @@ def main():
     if args.propagation_only or args.density_only or args.gas_only:
         from paper_1609_07757_gb300 import _lib as L
         L.iscsi_set_option("autotune", args.autotune)
-        L.iscsi_set_option("tc_cluster", args.tc_cluster)
     if args.propagation_only:
         # the propagation leg alone (profiling its launches)
         if rank == 0:

@@ -374,15 +374,11 @@ ISCSI_API iscsi_status iscsi_set_stream(void* stream);
  *   "autotune"         1 (default): before the first sigma of a context for a
  *                      given precision and vector count, time the candidate
  *                      kernel routings (opposite-spin contraction on the
- *                      tensor cores, in clusters of one or two CTAs, or on
- *                      the FMA kernels; same-spin level-block threshold
+ *                      tensor cores or on the FMA kernels; same-spin
+ *                      level-block threshold
  *                      16/64/256/none) that a flop model puts within 3x of
  *                      the best, and keep the fastest (iscsi_stats
  *                      "route_fp64" / "route_fp32"); 0: the defaults
- *   "tc_cluster"       opposite-spin tensor-core contraction in two-CTA
- *                      clusters that share the A operand by multicast: 0
- *                      never, 1 (default) when the autotuner measures it
- *                      faster, 2 always
  *   "phase_timing"     1: record per-phase CUDA events of every sigma call
  *                      (reported by iscsi_stats; the record restarts when set)
  * Errors: ISCSI_E_ARG for an unknown key or a value out of range.

@@ -2,7 +2,9 @@
 
 Test infrastructure only: the product library never links or loads it.
 """
+import hashlib
 import os
+import platform
 import subprocess
 import sys
 
@@ -11,14 +13,30 @@ SRC = os.path.join(HERE, "iscsi_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 
 
+CMD = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-Wall", "-Wno-unused-function"]
+
+
+def _digest():
+    h = hashlib.sha256()
+    with open(SRC, "rb") as f:
+        h.update(f.read())
+    h.update(" ".join(CMD).encode())
+    h.update(platform.machine().encode())
+    return h.hexdigest()
+
+
 def build(force=False):
-    """Build liboracle.so if missing or older than its source; return its path."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
-        return LIB
-    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-Wall", "-Wno-unused-function",
-           "-o", LIB + ".tmp", SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    """Build liboracle.so unless it was built from this source (SHA-256 stamp); return its path."""
+    stamp = LIB + ".sha256"
+    digest = _digest()
+    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+        with open(stamp) as f:
+            if f.read().strip() == digest:
+                return LIB
+    subprocess.run(CMD + ["-o", LIB + ".tmp", SRC, "-lm"], check=True)
     os.replace(LIB + ".tmp", LIB)
+    with open(stamp, "w") as f:
+        f.write(digest + "\n")
     return LIB
 
 

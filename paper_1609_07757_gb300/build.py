@@ -2,11 +2,16 @@
 
 Each translation unit is compiled by nvcc in parallel, then linked into
 paper_1609_07757_gb300/lib/libiscsi.so (the CUDA runtime is linked
-statically).  Rebuilds only when a source or header is newer than the library.
+statically).  Rebuilds unless the library was built from exactly these sources,
+flags, compiler and machine type: a SHA-256 over all of them is stored beside
+the library and compared (timestamps are not trusted: a copied tree may carry a
+library built elsewhere).
 """
 import concurrent.futures as cf
 import glob
+import hashlib
 import os
+import platform
 import subprocess
 import sys
 
@@ -33,12 +38,30 @@ def nvcc():
     return cand if os.path.exists(cand) else "nvcc"
 
 
+def source_hash():
+    """SHA-256 of the sources, headers, flags, nvcc version and machine type."""
+    h = hashlib.sha256()
+    for d in sorted(_deps()):
+        h.update(os.path.relpath(d, ROOT).encode())
+        with open(d, "rb") as f:
+            h.update(f.read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    try:
+        h.update(subprocess.run([nvcc(), "--version"], capture_output=True, text=True).stdout.encode())
+    except OSError:
+        pass
+    h.update(platform.machine().encode())
+    return h.hexdigest()
+
+
 def build(force=False, verbose=False):
-    """Compile (if stale) and return the path of libiscsi.so."""
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
-        if all(os.path.getmtime(d) <= t for d in _deps()):
-            return LIB
+    """Compile (unless built from the same sources) and return the path of libiscsi.so."""
+    stamp = LIB + ".sha256"
+    digest = source_hash()
+    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+        with open(stamp) as f:
+            if f.read().strip() == digest:
+                return LIB
     os.makedirs(OUT, exist_ok=True)
     objs = []
 
@@ -62,6 +85,8 @@ def build(force=False, verbose=False):
     os.replace(tmp, LIB)
     for o in objs:
         os.remove(o)
+    with open(stamp, "w") as f:
+        f.write(digest + "\n")
     return LIB
 
 

@@ -423,9 +423,6 @@ iscsi_status iscsi_set_option(const char* key, double value) {
     o.fp32_tc = value != 0;
   } else if (k == "autotune") {
     o.autotune = value != 0;
-  } else if (k == "tc_cluster") {
-    if (value != 0 && value != 1 && value != 2) return bad();
-    o.tc_cluster = (int)value;
   } else if (k == "phase_timing") {
     o.phase_timing = value != 0;
     Context* ctx = current();
@@ -511,18 +508,17 @@ iscsi_status iscsi_stats(char* json, int len) {
     out += v;
   }
   // the autotuner's routing per precision and its trials (ab_tc, ss_min or -1 =
-  // none on the tensor cores, cluster size, predicted ms, measured ms or -1 =
-  // pruned)
+  // none on the tensor cores, predicted ms, measured ms or -1 = pruned)
   for (int p = 0; p < 2; ++p) {
     const Context::Route& R = ctx->route[p];
     char v[192];
     std::snprintf(v, sizeof(v),
-                  ", \"route_fp%d\": {\"ab_tc\": %d, \"ss_min\": %d, \"cl\": %d, \"tuned_nvec\": %d, \"trials\": [",
-                  p == 0 ? 64 : 32, R.ab_tc, R.ss_min >= (1 << 30) ? -1 : R.ss_min, R.cl, R.tuned_nvec);
+                  ", \"route_fp%d\": {\"ab_tc\": %d, \"ss_min\": %d, \"tuned_nvec\": %d, \"trials\": [",
+                  p == 0 ? 64 : 32, R.ab_tc, R.ss_min >= (1 << 30) ? -1 : R.ss_min, R.tuned_nvec);
     out += v;
-    for (size_t i = 0; i + 4 < R.trials.size(); i += 5) {
-      std::snprintf(v, sizeof(v), "%s[%d, %d, %d, %.4g, %.4g]", i ? ", " : "", (int)R.trials[i],
-                    (int)R.trials[i + 1], (int)R.trials[i + 2], R.trials[i + 3], R.trials[i + 4]);
+    for (size_t i = 0; i + 3 < R.trials.size(); i += 4) {
+      std::snprintf(v, sizeof(v), "%s[%d, %d, %.4g, %.4g]", i ? ", " : "", (int)R.trials[i],
+                    (int)R.trials[i + 1], R.trials[i + 2], R.trials[i + 3]);
       out += v;
     }
     out += "]}";

@@ -30,12 +30,6 @@ int merge_jobs(MergedJob& mj, const std::vector<const OzJob*>& jobs, const std::
   mj.segs.clear();
   mj.maps.clear();
   mj.tiles = 0;
-  mj.cl = jobs.empty() ? 1 : jobs[0]->cl;
-  for (const OzJob* J : jobs)
-    if (J->cl != mj.cl) {
-      set_error("batched sigma: contexts with different cluster shapes");
-      return kErrArg;
-    }
   for (size_t i = 0; i < jobs.size(); ++i) {
     const OzJob& J = *jobs[i];
     const int seg0 = (int)mj.segs.size();
@@ -76,7 +70,7 @@ int merge_jobs(MergedJob& mj, const std::vector<const OzJob*>& jobs, const std::
 int launch_merged(const MergedJob& mj, int prec, int* err, cudaStream_t st) {
   if (mj.tiles == 0) return kOk;
   return launch_tc_problems(mj.d_probs.as<OzProblem>(), (int)mj.probs.size(), mj.d_segs.as<OzSeg>(),
-                            mj.d_maps.as<OzMaps>(), mj.d_tbases.as<void*>(), mj.tiles, prec, mj.cl, err, st);
+                            mj.d_maps.as<OzMaps>(), mj.d_tbases.as<void*>(), mj.tiles, prec, err, st);
 }
 
 struct BatchState {
@@ -183,9 +177,9 @@ int sigma_batch_sequence(SigmaBatch& B) {
     if (!B.ctxs[i]->capturing) ISCSI_TRY(sigma_autotune(*B.ctxs[i], B.cs[i], B.ss[i], B.nvec, B.prec));
   ISCSI_TRY(phase_all(B, kPhPre));
   {
-    // opposite spin: the tensor-core contexts in one launch per cluster shape,
-    // the others on their own
-    for (int cl = 1; cl <= 2; ++cl) {
+    // opposite spin: the tensor-core contexts in one launch, the others on
+    // their own
+    {
       std::vector<const OzJob*> jobs;
       std::vector<void*> tb;
       for (int i = 0; i < n; ++i) {
@@ -199,12 +193,11 @@ int sigma_batch_sequence(SigmaBatch& B) {
           if (!J) return kErrCuda;
           base = B.prec == 64 ? static_cast<void*>(B.ss[i]) : static_cast<void*>(c.s32.as<float>());
         }
-        if (J->cl != cl) continue;
         jobs.push_back(J);
         tb.push_back(base);
       }
-      ISCSI_TRY(merge_jobs(B.ab[cl - 1], jobs, tb, st));
-      ISCSI_TRY(launch_merged(B.ab[cl - 1], B.prec, B.err.as<int>(), st));
+      ISCSI_TRY(merge_jobs(B.ab, jobs, tb, st));
+      ISCSI_TRY(launch_merged(B.ab, B.prec, B.err.as<int>(), st));
     }
     ISCSI_TRY(phase_all(B, kPhAbGemm, /*skip_tc=*/true));
   }

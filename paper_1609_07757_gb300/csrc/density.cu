@@ -647,7 +647,7 @@ static int build_job(Context& ctx, bool sym) {
   }
   P.bf16_flops[sym ? 0 : 1] = f[0];
   P.fp64_flops[sym ? 0 : 1] = f[1];
-  ISCSI_TRY(oz_job_upload(job, 1, stream()));
+  ISCSI_TRY(oz_job_upload(job, stream()));
   (sym ? P.sym_ready : P.gen_ready) = true;
   return kOk;
 }

@@ -151,7 +151,6 @@ struct OzJob {
   int nvec = -1;
   const void* tbase = nullptr;
   long long version = 0;  // bumped at every rebuild (launches over several contexts re-merge)
-  int cl = 1;             // CTAs per cluster of its launches (2: A tiles multicast to CTA pairs)
   long long src_ver[2] = {-1, -1};  // a combined job: versions of the jobs it was built from
 };
 
@@ -214,9 +213,8 @@ struct Context {
     int ab_tc = 1;           // opposite-spin contraction on the tensor cores (else FMA kernels)
     int ss_min = kThinN;     // same-spin level blocks with more rows and allowed beta strings
                              // than this run on the tensor cores (else FMA kernels)
-    int cl = 1;              // CTAs per cluster of the opposite-spin tensor-core launch (1 or 2)
     int tuned_nvec = 0;      // vector count the autotuner ran for (0: not yet)
-    std::vector<double> trials;  // (ab_tc, ss_min, cl, predicted ms, measured ms) per candidate
+    std::vector<double> trials;  // (ab_tc, ss_min, predicted ms, measured ms) per candidate
   } route[2];
   long long pl_route_key = -1, pl_route_key32 = -1;  // routing the grouped-GEMM lists were built for
   int pl_ss_tc = -1;  // same-spin routing the FP64 grouped-GEMM list was built for
@@ -277,8 +275,6 @@ struct Options {
   int samespin_tc = 1;  // same for the same-spin blocks large enough for a 128 x 64 tile
   int fp32_tc = 1;      // FP32 form: contractions on the tensor cores (three bf16 terms, FP32 accumulation)
   int autotune = 1;     // time the routing candidates at the first sigma of each vector count
-  int tc_cluster = 1;   // opposite-spin contraction in two-CTA clusters (A tiles multicast):
-                        // 0 never, 1 when the autotuner measures it faster, 2 always
 };
 
 // gas.cu: GAS restriction (P H P, P the projector onto the kept determinants)
@@ -326,16 +322,16 @@ int both_tc_gemm(Context& ctx, double* sigma);  // opposite- and same-spin contr
 int both_tc32_gemm(Context& ctx, float* sigma);
 const OzJob* both_tc_job(Context& ctx, int prec);  // that combined job (built when needed), or nullptr
 int launch_tc_problems(const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
-                       void* const* tbases, int tiles, int prec, int cl, int* err, cudaStream_t st);
+                       void* const* tbases, int tiles, int prec, int* err, cudaStream_t st);
 int tc_check(Context& ctx);
 int samespin_matrices_changed(Context& ctx);  // re-cut the same-spin operand slices in place
 // M <- M_base + f M_v (cpl: the context of v); f = 0 restores (sigma.cu)
 int onebody_shift(Context& ctx, const Context& cpl, double f);
 // jobs assembled elsewhere: append a segment (K from column 0 of both arrays),
-// number the tiles and upload (cl CTAs per cluster), launch k_oz_gemm
+// number the tiles and upload, launch k_oz_gemm
 int oz_job_add_seg(OzJob& job, const SliceArray& A, int a_row0, const int* a_exp, const SliceArray& B, int b_row0,
                    const int* b_exp, int K, int nrows_b);
-int oz_job_upload(OzJob& job, int cl, cudaStream_t st);
+int oz_job_upload(OzJob& job, cudaStream_t st);
 int oz_job_launch(Context& ctx, const OzJob& job, cudaStream_t st);
 
 // density.cu: one- and two-body density matrices (Eqs. d1, d2)
@@ -392,7 +388,6 @@ struct MergedJob {
   std::vector<long long> ver;
   std::vector<void*> tbases;
   int tiles = 0;
-  int cl = 1;
 };
 // sigma_i = H(ctxs[i]) cs[i] for several contexts, contractions merged
 struct SigmaBatch {
@@ -400,7 +395,7 @@ struct SigmaBatch {
   std::vector<const double*> cs;
   std::vector<double*> ss;
   int nvec = 0, prec = 0;
-  MergedJob ab[2], sst;  // ab[cl - 1]: the opposite-spin jobs launched in clusters of cl CTAs
+  MergedJob ab, sst;  // the opposite-spin (or combined) jobs; the same-spin-only jobs
   DevBuf err;
   StreamPool pool;
 };

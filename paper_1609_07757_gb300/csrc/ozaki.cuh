@@ -89,23 +89,13 @@ __global__ void k_oz_slice(const double* __restrict__ X, int rows, int cols, lon
 //              epilogue warps, warps w and w+4 share TMEM lane quarter w % 4
 //              and take half of the columns each), finish each segment and
 //              release the accumulators (acc_free) for the next chunk.
-// With CL = 2 the kernel runs in clusters of two CTAs holding adjacent column
-// tiles of the same 128-row block (problems have an even tile count per
-// row): each CTA loads half of the rows of every A slice and multicasts it to
-// both, so the A operand crosses from L2 once per pair; a stage is released
-// only when both CTAs' MMAs are done with it (multicast commit, two arrivals
-// on empty[stage]); segments are skipped per pair, so both step through the
-// same K sequence; a cluster barrier follows the barrier set-up and precedes
-// the exit.
 // Every wait is bounded; a wait that runs out sets abort (all roles stop),
 // the kernel waits (bounded) for its copies in flight, frees TMEM and
 // reports through err.
-template <int CL>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_oz_gemm(const OzProblem* __restrict__ probs, int nprobs, const OzSeg* __restrict__ segs,
               const OzMaps* __restrict__ maps, double* tbase, double* const* __restrict__ tbases,
               int* __restrict__ err) {
-  static_assert(CL == 1 || CL == 2, "clusters of one or two CTAs");
   extern __shared__ unsigned char oz_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t s_stage0 = tc::smem_u32(smem);
@@ -128,14 +118,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   double* const Tp = P.t_rel ? (tbases ? tbases[P.tb] : tbase) + P.t : reinterpret_cast<double*>(P.t);
   const int tl = tile - P.tile_begin;
   const int m0 = (tl / P.tiles_n) * OZ_BM, n0 = (tl % P.tiles_n) * OZ_BN;
-  const int n0_pair = ((tl % P.tiles_n) & ~(CL - 1)) * OZ_BN;  // first column of the cluster
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int SPC = OZ_CHUNK / OZ_BK;  // steps per chunk
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < OZ_STAGES; ++s) {
       tc::mbar_init(tc::smem_u32(&full_b[s]), 1);
-      tc::mbar_init(tc::smem_u32(&empty_b[s]), CL);
+      tc::mbar_init(tc::smem_u32(&empty_b[s]), 1);
     }
     tc::mbar_init(tc::smem_u32(&chunk_b), 1);
     tc::mbar_init(tc::smem_u32(&free_b), 32 * OZ_EPI_WARPS);
@@ -144,7 +133,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     int ns = 0, steps = 0;
     for (int g = 0; g < P.seg_count && ns < OZ_MAX_SEGS; ++g) {
       OzSeg sg = segs[P.seg_begin + g];
-      if (n0_pair >= sg.nrows_b || sg.K <= 0) continue;
+      if (n0 >= sg.nrows_b || sg.K <= 0) continue;
       seg_s[ns] = sg;
       segid_s[ns] = P.seg_begin + g;
       step0_s[ns] = steps;
@@ -161,7 +150,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (CL == 2) tc::cluster_sync();  // the partner's barriers exist before any multicast
   tc::fence_after_sync();
   const uint32_t tmem = tmem_s;
   const int nseg = nseg_s;
@@ -181,10 +169,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // ---------------- producer (TMA)
     if (lane == 0) {
       int seg = -1, seg_end = 0, seg_begin = 0;
-      const CUtensorMap *ma = nullptr, *mah = nullptr, *mb = nullptr;
+      const CUtensorMap *ma = nullptr, *mb = nullptr;
       int ax = 0, ay = 0, bx = 0, by = 0;
       int issued = 0;
-      const int rank = CL == 2 ? (int)tc::cluster_rank() : 0;
       for (int g = 0; g < total; ++g) {
         const int st = g % OZ_STAGES;
         if (g >= OZ_STAGES && !wait(&empty_b[st], ((g / OZ_STAGES) - 1) & 1)) break;
@@ -194,7 +181,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           seg_end = step0_s[seg + 1];
           const OzSeg& S = seg_s[seg];
           ma = &maps[segid_s[seg]].a;
-          mah = &maps[segid_s[seg]].ah;
           mb = &maps[segid_s[seg]].b;
           ax = S.a_k0;
           ay = S.a_row0 + m0;
@@ -205,15 +191,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const uint32_t fb = tc::smem_u32(&full_b[st]);
         const uint32_t sa = s_stage0 + st * OZ_STAGE_BYTES;
         tc::mbar_arrive_expect_tx(fb, OZ_STAGE_BYTES);
-        if (CL == 1) {
-          tc::tma_load_3d(sa, ma, ax + k0, ay, 0, fb);
-        } else {
-          // this CTA's half of the rows of each A slice, to both CTAs
-#pragma unroll
-          for (int t = 0; t < OZ_S; ++t)
-            tc::tma_load_3d_mc(sa + t * OZ_A_SLICE_BYTES + rank * (OZ_A_SLICE_BYTES / 2), mah, ax + k0,
-                               ay + rank * (OZ_BM / 2), t, fb, (uint16_t)0x3);
-        }
+        tc::tma_load_3d(sa, ma, ax + k0, ay, 0, fb);
         tc::tma_load_3d(sa + OZ_S * OZ_A_SLICE_BYTES, mb, bx + k0, by, 0, fb);
         issued = g + 1;
       }
@@ -278,10 +256,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           tc::mma_bf16(tmem + 192, A(3), B(0), N128, 1u);
           tc::mma_bf16(tmem + 256, A(4), B(0), N64, 1u);
         }
-        if (CL == 2)
-          tc::mma_commit_mc(tc::smem_u32(&empty_b[st]), (uint16_t)0x3);  // both CTAs read this stage
-        else
-          tc::mma_commit(tc::smem_u32(&empty_b[st]));
+        tc::mma_commit(tc::smem_u32(&empty_b[st]));
         if (kin == SPC - 1 || local == seg_end - seg_begin - 1) {
           tc::mma_commit(tc::smem_u32(&chunk_b));
           ++chunk;
@@ -378,8 +353,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, OZ_TMEM_COLS);
   }
-  // no CTA leaves while its partner's copies or MMA commits may still reach it
-  if (CL == 2) tc::cluster_sync();
 }
 
 }  // namespace iscsi

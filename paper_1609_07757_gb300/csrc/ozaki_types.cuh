@@ -45,11 +45,10 @@ struct OzSeg {
 };
 
 // TMA descriptors of a segment's two slice arrays: dims (ld, rows, S), box
-// (16, 128 or 64, S), 32-byte swizzle; ah: A's array in boxes of (16, 64, 1).
-// Kept in global memory beside the segment list (one entry per segment).
+// (16, 128 or 64, S), 32-byte swizzle.  Kept in global memory beside the
+// segment list (one entry per segment).
 struct OzMaps {
   CUtensorMap a, b;
-  CUtensorMap ah;  // A in boxes of 16 x 64 rows x 1 slice (half tiles, two-CTA clusters)
   CUtensorMap bw;  // B in boxes of 16 x OZ_BW_ROWS rows x all slices (128-column tiles, tc32w.cuh)
 };
 

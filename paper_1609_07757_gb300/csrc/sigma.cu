@@ -870,9 +870,8 @@ int sigma_run(Context& ctx, const double* c, double* sigma, int nvec, int precis
 // ---------------------------------------------------------------------------
 // Autotuner: the kernel routing of a context (which products run on the
 // tensor cores, which on the FMA kernels) for one precision and vector count.
-// Candidates: the opposite-spin contraction on the tensor cores (in clusters
-// of one or two CTAs) or not, and the same-spin block threshold (16, 64, 256,
-// or none on the tensor cores).
+// Candidates: the opposite-spin contraction on the tensor cores or not, and
+// the same-spin block threshold (16, 64, 256, or none on the tensor cores).
 // A model from the flop counts and the kernels' measured rates (tensor-core
 // FP64-accurate contraction ~1.1 PFLOP/s of bf16 products, FP32 form ~0.6,
 // FP64 FMA ~1.1 TFLOP/s, FP32 FMA ~24 TFLOP/s) keeps the candidates within 3x
@@ -923,28 +922,27 @@ int sigma_autotune(Context& ctx, const double* c, double* sigma, int nvec, int p
   const bool tc_ok = prec == 32 ? options().fp32_tc : options().fp64_tc;
   const bool ss_ok = tc_ok && options().samespin_tc;
   struct Cand {
-    int ab, ss, cl;
+    int ab, ss;
     double pred, ms;
   };
   std::vector<Cand> cands;
   const int thr[4] = {kThinN, 64, 256, 1 << 30};
   for (int ab = tc_ok ? 1 : 0; ab >= 0; --ab)
-    for (int cl = 1; cl <= (ab && ctx.have_ab && options().tc_cluster == 1 ? 2 : 1); ++cl)
-      for (int i = 0; i < (ss_ok ? 4 : 1); ++i) {
-        const int ss = ss_ok ? thr[i] : (1 << 30);
-        // thresholds that route the same blocks are the same candidate
-        bool dup = false;
-        for (const Cand& q : cands) {
-          if (q.ab != ab || q.cl != cl) continue;
-          bool same = true;
-          for (int a = 0; a <= ctx.sp[0].maxlevel && same; ++a) {
-            double rows = block_rows(ctx, a), nba = (double)ctx.nb_allowed_lvl[a];
-            same = (rows > q.ss && nba > q.ss) == (rows > ss && nba > ss);
-          }
-          if (same) dup = true;
+    for (int i = 0; i < (ss_ok ? 4 : 1); ++i) {
+      const int ss = ss_ok ? thr[i] : (1 << 30);
+      // thresholds that route the same blocks are the same candidate
+      bool dup = false;
+      for (const Cand& q : cands) {
+        if (q.ab != ab) continue;
+        bool same = true;
+        for (int a = 0; a <= ctx.sp[0].maxlevel && same; ++a) {
+          double rows = block_rows(ctx, a), nba = (double)ctx.nb_allowed_lvl[a];
+          same = (rows > q.ss && nba > q.ss) == (rows > ss && nba > ss);
         }
-        if (!dup) cands.push_back({ab, ss, cl, route_model_ms(ctx, prec, ab, ss, nvec), -1.0});
+        if (same) dup = true;
       }
+      if (!dup) cands.push_back({ab, ss, route_model_ms(ctx, prec, ab, ss, nvec), -1.0});
+    }
   double best_pred = 1e300;
   for (const Cand& q : cands) best_pred = std::min(best_pred, q.pred);
   std::vector<Cand> keep;
@@ -959,7 +957,6 @@ int sigma_autotune(Context& ctx, const double* c, double* sigma, int nvec, int p
     for (Cand& q : keep) {
       R.ab_tc = q.ab;
       R.ss_min = q.ss;
-      R.cl = q.cl;
       ISCSI_TRY(sigma_run(ctx, c, sigma, nvec, prec));  // builds this routing's lists
       q.ms = 1e300;
       for (int rep = 0; rep < 3; ++rep) {
@@ -980,15 +977,13 @@ int sigma_autotune(Context& ctx, const double* c, double* sigma, int nvec, int p
     if ((q.ms >= 0 ? q.ms : q.pred) < (best->ms >= 0 ? best->ms : best->pred)) best = &q;
   R.ab_tc = best->ab;
   R.ss_min = best->ss;
-  R.cl = best->cl;
   for (const Cand& q : cands) {
     R.trials.push_back(q.ab);
     R.trials.push_back(q.ss >= (1 << 30) ? -1 : q.ss);
-    R.trials.push_back(q.cl);
     R.trials.push_back(q.pred);
     double ms = -1.0;
     for (const Cand& k2 : keep)
-      if (k2.ab == q.ab && k2.ss == q.ss && k2.cl == q.cl) ms = k2.ms;
+      if (k2.ab == q.ab && k2.ss == q.ss) ms = k2.ms;
     R.trials.push_back(ms);
   }
   return kOk;

@@ -181,10 +181,8 @@ __global__ void __launch_bounds__(256) k_t3_lift(TcTable tt, int n, int nholeA, 
 static int tc_attr() {
   static bool done = false;
   if (!done) {
-    ISCSI_CUDA(cudaFuncSetAttribute(k_oz_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES));
-    ISCSI_CUDA(cudaFuncSetAttribute(k_oz_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES));
-    ISCSI_CUDA(cudaFuncSetAttribute(k_tc32w_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, T3W_SMEM_BYTES));
-    ISCSI_CUDA(cudaFuncSetAttribute(k_tc32w_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, T3W_SMEM_BYTES));
+    ISCSI_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES));
+    ISCSI_CUDA(cudaFuncSetAttribute(k_tc32w_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, T3W_SMEM_BYTES));
     done = true;
   }
   return kOk;
@@ -240,7 +238,6 @@ static int add_seg(OzJob& job, const SliceArray& A, int a_row0, int a_k0, const 
   std::memset(&m, 0, sizeof(m));
   if (oz_encode_map(&m.a, A.base, A.ld, A.rows, nslice, A.slice, OZ_BM) ||
       oz_encode_map(&m.b, B.base, B.ld, B.rows, nslice, B.slice, OZ_BN) ||
-      oz_encode_map(&m.ah, A.base, A.ld, A.rows, nslice, A.slice, OZ_BM / 2, 1) ||
       oz_encode_map(&m.bw, B.base, B.ld, B.rows, nslice, B.slice, OZ_BW_ROWS)) {
     set_error("tensor-core sigma: TMA descriptor rejected");
     return kErrCuda;
@@ -268,44 +265,25 @@ static int upload_job(OzJob& job, cudaStream_t st) {
   return kOk;
 }
 
-// k_oz_gemm over a problem list; cl = 2 launches clusters of two CTAs (the
-// list's column-tile counts must then be even, add_tiles(probs, 2))
-static int launch_oz(int cl, int tiles, const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
+// k_oz_gemm over a problem list
+static int launch_oz(int tiles, const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
                      double* tbase, double* const* tbases, int* err, cudaStream_t st) {
   if (tiles == 0) return kOk;
-  if (cl == 2) {
-    cudaLaunchConfig_t cfg;
-    std::memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = dim3(tiles, 1, 1);
-    cfg.blockDim = dim3(OZ_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = OZ_SMEM_BYTES;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    ISCSI_CUDA(cudaLaunchKernelEx(&cfg, k_oz_gemm<2>, probs, nprobs, segs, maps, tbase, tbases, err)); ISCSI_COUNT_LAUNCH();
-  } else {
-    k_oz_gemm<1><<<tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(probs, nprobs, segs, maps, tbase, tbases, err); ISCSI_COUNT_LAUNCH();
-  }
+  k_oz_gemm<<<tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(probs, nprobs, segs, maps, tbase, tbases, err); ISCSI_COUNT_LAUNCH();
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
 }
 
 static int launch_job(Context& ctx, const OzJob& job, double* tbase, cudaStream_t st) {
-  return launch_oz(job.cl, job.tiles, job.d_probs.as<OzProblem>(), (int)job.probs.size(), job.d_segs.as<OzSeg>(),
+  return launch_oz(job.tiles, job.d_probs.as<OzProblem>(), (int)job.probs.size(), job.d_segs.as<OzSeg>(),
                    job.d_maps.as<OzMaps>(), tbase, nullptr, ctx.oz_err.as<int>(), st);
 }
 
-// tile numbering of a problem list; with cl = 2 every problem gets an even
-// number of column tiles (a cluster's two CTAs share a row block)
-static int add_tiles(std::vector<OzProblem>& probs, int cl = 1, int bn = OZ_BN) {
+// tile numbering of a problem list (bn columns per tile)
+static int add_tiles(std::vector<OzProblem>& probs, int bn = OZ_BN) {
   int tiles = 0;
   for (auto& p : probs) {
-    p.tiles_n = round_up(round_up(p.N, bn) / bn, cl);
+    p.tiles_n = round_up(p.N, bn) / bn;
     p.tile_begin = tiles;
     tiles += (round_up(p.M, OZ_BM) / OZ_BM) * p.tiles_n;
   }
@@ -352,8 +330,7 @@ int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec) {
   long long bs_elems = 0, exp_elems = 0;
   TcTable tt = ab_table(ctx, nvec, &bs_elems, &exp_elems);
   if (tt.nclass == 0) return kOk;
-  const int cl = options().tc_cluster == 2 || (options().tc_cluster == 1 && ctx.route[0].cl == 2) ? 2 : 1;
-  bool rebuild = ctx.oz_ab.nvec != nvec || ctx.oz_ab.tbase != (const void*)ttw || ctx.oz_ab.cl != cl;
+  bool rebuild = ctx.oz_ab.nvec != nvec || ctx.oz_ab.tbase != (const void*)ttw;
   if (ctx.oz_bs_elems < bs_elems) {
     ISCSI_TRY(ctx.oz_bs.alloc(sizeof(__nv_bfloat16) * bs_elems));
     ctx.oz_bs_elems = bs_elems;
@@ -392,8 +369,7 @@ int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec) {
                         C.ncols));
       job.probs.push_back(P);
     }
-    job.cl = cl;
-    job.tiles = add_tiles(job.probs, cl);
+    job.tiles = add_tiles(job.probs);
     ISCSI_TRY(upload_job(job, st));
     job.nvec = nvec;
     job.tbase = ttw;
@@ -631,34 +607,17 @@ static int t3_slice_matrix(const V* X, int rows, int cols, long long ld, int tra
   return kOk;
 }
 
-// k_tc32w_gemm over a problem list, in two-CTA clusters when cl = 2
-static int launch_t3(int cl, int tiles, const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
+// k_tc32w_gemm over a problem list
+static int launch_t3(int tiles, const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
                      float* tbase, float* const* tbases, int* err, cudaStream_t st) {
   if (tiles == 0) return kOk;
-  if (cl == 2) {
-    cudaLaunchConfig_t cfg;
-    std::memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = dim3(tiles, 1, 1);
-    cfg.blockDim = dim3(T3W_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = T3W_SMEM_BYTES;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    ISCSI_CUDA(cudaLaunchKernelEx(&cfg, k_tc32w_gemm<2>, probs, nprobs, segs, maps, tbase, tbases, err)); ISCSI_COUNT_LAUNCH();
-  } else {
-    k_tc32w_gemm<1><<<tiles, T3W_THREADS, T3W_SMEM_BYTES, st>>>(probs, nprobs, segs, maps, tbase, tbases, err); ISCSI_COUNT_LAUNCH();
-  }
+  k_tc32w_gemm<<<tiles, T3W_THREADS, T3W_SMEM_BYTES, st>>>(probs, nprobs, segs, maps, tbase, tbases, err); ISCSI_COUNT_LAUNCH();
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
 }
 
 static int t3_launch(Context& ctx, const OzJob& job, float* tbase, cudaStream_t st) {
-  return launch_t3(job.cl, job.tiles, job.d_probs.as<OzProblem>(), (int)job.probs.size(), job.d_segs.as<OzSeg>(),
+  return launch_t3(job.tiles, job.d_probs.as<OzProblem>(), (int)job.probs.size(), job.d_segs.as<OzSeg>(),
                    job.d_maps.as<OzMaps>(), tbase, nullptr, ctx.oz_err.as<int>(), st);
 }
 
@@ -681,8 +640,7 @@ int opposite_tc32_operands(Context& ctx, const float* c, float* ttw, int nvec) {
   long long bs_elems = 0, exp_elems = 0;
   TcTable tt = ab_table(ctx, nvec, &bs_elems, &exp_elems, T3_S);
   if (tt.nclass == 0) return kOk;
-  const int cl = options().tc_cluster == 2 || (options().tc_cluster == 1 && ctx.route[1].cl == 2) ? 2 : 1;
-  bool rebuild = ctx.t3_ab.nvec != nvec || ctx.t3_ab.tbase != (const void*)ttw || ctx.t3_ab.cl != cl;
+  bool rebuild = ctx.t3_ab.nvec != nvec || ctx.t3_ab.tbase != (const void*)ttw;
   if (ctx.t3_bs_elems < bs_elems) {
     ISCSI_TRY(ctx.t3_bs.alloc(sizeof(__nv_bfloat16) * bs_elems));
     ctx.t3_bs_elems = bs_elems;
@@ -711,8 +669,7 @@ int opposite_tc32_operands(Context& ctx, const float* c, float* ttw, int nvec) {
       ISCSI_TRY(add_seg(job, GA, 0, 0, nullptr, CB, 0, 0, nullptr, C.kpad, C.ncols, T3_S));
       job.probs.push_back(P);
     }
-    job.cl = cl;
-    job.tiles = add_tiles(job.probs, cl, T3W_BN);
+    job.tiles = add_tiles(job.probs, T3W_BN);
     ISCSI_TRY(upload_job(job, st));
     job.nvec = nvec;
     job.tbase = ttw;
@@ -827,7 +784,7 @@ int samespin_tc32_operands(Context& ctx, const float* c, float* sigma, int nvec)
         }
         if (P.seg_count > 0) job.probs.push_back(P);
       }
-    job.tiles = add_tiles(job.probs, 1, T3W_BN);
+    job.tiles = add_tiles(job.probs, T3W_BN);
     ISCSI_TRY(upload_job(job, st));
     job.nvec = nvec;
   }
@@ -853,10 +810,9 @@ int samespin_tc32_gemm(Context& ctx, float* sigma) { return t3_launch(ctx, ctx.t
 
 // The opposite-spin and same-spin problem lists of a context as one list
 // (one launch fills the GPU's waves better than two).  Rebuilt when either
-// source job changed; the same-spin problems take the opposite-spin job's
-// cluster shape.
+// source job changed.
 static int build_both(OzJob& both, const OzJob& ab, const OzJob& ss, int bn, cudaStream_t st) {
-  if (both.src_ver[0] == ab.version && both.src_ver[1] == ss.version && both.cl == ab.cl) return kOk;
+  if (both.src_ver[0] == ab.version && both.src_ver[1] == ss.version) return kOk;
   both.probs = ab.probs;
   both.segs = ab.segs;
   both.maps = ab.maps;
@@ -867,8 +823,7 @@ static int build_both(OzJob& both, const OzJob& ab, const OzJob& ss, int bn, cud
   }
   both.segs.insert(both.segs.end(), ss.segs.begin(), ss.segs.end());
   both.maps.insert(both.maps.end(), ss.maps.begin(), ss.maps.end());
-  both.cl = ab.cl;
-  both.tiles = add_tiles(both.probs, both.cl, bn);
+  both.tiles = add_tiles(both.probs, bn);
   ISCSI_TRY(upload_job(both, st));
   both.src_ver[0] = ab.version;
   both.src_ver[1] = ss.version;
@@ -898,13 +853,13 @@ int both_tc32_gemm(Context& ctx, float* sigma) {
 // one launch of the FP64-accurate (prec 64) or FP32-form (prec 32) contraction
 // over a device problem list whose relative outputs use the base table tbases
 int launch_tc_problems(const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
-                       void* const* tbases, int tiles, int prec, int cl, int* err, cudaStream_t st) {
+                       void* const* tbases, int tiles, int prec, int* err, cudaStream_t st) {
   if (tiles == 0) return kOk;
   ISCSI_TRY(tc_attr());
   if (prec == 64) {
-    return launch_oz(cl, tiles, probs, nprobs, segs, maps, nullptr, reinterpret_cast<double* const*>(tbases), err, st);
+    return launch_oz(tiles, probs, nprobs, segs, maps, nullptr, reinterpret_cast<double* const*>(tbases), err, st);
   } else {
-    return launch_t3(cl, tiles, probs, nprobs, segs, maps, nullptr, reinterpret_cast<float* const*>(tbases), err, st);
+    return launch_t3(tiles, probs, nprobs, segs, maps, nullptr, reinterpret_cast<float* const*>(tbases), err, st);
   }
 }
 
@@ -922,9 +877,8 @@ int oz_job_add_seg(OzJob& job, const SliceArray& A, int a_row0, const int* a_exp
   return add_seg(job, A, a_row0, 0, a_exp, B, b_row0, 0, b_exp, K, nrows_b);
 }
 
-int oz_job_upload(OzJob& job, int cl, cudaStream_t st) {
-  job.cl = cl;
-  job.tiles = add_tiles(job.probs, cl);
+int oz_job_upload(OzJob& job, cudaStream_t st) {
+  job.tiles = add_tiles(job.probs);
   return upload_job(job, st);
 }
 

@@ -14,8 +14,7 @@
 // the epilogue drains chunk c.  Per K step: one MMA of N = 128 into the
 // order-0 columns and five into the others.
 //
-// Warp 0 loads (TMA; A in 128-row boxes, or two 64-row halves multicast to a
-// cluster pair; B in 128-row boxes), warp 1 issues the MMAs, warps 2-9 drain
+// Warp 0 loads (TMA; A and B in 128-row boxes), warp 1 issues the MMAs, warps 2-9 drain
 // (two per TMEM lane quarter, 64 columns each).  Problems, segments and
 // tensor maps are the shared records (ozaki_types.cuh); tiles are numbered
 // with 128-column tiles (add_tiles with bn = 128).  Every wait is bounded; a
@@ -41,12 +40,10 @@ constexpr int T3W_EPI_WARPS = 8;
 constexpr int T3W_EPI_COLS = T3W_BN / (T3W_EPI_WARPS / 4);  // 64
 constexpr int T3W_THREADS = 64 + 32 * T3W_EPI_WARPS;
 
-template <int CL>
 __global__ void __launch_bounds__(T3W_THREADS, 1)
     k_tc32w_gemm(const OzProblem* __restrict__ probs, int nprobs, const OzSeg* __restrict__ segs,
                  const OzMaps* __restrict__ maps, float* tbase, float* const* __restrict__ tbases,
                  int* __restrict__ err) {
-  static_assert(CL == 1 || CL == 2, "clusters of one or two CTAs");
   extern __shared__ unsigned char t3w_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)t3w_smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t s_stage0 = tc::smem_u32(smem);
@@ -69,14 +66,13 @@ __global__ void __launch_bounds__(T3W_THREADS, 1)
   float* const Tp = P.t_rel ? (tbases ? tbases[P.tb] : tbase) + P.t : reinterpret_cast<float*>(P.t);
   const int tl = tile - P.tile_begin;
   const int m0 = (tl / P.tiles_n) * T3_BM, n0 = (tl % P.tiles_n) * T3W_BN;
-  const int n0_pair = ((tl % P.tiles_n) & ~(CL - 1)) * T3W_BN;  // first column of the cluster
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int SPC = T3_CHUNK_STEPS;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < T3W_STAGES; ++s) {
       tc::mbar_init(tc::smem_u32(&full_b[s]), 1);
-      tc::mbar_init(tc::smem_u32(&empty_b[s]), CL);
+      tc::mbar_init(tc::smem_u32(&empty_b[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(tc::smem_u32(&chunk_b[b]), 1);
@@ -87,7 +83,7 @@ __global__ void __launch_bounds__(T3W_THREADS, 1)
     int ns = 0, steps = 0;
     for (int g = 0; g < P.seg_count && ns < OZ_MAX_SEGS; ++g) {
       OzSeg sg = segs[P.seg_begin + g];
-      if (n0_pair >= sg.nrows_b || sg.K <= 0) continue;
+      if (n0 >= sg.nrows_b || sg.K <= 0) continue;
       seg_s[ns] = sg;
       segid_s[ns] = P.seg_begin + g;
       step0_s[ns] = steps;
@@ -104,7 +100,6 @@ __global__ void __launch_bounds__(T3W_THREADS, 1)
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (CL == 2) tc::cluster_sync();  // the partner's barriers exist before any multicast
   tc::fence_after_sync();
   const uint32_t tmem = tmem_s;
   const int nseg = nseg_s;
@@ -125,10 +120,9 @@ __global__ void __launch_bounds__(T3W_THREADS, 1)
     // ---------------- producer (TMA): all terms of A and of B per K step
     if (lane == 0) {
       int seg = -1, seg_end = 0, seg_begin = 0;
-      const CUtensorMap *ma = nullptr, *mah = nullptr, *mb = nullptr;
+      const CUtensorMap *ma = nullptr, *mb = nullptr;
       int ax = 0, ay = 0, bx = 0, by = 0;
       int issued = 0;
-      const int rank = CL == 2 ? (int)tc::cluster_rank() : 0;
       for (int g = 0; g < total; ++g) {
         const int st = g % T3W_STAGES;
         if (g >= T3W_STAGES && !wait(&empty_b[st], ((g / T3W_STAGES) - 1) & 1)) break;
@@ -138,7 +132,6 @@ __global__ void __launch_bounds__(T3W_THREADS, 1)
           seg_end = step0_s[seg + 1];
           const OzSeg& S = seg_s[seg];
           ma = &maps[segid_s[seg]].a;
-          mah = &maps[segid_s[seg]].ah;
           mb = &maps[segid_s[seg]].bw;
           ax = S.a_k0;
           ay = S.a_row0 + m0;
@@ -149,15 +142,7 @@ __global__ void __launch_bounds__(T3W_THREADS, 1)
         const uint32_t fb = tc::smem_u32(&full_b[st]);
         const uint32_t sa = s_stage0 + st * T3W_STAGE_BYTES;
         tc::mbar_arrive_expect_tx(fb, T3W_STAGE_BYTES);
-        if (CL == 1) {
-          tc::tma_load_3d(sa, ma, ax + k0, ay, 0, fb);
-        } else {
-          // this CTA's half of the rows of each A term, to both CTAs
-#pragma unroll
-          for (int t = 0; t < T3_S; ++t)
-            tc::tma_load_3d_mc(sa + t * T3_A_SLICE_BYTES + rank * (T3_A_SLICE_BYTES / 2), mah, ax + k0,
-                               ay + rank * (T3_BM / 2), t, fb, (uint16_t)0x3);
-        }
+        tc::tma_load_3d(sa, ma, ax + k0, ay, 0, fb);
         tc::tma_load_3d(sa + T3_S * T3_A_SLICE_BYTES, mb, bx + k0, by, 0, fb);
         issued = g + 1;
       }
@@ -186,10 +171,7 @@ __global__ void __launch_bounds__(T3W_THREADS, 1)
         tc::mma_bf16(D1, A(0), B(2), N128, 1u);
         tc::mma_bf16(D1, A(1), B(1), N128, 1u);
         tc::mma_bf16(D1, A(2), B(0), N128, 1u);
-        if (CL == 2)
-          tc::mma_commit_mc(tc::smem_u32(&empty_b[st]), (uint16_t)0x3);  // both CTAs read this stage
-        else
-          tc::mma_commit(tc::smem_u32(&empty_b[st]));
+        tc::mma_commit(tc::smem_u32(&empty_b[st]));
         if (kin == SPC - 1 || g == total - 1) tc::mma_commit(tc::smem_u32(&chunk_b[b]));
       }
       if (abort_s) {
@@ -248,8 +230,6 @@ __global__ void __launch_bounds__(T3W_THREADS, 1)
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, T3W_TMEM_COLS);
   }
-  // no CTA leaves while its partner's copies or MMA commits may still reach it
-  if (CL == 2) tc::cluster_sync();
 }
 
 }  // namespace iscsi

@@ -50,25 +50,6 @@ TC_DEVI void tma_load_3d(uint32_t dst, const void* map, int x, int y, int z, uin
       "l"(map), "r"(x), "r"(y), "r"(z), "r"(mbar)
       : "memory");
 }
-// the same, multicast: the box lands at the same shared-memory offset in every
-// CTA of the cluster named in cta_mask, each of whose mbarrier at offset mbar
-// receives the transaction bytes
-TC_DEVI void tma_load_3d_mc(uint32_t dst, const void* map, int x, int y, int z, uint32_t mbar, uint16_t cta_mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster "
-      "[%0], [%1, {%2, %3, %4}], [%5], %6;\n" ::"r"(dst),
-      "l"(map), "r"(x), "r"(y), "r"(z), "r"(mbar), "h"(cta_mask)
-      : "memory");
-}
-TC_DEVI uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
-  return r;
-}
-// all threads of all CTAs of the cluster (release / acquire)
-TC_DEVI void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
 TC_DEVI void prefetch_map(const void* map) {
   asm volatile("prefetch.tensormap [%0];\n" ::"l"(map) : "memory");
 }
@@ -115,13 +96,6 @@ TC_DEVI void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t 
 // arrive on an mbarrier once all previously issued MMAs of this thread complete
 TC_DEVI void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar) : "memory");
-}
-// the same, arriving on the mbarrier at offset mbar in every CTA of cta_mask
-TC_DEVI void mma_commit_mc(uint32_t mbar, uint16_t cta_mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n" ::"r"(
-                   mbar),
-               "h"(cta_mask)
-               : "memory");
 }
 // 32 lanes x 16 consecutive 32-bit columns: thread i gets lane (base lane + i)
 TC_DEVI void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
