@@ -494,6 +494,19 @@ iscsi_status iscsi_stats(char* json, int len) {
     std::snprintf(v, sizeof(v), ", \"samespin_tc_bf16_flops\": %.17g, \"both_tc_fp64\": %d, \"both_tc_fp32\": %d",
                   ctx_gemm_flops(*ctx, 3), both(64) ? 1 : 0, both(32) ? 1 : 0);
     out += v;
+    // the schedule of the FP64 tensor-core launch sigma makes (the combined
+    // list when both contractions run there): bf16 MMA flops it issues (live
+    // slices of non-screened blocks only), its CTAs, work items, split tiles
+    // and the cost model's balance
+    {
+      const OzJob& J = both(64) ? ctx->oz_both : ctx->oz_ab;
+      const OzPlan& pl = J.plan;
+      std::snprintf(v, sizeof(v),
+                    ", \"tc_schedule_fp64\": {\"issued_bf16_flops\": %.17g, \"grid\": %d, \"items\": %d, "
+                    "\"split_tiles\": %d, \"tiles\": %d, \"model_balance\": %.4f}",
+                    pl.issued_products, pl.grid, (int)pl.items.size(), pl.counters, J.tiles, pl.model_balance);
+      out += v;
+    }
     // GAS restriction: subspaces (0: none) and kept determinants
     std::snprintf(v, sizeof(v), ", \"gas_subspaces\": %d, \"gas_ndet\": %lld, \"level_split\": [%d, %d]",
                   ctx->gas_nspace, ctx->gas_ndet, ctx->sp[0].nocc, ctx->sp[1].nocc);

@@ -21,7 +21,7 @@ namespace iscsi {
 namespace {
 
 // one problem list over the given jobs; rebuilt only when a job changed
-int merge_jobs(MergedJob& mj, const std::vector<const OzJob*>& jobs, const std::vector<void*>& tbases,
+int merge_jobs(MergedJob& mj, const std::vector<const OzJob*>& jobs, const std::vector<void*>& tbases, int prec,
                cudaStream_t st) {
   bool same = mj.src == jobs && mj.tbases == tbases;
   for (size_t i = 0; same && i < jobs.size(); ++i) same = mj.ver[i] == jobs[i]->version;
@@ -29,6 +29,7 @@ int merge_jobs(MergedJob& mj, const std::vector<const OzJob*>& jobs, const std::
   mj.probs.clear();
   mj.segs.clear();
   mj.maps.clear();
+  mj.sh.clear();
   mj.tiles = 0;
   for (size_t i = 0; i < jobs.size(); ++i) {
     const OzJob& J = *jobs[i];
@@ -41,6 +42,7 @@ int merge_jobs(MergedJob& mj, const std::vector<const OzJob*>& jobs, const std::
     }
     mj.segs.insert(mj.segs.end(), J.segs.begin(), J.segs.end());
     mj.maps.insert(mj.maps.end(), J.maps.begin(), J.maps.end());
+    mj.sh.insert(mj.sh.end(), J.sh.begin(), J.sh.end());
     mj.tiles += J.tiles;
   }
   ISCSI_TRY(mj.d_probs.grow(sizeof(OzProblem) * std::max<size_t>(1, mj.probs.size())));
@@ -60,6 +62,8 @@ int merge_jobs(MergedJob& mj, const std::vector<const OzJob*>& jobs, const std::
     ISCSI_CUDA(cudaMemcpyAsync(mj.d_tbases.p, tbases.data(), sizeof(void*) * tbases.size(), cudaMemcpyHostToDevice,
                                st));
   ISCSI_CUDA(cudaStreamSynchronize(st));  // the host vectors may change after this call
+  // the FP64-accurate kernel is persistent: all contexts' tiles share one schedule
+  if (prec == 64) ISCSI_TRY(oz_plan_build(mj.probs, mj.segs, mj.sh, mj.plan, st));
   mj.src = jobs;
   mj.tbases = tbases;
   mj.ver.resize(jobs.size());
@@ -70,7 +74,7 @@ int merge_jobs(MergedJob& mj, const std::vector<const OzJob*>& jobs, const std::
 int launch_merged(const MergedJob& mj, int prec, int* err, cudaStream_t st) {
   if (mj.tiles == 0) return kOk;
   return launch_tc_problems(mj.d_probs.as<OzProblem>(), (int)mj.probs.size(), mj.d_segs.as<OzSeg>(),
-                            mj.d_maps.as<OzMaps>(), mj.d_tbases.as<void*>(), mj.tiles, prec, err, st);
+                            mj.d_maps.as<OzMaps>(), mj.d_tbases.as<void*>(), mj.tiles, &mj.plan, prec, err, st);
 }
 
 struct BatchState {
@@ -196,7 +200,7 @@ int sigma_batch_sequence(SigmaBatch& B) {
         jobs.push_back(J);
         tb.push_back(base);
       }
-      ISCSI_TRY(merge_jobs(B.ab, jobs, tb, st));
+      ISCSI_TRY(merge_jobs(B.ab, jobs, tb, B.prec, st));
       ISCSI_TRY(launch_merged(B.ab, B.prec, B.err.as<int>(), st));
     }
     ISCSI_TRY(phase_all(B, kPhAbGemm, /*skip_tc=*/true));
@@ -212,7 +216,7 @@ int sigma_batch_sequence(SigmaBatch& B) {
       jobs.push_back(B.prec == 64 ? &c.oz_ss : &c.t3_ss);
       tb.push_back(B.prec == 64 ? static_cast<void*>(B.ss[i]) : static_cast<void*>(c.s32.as<float>()));
     }
-    ISCSI_TRY(merge_jobs(B.sst, jobs, tb, st));
+    ISCSI_TRY(merge_jobs(B.sst, jobs, tb, B.prec, st));
     ISCSI_TRY(launch_merged(B.sst, B.prec, B.err.as<int>(), st));
   }
   ISCSI_TRY(phase_all(B, kPhPost));

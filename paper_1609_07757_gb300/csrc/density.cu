@@ -628,6 +628,7 @@ static int build_job(Context& ctx, bool sym) {
   job.probs.clear();
   job.segs.clear();
   job.maps.clear();
+  job.sh.clear();
   double f[2] = {0.0, 0.0};
   for (int b = 0; b < 3; ++b) {
     const DmBlock& B = P.blk[b];

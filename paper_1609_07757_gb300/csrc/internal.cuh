@@ -141,11 +141,36 @@ struct SliceArray {
   long long rows, slice;
 };
 
+// host copies of a segment's live-slice maps (OzSeg::a_live / b_live), read
+// by the scheduler's cost model (null: every slice live)
+struct OzSegHost {
+  const int* a_live = nullptr;
+  const int* b_live = nullptr;
+};
+
+// schedule of one persistent k_oz_gemm launch (oz_schedule.cu): work items in
+// execution order, CTA b running [cta_start[b], cta_start[b + 1]); split-K
+// workspace (slots blocks of 128 x 64 doubles) and its counters
+struct OzPlan {
+  std::vector<OzItem> items;
+  std::vector<int> cta_start;
+  int grid = 0;
+  int slots = 0, counters = 0;
+  double issued_products = 0;  // bf16 MMA flops the launch issues (live slices only)
+  double model_cycles = 0;     // predicted cycles of the busiest CTA
+  double model_balance = 1;    // average over busiest predicted CTA load
+  DevBuf d_items, d_cta, d_ws, d_cnt;
+};
+int oz_plan_build(const std::vector<OzProblem>& probs, const std::vector<OzSeg>& segs,
+                  const std::vector<OzSegHost>& sh, OzPlan& plan, cudaStream_t st);
+
 // a tensor-core work list (problems + segments) kept on the device
 struct OzJob {
   std::vector<OzProblem> probs;
   std::vector<OzSeg> segs;
   std::vector<OzMaps> maps;  // one per segment
+  std::vector<OzSegHost> sh; // one per segment (FP64-accurate jobs)
+  OzPlan plan;               // FP64-accurate jobs: the persistent launch's schedule
   DevBuf d_probs, d_segs, d_maps;
   int tiles = 0;
   int nvec = -1;
@@ -198,14 +223,20 @@ struct Context {
   ProblemList<double> pl_ab64, pl_ss64;
   ProblemList<float> pl_ab32, pl_ss32;
   int pl_nvec64 = 0, pl_nvec32 = 0;
-  // tensor-core FP64 contractions (sigma_tc.cu)
+  // tensor-core FP64 contractions (sigma_tc.cu); the slice arrays are tiled
+  // (ozaki_types.cuh) with live-slice maps per block (device and host)
   DevBuf oz_gs, oz_gexp, oz_bs, oz_bexp, oz_err;
+  DevBuf oz_glive, oz_malive, oz_mblive;
+  std::vector<int> oz_glive_h, oz_malive_h, oz_mblive_h;
+  std::vector<int> oz_mabase;  // first tiled row of each alpha level block in M_alpha's slices
   int oz_mpad = 0, oz_kpad = 0;
   long long oz_bs_elems = 0;
   OzJob oz_ab, oz_ss, oz_both;  // oz_both: oz_ab and oz_ss as one problem list
   DevBuf oz_mas, oz_maexp, oz_mbs, oz_mbexp, oz_cs, oz_csexp;
   std::vector<int> oz_kbase;
   int oz_ma_rows = 0, oz_ma_ld = 0, oz_mb_rows = 0, oz_mb_ld = 0;
+  int t3_ma_rows = 0;                 // rows of the FP32 form's M_alpha slices (TMA layout)
+  DevBuf oz_marow, oz_macol;          // tiled row -> alpha string, column -> alpha string of M_alpha's slices
   long long oz_cs_elems = 0;
   bool oz_m_ready = false;
   // kernel routing per precision ([0] FP64, [1] FP32), chosen by the autotuner
@@ -321,8 +352,11 @@ int samespin_tc32_gemm(Context& ctx, float* sigma);
 int both_tc_gemm(Context& ctx, double* sigma);  // opposite- and same-spin contractions, one launch
 int both_tc32_gemm(Context& ctx, float* sigma);
 const OzJob* both_tc_job(Context& ctx, int prec);  // that combined job (built when needed), or nullptr
+// one launch over a device problem list whose relative outputs use the base
+// table tbases: the FP64-accurate kernel on plan's schedule (prec 64), else
+// the FP32-form kernel over `tiles` tiles
 int launch_tc_problems(const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
-                       void* const* tbases, int tiles, int prec, int* err, cudaStream_t st);
+                       void* const* tbases, int tiles, const OzPlan* plan, int prec, int* err, cudaStream_t st);
 int tc_check(Context& ctx);
 int samespin_matrices_changed(Context& ctx);  // re-cut the same-spin operand slices in place
 // M <- M_base + f M_v (cpl: the context of v); f = 0 restores (sigma.cu)
@@ -383,6 +417,8 @@ struct MergedJob {
   std::vector<OzProblem> probs;
   std::vector<OzSeg> segs;
   std::vector<OzMaps> maps;
+  std::vector<OzSegHost> sh;
+  OzPlan plan;  // FP64-accurate batches
   DevBuf d_probs, d_segs, d_maps, d_tbases;
   std::vector<const OzJob*> src;
   std::vector<long long> ver;

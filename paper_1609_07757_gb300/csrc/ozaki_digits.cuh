@@ -41,6 +41,38 @@ __device__ __forceinline__ void oz_store_digits(const int (&a)[OZ_S], __nv_bfloa
   for (int s = 0; s < OZ_S; ++s) out[s * slice_stride] = __float2bfloat16_rn(__int2float_rn(a[s]) * scale[s]);
 }
 
+// bf16 bit pattern of slice s of a digit: a 2^-7s (exact)
+__device__ __forceinline__ uint32_t oz_digit_bits(int a, int s) {
+  const float scale[OZ_S] = {1.0f, 0.0078125f, 6.103515625e-05f, 4.76837158203125e-07f, 3.7252902984619141e-09f,
+                             2.9103830456733704e-11f, 2.2737367544323206e-13f};  // 2^-7t, exact
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(__int2float_rn(a) * scale[s]));
+}
+
+// q 2^e as the nearest double (ties to even), built in integer arithmetic
+// (GB300's FP64 units, which the int64 -> double conversion uses, issue about
+// two operations per clock per SM); |q| < 2^63; results below the normal
+// range give 0
+__device__ __forceinline__ double oz_i64_scaled(long long q, int e) {
+  if (q == 0) return 0.0;
+  unsigned long long u = q < 0 ? 0ull - (unsigned long long)q : (unsigned long long)q;
+  const int lz = __clzll((long long)u);
+  u <<= lz;  // leading one at bit 63
+  unsigned long long mant = u >> 11;  // 53 bits with the leading one
+  const unsigned long long rem = u & 0x7FFull;
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ++mant;
+  int ex = 63 - lz + e;  // q 2^e = mant 2^(ex - 52)
+  if (mant >> 53) {
+    mant >>= 1;
+    ++ex;
+  }
+  const int biased = ex + 1023;
+  if (biased <= 0) return 0.0;
+  unsigned long long bits = biased >= 2047 ? 0x7FF0000000000000ull
+                                           : ((unsigned long long)biased << 52) | (mant & 0xFFFFFFFFFFFFFull);
+  if (q < 0) bits |= 1ull << 63;
+  return __longlong_as_double((long long)bits);
+}
+
 // exponent field of |x|: frexp exponent = field - 1022 for normal x (0 for zero)
 __device__ __forceinline__ int oz_exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
 

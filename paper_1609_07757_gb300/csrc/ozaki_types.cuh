@@ -22,31 +22,64 @@ constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;  // warp 0 loads (TMA), warp 
 constexpr int OZ_A_SLICE_BYTES = OZ_BM * OZ_BK * 2;   // 4096
 constexpr int OZ_B_SLICE_BYTES = OZ_BN * OZ_BK * 2;   // 2048
 constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_SLICE_BYTES + OZ_B_SLICE_BYTES);
-constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + 1024;
+constexpr int OZ_ZERO_BYTES = OZ_A_SLICE_BYTES + OZ_B_SLICE_BYTES;  // zero operands (clearing MMAs)
+constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + OZ_ZERO_BYTES + 1024;
 constexpr int OZ_TMEM_COLS = 512;  // 7 levels x 64 columns used
 constexpr long long OZ_SPIN = 1ll << 24;
 
 constexpr int OZ_MAX_SEGS = 8;
 constexpr int OZ_BW_ROWS = 128;    // rows of B per 128-column tile; B arrays are padded to this
 
-// One operand pair of a product: A[M][K] and B[N][K], both read through TMA
-// from K-major slice arrays [S][rows][ld] (bf16).  The segment's block starts
-// at (a_row0, a_k0) in A's array and (b_row0, b_k0) in B's; k offsets are
-// multiples of 16.  Slice arrays are zero padded so that tiles need no bounds
-// checks: A rows to the tile multiple of 128, B rows to the multiple of 64, K
-// to a multiple of 16.  Rows of B at or beyond nrows_b contribute nothing
-// (tiles wholly beyond are skipped).
+// Tiled operand arrays (the FP64-accurate contraction's own layout).  An
+// array of R-row tiles (R = OZ_BM for an A operand, OZ_BN for a B operand) and
+// K steps of 16 is stored block by block, block (row tile rt, k step ks) at
+// element (rt * kst + ks) * OZ_S * R * 16, so that all slices of one tile and
+// K step are one contiguous run that a single bulk copy brings into shared
+// memory.  Inside a block, slice s starts at s * R * 16 and element (r, k)
+// sits in the tensor core's no-swizzle K-major layout of 8-row x 16-byte core
+// matrices: core matrix (r / 8, k / 8) at 128 bytes * (2 (r / 8) + k / 8),
+// row r % 8 at 16 bytes within it (descriptor: K-adjacent core matrices 128
+// bytes apart, row groups 256 bytes apart).  Consecutive slices of a B block
+// then read as one operand of 64 (levels) rows, which the MMA's N extent
+// spans.
+constexpr int OZ_TA_BLOCK = OZ_S * OZ_BM * OZ_BK;  // elements of one A block (28 KB)
+constexpr int OZ_TB_BLOCK = OZ_S * OZ_BN * OZ_BK;  // elements of one B block (14 KB)
+__host__ __device__ constexpr int oz_tiled_elem(int r, int k) {
+  return (((r >> 3) << 1) + ((k & 15) >> 3)) * 64 + ((r & 7) << 3) + (k & 7);
+}
+
+// One operand pair of a product: A[M][K] and B[N][K].  Two sources:
+//  * tiled (a_tiled != nullptr): both operands are tiled arrays; the segment
+//    starts at row tile a_rt0 / b_rt0 and k step a_ks0 / b_ks0 of its arrays,
+//    whose rows hold kst k steps each; a_live / b_live (or null: all live)
+//    give per block the number of live slices, 7 - (the first slice with a
+//    nonzero digit anywhere in the block): 0 marks a block whose values all
+//    vanish (screened units, zero rows), and the products of its leading
+//    zero slices are skipped;
+//  * TMA (a_tiled == nullptr): K-major slice arrays [S][rows][ld] read through
+//    the tensor maps of the segment (OzMaps), block (a_row0, a_k0) of A's and
+//    (b_row0, b_k0) of B's; k offsets are multiples of 16; arrays are zero
+//    padded so that tiles need no bounds checks (A rows to a multiple of 128,
+//    B rows to 64, K to 16).
+// Rows of B at or beyond nrows_b contribute nothing (tiles wholly beyond are
+// skipped).
 struct OzSeg {
   const int* a_exp;  // row exponents of A (index = problem row)
   const int* b_exp;  // row exponents of B (index = problem column)
   int a_row0, a_k0, b_row0, b_k0;
   int K;             // multiple of 16
   int nrows_b;       // valid rows of B
+  const __nv_bfloat16* a_tiled;
+  const __nv_bfloat16* b_tiled;
+  const int* a_live;
+  const int* b_live;
+  int a_kst, b_kst;
+  int a_rt0, a_ks0, b_rt0, b_ks0;
 };
 
 // TMA descriptors of a segment's two slice arrays: dims (ld, rows, S), box
 // (16, 128 or 64, S), 32-byte swizzle.  Kept in global memory beside the
-// segment list (one entry per segment).
+// segment list (one entry per segment; unused for tiled segments).
 struct OzMaps {
   CUtensorMap a, b;
   CUtensorMap bw;  // B in boxes of 16 x OZ_BW_ROWS rows x all slices (128-column tiles, tc32w.cuh)
@@ -65,6 +98,17 @@ struct OzProblem {
   int seg_begin, seg_count;
   int tiles_n, tile_begin;
   int accumulate;  // 1: add to T, 0: overwrite with the first segment
+};
+
+// One work item of the persistent contraction: the output tile (mt, nt) of
+// problem prob over the K steps [s0, s1) of its segments taken in order.  A
+// tile cut into nparts > 1 items (split K) leaves part p's FP64 result in
+// workspace block slot + p (128 x 64 doubles each); the part that raises
+// counter cnt to nparts adds the blocks in part order into T and resets it.
+struct OzItem {
+  int prob, mt, nt;
+  int s0, s1;
+  int part, nparts, slot, cnt;
 };
 
 }  // namespace iscsi

@@ -2,18 +2,21 @@
 // (tcgen05), with FP64 accuracy from exact bf16 slices (ozaki.cuh).
 //
 // Opposite spin, per sigma call and column level class c:
-//   k_oz_lift_row   : per column (X,Y,v), Ct^T[(X,Y,v)][(q,s)] = s s c[X u q, Y u s]
-//                     gathered once through the contraction/addition tables,
-//                     the column's exponent, and its 7 exact bf16 slices (the
-//                     B operand, K-major)
-//   k_oz_gemm       : T_c = G[:M_c, :K_c] Ct_c for all classes, one launch
+//   k_oz_lift_tiled : per column (X,Y,v), Ct^T[(X,Y,v)][(q,s)] = s s c[X u q, Y u s]
+//                     gathered through the contraction/addition tables, the
+//                     column's exponent, and its 7 exact bf16 slices (the B
+//                     operand, tiled: ozaki_types.cuh)
+//   k_oz_gemm       : T_c = G[:M_c, :K_c] Ct_c for all classes, one persistent
+//                     launch (schedule: oz_schedule.cu)
 // Same spin, per excitation-level block a of the CI vector (rows = alpha
 // strings of level a, columns = the allowed beta prefix):
 //   sigma_a += sum_a' M_alpha[a, a'] C_a'   (A = M_alpha slices, B = C_a'^T)
 //            + C_a M_beta^T                 (A = C_a slices, B = M_beta slices)
 // as one multi-segment product per block; blocks with at most 16 rows or
 // columns stay on the FP64 thin kernels of sigma.cu.
-// G's, M_alpha's and M_beta's slices are built once per context (first use).
+// G's, M_alpha's and M_beta's slices are built once per context (first use),
+// with a live-slice map per block: blocks of screened (zero) units are never
+// loaded, and leading zero slices are not multiplied.
 //
 // The FP32 form (tc32.cuh) runs the same two contractions with three bf16
 // terms per element and FP32 accumulation (k_tc32w_gemm): no exponents, no
@@ -49,6 +52,7 @@ struct TcTable {
   TcClass c[2 * kMaxElec];
   long long start[2 * kMaxElec + 1];  // flattened (col, k) element offsets
   int col_start[2 * kMaxElec + 1];    // first column of each class over all classes
+  int blk_start[2 * kMaxElec + 1];    // first block of 8 columns of each class (tiled lift)
 };
 
 static inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -109,54 +113,68 @@ __device__ __forceinline__ int oz_stage_column(const TcTable& tt, int n, int nho
   return cl;
 }
 
-__global__ void __launch_bounds__(256) k_oz_lift_row(TcTable tt, int n, int nholeA, int nholeB,
-                                                     const int* __restrict__ pair_of, const int* __restrict__ hp_inv,
-                                                     const int* __restrict__ liftA, const int* __restrict__ liftB,
-                                                     const int8_t* __restrict__ alevel,
-                                                     const int* __restrict__ nballow, const long long* __restrict__ off,
-                                                     const double* __restrict__ c, long long ndet,
-                                                     int* __restrict__ exps, __nv_bfloat16* __restrict__ bs) {
-  __shared__ OzLiftCol L;
-  __shared__ int sm[8];
-  __shared__ int ex_s;
-  int col, vv;
-  const TcClass& C = tt.c[oz_stage_column(tt, n, nholeA, nholeB, hp_inv, liftA, liftB, alevel, nballow, off, L, col, vv)];
-  const double* cv = c + (long long)vv * ndet;
-  double v[kOzRowRegs];
-  int m = 0;
-#pragma unroll
-  for (int i = 0; i < kOzRowRegs; ++i) {
-    const int k = threadIdx.x + i * blockDim.x;
-    v[i] = k < C.kpad ? oz_lift_value<double>(L, C, k, n, pair_of, cv) : 0.0;
-    m = max(m, oz_exp_field(v[i]));
-  }
-  for (int k = threadIdx.x + kOzRowRegs * blockDim.x; k < C.kpad; k += blockDim.x)
-    m = max(m, oz_exp_field(oz_lift_value<double>(L, C, k, n, pair_of, cv)));
-  m = __reduce_max_sync(0xffffffffu, m);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int x = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) x = max(x, sm[i]);
-    ex_s = x > 0 ? x - 1022 : 0;
-    exps[C.exp_off + col] = ex_s;
-  }
-  __syncthreads();
-  const int ex = ex_s;
-  __nv_bfloat16* row = bs + C.bs_off + (long long)col * C.kpad;
-  const long long stride = (long long)C.npad * C.kpad;
-  int a[OZ_S];
-#pragma unroll
-  for (int i = 0; i < kOzRowRegs; ++i) {
-    const int k = threadIdx.x + i * blockDim.x;
-    if (k < C.kpad) {
-      oz_digits(v[i], ex, a);
-      oz_store_digits(a, row + k, stride);
+// The B operand of the opposite-spin contraction in the tiled layout: one
+// block per 8 consecutive columns (X, Y, v) of one class, one warp per
+// column.  A warp stages its column's lift entries, finds the column's
+// exponent (largest |x|) in a first pass over the K values, then gathers them
+// again in 8-wide chunks, cuts each into exact slices and writes every slice's
+// chunk as one 16-byte store (the 8 warps of a block fill the 8 rows of a
+// core matrix: whole 128-byte runs).  Columns beyond the class stay zero.
+__global__ void __launch_bounds__(256) k_oz_lift_tiled(TcTable tt, int n, int nholeA, int nholeB,
+                                                       const int* __restrict__ pair_of,
+                                                       const int* __restrict__ hp_inv, const int* __restrict__ liftA,
+                                                       const int* __restrict__ liftB, const int8_t* __restrict__ alevel,
+                                                       const int* __restrict__ nballow,
+                                                       const long long* __restrict__ off, const double* __restrict__ c,
+                                                       long long ndet, int* __restrict__ exps,
+                                                       __nv_bfloat16* __restrict__ bs) {
+  __shared__ OzLiftCol Ls[8];
+  int cl = 0;
+  while ((int)blockIdx.x >= tt.blk_start[cl + 1]) ++cl;
+  const TcClass& C = tt.c[cl];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int col = ((int)blockIdx.x - tt.blk_start[cl]) * 8 + warp;
+  if (col >= C.ncols) return;  // the whole warp; nothing below synchronises the block
+  OzLiftCol& L = Ls[warp];
+  const int hp = col / tt.nvec, vv = col - (col / tt.nvec) * tt.nvec;
+  const int xy = hp_inv[C.hp_start + hp];
+  const int X = xy / nholeB, Y = xy - (xy / nholeB) * nholeB;
+  for (int q = lane; q < n; q += 32) {
+    const int ea = liftA[q * nholeA + X];
+    L.a[q] = ea;
+    L.b[q] = liftB[q * nholeB + Y];
+    if (ea >= 0) {
+      const int A = ea >> 1;
+      L.off[q] = off[A];
+      L.lim[q] = nballow[alevel[A]];
     }
   }
-  for (int k = threadIdx.x + kOzRowRegs * blockDim.x; k < C.kpad; k += blockDim.x) {
-    oz_digits(oz_lift_value<double>(L, C, k, n, pair_of, cv), ex, a);
-    oz_store_digits(a, row + k, stride);
+  __syncwarp();
+  const double* cv = c + (long long)vv * ndet;
+  int m = 0;
+  for (int k = lane; k < C.kpad; k += 32) m = max(m, oz_exp_field(oz_lift_value<double>(L, C, k, n, pair_of, cv)));
+  m = __reduce_max_sync(0xffffffffu, m);
+  const int ex = m > 0 ? m - 1022 : 0;
+  if (lane == 0) exps[C.exp_off + col] = ex;
+  const int kst = C.kpad / OZ_BK;
+  __nv_bfloat16* tile0 = bs + C.bs_off + (long long)(col / OZ_BN) * kst * OZ_TB_BLOCK;
+  for (int kc = lane; kc < 2 * kst; kc += 32) {
+    uint32_t pk[OZ_S][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      int a[OZ_S];
+      oz_digits(oz_lift_value<double>(L, C, kc * 8 + j, n, pair_of, cv), ex, a);
+#pragma unroll
+      for (int sl = 0; sl < OZ_S; ++sl) {
+        const uint32_t b = oz_digit_bits(a[sl], sl);
+        if (j & 1) pk[sl][j >> 1] |= b << 16;
+        else pk[sl][j >> 1] = b;
+      }
+    }
+    __nv_bfloat16* base = tile0 + (long long)(kc >> 1) * OZ_TB_BLOCK + oz_tiled_elem(col % OZ_BN, kc * 8);
+#pragma unroll
+    for (int sl = 0; sl < OZ_S; ++sl)
+      *reinterpret_cast<uint4*>(base + sl * OZ_BN * OZ_BK) = make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
   }
 }
 
@@ -195,15 +213,32 @@ static int tc_err_buf(Context& ctx) {
   return kOk;
 }
 
-// slices of a row-major (or transposed) FP64 matrix with per-row exponents
-static int slice_matrix(const double* X, int rows, int cols, long long ld, int trans, const int* colmap, int ldo,
-                        int rows_pad, int* exps, __nv_bfloat16* out, cudaStream_t st) {
-  if (rows > 0) k_oz_row_exp<<<rows, 256, 0, st>>>(X, rows, cols, ld, trans, exps); ISCSI_COUNT_LAUNCH();
-  long long slice = (long long)rows_pad * ldo;
-  if (slice > 0)
-    k_oz_slice<<<launch_blocks(slice, 256), 256, 0, st>>>(X, rows, cols, ld, trans, colmap, exps, out, slice, ldo,
-                                                          rows_pad); ISCSI_COUNT_LAUNCH();
+// tiled slices (ozaki_types.cuh) of a row-major (or transposed) FP64 matrix
+// with per-source-row exponents: rows_pad tiled rows (a multiple of RT) of
+// kpad columns (a multiple of 16), tiled row r holding source row rowmap[r]
+// (or r), tiled column k source column colmap[k] (or k); live (or null):
+// the live slices of every block, recomputed here
+static int slice_tiled(const double* X, int rows, int cols, long long ld, int trans, const int* rowmap,
+                       const int* colmap, int RT, int rows_pad, int kpad, int* exps, __nv_bfloat16* out, int* live,
+                       cudaStream_t st) {
+  if (rows > 0) {
+    k_oz_row_exp<<<rows, 256, 0, st>>>(X, rows, cols, ld, trans, exps); ISCSI_COUNT_LAUNCH();
+  }
+  const int kst = kpad / OZ_BK;
+  if (live) ISCSI_CUDA(cudaMemsetAsync(live, 0, sizeof(int) * (size_t)(rows_pad / RT) * kst, st));
+  const long long threads = (long long)rows_pad * 2 * kst;
+  if (threads > 0) {
+    k_oz_slice_tiled<<<launch_blocks(threads, 256), 256, 0, st>>>(X, rows, cols, ld, trans, rowmap, colmap, exps, out,
+                                                                  RT, rows_pad, kst, live); ISCSI_COUNT_LAUNCH();
+  }
   ISCSI_CUDA(cudaGetLastError());
+  return kOk;
+}
+
+// device live map -> host copy (the schedule's cost model; synchronises)
+static int live_to_host(const DevBuf& d, size_t n, std::vector<int>& h) {
+  h.resize(n);
+  if (n) ISCSI_CUDA(cudaMemcpy(h.data(), d.p, sizeof(int) * n, cudaMemcpyDeviceToHost));
   return kOk;
 }
 
@@ -216,16 +251,59 @@ static int tc_prepare_g(Context& ctx) {
   ctx.oz_mpad = round_up(np, OZ_BM);
   ctx.oz_kpad = round_up(np, OZ_BK);
   long long slice = (long long)ctx.oz_mpad * ctx.oz_kpad;
+  const size_t nblk = (size_t)(ctx.oz_mpad / OZ_BM) * (ctx.oz_kpad / OZ_BK);
   ISCSI_TRY(ctx.oz_gs.alloc(sizeof(__nv_bfloat16) * slice * OZ_S));
   ISCSI_TRY(ctx.oz_gexp.alloc(sizeof(int) * np));
-  return slice_matrix(ctx.G64.as<double>(), np, np, np, 0, nullptr, ctx.oz_kpad, ctx.oz_mpad, ctx.oz_gexp.as<int>(),
-                      ctx.oz_gs.as<__nv_bfloat16>(), st);
+  ISCSI_TRY(ctx.oz_glive.alloc(sizeof(int) * nblk));
+  ISCSI_TRY(slice_tiled(ctx.G64.as<double>(), np, np, np, 0, nullptr, nullptr, OZ_BM, ctx.oz_mpad, ctx.oz_kpad,
+                        ctx.oz_gexp.as<int>(), ctx.oz_gs.as<__nv_bfloat16>(), ctx.oz_glive.as<int>(), st));
+  return live_to_host(ctx.oz_glive, nblk, ctx.oz_glive_h);
+}
+
+// a tiled operand: the array (block (0, 0)), its k steps per row tile, the
+// segment's first row tile and k step, live map (device, host) or none
+struct TiledOp {
+  const __nv_bfloat16* base;
+  int kst, rt0, ks0;
+  const int* live;
+  const int* live_h;
+};
+
+// segment of a job over two tiled operands
+static int add_seg_tiled(OzJob& job, const TiledOp& A, const int* a_exp, const TiledOp& B, const int* b_exp, int K,
+                         int nrows_b) {
+  OzSeg sg;
+  std::memset(&sg, 0, sizeof(sg));
+  sg.a_exp = a_exp;
+  sg.b_exp = b_exp;
+  sg.K = K;
+  sg.nrows_b = nrows_b;
+  sg.a_tiled = A.base;
+  sg.b_tiled = B.base;
+  sg.a_live = A.live;
+  sg.b_live = B.live;
+  sg.a_kst = A.kst;
+  sg.b_kst = B.kst;
+  sg.a_rt0 = A.rt0;
+  sg.a_ks0 = A.ks0;
+  sg.b_rt0 = B.rt0;
+  sg.b_ks0 = B.ks0;
+  OzMaps m;
+  std::memset(&m, 0, sizeof(m));
+  OzSegHost h;
+  h.a_live = A.live_h;
+  h.b_live = B.live_h;
+  job.segs.push_back(sg);
+  job.maps.push_back(m);
+  job.sh.push_back(h);
+  return kOk;
 }
 
 // segment of a job: block (a_row0, a_k0) of A times block (b_row0, b_k0) of B
 static int add_seg(OzJob& job, const SliceArray& A, int a_row0, int a_k0, const int* a_exp, const SliceArray& B,
                    int b_row0, int b_k0, const int* b_exp, int K, int nrows_b, int nslice = OZ_S) {
   OzSeg sg;
+  std::memset(&sg, 0, sizeof(sg));
   sg.a_exp = a_exp;
   sg.b_exp = b_exp;
   sg.a_row0 = a_row0;
@@ -244,10 +322,13 @@ static int add_seg(OzJob& job, const SliceArray& A, int a_row0, int a_k0, const 
   }
   job.segs.push_back(sg);
   job.maps.push_back(m);
+  job.sh.push_back(OzSegHost());
   return kOk;
 }
 
-static int upload_job(OzJob& job, cudaStream_t st) {
+// the job's lists on the device; persistent (FP64-accurate) jobs also get
+// their schedule
+static int upload_job(OzJob& job, cudaStream_t st, bool persistent = true) {
   ++job.version;
   ISCSI_TRY(job.d_probs.grow(sizeof(OzProblem) * std::max<size_t>(1, job.probs.size())));
   ISCSI_TRY(job.d_segs.grow(sizeof(OzSeg) * std::max<size_t>(1, job.segs.size())));
@@ -262,21 +343,24 @@ static int upload_job(OzJob& job, cudaStream_t st) {
     ISCSI_CUDA(cudaMemcpyAsync(job.d_segs.p, job.segs.data(), sizeof(OzSeg) * job.segs.size(), cudaMemcpyHostToDevice,
                                st));
   ISCSI_CUDA(cudaStreamSynchronize(st));  // the host vectors must outlive the copies
+  if (persistent) ISCSI_TRY(oz_plan_build(job.probs, job.segs, job.sh, job.plan, st));
   return kOk;
 }
 
-// k_oz_gemm over a problem list
-static int launch_oz(int tiles, const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
+// one persistent k_oz_gemm launch on a schedule
+static int launch_oz(const OzPlan& plan, const OzProblem* probs, const OzSeg* segs, const OzMaps* maps,
                      double* tbase, double* const* tbases, int* err, cudaStream_t st) {
-  if (tiles == 0) return kOk;
-  k_oz_gemm<<<tiles, OZ_THREADS, OZ_SMEM_BYTES, st>>>(probs, nprobs, segs, maps, tbase, tbases, err); ISCSI_COUNT_LAUNCH();
+  if (plan.grid == 0) return kOk;
+  k_oz_gemm<<<plan.grid, OZ_THREADS, OZ_SMEM_BYTES, st>>>(probs, segs, maps, plan.d_items.as<OzItem>(),
+                                                          plan.d_cta.as<int>(), tbase, tbases, plan.d_ws.as<double>(),
+                                                          plan.d_cnt.as<int>(), err); ISCSI_COUNT_LAUNCH();
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
 }
 
 static int launch_job(Context& ctx, const OzJob& job, double* tbase, cudaStream_t st) {
-  return launch_oz(job.tiles, job.d_probs.as<OzProblem>(), (int)job.probs.size(), job.d_segs.as<OzSeg>(),
-                   job.d_maps.as<OzMaps>(), tbase, nullptr, ctx.oz_err.as<int>(), st);
+  return launch_oz(job.plan, job.d_probs.as<OzProblem>(), job.d_segs.as<OzSeg>(), job.d_maps.as<OzMaps>(), tbase,
+                   nullptr, ctx.oz_err.as<int>(), st);
 }
 
 // tile numbering of a problem list (bn columns per tile)
@@ -313,6 +397,7 @@ static TcTable ab_table(const Context& ctx, int nvec, long long* bs_elems, long 
     C.tot = (long long)C.ncols * C.kpad;
     tt.start[tt.nclass] = flat;
     tt.col_start[tt.nclass + 1] = tt.col_start[tt.nclass] + C.ncols;
+    tt.blk_start[tt.nclass + 1] = tt.blk_start[tt.nclass] + (C.ncols + 7) / 8;
     tt.c[tt.nclass++] = C;
     flat += C.tot;
     bs += (long long)nslice * C.npad * C.kpad;
@@ -347,11 +432,13 @@ int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec) {
     job.probs.clear();
     job.segs.clear();
     job.maps.clear();
+    job.sh.clear();
     long long t_off = 0;
-    const SliceArray GA{ctx.oz_gs.as<__nv_bfloat16>(), ctx.oz_kpad, ctx.oz_mpad, (long long)ctx.oz_mpad * ctx.oz_kpad};
+    const TiledOp GA{ctx.oz_gs.as<__nv_bfloat16>(), ctx.oz_kpad / OZ_BK, 0, 0, ctx.oz_glive.as<int>(),
+                     ctx.oz_glive_h.data()};
     for (int i = 0; i < tt.nclass; ++i) {
       const TcClass& C = tt.c[i];
-      const SliceArray CB{ctx.oz_bs.as<__nv_bfloat16>() + C.bs_off, C.kpad, C.npad, (long long)C.npad * C.kpad};
+      const TiledOp CB{ctx.oz_bs.as<__nv_bfloat16>() + C.bs_off, C.kpad / OZ_BK, 0, 0, nullptr, nullptr};
       OzProblem P;
       std::memset(&P, 0, sizeof(P));
       // T_c sits where the fold expects it: classes in order, mrows x ncols each
@@ -365,8 +452,8 @@ int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec) {
       P.seg_count = 1;
       P.accumulate = 0;
       t_off += (long long)mrows * C.ncols;
-      ISCSI_TRY(add_seg(job, GA, 0, 0, ctx.oz_gexp.as<int>(), CB, 0, 0, ctx.oz_bexp.as<int>() + C.exp_off, C.kpad,
-                        C.ncols));
+      ISCSI_TRY(add_seg_tiled(job, GA, ctx.oz_gexp.as<int>(), CB, ctx.oz_bexp.as<int>() + C.exp_off, C.kpad,
+                              C.ncols));
       job.probs.push_back(P);
     }
     job.tiles = add_tiles(job.probs);
@@ -376,12 +463,12 @@ int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec) {
   }
   const SpinSpace& SA = ctx.sp[0];
   const SpinSpace& SB = ctx.sp[1];
-  const int ncol_all = tt.col_start[tt.nclass];
-  if (ncol_all > 0) {
-    k_oz_lift_row<<<ncol_all, 256, 0, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_of.as<int>(), ctx.hp_inv.as<int>(),
-                                            SA.lift.as<int>(), SB.lift.as<int>(), SA.level.as<int8_t>(),
-                                            ctx.nballow.as<int>(), ctx.off.as<long long>(), c, ctx.ndet,
-                                            ctx.oz_bexp.as<int>(), ctx.oz_bs.as<__nv_bfloat16>()); ISCSI_COUNT_LAUNCH();
+  const int nblk = tt.blk_start[tt.nclass];
+  if (nblk > 0) {
+    k_oz_lift_tiled<<<nblk, 256, 0, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_of.as<int>(), ctx.hp_inv.as<int>(),
+                                          SA.lift.as<int>(), SB.lift.as<int>(), SA.level.as<int8_t>(),
+                                          ctx.nballow.as<int>(), ctx.off.as<long long>(), c, ctx.ndet,
+                                          ctx.oz_bexp.as<int>(), ctx.oz_bs.as<__nv_bfloat16>()); ISCSI_COUNT_LAUNCH();
   }
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
@@ -425,28 +512,42 @@ static int tc_prepare_m(Context& ctx, bool cut_only = false) {
   const SpinSpace& SA = ctx.sp[0];
   const SpinSpace& SB = ctx.sp[1];
   int nl = SA.maxlevel + 1;
-  // M_alpha: rows = alpha strings (+ one tile of zero rows), columns grouped
-  // by level with each group padded to 16 so every segment starts aligned
-  ctx.oz_kbase.assign(nl + 1, 0);
-  for (int a = 0; a < nl; ++a) ctx.oz_kbase[a + 1] = ctx.oz_kbase[a] + round_up(SA.level_start[a + 1] - SA.level_start[a], OZ_BK);
+  // M_alpha (the A operand of the alpha part): every level block's rows start
+  // at a 128-row tile of their own, columns grouped by level with each group
+  // padded to 16, so every segment starts on a block boundary
   if (ctx.na > 0 && ctx.M64[0].p) {
-    int kcols = ctx.oz_kbase[nl];
-    std::vector<int> colmap(kcols, -1);
-    for (int a = 0; a < nl; ++a)
-      for (int i = SA.level_start[a]; i < SA.level_start[a + 1]; ++i) colmap[ctx.oz_kbase[a] + i - SA.level_start[a]] = i;
-    DevBuf dmap;
-    ISCSI_TRY(dmap.alloc(sizeof(int) * kcols));
-    ISCSI_CUDA(cudaMemcpyAsync(dmap.p, colmap.data(), sizeof(int) * kcols, cudaMemcpyHostToDevice, st));
-    ctx.oz_ma_rows = SA.count + OZ_BM;
-    ctx.oz_ma_ld = kcols;
     if (!cut_only) {
-      ISCSI_TRY(ctx.oz_mas.alloc(sizeof(__nv_bfloat16) * OZ_S * (size_t)ctx.oz_ma_rows * kcols));
-      ISCSI_TRY(ctx.oz_maexp.alloc(sizeof(int) * ctx.oz_ma_rows));
-      ISCSI_CUDA(cudaMemsetAsync(ctx.oz_maexp.p, 0, sizeof(int) * ctx.oz_ma_rows, st));
+      ctx.oz_kbase.assign(nl + 1, 0);
+      ctx.oz_mabase.assign(nl + 1, 0);
+      for (int a = 0; a < nl; ++a) {
+        const int rows = SA.level_start[a + 1] - SA.level_start[a];
+        ctx.oz_kbase[a + 1] = ctx.oz_kbase[a] + round_up(rows, OZ_BK);
+        ctx.oz_mabase[a + 1] = ctx.oz_mabase[a] + round_up(rows, OZ_BM);
+      }
+      const int kcols = ctx.oz_kbase[nl], trows = ctx.oz_mabase[nl];
+      std::vector<int> colmap(kcols, -1), rowmap(trows, -1);
+      for (int a = 0; a < nl; ++a)
+        for (int i = SA.level_start[a]; i < SA.level_start[a + 1]; ++i) {
+          colmap[ctx.oz_kbase[a] + i - SA.level_start[a]] = i;
+          rowmap[ctx.oz_mabase[a] + i - SA.level_start[a]] = i;
+        }
+      ISCSI_TRY(ctx.oz_macol.alloc(sizeof(int) * kcols));
+      ISCSI_TRY(ctx.oz_marow.alloc(sizeof(int) * trows));
+      ISCSI_CUDA(cudaMemcpy(ctx.oz_macol.p, colmap.data(), sizeof(int) * kcols, cudaMemcpyHostToDevice));
+      ISCSI_CUDA(cudaMemcpy(ctx.oz_marow.p, rowmap.data(), sizeof(int) * trows, cudaMemcpyHostToDevice));
+      ctx.oz_ma_rows = trows;
+      ctx.oz_ma_ld = kcols;
+      ISCSI_TRY(ctx.oz_mas.alloc(sizeof(__nv_bfloat16) * OZ_S * (size_t)trows * kcols));
+      ISCSI_TRY(ctx.oz_maexp.alloc(sizeof(int) * (SA.count + OZ_BM)));
+      ISCSI_CUDA(cudaMemsetAsync(ctx.oz_maexp.p, 0, sizeof(int) * (SA.count + OZ_BM), st));
+      ISCSI_TRY(ctx.oz_malive.alloc(sizeof(int) * (size_t)(trows / OZ_BM) * (kcols / OZ_BK)));
     }
-    ISCSI_TRY(slice_matrix(ctx.M64[0].as<double>(), SA.count, SA.count, SA.count, 0, dmap.as<int>(), kcols,
-                           ctx.oz_ma_rows, ctx.oz_maexp.as<int>(), ctx.oz_mas.as<__nv_bfloat16>(), st));
-    ISCSI_CUDA(cudaStreamSynchronize(st));  // colmap lives until here
+    ISCSI_TRY(slice_tiled(ctx.M64[0].as<double>(), SA.count, SA.count, SA.count, 0, ctx.oz_marow.as<int>(),
+                          ctx.oz_macol.as<int>(), OZ_BM, ctx.oz_ma_rows, ctx.oz_ma_ld, ctx.oz_maexp.as<int>(),
+                          ctx.oz_mas.as<__nv_bfloat16>(), ctx.oz_malive.as<int>(), st));
+    if (!cut_only)
+      ISCSI_TRY(live_to_host(ctx.oz_malive, (size_t)(ctx.oz_ma_rows / OZ_BM) * (ctx.oz_ma_ld / OZ_BK),
+                             ctx.oz_malive_h));
   }
   if (ctx.nb > 0) {
     // M_beta[B][B'] as the B operand; the stored beta matrix is M_beta^T
@@ -455,12 +556,17 @@ static int tc_prepare_m(Context& ctx, bool cut_only = false) {
     int trans = ctx.beta_alias ? 0 : 1;
     ctx.oz_mb_rows = round_up(SB.count, OZ_BW_ROWS);
     ctx.oz_mb_ld = round_up(SB.count, OZ_BK);
+    const size_t nblk = (size_t)(ctx.oz_mb_rows / OZ_BN) * (ctx.oz_mb_ld / OZ_BK);
     if (!cut_only) {
       ISCSI_TRY(ctx.oz_mbs.alloc(sizeof(__nv_bfloat16) * OZ_S * (size_t)ctx.oz_mb_rows * ctx.oz_mb_ld));
       ISCSI_TRY(ctx.oz_mbexp.alloc(sizeof(int) * ctx.oz_mb_rows));
+      ISCSI_CUDA(cudaMemsetAsync(ctx.oz_mbexp.p, 0, sizeof(int) * ctx.oz_mb_rows, st));
+      ISCSI_TRY(ctx.oz_mblive.alloc(sizeof(int) * nblk));
     }
-    ISCSI_TRY(slice_matrix(Mb, SB.count, SB.count, SB.count, trans, nullptr, ctx.oz_mb_ld, ctx.oz_mb_rows,
-                           ctx.oz_mbexp.as<int>(), ctx.oz_mbs.as<__nv_bfloat16>(), st));
+    ISCSI_TRY(slice_tiled(Mb, SB.count, SB.count, SB.count, trans, nullptr, nullptr, OZ_BN, ctx.oz_mb_rows,
+                          ctx.oz_mb_ld, ctx.oz_mbexp.as<int>(), ctx.oz_mbs.as<__nv_bfloat16>(),
+                          ctx.oz_mblive.as<int>(), st));
+    if (!cut_only) ISCSI_TRY(live_to_host(ctx.oz_mblive, nblk, ctx.oz_mblive_h));
   }
   ctx.oz_m_ready = true;
   return kOk;
@@ -534,10 +640,9 @@ int samespin_tc_operands(Context& ctx, const double* c, double* sigma, int nvec)
     job.probs.clear();
     job.segs.clear();
     job.maps.clear();
-    const SliceArray MA{ctx.oz_mas.as<__nv_bfloat16>(), ctx.oz_ma_ld, ctx.oz_ma_rows,
-                        (long long)ctx.oz_ma_rows * ctx.oz_ma_ld};
-    const SliceArray MB{ctx.oz_mbs.as<__nv_bfloat16>(), ctx.oz_mb_ld, ctx.oz_mb_rows,
-                        (long long)ctx.oz_mb_rows * ctx.oz_mb_ld};
+    job.sh.clear();
+    const TiledOp MB{ctx.oz_mbs.as<__nv_bfloat16>(), ctx.oz_mb_ld / OZ_BK, 0, 0, ctx.oz_mblive.as<int>(),
+                     ctx.oz_mblive_h.data()};
     for (int v = 0; v < nvec; ++v)
       for (const SsBlock& b : blocks) {
         if (!samespin_block_on_tc(ctx, b.a, 64)) continue;
@@ -553,15 +658,16 @@ int samespin_tc_operands(Context& ctx, const double* c, double* sigma, int nvec)
         if (ctx.na > 0 && ctx.oz_mas.p)
           for (const SsBlock& b2 : blocks) {
             if (std::abs(b.a - b2.a) > 2) continue;
-            const SliceArray CT{cs + v * elems1 + b2.bt_off, b2.bt_ld, b2.bt_rows, (long long)b2.bt_rows * b2.bt_ld};
-            ISCSI_TRY(add_seg(job, MA, b.start, ctx.oz_kbase[b2.a], ctx.oz_maexp.as<int>() + b.start, CT, 0, 0,
-                              cx + v * exps1 + b2.bt_exp, b2.bt_ld, std::min(b.nba, b2.nba)));
+            const TiledOp MA{ctx.oz_mas.as<__nv_bfloat16>(), ctx.oz_ma_ld / OZ_BK, ctx.oz_mabase[b.a] / OZ_BM,
+                             ctx.oz_kbase[b2.a] / OZ_BK, ctx.oz_malive.as<int>(), ctx.oz_malive_h.data()};
+            const TiledOp CT{cs + v * elems1 + b2.bt_off, b2.bt_ld / OZ_BK, 0, 0, nullptr, nullptr};
+            ISCSI_TRY(add_seg_tiled(job, MA, ctx.oz_maexp.as<int>() + b.start, CT, cx + v * exps1 + b2.bt_exp,
+                                    b2.bt_ld, std::min(b.nba, b2.nba)));
             P.seg_count++;
           }
         if (ctx.nb > 0 && ctx.oz_mbs.p) {
-          const SliceArray CA{cs + v * elems1 + b.ca_off, b.ca_ld, b.ca_rows, (long long)b.ca_rows * b.ca_ld};
-          ISCSI_TRY(add_seg(job, CA, 0, 0, cx + v * exps1 + b.ca_exp, MB, 0, 0, ctx.oz_mbexp.as<int>(), b.ca_ld,
-                            b.nba));
+          const TiledOp CA{cs + v * elems1 + b.ca_off, b.ca_ld / OZ_BK, 0, 0, nullptr, nullptr};
+          ISCSI_TRY(add_seg_tiled(job, CA, cx + v * exps1 + b.ca_exp, MB, ctx.oz_mbexp.as<int>(), b.ca_ld, b.nba));
           P.seg_count++;
         }
         if (P.seg_count > 0) job.probs.push_back(P);
@@ -579,11 +685,11 @@ int samespin_tc_operands(Context& ctx, const double* c, double* sigma, int nvec)
       if (!used) continue;
       const double* X = c + (long long)v * ctx.ndet + b.obase;  // [rows][nba]
       if (ctx.na > 0)
-        ISCSI_TRY(slice_matrix(X, b.nba, b.rows, b.nba, 1, nullptr, b.bt_ld, b.bt_rows, cx + v * exps1 + b.bt_exp,
-                               cs + v * elems1 + b.bt_off, st));
+        ISCSI_TRY(slice_tiled(X, b.nba, b.rows, b.nba, 1, nullptr, nullptr, OZ_BN, b.bt_rows, b.bt_ld,
+                              cx + v * exps1 + b.bt_exp, cs + v * elems1 + b.bt_off, nullptr, st));
       if (ctx.nb > 0 && samespin_block_on_tc(ctx, b.a, 64))
-        ISCSI_TRY(slice_matrix(X, b.rows, b.nba, b.nba, 0, nullptr, b.ca_ld, b.ca_rows, cx + v * exps1 + b.ca_exp,
-                               cs + v * elems1 + b.ca_off, st));
+        ISCSI_TRY(slice_tiled(X, b.rows, b.nba, b.nba, 0, nullptr, nullptr, OZ_BM, b.ca_rows, b.ca_ld,
+                              cx + v * exps1 + b.ca_exp, cs + v * elems1 + b.ca_off, nullptr, st));
     }
   (void)SB;
   (void)sigma;
@@ -652,6 +758,7 @@ int opposite_tc32_operands(Context& ctx, const float* c, float* ttw, int nvec) {
     job.probs.clear();
     job.segs.clear();
     job.maps.clear();
+    job.sh.clear();
     long long t_off = 0;
     const SliceArray GA{ctx.t3_gs.as<__nv_bfloat16>(), ctx.oz_kpad, ctx.oz_mpad, (long long)ctx.oz_mpad * ctx.oz_kpad};
     for (int i = 0; i < tt.nclass; ++i) {
@@ -670,7 +777,7 @@ int opposite_tc32_operands(Context& ctx, const float* c, float* ttw, int nvec) {
       job.probs.push_back(P);
     }
     job.tiles = add_tiles(job.probs, T3W_BN);
-    ISCSI_TRY(upload_job(job, st));
+    ISCSI_TRY(upload_job(job, st, false));
     job.nvec = nvec;
     job.tbase = ttw;
   }
@@ -714,11 +821,11 @@ static int t3_prepare_m(Context& ctx, bool cut_only = false) {
     DevBuf dmap;
     ISCSI_TRY(dmap.alloc(sizeof(int) * kcols));
     ISCSI_CUDA(cudaMemcpyAsync(dmap.p, colmap.data(), sizeof(int) * kcols, cudaMemcpyHostToDevice, st));
-    ctx.oz_ma_rows = SA.count + OZ_BM;
+    ctx.t3_ma_rows = SA.count + OZ_BM;
     ctx.oz_ma_ld = kcols;
-    if (!cut_only) ISCSI_TRY(ctx.t3_mas.alloc(sizeof(__nv_bfloat16) * T3_S * (size_t)ctx.oz_ma_rows * kcols));
+    if (!cut_only) ISCSI_TRY(ctx.t3_mas.alloc(sizeof(__nv_bfloat16) * T3_S * (size_t)ctx.t3_ma_rows * kcols));
     ISCSI_TRY(t3_slice_matrix<double>(ctx.M64[0].as<double>(), SA.count, SA.count, SA.count, 0, dmap.as<int>(), kcols,
-                                      ctx.oz_ma_rows, ctx.t3_mas.as<__nv_bfloat16>(), st));
+                                      ctx.t3_ma_rows, ctx.t3_mas.as<__nv_bfloat16>(), st));
     ISCSI_CUDA(cudaStreamSynchronize(st));  // colmap lives until here
   }
   if (ctx.nb > 0) {
@@ -753,8 +860,9 @@ int samespin_tc32_operands(Context& ctx, const float* c, float* sigma, int nvec)
     job.probs.clear();
     job.segs.clear();
     job.maps.clear();
-    const SliceArray MA{ctx.t3_mas.as<__nv_bfloat16>(), ctx.oz_ma_ld, ctx.oz_ma_rows,
-                        (long long)ctx.oz_ma_rows * ctx.oz_ma_ld};
+    job.sh.clear();
+    const SliceArray MA{ctx.t3_mas.as<__nv_bfloat16>(), ctx.oz_ma_ld, ctx.t3_ma_rows,
+                        (long long)ctx.t3_ma_rows * ctx.oz_ma_ld};
     const SliceArray MB{ctx.t3_mbs.as<__nv_bfloat16>(), ctx.oz_mb_ld, ctx.oz_mb_rows,
                         (long long)ctx.oz_mb_rows * ctx.oz_mb_ld};
     for (int v = 0; v < nvec; ++v)
@@ -785,7 +893,7 @@ int samespin_tc32_operands(Context& ctx, const float* c, float* sigma, int nvec)
         if (P.seg_count > 0) job.probs.push_back(P);
       }
     job.tiles = add_tiles(job.probs, T3W_BN);
-    ISCSI_TRY(upload_job(job, st));
+    ISCSI_TRY(upload_job(job, st, false));
     job.nvec = nvec;
   }
   for (int v = 0; v < nvec; ++v)
@@ -823,8 +931,10 @@ static int build_both(OzJob& both, const OzJob& ab, const OzJob& ss, int bn, cud
   }
   both.segs.insert(both.segs.end(), ss.segs.begin(), ss.segs.end());
   both.maps.insert(both.maps.end(), ss.maps.begin(), ss.maps.end());
+  both.sh = ab.sh;
+  both.sh.insert(both.sh.end(), ss.sh.begin(), ss.sh.end());
   both.tiles = add_tiles(both.probs, bn);
-  ISCSI_TRY(upload_job(both, st));
+  ISCSI_TRY(upload_job(both, st, bn == OZ_BN));
   both.src_ver[0] = ab.version;
   both.src_ver[1] = ss.version;
   return kOk;
@@ -853,14 +963,14 @@ int both_tc32_gemm(Context& ctx, float* sigma) {
 // one launch of the FP64-accurate (prec 64) or FP32-form (prec 32) contraction
 // over a device problem list whose relative outputs use the base table tbases
 int launch_tc_problems(const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
-                       void* const* tbases, int tiles, int prec, int* err, cudaStream_t st) {
-  if (tiles == 0) return kOk;
+                       void* const* tbases, int tiles, const OzPlan* plan, int prec, int* err, cudaStream_t st) {
   ISCSI_TRY(tc_attr());
   if (prec == 64) {
-    return launch_oz(tiles, probs, nprobs, segs, maps, nullptr, reinterpret_cast<double* const*>(tbases), err, st);
-  } else {
-    return launch_t3(tiles, probs, nprobs, segs, maps, nullptr, reinterpret_cast<float* const*>(tbases), err, st);
+    if (!plan) return kOk;
+    return launch_oz(*plan, probs, segs, maps, nullptr, reinterpret_cast<double* const*>(tbases), err, st);
   }
+  if (tiles == 0) return kOk;
+  return launch_t3(tiles, probs, nprobs, segs, maps, nullptr, reinterpret_cast<float* const*>(tbases), err, st);
 }
 
 // the same-spin string matrices changed in place: cut the slices prepared so far again
@@ -894,6 +1004,10 @@ int tc_check(Context& ctx) {
   int h = 0;
   ISCSI_CUDA(cudaMemcpy(&h, ctx.oz_err.p, sizeof(int), cudaMemcpyDeviceToHost));
   if (h) {
+    // the aborted launch may have left split-K counters raised: rebuild the
+    // context's work lists (and schedules) before the next launch
+    ctx.oz_ab.nvec = ctx.oz_ss.nvec = ctx.t3_ab.nvec = ctx.t3_ss.nvec = -1;
+    ctx.oz_both.src_ver[0] = ctx.t3_both.src_ver[0] = -1;
     set_error("tensor-core sigma: a bounded device wait ran out");
     return kErrWait;
   }
