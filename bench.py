@@ -38,9 +38,11 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 rate (no FP64 figure in MEASURED_PEAKS.js
 BF16_FALLBACK_TFLOPS = 1900.0  # dense bf16, recipe fallback (burst) when MEASURED_PEAKS.json is absent
 FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
 L2_FLUSH_BYTES = 512 << 20
+ORACLE_UPDATES_PER_S = 2.0e8  # the row-wise oracle on 16 Grace cores (sizes its samples)
 
 WORKLOADS = {
-    "fci_n60": dict(n=60, na=2, nb=2, kmax=4, ell=4.0, nchol=60, box=False, seed=1000, tau=1e-14),
+    "fci_n60": dict(n=60, na=2, nb=2, kmax=4, ell=4.0, nchol=60, box=False, seed=1000, tau=1e-14,
+                    taus=(1e-14, 1e-12, 1e-10)),
     "fci_n10": dict(n=10, na=2, nb=2, kmax=4, ell=3.0, nchol=20, box=False, seed=0, tau=1e-14),
     "fci_n100": dict(n=100, na=2, nb=2, kmax=4, ell=5.0, nchol=20, box=False, seed=3000, tau=1e-12),
     "cisd_n200": dict(n=200, na=2, nb=2, kmax=2, ell=5.0, nchol=20, box=True, seed=2000, tau=1e-14),
@@ -333,8 +335,10 @@ def run_ours(args, wl, ws, rank, local):
     what = "opposite- and same-spin contractions in one launch" if both else "opposite-spin contraction"
     tag = "_both" if both else ""
     if tc and args.precision == 64:
-        # tensor-core kernel: bf16 MMA flops it issues (28 exact slice products)
-        flops = st["opposite_tc_bf16_flops"] + (st.get("samespin_tc_bf16_flops", 0.0) if both else 0.0)
+        # tensor-core kernel: bf16 MMA flops its schedule issues (the exact slice
+        # products of live slices of non-screened blocks, over whole tiles)
+        flops = st.get("tc_schedule_fp64", {}).get("issued_bf16_flops") or (
+            st["opposite_tc_bf16_flops"] + (st.get("samespin_tc_bf16_flops", 0.0) if both else 0.0))
         peak, peak_src = bf16_peak()
         bound, kname, kkey = "tensor", "k_oz_gemm (tcgen05, FP64-accurate %s)" % what, \
             "k_oz_gemm%s_%s" % (tag, args.workload)
@@ -386,6 +390,12 @@ def run_ours(args, wl, ws, rank, local):
                      "traffic": traffic, "kernel": kname, "kernel_ms": round(gemm_ms, 4), "flops_per_launch": flops,
                      "fp64_equivalent_tflops": round(st["opposite_gemm_flops"] / (gemm_ms * 1e-3) / 1e12, 3)
                      if gemm_ms > 0 else None,
+                     # the method's own work: one multiply-add (2 flops) per surviving update
+                     "method_flops_per_launch": 2.0 * updates,
+                     "method_tflops": round(2.0 * updates / (gemm_ms * 1e-3) / 1e12, 3) if gemm_ms > 0 else None,
+                     "method_frac": round(2.0 * updates / (gemm_ms * 1e-3) / 1e12 / peak, 5) if gemm_ms > 0 else None,
+                     "emulation_factor": round(flops / (2.0 * updates), 3) if updates > 0 else None,
+                     "schedule": st.get("tc_schedule_fp64"),
                      "peak_source": peak_src},
         "hbm": {"compulsory_bytes_per_step": comp_bytes,
                 "achieved_gbs": round(comp_bytes / (ms * 1e-3) / 1e9, 2),
@@ -398,10 +408,128 @@ def run_ours(args, wl, ws, rank, local):
     }
     # kernel launches of the library inside the timed region (counted by the library)
     line["gpu_launches"] = st.get("kernel_launches")
+    line["config"]["opposite_units_kept"] = round(st["units_kept_opposite"] / max(1, st["units_total"]["opposite"]), 6)
+    if ws == 1 and args.roots > 0:
+        # the lowest roots of the same context, pinned to the oracle
+        line["roots"] = run_roots(L, wl, tau, args.roots, with_oracle=not args.no_cpu_baseline,
+                                  full_oracle=args.oracle_full)
+    L.iscsi_finalize()
+    if ws == 1 and args.tau_sweep:
+        # the same sigma at the workload's other screening thresholds
+        line["tau_sweep"] = run_tau_sweep(L, wl, [t for t in wl.get("taus", ()) if t != tau], steps=args.steps,
+                                          warmup=args.warmup)
     return line
 
 
-def run_precision_form(name, nroots=3, tol=1e-8):
+def run_tau_sweep(L, wl, taus, steps=5, warmup=3):
+    """sigma time, survivor fraction, updates and the contraction's time at other
+    screening thresholds tau (L2 flushed between steps)."""
+    import torch
+
+    from paper_1609_07757_gb300.synthetic import make_integrals, unit_vector
+
+    h1, eri = make_integrals(wl["n"], wl["seed"], ell=wl["ell"], nchol=wl["nchol"], box=wl["box"])
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = []
+    for tau in taus:
+        L.iscsi_init(wl["n"], wl["na"], wl["nb"], wl["kmax"], h1, eri, tau)
+        nd = L.iscsi_ndet()
+        c = torch.tensor(unit_vector(nd, 17), dtype=torch.float64, device="cuda")
+        s = torch.empty_like(c)
+        for _ in range(warmup):
+            L.iscsi_sigma(c, s, 1)
+        L.iscsi_set_option("phase_timing", 1)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record()
+            L.iscsi_sigma(c, s, 1)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        st = L.iscsi_stats()
+        L.iscsi_set_option("phase_timing", 0)
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        upd = L.iscsi_updates_per_sigma()
+        sched = st.get("tc_schedule_fp64", {})
+        out.append({"tau": tau, "sigma_ms": round(ms, 4), "gupdates_per_s": round(upd / (ms * 1e-3) / 1e9, 1),
+                    "updates_per_sigma": upd,
+                    "opposite_units_kept": round(st["units_kept_opposite"] / max(1, st["units_total"]["opposite"]), 6),
+                    "contraction_ms": round(st["phase_ms"]["opposite_gemm"] / max(1, st["timed_calls"]), 4),
+                    "issued_bf16_flops": sched.get("issued_bf16_flops")})
+        L.iscsi_finalize()
+    return out
+
+
+def oracle_pin_roots(o, energies, x, w, sample_rows, seed=23):
+    """Pin approximate eigenpairs (E, x) of the GPU (w = H x by the GPU) to the
+    oracle on sampled rows I: the oracle's (H x)_I against the GPU's, and the
+    residual estimate ||r||^2 ~ ndet / m sum_I (r_I)^2 with r = H_oracle x - E x.
+    With the gap delta of each root to its computed neighbours, the a-posteriori
+    bound |E - lambda| <= ||r||^2 / delta (Kato-Temple, for the Rayleigh
+    quotient) is reported from the GPU's full residual and from the estimate."""
+    import numpy as np
+
+    nd = x.shape[1]
+    rows = np.random.default_rng(seed).choice(nd, size=min(nd, sample_rows), replace=False)
+    out = []
+    for i, e in enumerate(energies):
+        xi = x[i] / np.linalg.norm(x[i])
+        wi = w[i] / np.linalg.norm(x[i])
+        rho = float(xi @ wi)
+        r_gpu = float(np.linalg.norm(wi - e * xi))
+        so = o.sigma_rows(xi, rows)
+        d = np.abs(so - wi[rows]).max()
+        r_est = float(np.sqrt(nd / rows.size * np.sum((so - e * xi[rows]) ** 2)))
+        gaps = [abs(e - f) for j, f in enumerate(energies) if j != i]
+        gap = min(gaps) if gaps else None
+        out.append({"energy": float(e), "rayleigh_gpu": rho, "abs_E_minus_rayleigh": abs(float(e) - rho),
+                    "residual_gpu": r_gpu, "residual_oracle_estimate": r_est,
+                    "oracle_vs_gpu_sigma_max_abs": float(d), "sigma_inf": float(np.abs(wi).max()),
+                    "gap": gap, "bound_gpu": r_gpu ** 2 / gap if gap else None,
+                    "bound_oracle_estimate": r_est ** 2 / gap if gap else None})
+    return {"sample_rows": int(rows.size), "roots": out}
+
+
+def run_roots(L, wl, tau, nroots=2, tol=1e-8, with_oracle=True, full_oracle=False, oracle_s=12.0):
+    """The lowest `nroots` roots of the current context (device Davidson, FP64; one
+    more root is computed for the gaps), each pinned to the oracle on a sample of
+    rows sized for about oracle_s seconds of the oracle's work (or all rows with
+    full_oracle, minutes at full CI in 60 orbitals)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1609_07757_gb300.synthetic import make_integrals
+
+    nd = L.iscsi_ndet()
+    k = nroots + 1
+    vecs = torch.zeros((k, nd), dtype=torch.float64, device="cuda")
+    L.iscsi_set_option("precision", 64)
+    t0 = time.time()
+    st, e = L.iscsi_davidson(k, tol, vecs)
+    wall = time.time() - t0
+    stt = L.iscsi_stats()
+    w = torch.empty_like(vecs)
+    L.iscsi_sigma(vecs, w, k)
+    torch.cuda.synchronize()
+    out = {"nroots": nroots, "tol": tol, "status": int(st), "energies": [float(x) for x in e[:nroots]],
+           "next_energy": float(e[nroots]), "iterations": stt["davidson_iters"], "seconds": round(wall, 3)}
+    if with_oracle:
+        h1, eri = make_integrals(wl["n"], wl["seed"], ell=wl["ell"], nchol=wl["nchol"], box=wl["box"])
+        o = oracle.Oracle(wl["n"], wl["na"], wl["nb"], wl["kmax"], tau, h1, eri)
+        upd_row = L.iscsi_updates_per_sigma() / max(1, nd)
+        rows = nd if full_oracle else int(oracle_s * ORACLE_UPDATES_PER_S / upd_row / nroots)
+        t1 = time.time()
+        pin = oracle_pin_roots(o, [float(x) for x in e], vecs.cpu().numpy(), w.cpu().numpy(), rows)
+        pin["roots"] = pin["roots"][:nroots]
+        pin["oracle_seconds"] = round(time.time() - t1, 2)
+        pin["cores"] = len(os.sched_getaffinity(0))
+        out["oracle_pin"] = pin
+    return out
+
+
+def run_precision_form(name, nroots=3, tol=1e-8, with_oracle=True, oracle_s=12.0):
     """FP32-mixed against plain FP64 Davidson on one workload: lowest roots, time,
     iterations (FP32 phase), and |dE| between the two.  Before the timed runs,
     untimed sigma calls with the vector counts the solvers use (1 and nroots:
@@ -422,6 +550,7 @@ def run_precision_form(name, nroots=3, tol=1e-8):
     s = torch.empty_like(c)
     out = {"workload": name, "ndet": ndet, "nroots": nroots, "tol": tol}
     res = {}
+    orc = None
     cw = torch.tensor(np.stack([unit_vector(ndet, 5 + i) for i in range(nroots)]), dtype=torch.float64,
                       device="cuda")
     sw = torch.empty_like(cw)
@@ -450,6 +579,18 @@ def run_precision_form(name, nroots=3, tol=1e-8):
         res[prec] = {"status": int(st), "energies": [float(x) for x in e], "iters": stt["davidson_iters"],
                      "fp32_iters": stt.get("davidson_fp32_iters", 0), "ms": round(stt["davidson_ms"], 3),
                      "wall_s": round(wall, 3), "residual_norms": [float("%.3e" % r) for r in rnorm]}
+        if with_oracle:
+            # the returned eigenpairs pinned to the oracle on a sample of rows
+            import oracle
+            if orc is None:
+                orc = oracle.Oracle(wl["n"], wl["na"], wl["nb"], wl["kmax"], wl["tau"], h1, eri)
+            upd_row = L.iscsi_updates_per_sigma() / max(1, ndet)
+            rows = int(oracle_s * ORACLE_UPDATES_PER_S / upd_row / (2 * nroots))
+            t1 = time.time()
+            pin = oracle_pin_roots(orc, [float(x) for x in e], vecs.cpu().numpy(), w.cpu().numpy(), rows)
+            pin["oracle_seconds"] = round(time.time() - t1, 2)
+            pin["cores"] = len(os.sched_getaffinity(0))
+            res[prec]["oracle_pin"] = pin
     L.iscsi_set_option("precision", 64)
     L.iscsi_finalize()
     de = max(abs(a - b) for a, b in zip(res[32]["energies"], res[64]["energies"]))
@@ -941,12 +1082,6 @@ def cpu_baseline(wl, tau, target_s=15.0, steps=1):
     return o, nrow, times, cores
 
 
-def updates_estimate(wl, tau):
-    """Exact updates per sigma from the oracle's closed-form-free count is too slow at
-    full size; the CUDA library's exact count is used when a GPU is present, else None."""
-    return None
-
-
 def run_reference(args, wl, ws, rank):
     tau = args.tau if args.tau is not None else wl["tau"]
     if rank != 0:
@@ -987,6 +1122,12 @@ def main():
     ap.add_argument("--mixed-workload", default="fci_n100", choices=sorted(WORKLOADS) + ["none"],
                     help="workload of the FP32-mixed vs FP64 Davidson comparison added to the line")
     ap.add_argument("--mixed-roots", type=int, default=3)
+    ap.add_argument("--roots", type=int, default=2,
+                    help="lowest roots of the main workload by Davidson, pinned to the oracle (0: skip)")
+    ap.add_argument("--oracle-full", action="store_true",
+                    help="pin the roots with a full oracle sigma (minutes) instead of a sample of rows")
+    ap.add_argument("--tau-sweep", type=int, default=1, choices=[0, 1],
+                    help="time sigma at the workload's other screening thresholds")
     ap.add_argument("--batching", type=int, default=0, metavar="COUNT",
                     help="add the batching form: COUNT full-CI instances, batched vs one at a time")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
@@ -1015,19 +1156,12 @@ def main():
         dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
     if args.impl == "reference":
         if args.updates is None:
-            # exact update count of the workload from the CUDA library's set-up when available
-            try:
-                import torch
-                if torch.cuda.is_available():
-                    from paper_1609_07757_gb300 import _lib as L
-                    from paper_1609_07757_gb300.synthetic import make_integrals
-                    tau = args.tau if args.tau is not None else wl["tau"]
-                    h1, eri = make_integrals(wl["n"], wl["seed"], ell=wl["ell"], nchol=wl["nchol"], box=wl["box"])
-                    L.iscsi_init(wl["n"], wl["na"], wl["nb"], wl["kmax"], h1, eri, tau)
-                    args.updates = L.iscsi_updates_per_sigma()
-                    L.iscsi_finalize()
-            except Exception:  # noqa: BLE001
-                args.updates = None
+            # the oracle's own count of the workload's updates per sigma (oracle/counts.py)
+            from oracle.counts import updates_per_sigma
+            from paper_1609_07757_gb300.synthetic import make_integrals
+            tau = args.tau if args.tau is not None else wl["tau"]
+            h1, eri = make_integrals(wl["n"], wl["seed"], ell=wl["ell"], nchol=wl["nchol"], box=wl["box"])
+            args.updates = updates_per_sigma(wl["n"], wl["na"], wl["nb"], wl["kmax"], tau, h1, eri)
         line = run_reference(args, wl, ws, rank)
         if rank == 0 and line:
             print(json.dumps(line))
@@ -1057,7 +1191,8 @@ def main():
     line = run_ours(args, wl, ws, rank, local)
     if rank == 0 and ws == 1 and args.mixed_workload != "none":
         # the precision form: FP32-mixed vs FP64 Davidson, |dE| and speedup (untimed by the contract)
-        line["mixed_precision"] = run_precision_form(args.mixed_workload, args.mixed_roots)
+        line["mixed_precision"] = run_precision_form(args.mixed_workload, args.mixed_roots,
+                                                     with_oracle=not args.no_cpu_baseline)
     if args.batching > 0:
         # every rank runs its share of the instances; rank 0 reports the job
         b = run_batching(args.batching, rank=rank, ws=ws)

@@ -158,10 +158,13 @@ ISCSI_API iscsi_status iscsi_sigma(const void* c, void* sigma, int nvec);
  * callback contexts where cudaMalloc, which may synchronise the device, is not
  * allowed.)  It allocates nothing: the lifted vector, the contraction product
  * and the GEMM problem lists live in one static 32 MiB device array that every
- * GPU loading this library holds until the process exits.
+ * GPU loading this library holds until the process exits.  It computes on the
+ * FP64 FMA kernels (the route of option fp64_tc = 0), not on the tensor
+ * cores.  The problem lists stay in the array: a call copies them from host
+ * memory only when the array last served another context.
  *   c      device, FP64 [ndet]; sigma: device, FP64 [ndet], overwritten.
  * The context must need at most 32 MiB of scratch (full CI with 2+2
- * electrons: up to 37 orbitals); larger contexts are rejected with
+ * electrons: up to 38 orbitals); larger contexts are rejected with
  * ISCSI_E_ARG and a message naming the bytes needed.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress); make that
  * first call before any stream capture.  All calls share the array: calls

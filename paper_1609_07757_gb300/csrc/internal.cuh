@@ -287,6 +287,7 @@ struct Context {
   DevBuf gas_mask;                  // uint8 [ndet], 1 = kept
   std::vector<uint8_t> gas_mask_h;  // host copy (start vectors of the Davidson method)
   DevBuf gas_in;                    // projected copy of a caller's vectors
+  long long noalloc_gen = 0;        // distinct per build (iscsi_sigma_noalloc keeps its lists in its array)
   ~Context();
 };
 

@@ -19,15 +19,18 @@ namespace iscsi {
 
 // C(n, k); LLONG_MAX when it does not fit (every partial product r is itself
 // the binomial C(n - k + i, i), so the division is exact)
+// C(n, k), saturating at LLONG_MAX only when the value itself does not fit:
+// after step i, r = C(n - k + i, i), and the product r (n - k + i) is formed in
+// 128 bits before the exact division by i
 long long binom_ll(int n, int k) {
   if (k < 0 || n < 0 || k > n) return 0;
   if (k > n - k) k = n - k;
-  long long r = 1;
+  unsigned __int128 r = 1;
   for (int i = 1; i <= k; ++i) {
-    if (r > LLONG_MAX / (n - k + i)) return LLONG_MAX;
-    r = r * (n - k + i) / i;
+    r = r * (unsigned __int128)(n - k + i) / (unsigned __int128)i;
+    if (r > (unsigned __int128)LLONG_MAX) return LLONG_MAX;
   }
-  return r;
+  return (long long)r;
 }
 
 int launch_blocks(long long work, int threads) {
@@ -591,6 +594,8 @@ int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h
   cudaStream_t st = stream();
   host_binom_table();
   ISCSI_CUDA(cudaGetLastError());
+  static long long builds = 0;
+  ctx.noalloc_gen = ++builds;
   ctx.n = n;
   ctx.na = na;
   ctx.nb = nb;

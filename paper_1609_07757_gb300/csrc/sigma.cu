@@ -997,17 +997,24 @@ int sigma_autotune(Context& ctx, const double* c, double* sigma, int nvec, int p
 // whose memory is already committed.  For them this variant keeps every
 // per-call buffer -- the lifted vector Ct, the product T and the GEMM problem
 // lists -- in one file-scope device array of fixed size instead of
-// library-allocated workspace.  It runs the same kernels as iscsi_sigma (FP64,
-// one vector).  The array belongs to the module: every GPU that loads the
-// library holds it until the process exits.  All calls share it, so calls
-// whose work overlaps on the GPU (different streams, or several host threads)
-// race on it and must be serialised by the caller.  Nothing in it has to
-// start at zero: each call overwrites every element it later reads.
+// library-allocated workspace.  It computes the FP64 sigma of one vector on the
+// FP64 FMA kernels (k_lift_ct, k_grouped_gemm, k_fold: the fp64_tc = 0 route of
+// iscsi_sigma), not on the tensor cores, whose per-call operand slices would
+// not fit a modest array.  The array belongs to the module: every GPU that
+// loads the library holds it until the process exits.  All calls share it, so
+// calls whose work overlaps on the GPU (different streams, or several host
+// threads) race on it and must be serialised by the caller.  Nothing in it
+// has to start at zero: each call overwrites every element it later reads.
+// The problem lists stay in the array between calls: a call copies them from
+// host memory only when the array last held another context's (or another
+// build of this context's) lists.
 
 constexpr size_t kNoAllocScratchBytes = 32u << 20;  // 32 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 static void* g_noalloc_ptr[64] = {nullptr};
+static const Context* g_noalloc_lists_of[64] = {nullptr};  // whose lists the array holds, per device
+static long long g_noalloc_lists_gen[64] = {0};
 
 size_t noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
 
@@ -1121,21 +1128,30 @@ int sigma_noalloc_run(Context& ctx, const double* c, double* sigma) {
     set_error("iscsi_sigma_noalloc: too many GEMM problems for the static lists");
     return kErrArg;
   }
-  if (!all.empty())
-    ISCSI_CUDA(cudaMemcpyAsync(dprobs, all.data(), sizeof(Problem<double>) * all.size(), cudaMemcpyHostToDevice, st));
-  if (!segs.empty())
-    ISCSI_CUDA(cudaMemcpyAsync(dsegs, segs.data(), sizeof(Segment<double>) * segs.size(), cudaMemcpyHostToDevice, st));
+  if (g_noalloc_lists_of[dev] != &ctx || g_noalloc_lists_gen[dev] != ctx.noalloc_gen) {
+    if (!all.empty())
+      ISCSI_CUDA(cudaMemcpyAsync(dprobs, all.data(), sizeof(Problem<double>) * all.size(), cudaMemcpyHostToDevice, st));
+    if (!segs.empty())
+      ISCSI_CUDA(
+          cudaMemcpyAsync(dsegs, segs.data(), sizeof(Segment<double>) * segs.size(), cudaMemcpyHostToDevice, st));
+    g_noalloc_lists_of[dev] = &ctx;
+    g_noalloc_lists_gen[dev] = ctx.noalloc_gen;
+  }
   constexpr int NT = (C::BM / C::TM) * (C::BN / C::TN);
   if (ctx.have_ab) {
     long long tot = ct.start[ct.nclass];
-    if (tot > 0)
+    if (tot > 0) {
       k_lift_ct<double, double><<<launch_blocks(tot, 256), 256, 0, st>>>(
           ct, 1, ctx.n, ctx.sp[0].nhole, ctx.sp[1].nhole, ctx.pair_of.as<int>(), ctx.hp_inv.as<int>(),
           ctx.sp[0].lift.as<int>(), ctx.sp[1].lift.as<int>(), ctx.sp[0].level.as<int8_t>(), ctx.nballow.as<int>(),
-          ctx.off.as<long long>(), c, ctx.ndet, ctw); ISCSI_COUNT_LAUNCH();
-    if (ab_tiles > 0)
+          ctx.off.as<long long>(), c, ctx.ndet, ctw);
+      ISCSI_COUNT_LAUNCH();
+    }
+    if (ab_tiles > 0) {
       k_grouped_gemm<double, C::BM, C::BN, C::BK, C::TM, C::TN>
-          <<<ab_tiles, NT, 0, st>>>(dprobs, (int)ab.size(), dsegs, c, sigma); ISCSI_COUNT_LAUNCH();
+          <<<ab_tiles, NT, 0, st>>>(dprobs, (int)ab.size(), dsegs, c, sigma);
+      ISCSI_COUNT_LAUNCH();
+    }
     k_fold<double><<<ctx.sp[0].count, 256, 0, st>>>(ct, 1, ctx.n, ctx.na, ctx.nb, ctx.sp[1].nhole,
                                                     ctx.sp[0].dec.as<int>(), ctx.sp[1].dec.as<int>(),
                                                     ctx.hp_class.as<int8_t>(), ctx.hp_local.as<int>(),
@@ -1144,9 +1160,11 @@ int sigma_noalloc_run(Context& ctx, const double* c, double* sigma) {
   } else {
     ISCSI_CUDA(cudaMemsetAsync(sigma, 0, sizeof(double) * ctx.ndet, st));
   }
-  if (ss_tiles > 0)
+  if (ss_tiles > 0) {
     k_grouped_gemm<double, C::BM, C::BN, C::BK, C::TM, C::TN>
-        <<<ss_tiles, NT, 0, st>>>(dprobs + ab.size(), (int)ss.size(), dsegs, c, sigma); ISCSI_COUNT_LAUNCH();
+        <<<ss_tiles, NT, 0, st>>>(dprobs + ab.size(), (int)ss.size(), dsegs, c, sigma);
+    ISCSI_COUNT_LAUNCH();
+  }
   ISCSI_CUDA(cudaGetLastError());
   return kOk;
 }

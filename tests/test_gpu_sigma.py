@@ -57,11 +57,12 @@ def gpu_sigma(C, nvec=1, precision=64):
 
 
 def assert_close(s_gpu, s_ref, rel):
+    """The FP64 bar: ||d||_2 <= rel ||s||_2 and max |d_I| <= rel ||s||_inf."""
     nrm = np.linalg.norm(s_ref)
     inf = np.abs(s_ref).max()
     d = s_gpu - s_ref
     assert np.linalg.norm(d) <= rel * max(nrm, 1e-300), (np.linalg.norm(d), nrm)
-    assert np.abs(d).max() <= rel * max(inf, 1e-300) * 10, (np.abs(d).max(), inf)
+    assert np.abs(d).max() <= rel * max(inf, 1e-300), (np.abs(d).max(), inf)
 
 
 CASES = [  # n, na, nb, kmax, tau

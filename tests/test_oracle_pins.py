@@ -417,3 +417,17 @@ def test_string_order_and_addressing():
         assert o.det_index(A, B) == idx
     # a determinant above the truncation is outside the space
     assert o.det_index([5, 6, 7], [6, 7]) == -1
+
+
+@pytest.mark.parametrize("n,na,nb,k,tau", [(6, 2, 2, 4, 0.0), (8, 2, 2, 2, 1e-6), (9, 2, 2, 3, 1e-3), (7, 3, 2, 3, 1e-5),
+                                           (7, 1, 1, 2, 0.0), (8, 2, 1, 9, 1e-4), (6, 2, 0, 2, 0.0), (5, 0, 3, 9, 0.0),
+                                           (6, 3, 3, 2, 0.0), (8, 2, 2, 0, 0.0)])
+def test_update_count_from_string_levels(n, na, nb, k, tau):
+    # the count from binomials over string levels (oracle/counts.py) equals the
+    # number of updates the oracle performs applying every surviving term to
+    # every determinant
+    from oracle.counts import updates_per_sigma
+    h1, eri = make_integrals(n, 300 + n, ell=3.0, nchol=8)
+    o = Oracle(n, na, nb, k, tau, h1, eri)
+    _, nup = o.sigma_terms(np.ones(o.ndet))
+    assert updates_per_sigma(n, na, nb, k, tau, h1, eri) == nup
