@@ -305,13 +305,11 @@ int batch_sigma(const std::vector<Context*>& ctxs, const std::vector<const doubl
 // status of the bounded waits of the merged launches (synchronises)
 int batch_check() {
   if (!g_batch || !g_batch->sb.err.p) return kOk;
-  int h = 0;
-  ISCSI_CUDA(cudaMemcpy(&h, g_batch->sb.err.p, sizeof(int), cudaMemcpyDeviceToHost));
-  if (h) {
-    set_error("batched sigma: a bounded device wait ran out");
-    return kErrWait;
-  }
-  return kOk;
+  const int rc = tc_wait_status(g_batch->sb.err.as<int>(), "batched sigma");
+  // the aborted launch may have left split-K counters raised: the next call
+  // builds the batch (lists, schedules, graph) anew
+  if (rc == kErrWait) g_batch.reset();
+  return rc;
 }
 
 bool batch_graph_active() { return g_batch && g_batch->x; }

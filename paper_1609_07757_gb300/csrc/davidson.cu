@@ -1114,12 +1114,7 @@ int start_vectors(Dav& d, DavCtl& h, const double* vecs) {
 int batch_wait_status(const std::unique_ptr<SigmaBatch> (&sb)[2]) {
   for (int g = 0; g < 2; ++g) {
     if (!sb[g] || !sb[g]->err.p) continue;
-    int h = 0;
-    ISCSI_CUDA(cudaMemcpy(&h, sb[g]->err.p, sizeof(int), cudaMemcpyDeviceToHost));
-    if (h) {
-      set_error("iscsi_davidson: a bounded device wait ran out in a tensor-core contraction");
-      return kErrWait;
-    }
+    ISCSI_TRY(tc_wait_status(sb[g]->err.as<int>(), "iscsi_davidson"));
   }
   return kOk;
 }

@@ -338,13 +338,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   tc::fence_after_sync();
   const uint32_t tmem = tmem_s;
 
-  auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+  // a wait that runs out records where (oz_wait_code) and stops every role
+  auto wait = [&](uint64_t* bar, uint32_t parity, int site, int detail) -> bool {
     uint32_t a = tc::smem_u32(bar);
     for (long long i = 0; i < OZ_SPIN; ++i) {
       if (tc::mbar_try_wait(a, parity)) return true;
       if ((i & 1023) == 1023 && abort_s) return false;
     }
-    abort_s = 1;
+    atomicCAS((int*)&abort_s, 0, oz_wait_code(site, detail));
     return false;
   };
 
@@ -373,7 +374,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             int tA, uB;
             if (!oz_step(V, ks, tA, uB)) continue;
             const int st = g % OZ_STAGES;
-            if (g >= OZ_STAGES && !wait(&empty_b[st], ((g / OZ_STAGES) - 1) & 1)) {
+            if (g >= OZ_STAGES && !wait(&empty_b[st], ((g / OZ_STAGES) - 1) & 1, OZ_SITE_EMPTY, it)) {
               ok = false;
               break;
             }
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       if (ok) {
         // the end marker: a stage without data
         const int st = g % OZ_STAGES;
-        if (g < OZ_STAGES || wait(&empty_b[st], ((g / OZ_STAGES) - 1) & 1)) {
+        if (g < OZ_STAGES || wait(&empty_b[st], ((g / OZ_STAGES) - 1) & 1, OZ_SITE_EMPTY_END, g)) {
           info_s[st] = OZ_INFO_END;
           tc::mbar_arrive(tc::smem_u32(&full_b[st]));
           ++g;
@@ -428,7 +429,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       uint32_t wmask = 0;  // levels written since their last drain
       volatile uint32_t* vinfo = info_s;
       uint32_t info = 0;
-      bool ok = wait(&full_b[0], 0);
+      bool ok = wait(&full_b[0], 0, OZ_SITE_FULL, 0);
       if (ok) {
         tc::fence_after_sync();
         info = vinfo[0];
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           const bool seg = (info & OZ_INFO_SEG) != 0;
           mid();
           if (!seg) oz_issue_general(tmem, wmask, dA, dB, tA, uB, 1);
-          if (!wait(&free_b, chunk & 1)) break;
+          if (!wait(&free_b, chunk & 1, OZ_SITE_FREE, chunk)) break;
           tc::fence_after_sync();
           wmask &= seg ? 0u : ~OZ_EXACT_MASK;
           oz_issue_general(tmem, wmask, dA, dB, tA, uB, seg ? 0 : 2);
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         open = true;
         g = gn;
         if (!ready) {
-          if (!wait(&full_b[stn], pn)) break;
+          if (!wait(&full_b[stn], pn, OZ_SITE_FULL, gn)) break;
           info_n = vinfo[stn];
         }
         tc::fence_after_sync();
@@ -511,7 +512,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // all epilogue threads meet (bounded, unlike a named barrier, so an abort cannot hang it)
     auto epi_sync = [&]() -> bool {
       tc::mbar_arrive(tc::smem_u32(&epi_b));
-      return wait(&epi_b, (epi_phase++) & 1);
+      const int ph = epi_phase++;
+      return wait(&epi_b, ph & 1, OZ_SITE_EPI_SYNC, ph);
     };
     for (int it = it0; it < it1 && ok; ++it) {
       const OzItem I = items[it];
@@ -540,7 +542,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int nch = (niss + SPC - 1) / SPC;
         for (int ch = 0; ch < nch; ++ch, ++chunk) {
           // warp-uniform decision: tcgen05.ld below is warp-collective
-          const bool w_ok = wait(&chunk_b, chunk & 1);
+          const bool w_ok = wait(&chunk_b, chunk & 1, OZ_SITE_CHUNK, chunk);
           if (!__all_sync(0xffffffffu, w_ok)) {
             ok = false;
             break;
@@ -586,32 +588,52 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           tc::mbar_arrive(tc::smem_u32(&free_b));
           if (last) {
             // this segment's result 2^(ea+eb-14) (S 2^-28 + tail), after the
-            // accumulators are released (the MMAs of the next chunk run meanwhile)
-            const int ea = gm < P.M ? S.a_exp[gm] : 0;
-            uint32_t tl[8];
+            // accumulators are released (the MMAs of the next chunk run
+            // meanwhile).  Everything read from global memory is loaded into
+            // registers first, eight columns at a time: the stores below could
+            // alias it, and a chain of dependent reloads would cost far longer
+            // than the chunks of MMAs it overlaps.
+            const int Mp = P.M, Np = P.N, nrb = S.nrows_b;
+            const long long ldt = P.ldt;
+            const bool addT = P.accumulate || wrote;
+            const int* __restrict__ bexp = S.b_exp;
+            const int ea = gm < Mp ? __ldg(S.a_exp + gm) : 0;
+            double* const rowT = part_base ? part_base + row * OZ_BN + cbase : Tp + (long long)gm * ldt;
 #pragma unroll
-            for (int j = 0; j < OZ_EPI_COLS; ++j) {
-              if ((j & 7) == 0) {
-                tc::tmem_ld8(tail_base + j, tl);
-                tc::tmem_wait_ld();
+            for (int c0 = 0; c0 < OZ_EPI_COLS; c0 += 8) {
+              uint32_t tl[8];
+              tc::tmem_ld8(tail_base + c0, tl);
+              int eb[8];
+              double old[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int gn = n0 + cbase + c0 + j;
+                const bool in = gm < Mp && gn < Np && gn < nrb;
+                eb[j] = in ? __ldg(bexp + gn) : 0;
+                old[j] = 0.0;
+                if (part_base) {
+                  if (wrote) old[j] = rowT[c0 + j];
+                } else if (in && addT) {
+                  old[j] = rowT[gn];
+                }
               }
-              const int gn = n0 + cbase + j;
-              const bool in = gm < P.M && gn < P.N && gn < S.nrows_b;
-              double v = 0.0;
-              if (in) {
-                // S 2^-28 + tail, the tail rounded to S's unit (2^-43 of the
-                // largest single product: below the slices' own error)
-                const long long q = sums[j] + __float2ll_rn(__uint_as_float(tl[j & 7]) * 268435456.0f /* 2^28 */);
-                v = oz_i64_scaled(q, ea + S.b_exp[gn] - 14 - 28);
+              tc::tmem_wait_ld();
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int gn = n0 + cbase + c0 + j;
+                const bool in = gm < Mp && gn < Np && gn < nrb;
+                double v = 0.0;
+                if (in) {
+                  // S 2^-28 + tail, the tail rounded to S's unit (2^-43 of the
+                  // largest single product: below the slices' own error)
+                  const long long q =
+                      sums[c0 + j] + __float2ll_rn(__uint_as_float(tl[j]) * 268435456.0f /* 2^28 */);
+                  v = oz_i64_scaled(q, ea + eb[j] - 14 - 28);
+                }
+                if (part_base) rowT[c0 + j] = old[j] + v;
+                else if (in) rowT[gn] = old[j] + v;
+                sums[c0 + j] = 0;
               }
-              if (part_base) {
-                double* dst = part_base + row * OZ_BN + cbase + j;
-                *dst = wrote ? *dst + v : v;
-              } else if (in) {
-                double* dst = Tp + (long long)gm * P.ldt + gn;
-                *dst = (P.accumulate || wrote) ? *dst + v : v;
-              }
-              sums[j] = 0;
             }
             wrote = true;
           }
@@ -651,7 +673,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
   }
   __syncthreads();
-  if (abort_s && threadIdx.x == 0) atomicExch(err, 1);
+  if (abort_s && threadIdx.x == 0) atomicCAS(err, 0, abort_s + (int)min(blockIdx.x, 4095u) * OZ_WAIT_CTA);
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 1) {

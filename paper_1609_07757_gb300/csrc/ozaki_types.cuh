@@ -26,6 +26,17 @@ constexpr int OZ_ZERO_BYTES = OZ_A_SLICE_BYTES + OZ_B_SLICE_BYTES;  // zero oper
 constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + OZ_ZERO_BYTES + 1024;
 constexpr int OZ_TMEM_COLS = 512;  // 7 levels x 64 columns used
 constexpr long long OZ_SPIN = 1ll << 24;
+// Where a bounded wait of the contraction kernels ran out, as the error word
+// they leave: bits 0-2 the wait (OZ_SITE_*), bits 3-18 the role's position
+// (item, stage or chunk count, low 16 bits), bits 19-30 the CTA.
+constexpr int OZ_SITE_EMPTY = 1;      // producer: a stage's release (the item in the CTA's list)
+constexpr int OZ_SITE_EMPTY_END = 2;  // producer: the stage of the end marker (stages filled)
+constexpr int OZ_SITE_FULL = 3;       // MMA thread: a stage's data (stages consumed)
+constexpr int OZ_SITE_FREE = 4;       // MMA thread: the accumulators' drain (chunks closed)
+constexpr int OZ_SITE_CHUNK = 5;      // epilogue: a chunk's products (chunks drained)
+constexpr int OZ_SITE_EPI_SYNC = 6;   // epilogue: the split-K meeting (meetings passed)
+constexpr int OZ_WAIT_CTA = 1 << 19;
+__host__ __device__ constexpr int oz_wait_code(int site, int detail) { return site | ((detail & 0xFFFF) << 3); }
 
 constexpr int OZ_MAX_SEGS = 8;
 constexpr int OZ_BW_ROWS = 128;    // rows of B per 128-column tile; B arrays are padded to this

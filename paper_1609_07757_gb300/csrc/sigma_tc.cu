@@ -998,20 +998,39 @@ int oz_job_launch(Context& ctx, const OzJob& job, cudaStream_t st) {
   return launch_job(ctx, job, nullptr, st);
 }
 
-// status of the bounded waits of the tensor-core kernels (synchronises)
-int tc_check(Context& ctx) {
-  if (!ctx.oz_err.p) return kOk;
+// the error word of the contraction kernels' bounded waits (device, one int):
+// kOk, or kErrWait with a message naming the wait that ran out (its site,
+// CTA and position, as oz_wait_code packs them); a raised word is cleared so
+// that later launches report only their own waits (synchronises)
+int tc_wait_status(int* err, const char* what) {
+  if (!err) return kOk;
   int h = 0;
-  ISCSI_CUDA(cudaMemcpy(&h, ctx.oz_err.p, sizeof(int), cudaMemcpyDeviceToHost));
-  if (h) {
+  ISCSI_CUDA(cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!h) return kOk;
+  static const char* const kSite[8] = {"an unknown wait",
+                                       "a stage's release (producer)",
+                                       "the end marker's stage (producer)",
+                                       "a stage's data (MMA thread)",
+                                       "the accumulators' drain (MMA thread)",
+                                       "a chunk's products (epilogue)",
+                                       "the split-K meeting (epilogue)",
+                                       "an unknown wait"};
+  ISCSI_CUDA(cudaMemset(err, 0, sizeof(int)));
+  set_error(std::string(what) + ": a bounded device wait ran out in a tensor-core contraction (" + kSite[h & 7] +
+            ", CTA " + std::to_string((h >> 19) & 4095) + ", position " + std::to_string((h >> 3) & 0xFFFF) + ")");
+  return kErrWait;
+}
+
+// status of the bounded waits of the context's tensor-core kernels (synchronises)
+int tc_check(Context& ctx) {
+  const int rc = tc_wait_status(ctx.oz_err.as<int>(), "tensor-core sigma");
+  if (rc != kOk) {
     // the aborted launch may have left split-K counters raised: rebuild the
     // context's work lists (and schedules) before the next launch
     ctx.oz_ab.nvec = ctx.oz_ss.nvec = ctx.t3_ab.nvec = ctx.t3_ss.nvec = -1;
     ctx.oz_both.src_ver[0] = ctx.t3_both.src_ver[0] = -1;
-    set_error("tensor-core sigma: a bounded device wait ran out");
-    return kErrWait;
   }
-  return kOk;
+  return rc;
 }
 
 }  // namespace iscsi

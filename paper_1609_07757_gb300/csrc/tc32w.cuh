@@ -106,13 +106,14 @@ __global__ void __launch_bounds__(T3W_THREADS, 1)
   const int total = step0_s[nseg];
   const int nchunks = (total + SPC - 1) / SPC;
 
-  auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+  // a wait that runs out records where (oz_wait_code) and stops every role
+  auto wait = [&](uint64_t* bar, uint32_t parity, int site, int detail) -> bool {
     uint32_t a = tc::smem_u32(bar);
     for (long long i = 0; i < OZ_SPIN; ++i) {
       if (tc::mbar_try_wait(a, parity)) return true;
       if ((i & 1023) == 1023 && abort_s) return false;
     }
-    abort_s = 1;
+    atomicCAS((int*)&abort_s, 0, oz_wait_code(site, detail));
     return false;
   };
 
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(T3W_THREADS, 1)
       int issued = 0;
       for (int g = 0; g < total; ++g) {
         const int st = g % T3W_STAGES;
-        if (g >= T3W_STAGES && !wait(&empty_b[st], ((g / T3W_STAGES) - 1) & 1)) break;
+        if (g >= T3W_STAGES && !wait(&empty_b[st], ((g / T3W_STAGES) - 1) & 1, OZ_SITE_EMPTY, g)) break;
         while (g >= seg_end) {
           ++seg;
           seg_begin = step0_s[seg];
@@ -156,8 +157,8 @@ __global__ void __launch_bounds__(T3W_THREADS, 1)
       for (int g = 0; g < total; ++g) {
         const int st = g % T3W_STAGES;
         const int ch = g / SPC, kin = g % SPC, b = ch & 1;
-        if (kin == 0 && ch >= 2 && !wait(&free_b[b], ((ch >> 1) - 1) & 1)) break;
-        if (!wait(&full_b[st], (g / T3W_STAGES) & 1)) break;
+        if (kin == 0 && ch >= 2 && !wait(&free_b[b], ((ch >> 1) - 1) & 1, OZ_SITE_FREE, ch)) break;
+        if (!wait(&full_b[st], (g / T3W_STAGES) & 1, OZ_SITE_FULL, g)) break;
         tc::fence_after_sync();
         const uint32_t sa = s_stage0 + st * T3W_STAGE_BYTES;
         const uint32_t sb = sa + T3_S * T3_A_SLICE_BYTES;
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(T3W_THREADS, 1)
     bool ok = true;
     for (int ch = 0; ch < nchunks && ok; ++ch) {
       const int b = ch & 1;
-      ok = wait(&chunk_b[b], (ch >> 1) & 1);
+      ok = wait(&chunk_b[b], (ch >> 1) & 1, OZ_SITE_CHUNK, ch);
       if (!__all_sync(0xffffffffu, ok)) {  // tcgen05.ld is warp-collective
         ok = false;
         break;
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(T3W_THREADS, 1)
     }
   }
   __syncthreads();
-  if (abort_s && threadIdx.x == 0) atomicExch(err, 1);
+  if (abort_s && threadIdx.x == 0) atomicCAS(err, 0, abort_s + (int)min(blockIdx.x, 4095u) * OZ_WAIT_CTA);
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 1) {
