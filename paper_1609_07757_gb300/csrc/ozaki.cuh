@@ -175,6 +175,13 @@ constexpr uint32_t OZ_INFO_TILED = 1u << 6;        // tiled operands (no-swizzle
 constexpr uint32_t OZ_INFO_CHUNK = 1u << 7;        // first step of a chunk
 constexpr uint32_t OZ_INFO_SEG = 1u << 8;          // first step of a segment (of an item)
 constexpr uint32_t OZ_INFO_END = 1u << 9;          // no step: the CTA's work is done
+// Bits 16-31 hold the low 16 bits of the stage's sequence number (the CTA's
+// running step count).  The MMA thread takes a description only when its stamp
+// is the step it expects: the end marker's barrier phase completes on a plain
+// arrival right after the word is written, and a reader that saw the phase
+// before the word (stale description of the stage's previous step) issued
+// that stage as a data step and then waited for a step that never came.
+__device__ __forceinline__ uint32_t oz_info_seq(int g) { return ((uint32_t)g & 0xFFFFu) << 16; }
 
 // Accumulators restart without a separate clearing pass: the MMA thread keeps
 // a mask of the levels written since their last drain, and the first MMA that
@@ -378,7 +385,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               ok = false;
               break;
             }
-            info_s[st] = (uint32_t)tA | ((uint32_t)uB << 3) | (V.a ? OZ_INFO_TILED : 0u) |
+            info_s[st] = oz_info_seq(g) | (uint32_t)tA | ((uint32_t)uB << 3) | (V.a ? OZ_INFO_TILED : 0u) |
                          (j % SPC == 0 ? OZ_INFO_CHUNK : 0u) | (j == 0 ? OZ_INFO_SEG : 0u);
             ++j;
             const uint32_t fb = tc::smem_u32(&full_b[st]);
@@ -405,7 +412,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         // the end marker: a stage without data
         const int st = g % OZ_STAGES;
         if (g < OZ_STAGES || wait(&empty_b[st], ((g / OZ_STAGES) - 1) & 1, OZ_SITE_EMPTY_END, g)) {
-          info_s[st] = OZ_INFO_END;
+          info_s[st] = oz_info_seq(g) | OZ_INFO_END;
+          __threadfence_block();
           tc::mbar_arrive(tc::smem_u32(&full_b[st]));
           ++g;
         }
@@ -428,11 +436,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       bool open = false;   // MMAs issued since the last chunk commit
       uint32_t wmask = 0;  // levels written since their last drain
       volatile uint32_t* vinfo = info_s;
+      // the description of step `step` from its stage, once its stamp says so
+      // (bounded re-reads)
+      auto take = [&](int stage, int step, uint32_t& out) -> bool {
+        const uint32_t want = oz_info_seq(step);
+        for (long long i = 0; i < OZ_SPIN; ++i) {
+          const uint32_t v = vinfo[stage];
+          if ((v & 0xFFFF0000u) == want) {
+            out = v;
+            return true;
+          }
+          if ((i & 1023) == 1023 && abort_s) return false;
+        }
+        atomicCAS((int*)&abort_s, 0, oz_wait_code(OZ_SITE_INFO, step));
+        return false;
+      };
       uint32_t info = 0;
       bool ok = wait(&full_b[0], 0, OZ_SITE_FULL, 0);
       if (ok) {
         tc::fence_after_sync();
-        info = vinfo[0];
+        ok = take(0, 0, info);
       }
       while (ok) {
         const int st = g % OZ_STAGES;
@@ -460,7 +483,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           // the previous stage is released once the MMAs issued so far are done
           if (g > 0) tc::mma_commit(tc::smem_u32(&empty_b[(g - 1) % OZ_STAGES]));
           ready = tc::mbar_test_wait(tc::smem_u32(&full_b[stn]), pn);
-          info_n = vinfo[stn];  // valid when ready (read after the acquiring test)
+          info_n = vinfo[stn];  // used when ready (read after the acquiring test) and stamped gn
+          if ((info_n & 0xFFFF0000u) != oz_info_seq(gn)) ready = 0;
         };
         if (info & OZ_INFO_CHUNK) {
           // the exact levels restart once the epilogue has drained the
@@ -481,7 +505,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         g = gn;
         if (!ready) {
           if (!wait(&full_b[stn], pn, OZ_SITE_FULL, gn)) break;
-          info_n = vinfo[stn];
+          if (!take(stn, gn, info_n)) break;
         }
         tc::fence_after_sync();
         info = info_n;

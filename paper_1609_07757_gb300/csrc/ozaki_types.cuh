@@ -35,6 +35,7 @@ constexpr int OZ_SITE_FULL = 3;       // MMA thread: a stage's data (stages cons
 constexpr int OZ_SITE_FREE = 4;       // MMA thread: the accumulators' drain (chunks closed)
 constexpr int OZ_SITE_CHUNK = 5;      // epilogue: a chunk's products (chunks drained)
 constexpr int OZ_SITE_EPI_SYNC = 6;   // epilogue: the split-K meeting (meetings passed)
+constexpr int OZ_SITE_INFO = 7;       // MMA thread: a stage's description (stages consumed)
 constexpr int OZ_WAIT_CTA = 1 << 19;
 __host__ __device__ constexpr int oz_wait_code(int site, int detail) { return site | ((detail & 0xFFFF) << 3); }
 

@@ -1014,7 +1014,7 @@ int tc_wait_status(int* err, const char* what) {
                                        "the accumulators' drain (MMA thread)",
                                        "a chunk's products (epilogue)",
                                        "the split-K meeting (epilogue)",
-                                       "an unknown wait"};
+                                       "a stage's description (MMA thread)"};
   ISCSI_CUDA(cudaMemset(err, 0, sizeof(int)));
   set_error(std::string(what) + ": a bounded device wait ran out in a tensor-core contraction (" + kSite[h & 7] +
             ", CTA " + std::to_string((h >> 19) & 4095) + ", position " + std::to_string((h >> 3) & 0xFFFF) + ")");
