@@ -55,6 +55,9 @@ WORKLOADS = {
     "cisdt_n200": dict(n=200, na=2, nb=2, kmax=3, ell=5.0, nchol=20, box=True, seed=2000, tau=1e-14),
     # the batching form's block Davidson (16 roots, FP32-mixed)
     "cisdt_n120": dict(n=120, na=2, nb=2, kmax=3, ell=5.0, nchol=20, box=True, seed=4500, tau=1e-14),
+    # more electrons per spin (strings of 3 and 4 electrons), full CI of about fci_n60's size
+    "fci_n24_3a3b": dict(n=24, na=3, nb=3, kmax=6, ell=4.0, nchol=24, box=False, seed=5000, tau=1e-14),
+    "fci_n16_4a4b": dict(n=16, na=4, nb=4, kmax=8, ell=4.0, nchol=16, box=False, seed=5100, tau=1e-14),
 }
 
 
@@ -395,7 +398,7 @@ def run_ours(args, wl, ws, rank, local):
                      "method_tflops": round(2.0 * updates / (gemm_ms * 1e-3) / 1e12, 3) if gemm_ms > 0 else None,
                      "method_frac": round(2.0 * updates / (gemm_ms * 1e-3) / 1e12 / peak, 5) if gemm_ms > 0 else None,
                      "emulation_factor": round(flops / (2.0 * updates), 3) if updates > 0 else None,
-                     "schedule": st.get("tc_schedule_fp64"),
+                     "schedule": st.get("tc_schedule_fp64") if (tc and args.precision == 64) else None,
                      "peak_source": peak_src},
         "hbm": {"compulsory_bytes_per_step": comp_bytes,
                 "achieved_gbs": round(comp_bytes / (ms * 1e-3) / 1e9, 2),
@@ -785,6 +788,101 @@ def dipole_like(n):
     return v + 0.05 * (np.eye(n, k=1) + np.eye(n, k=-1))
 
 
+def run_operators(name, electron_workloads=("fci_n24_3a3b", "fci_n16_4a4b"), steps=5, warmup=3):
+    """Operators other than the Hamiltonian through the same sigma (Sec. "Second
+    part": only the integrals change), on full CI: a transition operator
+    a+_p a_q (one-body, not symmetric), a one-body operator D (dipole-like) and
+    the two-body property operator D^2 (h1 = d d, (pq|rs) = 2 d_pq d_rs).  Each
+    is timed (L2 flushed between calls) and checked by a closed form of its
+    own: <x|A c> = <A^T x|c> for the transition operator, D^2 c = D (D c) for
+    the square.  Then sigma of the Hamiltonian with 3 and 4 electrons per spin."""
+    import numpy as np
+    import torch
+
+    from paper_1609_07757_gb300 import _lib as L
+    from paper_1609_07757_gb300.synthetic import (make_integrals, square_operator_integrals, transition_operator,
+                                                  unit_vector)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed(c, s):
+        for _ in range(warmup):
+            L.iscsi_sigma(c, s, 1)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record()
+            L.iscsi_sigma(c, s, 1)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    def apply(c):
+        s = torch.empty_like(c)
+        L.iscsi_sigma(c, s, 1)
+        return s
+
+    wl = WORKLOADS[name]
+    n, na, nb = wl["n"], wl["na"], wl["nb"]
+    kfull = na + nb
+    d = dipole_like(n)
+    h2, eri2 = square_operator_integrals(d)
+    p, q = n - 1, 0
+    ops = {}
+    handles = {}
+    for key, h1, eri in (("transition", transition_operator(n, p, q), None),
+                         ("transition_adjoint", transition_operator(n, q, p), None),
+                         ("dipole", d, None), ("dipole_squared", h2, eri2)):
+        L.iscsi_init(n, na, nb, kfull, h1, eri, 0.0)
+        handles[key] = L.iscsi_ctx_current()
+    nd = L.iscsi_ndet()
+    c = torch.tensor(unit_vector(nd, 41), dtype=torch.float64, device="cuda")
+    x = torch.tensor(unit_vector(nd, 42), dtype=torch.float64, device="cuda")
+    for key in ("transition", "dipole", "dipole_squared"):
+        L.iscsi_ctx_use(handles[key])
+        s = torch.empty_like(c)
+        ms = timed(c, s)
+        upd = L.iscsi_updates_per_sigma()
+        ops[key] = {"ms_per_sigma": round(ms, 4), "updates_per_sigma": upd,
+                    "gupdates_per_s": round(upd / (ms * 1e-3) / 1e9, 1)}
+    L.iscsi_ctx_use(handles["transition"])
+    ac = apply(c)
+    L.iscsi_ctx_use(handles["transition_adjoint"])
+    atx = apply(x)
+    lhs, rhs = float(torch.dot(x, ac)), float(torch.dot(atx, c))
+    ops["transition"].update({"p": p, "q": q, "adjoint_check": {"x_Ac": lhs, "ATx_c": rhs,
+                                                                "abs_diff": abs(lhs - rhs)}})
+    L.iscsi_ctx_use(handles["dipole_squared"])
+    s2 = apply(c)
+    L.iscsi_ctx_use(handles["dipole"])
+    dd = apply(apply(c))
+    ops["dipole_squared"]["check_vs_d_twice"] = {
+        "max_abs_diff_rel": float((s2 - dd).abs().max() / dd.abs().max())}
+    L.iscsi_finalize()
+    out = {"workload": name, "ndet": nd, "tau": 0.0, "operators": ops,
+           "meaning": "transition: a+_%d a_%d (both spins); dipole: d = diag(p - (n-1)/2)/n + 0.05 "
+                      "nearest-neighbour coupling; dipole_squared: D^2 as a two-body operator" % (p, q)}
+    electrons = []
+    for ename in electron_workloads:
+        ew = WORKLOADS[ename]
+        h1, eri = make_integrals(ew["n"], ew["seed"], ell=ew["ell"], nchol=ew["nchol"], box=ew["box"])
+        L.iscsi_init(ew["n"], ew["na"], ew["nb"], ew["kmax"], h1, eri, ew["tau"])
+        nde = L.iscsi_ndet()
+        ce = torch.tensor(unit_vector(nde, 43), dtype=torch.float64, device="cuda")
+        se = torch.empty_like(ce)
+        ms = timed(ce, se)
+        upd = L.iscsi_updates_per_sigma()
+        st = L.iscsi_stats()
+        electrons.append({"workload": ename, "norb": ew["n"], "nalpha": ew["na"], "nbeta": ew["nb"],
+                          "ndet": nde, "ms_per_sigma": round(ms, 4), "updates_per_sigma": upd,
+                          "gupdates_per_s": round(upd / (ms * 1e-3) / 1e9, 1),
+                          "route_fp64": st.get("route_fp64")})
+        L.iscsi_finalize()
+    out["electron_counts"] = electrons
+    return out
+
+
 def run_propagation(name, nsteps=4, dt=0.02, krylov=12, with_cpu=True):
     """Real-time propagation under H(t) = H_tau + f(t) V (Eq. ham with h(t) =
     h + f(t) v, v dipole-like, f(t) = 0.05 sin(0.8 t)) by the short-iterative
@@ -1138,6 +1236,10 @@ def main():
                     help="real-time propagation under a field on this workload (none: skip)")
     ap.add_argument("--gas-workload", default="fci_n60", choices=sorted(GAS_SPLIT) + ["none"],
                     help="sigma and ground state under a GAS restriction on this workload (none: skip)")
+    ap.add_argument("--operators-workload", default="fci_n60", choices=sorted(WORKLOADS) + ["none"],
+                    help="operators other than H (transition, dipole, dipole squared) and sigma at 3 and 4 "
+                         "electrons per spin")
+    ap.add_argument("--operators-only", action="store_true", help="run only the operators leg and print its object")
     ap.add_argument("--gas-only", action="store_true", help="run only the GAS leg and print its object")
     ap.add_argument("--gas-context-only", action="store_true",
                     help="with --gas-only: only the GAS context (iscsi_init_gas), not the projected form")
@@ -1165,6 +1267,13 @@ def main():
         line = run_reference(args, wl, ws, rank)
         if rank == 0 and line:
             print(json.dumps(line))
+        return
+    if args.operators_only:
+        if rank == 0:
+            from paper_1609_07757_gb300 import _lib as L
+            L.iscsi_set_option("autotune", args.autotune)
+            print(json.dumps({"operators": run_operators(args.operators_workload, steps=args.steps,
+                                                         warmup=args.warmup)}))
         return
     if args.propagation_only or args.density_only or args.gas_only:
         from paper_1609_07757_gb300 import _lib as L
@@ -1206,6 +1315,8 @@ def main():
         line["propagation"] = run_propagation(args.propagation_workload, with_cpu=not args.no_cpu_baseline)
     if rank == 0 and ws == 1 and args.gas_workload != "none":
         line["gas"] = run_gas(args.gas_workload, with_cpu=not args.no_cpu_baseline)
+    if rank == 0 and ws == 1 and args.operators_workload != "none":
+        line["operators"] = run_operators(args.operators_workload)
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
             tau = args.tau if args.tau is not None else wl["tau"]

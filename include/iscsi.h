@@ -94,11 +94,20 @@ typedef int iscsi_status;
  * Create a context for n = norb orbitals, nalpha / nbeta electrons, CI space
  * truncated at total excitation level max_excitation (Eq. ci_hierarchy), and
  * make it current.
- *   h1   host, n*n doubles, row-major h_pq; must be symmetric.
+ *   h1   host, n*n doubles, row-major h_pq: the one-body part
+ *        sum_pq h_pq (a+_p a_q) of each spin.  Any real matrix: the
+ *        Hamiltonian's (symmetric), or a general one-body operator such as
+ *        a transition operator a+_p a_q (h = e_p e_q^T, not symmetric); the
+ *        eigen-solvers and the propagator need a symmetric h1 (ISCSI_E_ARG
+ *        otherwise), sigma and the counts take any.
  *   eri  host, npair*npair doubles, npair = n(n+1)/2, pair-packed chemist
  *        integrals: (pq|rs) = eri[P(p,q)*npair + P(r,s)] with
  *        P(p,q) = max(p,q)*(max(p,q)+1)/2 + min(p,q).  The matrix must be
  *        symmetric ((pq|rs) = (rs|pq)); eri may be NULL (no two-electron part).
+ *        The two-body part is (1/2) sum (pq|rs) (E_pq E_rs - delta_qr E_ps)
+ *        (Eq. ham): the electron repulsion, or any two-body property
+ *        operator with these symmetries (the square of a one-body operator
+ *        d, say: (pq|rs) = 2 d_pq d_rs with h1 = d d).
  *   tau  screening threshold, >= 0: a unit u is kept iff |u| > tau
  *        (the algorithm's "if |I| > epsilon", Sec. "Second part").
  * The library copies h1 and eri; the caller may free them on return.  Builds
@@ -252,8 +261,8 @@ ISCSI_API iscsi_status iscsi_density_host(const double* bra, const double* ket, 
  *             <c|H_k|c> / <c|c> at the step's start.
  * Sigma runs in the "precision" option's arithmetic.  Synchronises (twice per
  * step).  Errors: ISCSI_E_NOINIT, ISCSI_E_ARG (arguments, a coupling on another
- * space, a field without a coupling), ISCSI_E_NAN, ISCSI_E_NOMEM, ISCSI_E_CUDA,
- * ISCSI_E_WAIT.
+ * space, a field without a coupling, a context or coupling whose h1 is not
+ * symmetric), ISCSI_E_NAN, ISCSI_E_NOMEM, ISCSI_E_CUDA, ISCSI_E_WAIT.
  */
 ISCSI_API iscsi_status iscsi_propagate(void* c, int nsteps, double dt, const double* field, int coupling, int krylov,
                                        int imaginary, double* diag);
@@ -306,7 +315,8 @@ ISCSI_API iscsi_status iscsi_gas_mask(void* mask);
  * With option "precision" = 32 the sigma steps run in FP32 until the residual
  * reaches "switch_tol" (option), then in FP64 for the refinement.
  * Synchronises.  Errors: ISCSI_E_NOINIT, ISCSI_E_ARG (nroots < 1 or > ndet,
- * tol <= 0), ISCSI_E_NOCONV, ISCSI_E_NAN, ISCSI_E_NOMEM, ISCSI_E_CUDA.
+ * tol <= 0, h1 not symmetric), ISCSI_E_NOCONV, ISCSI_E_NAN, ISCSI_E_NOMEM,
+ * ISCSI_E_CUDA.
  */
 ISCSI_API iscsi_status iscsi_davidson(int nroots, double tol, double* energies, void* vecs);
 
@@ -446,7 +456,8 @@ ISCSI_API iscsi_status iscsi_batch_check(void);
  * each context's own status.  Synchronises.  Returns ISCSI_OK when every
  * context converged, else the first failing context's status.
  * Errors: ISCSI_E_ARG (count or nroots < 1, nroots > ndet_i, tol <= 0, NULL
- * handles or energies, unknown or repeated handle), ISCSI_E_NOCONV,
+ * handles or energies, unknown or repeated handle, a context whose h1 is not
+ * symmetric), ISCSI_E_NOCONV,
  * ISCSI_E_NAN, ISCSI_E_WAIT, ISCSI_E_NOMEM, ISCSI_E_CUDA.
  */
 ISCSI_API iscsi_status iscsi_batch_davidson(const int* handles, int count, int nroots, double tol, double* energies,

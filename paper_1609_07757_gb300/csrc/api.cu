@@ -258,6 +258,10 @@ iscsi_status iscsi_propagate(void* c, int nsteps, double dt, const double* field
     set_error("iscsi_propagate: a field needs a coupling context");
     return ISCSI_E_ARG;
   }
+  if (!ctx->h1_symmetric || (cpl && !cpl->h1_symmetric)) {
+    set_error("iscsi_propagate: a one-body part that is not symmetric (the propagator needs Hermitian operators)");
+    return ISCSI_E_ARG;
+  }
   if (field)
     for (int k = 0; k < nsteps; ++k)
       if (!std::isfinite(field[k])) {
@@ -295,6 +299,10 @@ iscsi_status iscsi_davidson(int nroots, double tol, double* energies, void* vecs
   NEED_CTX(ctx);
   if (nroots < 1 || nroots > ctx->gas_ndet || !(tol > 0) || !energies) {
     set_error("iscsi_davidson: invalid argument (1 <= nroots <= determinants of the space, tol > 0, energies)");
+    return ISCSI_E_ARG;
+  }
+  if (!ctx->h1_symmetric) {
+    set_error("iscsi_davidson: the context's one-body part is not symmetric (not a Hamiltonian)");
     return ISCSI_E_ARG;
   }
   int s = davidson_run(*ctx, nroots, tol, energies, static_cast<double*>(vecs));
@@ -612,6 +620,11 @@ iscsi_status iscsi_batch_davidson(const int* handles, int count, int nroots, dou
         set_error("iscsi_batch_davidson: a context appears twice");
         return ISCSI_E_ARG;
       }
+    if (!it->second->h1_symmetric) {
+      set_error("iscsi_batch_davidson: the one-body part of the context at position " + std::to_string(i) +
+                " is not symmetric (not a Hamiltonian)");
+      return ISCSI_E_ARG;
+    }
     ctxs[i] = it->second.get();
   }
   int s = davidson_batch_run(ctxs, nroots, tol, energies, reinterpret_cast<double* const*>(vecs), statuses);

@@ -213,6 +213,7 @@ struct Context {
   DevBuf M64base[2];                      // M64 without a per-step one-body term (propagation)
   double m_shift = 0.0;                   // the factor f of that term now in M64
   bool beta_alias = false;
+  bool h1_symmetric = true;  // h_pq == h_qp exactly (a Hermitian one-body part)
   DevBuf diag;                            // FP64 [ndet]
   // workspaces
   size_t ct_elems = 0;                    // elements of all Ct_c (= of all T_c) for one vector

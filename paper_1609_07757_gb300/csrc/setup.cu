@@ -596,6 +596,15 @@ int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h
   ISCSI_CUDA(cudaGetLastError());
   static long long builds = 0;
   ctx.noalloc_gen = ++builds;
+  // a general one-body operator (a transition operator a+_p a_q, say) has
+  // h_pq != h_qp; the string matrices are then not symmetric
+  ctx.h1_symmetric = true;
+  for (int p = 0; p < n && ctx.h1_symmetric; ++p)
+    for (int q = 0; q < p; ++q)
+      if (!(h1[(long long)p * n + q] == h1[(long long)q * n + p])) {
+        ctx.h1_symmetric = false;
+        break;
+      }
   ctx.n = n;
   ctx.na = na;
   ctx.nb = nb;
@@ -681,11 +690,12 @@ int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h
 
   // --- same-spin string Hamiltonians
   unsigned long long cm = ctx.class_mask;
-  // with every one-body and same-spin class kept, M is symmetric (each term's
-  // adjoint is present with the same unit) and identical for both spins when
-  // na == nb, so one matrix serves alpha and (transposed) beta
+  // with a symmetric one-body part and every one-body and same-spin class
+  // kept, M is symmetric (each term's adjoint is present with the same unit)
+  // and identical for both spins when na == nb, so one matrix serves alpha and
+  // (transposed) beta
   const unsigned long long same_spin_bits = 0xFFull | (0x3FFFFull << 24);
-  ctx.beta_alias = (na == nb) && ((cm & same_spin_bits) == same_spin_bits);
+  ctx.beta_alias = (na == nb) && ((cm & same_spin_bits) == same_spin_bits) && ctx.h1_symmetric;
   for (int s = 0; s < 2; ++s) {
     SpinSpace& S = ctx.sp[s];
     if (S.ne == 0) continue;

@@ -74,3 +74,21 @@ def unit_vector(ndet, seed):
 def multi_instance_sizes(count=64, lo=20, hi=80, seed=4100):
     """Orbital counts of the independent instances, uniform on [lo, hi]."""
     return np.random.default_rng(seed).integers(lo, hi + 1, size=count)
+
+
+def transition_operator(n, p, q):
+    """h of the one-body operator a+_p a_q (summed over spin): e_p e_q^T."""
+    h = np.zeros((n, n))
+    h[p, q] = 1.0
+    return h
+
+
+def square_operator_integrals(d):
+    """(h1, eri) that express D^2, D = sum_pq d_pq E_pq with d symmetric, in the
+    Hamiltonian's form sum h_pq E_pq + (1/2) sum (pq|rs) (E_pq E_rs - delta_qr E_ps):
+    h1 = d d, (pq|rs) = 2 d_pq d_rs (pair-packed as make_integrals)."""
+    d = np.asarray(d, dtype=np.float64)
+    n = d.shape[0]
+    pairs = np.array([d[p, q] for p in range(n) for q in range(p + 1)])  # pair_index order
+    eri = 2.0 * np.outer(pairs, pairs)
+    return np.ascontiguousarray(d @ d), np.ascontiguousarray(eri)

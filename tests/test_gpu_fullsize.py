@@ -186,3 +186,39 @@ def test_fullsize_repeated_solves_complete():
         energies.append(e[0])
     # the restriction removes determinants: the restricted ground state lies higher
     assert energies[1] >= energies[0] - 1e-10
+
+
+# more electrons per spin, full CI of about fci_n60's size:
+# name: (n, na, nb, ell, nchol, seed, expected ndet)
+ELECTRONS = {
+    "fci_n24_3a3b": (24, 3, 3, 4.0, 24, 5000, 2024 ** 2),
+    "fci_n16_4a4b": (16, 4, 4, 4.0, 16, 5100, 1820 ** 2),
+}
+
+
+@pytest.mark.parametrize("name", sorted(ELECTRONS))
+def test_fullsize_more_electrons_sampled_rows(name):
+    """Strings of 3 and 4 electrons (the lift over hole strings of 2 and 3):
+    sigma of full CI against the oracle on sampled rows, and the update count
+    against the oracle's count by string levels."""
+    from oracle.counts import updates_per_sigma
+    n, na, nb, ell, nchol, seed, nd = ELECTRONS[name]
+    tau = 1e-14
+    h1, eri = make_integrals(n, seed, ell=ell, nchol=nchol)
+    L.iscsi_init(n, na, nb, na + nb, h1, eri, tau)
+    assert L.iscsi_ndet() == nd
+    c = unit_vector(nd, 19)
+    ct = torch.tensor(c, dtype=torch.float64, device="cuda")
+    st = torch.empty_like(ct)
+    L.iscsi_sigma(ct, st, 1)
+    torch.cuda.synchronize()
+    s = st.cpu().numpy()
+    assert L.iscsi_updates_per_sigma() == updates_per_sigma(n, na, nb, na + nb, tau, h1, eri)
+    L.iscsi_finalize()
+    o = Oracle(n, na, nb, na + nb, tau, h1, eri)
+    rng = np.random.default_rng(7)
+    rows = np.unique(np.concatenate([[0, 1, nd // 2, nd - 1], rng.choice(nd, size=300, replace=False)]))
+    ref = o.sigma_rows(c, rows)
+    scale = np.abs(s).max()
+    err = np.abs(s[rows] - ref).max()
+    assert err <= 1e-12 * scale, (err, scale)

@@ -431,3 +431,59 @@ def test_update_count_from_string_levels(n, na, nb, k, tau):
     o = Oracle(n, na, nb, k, tau, h1, eri)
     _, nup = o.sigma_terms(np.ones(o.ndet))
     assert updates_per_sigma(n, na, nb, k, tau, h1, eri) == nup
+
+
+# ----------------------------------------------------------------------------
+# operators other than the Hamiltonian (Sec. "Second part": any one- or
+# two-electron operator through the same terms with its own integrals)
+
+
+@pytest.mark.parametrize("n,na,nb,k", [(4, 2, 2, 4), (4, 2, 1, 3), (5, 2, 2, 2), (4, 3, 2, 9)])
+def test_nonsymmetric_one_body_operator_against_jordan_wigner(n, na, nb, k):
+    # a general one-body operator sum h_pq a+_p a_q (h not symmetric): the
+    # oracle's dense matrix and its term-by-term sigma against the Fock-space
+    # brute force; a transposed h must give the transposed matrix
+    rng = np.random.default_rng(50 + n + na + k)
+    h = rng.normal(0.0, 0.5, size=(n, n))
+    _, eri = make_integrals(n, 60 + n, ell=2.5, nchol=6)
+    o = Oracle(n, na, nb, k, 0.0, h, eri)
+    H = o.dense_h()
+    Hj = jw.projected(h, jw.unpack_eri(eri, n), n, _det_list(o))
+    assert np.max(np.abs(H - Hj)) < 1e-12
+    assert np.max(np.abs(H - H.T)) > 1e-3  # really not symmetric
+    c = np.random.default_rng(1).normal(size=o.ndet)
+    assert np.max(np.abs(o.sigma_terms(c)[0] - H @ c)) < 1e-12
+    Ht = Oracle(n, na, nb, k, 0.0, np.ascontiguousarray(h.T), eri).dense_h()
+    assert np.max(np.abs(Ht - H.T)) < 1e-12
+
+
+def _square_operator(d):
+    n = d.shape[0]
+    npair = n * (n + 1) // 2
+    eri = np.zeros((npair, npair))
+    for p in range(n):
+        for q in range(p + 1):
+            for r in range(n):
+                for s in range(r + 1):
+                    eri[p * (p + 1) // 2 + q, r * (r + 1) // 2 + s] = 2.0 * d[p, q] * d[r, s]
+    return np.ascontiguousarray(d @ d), eri
+
+
+@pytest.mark.parametrize("n,na,nb", [(4, 2, 2), (5, 2, 1), (5, 3, 2), (6, 2, 2)])
+def test_two_body_property_operator_is_the_square(n, na, nb):
+    # D^2 for D = sum d_pq E_pq as a two-body operator (Eq. ham with
+    # (pq|rs) = 2 d_pq d_rs, h1 = d d) equals D applied twice on full CI,
+    # and matches the Fock-space brute force
+    rng = np.random.default_rng(70 + n + na)
+    d = rng.normal(0.0, 0.4, size=(n, n))
+    d = 0.5 * (d + d.T)
+    h2, eri2 = _square_operator(d)
+    kfull = na + nb
+    od = Oracle(n, na, nb, kfull, 0.0, d, None)
+    od2 = Oracle(n, na, nb, kfull, 0.0, h2, eri2)
+    Hd, Hd2 = od.dense_h(), od2.dense_h()
+    assert np.max(np.abs(Hd2 - Hd @ Hd)) < 1e-12
+    c = np.random.default_rng(2).normal(size=od.ndet)
+    assert np.max(np.abs(od2.sigma_terms(c)[0] - od.sigma_terms(od.sigma_terms(c)[0])[0])) < 1e-11
+    Hj = jw.projected(h2, jw.unpack_eri(eri2, n), n, _det_list(od2))
+    assert np.max(np.abs(Hd2 - Hj)) < 1e-12
