@@ -1226,8 +1226,8 @@ def main():
                     help="pin the roots with a full oracle sigma (minutes) instead of a sample of rows")
     ap.add_argument("--tau-sweep", type=int, default=1, choices=[0, 1],
                     help="time sigma at the workload's other screening thresholds")
-    ap.add_argument("--batching", type=int, default=0, metavar="COUNT",
-                    help="add the batching form: COUNT full-CI instances, batched vs one at a time")
+    ap.add_argument("--batching", type=int, default=16, metavar="COUNT",
+                    help="the batching form: COUNT full-CI instances, batched vs one at a time (0: off)")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="library option autotune (kernel routing timed at the first sigma)")
     ap.add_argument("--density-workload", default="fci_n60", choices=sorted(WORKLOADS) + ["none"],
@@ -1247,8 +1247,8 @@ def main():
                     help="run only the propagation leg (--steps steps) and print its object")
     ap.add_argument("--density-only", action="store_true",
                     help="run only the density-matrix leg and print its object")
-    ap.add_argument("--sweep", action="store_true",
-                    help="add the CISD/CISDT box-size sweep (n = 50..200) with its fitted scaling exponents")
+    ap.add_argument("--sweep", type=int, default=1, choices=[0, 1],
+                    help="the CISD/CISDT box-size sweep (n = 50..200) with its fitted scaling exponents")
     ap.add_argument("--updates", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     ws, rank, local = dist_env()
