@@ -22,6 +22,7 @@
 //     in registers, so no atomics are needed.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 
 #include "internal.cuh"
@@ -1012,6 +1013,9 @@ int sigma_autotune(Context& ctx, const double* c, double* sigma, int nvec, int p
 constexpr size_t kNoAllocScratchBytes = 32u << 20;  // 32 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
+// per-device bookkeeping (the array's address, whose lists it holds), guarded
+// so that host threads calling at once at least keep it consistent
+static std::mutex g_noalloc_mu;
 static void* g_noalloc_ptr[64] = {nullptr};
 static const Context* g_noalloc_lists_of[64] = {nullptr};  // whose lists the array holds, per device
 static long long g_noalloc_lists_gen[64] = {0};
@@ -1043,12 +1047,16 @@ int sigma_noalloc_run(Context& ctx, const double* c, double* sigma) {
     set_error("iscsi_sigma_noalloc: device index out of range");
     return kErrArg;
   }
-  if (!g_noalloc_ptr[dev]) {
-    void* ptr = nullptr;
-    ISCSI_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = ptr;
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      ISCSI_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+      g_noalloc_ptr[dev] = ptr;
+    }
+    base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
   }
-  unsigned char* base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
   double* ctw = reinterpret_cast<double*>(base);
   double* ttw = ctw + ctx.ct_elems;
   size_t lists_off = ctx.have_ab ? ((2 * sizeof(double) * ctx.ct_elems + 255) & ~(size_t)255) : 0;
@@ -1128,6 +1136,7 @@ int sigma_noalloc_run(Context& ctx, const double* c, double* sigma) {
     set_error("iscsi_sigma_noalloc: too many GEMM problems for the static lists");
     return kErrArg;
   }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (g_noalloc_lists_of[dev] != &ctx || g_noalloc_lists_gen[dev] != ctx.noalloc_gen) {
     if (!all.empty())
       ISCSI_CUDA(cudaMemcpyAsync(dprobs, all.data(), sizeof(Problem<double>) * all.size(), cudaMemcpyHostToDevice, st));
