@@ -202,6 +202,7 @@ struct Context {
   int npairs = 0;                         // n*n
   std::vector<int> pair_level_start;      // first pair of each level sum (0..2), size 4
   DevBuf pair_of, pair_index;             // int32 [npairs] -> p*n+r ; int32 [n*n] -> m
+  DevBuf pair_split;                      // int32 [npairs] -> (p << 16) | r (no division in the lifts)
   std::vector<ColClass> cls;
   DevBuf hp_class, hp_local;              // int8 / int32 [nholeA * nholeB]
   DevBuf hp_inv;                          // int32 [total hole pairs] -> X * nholeB + Y, grouped by class

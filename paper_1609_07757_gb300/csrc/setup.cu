@@ -776,6 +776,12 @@ int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h
     ISCSI_TRY(ctx.pair_index.alloc(sizeof(int) * ctx.npairs));
     ISCSI_CUDA(cudaMemcpyAsync(ctx.pair_of.p, pair_of.data(), sizeof(int) * ctx.npairs, cudaMemcpyHostToDevice, st));
     ISCSI_CUDA(cudaMemcpyAsync(ctx.pair_index.p, pair_index.data(), sizeof(int) * ctx.npairs, cudaMemcpyHostToDevice, st));
+    std::vector<int> pair_split(ctx.npairs);
+    for (int m = 0; m < ctx.npairs; ++m) pair_split[m] = ((pair_of[m] / n) << 16) | (pair_of[m] % n);
+    ISCSI_TRY(ctx.pair_split.alloc(sizeof(int) * ctx.npairs));
+    ISCSI_CUDA(cudaMemcpyAsync(ctx.pair_split.p, pair_split.data(), sizeof(int) * ctx.npairs, cudaMemcpyHostToDevice,
+                               st));
+    ISCSI_CUDA(cudaStreamSynchronize(st));  // the host vector must outlive the copy
 
     // hole pairs (X, Y) grouped by column level class c = level(X) + level(Y)
     const SpinSpace& HA = ctx.sp[0];

@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(256)
 // part[chunk][problem offset + m * N + n] and a second kernel adds them in
 // chunk order (deterministic).  tile_begin = first column item of the
 // problem, seg K ranges are taken in order.
-constexpr int kMthinChunk = 512;
+constexpr int kMthinChunk = 64;
 
 template <typename T>
 __global__ void __launch_bounds__(256)

@@ -52,7 +52,7 @@ struct TcTable {
   TcClass c[2 * kMaxElec];
   long long start[2 * kMaxElec + 1];  // flattened (col, k) element offsets
   int col_start[2 * kMaxElec + 1];    // first column of each class over all classes
-  int blk_start[2 * kMaxElec + 1];    // first block of 8 columns of each class (tiled lift)
+  int blk_start[2 * kMaxElec + 1];    // first block of each class in the tiled lift (kLiftCols columns each)
 };
 
 static inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -72,11 +72,11 @@ struct OzLiftCol {
 };
 
 template <typename V>
-__device__ __forceinline__ V oz_lift_value(const OzLiftCol& L, const TcClass& C, int k, int n,
-                                           const int* __restrict__ pair_of, const V* __restrict__ cv) {
+__device__ __forceinline__ V oz_lift_value(const OzLiftCol& L, const TcClass& C, int k,
+                                           const int* __restrict__ pair_split, const V* __restrict__ cv) {
   if (k >= C.krows) return (V)0;
-  const int qs = pair_of[k];
-  const int q = qs / n, s = qs - (qs / n) * n;
+  const int qs = __ldg(pair_split + k);
+  const int q = qs >> 16, s = qs & 0xFFFF;
   const int ea = L.a[q], eb = L.b[s];
   if (ea < 0 || eb < 0) return (V)0;
   const int Bp = eb >> 1;
@@ -113,57 +113,74 @@ __device__ __forceinline__ int oz_stage_column(const TcTable& tt, int n, int nho
   return cl;
 }
 
-// The B operand of the opposite-spin contraction in the tiled layout: one
-// block per 8 consecutive columns (X, Y, v) of one class, one warp per
-// column.  A warp stages its column's lift entries, finds the column's
-// exponent (largest |x|) in a first pass over the K values, then gathers them
-// again in 8-wide chunks, cuts each into exact slices and writes every slice's
-// chunk as one 16-byte store (the 8 warps of a block fill the 8 rows of a
-// core matrix: whole 128-byte runs).  Columns beyond the class stay zero.
-__global__ void __launch_bounds__(256) k_oz_lift_tiled(TcTable tt, int n, int nholeA, int nholeB,
-                                                       const int* __restrict__ pair_of,
+// The lifted column (X, Y, v) of class c, cut into tiled slices: a column is
+// walked by kLiftWarps warps (each a share of the K range, in 8-wide chunks
+// per lane: eight independent gathers in flight), which
+// first find the column's exponent (largest |x|; the warps' maxima meet
+// in shared memory), then gather their chunks again, cut each into exact
+// slices and write every slice's chunk as one 16-byte store.  One warp per
+// column left most SMs with a few warps waiting on gathers.  Columns beyond
+// the class stay zero.
+constexpr int kLiftCols = 1;   // columns per block
+constexpr int kLiftWarps = 8;  // warps per column
+constexpr int kLiftThreads = 32 * kLiftCols * kLiftWarps;
+__global__ void __launch_bounds__(kLiftThreads) k_oz_lift_tiled(TcTable tt, int n, int nholeA, int nholeB,
+                                                       const int* __restrict__ pair_split,
                                                        const int* __restrict__ hp_inv, const int* __restrict__ liftA,
                                                        const int* __restrict__ liftB, const int8_t* __restrict__ alevel,
                                                        const int* __restrict__ nballow,
                                                        const long long* __restrict__ off, const double* __restrict__ c,
                                                        long long ndet, int* __restrict__ exps,
                                                        __nv_bfloat16* __restrict__ bs) {
-  __shared__ OzLiftCol Ls[8];
+  __shared__ OzLiftCol Ls[kLiftCols];
+  __shared__ int mx[kLiftCols][kLiftWarps];
   int cl = 0;
   while ((int)blockIdx.x >= tt.blk_start[cl + 1]) ++cl;
   const TcClass& C = tt.c[cl];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int col = ((int)blockIdx.x - tt.blk_start[cl]) * 8 + warp;
-  if (col >= C.ncols) return;  // the whole warp; nothing below synchronises the block
-  OzLiftCol& L = Ls[warp];
-  const int hp = col / tt.nvec, vv = col - (col / tt.nvec) * tt.nvec;
-  const int xy = hp_inv[C.hp_start + hp];
-  const int X = xy / nholeB, Y = xy - (xy / nholeB) * nholeB;
-  for (int q = lane; q < n; q += 32) {
-    const int ea = liftA[q * nholeA + X];
-    L.a[q] = ea;
-    L.b[q] = liftB[q * nholeB + Y];
-    if (ea >= 0) {
-      const int A = ea >> 1;
-      L.off[q] = off[A];
-      L.lim[q] = nballow[alevel[A]];
+  const int wc = warp / kLiftWarps, wk = warp % kLiftWarps;  // column in the block, quarter of K
+  const int col = ((int)blockIdx.x - tt.blk_start[cl]) * kLiftCols + wc;
+  const bool live = col < C.ncols;  // no early return: the block meets below
+  OzLiftCol& L = Ls[wc];
+  const int hp = live ? col / tt.nvec : 0, vv = live ? col - hp * tt.nvec : 0;
+  if (live) {
+    const int xy = hp_inv[C.hp_start + hp];
+    const int X = xy / nholeB, Y = xy - (xy / nholeB) * nholeB;
+    for (int q = wk * 32 + lane; q < n; q += 32 * kLiftWarps) {
+      const int ea = liftA[q * nholeA + X];
+      L.a[q] = ea;
+      L.b[q] = liftB[q * nholeB + Y];
+      if (ea >= 0) {
+        const int A = ea >> 1;
+        L.off[q] = off[A];
+        L.lim[q] = nballow[alevel[A]];
+      }
     }
   }
-  __syncwarp();
+  __syncthreads();
   const double* cv = c + (long long)vv * ndet;
-  int m = 0;
-  for (int k = lane; k < C.kpad; k += 32) m = max(m, oz_exp_field(oz_lift_value<double>(L, C, k, n, pair_of, cv)));
-  m = __reduce_max_sync(0xffffffffu, m);
-  const int ex = m > 0 ? m - 1022 : 0;
-  if (lane == 0) exps[C.exp_off + col] = ex;
   const int kst = C.kpad / OZ_BK;
+  int m = 0;
+  if (live)
+    for (int kc = wk * 32 + lane; kc < 2 * kst; kc += 32 * kLiftWarps) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) m = max(m, oz_exp_field(oz_lift_value<double>(L, C, kc * 8 + j, pair_split, cv)));
+    }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if (lane == 0) mx[wc][wk] = m;
+  __syncthreads();
+  if (!live) return;
+#pragma unroll
+  for (int w = 0; w < kLiftWarps; ++w) m = max(m, mx[wc][w]);
+  const int ex = m > 0 ? m - 1022 : 0;
+  if (wk == 0 && lane == 0) exps[C.exp_off + col] = ex;
   __nv_bfloat16* tile0 = bs + C.bs_off + (long long)(col / OZ_BN) * kst * OZ_TB_BLOCK;
-  for (int kc = lane; kc < 2 * kst; kc += 32) {
+  for (int kc = wk * 32 + lane; kc < 2 * kst; kc += 32 * kLiftWarps) {
     uint32_t pk[OZ_S][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       int a[OZ_S];
-      oz_digits(oz_lift_value<double>(L, C, kc * 8 + j, n, pair_of, cv), ex, a);
+      oz_digits(oz_lift_value<double>(L, C, kc * 8 + j, pair_split, cv), ex, a);
 #pragma unroll
       for (int sl = 0; sl < OZ_S; ++sl) {
         const uint32_t b = oz_digit_bits(a[sl], sl);
@@ -181,7 +198,7 @@ __global__ void __launch_bounds__(256) k_oz_lift_tiled(TcTable tt, int n, int nh
 // FP32 form: Ct^T gathered from the FP32 vector and split into three bf16
 // terms, one block per column with its lift entries staged as above
 __global__ void __launch_bounds__(256) k_t3_lift(TcTable tt, int n, int nholeA, int nholeB,
-                                                 const int* __restrict__ pair_of, const int* __restrict__ hp_inv,
+                                                 const int* __restrict__ pair_split, const int* __restrict__ hp_inv,
                                                  const int* __restrict__ liftA, const int* __restrict__ liftB,
                                                  const int8_t* __restrict__ alevel, const int* __restrict__ nballow,
                                                  const long long* __restrict__ off, const float* __restrict__ c,
@@ -193,7 +210,7 @@ __global__ void __launch_bounds__(256) k_t3_lift(TcTable tt, int n, int nholeA, 
   __nv_bfloat16* row = bs + C.bs_off + (long long)col * C.kpad;
   const long long stride = (long long)C.npad * C.kpad;
   for (int k = threadIdx.x; k < C.kpad; k += blockDim.x)
-    t3_store_terms<float>(oz_lift_value<float>(L, C, k, n, pair_of, cv), row + k, stride);
+    t3_store_terms<float>(oz_lift_value<float>(L, C, k, pair_split, cv), row + k, stride);
 }
 
 static int tc_attr() {
@@ -397,7 +414,7 @@ static TcTable ab_table(const Context& ctx, int nvec, long long* bs_elems, long 
     C.tot = (long long)C.ncols * C.kpad;
     tt.start[tt.nclass] = flat;
     tt.col_start[tt.nclass + 1] = tt.col_start[tt.nclass] + C.ncols;
-    tt.blk_start[tt.nclass + 1] = tt.blk_start[tt.nclass] + (C.ncols + 7) / 8;
+    tt.blk_start[tt.nclass + 1] = tt.blk_start[tt.nclass] + (C.ncols + kLiftCols - 1) / kLiftCols;
     tt.c[tt.nclass++] = C;
     flat += C.tot;
     bs += (long long)nslice * C.npad * C.kpad;
@@ -465,7 +482,7 @@ int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec) {
   const SpinSpace& SB = ctx.sp[1];
   const int nblk = tt.blk_start[tt.nclass];
   if (nblk > 0) {
-    k_oz_lift_tiled<<<nblk, 256, 0, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_of.as<int>(), ctx.hp_inv.as<int>(),
+    k_oz_lift_tiled<<<nblk, kLiftThreads, 0, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_split.as<int>(), ctx.hp_inv.as<int>(),
                                           SA.lift.as<int>(), SB.lift.as<int>(), SA.level.as<int8_t>(),
                                           ctx.nballow.as<int>(), ctx.off.as<long long>(), c, ctx.ndet,
                                           ctx.oz_bexp.as<int>(), ctx.oz_bs.as<__nv_bfloat16>()); ISCSI_COUNT_LAUNCH();
@@ -784,7 +801,7 @@ int opposite_tc32_operands(Context& ctx, const float* c, float* ttw, int nvec) {
   const SpinSpace& SA = ctx.sp[0];
   const SpinSpace& SB = ctx.sp[1];
   if (tt.col_start[tt.nclass] > 0)
-  k_t3_lift<<<tt.col_start[tt.nclass], 256, 0, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_of.as<int>(),
+  k_t3_lift<<<tt.col_start[tt.nclass], 256, 0, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_split.as<int>(),
                                                        ctx.hp_inv.as<int>(), SA.lift.as<int>(), SB.lift.as<int>(),
                                                        SA.level.as<int8_t>(), ctx.nballow.as<int>(),
                                                        ctx.off.as<long long>(), c, ctx.ndet,
