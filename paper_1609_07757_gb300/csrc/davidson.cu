@@ -748,6 +748,7 @@ struct Dav {
   int k, maxsub, kc, parts, rows_cap, eig_smem;
   cudaStream_t st;
   DevBuf ctl_d, S, Y, thetas, eigA, eigQ, partial, C1, C2, G, Rinv, rr_part;
+  DevBuf rq;  // x_j . r_j and x_j . x_j of the returned vectors
   double *V = nullptr, *W = nullptr, *X = nullptr, *R = nullptr, *T = nullptr, *Wn = nullptr, *tmp = nullptr;
   DavCtl* ctl = nullptr;
 
@@ -1291,12 +1292,30 @@ static int davidson_batch_body(const std::vector<Context*>& ctxs, int kw, double
     for (int i : members) ++iters[i];
   }
   ISCSI_TRY(batch_wait_status(sb));
-  // results: the last evaluation of every instance
-  for (int i = 0; i < n; ++i) ISCSI_CUDA(cudaMemcpyAsync(&H[i], D[i]->ctl, sizeof(DavCtl), cudaMemcpyDeviceToHost, st));
+  // results: the last evaluation of every instance.  The energies returned are
+  // the Rayleigh quotients of the vectors returned, rho_j = theta_j + x_j.r_j /
+  // x_j.x_j with r_j = W y_j - theta_j x_j the last residual: the Ritz values
+  // of the projected matrix also carry the basis' small departure from
+  // orthonormality (~2e-12 Eh at full CI n = 60)
+  std::vector<std::vector<double>> rqh(n, std::vector<double>(2 * (size_t)kw * kw, 0.0));
+  for (int i = 0; i < n; ++i) {
+    Dav& d = *D[i];
+    ISCSI_CUDA(cudaMemcpyAsync(&H[i], d.ctl, sizeof(DavCtl), cudaMemcpyDeviceToHost, st));
+    ISCSI_TRY(d.rq.grow(sizeof(double) * 2 * (size_t)kw * kw));
+    d.st = st;
+    d.dots(d.X, nullptr, kw, d.R, kw, d.rq.as<double>());
+    d.dots(d.X, nullptr, kw, d.X, kw, d.rq.as<double>() + (size_t)kw * kw);
+    ISCSI_CUDA(cudaMemcpyAsync(rqh[i].data(), d.rq.p, sizeof(double) * 2 * (size_t)kw * kw, cudaMemcpyDeviceToHost,
+                               st));
+  }
   ISCSI_CUDA(cudaStreamSynchronize(st));
   for (int i = 0; i < n; ++i) {
     if (status[i] == kErrNoConv && prec[i] == 64 && (H[i].status & kStatusConverged)) status[i] = kOk;
-    for (int j = 0; j < kw; ++j) energies[(size_t)i * kw + j] = H[i].theta[j];
+    for (int j = 0; j < kw; ++j) {
+      const double xr = rqh[i][(size_t)j * kw + j], xx = rqh[i][(size_t)kw * kw + (size_t)j * kw + j];
+      const double rho = H[i].theta[j] + (xx > 0.0 ? xr / xx : 0.0);
+      energies[(size_t)i * kw + j] = std::isfinite(rho) ? rho : H[i].theta[j];
+    }
     if (vecs && vecs[i])
       ISCSI_CUDA(cudaMemcpyAsync(vecs[i], D[i]->X, sizeof(double) * kw * D[i]->N, cudaMemcpyDeviceToDevice, st));
     if (statuses) statuses[i] = status[i];
