@@ -320,6 +320,21 @@ ISCSI_API iscsi_status iscsi_gas_mask(void* mask);
  */
 ISCSI_API iscsi_status iscsi_davidson(int nroots, double tol, double* energies, void* vecs);
 
+/*
+ * Exercises the failure path of the tensor-core kernels' bounded waits
+ * without a fault (the paper has no counterpart; this is the library's own
+ * failure detection): one CTA waits, with the kernels' own bounded wait, on a
+ * barrier that nothing arrives on, gives up after `polls` polls and reports
+ * through the current context's error word.  The call synchronises and returns
+ * ISCSI_E_WAIT with the wait's site, CTA and position in iscsi_last_error
+ * ("a stage's data (MMA thread), CTA 0, position 1"), as a contraction whose
+ * wait ran out would; the word is cleared and the context stays usable.
+ *   polls  in [1024, 2^24] (about a microsecond per 100 polls).
+ * Errors: ISCSI_E_NOINIT, ISCSI_E_ARG (polls out of range), ISCSI_E_CUDA;
+ * ISCSI_E_WAIT is the expected result.
+ */
+ISCSI_API iscsi_status iscsi_check_bounded_wait(long long polls);
+
 /* number of determinants of the current context, or -1 if none */
 ISCSI_API long long iscsi_ndet(void);
 

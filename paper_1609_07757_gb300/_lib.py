@@ -51,6 +51,7 @@ def load(build_if_missing=True):
         "iscsi_sigma_host": (c_int, [vp, vp, c_int]),
         "iscsi_sigma_noalloc": (c_int, [vp, vp]),
         "iscsi_davidson": (c_int, [c_int, c_d, vp, vp]),
+        "iscsi_check_bounded_wait": (c_int, [c_ll]),
         "iscsi_density": (c_int, [vp, vp, vp, vp]),
         "iscsi_propagate": (c_int, [vp, c_int, c_d, vp, c_int, c_int, c_int, vp]),
         "iscsi_density_host": (c_int, [vp, vp, vp, vp]),
@@ -241,6 +242,11 @@ def iscsi_gas_mask(mask):
     if not (mask.is_cuda and mask.dtype == torch.uint8 and mask.is_contiguous() and mask.numel() == iscsi_ndet()):
         raise ValueError("expected a contiguous uint8 CUDA tensor of ndet elements")
     _check(load().iscsi_gas_mask(mask.data_ptr()))
+
+
+def iscsi_check_bounded_wait(polls):
+    """The bounded waits' failure path (ISCSI_E_WAIT is the expected status; raises IscsiError with it)."""
+    return _check(load().iscsi_check_bounded_wait(int(polls)))
 
 
 def iscsi_davidson(nroots, tol, vecs=None):

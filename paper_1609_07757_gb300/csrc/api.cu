@@ -295,6 +295,15 @@ iscsi_status iscsi_gas_mask(void* mask) {
   return ISCSI_OK;
 }
 
+iscsi_status iscsi_check_bounded_wait(long long polls) {
+  NEED_CTX(ctx);
+  if (polls < 1024 || polls > (1ll << 24)) {
+    set_error("iscsi_check_bounded_wait: polls must lie in [1024, 2^24]");
+    return ISCSI_E_ARG;
+  }
+  return tc_wait_selftest(*ctx, polls);
+}
+
 iscsi_status iscsi_davidson(int nroots, double tol, double* energies, void* vecs) {
   NEED_CTX(ctx);
   if (nroots < 1 || nroots > ctx->gas_ndet || !(tol > 0) || !energies) {

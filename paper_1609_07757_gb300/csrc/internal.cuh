@@ -361,6 +361,7 @@ const OzJob* both_tc_job(Context& ctx, int prec);  // that combined job (built w
 int launch_tc_problems(const OzProblem* probs, int nprobs, const OzSeg* segs, const OzMaps* maps,
                        void* const* tbases, int tiles, const OzPlan* plan, int prec, int* err, cudaStream_t st);
 int tc_check(Context& ctx);
+int tc_wait_selftest(Context& ctx, long long polls);
 int tc_wait_status(int* err, const char* what);
 int samespin_matrices_changed(Context& ctx);  // re-cut the same-spin operand slices in place
 // M <- M_base + f M_v (cpl: the context of v); f = 0 restores (sigma.cu)

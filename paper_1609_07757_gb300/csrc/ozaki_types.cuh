@@ -4,6 +4,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include "tc_ptx.cuh"
+
 namespace iscsi {
 
 constexpr int OZ_S = 7;            // slices per operand
@@ -38,6 +40,21 @@ constexpr int OZ_SITE_EPI_SYNC = 6;   // epilogue: the split-K meeting (meetings
 constexpr int OZ_SITE_INFO = 7;       // MMA thread: a stage's description (stages consumed)
 constexpr int OZ_WAIT_CTA = 1 << 19;
 __host__ __device__ constexpr int oz_wait_code(int site, int detail) { return site | ((detail & 0xFFFF) << 3); }
+
+// The bounded wait of the contraction kernels: polls the phase of `parity` at
+// most `limit` times; every 1024 polls it looks at the CTA's abort word, and a
+// wait that runs out stores its code there (the first one wins), so that every
+// role stops and the kernel reports through its error word.
+__device__ __forceinline__ bool oz_wait_bounded(uint64_t* bar, uint32_t parity, int site, int detail,
+                                                volatile int* abort_word, long long limit) {
+  const uint32_t a = tc::smem_u32(bar);
+  for (long long i = 0; i < limit; ++i) {
+    if (tc::mbar_try_wait(a, parity)) return true;
+    if ((i & 1023) == 1023 && *abort_word) return false;
+  }
+  atomicCAS((int*)abort_word, 0, oz_wait_code(site, detail));
+  return false;
+}
 
 constexpr int OZ_MAX_SEGS = 8;
 constexpr int OZ_BW_ROWS = 128;    // rows of B per 128-column tile; B arrays are padded to this

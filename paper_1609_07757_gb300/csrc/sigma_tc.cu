@@ -1038,6 +1038,32 @@ int tc_wait_status(int* err, const char* what) {
   return kErrWait;
 }
 
+// The failure path of the contraction kernels' bounded waits, without a fault:
+// one CTA waits (oz_wait_bounded, the kernels' own wait) on a barrier that
+// nothing arrives on, gives up after `limit` polls and reports through the
+// context's error word as the kernels do (site: a stage's data, position 1).
+// No tensor memory is involved.
+__global__ void k_wait_selftest(int* err, long long limit) {
+  __shared__ uint64_t bar;
+  __shared__ volatile int abort_s;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(tc::smem_u32(&bar), 1);
+    abort_s = 0;
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  oz_wait_bounded(&bar, 0, OZ_SITE_FULL, 1, &abort_s, limit);
+  __syncthreads();
+  if (abort_s && threadIdx.x == 0) atomicCAS(err, 0, abort_s + (int)blockIdx.x * OZ_WAIT_CTA);
+}
+
+int tc_wait_selftest(Context& ctx, long long polls) {
+  ISCSI_TRY(tc_err_buf(ctx));
+  k_wait_selftest<<<1, 64, 0, stream()>>>(ctx.oz_err.as<int>(), polls); ISCSI_COUNT_LAUNCH();
+  ISCSI_CUDA(cudaGetLastError());
+  return tc_check(ctx);
+}
+
 // status of the bounded waits of the context's tensor-core kernels (synchronises)
 int tc_check(Context& ctx) {
   const int rc = tc_wait_status(ctx.oz_err.as<int>(), "tensor-core sigma");

@@ -108,13 +108,7 @@ __global__ void __launch_bounds__(T3W_THREADS, 1)
 
   // a wait that runs out records where (oz_wait_code) and stops every role
   auto wait = [&](uint64_t* bar, uint32_t parity, int site, int detail) -> bool {
-    uint32_t a = tc::smem_u32(bar);
-    for (long long i = 0; i < OZ_SPIN; ++i) {
-      if (tc::mbar_try_wait(a, parity)) return true;
-      if ((i & 1023) == 1023 && abort_s) return false;
-    }
-    atomicCAS((int*)&abort_s, 0, oz_wait_code(site, detail));
-    return false;
+    return oz_wait_bounded(bar, parity, site, detail, &abort_s, OZ_SPIN);
   };
 
   if (warp == 0) {
