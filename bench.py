@@ -61,6 +61,10 @@ WORKLOADS = {
 }
 
 
+# the screening sweep: a workload whose integrals decay with the box, and thresholds
+SCREEN_SWEEP = ("cisdt_n100", (1e-14, 1e-10, 1e-8, 1e-6, 1e-4))
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -421,6 +425,11 @@ def run_ours(args, wl, ws, rank, local):
         # the same sigma at the workload's other screening thresholds
         line["tau_sweep"] = run_tau_sweep(L, wl, [t for t in wl.get("taus", ()) if t != tau], steps=args.steps,
                                           warmup=args.warmup)
+        # where the screen removes whole blocks of units: the box-decay CISDT
+        # workload at rising thresholds (sigma time against the units kept)
+        sw = WORKLOADS[SCREEN_SWEEP[0]]
+        line["screen_sweep"] = {"workload": SCREEN_SWEEP[0],
+                                "points": run_tau_sweep(L, sw, SCREEN_SWEEP[1], steps=args.steps, warmup=args.warmup)}
     return line
 
 

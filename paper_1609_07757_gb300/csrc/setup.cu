@@ -754,21 +754,29 @@ int context_build(Context& ctx, int n, int na, int nb, int kmax, const double* h
     }
   }
   if (na > 0 && nb > 0) {
-    // pair ordering pi(p, r): sorted by (level(p) + level(r), p, r)
+    // pair ordering pi(p, r): sorted by level(p) + level(r); within a level
+    // sum in 8 x 8 patches of (p, r) (patches by p, then r; inside one, p
+    // then r).  A 128-row block of G then covers a 8 x 16 patch of (p, r)
+    // and a 16-wide K step a 2 x 8 patch of (q, s), so that a block's units
+    // are all small (screened, or with leading zero slices) whenever the
+    // integrals decay in either |p - q| or |r - s|, not only in |p - q|.
     ctx.npairs = n * n;
     std::vector<int> pair_of(ctx.npairs), pair_index(ctx.npairs);
     ctx.pair_level_start.assign(4, 0);
     {
+      constexpr int kPatch = 8;
       int m = 0;
       for (int lvl = 0; lvl <= 2; ++lvl) {
         ctx.pair_level_start[lvl] = m;
-        for (int p = 0; p < n; ++p)
-          for (int r = 0; r < n; ++r)
-            if ((p >= ctx.sp[0].nocc) + (r >= ctx.sp[1].nocc) == lvl) {
-              pair_of[m] = p * n + r;
-              pair_index[p * n + r] = m;
-              ++m;
-            }
+        for (int p0 = 0; p0 < n; p0 += kPatch)
+          for (int r0 = 0; r0 < n; r0 += kPatch)
+            for (int p = p0; p < std::min(n, p0 + kPatch); ++p)
+              for (int r = r0; r < std::min(n, r0 + kPatch); ++r)
+                if ((p >= ctx.sp[0].nocc) + (r >= ctx.sp[1].nocc) == lvl) {
+                  pair_of[m] = p * n + r;
+                  pair_index[p * n + r] = m;
+                  ++m;
+                }
       }
       ctx.pair_level_start[3] = m;
     }
