@@ -44,6 +44,7 @@ struct TcClass {
   long long bs_off; // element offset of the class's slices in the B buffer (slice 0)
   long long exp_off;
   long long tot;    // ncols * kpad (elements gathered)
+  int wpc;          // warps per column in the tiled lift (1, 2, 4 or 8; the block's 8 warps)
 };
 
 struct TcTable {
@@ -52,7 +53,7 @@ struct TcTable {
   TcClass c[2 * kMaxElec];
   long long start[2 * kMaxElec + 1];  // flattened (col, k) element offsets
   int col_start[2 * kMaxElec + 1];    // first column of each class over all classes
-  int blk_start[2 * kMaxElec + 1];    // first block of each class in the tiled lift (kLiftCols columns each)
+  int blk_start[2 * kMaxElec + 1];    // first block of each class in the tiled lift (8 / wpc columns each)
 };
 
 static inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -114,16 +115,19 @@ __device__ __forceinline__ int oz_stage_column(const TcTable& tt, int n, int nho
 }
 
 // The lifted column (X, Y, v) of class c, cut into tiled slices: a column is
-// walked by kLiftWarps warps (each a share of the K range, in 8-wide chunks
-// per lane: eight independent gathers in flight), which
-// first find the column's exponent (largest |x|; the warps' maxima meet
-// in shared memory), then gather their chunks again, cut each into exact
-// slices and write every slice's chunk as one 16-byte store.  One warp per
-// column left most SMs with a few warps waiting on gathers.  Columns beyond
-// the class stay zero.
-constexpr int kLiftCols = 1;   // columns per block
-constexpr int kLiftWarps = 8;  // warps per column
-constexpr int kLiftThreads = 32 * kLiftCols * kLiftWarps;
+// walked by C.wpc warps of the block's eight (each a share of the K range, in
+// 8-wide chunks per lane: eight independent gathers in flight), which first
+// find the column's exponent (largest |x|; the warps' maxima meet in shared
+// memory), then gather their chunks again, cut each into exact slices and
+// write every slice's chunk as one 16-byte store.  Long columns take eight
+// warps (one warp per column left most SMs with a few warps waiting on
+// gathers), short ones one (8 columns per block: a K of 256 is 32 chunks, one
+// per lane).  Columns beyond the class stay zero.
+constexpr int kLiftThreads = 256;
+__host__ __device__ constexpr int oz_lift_wpc(int kpad) {
+  // 8-wide chunks of the column, at least 48 per warp
+  return kpad / 8 >= 384 ? 8 : kpad / 8 >= 192 ? 4 : kpad / 8 >= 96 ? 2 : 1;
+}
 __global__ void __launch_bounds__(kLiftThreads) k_oz_lift_tiled(TcTable tt, int n, int nholeA, int nholeB,
                                                        const int* __restrict__ pair_split,
                                                        const int* __restrict__ hp_inv, const int* __restrict__ liftA,
@@ -132,21 +136,25 @@ __global__ void __launch_bounds__(kLiftThreads) k_oz_lift_tiled(TcTable tt, int 
                                                        const long long* __restrict__ off, const double* __restrict__ c,
                                                        long long ndet, int* __restrict__ exps,
                                                        __nv_bfloat16* __restrict__ bs) {
-  __shared__ OzLiftCol Ls[kLiftCols];
-  __shared__ int mx[kLiftCols][kLiftWarps];
+  // the staged lift tables of the block's columns (dynamic: as many as the
+  // launch's largest columns-per-block needs, so that long columns leave the
+  // SM's L1 to the gathers)
+  extern __shared__ OzLiftCol Ls[];
+  __shared__ int mx[8];
   int cl = 0;
   while ((int)blockIdx.x >= tt.blk_start[cl + 1]) ++cl;
   const TcClass& C = tt.c[cl];
+  const int wpc = C.wpc, cpb = 8 / wpc;  // warps per column, columns per block
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wc = warp / kLiftWarps, wk = warp % kLiftWarps;  // column in the block, quarter of K
-  const int col = ((int)blockIdx.x - tt.blk_start[cl]) * kLiftCols + wc;
+  const int wc = warp / wpc, wk = warp % wpc;  // column in the block, share of K
+  const int col = ((int)blockIdx.x - tt.blk_start[cl]) * cpb + wc;
   const bool live = col < C.ncols;  // no early return: the block meets below
   OzLiftCol& L = Ls[wc];
   const int hp = live ? col / tt.nvec : 0, vv = live ? col - hp * tt.nvec : 0;
   if (live) {
     const int xy = hp_inv[C.hp_start + hp];
     const int X = xy / nholeB, Y = xy - (xy / nholeB) * nholeB;
-    for (int q = wk * 32 + lane; q < n; q += 32 * kLiftWarps) {
+    for (int q = wk * 32 + lane; q < n; q += 32 * wpc) {
       const int ea = liftA[q * nholeA + X];
       L.a[q] = ea;
       L.b[q] = liftB[q * nholeB + Y];
@@ -162,20 +170,19 @@ __global__ void __launch_bounds__(kLiftThreads) k_oz_lift_tiled(TcTable tt, int 
   const int kst = C.kpad / OZ_BK;
   int m = 0;
   if (live)
-    for (int kc = wk * 32 + lane; kc < 2 * kst; kc += 32 * kLiftWarps) {
+    for (int kc = wk * 32 + lane; kc < 2 * kst; kc += 32 * wpc) {
 #pragma unroll
       for (int j = 0; j < 8; ++j) m = max(m, oz_exp_field(oz_lift_value<double>(L, C, kc * 8 + j, pair_split, cv)));
     }
   m = __reduce_max_sync(0xffffffffu, m);
-  if (lane == 0) mx[wc][wk] = m;
+  if (lane == 0) mx[warp] = m;
   __syncthreads();
   if (!live) return;
-#pragma unroll
-  for (int w = 0; w < kLiftWarps; ++w) m = max(m, mx[wc][w]);
+  for (int w = 0; w < wpc; ++w) m = max(m, mx[wc * wpc + w]);
   const int ex = m > 0 ? m - 1022 : 0;
   if (wk == 0 && lane == 0) exps[C.exp_off + col] = ex;
   __nv_bfloat16* tile0 = bs + C.bs_off + (long long)(col / OZ_BN) * kst * OZ_TB_BLOCK;
-  for (int kc = wk * 32 + lane; kc < 2 * kst; kc += 32 * kLiftWarps) {
+  for (int kc = wk * 32 + lane; kc < 2 * kst; kc += 32 * wpc) {
     uint32_t pk[OZ_S][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -414,7 +421,8 @@ static TcTable ab_table(const Context& ctx, int nvec, long long* bs_elems, long 
     C.tot = (long long)C.ncols * C.kpad;
     tt.start[tt.nclass] = flat;
     tt.col_start[tt.nclass + 1] = tt.col_start[tt.nclass] + C.ncols;
-    tt.blk_start[tt.nclass + 1] = tt.blk_start[tt.nclass] + (C.ncols + kLiftCols - 1) / kLiftCols;
+    C.wpc = oz_lift_wpc(C.kpad);
+    tt.blk_start[tt.nclass + 1] = tt.blk_start[tt.nclass] + (C.ncols + 8 / C.wpc - 1) / (8 / C.wpc);
     tt.c[tt.nclass++] = C;
     flat += C.tot;
     bs += (long long)nslice * C.npad * C.kpad;
@@ -482,7 +490,9 @@ int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec) {
   const SpinSpace& SB = ctx.sp[1];
   const int nblk = tt.blk_start[tt.nclass];
   if (nblk > 0) {
-    k_oz_lift_tiled<<<nblk, kLiftThreads, 0, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_split.as<int>(), ctx.hp_inv.as<int>(),
+    int cpb_max = 1;
+    for (int i = 0; i < tt.nclass; ++i) cpb_max = std::max(cpb_max, 8 / tt.c[i].wpc);
+    k_oz_lift_tiled<<<nblk, kLiftThreads, sizeof(OzLiftCol) * cpb_max, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_split.as<int>(), ctx.hp_inv.as<int>(),
                                           SA.lift.as<int>(), SB.lift.as<int>(), SA.level.as<int8_t>(),
                                           ctx.nballow.as<int>(), ctx.off.as<long long>(), c, ctx.ndet,
                                           ctx.oz_bexp.as<int>(), ctx.oz_bs.as<__nv_bfloat16>()); ISCSI_COUNT_LAUNCH();
