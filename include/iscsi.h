@@ -335,6 +335,29 @@ ISCSI_API iscsi_status iscsi_davidson(int nroots, double tol, double* energies, 
  */
 ISCSI_API iscsi_status iscsi_check_bounded_wait(long long polls);
 
+/*
+ * Self-check of the host-built schedule of the persistent FP64-accurate
+ * contraction (the paper has no counterpart: it is how this library spreads
+ * the opposite-spin products over the SMs).  Host only: needs no context and
+ * no GPU.  Plans nprob synthetic problems T_p[M_p][N_p] = sum over the
+ * problem's segments of A_g B_g^T (inner dimension K_g, B_g with nrows_b_g
+ * valid rows, no screened blocks) for nsm SMs and checks the plan: every
+ * 128 x 64 output tile's K steps covered exactly once, split tiles' parts
+ * numbered in K order on one counter and one run of workspace blocks, no CTA
+ * without work.
+ *   M, N, nseg  host, nprob ints each (M, N in [1, 2^24]; nseg in [1, 64]).
+ *   K, nrows_b  host, sum(nseg) ints each, the segments problem by problem
+ *               (K a multiple of 16 in [0, 2^24]; 1 <= nrows_b <= N).
+ *   nsm         SMs to plan for, in [1, 1024].
+ *   balance     host, 1 double (output): the cost model's mean CTA load over
+ *               the busiest CTA's.
+ *   counts      host, 5 ints (output): CTAs, work items, output tiles, split
+ *               tiles, faults found (0 for a correct plan).
+ * Errors: ISCSI_E_ARG (limits above, more than 2^20 tiles, NULL arrays).
+ */
+ISCSI_API iscsi_status iscsi_check_schedule(int nprob, const int* M, const int* N, const int* nseg, const int* K,
+                                            const int* nrows_b, int nsm, double* balance, int* counts);
+
 /* number of determinants of the current context, or -1 if none */
 ISCSI_API long long iscsi_ndet(void);
 

@@ -52,6 +52,7 @@ def load(build_if_missing=True):
         "iscsi_sigma_noalloc": (c_int, [vp, vp]),
         "iscsi_davidson": (c_int, [c_int, c_d, vp, vp]),
         "iscsi_check_bounded_wait": (c_int, [c_ll]),
+        "iscsi_check_schedule": (c_int, [c_int, vp, vp, vp, vp, vp, c_int, vp, vp]),
         "iscsi_density": (c_int, [vp, vp, vp, vp]),
         "iscsi_propagate": (c_int, [vp, c_int, c_d, vp, c_int, c_int, c_int, vp]),
         "iscsi_density_host": (c_int, [vp, vp, vp, vp]),
@@ -247,6 +248,23 @@ def iscsi_gas_mask(mask):
 def iscsi_check_bounded_wait(polls):
     """The bounded waits' failure path (ISCSI_E_WAIT is the expected status; raises IscsiError with it)."""
     return _check(load().iscsi_check_bounded_wait(int(polls)))
+
+
+def iscsi_check_schedule(problems, nsm):
+    """Plan synthetic contraction problems, each (M, N, [(K, nrows_b), ...]),
+    for nsm SMs and check the plan (host only).  Returns (balance, counts) with
+    counts = {"ctas", "items", "tiles", "split_tiles", "faults"}."""
+    M = np.array([p[0] for p in problems], dtype=np.int32)
+    N = np.array([p[1] for p in problems], dtype=np.int32)
+    nseg = np.array([len(p[2]) for p in problems], dtype=np.int32)
+    K = np.array([g[0] for p in problems for g in p[2]], dtype=np.int32)
+    nrb = np.array([g[1] for p in problems for g in p[2]], dtype=np.int32)
+    bal = np.zeros(1)
+    cnt = np.zeros(5, dtype=np.int32)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(load().iscsi_check_schedule(len(problems), ptr(M), ptr(N), ptr(nseg), ptr(K), ptr(nrb), int(nsm),
+                                       ptr(bal), ptr(cnt)))
+    return float(bal[0]), dict(zip(("ctas", "items", "tiles", "split_tiles", "faults"), (int(x) for x in cnt)))
 
 
 def iscsi_davidson(nroots, tol, vecs=None):

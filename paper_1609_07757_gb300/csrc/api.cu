@@ -304,6 +304,64 @@ iscsi_status iscsi_check_bounded_wait(long long polls) {
   return tc_wait_selftest(*ctx, polls);
 }
 
+iscsi_status iscsi_check_schedule(int nprob, const int* M, const int* N, const int* nseg, const int* K,
+                                  const int* nrows_b, int nsm, double* balance, int* counts) {
+  if (nprob < 1 || nprob > 4096 || !M || !N || !nseg || !K || !nrows_b || nsm < 1 || nsm > 1024 || !balance ||
+      !counts) {
+    set_error("iscsi_check_schedule: invalid argument (1 <= nprob <= 4096, 1 <= nsm <= 1024, non-NULL arrays)");
+    return ISCSI_E_ARG;
+  }
+  static const unsigned char tiled_marker = 0;  // marks segments as tiled (bulk-copy costs); never read
+  const auto* tiled = reinterpret_cast<const __nv_bfloat16*>(&tiled_marker);
+  std::vector<OzProblem> probs(nprob);
+  std::vector<OzSeg> segs;
+  long long tiles = 0;
+  for (int p = 0; p < nprob; ++p) {
+    if (M[p] < 1 || N[p] < 1 || nseg[p] < 1 || nseg[p] > 64 || M[p] > (1 << 24) || N[p] > (1 << 24)) {
+      set_error("iscsi_check_schedule: problem sizes out of range (M, N in [1, 2^24], 1 <= nseg <= 64)");
+      return ISCSI_E_ARG;
+    }
+    OzProblem& P = probs[p];
+    std::memset(&P, 0, sizeof(P));
+    P.M = M[p];
+    P.N = N[p];
+    P.ldt = N[p];
+    P.seg_begin = (int)segs.size();
+    P.seg_count = nseg[p];
+    for (int g = 0; g < nseg[p]; ++g) {
+      const int i = P.seg_begin + g;
+      if (K[i] < 0 || K[i] % OZ_BK || K[i] > (1 << 24) || nrows_b[i] < 1 || nrows_b[i] > N[p]) {
+        set_error("iscsi_check_schedule: segment out of range (K a multiple of 16 in [0, 2^24], 1 <= nrows_b <= N)");
+        return ISCSI_E_ARG;
+      }
+      OzSeg S;
+      std::memset(&S, 0, sizeof(S));
+      S.K = K[i];
+      S.nrows_b = nrows_b[i];
+      S.a_tiled = tiled;
+      S.b_tiled = tiled;
+      segs.push_back(S);
+    }
+    tiles += (long long)((M[p] + OZ_BM - 1) / OZ_BM) * ((N[p] + OZ_BN - 1) / OZ_BN);
+    if (tiles > (1 << 20)) {
+      set_error("iscsi_check_schedule: more than 2^20 output tiles");
+      return ISCSI_E_ARG;
+    }
+  }
+  std::vector<OzSegHost> sh(segs.size());
+  OzPlan plan;
+  int errors = 0;
+  const int s = oz_plan_check(probs, segs, sh, nsm, plan, errors);
+  if (s != kOk) return s;
+  *balance = plan.model_balance;
+  counts[0] = plan.grid;
+  counts[1] = (int)plan.items.size();
+  counts[2] = (int)tiles;
+  counts[3] = plan.counters;
+  counts[4] = errors;
+  return ISCSI_OK;
+}
+
 iscsi_status iscsi_davidson(int nroots, double tol, double* energies, void* vecs) {
   NEED_CTX(ctx);
   if (nroots < 1 || nroots > ctx->gas_ndet || !(tol > 0) || !energies) {

@@ -161,6 +161,11 @@ struct OzPlan {
   double model_balance = 1;    // average over busiest predicted CTA load
   DevBuf d_items, d_cta, d_ws, d_cnt;
 };
+// host only: plan for nsm SMs and count the plan's faults (tiles whose K steps
+// are not covered exactly once in part order, misnumbered parts, workspace
+// slots or counters used other than once, CTAs without work)
+int oz_plan_check(const std::vector<OzProblem>& probs, const std::vector<OzSeg>& segs,
+                  const std::vector<OzSegHost>& sh, int nsm, OzPlan& plan, int& errors);
 int oz_plan_build(const std::vector<OzProblem>& probs, const std::vector<OzSeg>& segs,
                   const std::vector<OzSegHost>& sh, OzPlan& plan, cudaStream_t st);
 

@@ -13,7 +13,12 @@
 //   3. takes back the tiles that would end after the balanced finish time
 //      and cuts them along K into parts that fill the CTAs up to a common
 //      level (water filling), so the last wave ends together; the parts of a
-//      tile are added in part order by whichever finishes last (ozaki.cuh).
+//      tile are added in part order by whichever finishes last (ozaki.cuh);
+//   4. repeats 2-3 with a few take-back thresholds and smallest part sizes
+//      and keeps the plan whose busiest CTA is predicted to end first: when
+//      single tiles come close to the balanced load (short launches), the
+//      CTAs that hold them keep gaps too small for a part unless those tiles
+//      are cut as well.
 // Steps whose blocks are all zero (screened) cost nothing and are never
 // issued, so the schedule follows the screen.
 #include <algorithm>
@@ -99,120 +104,28 @@ class Planner {
       plan.issued_products += products_of(T);
     }
     const int ncta = std::max(1, nsm);  // split-K parts spread small problems over every SM
-    // 2. list scheduling
-    struct Slot {
-      std::vector<OzItem> items;
-      double load = 0.0;
-    };
-    std::vector<Slot> cta(ncta);
-    std::vector<std::vector<int>> tile_of(ncta);  // tile index of each whole item
-    using Q = std::pair<double, int>;
-    std::priority_queue<Q, std::vector<Q>, std::greater<Q>> heap;
-    for (int b = 0; b < ncta; ++b) heap.push({0.0, b});
-    for (int i = 0; i < (int)tiles.size(); ++i) {
-      Q q = heap.top();
-      heap.pop();
-      const Tile& T = tiles[i];
-      cta[q.second].items.push_back({T.prob, T.mt, T.nt, 0, T.nsteps, 0, 1, -1, -1});
-      tile_of[q.second].push_back(i);
-      cta[q.second].load += T.cost;
-      heap.push({cta[q.second].load, q.second});
-    }
-    // 3. take back the tiles ending late, cut them into parts (water filling)
-    const double target = total / ncta;
-    std::vector<int> pool;
-    for (int b = 0; b < ncta; ++b) {
-      while (!cta[b].items.empty() && cta[b].load > target * 1.02) {
-        const int i = tile_of[b].back();
-        pool.push_back(i);
-        cta[b].load -= tiles[i].cost;
-        cta[b].items.pop_back();
-        tile_of[b].pop_back();
+    // Tiles close to the balanced load leave gaps too small for a part, and
+    // a part's fixed cost is large against a short launch: try a few take-back
+    // thresholds and part sizes, keep the plan whose busiest CTA ends first
+    // (the first, least split, unless another ends clearly sooner).
+    const double ovh = kItemOverhead + kPartOverhead;
+    const double variants[][2] = {{1.02, 4.0}, {0.97, 2.0}, {0.9, 2.0}, {0.75, 1.0}, {0.0, 1.0}};
+    std::vector<Slot> best, cur;
+    int best_slots = 0, best_counters = 0;
+    double best_max = 0.0;
+    for (const auto& v : variants) {
+      int slots = 0, counters = 0;
+      const double mx = attempt(tiles, total / ncta, ncta, v[0], v[1] * ovh, cur, slots, counters);
+      if (best.empty() || mx < 0.99 * best_max) {
+        best.swap(cur);
+        best_max = mx;
+        best_slots = slots;
+        best_counters = counters;
       }
     }
-    std::sort(pool.begin(), pool.end());  // banded order again
-    plan.slots = 0;
-    plan.counters = 0;
-    if (!pool.empty()) {
-      std::vector<int> order(ncta);
-      for (int b = 0; b < ncta; ++b) order[b] = b;
-      std::sort(order.begin(), order.end(), [&](int x, int y) { return cta[x].load < cta[y].load; });
-      // Fill the CTAs in order of increasing load up to a common level, each
-      // CTA taking consecutive pieces of the pool (parts of at least min_part:
-      // smaller ones cost more in overhead than they balance); the level is
-      // the lowest at which the pool fits (binary search on a dry run).
-      const double min_part = 4.0 * (kItemOverhead + kPartOverhead);
-      std::vector<std::vector<double>> psc(pool.size());
-      for (size_t q = 0; q < pool.size(); ++q) step_costs(tiles[pool[q]], psc[q]);
-      struct Part {
-        int tile, s0, s1, cta;
-      };
-      std::vector<Part> parts;
-      auto fill = [&](double lev, bool commit) -> bool {
-        std::vector<double> load(ncta);
-        for (int b = 0; b < ncta; ++b) load[b] = cta[b].load;
-        auto room = [&](int b) { return lev - load[b] - kItemOverhead - kPartOverhead; };
-        size_t oi = 0;
-        if (commit) parts.clear();
-        for (size_t q = 0; q < pool.size(); ++q) {
-          const Tile& T = tiles[pool[q]];
-          const std::vector<double>& sc = psc[q];
-          double left = T.cost - kItemOverhead;
-          int s = 0;
-          do {
-            while (oi < order.size() && room(order[oi]) < min_part) ++oi;
-            if (oi == order.size()) return false;
-            const int b = order[oi];
-            const double cap = room(b);
-            int e = s;
-            double got = 0.0;
-            if (left - cap < min_part) {
-              e = T.nsteps;  // the rest of the tile
-              got = left;
-            } else {
-              while (e < T.nsteps && got + sc[e] <= cap) got += sc[e++];
-              if (e == s) got += sc[e++];  // at least one step
-            }
-            if (commit) parts.push_back({pool[q], s, e, b});
-            load[b] += got + kItemOverhead + kPartOverhead;
-            left -= got;
-            s = e;
-          } while (s < T.nsteps);
-        }
-        if (commit)
-          for (int b = 0; b < ncta; ++b) cta[b].load = load[b];
-        return true;
-      };
-      double lo = target, hi = target;
-      for (int rep = 0; rep < 60 && !fill(hi, false); ++rep) hi = hi * 1.25 + min_part;
-      for (int rep = 0; rep < 40; ++rep) {
-        const double mid = 0.5 * (lo + hi);
-        (fill(mid, false) ? hi : lo) = mid;
-      }
-      fill(hi, true);
-      // number the parts of split tiles and hand them to their CTAs
-      for (size_t i = 0; i < parts.size();) {
-        size_t j = i;
-        while (j < parts.size() && parts[j].tile == parts[i].tile) ++j;
-        const int np = (int)(j - i);
-        const Tile& T = tiles[parts[i].tile];
-        for (size_t q = i; q < j; ++q) {
-          OzItem it{T.prob, T.mt, T.nt, parts[q].s0, parts[q].s1, 0, 1, -1, -1};
-          if (np > 1) {
-            it.part = (int)(q - i);
-            it.nparts = np;
-            it.slot = plan.slots;
-            it.cnt = plan.counters;
-          }
-          cta[parts[q].cta].items.push_back(it);
-        }
-        if (np > 1) {
-          plan.slots += np;
-          ++plan.counters;
-        }
-        i = j;
-      }
-    }
+    plan.slots = best_slots;
+    plan.counters = best_counters;
+    std::vector<Slot>& cta = best;
     // flatten (CTAs without items are left out)
     plan.items.clear();
     plan.cta_start.assign(1, 0);
@@ -230,6 +143,133 @@ class Planner {
   }
 
  private:
+  struct Slot {
+    std::vector<OzItem> items;
+    double load = 0.0;
+  };
+
+  // One schedule: list scheduling of whole tiles, then the tiles of CTAs
+  // loaded above thr x target taken back and water-filled in parts of at
+  // least min_part.  Returns the busiest CTA's predicted load.
+  double attempt(const std::vector<Tile>& tiles, double target, int ncta, double thr, double min_part,
+                 std::vector<Slot>& cta, int& slots, int& counters) const {
+    cta.assign(ncta, Slot());
+    std::vector<std::vector<int>> tile_of(ncta);  // tile index of each whole item
+    using Q = std::pair<double, int>;
+    std::priority_queue<Q, std::vector<Q>, std::greater<Q>> heap;
+    for (int b = 0; b < ncta; ++b) heap.push({0.0, b});
+    for (int i = 0; i < (int)tiles.size(); ++i) {
+      Q q = heap.top();
+      heap.pop();
+      const Tile& T = tiles[i];
+      cta[q.second].items.push_back({T.prob, T.mt, T.nt, 0, T.nsteps, 0, 1, -1, -1});
+      tile_of[q.second].push_back(i);
+      cta[q.second].load += T.cost;
+      heap.push({cta[q.second].load, q.second});
+    }
+    std::vector<int> pool;
+    for (int b = 0; b < ncta; ++b) {
+      while (!cta[b].items.empty() && cta[b].load > target * thr) {
+        const int i = tile_of[b].back();
+        pool.push_back(i);
+        cta[b].load -= tiles[i].cost;
+        cta[b].items.pop_back();
+        tile_of[b].pop_back();
+      }
+    }
+    std::sort(pool.begin(), pool.end());  // banded order again
+    slots = 0;
+    counters = 0;
+    if (!pool.empty()) {
+      std::vector<int> order(ncta);
+      for (int b = 0; b < ncta; ++b) order[b] = b;
+      std::sort(order.begin(), order.end(),
+                [&](int x, int y) { return cta[x].load < cta[y].load || (cta[x].load == cta[y].load && x < y); });
+      // Fill the CTAs in order of increasing load up to a common level, each
+      // CTA taking consecutive pieces of the pool; the level is the lowest at
+      // which the pool fits (binary search on a dry run).
+      std::vector<std::vector<double>> psc(pool.size());
+      for (size_t q = 0; q < pool.size(); ++q) step_costs(tiles[pool[q]], psc[q]);
+      struct Part {
+        int tile, s0, s1, cta;
+      };
+      std::vector<Part> parts;
+      std::vector<double> load(ncta);
+      auto fill = [&](double lev, bool commit) -> bool {
+        for (int b = 0; b < ncta; ++b) load[b] = cta[b].load;
+        auto room = [&](int b) { return lev - load[b] - kItemOverhead - kPartOverhead; };
+        size_t oi = 0;
+        if (commit) parts.clear();
+        for (size_t q = 0; q < pool.size(); ++q) {
+          const Tile& T = tiles[pool[q]];
+          const std::vector<double>& sc = psc[q];
+          double left = T.cost - kItemOverhead;
+          int s = 0;
+          do {
+            while (oi < order.size() && room(order[oi]) < min_part) ++oi;
+            if (oi == order.size()) return false;
+            const int b = order[oi];
+            const double cap = room(b);
+            int e = s;
+            double got = 0.0;
+            // what is left of the tile fits; or would leave less than a part
+            // behind (the rest of a small tile goes whole; of a larger one, a
+            // part of min_part stays for the next CTA); or is cut at the level
+            const double want = left <= cap ? left : left - cap >= min_part ? cap : left >= 2.0 * min_part ? left - min_part : left;
+            if (want >= left) {
+              e = T.nsteps;
+              got = left;
+            } else {
+              while (e < T.nsteps && got + sc[e] <= want) got += sc[e++];
+              if (e == s) got += sc[e++];  // at least one step
+            }
+            if (commit) parts.push_back({pool[q], s, e, b});
+            load[b] += got + kItemOverhead + kPartOverhead;
+            left -= got;
+            s = e;
+          } while (s < T.nsteps);
+        }
+        return true;
+      };
+      double lo = target, hi = target;
+      for (int rep = 0; rep < 60 && !fill(hi, false); ++rep) hi = hi * 1.25 + min_part;
+      for (int rep = 0; rep < 40; ++rep) {
+        const double mid = 0.5 * (lo + hi);
+        (fill(mid, false) ? hi : lo) = mid;
+      }
+      fill(hi, true);
+      for (int b = 0; b < ncta; ++b) cta[b].load = load[b];
+      // number the parts of split tiles and hand them to their CTAs
+      for (size_t i = 0; i < parts.size();) {
+        size_t j = i;
+        while (j < parts.size() && parts[j].tile == parts[i].tile) ++j;
+        const int np = (int)(j - i);
+        const Tile& T = tiles[parts[i].tile];
+        for (size_t q = i; q < j; ++q) {
+          OzItem it{T.prob, T.mt, T.nt, parts[q].s0, parts[q].s1, 0, 1, -1, -1};
+          if (np > 1) {
+            it.part = (int)(q - i);
+            it.nparts = np;
+            it.slot = slots;
+            it.cnt = counters;
+          } else {
+            load[parts[q].cta] -= kPartOverhead;  // a whole tile has no partial block
+          }
+          cta[parts[q].cta].items.push_back(it);
+        }
+        if (np > 1) {
+          slots += np;
+          ++counters;
+        }
+        i = j;
+      }
+      for (int b = 0; b < ncta; ++b) cta[b].load = load[b];
+    }
+    double mx = 0.0;
+    for (int b = 0; b < ncta; ++b) mx = std::max(mx, cta[b].load);
+    return mx;
+  }
+
   // bf16 slice products of a whole tile (x 2 M N K per step)
   double products_of(const Tile& T) const {
     const OzProblem& P = probs_[T.prob];
@@ -265,6 +305,75 @@ int sm_count() {
 }
 
 }  // namespace
+
+int oz_plan_check(const std::vector<OzProblem>& probs, const std::vector<OzSeg>& segs,
+                  const std::vector<OzSegHost>& sh, int nsm, OzPlan& plan, int& errors) {
+  if (sh.size() != segs.size() || nsm < 1) {
+    set_error("tensor-core schedule check: segment host records missing or no SMs");
+    return kErrArg;
+  }
+  Planner pl(probs, segs, sh);
+  ISCSI_TRY(pl.build(nsm, plan));
+  errors = 0;
+  const int nitems = (int)plan.items.size();
+  if (plan.grid < 1 || plan.grid > nsm || (int)plan.cta_start.size() != plan.grid + 1 || plan.cta_start[0] != 0 ||
+      plan.cta_start[plan.grid] != nitems)
+    ++errors;
+  for (int b = 0; b < plan.grid && !errors; ++b)
+    if (plan.cta_start[b + 1] <= plan.cta_start[b]) ++errors;  // no CTA runs without work
+  // every tile's K steps exactly once; a split tile's parts numbered in K
+  // order, sharing one counter and one run of workspace slots
+  std::vector<std::vector<const OzItem*>> of_tile;
+  std::vector<long long> first_tile(probs.size() + 1, 0);
+  for (size_t p = 0; p < probs.size(); ++p) {
+    const long long tm = (probs[p].M + OZ_BM - 1) / OZ_BM, tn = (probs[p].N + OZ_BN - 1) / OZ_BN;
+    first_tile[p + 1] = first_tile[p] + tm * tn;
+  }
+  of_tile.resize(first_tile.back());
+  for (const OzItem& it : plan.items) {
+    if (it.prob < 0 || it.prob >= (int)probs.size()) {
+      ++errors;
+      continue;
+    }
+    const OzProblem& P = probs[it.prob];
+    const int tn = (P.N + OZ_BN - 1) / OZ_BN, tm = (P.M + OZ_BM - 1) / OZ_BM;
+    if (it.mt < 0 || it.mt >= tm || it.nt < 0 || it.nt >= tn) {
+      ++errors;
+      continue;
+    }
+    of_tile[first_tile[it.prob] + (long long)it.mt * tn + it.nt].push_back(&it);
+  }
+  std::vector<int> slot_used(std::max(0, plan.slots), 0), cnt_used(std::max(0, plan.counters), 0);
+  for (size_t p = 0; p < probs.size(); ++p) {
+    int nsteps = 0;
+    for (int g = 0; g < probs[p].seg_count; ++g) nsteps += segs[probs[p].seg_begin + g].K / OZ_BK;
+    for (long long t = first_tile[p]; t < first_tile[p + 1]; ++t) {
+      std::vector<const OzItem*>& v = of_tile[t];
+      std::sort(v.begin(), v.end(), [](const OzItem* x, const OzItem* y) { return x->s0 < y->s0; });
+      const int np = (int)v.size();
+      int s = 0;
+      bool ok = np > 0;
+      for (int q = 0; q < np && ok; ++q) {
+        const OzItem& it = *v[q];
+        ok = it.s0 == s && (it.s1 > it.s0 || nsteps == 0) && it.s1 <= nsteps;
+        s = it.s1;
+        if (np == 1) {
+          ok = ok && it.nparts == 1;
+        } else {
+          ok = ok && it.nparts == np && it.part == q && it.slot == v[0]->slot && it.cnt == v[0]->cnt &&
+               it.slot >= 0 && it.slot + np <= plan.slots && it.cnt >= 0 && it.cnt < plan.counters;
+          if (ok) ++slot_used[it.slot + q];
+        }
+      }
+      ok = ok && s == nsteps;
+      if (ok && np > 1) ++cnt_used[v[0]->cnt];
+      if (!ok) ++errors;
+    }
+  }
+  for (int x : slot_used) errors += x != 1;
+  for (int x : cnt_used) errors += x != 1;
+  return kOk;
+}
 
 int oz_plan_build(const std::vector<OzProblem>& probs, const std::vector<OzSeg>& segs,
                   const std::vector<OzSegHost>& sh, OzPlan& plan, cudaStream_t st) {

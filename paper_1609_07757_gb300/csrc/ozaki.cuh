@@ -183,6 +183,26 @@ constexpr uint32_t OZ_INFO_END = 1u << 9;          // no step: the CTA's work is
 // that stage as a data step and then waited for a step that never came.
 __device__ __forceinline__ uint32_t oz_info_seq(int g) { return ((uint32_t)g & 0xFFFFu) << 16; }
 
+// W x W transpose (W a power of two up to 32) within each group of W lanes:
+// lane i of a group holds row i of the group's block on entry and column i on
+// return (butterfly exchanges over lane distances W/2, ..., 1).  The epilogue
+// holds one output row per thread; after this, each store instruction writes
+// runs of W consecutive doubles instead of 32 scattered 8-byte words.
+template <int W>
+__device__ __forceinline__ void oz_lane_transpose(double (&a)[W], int lane) {
+#pragma unroll
+  for (int s = W / 2; s >= 1; s >>= 1) {
+    const bool hi = (lane & s) != 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      if (j & s) continue;
+      const double recv = __shfl_xor_sync(0xffffffffu, hi ? a[j] : a[j ^ s], s);
+      if (hi) a[j] = recv;
+      else a[j ^ s] = recv;
+    }
+  }
+}
+
 // Accumulators restart without a separate clearing pass: the MMA thread keeps
 // a mask of the levels written since their last drain, and the first MMA that
 // writes a level uses accumulate = 0 (a run of levels whose written state
@@ -610,13 +630,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             // meanwhile).  Everything read from global memory is loaded into
             // registers first, eight columns at a time: the stores below could
             // alias it, and a chain of dependent reloads would cost far longer
-            // than the chunks of MMAs it overlaps.
+            // than the chunks of MMAs it overlaps.  A split tile's part block
+            // is column-major (the 32 rows of a warp are one contiguous run per
+            // column), so the part's writes and the combining reads coalesce.
             const int Mp = P.M, Np = P.N, nrb = S.nrows_b;
             const long long ldt = P.ldt;
             const bool addT = P.accumulate || wrote;
             const int* __restrict__ bexp = S.b_exp;
             const int ea = gm < Mp ? __ldg(S.a_exp + gm) : 0;
-            double* const rowT = part_base ? part_base + row * OZ_BN + cbase : Tp + (long long)gm * ldt;
+            double* const rowT = part_base ? part_base + cbase * OZ_BM + row : Tp + (long long)gm * ldt;
 #pragma unroll
             for (int c0 = 0; c0 < OZ_EPI_COLS; c0 += 8) {
               uint32_t tl[8];
@@ -630,7 +652,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 eb[j] = in ? __ldg(bexp + gn) : 0;
                 old[j] = 0.0;
                 if (part_base) {
-                  if (wrote) old[j] = rowT[c0 + j];
+                  if (wrote) old[j] = rowT[(c0 + j) * OZ_BM];
                 } else if (in && addT) {
                   old[j] = rowT[gn];
                 }
@@ -648,7 +670,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                       sums[c0 + j] + __float2ll_rn(__uint_as_float(tl[j]) * 268435456.0f /* 2^28 */);
                   v = oz_i64_scaled(q, ea + eb[j] - 14 - 28);
                 }
-                if (part_base) rowT[c0 + j] = old[j] + v;
+                if (part_base) rowT[(c0 + j) * OZ_BM] = old[j] + v;
                 else if (in) rowT[gn] = old[j] + v;
                 sums[c0 + j] = 0;
               }
@@ -662,7 +684,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         // no step of this item survived: its part (or tile) is zero
         for (int j = 0; j < OZ_EPI_COLS; ++j) {
           const int gn = n0 + cbase + j;
-          if (part_base) part_base[row * OZ_BN + cbase + j] = 0.0;
+          if (part_base) part_base[(cbase + j) * OZ_BM + row] = 0.0;
           else if (!P.accumulate && gm < P.M && gn < P.N) Tp[(long long)gm * P.ldt + gn] = 0.0;
         }
       }
@@ -674,16 +696,33 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         if (!epi_sync()) break;
         // every thread reads last_s before any reaches the next item's first epi_sync
         if (last_s) {
+          // parts summed in part order (the result does not depend on which
+          // part finished last), eight columns at a time, then turned across
+          // the lane octets for row-major runs in T
           __threadfence();
           const double* slot = ws + (long long)I.slot * (OZ_BM * OZ_BN);
-          for (int j = 0; j < OZ_EPI_COLS; ++j) {
-            const int gn = n0 + cbase + j;
-            double v = 0.0;
-            for (int q = 0; q < I.nparts; ++q) v += __ldcg(slot + (long long)q * (OZ_BM * OZ_BN) + row * OZ_BN + cbase + j);
-            if (gm < P.M && gn < P.N) {
-              double* dst = Tp + (long long)gm * P.ldt + gn;
-              *dst = P.accumulate ? *dst + v : v;
+          const int rb = m0 + quarter * 32 + (lane & ~7);
+#pragma unroll
+          for (int c0 = 0; c0 < OZ_EPI_COLS; c0 += 8) {
+            double v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = 0.0;
+#pragma unroll 2
+            for (int q = 0; q < I.nparts; ++q) {
+              const double* src = slot + (long long)q * (OZ_BM * OZ_BN) + (cbase + c0) * OZ_BM + row;
+#pragma unroll
+              for (int j = 0; j < 8; ++j) v[j] += __ldcg(src + j * OZ_BM);
             }
+            oz_lane_transpose<8>(v, lane);  // v[k]: row rb + k, column gnt
+            const int gnt = n0 + cbase + c0 + (lane & 7);
+            const bool cin = gnt < P.N;
+            double old[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              old[k] = P.accumulate && cin && rb + k < P.M ? Tp[(long long)(rb + k) * P.ldt + gnt] : 0.0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (cin && rb + k < P.M) Tp[(long long)(rb + k) * P.ldt + gnt] = old[k] + v[k];
           }
           if (threadIdx.x == 64) ws_cnt[I.cnt] = 0;  // ready for the next launch
         }

@@ -132,7 +132,7 @@ struct OzProblem {
 // One work item of the persistent contraction: the output tile (mt, nt) of
 // problem prob over the K steps [s0, s1) of its segments taken in order.  A
 // tile cut into nparts > 1 items (split K) leaves part p's FP64 result in
-// workspace block slot + p (128 x 64 doubles each); the part that raises
+// workspace block slot + p (128 x 64 doubles each, column-major); the part that raises
 // counter cnt to nparts adds the blocks in part order into T and resets it.
 struct OzItem {
   int prob, mt, nt;
