@@ -468,7 +468,12 @@ ISCSI_API void iscsi_finalize(void);
  * caller owns them).  The precision option applies to all.  The tensor-core
  * contractions of all contexts run as one launch each; from the second call
  * with the same handles, pointers, nvec and precision the whole batch is
- * replayed from one captured CUDA graph (option "use_graph").  Asynchronous
+ * replayed from one captured CUDA graph (option "use_graph").  The FP64
+ * contraction's schedule covers the whole launch and may cut a tile along K
+ * at other points than a single-context call would (each part is rounded to
+ * FP64 before the parts are added), so sigma_i agrees with iscsi_sigma on
+ * context i to FP64 rounding, not bit for bit; calls of one batch reproduce
+ * each other exactly.  Asynchronous
  * on the library stream; the current context is unchanged.  A bounded
  * device wait that runs out in a merged launch is reported by
  * iscsi_batch_check.

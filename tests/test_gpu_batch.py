@@ -1,8 +1,13 @@
 """GPU: the batching form (iscsi_batch_sigma) against one-at-a-time sigma.
 
-The batch runs the same kernels on the same tiles as the single-context call
-(only the launch grouping differs), so its result is bit-identical; the first
-call runs directly, the second captures a CUDA graph, later calls replay it.
+The batch runs the same kernels on the same tiles as the single-context call;
+only the launch grouping differs.  The FP64-accurate contraction's schedule is
+planned over the whole launch, so a tile may be cut along K at other points
+than in the single-context launch: each part is rounded to FP64 before the
+parts are added, and the two results agree to the FP64 bar (1e-12 of the
+largest element and of the 2-norm), not bit for bit.  Calls of one batch
+reproduce each other exactly: the first runs directly, the second captures a
+CUDA graph, later calls replay it.
 """
 import numpy as np
 import pytest
@@ -65,6 +70,8 @@ def test_batch_sigma_matches_single_contexts(precision, nvec, graph):
         ref.append(s)
     torch.cuda.synchronize()
     outs = [torch.full_like(c, np.nan) for c in cs]
+    rel = 1e-12 if precision == 64 else 2e-5
+    first = None
     for call in range(3):  # direct, captured, replayed
         for o in outs:
             o.fill_(np.nan)
@@ -72,7 +79,13 @@ def test_batch_sigma_matches_single_contexts(precision, nvec, graph):
         torch.cuda.synchronize()
         L.iscsi_batch_check()
         for o, r in zip(outs, ref):
-            assert torch.equal(o, r), call
+            d = (o - r).abs()
+            assert d.max().item() <= rel * r.abs().max().item(), (call, d.max().item())
+            assert torch.linalg.norm(o - r).item() <= rel * torch.linalg.norm(r).item(), call
+        if first is None:
+            first = [o.clone() for o in outs]
+        else:
+            assert all(torch.equal(o, f) for o, f in zip(outs, first)), call
     assert L.iscsi_ctx_current() == hs[-1]
 
 
