@@ -998,10 +998,12 @@ def run_gas(name, steps=10, warmup=3, with_cpu=True, projected=True):
     s = torch.empty_like(c)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def timed():
+    def timed(phases=False):
         for _ in range(max(3, warmup)):
             L.iscsi_sigma(c, s, 1)
         torch.cuda.synchronize()
+        if phases:  # per-phase events of the timed calls only (restarts the record)
+            L.iscsi_set_option("phase_timing", 1)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for k in range(steps):
             flush.zero_()
@@ -1040,8 +1042,7 @@ def run_gas(name, steps=10, warmup=3, with_cpu=True, projected=True):
     ndet_ctx = L.iscsi_ndet()
     c = torch.tensor(unit_vector(ndet_ctx, 31), dtype=torch.float64, device="cuda")
     s = torch.empty_like(c)
-    L.iscsi_set_option("phase_timing", 1)
-    ms_ctx = timed()
+    ms_ctx = timed(phases=True)
     st_t = L.iscsi_stats()
     L.iscsi_set_option("phase_timing", 0)
     upd_ctx = L.iscsi_updates_per_sigma()
