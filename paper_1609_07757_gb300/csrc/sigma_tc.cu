@@ -59,14 +59,10 @@ struct TcTable {
 static inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 
-// One block per column (X, Y, v) of Ct^T over all classes.  The column's lift
-// entries for every orbital (a+_q |X> and a+_s |Y>: target string and sign,
-// and the target alpha string's offset and allowed beta count) are staged in
-// shared memory first, so an element (q, s) costs the pair table and c.  The
-// K values are gathered once (kOzRowRegs per thread in registers; a longer K
-// is gathered again beyond that), the column's exponent (frexp of the largest
-// |x|, 0 for an all-zero column) is taken and its exact slices written.
-constexpr int kOzRowRegs = 24;
+// A column (X, Y, v) of Ct^T: its lift entries for every orbital (a+_q |X> and
+// a+_s |Y>: target string and sign, and the target alpha string's offset and
+// allowed beta count) are staged in shared memory first, so an element (q, s)
+// costs the pair table and c.
 struct OzLiftCol {
   int a[kMaxOrb], b[kMaxOrb], lim[kMaxOrb];
   long long off[kMaxOrb];
@@ -117,13 +113,16 @@ __device__ __forceinline__ int oz_stage_column(const TcTable& tt, int n, int nho
 // The lifted column (X, Y, v) of class c, cut into tiled slices: a column is
 // walked by C.wpc warps of the block's eight (each a share of the K range, in
 // 8-wide chunks per lane: eight independent gathers in flight), which first
-// find the column's exponent (largest |x|; the warps' maxima meet in shared
-// memory), then gather their chunks again, cut each into exact slices and
-// write every slice's chunk as one 16-byte store.  Long columns take eight
-// warps (one warp per column left most SMs with a few warps waiting on
-// gathers), short ones one (8 columns per block: a K of 256 is 32 chunks, one
-// per lane).  Columns beyond the class stay zero.
+// find the column's exponent (frexp of the largest |x|, 0 for an all-zero
+// column; the warps' maxima meet in shared memory), then cut each chunk into
+// exact slices and write every slice's chunk as one 16-byte store.  A lane's
+// first kLiftKeep chunks stay in registers between the two passes (all of a
+// full-CI n = 60 column); chunks beyond them are gathered again.  Long columns
+// take eight warps (one warp per column left most SMs with a few warps
+// waiting on gathers), short ones one (8 columns per block: a K of 256 is 32
+// chunks, one per lane).  Columns beyond the class stay zero.
 constexpr int kLiftThreads = 256;
+constexpr int kLiftKeep = 2;
 __host__ __device__ constexpr int oz_lift_wpc(int kpad) {
   // 8-wide chunks of the column, at least 48 per warp
   return kpad / 8 >= 384 ? 8 : kpad / 8 >= 192 ? 4 : kpad / 8 >= 96 ? 2 : 1;
@@ -168,12 +167,24 @@ __global__ void __launch_bounds__(kLiftThreads) k_oz_lift_tiled(TcTable tt, int 
   __syncthreads();
   const double* cv = c + (long long)vv * ndet;
   const int kst = C.kpad / OZ_BK;
+  const int kc0 = wk * 32 + lane, kstride = 32 * wpc, nch = 2 * kst;
+  double keep[kLiftKeep][8];
   int m = 0;
-  if (live)
-    for (int kc = wk * 32 + lane; kc < 2 * kst; kc += 32 * wpc) {
+  if (live) {
+#pragma unroll
+    for (int i = 0; i < kLiftKeep; ++i) {
+      const int kc = kc0 + i * kstride;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        keep[i][j] = kc < nch ? oz_lift_value<double>(L, C, kc * 8 + j, pair_split, cv) : 0.0;
+        m = max(m, oz_exp_field(keep[i][j]));
+      }
+    }
+    for (int kc = kc0 + kLiftKeep * kstride; kc < nch; kc += kstride) {
 #pragma unroll
       for (int j = 0; j < 8; ++j) m = max(m, oz_exp_field(oz_lift_value<double>(L, C, kc * 8 + j, pair_split, cv)));
     }
+  }
   m = __reduce_max_sync(0xffffffffu, m);
   if (lane == 0) mx[warp] = m;
   __syncthreads();
@@ -182,12 +193,13 @@ __global__ void __launch_bounds__(kLiftThreads) k_oz_lift_tiled(TcTable tt, int 
   const int ex = m > 0 ? m - 1022 : 0;
   if (wk == 0 && lane == 0) exps[C.exp_off + col] = ex;
   __nv_bfloat16* tile0 = bs + C.bs_off + (long long)(col / OZ_BN) * kst * OZ_TB_BLOCK;
-  for (int kc = wk * 32 + lane; kc < 2 * kst; kc += 32 * wpc) {
+  // exact slices of one chunk, each slice's 8 values as one 16-byte store
+  auto cut = [&](const double (&x)[8], int kc) {
     uint32_t pk[OZ_S][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       int a[OZ_S];
-      oz_digits(oz_lift_value<double>(L, C, kc * 8 + j, pair_split, cv), ex, a);
+      oz_digits(x[j], ex, a);
 #pragma unroll
       for (int sl = 0; sl < OZ_S; ++sl) {
         const uint32_t b = oz_digit_bits(a[sl], sl);
@@ -199,6 +211,15 @@ __global__ void __launch_bounds__(kLiftThreads) k_oz_lift_tiled(TcTable tt, int 
 #pragma unroll
     for (int sl = 0; sl < OZ_S; ++sl)
       *reinterpret_cast<uint4*>(base + sl * OZ_BN * OZ_BK) = make_uint4(pk[sl][0], pk[sl][1], pk[sl][2], pk[sl][3]);
+  };
+#pragma unroll
+  for (int i = 0; i < kLiftKeep; ++i)
+    if (kc0 + i * kstride < nch) cut(keep[i], kc0 + i * kstride);
+  for (int kc = kc0 + kLiftKeep * kstride; kc < nch; kc += kstride) {
+    double x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = oz_lift_value<double>(L, C, kc * 8 + j, pair_split, cv);
+    cut(x, kc);
   }
 }
 
