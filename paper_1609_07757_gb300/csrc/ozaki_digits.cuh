@@ -24,14 +24,25 @@ __device__ __forceinline__ void oz_digits(double v, int e, int (&a)[OZ_S]) {
     else if (sh > -63) N = (m + (1ll << (-sh - 1))) >> (-sh);
     if (bits < 0) N = -N;
   }
+  // the digits in 32-bit halves, N = hi 2^28 + lo with 0 <= lo < 2^28: a digit
+  // of x is (x + 64 mod 128) - 64 and leaves floor((x + 64) / 128); the low
+  // half's four digits leave a carry of 0 or 1 for the high half
+  static_assert(OZ_S == 7, "four digits in the low 28 bits, two and a[0] in the rest");
+  int x = (int)(N & 0x0FFFFFFFll);
 #pragma unroll
-  for (int t = OZ_S - 1; t >= 1; --t) {
-    int r = (int)(N & 127);
-    if (r >= 64) r -= 128;
-    a[t] = r;
-    N = (N - r) >> 7;
+  for (int t = OZ_S - 1; t >= OZ_S - 4; --t) {
+    const int s = x + 64;
+    a[t] = (s & 127) - 64;
+    x = s >> 7;
   }
-  a[0] = (int)N;
+  x += (int)(N >> 28);
+#pragma unroll
+  for (int t = OZ_S - 5; t >= 1; --t) {
+    const int s = x + 64;
+    a[t] = (s & 127) - 64;
+    x = s >> 7;
+  }
+  a[0] = x;
 }
 
 __device__ __forceinline__ void oz_store_digits(const int (&a)[OZ_S], __nv_bfloat16* out, long long slice_stride) {

@@ -68,8 +68,24 @@ struct OzLiftCol {
   long long off[kMaxOrb];
 };
 
-template <typename V>
-__device__ __forceinline__ V oz_lift_value(const OzLiftCol& L, const TcClass& C, int k,
+// the same entries laid out for n orbitals (off[n], then a[n], b[n], lim[n]),
+// as the tiled lift stages them in dynamic shared memory
+struct OzLiftView {
+  long long* off;
+  int *a, *b, *lim;
+};
+__device__ __forceinline__ OzLiftView oz_lift_view(unsigned char* base, int n) {
+  OzLiftView v;
+  v.off = reinterpret_cast<long long*>(base);
+  v.a = reinterpret_cast<int*>(base + 8 * n);
+  v.b = v.a + n;
+  v.lim = v.b + n;
+  return v;
+}
+__host__ __device__ constexpr int oz_lift_col_bytes(int n) { return (20 * n + 7) / 8 * 8; }
+
+template <typename V, typename Tab>
+__device__ __forceinline__ V oz_lift_value(const Tab& L, const TcClass& C, int k,
                                            const int* __restrict__ pair_split, const V* __restrict__ cv) {
   if (k >= C.krows) return (V)0;
   const int qs = __ldg(pair_split + k);
@@ -135,10 +151,11 @@ __global__ void __launch_bounds__(kLiftThreads) k_oz_lift_tiled(TcTable tt, int 
                                                        const long long* __restrict__ off, const double* __restrict__ c,
                                                        long long ndet, int* __restrict__ exps,
                                                        __nv_bfloat16* __restrict__ bs) {
-  // the staged lift tables of the block's columns (dynamic: as many as the
-  // launch's largest columns-per-block needs, so that long columns leave the
-  // SM's L1 to the gathers)
-  extern __shared__ OzLiftCol Ls[];
+  // the staged lift tables of the block's columns (dynamic: n entries for as
+  // many columns as the launch's largest columns-per-block needs, so that
+  // long columns leave the SM's L1 to the gathers and short ones leave room
+  // for more blocks)
+  extern __shared__ __align__(16) unsigned char lift_tabs[];
   __shared__ int mx[8];
   int cl = 0;
   while ((int)blockIdx.x >= tt.blk_start[cl + 1]) ++cl;
@@ -148,7 +165,7 @@ __global__ void __launch_bounds__(kLiftThreads) k_oz_lift_tiled(TcTable tt, int 
   const int wc = warp / wpc, wk = warp % wpc;  // column in the block, share of K
   const int col = ((int)blockIdx.x - tt.blk_start[cl]) * cpb + wc;
   const bool live = col < C.ncols;  // no early return: the block meets below
-  OzLiftCol& L = Ls[wc];
+  const OzLiftView L = oz_lift_view(lift_tabs + wc * oz_lift_col_bytes(n), n);
   const int hp = live ? col / tt.nvec : 0, vv = live ? col - hp * tt.nvec : 0;
   if (live) {
     const int xy = hp_inv[C.hp_start + hp];
@@ -513,7 +530,7 @@ int opposite_tc_operands(Context& ctx, const double* c, double* ttw, int nvec) {
   if (nblk > 0) {
     int cpb_max = 1;
     for (int i = 0; i < tt.nclass; ++i) cpb_max = std::max(cpb_max, 8 / tt.c[i].wpc);
-    k_oz_lift_tiled<<<nblk, kLiftThreads, sizeof(OzLiftCol) * cpb_max, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_split.as<int>(), ctx.hp_inv.as<int>(),
+    k_oz_lift_tiled<<<nblk, kLiftThreads, oz_lift_col_bytes(ctx.n) * cpb_max, st>>>(tt, ctx.n, SA.nhole, SB.nhole, ctx.pair_split.as<int>(), ctx.hp_inv.as<int>(),
                                           SA.lift.as<int>(), SB.lift.as<int>(), SA.level.as<int8_t>(),
                                           ctx.nballow.as<int>(), ctx.off.as<long long>(), c, ctx.ndet,
                                           ctx.oz_bexp.as<int>(), ctx.oz_bs.as<__nv_bfloat16>()); ISCSI_COUNT_LAUNCH();
