@@ -107,7 +107,9 @@ class Planner {
     // Tiles close to the balanced load leave gaps too small for a part, and
     // a part's fixed cost is large against a short launch: try a few take-back
     // thresholds and part sizes, keep the plan whose busiest CTA ends first
-    // (the first, least split, unless another ends clearly sooner).
+    // (the first, least split, unless another ends clearly sooner).  A first
+    // plan within 1.5 % of the balanced load is kept as it is (large launches,
+    // whose plans are also rebuilt most often: batches of many contexts).
     const double ovh = kItemOverhead + kPartOverhead;
     const double variants[][2] = {{1.02, 4.0}, {0.97, 2.0}, {0.9, 2.0}, {0.75, 1.0}, {0.0, 1.0}};
     std::vector<Slot> best, cur;
@@ -122,6 +124,7 @@ class Planner {
         best_slots = slots;
         best_counters = counters;
       }
+      if (best_max * 0.985 <= total / ncta) break;
     }
     plan.slots = best_slots;
     plan.counters = best_counters;
@@ -187,9 +190,9 @@ class Planner {
                 [&](int x, int y) { return cta[x].load < cta[y].load || (cta[x].load == cta[y].load && x < y); });
       // Fill the CTAs in order of increasing load up to a common level, each
       // CTA taking consecutive pieces of the pool; the level is the lowest at
-      // which the pool fits (binary search on a dry run).
+      // which the pool fits (binary search on a dry run).  Step costs are
+      // taken only for the tiles that get cut.
       std::vector<std::vector<double>> psc(pool.size());
-      for (size_t q = 0; q < pool.size(); ++q) step_costs(tiles[pool[q]], psc[q]);
       struct Part {
         int tile, s0, s1, cta;
       };
@@ -202,7 +205,7 @@ class Planner {
         if (commit) parts.clear();
         for (size_t q = 0; q < pool.size(); ++q) {
           const Tile& T = tiles[pool[q]];
-          const std::vector<double>& sc = psc[q];
+          std::vector<double>& sc = psc[q];
           double left = T.cost - kItemOverhead;
           int s = 0;
           do {
@@ -220,6 +223,7 @@ class Planner {
               e = T.nsteps;
               got = left;
             } else {
+              if (sc.empty()) step_costs(T, sc);
               while (e < T.nsteps && got + sc[e] <= want) got += sc[e++];
               if (e == s) got += sc[e++];  // at least one step
             }
