@@ -107,9 +107,11 @@ class Planner {
     // Tiles close to the balanced load leave gaps too small for a part, and
     // a part's fixed cost is large against a short launch: try a few take-back
     // thresholds and part sizes, keep the plan whose busiest CTA ends first
-    // (the first, least split, unless another ends clearly sooner).  A first
-    // plan within 1.5 % of the balanced load is kept as it is (large launches,
-    // whose plans are also rebuilt most often: batches of many contexts).
+    // (the first, least split, unless another ends at least 1 % sooner).  No
+    // plan ends before the balanced load (parts only add overhead), so a first
+    // plan within 1 % of it cannot be replaced and the others are not tried
+    // (large launches, whose plans are also rebuilt most often: batches of
+    // many contexts).
     const double ovh = kItemOverhead + kPartOverhead;
     const double variants[][2] = {{1.02, 4.0}, {0.97, 2.0}, {0.9, 2.0}, {0.75, 1.0}, {0.0, 1.0}};
     std::vector<Slot> best, cur;
@@ -124,7 +126,7 @@ class Planner {
         best_slots = slots;
         best_counters = counters;
       }
-      if (best_max * 0.985 <= total / ncta) break;
+      if (best_max * 0.99 <= total / ncta) break;
     }
     plan.slots = best_slots;
     plan.counters = best_counters;
